@@ -1,0 +1,235 @@
+"""FP64 CPU oracle for the restricted-domain dual TV segmentation (arXiv 1807.11534).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``.  The product path (the CUDA
+library and its binding) never imports it, and it shares no code with them.
+
+The arithmetic lives in plain C (``seg_oracle.c``, compiled with FMA
+contraction off so every FP64 operation is one IEEE rounding); this module
+only compiles it and marshals numpy arrays in and out.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "seg_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc).
+
+    SEG_ORACLE_LIB names a prebuilt copy instead (used to check that the pins
+    fail on a deliberately mutated oracle)."""
+    if os.environ.get("SEG_ORACLE_LIB"):
+        return os.environ["SEG_ORACLE_LIB"]
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    hdr = os.path.join(_HERE, "seg_oracle.h")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        I, L, D, F = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_float
+        lib.oracle_fitting.argtypes = [P, I, I, D, D, P, I, D, P, P]
+        lib.oracle_fitting.restype = None
+        lib.oracle_class_means.argtypes = [P, P, L, P, P]
+        lib.oracle_class_means.restype = None
+        lib.oracle_quantile_delta.argtypes = [P, L, D]
+        lib.oracle_quantile_delta.restype = F
+        lib.oracle_domain.argtypes = [P, L, F, P]
+        lib.oracle_domain.restype = None
+        lib.oracle_pixel_list.argtypes = [P, L, P]
+        lib.oracle_pixel_list.restype = L
+        lib.oracle_tile_list.argtypes = [P, I, I, I, I, P]
+        lib.oracle_tile_list.restype = L
+        lib.oracle_grad.argtypes = [P, I, I, P, P]
+        lib.oracle_grad.restype = None
+        lib.oracle_div.argtypes = [P, P, I, I, P]
+        lib.oracle_div.restype = None
+        lib.oracle_solve.argtypes = [P, I, I, P, D, D, D, I, I, D, I, P, P, P, P, P]
+        lib.oracle_solve.restype = I
+        lib.oracle_energy.argtypes = [P, P, P, P, P, I, I, D, D, P]
+        lib.oracle_energy.restype = None
+        lib.oracle_errors.argtypes = [P, P, L, D, P]
+        lib.oracle_errors.restype = None
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+# ------------------------------------------------------------------ wrappers
+
+def fitting(z, c1, c2, markers=None, gamma=0.0):
+    """Eq. CV / Eq. DS in FP64; returns (f64, f32) with f32 = round(f64)."""
+    lib = _load()
+    z = _c(z, np.float32)
+    H, W = z.shape
+    m = _c(markers if markers is not None else np.zeros((0, 2)), np.int32).reshape(-1, 2)
+    f64 = np.empty((H, W), np.float64)
+    f32 = np.empty((H, W), np.float32)
+    lib.oracle_fitting(_ptr(z), H, W, float(c1), float(c2), _ptr(m) if len(m) else None,
+                       len(m), float(gamma), _ptr(f64), _ptr(f32))
+    return f64, f32
+
+
+def class_means(z, label):
+    lib = _load()
+    z = _c(z, np.float32)
+    lab = _c(label, np.uint8)
+    c1, c2 = ctypes.c_double(), ctypes.c_double()
+    lib.oracle_class_means(_ptr(z), _ptr(lab), z.size, ctypes.byref(c1), ctypes.byref(c2))
+    return c1.value, c2.value
+
+
+def quantile_delta(f32, q):
+    lib = _load()
+    f = _c(f32, np.float32)
+    return float(np.float32(lib.oracle_quantile_delta(_ptr(f), f.size, float(q))))
+
+
+def domain(f32, delta):
+    """Region codes (0 Bg, 1 Fg, 2 RD) for threshold `delta` (float32)."""
+    lib = _load()
+    f = _c(f32, np.float32)
+    reg = np.empty(f.shape, np.uint8)
+    lib.oracle_domain(_ptr(f), f.size, float(np.float32(delta)), _ptr(reg))
+    return reg
+
+
+def pixel_list(region):
+    lib = _load()
+    r = _c(region, np.uint8)
+    n = lib.oracle_pixel_list(_ptr(r), r.size, None)
+    out = np.empty(max(n, 1), np.int32)
+    lib.oracle_pixel_list(_ptr(r), r.size, _ptr(out))
+    return out[:n]
+
+
+def tile_list(region, th, tw):
+    lib = _load()
+    r = _c(region, np.uint8)
+    H, W = r.shape
+    n = lib.oracle_tile_list(_ptr(r), H, W, th, tw, None)
+    out = np.empty(max(n, 1), np.int32)
+    lib.oracle_tile_list(_ptr(r), H, W, th, tw, _ptr(out))
+    return out[:n]
+
+
+def grad(w):
+    lib = _load()
+    w = _c(w, np.float64)
+    H, W = w.shape
+    g1, g2 = np.empty_like(w), np.empty_like(w)
+    lib.oracle_grad(_ptr(w), H, W, _ptr(g1), _ptr(g2))
+    return g1, g2
+
+
+def div(p1, p2):
+    lib = _load()
+    p1, p2 = _c(p1, np.float64), _c(p2, np.float64)
+    H, W = p1.shape
+    d = np.empty_like(p1)
+    lib.oracle_div(_ptr(p1), _ptr(p2), H, W, _ptr(d))
+    return d
+
+
+class State:
+    """Oracle iterate (u, v, p1, p2) in FP64 plus the per-iteration increments."""
+
+    def __init__(self, u, v, p1, p2, iters_done, hist):
+        self.u, self.v, self.p1, self.p2 = u, v, p1, p2
+        self.iters_done = iters_done
+        self.hist = hist
+
+    def copy(self):
+        return State(self.u.copy(), self.v.copy(), self.p1.copy(), self.p2.copy(),
+                     self.iters_done, self.hist.copy())
+
+
+def solve(f32, region, lam, theta=0.2, tau=0.125, iters=100, n_inner=1, tol=0.0,
+          state: State | None = None) -> State:
+    """Run the restricted dual iteration (Section 3); warm-starts from `state`."""
+    lib = _load()
+    f = _c(f32, np.float32)
+    reg = _c(region, np.uint8)
+    H, W = f.shape
+    if state is None:
+        u = np.zeros((H, W)); v = np.zeros((H, W)); p1 = np.zeros((H, W)); p2 = np.zeros((H, W))
+        warm = 0
+    else:
+        u, v, p1, p2 = (_c(a, np.float64).copy() for a in (state.u, state.v, state.p1, state.p2))
+        warm = 1
+    hist = np.zeros((max(iters, 1), 2))
+    done = lib.oracle_solve(_ptr(f), H, W, _ptr(reg), float(lam), float(theta), float(tau),
+                            int(iters), int(n_inner), float(tol), warm,
+                            _ptr(u), _ptr(v), _ptr(p1), _ptr(p2), _ptr(hist))
+    return State(u, v, p1, p2, done, hist[:done])
+
+
+def energy(u, v, p1, p2, f32, lam, theta=0.2):
+    """dict with TV(u), E_CR(u), E_CR(v), E_DF, dual bound D(p) and gap."""
+    lib = _load()
+    f = _c(f32, np.float32)
+    H, W = f.shape
+    arrs = [_c(a, np.float64) for a in (u, v, p1, p2)]
+    out = np.zeros(6)
+    lib.oracle_energy(*(_ptr(a) for a in arrs), _ptr(f), H, W, float(lam), float(theta), _ptr(out))
+    return dict(tv=out[0], ecr_u=out[1], ecr_v=out[2], edf=out[3], dual=out[4], gap=out[5])
+
+
+def errors(u_star, u_gt, eps=0.5):
+    """(E1, E2) of Section 4."""
+    lib = _load()
+    a, b = _c(u_star, np.float64), _c(u_gt, np.float64)
+    out = np.zeros(2)
+    lib.oracle_errors(_ptr(a), _ptr(b), a.size, float(eps), _ptr(out))
+    return float(out[0]), float(out[1])
+
+
+def pipeline(problem, delta=None, q=None, iters=None, n_inner=1, tol=0.0):
+    """Fitting -> domain -> solve for a synthetic problem; returns a dict."""
+    import math
+    c1, c2 = problem.c1, problem.c2
+    if math.isnan(c1) or math.isnan(c2):
+        c1, c2 = class_means(problem.z, problem.label)
+    _, f32 = fitting(problem.z, c1, c2, problem.markers if problem.gamma else None,
+                     problem.gamma)
+    if q is None and delta is None:
+        q = problem.q if problem.q >= 0 else None
+        delta = problem.delta
+    if q is not None and q >= 0:
+        delta = quantile_delta(f32, q)
+    reg = domain(f32, np.float32(delta) if np.isfinite(delta) else np.float32(np.inf))
+    st = solve(f32, reg, problem.lam, problem.theta, problem.tau,
+               problem.iters if iters is None else iters, n_inner, tol)
+    return dict(c1=c1, c2=c2, f32=f32, delta=delta, region=reg, state=st)

@@ -1,0 +1,341 @@
+/*
+ * seg_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see the
+ * header).  Every function follows one passage of the paper and is written
+ * for reading, not for speed: whole-image loops, no blocking, no fusion.
+ *
+ * Paper: J. Spencer, "A Restricted-Domain Dual Formulation for Two-Phase
+ * Image Segmentation", arXiv 1807.11534.
+ *
+ * Readings taken where the paper is silent or garbled:
+ *  - The discrete gradient/divergence are those of Chambolle (2004), which
+ *    Section 2.1 cites without printing: forward differences set to 0 on the
+ *    last row/column, and div = -grad^T.
+ *  - The v-step of Section 2.1 prints r(x); Section 3 prints f(x).  f is used.
+ *  - Section 3 writes "Fg cap Bg" for where rho = 0; that set is empty, so the
+ *    union Fg cup Bg is used (rho = 0 outside RD).
+ *  - The initialisation is u0 = H(-f) (Section 1; Section 3 garbles it as
+ *    -H(f)), with H(s) = 1 iff s > 0, so f = 0 starts (and, outside RD, stays)
+ *    in Bg.  RD = {|f| < q-hat} strictly, Fg = {f < 0} \ RD, Bg = the rest.
+ *  - v0 is the v-step applied to u0; p0 = 0 (Section 3: rho initialised to 0).
+ *  - n_inner fixed-point sweeps for rho per outer iteration (the paper does
+ *    not say how many); the sweeps are Jacobi (all of RD from the same p^n).
+ *  - The stopping norm of Section 4 is the Euclidean norm over all pixels.
+ *
+ * parity unpinned: the values of the restricted solution for 0 < q-hat < inf
+ * have no closed form; they are pinned only through the special cases and
+ * invariants the tests check (q-hat = 0, q-hat = inf, |p| <= 1, v in [0,1],
+ * large lambda, the disk, the 1-D ROF sub-problem, weak duality).
+ */
+#include "seg_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define IDX(i, j) ((int64_t)(i) * (int64_t)W + (int64_t)(j))
+
+/* ---------------------------------------------------------------- fitting */
+
+/* Eq. CV: f = (z - c1)^2 - (z - c2)^2 (Section 1).
+ * Eq. DS: f = CV + gamma P(x), with P the Euclidean distance to the nearest
+ * marker pixel divided by its maximum over the image (the paper takes P from
+ * its reference [CDSS] without defining it; this normalised distance is the
+ * reading used here).  Computed in FP64 in this fixed order, then rounded once
+ * to float32. */
+void oracle_fitting(const float* z, int H, int W, double c1, double c2,
+                    const int32_t* markers, int n_markers, double gamma,
+                    double* f64_out, float* f32_out)
+{
+    int64_t n = (int64_t)H * W;
+    int64_t* d2 = NULL;
+    int64_t d2max = 0;
+    if (n_markers > 0) {
+        d2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                int64_t best = -1;
+                for (int k = 0; k < n_markers; ++k) {
+                    int64_t dy = (int64_t)i - markers[2 * k];
+                    int64_t dx = (int64_t)j - markers[2 * k + 1];
+                    int64_t s = dy * dy + dx * dx;
+                    if (best < 0 || s < best) best = s;
+                }
+                d2[IDX(i, j)] = best;
+                if (best > d2max) d2max = best;
+            }
+    }
+    double dmax = sqrt((double)d2max);
+    for (int64_t x = 0; x < n; ++x) {
+        double zz = (double)z[x];
+        double t1 = zz - c1;
+        double t2 = zz - c2;
+        double a = t1 * t1;
+        double b = t2 * t2;
+        double f = a - b;
+        if (n_markers > 0) {
+            double P = (d2max > 0) ? sqrt((double)d2[x]) / dmax : 0.0;
+            double gp = gamma * P;
+            f = f + gp;
+        }
+        if (f64_out) f64_out[x] = f;
+        if (f32_out) f32_out[x] = (float)f;
+    }
+    free(d2);
+}
+
+/* c1, c2 as the average foreground / background intensities (Section 1,
+ * below Eq. CV), with the classes given by a label mask. */
+void oracle_class_means(const float* z, const uint8_t* label, int64_t n,
+                        double* c1, double* c2)
+{
+    double s1 = 0.0, s0 = 0.0;
+    int64_t n1 = 0, n0 = 0;
+    for (int64_t x = 0; x < n; ++x) {
+        if (label[x]) { s1 += (double)z[x]; ++n1; }
+        else          { s0 += (double)z[x]; ++n0; }
+    }
+    *c1 = n1 ? s1 / (double)n1 : 0.0;
+    *c2 = n0 ? s0 / (double)n0 : 0.0;
+}
+
+/* --------------------------------------------------------------- domain */
+
+static int cmp_float(const void* a, const void* b)
+{
+    float x = *(const float*)a, y = *(const float*)b;
+    return (x > y) - (x < y);
+}
+
+/* Section 3: q-hat starts at 0 and grows until the fraction of pixels in RD
+ * reaches q.  With RD = {|f| < q-hat}: k = ceil(q n); q-hat = 0 for k = 0,
+ * else the next float above the k-th smallest |f|. */
+float oracle_quantile_delta(const float* f32, int64_t n, double q)
+{
+    if (n <= 0) return 0.0f;
+    int64_t k = (int64_t)ceil(q * (double)n);
+    if (k <= 0) return 0.0f;
+    if (k > n) k = n;
+    float* a = (float*)malloc(sizeof(float) * (size_t)n);
+    for (int64_t x = 0; x < n; ++x) a[x] = fabsf(f32[x]);
+    qsort(a, (size_t)n, sizeof(float), cmp_float);
+    float t = a[k - 1];
+    free(a);
+    return nextafterf(t, INFINITY);
+}
+
+/* Section 3: Fg = {f <= -q-hat}, Bg = {f >= q-hat}, RD = the rest; u0 = H(-f)
+ * (Section 1) decides the fixed value, so f = 0 outside RD is Bg. */
+void oracle_domain(const float* f32, int64_t n, float delta, uint8_t* region)
+{
+    for (int64_t x = 0; x < n; ++x) {
+        float f = f32[x];
+        if (fabsf(f) < delta) region[x] = 2;
+        else if (f < 0.0f) region[x] = 1;
+        else region[x] = 0;
+    }
+}
+
+int64_t oracle_pixel_list(const uint8_t* region, int64_t n, int32_t* list)
+{
+    int64_t c = 0;
+    for (int64_t x = 0; x < n; ++x)
+        if (region[x] == 2) {
+            if (list) list[c] = (int32_t)x;
+            ++c;
+        }
+    return c;
+}
+
+int64_t oracle_tile_list(const uint8_t* region, int H, int W, int th, int tw,
+                         int32_t* list)
+{
+    int nty = (H + th - 1) / th, ntx = (W + tw - 1) / tw;
+    int64_t c = 0;
+    for (int ty = 0; ty < nty; ++ty)
+        for (int tx = 0; tx < ntx; ++tx) {
+            int any = 0;
+            for (int i = ty * th; i < H && i < (ty + 1) * th && !any; ++i)
+                for (int j = tx * tw; j < W && j < (tx + 1) * tw; ++j)
+                    if (region[IDX(i, j)] == 2) { any = 1; break; }
+            if (any) {
+                if (list) list[c] = ty * ntx + tx;
+                ++c;
+            }
+        }
+    return c;
+}
+
+/* ------------------------------------------------------------ operators */
+
+/* Chambolle (2004) gradient: forward differences, zero on the last row
+ * (first component) and last column (second component). */
+void oracle_grad(const double* w, int H, int W, double* g1, double* g2)
+{
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            g1[IDX(i, j)] = (i < H - 1) ? w[IDX(i + 1, j)] - w[IDX(i, j)] : 0.0;
+            g2[IDX(i, j)] = (j < W - 1) ? w[IDX(i, j + 1)] - w[IDX(i, j)] : 0.0;
+        }
+}
+
+/* Chambolle (2004) divergence, the negative adjoint of oracle_grad:
+ * (div p) = [i<H-1] p1(i,j) - [i>0] p1(i-1,j) + [j<W-1] p2(i,j) - [j>0] p2(i,j-1). */
+void oracle_div(const double* p1, const double* p2, int H, int W, double* d)
+{
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double a = (i < H - 1 ? p1[IDX(i, j)] : 0.0) - (i > 0 ? p1[IDX(i - 1, j)] : 0.0);
+            double b = (j < W - 1 ? p2[IDX(i, j)] : 0.0) - (j > 0 ? p2[IDX(i, j - 1)] : 0.0);
+            d[IDX(i, j)] = a + b;
+        }
+}
+
+/* -------------------------------------------------------------- solver */
+
+static double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
+
+/* Section 3.  Outside RD: u = v = 1 on Fg, 0 on Bg, rho = 0.  On RD:
+ *   rho^{n+1} = (rho^n + tau grad(div rho^n - v/theta))
+ *               / (1 + tau |grad(div rho^n - v/theta)|)        (fixed point)
+ *   u = v - theta div rho                                     (u-step)
+ *   v = min(max(u - theta lambda f, 0), 1)                    (v-step)
+ * alternated until the Section 4 criterion
+ *   max(||u^l - u^(l-1)||, ||v^l - v^(l-1)||) <= tol
+ * holds (tol <= 0: run exactly `iters` iterations). */
+int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
+                 double lambda, double theta, double tau,
+                 int iters, int n_inner, double tol, int warm,
+                 double* u, double* v, double* p1, double* p2, double* hist)
+{
+    int64_t n = (int64_t)H * W;
+    double* d = (double*)malloc(sizeof(double) * (size_t)n);
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    double* g1 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* g2 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* q1 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* q2 = (double*)malloc(sizeof(double) * (size_t)n);
+
+    if (!warm) {
+        for (int64_t x = 0; x < n; ++x) {
+            double f = (double)f32[x];
+            double h = (f < 0.0) ? 1.0 : 0.0;     /* u0 = H(-f) */
+            u[x] = h;
+            p1[x] = 0.0;
+            p2[x] = 0.0;
+            v[x] = (region[x] == 2) ? clamp01(h - theta * lambda * f) : h;
+        }
+    }
+    /* the fixed values outside RD (also enforced on a warm start) */
+    for (int64_t x = 0; x < n; ++x)
+        if (region[x] != 2) {
+            double h = (region[x] == 1) ? 1.0 : 0.0;
+            u[x] = h;
+            v[x] = h;
+            p1[x] = 0.0;
+            p2[x] = 0.0;
+        }
+
+    int done = 0;
+    for (int it = 0; it < iters; ++it) {
+        /* fixed-point sweeps for rho with v held fixed */
+        for (int s = 0; s < n_inner; ++s) {
+            oracle_div(p1, p2, H, W, d);
+            for (int64_t x = 0; x < n; ++x) w[x] = d[x] - v[x] / theta;
+            oracle_grad(w, H, W, g1, g2);
+            for (int64_t x = 0; x < n; ++x) {
+                if (region[x] == 2) {
+                    double nrm = sqrt(g1[x] * g1[x] + g2[x] * g2[x]);
+                    double den = 1.0 + tau * nrm;
+                    q1[x] = (p1[x] + tau * g1[x]) / den;
+                    q2[x] = (p2[x] + tau * g2[x]) / den;
+                } else {
+                    q1[x] = 0.0;
+                    q2[x] = 0.0;
+                }
+            }
+            memcpy(p1, q1, sizeof(double) * (size_t)n);
+            memcpy(p2, q2, sizeof(double) * (size_t)n);
+        }
+        /* u-step then v-step on RD */
+        oracle_div(p1, p2, H, W, d);
+        double su = 0.0, sv = 0.0;
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] != 2) continue;
+            double un = v[x] - theta * d[x];
+            double vn = clamp01(un - theta * lambda * (double)f32[x]);
+            su += (un - u[x]) * (un - u[x]);
+            sv += (vn - v[x]) * (vn - v[x]);
+            u[x] = un;
+            v[x] = vn;
+        }
+        double du = sqrt(su), dv = sqrt(sv);
+        if (hist) { hist[2 * it] = du; hist[2 * it + 1] = dv; }
+        done = it + 1;
+        if (tol > 0.0 && (du > dv ? du : dv) <= tol) break;
+    }
+    free(d); free(w); free(g1); free(g2); free(q1); free(q2);
+    return done;
+}
+
+/* ------------------------------------------------------------- energies */
+
+static double tv(const double* u, int H, int W)
+{
+    double s = 0.0;
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double a = (i < H - 1) ? u[IDX(i + 1, j)] - u[IDX(i, j)] : 0.0;
+            double b = (j < W - 1) ? u[IDX(i, j + 1)] - u[IDX(i, j)] : 0.0;
+            s += sqrt(a * a + b * b);
+        }
+    return s;
+}
+
+/* Eq. CR energy TV(u) + lambda sum f u; Eq. DF energy (with the exact-penalty
+ * term psi(v) = 0 for v in [0,1]); the dual bound
+ *   D(p) = sum min(0, lambda f + div p),
+ * obtained from TV(u) = max_{|p|<=1} <u, div p> and minimising over u in [0,1]
+ * pixel by pixel (valid when |p| <= 1); gap = E_CR(v) - D(p) >= 0. */
+void oracle_energy(const double* u, const double* v, const double* p1,
+                   const double* p2, const float* f32, int H, int W,
+                   double lambda, double theta, double* out)
+{
+    int64_t n = (int64_t)H * W;
+    double* d = (double*)malloc(sizeof(double) * (size_t)n);
+    oracle_div(p1, p2, H, W, d);
+    double tvu = tv(u, H, W), tvv = tv(v, H, W);
+    double fu = 0.0, fv = 0.0, quad = 0.0, dual = 0.0;
+    for (int64_t x = 0; x < n; ++x) {
+        double f = (double)f32[x];
+        fu += f * u[x];
+        fv += f * v[x];
+        quad += (u[x] - v[x]) * (u[x] - v[x]);
+        double c = lambda * f + d[x];
+        dual += (c < 0.0) ? c : 0.0;
+    }
+    out[0] = tvu;
+    out[1] = tvu + lambda * fu;
+    out[2] = tvv + lambda * fv;
+    out[3] = tvu + quad / (2.0 * theta) + lambda * fv;
+    out[4] = dual;
+    out[5] = out[2] - dual;
+    free(d);
+}
+
+/* Section 4: GT = {u_gt > eps}, Omega* = {u* > eps};
+ * E1 = N(GT cap Omega*) / N(GT cup Omega*) (1 when both are empty),
+ * E2 = sum (u* - u_gt)^2 (h = 1). */
+void oracle_errors(const double* u_star, const double* u_gt, int64_t n,
+                   double eps, double* out)
+{
+    int64_t inter = 0, uni = 0;
+    double e2 = 0.0;
+    for (int64_t x = 0; x < n; ++x) {
+        int a = u_gt[x] > eps, b = u_star[x] > eps;
+        inter += a && b;
+        uni += a || b;
+        e2 += (u_star[x] - u_gt[x]) * (u_star[x] - u_gt[x]);
+    }
+    out[0] = uni ? (double)inter / (double)uni : 1.0;
+    out[1] = e2;
+}

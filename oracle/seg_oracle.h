@@ -1,0 +1,75 @@
+/*
+ * seg_oracle.h -- plain, slow FP64 CPU oracle for the restricted-domain dual
+ * formulation of two-phase TV segmentation (Spencer, "A Restricted-Domain
+ * Dual Formulation for Two-Phase Image Segmentation", arXiv 1807.11534).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link
+ * or call this code: only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no header, helper or constant with the
+ * CUDA library.
+ *
+ * Conventions: images are row-major [H][W] (no pitch), index i over rows,
+ * j over columns, h = 1.  Region codes: 0 = Bg (u fixed at 0), 1 = Fg (u fixed
+ * at 1), 2 = RD (restricted domain, where the iteration runs).
+ */
+#ifndef SEG_ORACLE_H
+#define SEG_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Fitting term: Eq. CV, and Eq. DS when n_markers > 0 (Section 1). */
+void oracle_fitting(const float* z, int H, int W, double c1, double c2,
+                    const int32_t* markers, int n_markers, double gamma,
+                    double* f64_out, float* f32_out);
+
+/* Class means of z over label==1 (c1, foreground) and label==0 (c2). */
+void oracle_class_means(const float* z, const uint8_t* label, int64_t n,
+                        double* c1, double* c2);
+
+/* q -> q-hat (Section 3): smallest threshold whose restricted domain holds at
+ * least ceil(q n) pixels, decided on the float32 |f|. */
+float oracle_quantile_delta(const float* f32, int64_t n, double q);
+
+/* Fg / Bg / RD partition of Section 3, decided in float32. */
+void oracle_domain(const float* f32, int64_t n, float delta, uint8_t* region);
+
+/* Row-major linear indices of RD pixels; returns the count. */
+int64_t oracle_pixel_list(const uint8_t* region, int64_t n, int32_t* list);
+
+/* Linear ids (ty*ntx+tx, ascending) of th x tw tiles holding an RD pixel. */
+int64_t oracle_tile_list(const uint8_t* region, int H, int W, int th, int tw,
+                         int32_t* list);
+
+/* Discrete gradient and divergence (forward differences, Neumann; the
+ * divergence is minus the adjoint of the gradient). */
+void oracle_grad(const double* w, int H, int W, double* g1, double* g2);
+void oracle_div(const double* p1, const double* p2, int H, int W, double* d);
+
+/* The restricted dual iteration (Sections 2.1 and 3).  warm = 0 starts from
+ * u = H(-f), p = 0, v = v-step(u); warm = 1 continues from the given u, v,
+ * p1, p2.  hist (nullable, 2*iters) receives ||u^l - u^(l-1)||, ||v^l - v^(l-1)||
+ * for each iteration run.  Returns the number of iterations run. */
+int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
+                 double lambda, double theta, double tau,
+                 int iters, int n_inner, double tol, int warm,
+                 double* u, double* v, double* p1, double* p2, double* hist);
+
+/* out[0] = TV(u), out[1] = E_CR(u), out[2] = E_CR(v), out[3] = E_DF(u, v),
+ * out[4] = D(p) (dual lower bound), out[5] = E_CR(v) - D(p) (duality gap). */
+void oracle_energy(const double* u, const double* v, const double* p1,
+                   const double* p2, const float* f32, int H, int W,
+                   double lambda, double theta, double* out);
+
+/* E1 (Tanimoto of the 0.5-thresholded masks) and E2 (sum of squared
+ * differences), Section 4. out[0] = E1, out[1] = E2. */
+void oracle_errors(const double* u_star, const double* u_gt, int64_t n,
+                   double eps, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,463 @@
+"""Pins for the FP64 oracle: facts the paper and the mathematics fix, checked
+without re-typing the oracle's own formulas.
+
+Each test names the passage it rests on (section / equation of arXiv
+1807.11534, or the cited method it reduces to).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1807_11534_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- operators
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (6, 1), (5, 9), (17, 4)])
+def test_div_is_minus_adjoint_of_grad(orc, shape):
+    """Chambolle (2004) operators (cited in Section 2.1): <grad w, p> = -<w, div p>."""
+    rng = np.random.default_rng(1)
+    w = rng.normal(size=shape)
+    p1, p2 = rng.normal(size=shape), rng.normal(size=shape)
+    g1, g2 = orc.grad(w)
+    d = orc.div(p1, p2)
+    lhs = float(np.sum(g1 * p1) + np.sum(g2 * p2))
+    rhs = -float(np.sum(w * d))
+    assert abs(lhs - rhs) <= 1e-12 * (1 + abs(lhs))
+
+
+def test_grad_div_textbook_values(orc):
+    """Forward differences with Neumann boundary: a ramp in i has gradient
+    (1, 0) except on the last row; a constant unit field p1 has divergence
+    +1 on the first row, 0 inside, -1 on the last row."""
+    H, W = 5, 4
+    ramp = np.repeat(np.arange(H, dtype=float)[:, None], W, axis=1)
+    g1, g2 = orc.grad(ramp)
+    exp1 = np.ones((H, W)); exp1[-1] = 0
+    np.testing.assert_array_equal(g1, exp1)
+    np.testing.assert_array_equal(g2, np.zeros((H, W)))
+    d = orc.div(np.ones((H, W)), np.zeros((H, W)))
+    exp = np.zeros((H, W)); exp[0] = 1; exp[-1] = -1
+    np.testing.assert_array_equal(d, exp)
+    d = orc.div(np.zeros((H, W)), np.ones((H, W)))
+    exp = np.zeros((H, W)); exp[:, 0] = 1; exp[:, -1] = -1
+    np.testing.assert_array_equal(d, exp)
+
+
+# ----------------------------------------------------------------- fitting
+
+def test_cv_term_is_affine_in_z(orc):
+    """Eq. CV expands to f = 2 z (c2 - c1) + c1^2 - c2^2; for c1 = .3, c2 = .7
+    this is 0.8 z - 0.4."""
+    rng = np.random.default_rng(2)
+    z = rng.uniform(-1, 2, (13, 11)).astype(np.float32)
+    f64, f32 = orc.fitting(z, 0.3, 0.7)
+    np.testing.assert_allclose(f64, 0.8 * z.astype(np.float64) - 0.4, atol=1e-14)
+    assert f32.dtype == np.float32
+    np.testing.assert_array_equal(f32, f64.astype(np.float32))
+    # the sign decides the phase: f < 0 iff z is closer to c1
+    assert np.all((f64 < 0) == (np.abs(z - 0.3) < np.abs(z - 0.7)))
+
+
+def test_ds_term_distance_properties(orc):
+    """Eq. DS: f = CV + gamma P, P the normalised distance to the markers:
+    P = 0 on a marker, max P = 1, and on one row with a marker at column 0
+    P(j) = j / (W-1)."""
+    H, W = 1, 9
+    z = np.full((H, W), 0.5, np.float32)  # CV = 0 at z = (c1+c2)/2
+    f64, _ = orc.fitting(z, 0.3, 0.7, markers=np.array([[0, 0]]), gamma=2.0)
+    np.testing.assert_allclose(f64[0], 2.0 * np.arange(W) / (W - 1), atol=1e-15)
+    rng = np.random.default_rng(3)
+    H, W = 20, 31
+    m = np.stack([rng.integers(0, H, 5), rng.integers(0, W, 5)], 1)
+    z = np.full((H, W), 0.5, np.float32)
+    f64, _ = orc.fitting(z, 0.3, 0.7, markers=m, gamma=1.0)
+    assert np.all(np.abs(f64[m[:, 0], m[:, 1]]) < 1e-15)
+    assert abs(f64.max() - 1.0) < 1e-15
+    # brute force on the distance itself
+    yy, xx = np.mgrid[0:H, 0:W]
+    dist = np.min(np.hypot(yy[..., None] - m[:, 0], xx[..., None] - m[:, 1]), axis=-1)
+    np.testing.assert_allclose(f64, dist / dist.max(), atol=1e-14)
+
+
+def test_class_means_match_numpy(orc):
+    rng = np.random.default_rng(4)
+    z = rng.normal(size=(40, 50)).astype(np.float32)
+    lab = (rng.random((40, 50)) < 0.3).astype(np.uint8)
+    c1, c2 = orc.class_means(z, lab)
+    assert abs(c1 - z[lab == 1].astype(np.float64).mean()) < 1e-13
+    assert abs(c2 - z[lab == 0].astype(np.float64).mean()) < 1e-13
+
+
+# ------------------------------------------------------------------ domain
+
+@pytest.mark.parametrize("q", [0.0, 0.013, 0.25, 0.5, 0.97, 1.0])
+def test_quantile_delta_is_minimal_by_brute_force(orc, q):
+    """Section 3: q-hat grows from 0 until the RD fraction reaches q.  Brute
+    force: |RD(q-hat)| >= ceil(qn), and the next smaller threshold misses it."""
+    rng = np.random.default_rng(5)
+    f = rng.normal(0, 0.2, 500).astype(np.float32)
+    f[::7] = f[3]  # ties
+    delta = orc.quantile_delta(f, q)
+    k = math.ceil(q * f.size)
+    cnt = int(np.sum(np.abs(f) < np.float32(delta)))
+    assert cnt >= k
+    if k > 0:
+        below = np.nextafter(np.float32(delta), np.float32(0))
+        assert int(np.sum(np.abs(f) < below)) < k
+    else:
+        assert delta == 0.0 and cnt == 0
+
+
+def test_domain_special_cases(orc):
+    """Section 3: q = 0 gives RD empty (zero-thresholding of f); q = 1 gives
+    Fg = Bg = empty (the conventional problem)."""
+    rng = np.random.default_rng(6)
+    f = rng.normal(0, 1, (9, 14)).astype(np.float32)
+    f[0, 0] = 0.0
+    reg0 = orc.domain(f, 0.0)
+    assert not np.any(reg0 == 2)
+    np.testing.assert_array_equal(reg0 == 1, f < 0)   # u0 = H(-f): f = 0 is background
+    reg1 = orc.domain(f, np.inf)
+    assert np.all(reg1 == 2)
+    d = orc.quantile_delta(f, 1.0)
+    assert np.all(orc.domain(f, d) == 2)
+
+
+def test_pixel_and_tile_lists_brute_force(orc):
+    rng = np.random.default_rng(7)
+    f = rng.normal(0, 1, (37, 70)).astype(np.float32)
+    reg = orc.domain(f, 0.2)
+    pl = orc.pixel_list(reg)
+    np.testing.assert_array_equal(pl, np.flatnonzero(reg.ravel() == 2))
+    th, tw = 8, 32
+    tl = orc.tile_list(reg, th, tw)
+    ntx = -(-70 // tw)
+    exp = [ty * ntx + tx for ty in range(-(-37 // th)) for tx in range(ntx)
+           if np.any(reg[ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw] == 2)]
+    np.testing.assert_array_equal(tl, np.array(exp, np.int32))
+
+
+# ------------------------------------------------------------------ solver
+
+def _numpy_bresson_full(f, lam, theta, tau, iters):
+    """The original, unrestricted dual iteration (Section 2.1) written
+    independently with numpy slicing: no region logic at all."""
+    f = f.astype(np.float64)
+    u = (f < 0).astype(np.float64)
+    p1 = np.zeros_like(u); p2 = np.zeros_like(u)
+    v = np.clip(u - theta * lam * f, 0, 1)
+
+    def dv(a, b):
+        d = np.zeros_like(a)
+        d[:-1, :] += a[:-1, :]; d[1:, :] -= a[:-1, :]
+        d[:, :-1] += b[:, :-1]; d[:, 1:] -= b[:, :-1]
+        return d
+
+    for _ in range(iters):
+        w = dv(p1, p2) - v / theta
+        g1 = np.zeros_like(w); g1[:-1] = w[1:] - w[:-1]
+        g2 = np.zeros_like(w); g2[:, :-1] = w[:, 1:] - w[:, :-1]
+        den = 1 + tau * np.sqrt(g1 * g1 + g2 * g2)
+        p1 = (p1 + tau * g1) / den; p2 = (p2 + tau * g2) / den
+        u = v - theta * dv(p1, p2)
+        v = np.clip(u - theta * lam * f, 0, 1)
+    return u, v, p1, p2
+
+
+def test_unrestricted_domain_is_the_original_method(orc):
+    """Section 3: for q = 1 the restricted method is the conventional one."""
+    P = synth.small_example(seed=0, H=40, W=52)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    st = orc.solve(f, orc.domain(f, np.inf), 1.0, 0.2, 0.125, iters=60)
+    u, v, p1, p2 = _numpy_bresson_full(f, 1.0, 0.2, 0.125, 60)
+    for a, b in ((st.u, u), (st.v, v), (st.p1, p1), (st.p2, p2)):
+        np.testing.assert_allclose(a, b, atol=1e-12, rtol=0)
+
+
+def test_empty_domain_is_zero_thresholding(orc):
+    """Section 3: q = 0 gives the zero-thresholding of the fitting term:
+    u = v = H(-f), rho = 0, and no increment."""
+    P = synth.small_example(seed=1, H=33, W=45)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    st = orc.solve(f, orc.domain(f, 0.0), 1.0, iters=5)
+    h = (f < 0).astype(np.float64)
+    np.testing.assert_array_equal(st.u, h)
+    np.testing.assert_array_equal(st.v, h)
+    assert not st.p1.any() and not st.p2.any()
+    assert np.all(st.hist == 0)
+
+
+@pytest.mark.parametrize("delta", [0.05, 0.15, np.inf])
+def test_dual_field_and_v_stay_feasible(orc, delta):
+    """The fixed-point step keeps |rho| <= 1 (its denominator dominates the
+    numerator once |rho^n| <= 1) and the v-step keeps v in [0, 1]."""
+    P = synth.small_example(seed=2, H=48, W=40)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    reg = orc.domain(f, delta)
+    st = None
+    for _ in range(4):
+        st = orc.solve(f, reg, 1.0, iters=25, state=st)
+        nrm = np.sqrt(st.p1 ** 2 + st.p2 ** 2)
+        assert nrm.max() <= 1 + 1e-12
+        assert st.v.min() >= 0 and st.v.max() <= 1
+        assert np.all(st.p1[reg != 2] == 0) and np.all(st.p2[reg != 2] == 0)
+        assert np.all(st.u[reg == 1] == 1) and np.all(st.u[reg == 0] == 0)
+
+
+def test_large_lambda_gives_heaviside(orc):
+    """Section 1: for large lambda the solution is f < 0 foreground, f > 0
+    background.  With |rho| <= 1, |div rho| <= 4, so once
+    theta lambda |f| >= 1 + 4 theta the v-step returns H(-f) exactly."""
+    rng = np.random.default_rng(8)
+    f = rng.uniform(0.05, 1.0, (30, 30)) * rng.choice([-1, 1], (30, 30))
+    f = f.astype(np.float32)
+    theta = 0.2
+    lam = (1 + 4 * theta) / (theta * 0.05) * 1.01
+    st = orc.solve(f, orc.domain(f, np.inf), lam, theta, 0.125, iters=40)
+    np.testing.assert_array_equal(st.v, (f < 0).astype(np.float64))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("r", [8, 12])
+def test_disk_closed_form(orc, r):
+    """f = -1 inside a disk of radius r, +1 outside (Chan-Esedoglu-Nikolova,
+    the model Section 2 relaxes): the disk costs 2 pi r - lambda pi r^2 and
+    any sub-disk is worse than one of the two ends, so the minimiser is empty
+    for lambda < 2/r and the disk for lambda > 2/r."""
+    n = 2 * r + 16
+    f, inside = synth.disk_fitting(n, n, r)
+    reg = orc.domain(f, np.inf)
+    lam_c = 2.0 / r
+    st = orc.solve(f, reg, 0.5 * lam_c, iters=3000, tol=1e-7)
+    assert st.u.max() < 0.5 and st.v.max() < 0.5
+    st = orc.solve(f, reg, 5.0 * lam_c, iters=3000, tol=1e-7)
+    np.testing.assert_array_equal(st.u > 0.5, inside)
+
+
+def test_rof_subproblem_matches_bounded_least_squares(orc):
+    """The rho fixed point solves min_u TV(u) + ||u - v||^2/(2 theta)
+    (Chambolle 2004; the u-equation of Section 2.1).  For v constant along
+    columns this is 1-D TV denoising with weight theta, whose dual is a
+    box-constrained least-squares problem solved here by scipy's BVLS."""
+    lsq_linear = pytest.importorskip("scipy.optimize").lsq_linear
+    rng = np.random.default_rng(9)
+    H, W, theta = 20, 3, 0.2
+    s = np.clip(np.repeat([0.2, 0.9, 0.4, 0.6], 5) + rng.normal(0, 0.1, H), 0, 1)
+    v = np.repeat(s[:, None], W, axis=1)
+    f = np.zeros((H, W), np.float32)
+    reg = np.full((H, W), 2, np.uint8)
+    z0 = np.zeros((H, W))
+    st = orc.solve(f, reg, 0.0, theta, 0.125, iters=1, n_inner=60000,
+                   state=orc.State(v.copy(), v.copy(), z0, z0, 0, np.zeros((0, 2))))
+    D = np.diff(np.eye(H), axis=0)                     # (H-1) x H forward difference
+    res = lsq_linear(D.T, s, bounds=(-theta, theta), method="bvls", tol=1e-14)
+    x = s - D.T @ res.x
+    for j in range(W):
+        np.testing.assert_allclose(st.u[:, j], x, atol=2e-6)
+
+
+def _smoothed_min(f, lam, theta, eps, relaxed_only=False):
+    """Independent minimiser (scipy L-BFGS-B) of the Eq. DF energy (or of
+    Eq. CR when relaxed_only) with TV smoothed as sqrt(a^2 + b^2 + e^2),
+    e lowered by continuation from 1e-2 down to `eps`."""
+    minimize = pytest.importorskip("scipy.optimize").minimize
+    H, W = f.shape
+    N = H * W
+    f = f.astype(np.float64).ravel()
+
+    def tv_and_grad(u, e):
+        u = u.reshape(H, W)
+        a = np.zeros_like(u); a[:-1] = u[1:] - u[:-1]
+        b = np.zeros_like(u); b[:, :-1] = u[:, 1:] - u[:, :-1]
+        r = np.sqrt(a * a + b * b + e * e)
+        ga, gb = a / r, b / r
+        g = np.zeros_like(u)
+        g[1:] += ga[:-1]; g[:-1] -= ga[:-1]
+        g[:, 1:] += gb[:, :-1]; g[:, :-1] -= gb[:, :-1]
+        return r.sum(), g.ravel()
+
+    if relaxed_only:
+        def obj(x, e):
+            t, g = tv_and_grad(x, e)
+            return t + lam * np.dot(f, x), g + lam * f
+        x = np.full(N, 0.5)
+        bounds = [(0, 1)] * N
+    else:
+        def obj(x, e):
+            u, v = x[:N], x[N:]
+            t, g = tv_and_grad(u, e)
+            dq = (u - v) / theta
+            val = t + 0.5 * np.dot(u - v, u - v) / theta + lam * np.dot(f, v)
+            return val, np.concatenate([g + dq, -dq + lam * f])
+        x = np.full(2 * N, 0.5)
+        bounds = [(None, None)] * N + [(0, 1)] * N
+    e = 1e-2
+    while True:
+        res = minimize(obj, x, args=(e,), jac=True, method="L-BFGS-B", bounds=bounds,
+                       options=dict(maxiter=200000, maxfun=400000, ftol=1e-16, gtol=1e-13,
+                                    maxcor=50))
+        x = res.x
+        if e <= eps:
+            break
+        e = max(eps, e / 10)
+    if relaxed_only:
+        return res.fun, x.reshape(H, W)
+    return res.fun, x[:N].reshape(H, W), x[N:].reshape(H, W)
+
+
+@pytest.mark.parametrize("seed,lam", [(0, 2.0), (1, 4.0)])
+def test_iteration_reaches_the_df_minimum(orc, seed, lam):
+    """Section 2.1: alternating the u- and v-minimisations minimises Eq. DF.
+    The converged oracle energy must equal an independent L-BFGS-B minimum of
+    the (slightly smoothed) Eq. DF energy on a tiny image with an edge."""
+    rng = np.random.default_rng(10 + seed)
+    blk = np.zeros((5, 6), bool)
+    blk[1:4, 1 + seed:4 + seed] = True
+    f = (np.where(blk, -0.5, 0.5) + rng.normal(0, 0.3, (5, 6))).astype(np.float32)
+    theta, eps = 0.2, 1e-7
+    st = orc.solve(f, orc.domain(f, np.inf), lam, theta, 0.125, iters=40000, tol=1e-13)
+    e = orc.energy(st.u, st.v, st.p1, st.p2, f, lam, theta)
+    assert e["tv"] > 0.5                      # the solution has an edge
+    emin, _, _ = _smoothed_min(f, lam, theta, eps)
+    # smoothing only raises the energy (by at most N eps), and the iteration
+    # cannot beat the true minimum: E_DF(oracle) >= emin - N eps
+    assert e["edf"] >= emin - 30 * eps - 1e-9
+    assert abs(e["edf"] - emin) <= 1e-5 * max(1.0, abs(emin))
+
+
+def test_tv_textbook_value(orc):
+    """Isotropic discrete TV (forward differences): one raised pixel inside a
+    3x3 image has TV = 2 + sqrt(2) (its own corner term is sqrt(1 + 1), the
+    pixels above and to the left each see a unit jump)."""
+    u = np.zeros((3, 3)); u[1, 1] = 1.0
+    z = np.zeros((3, 3))
+    e = orc.energy(u, u, z, z, np.zeros((3, 3), np.float32), 1.0)
+    assert abs(e["tv"] - (2 + math.sqrt(2))) < 1e-15
+
+
+def test_duality_gap_and_brute_force_bounds(orc):
+    """Weak duality (derived from TV(u) = max_{|p|<=1} <u, div p>): for any
+    feasible pair D(p) <= min over u in [0,1] <= E_CR(v); the binary brute
+    force minimum over all 2^9 labelings of a 3x3 image is itself above the
+    relaxed minimum.  At convergence the gap shrinks with theta (Eq. DF
+    approaches Eq. CR as theta -> 0)."""
+    rng = np.random.default_rng(11)
+    f = rng.normal(0, 0.7, (3, 3)).astype(np.float32)
+    lam = 1.0
+    best = np.inf
+    for code in range(512):
+        u = np.array([(code >> k) & 1 for k in range(9)], float).reshape(3, 3)
+        e = orc.energy(u, u, np.zeros((3, 3)), np.zeros((3, 3)), f, lam)["ecr_u"]
+        best = min(best, e)
+    relaxed, _ = _smoothed_min(f, lam, 0.2, 1e-8, relaxed_only=True)
+    assert relaxed <= best + 1e-6
+    gaps = []
+    for theta in (0.2, 0.05, 0.0125):
+        st = orc.solve(f, orc.domain(f, np.inf), lam, theta, 0.125, iters=60000, tol=1e-13)
+        e = orc.energy(st.u, st.v, st.p1, st.p2, f, lam, theta)
+        assert e["dual"] <= relaxed + 1e-6 <= e["ecr_v"] + 2e-6
+        assert e["gap"] >= -1e-12
+        gaps.append(e["gap"])
+    assert gaps[2] < gaps[0]
+    assert gaps[2] < 0.05 * max(1.0, abs(best))
+    # random feasible pairs obey weak duality too
+    for k in range(20):
+        p1, p2, v = synth.random_state(3, 3, seed=100 + k)
+        e = orc.energy(v, v, p1, p2, f, lam)
+        assert e["dual"] <= e["ecr_v"] + 1e-12
+
+
+def test_df_energy_decreases_with_exact_inner_solves(orc):
+    """With the rho fixed point run (nearly) to convergence each outer step,
+    the alternation is exact block minimisation of Eq. DF, so E_DF(u^l, v^l)
+    cannot increase."""
+    P = synth.small_example(seed=3, H=24, W=24)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    reg = orc.domain(f, np.inf)
+    st = orc.solve(f, reg, 1.0, iters=1, n_inner=300)
+    last = orc.energy(st.u, st.v, st.p1, st.p2, f, 1.0)["edf"]
+    for _ in range(12):
+        st = orc.solve(f, reg, 1.0, iters=1, n_inner=300, state=st)
+        e = orc.energy(st.u, st.v, st.p1, st.p2, f, 1.0)["edf"]
+        assert e <= last + 1e-9
+        last = e
+
+
+def test_stopping_rule_and_history(orc):
+    """Section 4: the increments are the Euclidean norms of the change of u and
+    v over one iteration (checked against consecutive warm-started states),
+    and the solve stops at the first l with max(||du||, ||dv||) <= tol."""
+    P = synth.small_example(seed=4, H=32, W=32)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    reg = orc.domain(f, 0.2)
+    full = orc.solve(f, reg, 1.0, iters=400)
+    assert np.all(full.hist[:20] > 0)
+    a = orc.solve(f, reg, 1.0, iters=7)
+    b = orc.solve(f, reg, 1.0, iters=1, state=a)
+    assert abs(full.hist[7, 0] - np.linalg.norm(b.u - a.u)) < 1e-14
+    assert abs(full.hist[7, 1] - np.linalg.norm(b.v - a.v)) < 1e-14
+    tol = 1e-2
+    crit = np.max(full.hist, axis=1)
+    l = int(np.argmax(crit <= tol)) + 1
+    st = orc.solve(f, reg, 1.0, iters=400, tol=tol)
+    assert st.iters_done == l
+    np.testing.assert_allclose(st.hist, full.hist[:l], rtol=0, atol=0)
+
+
+def test_initialisation_is_heaviside_of_minus_f(orc):
+    """Section 1: u0 = H(-f) on the whole image, whatever the restriction;
+    with H(0) = 0 a pixel with f = 0 starts in the background both when it is
+    fixed (q-hat = 0) and when it lies in RD (any q-hat > 0)."""
+    rng = np.random.default_rng(12)
+    f = rng.normal(0, 0.2, (11, 13)).astype(np.float32)
+    f[2, 3] = 0.0; f[5, 5] = -0.0; f[7, 1] = 1e-30
+    h = (f < 0).astype(np.float64)
+    for delta in (0.0, np.float32(1e-38), 0.1, np.inf):
+        st = orc.solve(f, orc.domain(f, delta), 1.0, iters=0)
+        np.testing.assert_array_equal(st.u, h)
+        assert not st.p1.any() and not st.p2.any()
+
+
+# ------------------------------------------------------------------ metrics
+
+def test_errors_hand_computed(orc):
+    """Section 4: E1 = |GT & O| / |GT | O| with 0.5 thresholds, E2 = sum of
+    squared differences."""
+    gt = np.array([0.9, 0.8, 0.1, 0.6, 0.2])
+    us = np.array([0.7, 0.2, 0.3, 0.9, 0.6])
+    # GT = {0, 1, 3}, O = {0, 3, 4}: intersection 2, union 4
+    e1, e2 = orc.errors(us, gt)
+    assert e1 == 0.5
+    assert abs(e2 - np.sum((us - gt) ** 2)) < 1e-15
+    assert orc.errors(np.zeros(4), np.zeros(4)) == (1.0, 0.0)
+
+
+@pytest.mark.slow
+def test_restriction_trend_like_table1(orc):
+    """Table 1 (Section 4): q = 1 reproduces the full-domain result (E1 = 1 up
+    to the loose 1e-2 stop) and has the smallest E2 of all q in every example
+    of the paper's table.  The same must hold on a synthetic 128x128
+    piecewise-constant image (here lambda = 1, where small shapes vanish in
+    the full solution, so restriction costs accuracy until q -> 1)."""
+    with open(os.path.join(GOLDEN, "table1_paper.json")) as fh:
+        table = json.load(fh)
+    for ex in table["examples"]:
+        e1 = dict(zip(table["q"], ex["E1"]))
+        e2 = dict(zip(table["q"], ex["E2"]))
+        assert e1[1.0] == 1.0 and min(e2.values()) == e2[1.0]
+    P = synth.small_example(seed=5, H=128, W=128)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    gt = orc.solve(f, orc.domain(f, np.inf), 1.0, iters=6000, tol=1e-9)
+    res = {}
+    for q in (0.0, 0.2, 0.4, 0.7, 0.9, 1.0):
+        reg = orc.domain(f, orc.quantile_delta(f, q))
+        st = orc.solve(f, reg, 1.0, iters=6000, tol=1e-2)
+        res[q] = orc.errors(st.u, gt.u)
+    assert res[1.0][0] >= 0.99
+    assert all(res[1.0][1] < res[q][1] for q in res if q < 1.0)
