@@ -1,0 +1,191 @@
+/*
+ * seg.h -- C ABI of libseg, a GB300 (sm_103a) implementation of the
+ * restricted-domain dual formulation of two-phase TV segmentation
+ * (J. Spencer, "A Restricted-Domain Dual Formulation for Two-Phase Image
+ * Segmentation", arXiv 1807.11534).
+ *
+ * The method minimises the convex relaxation (Eq. CR, Section 2)
+ *     min_{u in [0,1]}  TV(u) + lambda * sum f u
+ * with the dual splitting of Section 2.1 (Eq. DF): a fixed-point step on the
+ * dual field p (the paper's rho), u = v - theta div p, and
+ * v = clip(u - theta lambda f, 0, 1), run only on the restricted domain
+ * RD = {|f| < delta} of Section 3 while u = v = H(-f) elsewhere and p = 0.
+ *
+ * Conventions (all entry points):
+ *  - Images are row-major float32 [H][ld] in device memory; ld (elements) is
+ *    a multiple of 32 and ld >= W.  Entries in columns W..ld-1 are ignored on
+ *    input and left untouched on output.
+ *  - Bit masks are uint32 [H][ld/32]: bit b of word k in row i is pixel
+ *    (i, 32k + b); bits beyond W are 0.
+ *  - Tiles are 32 columns wide (one mask word) and tile_h rows high
+ *    (tile_h in {4, 8, 16, 32}); tile id = ty * ceil(W/32) + tx.
+ *  - All pointers are device pointers unless a comment says "host".  The
+ *    caller allocates every buffer (through any allocator; PyTorch in the
+ *    Python binding); the library never allocates device memory.  Scratch
+ *    comes from a caller-provided workspace of seg_workspace_bytes() bytes,
+ *    16-byte aligned, owned by the caller, used by one call at a time.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) and returns a seg_status for errors found on the host
+ *    (arguments, launch failures).  Errors found on the device (non-finite
+ *    input, capacity overflow) are recorded in the workspace status word and
+ *    returned by seg_read_status(), which synchronises the stream.
+ *  - seg_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef SEG_H
+#define SEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int seg_status;
+#define SEG_OK 0
+#define SEG_ERR_INVALID_ARG 1   /* bad size, null pointer, bad parameter */
+#define SEG_ERR_ALIGN 2         /* ld not a multiple of 32, pointer not 16-byte aligned */
+#define SEG_ERR_CUDA 3          /* a CUDA runtime call failed (message has the reason) */
+#define SEG_ERR_CAPACITY 4      /* an output buffer is smaller than the result */
+#define SEG_ERR_TIMEOUT 5       /* a bounded device-side wait ran out */
+#define SEG_ERR_NONFINITE 6     /* the fitting term holds NaN or Inf */
+#define SEG_ERR_WORKSPACE 7     /* workspace missing or smaller than required */
+
+/* solve modes */
+#define SEG_MODE_DENSE 0        /* dense [H][ld] state, tile list of the domain, fused stencil */
+#define SEG_MODE_COMPACT 1      /* state stored only for RD pixels (tile-major compact order) */
+
+/* storage types of the iteration state (p1, p2, v); arithmetic is float32 */
+#define SEG_STORE_F32 0
+#define SEG_STORE_BF16 1
+#define SEG_STORE_F16 2
+
+/* Parameters of one solve (host struct, read during the call only). */
+typedef struct seg_params {
+    double lambda;      /* weight of the fitting term, Eq. CR */
+    double theta;       /* coupling of u and v, Eq. DF (default 0.2) */
+    double tau;         /* fixed-point step for p, Section 3 (default 0.125 = 1/8) */
+    double tol;         /* stop when max(||du||,||dv||) <= tol (Section 4); <= 0: run `iters` */
+    int iters;          /* maximum number of outer iterations */
+    int n_inner;        /* fixed-point sweeps for p per outer iteration (>= 1; default 1) */
+    int check_every;    /* evaluate the stopping test every this many iterations (>= 1) */
+    int warm_start;     /* 0: start from u = H(-f), p = 0, v = v-step(u); 1: from the u, v, p1, p2 given */
+    int mode;           /* SEG_MODE_DENSE or SEG_MODE_COMPACT */
+    int storage;        /* SEG_STORE_*; 16-bit storage is SEG_MODE_COMPACT only */
+    int tile_h;         /* tile height used by seg_build_domain for this domain */
+    int reserved;
+} seg_params;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int seg_version(void);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* seg_last_error(void);
+
+/* Number of kernel launches the library has issued in this process (host
+ * counter, for diagnostics and launch accounting). */
+unsigned long long seg_launch_count(void);
+
+/* Workspace bytes needed by any call on an H x W image with pitch ld, up to
+ * n_tiles_cap active tiles of height tile_h.  Never zero. */
+size_t seg_workspace_bytes(int H, int W, int ld, int tile_h);
+
+/* Bytes of iteration state for seg_solve: dense mode 6*H*ld float32
+ * (ping-pong p1, p2, v); compact mode room for `capacity` RD pixels
+ * (ping-pong p1, p2, v in the storage type, plus f, u and the pixel list). */
+size_t seg_state_bytes(int H, int ld, int64_t capacity, int mode, int storage);
+
+/* Synchronise `stream` and return the device status word of the workspace
+ * (SEG_OK or the first device-side error), then clear it. */
+seg_status seg_read_status(void* ws, size_t ws_bytes, void* stream);
+
+/* Fitting term (Section 1): Eq. CV  f = (z - c1)^2 - (z - c2)^2, and when
+ * n_markers > 0 Eq. DS  f = CV + gamma P(x), with P the Euclidean distance to
+ * the nearest marker pixel divided by its maximum over the image.
+ *   z        [H][ld] float32 image.
+ *   c1, c2   foreground / background intensities (host doubles), used when
+ *            label == NULL.
+ *   label    NULL, or uint8 [H][ld] class mask: c1 = mean of z where label != 0,
+ *            c2 = mean where label == 0 (FP64 on the device).
+ *   markers  NULL or int32 [n_markers][2] (row, col) device array.
+ *   f        out [H][ld] float32; computed in FP64 and rounded once.
+ *   c_out    NULL or out double[2] (device): the c1, c2 used.
+ * Errors: INVALID_ARG (sizes, null z/f, markers NULL with n_markers > 0),
+ * ALIGN, WORKSPACE, CUDA. */
+seg_status seg_make_fitting(const float* z, int H, int W, int ld,
+                            double c1, double c2, const uint8_t* label,
+                            const int32_t* markers, int n_markers, double gamma,
+                            float* f, double* c_out,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* Restricted domain (Section 3): RD = {|f| < delta}, Fg = {f < 0} \ RD,
+ * Bg = rest (u0 = H(-f), Section 1, with H(0) = 0).  When q >= 0 delta is
+ * chosen from q as in Section 3: the smallest threshold whose RD holds at
+ * least ceil(q * H * W) pixels, i.e. the float just above the k-th smallest
+ * |f| (exact radix select on the float bits); q < 0 uses `delta` as given.
+ *   act, fg   out uint32 [H][ld/32]: RD bits, and f < 0 bits (all pixels).
+ *   wstart    out int32 [H][ld/32]: compact index of the first RD pixel of
+ *             each word in tile-major order (tiles row-major, rows top to
+ *             bottom inside a tile, columns left to right).
+ *   tiles     out int32 [tiles_cap]: ids of tiles holding an RD pixel, ascending.
+ *   pixels    NULL or out int32 [pixels_cap]: linear ids i*W + j of RD pixels
+ *             in tile-major compact order.
+ *   counts    out int32[4] (device): n_tiles, n_active, n_fg (fixed Fg pixels),
+ *             and the k of quantile mode (0 otherwise).
+ *   delta_out NULL or out float[1] (device): the threshold used.
+ * The lists are bit-exact functions of f.  Overflowing tiles_cap/pixels_cap
+ * records SEG_ERR_CAPACITY in the status word; a NaN/Inf in f records
+ * SEG_ERR_NONFINITE.  Host-side errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA. */
+seg_status seg_build_domain(const float* f, int H, int W, int ld,
+                            double delta, double q, int tile_h,
+                            uint32_t* act, uint32_t* fg, int32_t* wstart,
+                            int32_t* tiles, int tiles_cap,
+                            int32_t* pixels, int64_t pixels_cap,
+                            int32_t* counts, float* delta_out,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* Restricted dual iteration (Sections 2.1 and 3) on the domain built by
+ * seg_build_domain for the same f and tile_h:
+ *   p <- (p + tau g) / (1 + tau |g|),  g = grad(div p - v/theta)   on RD
+ *   u  = v - theta div p,  v = clip(u - theta lambda f, 0, 1)       on RD
+ * with p = 0 and u = v = H(-f) outside RD, alternated prm->iters times or
+ * until the Section 4 test max(||u^l - u^(l-1)||, ||v^l - v^(l-1)||) <= tol
+ * (Euclidean norms over the image, checked every check_every iterations).
+ *   u, v, p1, p2  [H][ld] float32: the warm start on input when
+ *                 prm->warm_start, and the final iterate on output.
+ *   state         seg_state_bytes(H, ld, capacity, mode, storage) bytes
+ *                 (compact mode: capacity >= n_active).
+ *   stats         out double[8] (device): [0] iterations run, [1] last
+ *                 ||du||, [2] last ||dv|| (from the last check), [3] n_active,
+ *                 [4] n_tiles, [5] iteration of the last check.
+ * Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA on the host; CAPACITY (compact
+ * state too small) in the status word. */
+seg_status seg_solve(const float* f, int H, int W, int ld,
+                     const uint32_t* act, const uint32_t* fg, const int32_t* wstart,
+                     const int32_t* tiles, const int32_t* counts,
+                     const seg_params* prm,
+                     float* u, float* v, float* p1, float* p2,
+                     void* state, size_t state_bytes, double* stats,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* Energies of an iterate (FP64 reductions over the image):
+ *   out[0] TV(u) (isotropic, forward differences), out[1] E_CR(u) = TV(u) +
+ *   lambda sum f u (Eq. CR), out[2] E_CR(v), out[3] E_DF(u, v) (Eq. DF with
+ *   psi(v) = 0 on [0,1]), out[4] the dual bound D(p) = sum min(0, lambda f +
+ *   div p) (valid when |p| <= 1), out[5] the duality gap E_CR(v) - D(p).
+ *   out: device double[6].  Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA. */
+seg_status seg_energy(const float* f, int H, int W, int ld,
+                      const float* u, const float* v, const float* p1, const float* p2,
+                      double lambda, double theta, double* out,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Error measures of Section 4: out[0] = E1 = N(GT & O*) / N(GT | O*) with
+ * GT = {u_gt > eps}, O* = {u_star > eps} (1 when both are empty), out[1] =
+ * E2 = sum (u_star - u_gt)^2.  out: device double[2]. */
+seg_status seg_errors(const float* u_star, const float* u_gt, int H, int W, int ld,
+                      double eps, double* out, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEG_H */

@@ -65,6 +65,8 @@ def _load():
         lib.oracle_pixel_list.restype = L
         lib.oracle_tile_list.argtypes = [P, I, I, I, I, P]
         lib.oracle_tile_list.restype = L
+        lib.oracle_pixel_list_tiled.argtypes = [P, I, I, I, I, P]
+        lib.oracle_pixel_list_tiled.restype = L
         lib.oracle_grad.argtypes = [P, I, I, P, P]
         lib.oracle_grad.restype = None
         lib.oracle_div.argtypes = [P, P, I, I, P]
@@ -142,6 +144,16 @@ def tile_list(region, th, tw):
     n = lib.oracle_tile_list(_ptr(r), H, W, th, tw, None)
     out = np.empty(max(n, 1), np.int32)
     lib.oracle_tile_list(_ptr(r), H, W, th, tw, _ptr(out))
+    return out[:n]
+
+
+def pixel_list_tiled(region, th, tw=32):
+    lib = _load()
+    r = _c(region, np.uint8)
+    H, W = r.shape
+    n = lib.oracle_pixel_list_tiled(_ptr(r), H, W, th, tw, None)
+    out = np.empty(max(n, 1), np.int32)
+    lib.oracle_pixel_list_tiled(_ptr(r), H, W, th, tw, _ptr(out))
     return out[:n]
 
 

@@ -165,6 +165,24 @@ int64_t oracle_tile_list(const uint8_t* region, int H, int W, int th, int tw,
     return c;
 }
 
+/* RD pixels numbered tile by tile (tiles in row-major order, then rows, then
+ * columns inside a tile): the compact order of the GPU library's state. */
+int64_t oracle_pixel_list_tiled(const uint8_t* region, int H, int W, int th, int tw,
+                                int32_t* list)
+{
+    int nty = (H + th - 1) / th, ntx = (W + tw - 1) / tw;
+    int64_t c = 0;
+    for (int ty = 0; ty < nty; ++ty)
+        for (int tx = 0; tx < ntx; ++tx)
+            for (int i = ty * th; i < H && i < (ty + 1) * th; ++i)
+                for (int j = tx * tw; j < W && j < (tx + 1) * tw; ++j)
+                    if (region[IDX(i, j)] == 2) {
+                        if (list) list[c] = (int32_t)IDX(i, j);
+                        ++c;
+                    }
+    return c;
+}
+
 /* ------------------------------------------------------------ operators */
 
 /* Chambolle (2004) gradient: forward differences, zero on the last row

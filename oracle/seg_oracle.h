@@ -44,6 +44,10 @@ int64_t oracle_pixel_list(const uint8_t* region, int64_t n, int32_t* list);
 int64_t oracle_tile_list(const uint8_t* region, int H, int W, int th, int tw,
                          int32_t* list);
 
+/* RD pixel ids in tile-major order (tiles row-major, rows, columns). */
+int64_t oracle_pixel_list_tiled(const uint8_t* region, int H, int W, int th, int tw,
+                                int32_t* list);
+
 /* Discrete gradient and divergence (forward differences, Neumann; the
  * divergence is minus the adjoint of the gradient). */
 void oracle_grad(const double* w, int H, int W, double* g1, double* g2);

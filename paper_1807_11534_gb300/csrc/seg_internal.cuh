@@ -1,0 +1,164 @@
+// seg_internal.cuh -- internals shared by the libseg translation units:
+// error reporting, the workspace layout, storage-type converters and small
+// device helpers.  Nothing here is visible through the C ABI (include/seg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "seg.h"
+
+namespace seg {
+
+// ------------------------------------------------------------------ errors
+
+// Records `msg` as the thread-local last error and returns `st`.
+seg_status fail(seg_status st, const char* fmt, ...);
+void clear_error();
+
+#define SEG_TRY_CUDA(expr)                                                           \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess)                                                       \
+            return ::seg::fail(SEG_ERR_CUDA, "%s: %s (%s:%d)", #expr,                \
+                               cudaGetErrorString(_e), __FILE__, __LINE__);          \
+    } while (0)
+
+#define SEG_TRY(expr)                                                                \
+    do {                                                                             \
+        seg_status _s = (expr);                                                      \
+        if (_s != SEG_OK) return _s;                                                 \
+    } while (0)
+
+// Host-side count of kernel launches issued by the library (diagnostics).
+void count_launch();
+
+// Checks the launch that was just issued.
+#define SEG_LAUNCHED(name)                                                           \
+    do {                                                                             \
+        ::seg::count_launch();                                                       \
+        cudaError_t _e = cudaGetLastError();                                         \
+        if (_e != cudaSuccess)                                                       \
+            return ::seg::fail(SEG_ERR_CUDA, "launch of %s failed: %s", name,        \
+                               cudaGetErrorString(_e));                              \
+    } while (0)
+
+// -------------------------------------------------------------- workspace
+
+// Device-side header at the start of every workspace.
+struct WsHeader {
+    int status;          // first device-side error (SEG_OK when none)
+    int done;            // set by the stopping test; step kernels then return at once
+    int iters_done;      // iteration at which the stopping test fired
+    int last_check;      // iteration of the last stopping test
+    double c[2];         // c1, c2 used by the fitting term
+    double du, dv;       // last ||u^l - u^(l-1)||, ||v^l - v^(l-1)||
+    unsigned long long d2max;   // largest squared marker distance (Eq. DS)
+    float delta;         // domain threshold in use
+    unsigned int qprefix;       // radix-select prefix (quantile mode)
+    long long qk;        // rank still to find (quantile mode)
+    long long qk0;       // rank asked for, k = ceil(q n)
+    int n_fg;            // fixed foreground pixels
+    int pad[7];
+};
+static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
+
+constexpr int kScanItems = 1024;        // items per block of the exclusive scan
+constexpr int kHistBins = 256;          // radix-select digit bins (8 bits per pass)
+constexpr int kReduceBlocks = 1024;     // fixed grid of deterministic FP64 reductions
+constexpr int kEnergyTerms = 8;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Byte offsets of the workspace regions for one image geometry.
+struct WsLayout {
+    size_t header, tile_cnt, tile_flag, tile_start, tile_pos, scan_tmp, partials,
+        hist, red, total;
+    int64_t ntiles;
+    int64_t scan_tmp_items;
+};
+
+inline int64_t scan_tmp_items_for(int64_t n) {
+    int64_t tot = 0;
+    while (n > 1) {
+        n = (n + kScanItems - 1) / kScanItems;
+        tot += n + 1;
+    }
+    return tot + 2;
+}
+
+// Geometry-independent regions come first so that calls that need only
+// them (fitting, energy) accept any workspace sized for the image.
+constexpr size_t kWsHeaderOff = 0;
+constexpr size_t kWsRedOff = 256;
+constexpr size_t kWsHistOff = kWsRedOff + 8 * (size_t)kReduceBlocks * kEnergyTerms;
+constexpr size_t kWsFixedBytes = kWsHistOff + 4 * (size_t)kHistBins;
+
+inline WsLayout ws_layout(int H, int W, int tile_h) {
+    WsLayout L{};
+    int64_t nty = (H + tile_h - 1) / tile_h, ntx = (W + 31) / 32;
+    L.ntiles = nty * ntx;
+    L.scan_tmp_items = scan_tmp_items_for(L.ntiles);
+    L.header = kWsHeaderOff;
+    L.red = kWsRedOff;
+    L.hist = kWsHistOff;
+    size_t o = align_up(kWsFixedBytes, 256);
+    L.tile_cnt = o;   o = align_up(o + 4 * (size_t)(L.ntiles + 1), 256);
+    L.tile_flag = o;  o = align_up(o + 4 * (size_t)(L.ntiles + 1), 256);
+    L.tile_start = o; o = align_up(o + 4 * (size_t)(L.ntiles + 1), 256);
+    L.tile_pos = o;   o = align_up(o + 4 * (size_t)(L.ntiles + 1), 256);
+    L.scan_tmp = o;   o = align_up(o + 4 * (size_t)L.scan_tmp_items, 256);
+    L.partials = o;   o = align_up(o + 2 * 8 * (size_t)(L.ntiles + 1), 256);
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+inline T* ws_at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+// Validates a workspace pointer/size for a geometry.
+seg_status check_ws(void* ws, size_t ws_bytes, const WsLayout& L);
+
+// ------------------------------------------------------ device utilities
+
+__device__ __forceinline__ void record_status(WsHeader* h, int st) {
+    atomicCAS(&h->status, SEG_OK, st);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt(int b) { return (1u << b) - 1u; }
+
+// storage-type converters (arithmetic is always float32)
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float* p, int64_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ float ld_rw(const float* p, int64_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(float* p, int64_t i, float x) { p[i] = x; }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(__ldg(p + i)); }
+    static __device__ __forceinline__ float ld_rw(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float x) { p[i] = __float2bfloat16_rn(x); }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
+    static __device__ __forceinline__ float ld_rw(const __half* p, int64_t i) { return __half2float(p[i]); }
+    static __device__ __forceinline__ void st(__half* p, int64_t i, float x) { p[i] = __float2half_rn(x); }
+};
+
+inline size_t storage_size(int storage) { return storage == SEG_STORE_F32 ? 4 : 2; }
+
+// ---------------------------------------------------- internal launchers
+
+// Exclusive scan of n int32 values (in may equal out); writes the total to
+// *total (device).  Deterministic (integer adds in a fixed tree).
+seg_status scan_exclusive(const int* in, int* out, int64_t n, int* total, int* tmp,
+                          cudaStream_t s);
+
+// Deterministic FP64 sum of `terms` interleaved partial arrays written by
+// `nblk` blocks (red[k * terms + t]); writes sums to out[t].
+seg_status reduce_partials(const double* red, int nblk, int terms, double* out, cudaStream_t s);
+
+}  // namespace seg

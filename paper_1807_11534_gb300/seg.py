@@ -1,0 +1,349 @@
+"""Python binding of libseg (include/seg.h): the same entry points, argument
+marshalling only.
+
+Every ``seg_*`` function here forwards to the C ABI with raw device pointers
+taken from torch tensors and the current torch CUDA stream; all arithmetic runs
+in the CUDA kernels of libseg.  There is no CPU fallback: if the library cannot
+be loaded the import raises.
+
+Higher up, ``Domain`` and ``solve_image`` only allocate buffers (through
+torch) and chain the entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+SEG_OK = 0
+SEG_ERR_INVALID_ARG = 1
+SEG_ERR_ALIGN = 2
+SEG_ERR_CUDA = 3
+SEG_ERR_CAPACITY = 4
+SEG_ERR_TIMEOUT = 5
+SEG_ERR_NONFINITE = 6
+SEG_ERR_WORKSPACE = 7
+
+SEG_MODE_DENSE = 0
+SEG_MODE_COMPACT = 1
+SEG_STORE_F32 = 0
+SEG_STORE_BF16 = 1
+SEG_STORE_F16 = 2
+
+_STORE_BY_NAME = {"f32": SEG_STORE_F32, "fp32": SEG_STORE_F32, "bf16": SEG_STORE_BF16,
+                  "f16": SEG_STORE_F16, "fp16": SEG_STORE_F16}
+
+
+class SegError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libseg status {status}: {msg}")
+        self.status = status
+
+
+class seg_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("theta", ctypes.c_double),
+                ("tau", ctypes.c_double), ("tol", ctypes.c_double),
+                ("iters", ctypes.c_int), ("n_inner", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("mode", ctypes.c_int), ("storage", ctypes.c_int),
+                ("tile_h", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+_lib = None
+
+# exported entry points and their C signatures (include/seg.h)
+_P, _I, _L, _D, _F, _Z = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                          ctypes.c_float, ctypes.c_size_t)
+SIGNATURES = {
+    "seg_version": ([], _I),
+    "seg_last_error": ([], ctypes.c_char_p),
+    "seg_launch_count": ([], ctypes.c_ulonglong),
+    "seg_workspace_bytes": ([_I, _I, _I, _I], _Z),
+    "seg_state_bytes": ([_I, _I, _L, _I, _I], _Z),
+    "seg_read_status": ([_P, _Z, _P], _I),
+    "seg_make_fitting": ([_P, _I, _I, _I, _D, _D, _P, _P, _I, _D, _P, _P, _P, _Z, _P], _I),
+    "seg_build_domain": ([_P, _I, _I, _I, _D, _D, _I, _P, _P, _P, _P, _I, _P, _L, _P, _P, _P, _Z, _P], _I),
+    "seg_solve": ([_P, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(seg_params),
+                   _P, _P, _P, _P, _P, _Z, _P, _P, _Z, _P], _I),
+    "seg_energy": ([_P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _P, _P, _Z, _P], _I),
+    "seg_errors": ([_P, _P, _I, _I, _I, _D, _P, _P, _Z, _P], _I),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libseg.so (building it first if needed).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"libseg not built at {path}")
+        _build.build()
+    if torch.cuda.is_available():
+        torch.cuda.init()   # share torch's CUDA runtime / primary context
+    lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != SEG_OK:
+        msg = _lib.seg_last_error().decode(errors="replace")
+        raise SegError(st, msg)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("libseg takes device tensors only")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------- thin wrappers
+
+def seg_version():
+    return load().seg_version()
+
+
+def seg_launch_count():
+    return load().seg_launch_count()
+
+
+def seg_workspace_bytes(H, W, ld, tile_h):
+    return load().seg_workspace_bytes(H, W, ld, tile_h)
+
+
+def seg_state_bytes(H, ld, capacity, mode, storage):
+    return load().seg_state_bytes(H, ld, capacity, mode, storage)
+
+
+def seg_read_status(ws, stream=None):
+    lib = load()
+    _check(lib.seg_read_status(_ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def seg_make_fitting(z, c1, c2, label, markers, gamma, f, c_out, ws, stream=None):
+    lib = load()
+    n_markers = 0 if markers is None else markers.shape[0]
+    _check(lib.seg_make_fitting(_ptr(z), z.shape[0], _W(z), z.stride(0), float(c1), float(c2), _ptr(label),
+                                _ptr(markers), n_markers, float(gamma), _ptr(f), _ptr(c_out),
+                                _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def seg_build_domain(f, delta, q, tile_h, act, fg, wstart, tiles, pixels, counts, delta_out, ws,
+                     stream=None):
+    lib = load()
+    _check(lib.seg_build_domain(_ptr(f), f.shape[0], _W(f), f.stride(0), float(delta), float(q),
+                                int(tile_h), _ptr(act), _ptr(fg), _ptr(wstart), _ptr(tiles),
+                                tiles.numel(), _ptr(pixels),
+                                0 if pixels is None else pixels.numel(), _ptr(counts),
+                                _ptr(delta_out), _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def seg_solve(f, act, fg, wstart, tiles, counts, params: seg_params, u, v, p1, p2, state, stats,
+              ws, stream=None):
+    lib = load()
+    _check(lib.seg_solve(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(act), _ptr(fg), _ptr(wstart),
+                         _ptr(tiles), _ptr(counts), ctypes.byref(params), _ptr(u), _ptr(v), _ptr(p1),
+                         _ptr(p2), _ptr(state), _nbytes(state), _ptr(stats), _ptr(ws), _nbytes(ws),
+                         _stream(stream)))
+
+
+def seg_energy(f, u, v, p1, p2, lam, theta, out, ws, stream=None):
+    lib = load()
+    _check(lib.seg_energy(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(u), _ptr(v), _ptr(p1),
+                          _ptr(p2), float(lam), float(theta), _ptr(out), _ptr(ws), _nbytes(ws),
+                          _stream(stream)))
+
+
+def seg_errors(u_star, u_gt, eps, out, ws, stream=None):
+    lib = load()
+    _check(lib.seg_errors(_ptr(u_star), _ptr(u_gt), u_star.shape[0], _W(u_star), u_star.stride(0),
+                          float(eps), _ptr(out), _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def _nbytes(t):
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+# Images are passed as [H][ld] views whose logical width is kept in an
+# attribute set by `image()`; a plain [H][W] contiguous tensor is fine too
+# when W is a multiple of 32.
+def _W(t):
+    return getattr(t, "_seg_w", t.shape[1])
+
+
+# ------------------------------------------------------------ allocation
+
+def pitch(W: int) -> int:
+    return (W + 31) // 32 * 32
+
+
+def image(H, W, dtype=torch.float32, device="cuda", fill=0):
+    """[H][ld] device buffer with ld = W rounded up to 32; returns a tensor of
+    shape [H, ld] tagged with its logical width W."""
+    ld = pitch(W)
+    t = torch.full((H, ld), fill, dtype=dtype, device=device)
+    t._seg_w = W
+    return t
+
+
+def upload(a, device="cuda"):
+    """Host array [H, W] -> pitched device image [H, ld]."""
+    a = torch.as_tensor(a)
+    H, W = a.shape
+    t = image(H, W, dtype=a.dtype, device=device)
+    t[:, :W].copy_(a)
+    return t
+
+
+def download(t):
+    return t[:, :_W(t)].cpu().numpy()
+
+
+def workspace(H, W, tile_h=16, device="cuda"):
+    nb = seg_workspace_bytes(H, W, pitch(W), tile_h)
+    return torch.zeros((nb + 15) // 16 * 16, dtype=torch.uint8, device=device)
+
+
+@dataclass
+class Domain:
+    """Outputs of seg_build_domain for one image."""
+
+    H: int
+    W: int
+    tile_h: int
+    act: torch.Tensor
+    fg: torch.Tensor
+    wstart: torch.Tensor
+    tiles: torch.Tensor
+    pixels: torch.Tensor | None
+    counts: torch.Tensor
+    delta: torch.Tensor
+
+    @property
+    def n_tiles_total(self):
+        return -(-self.H // self.tile_h) * -(-self.W // 32)
+
+
+def build_domain(f, delta=math.inf, q=-1.0, tile_h=16, ws=None, with_pixels=True, stream=None):
+    H, W = f.shape[0], _W(f)
+    ld = f.stride(0)
+    dev = f.device
+    nw = ld // 32
+    ntiles = -(-H // tile_h) * -(-W // 32)
+    dom = Domain(H, W, tile_h,
+                 act=torch.zeros((H, nw), dtype=torch.int32, device=dev),
+                 fg=torch.zeros((H, nw), dtype=torch.int32, device=dev),
+                 wstart=torch.zeros((H, nw), dtype=torch.int32, device=dev),
+                 tiles=torch.zeros(max(ntiles, 1), dtype=torch.int32, device=dev),
+                 pixels=torch.zeros(max(H * W, 1), dtype=torch.int32, device=dev) if with_pixels else None,
+                 counts=torch.zeros(4, dtype=torch.int32, device=dev),
+                 delta=torch.zeros(1, dtype=torch.float32, device=dev))
+    if ws is None:
+        ws = workspace(H, W, tile_h, dev)
+    seg_build_domain(f, delta, q, tile_h, dom.act, dom.fg, dom.wstart, dom.tiles, dom.pixels,
+                     dom.counts, dom.delta, ws, stream)
+    return dom
+
+
+def make_params(lam, theta=0.2, tau=0.125, iters=100, tol=0.0, n_inner=1, check_every=10,
+                warm_start=False, mode="compact", storage="f32", tile_h=16) -> seg_params:
+    return seg_params(float(lam), float(theta), float(tau), float(tol), int(iters), int(n_inner),
+                      int(check_every), int(bool(warm_start)),
+                      SEG_MODE_COMPACT if mode == "compact" else SEG_MODE_DENSE,
+                      _STORE_BY_NAME[storage] if isinstance(storage, str) else int(storage),
+                      int(tile_h), 0)
+
+
+def state_buffer(H, W, capacity, mode="compact", storage="f32", device="cuda"):
+    m = SEG_MODE_COMPACT if mode == "compact" else SEG_MODE_DENSE
+    s = _STORE_BY_NAME[storage] if isinstance(storage, str) else int(storage)
+    nb = seg_state_bytes(H, pitch(W), int(capacity), m, s)
+    return torch.empty((nb + 15) // 16 * 16, dtype=torch.uint8, device=device)
+
+
+class Solver:
+    """Buffers for one H x W image and the chain fitting -> domain -> solve ->
+    energy through the C ABI.  Allocation only (torch); every step runs in
+    libseg's kernels on the current (or given) stream."""
+
+    def __init__(self, H, W, tile_h=16, mode="compact", storage="f32", capacity=None,
+                 device="cuda", stream=None):
+        self.H, self.W, self.tile_h = H, W, tile_h
+        self.mode, self.storage = mode, storage
+        self.device = torch.device(device)
+        self.stream = stream
+        self.ws = workspace(H, W, tile_h, self.device)
+        self.capacity = H * W if capacity is None else int(capacity)
+        self.state = state_buffer(H, W, self.capacity, mode, storage, self.device)
+        self.f = image(H, W, device=self.device)
+        self.u = image(H, W, device=self.device)
+        self.v = image(H, W, device=self.device)
+        self.p1 = image(H, W, device=self.device)
+        self.p2 = image(H, W, device=self.device)
+        self.stats = torch.zeros(8, dtype=torch.float64, device=self.device)
+        self.c = torch.zeros(2, dtype=torch.float64, device=self.device)
+        self.energy_out = torch.zeros(6, dtype=torch.float64, device=self.device)
+        self.err_out = torch.zeros(2, dtype=torch.float64, device=self.device)
+        self.dom = None
+
+    def fitting(self, z, c1=0.3, c2=0.7, label=None, markers=None, gamma=0.0):
+        seg_make_fitting(z, c1, c2, label, markers, gamma, self.f, self.c, self.ws, self.stream)
+        return self.f
+
+    def domain(self, f=None, delta=math.inf, q=-1.0, with_pixels=True):
+        f = self.f if f is None else f
+        if self.dom is None or (self.dom.pixels is None) == with_pixels:
+            self.dom = build_domain(f, delta, q, self.tile_h, self.ws, with_pixels, self.stream)
+        else:
+            d = self.dom
+            seg_build_domain(f, delta, q, self.tile_h, d.act, d.fg, d.wstart, d.tiles, d.pixels,
+                             d.counts, d.delta, self.ws, self.stream)
+        return self.dom
+
+    def solve(self, lam, theta=0.2, tau=0.125, iters=100, tol=0.0, n_inner=1, check_every=10,
+              warm_start=False, f=None):
+        f = self.f if f is None else f
+        d = self.dom
+        prm = make_params(lam, theta, tau, iters, tol, n_inner, check_every, warm_start,
+                          self.mode, self.storage, self.tile_h)
+        seg_solve(f, d.act, d.fg, d.wstart, d.tiles, d.counts, prm, self.u, self.v, self.p1,
+                  self.p2, self.state, self.stats, self.ws, self.stream)
+        return self.stats
+
+    def energy(self, lam, theta=0.2, f=None):
+        f = self.f if f is None else f
+        seg_energy(f, self.u, self.v, self.p1, self.p2, lam, theta, self.energy_out, self.ws,
+                   self.stream)
+        return self.energy_out
+
+    def errors(self, u_star, u_gt, eps=0.5):
+        seg_errors(u_star, u_gt, eps, self.err_out, self.ws, self.stream)
+        return self.err_out
+
+    def check_status(self):
+        seg_read_status(self.ws, self.stream)

@@ -141,6 +141,14 @@ def test_pixel_and_tile_lists_brute_force(orc):
     exp = [ty * ntx + tx for ty in range(-(-37 // th)) for tx in range(ntx)
            if np.any(reg[ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw] == 2)]
     np.testing.assert_array_equal(tl, np.array(exp, np.int32))
+    # tile-major numbering: same set as the row-major list, grouped by tile
+    pt = orc.pixel_list_tiled(reg, th, tw)
+    np.testing.assert_array_equal(np.sort(pt), pl)
+    key = (pt // 70 // th) * ntx + (pt % 70) // tw
+    assert np.all(np.diff(key) >= 0)
+    for t in np.unique(key):
+        seg_ = pt[key == t]
+        assert np.all(np.diff(seg_) > 0)
 
 
 # ------------------------------------------------------------------ solver
