@@ -179,6 +179,23 @@ seg_status seg_energy(const float* f, int H, int W, int ld,
                       double lambda, double theta, double* out,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* seg_energy without a workspace, for callers that cannot allocate device
+ * memory (code running under stream capture, hosts that forbid further device
+ * allocation, loops where an allocation's implicit synchronisation is not
+ * acceptable).  The paper has no counterpart: this is a library convenience.
+ * Same inputs and output as seg_energy (out: device double[6]); the per-block
+ * partial sums live in a fixed 196,672-byte device array inside the library,
+ * present on every GPU that loads it until the process exits.  Images above
+ * 33,554,432 pixels are rejected with SEG_ERR_CAPACITY.  The first call on a
+ * device looks up that array's address (cudaGetSymbolAddress) and caches it,
+ * so make the first call before any stream capture.  No slot needs clearing
+ * (each call writes every slot it reads); all calls share the array, so calls
+ * that overlap on the GPU race and may return wrong sums.  It never calls
+ * cudaMalloc or cudaFree.  Errors: INVALID_ARG, ALIGN, CAPACITY, CUDA. */
+seg_status seg_energy_noalloc(const float* f, int H, int W, int ld,
+                              const float* u, const float* v, const float* p1, const float* p2,
+                              double lambda, double theta, double* out, void* stream);
+
 /* Error measures of Section 4: out[0] = E1 = N(GT & O*) / N(GT | O*) with
  * GT = {u_gt > eps}, O* = {u_star > eps} (1 when both are empty), out[1] =
  * E2 = sum (u_star - u_gt)^2.  out: device double[2]. */

@@ -17,7 +17,7 @@
 
 namespace seg {
 
-constexpr int kEnThreads = 256;
+constexpr int kEnThreads = kEnergyBlockThreads;
 
 template <int NTERMS>
 __device__ __forceinline__ void block_store_terms(double (&acc)[NTERMS], double* red) {

@@ -70,6 +70,7 @@ constexpr int kScanItems = 1024;        // items per block of the exclusive scan
 constexpr int kHistBins = 256;          // radix-select digit bins (8 bits per pass)
 constexpr int kReduceBlocks = 1024;     // fixed grid of deterministic FP64 reductions
 constexpr int kEnergyTerms = 8;
+constexpr int kEnergyBlockThreads = 256;  // block size of the energy / error kernels
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -156,6 +157,16 @@ inline size_t storage_size(int storage) { return storage == SEG_STORE_F32 ? 4 : 
 // *total (device).  Deterministic (integer adds in a fixed tree).
 seg_status scan_exclusive(const int* in, int* out, int64_t n, int* total, int* tmp,
                           cudaStream_t s);
+
+// Energy kernels (energy.cu), written for blocks of kEnergyBlockThreads
+// threads: per-block FP64 partials of the six energy
+// terms over a grid-stride loop, and the combination of their sums.
+__global__ void k_energy_terms(const float* __restrict__ f, int H, int W, int ld,
+                               const float* __restrict__ u, const float* __restrict__ v,
+                               const float* __restrict__ p1, const float* __restrict__ p2,
+                               double lambda, double* __restrict__ red);
+__global__ void k_energy_final(const double* __restrict__ sums, double lambda, double theta,
+                               double* out);
 
 // Deterministic FP64 sum of `terms` interleaved partial arrays written by
 // `nblk` blocks (red[k * terms + t]); writes sums to out[t].

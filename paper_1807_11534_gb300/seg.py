@@ -72,6 +72,7 @@ SIGNATURES = {
                    _P, _P, _P, _P, _P, _Z, _P, _P, _Z, _P], _I),
     "seg_energy": ([_P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _P, _P, _Z, _P], _I),
     "seg_errors": ([_P, _P, _I, _I, _I, _D, _P, _P, _Z, _P], _I),
+    "seg_energy_noalloc": ([_P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _P, _P], _I),
 }
 
 
@@ -177,6 +178,15 @@ def seg_energy(f, u, v, p1, p2, lam, theta, out, ws, stream=None):
     _check(lib.seg_energy(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(u), _ptr(v), _ptr(p1),
                           _ptr(p2), float(lam), float(theta), _ptr(out), _ptr(ws), _nbytes(ws),
                           _stream(stream)))
+
+
+def seg_energy_noalloc(f, u, v, p1, p2, lam, theta, out, stream=None):
+    """seg_energy for callers that cannot allocate: no workspace argument; the
+    library's fixed device scratch array is used instead (see include/seg.h)."""
+    lib = load()
+    _check(lib.seg_energy_noalloc(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(u), _ptr(v),
+                                  _ptr(p1), _ptr(p2), float(lam), float(theta), _ptr(out),
+                                  _stream(stream)))
 
 
 def seg_errors(u_star, u_gt, eps, out, ws, stream=None):
