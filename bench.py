@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile", action="store_true",
+                    help="no timing: one restricted step (delta given by --delta) and one "
+                         "full-domain step, for ncu captures")
+    ap.add_argument("--delta", type=float, default=0.2)
     return ap.parse_args()
 
 
@@ -275,6 +279,30 @@ def run_ours(args, rank, world):
     return res
 
 
+def run_profile(args):
+    """One restricted and one full-domain step of the workload, untimed (the
+    command line that the ncu captures under profiles/ run)."""
+    import torch
+    from paper_1807_11534_gb300 import seg
+    dev = torch.device("cuda", 0)
+    P = make_problem(args)
+    H, W = P.z.shape
+    z = seg.upload(P.z, dev)
+    label = seg.upload(P.label, dev)
+    markers = torch.from_numpy(P.markers.astype(np.int32)).to(dev)
+    for mode, delta in (("compact", args.delta), ("dense", math.inf)):
+        S = seg.Solver(H, W, tile_h=args.tile_h, mode=mode,
+                       storage=args.storage if mode == "compact" else "f32", device=dev)
+        S.fitting(z, label=label, markers=markers, gamma=P.gamma)
+        S.domain(delta=delta)
+        S.solve(args.lam, iters=P.iters, check_every=10)
+        S.energy(args.lam)
+        torch.cuda.synchronize()
+        S.check_status()
+        print(f"{mode}: delta={delta} active={int(S.dom.counts[1])} tiles={int(S.dom.counts[0])} "
+              f"iters={int(S.stats[0])}")
+
+
 def cpu_baseline(P, delta, seconds):
     """The FP64 oracle (single thread) on a bounded sample of the workload:
     fitting + domain on the full image, then as many restricted iterations as
@@ -305,6 +333,10 @@ def main():
         import torch
         import torch.distributed as dist
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+
+    if args.profile:
+        run_profile(args)
+        return
 
     if args.impl == "reference":
         if rank != 0:

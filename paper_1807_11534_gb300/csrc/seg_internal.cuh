@@ -80,6 +80,7 @@ struct WsLayout {
         hist, red, total;
     int64_t ntiles;
     int64_t scan_tmp_items;
+    int64_t npartials;      // stopping-test partial pairs the workspace holds
 };
 
 inline int64_t scan_tmp_items_for(int64_t n) {
@@ -112,7 +113,12 @@ inline WsLayout ws_layout(int H, int W, int tile_h) {
     L.tile_start = o; o = align_up(o + 4 * (size_t)(L.ntiles + 1), 256);
     L.tile_pos = o;   o = align_up(o + 4 * (size_t)(L.ntiles + 1), 256);
     L.scan_tmp = o;   o = align_up(o + 4 * (size_t)L.scan_tmp_items, 256);
-    L.partials = o;   o = align_up(o + 2 * 8 * (size_t)(L.ntiles + 1), 256);
+    // stopping-test partials: one pair per 29-column x 32-row warp task
+    // (dense mode) or per block of the primal step (compact mode, at most
+    // 4096 blocks)
+    int64_t dense_tasks = (int64_t)((W + 28) / 29) * ((H + 31) / 32);
+    L.npartials = dense_tasks > 4096 ? dense_tasks : 4096;
+    L.partials = o;   o = align_up(o + 2 * 8 * (size_t)(L.npartials + 1), 256);
     L.total = o;
     return L;
 }
@@ -131,22 +137,51 @@ __device__ __forceinline__ void record_status(WsHeader* h, int st) {
 
 __device__ __forceinline__ unsigned lanemask_lt(int b) { return (1u << b) - 1u; }
 
-// storage-type converters (arithmetic is always float32)
+// 32-bit integer hash (the "lowbias32" finaliser of C. Wellons' hash-prospector,
+// a published xorshift-multiply mixer); used as a counter-based generator.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352du;
+    x ^= x >> 15; x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// storage-type converters (arithmetic is always float32).  16-bit stores use
+// unbiased stochastic rounding with the random word `r`: a round-to-nearest
+// store would drop every update smaller than half a unit in the last place,
+// which stalls the fixed-point iteration long before it converges.
 template <typename T> struct Store;
 template <> struct Store<float> {
     static __device__ __forceinline__ float ld(const float* p, int64_t i) { return __ldg(p + i); }
     static __device__ __forceinline__ float ld_rw(const float* p, int64_t i) { return p[i]; }
     static __device__ __forceinline__ void st(float* p, int64_t i, float x) { p[i] = x; }
+    static __device__ __forceinline__ void st_sr(float* p, int64_t i, float x, uint32_t) { p[i] = x; }
 };
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(__ldg(p + i)); }
     static __device__ __forceinline__ float ld_rw(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float x) { p[i] = __float2bfloat16_rn(x); }
+    // bf16 keeps the top 16 bits of the float: adding a uniform 16-bit word to
+    // the discarded bits before truncating rounds up with probability equal
+    // to the discarded fraction (finite values; |x| <= 1 here)
+    static __device__ __forceinline__ void st_sr(__nv_bfloat16* p, int64_t i, float x, uint32_t r) {
+        uint32_t b = __float_as_uint(x);
+        b += r & 0xffffu;
+        p[i] = __ushort_as_bfloat16((unsigned short)(b >> 16));
+    }
 };
 template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
     static __device__ __forceinline__ float ld_rw(const __half* p, int64_t i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void st(__half* p, int64_t i, float x) { p[i] = __float2half_rn(x); }
+    // round to one of the two neighbouring halves with probabilities given by
+    // the distance to each
+    static __device__ __forceinline__ void st_sr(__half* p, int64_t i, float x, uint32_t r) {
+        __half lo = __float2half_rd(x), hi = __float2half_ru(x);
+        float fl = __half2float(lo), fh = __half2float(hi);
+        float u = (float)(r >> 8) * (1.0f / 16777216.0f);
+        p[i] = (fh > fl && u * (fh - fl) < x - fl) ? hi : lo;
+    }
 };
 
 inline size_t storage_size(int storage) { return storage == SEG_STORE_F32 ? 4 : 2; }

@@ -10,20 +10,20 @@
 // row / column; div = -grad^T).  The stopping test of Section 4 compares
 // max(||u'-u||, ||v'-v||) with tol every check_every iterations.
 //
-// Two fused single-pass stencils implement one iteration each:
-//  * dense   : state in [H][ld] float32 ping-pong images; one CTA per 32 x TH
-//              tile of the tile list, with its halo staged in shared memory;
-//              p' is recomputed on the one-pixel halo above / left so u', v'
-//              need no second pass.  RD is the tile list plus the RD bits
-//              (delta = inf makes it the original full-domain method).
-//  * compact : state stored only for RD pixels, in tile-major compact order
-//              (float32, bf16 or fp16 storage, float32 arithmetic).  One CTA
-//              per active tile enumerates its RD pixels (and the RD pixels of
-//              the halo row above / column left), computes p' for them into
-//              shared memory, then u', v' for its own pixels.  Neighbours are
-//              found through the RD bit planes: the compact index of pixel
-//              (i, j) is wstart[i][j/32] + popc(act & lanemask_lt(j%32)).
-// Per-tile FP64 partial sums of |du|^2, |dv|^2 feed a fixed-order reduction,
+// Two implementations:
+//  * dense   : state in [H][ld] float32 ping-pong images.  One warp walks down
+//              a strip of 32 columns with the previous row in registers and
+//              its horizontal neighbours from shuffles; one pass per
+//              iteration, no shared memory.  RD is given by the RD bit plane
+//              (every pixel when RD is the whole image: the original method).
+//  * compact : state stored only for RD pixels, in the tile-major compact order
+//              of the domain (float32, bf16 or fp16 storage, float32
+//              arithmetic).  A neighbour table, built once per solve, holds
+//              for each RD pixel the compact index of the six pixels the
+//              fixed-point step reads (or a code for a fixed / outside pixel).
+//              Each iteration is two fully parallel passes over the RD pixels:
+//              the dual step (p') and the primal step (u', v').
+// Per-block FP64 partial sums of |du|^2, |dv|^2 feed a fixed-order reduction,
 // so the stopping test is deterministic.  Once it fires, a device flag makes
 // every later launch of the solve return immediately.
 #include <algorithm>
@@ -37,154 +37,145 @@ struct IterParams {
     float theta, inv_theta, tau, theta_lambda;
     int H, W, ld, nw, ntx, th;
     int check, write_u;
+    uint32_t seed;   // per-launch seed of the stochastic rounding of 16-bit stores
 };
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
 
-// p' = (p + tau g) / (1 + tau |g|)
+// p' = (p + tau g) / (1 + tau |g|); |g| through the hardware reciprocal square
+// root and the quotient through the fast divide (a few ulp; the iteration is
+// checked against the FP64 oracle to 1e-4).
 __device__ __forceinline__ void chambolle_update(float p1, float p2, float g1, float g2, float tau,
                                                  float& q1, float& q2) {
-    float nrm = sqrtf(fmaf(g1, g1, g2 * g2));
-    float r = __frcp_rn(fmaf(tau, nrm, 1.0f));
+    const float s = fmaf(g1, g1, g2 * g2);
+    const float nrm = s > 0.f ? s * rsqrtf(s) : 0.f;
+    const float r = __fdividef(1.0f, fmaf(tau, nrm, 1.0f));
     q1 = fmaf(tau, g1, p1) * r;
     q2 = fmaf(tau, g2, p2) * r;
 }
 
-// Deterministic block reduction of two FP64 values; returns the sums in
-// thread 0.  All threads of the block must call it.
-template <int NT>
-__device__ __forceinline__ void block_sum2(double a, double b, double* s_red, double& ra, double& rb) {
-    for (int d = 16; d > 0; d >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, d);
-        b += __shfl_down_sync(0xffffffffu, b, d);
-    }
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { s_red[2 * wid] = a; s_red[2 * wid + 1] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0, y = 0;
-        for (int w = 0; w < NT / 32; ++w) { x += s_red[2 * w]; y += s_red[2 * w + 1]; }
-        ra = x;
-        rb = y;
-    }
-    __syncthreads();
-}
-
 // ============================================================ dense stencil
 
-constexpr int kDenseThreads = 256;
-constexpr int kSW = 36;   // shared row stride: columns c0-2 .. c0+33
+// One warp walks down a strip of 32 image columns (lanes) and a band of
+// kDenseBand output rows, keeping the previous row of p1, p2, v, w and p1' in
+// registers.  Per step i it has row i (loaded one step ahead), forms
+// w(i) = div p - v/theta, then p'(i-1) from w(i-1), w(i) and w(i-1) one
+// column right, then u', v' of row i-1 from p'(i-1), p1'(i-2) and p2'(i-1)
+// one column left.  Lane 0 lacks its left neighbour and lane 31 its right
+// one, so p' is exact on lanes 1..30 and u', v' on lanes 2..30: strips
+// overlap by 3 columns and each warp writes kStripOut = 29 columns.
+constexpr int kStripOut = 29;
+constexpr int kDenseBand = 32;
+constexpr int kDenseWarps = 4;
 
-// MASKED: RD given by the act bit plane (restricted); else every pixel of the
-// image is in RD (the unrestricted method).  PONLY: fixed-point sweep for p
-// only (extra inner sweeps), v unchanged.
-template <int TH, bool MASKED, bool PONLY>
-__global__ void __launch_bounds__(kDenseThreads)
-k_step_dense(IterParams P, const int32_t* __restrict__ tiles, const int32_t* __restrict__ counts,
+struct RowVals {
+    float p1, p2, v, f, u;
+    uint32_t act;
+};
+
+template <bool PONLY>
+__device__ __forceinline__ void load_row(RowVals& r, bool valid, int off, int moff, int bit,
+                                         bool need_u, bool full, const uint32_t* __restrict__ act,
+                                         const float* __restrict__ f, const float* __restrict__ p1i,
+                                         const float* __restrict__ p2i, const float* __restrict__ vi,
+                                         const float* u) {
+    if (valid) {
+        r.p1 = __ldg(p1i + off);
+        r.p2 = __ldg(p2i + off);
+        r.v = __ldg(vi + off);
+        r.f = PONLY ? 0.f : __ldg(f + off);
+        r.u = need_u ? u[off] : 0.f;
+        r.act = full ? 1u : ((__ldg(act + moff) >> bit) & 1u);
+    } else {
+        r.p1 = 0.f; r.p2 = 0.f; r.v = 0.f; r.f = 0.f; r.u = 0.f; r.act = 0u;
+    }
+}
+
+// PONLY: fixed-point sweep for p only (extra inner sweeps), v unchanged.
+template <bool PONLY>
+__global__ void __launch_bounds__(kDenseWarps * 32)
+k_step_dense(IterParams P, int n_strips, int n_tasks, const int32_t* __restrict__ counts,
              const uint32_t* __restrict__ act, const float* __restrict__ f,
              const float* __restrict__ p1i, const float* __restrict__ p2i, const float* __restrict__ vi,
              float* __restrict__ p1o, float* __restrict__ p2o, float* __restrict__ vo,
              float* __restrict__ u, double* __restrict__ partials, WsHeader* h) {
-    __shared__ float s1[(TH + 3) * kSW], s2[(TH + 3) * kSW], sv[(TH + 3) * kSW];
-    __shared__ float sw[(TH + 2) * kSW];
-    __shared__ float q1[(TH + 1) * kSW], q2[(TH + 1) * kSW];
-    __shared__ uint32_t sm[TH + 1][2];
-    __shared__ double s_red[2 * (kDenseThreads / 32)];
     if (*(volatile int*)&h->done) return;
-    const int n_tiles = counts[0];
-    const int tid = threadIdx.x;
-    for (int k = blockIdx.x; k < n_tiles; k += gridDim.x) {
-        const int t = tiles[k];
-        const int ty = t / P.ntx, tx = t - ty * P.ntx;
-        const int r0 = ty * TH, c0 = tx * 32;
-        // ---- stage p1, p2, v on rows r0-2..r0+TH, columns c0-2..c0+33
-        for (int e = tid; e < (TH + 3) * kSW; e += kDenseThreads) {
-            int r = e / kSW - 2, c = e % kSW - 2;
-            int i = r0 + r, j = c0 + c;
-            float a = 0.f, b = 0.f, d = 0.f;
-            if (i >= 0 && i < P.H && j >= 0 && j < P.W) {
-                int64_t o = (int64_t)i * P.ld + j;
-                a = p1i[o]; b = p2i[o]; d = vi[o];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool full = counts[1] == P.H * P.W;     // every pixel in RD: no mask loads
+    const bool need_u = !PONLY && P.check;
+    for (int task = blockIdx.x * kDenseWarps + warp; task < n_tasks;
+         task += gridDim.x * kDenseWarps) {
+        const int strip = task % n_strips, band = task / n_strips;
+        const int j = strip * kStripOut - 2 + lane;
+        const bool jin = j >= 0 && j < P.W;
+        const bool notlastc = j < P.W - 1;
+        const bool hasleft = j > 0;
+        const bool outl = lane >= 2 && lane <= 30 && jin;
+        const int rb = band * kDenseBand;
+        const int re = min(rb + kDenseBand, P.H);
+        const int jc = jin ? j : 0;
+        const int bit = jc & 31;
+        int off = (rb - 2) * P.ld + jc;          // H * ld < 2^31 (checked by the caller)
+        int moff = (rb - 2) * P.nw + (jc >> 5);
+        float p1m = 0.f, p2m = 0.f, vm = 0.f, fm = 0.f, um = 0.f, wm = 0.f, q1m = 0.f;
+        uint32_t am = 0u;
+        float du2 = 0.f, dv2 = 0.f;
+        RowVals cur, nxt;
+        int i = rb - 2;
+        load_row<PONLY>(cur, jin && i >= 0 && i < P.H, off, moff, bit, need_u, full, act, f, p1i,
+                        p2i, vi, u);
+        for (; i <= re; ++i) {
+            const int offn = off + P.ld, moffn = moff + P.nw;
+            load_row<PONLY>(nxt, jin && i + 1 >= 0 && i + 1 < P.H && i + 1 <= re, offn, moffn, bit,
+                            need_u, full, act, f, p1i, p2i, vi, u);
+            // w at row i
+            const float a2l = __shfl_up_sync(FULL, cur.p2, 1);
+            const float d1 = (i < P.H - 1 ? cur.p1 : 0.f) - p1m;
+            const float d2 = (notlastc ? cur.p2 : 0.f) - (hasleft ? a2l : 0.f);
+            const float w = (d1 + d2) - cur.v * P.inv_theta;
+            // p' at row i-1
+            const int im = i - 1;
+            const float wr = __shfl_down_sync(FULL, wm, 1);
+            float q1 = 0.f, q2 = 0.f;
+            if (am) {
+                const float g1 = im < P.H - 1 ? w - wm : 0.f;
+                const float g2 = notlastc ? wr - wm : 0.f;
+                chambolle_update(p1m, p2m, g1, g2, P.tau, q1, q2);
             }
-            s1[e] = a; s2[e] = b; sv[e] = d;
-        }
-        if (MASKED && tid < (TH + 1) * 2) {
-            int r = tid / 2 - 1, wsel = tid & 1;     // wsel 0: left word, 1: own word
-            int i = r0 + r, wx = tx - 1 + wsel;
-            sm[r + 1][wsel] = (i >= 0 && i < P.H && wx >= 0) ? act[(int64_t)i * P.nw + wx] : 0u;
-        }
-        __syncthreads();
-        // ---- w = div p - v/theta on rows -1..TH, columns -1..32
-        for (int e = tid; e < (TH + 2) * 34; e += kDenseThreads) {
-            int r = e / 34 - 1, c = e % 34 - 1;
-            int i = r0 + r, j = c0 + c;
-            int o = (r + 2) * kSW + (c + 2);
-            float w = 0.f;
-            if (i >= 0 && i < P.H && j >= 0 && j < P.W) {
-                float d1 = (i < P.H - 1 ? s1[o] : 0.f) - s1[o - kSW];
-                float d2 = (j < P.W - 1 ? s2[o] : 0.f) - s2[o - 1];
-                w = (d1 + d2) - sv[o] * P.inv_theta;
-            }
-            sw[(r + 1) * kSW + (c + 1)] = w;
-        }
-        __syncthreads();
-        // ---- p' on rows -1..TH-1, columns -1..31 (RD pixels only)
-        const int prow0 = PONLY ? 0 : -1, pcol0 = PONLY ? 0 : -1;
-        const int npr = TH - prow0, npc = 32 - pcol0;
-        for (int e = tid; e < npr * npc; e += kDenseThreads) {
-            int r = e / npc + prow0, c = e % npc + pcol0;
-            int i = r0 + r, j = c0 + c;
-            float a = 0.f, b = 0.f;
-            bool in = i >= 0 && i < P.H && j >= 0 && j < P.W;
-            if (MASKED && in) {
-                uint32_t wd = c < 0 ? sm[r + 1][0] : sm[r + 1][1];
-                in = (wd >> (c & 31)) & 1u;
-            }
-            if (in) {
-                int ow = (r + 1) * kSW + (c + 1);
-                float g1 = i < P.H - 1 ? sw[ow + kSW] - sw[ow] : 0.f;
-                float g2 = j < P.W - 1 ? sw[ow + 1] - sw[ow] : 0.f;
-                int o = (r + 2) * kSW + (c + 2);
-                chambolle_update(s1[o], s2[o], g1, g2, P.tau, a, b);
-            }
-            q1[(r + 1) * kSW + (c + 1)] = a;
-            q2[(r + 1) * kSW + (c + 1)] = b;
-        }
-        __syncthreads();
-        // ---- u', v' on the tile
-        double du2 = 0.0, dv2 = 0.0;
-        for (int e = tid; e < TH * 32; e += kDenseThreads) {
-            int r = e >> 5, c = e & 31;
-            int i = r0 + r, j = c0 + c;
-            bool in = i < P.H && j < P.W;
-            if (MASKED && in) in = (sm[r + 1][1] >> c) & 1u;
-            if (in) {
-                int64_t og = (int64_t)i * P.ld + j;
-                int oq = (r + 1) * kSW + (c + 1);
-                p1o[og] = q1[oq];
-                p2o[og] = q2[oq];
+            const float q2l = __shfl_up_sync(FULL, q2, 1);
+            // u', v' at row i-1
+            if (am && outl && im >= rb) {
+                const int o = off - P.ld;
+                p1o[o] = q1;
+                p2o[o] = q2;
                 if (!PONLY) {
-                    float div = (i < P.H - 1 ? q1[oq] : 0.f) - q1[oq - kSW] +
-                                (j < P.W - 1 ? q2[oq] : 0.f) - q2[oq - 1];
-                    float vv = sv[(r + 2) * kSW + (c + 2)];
-                    float un = fmaf(-P.theta, div, vv);
-                    float vn = clamp01(fmaf(-P.theta_lambda, f[og], un));
-                    vo[og] = vn;
+                    const float div = ((im < P.H - 1 ? q1 : 0.f) - q1m) +
+                                      ((notlastc ? q2 : 0.f) - (hasleft ? q2l : 0.f));
+                    const float un = fmaf(-P.theta, div, vm);
+                    const float vn = clamp01(fmaf(-P.theta_lambda, fm, un));
+                    vo[o] = vn;
                     if (P.check) {
-                        float a = un - u[og], b = vn - vv;
-                        du2 += (double)(a * a);
-                        dv2 += (double)(b * b);
+                        const float da = un - um, db = vn - vm;
+                        du2 = fmaf(da, da, du2);
+                        dv2 = fmaf(db, db, dv2);
                     }
-                    if (P.write_u) u[og] = un;
+                    if (P.write_u) u[o] = un;
                 }
             }
+            p1m = cur.p1; p2m = cur.p2; vm = cur.v; fm = cur.f; um = cur.u; am = cur.act;
+            wm = w; q1m = q1;
+            cur = nxt;
+            off = offn;
+            moff = moffn;
         }
         if (!PONLY && P.check) {
-            double ra, rb;
-            block_sum2<kDenseThreads>(du2, dv2, s_red, ra, rb);
-            if (tid == 0) { partials[2 * k] = ra; partials[2 * k + 1] = rb; }
-        } else {
-            __syncthreads();
+            double a = du2, b = dv2;
+            for (int d = 16; d > 0; d >>= 1) {
+                a += __shfl_down_sync(FULL, a, d);
+                b += __shfl_down_sync(FULL, b, d);
+            }
+            if (lane == 0) { partials[2 * task] = a; partials[2 * task + 1] = b; }
         }
     }
 }
@@ -235,216 +226,37 @@ __global__ void k_final_dense(IterParams P, const WsHeader* __restrict__ h, int 
 
 // ========================================================== compact stencil
 
-constexpr int kCompactThreads = 128;
+constexpr int kCompactThreads = 256;
+
+// neighbour slots of the table and the codes for pixels that are not in RD
+enum { NB_UP = 0, NB_LEFT = 1, NB_DOWN = 2, NB_RIGHT = 3, NB_DOWNLEFT = 4, NB_UPRIGHT = 5, NB_COUNT = 6 };
+constexpr int kNbBg = -1;    // fixed background: p = 0, v = 0
+constexpr int kNbFg = -2;    // fixed foreground: p = 0, v = 1
+constexpr int kNbOut = -3;   // outside the image (the gradient there is 0)
 
 struct CompactState {
-    void *p1[2], *p2[2], *v[2];
+    void *p1[2], *p2[2], *v;
     float* f;
     float* u;
+    int32_t* nb;     // [NB_COUNT][cap]
     int64_t cap;
 };
 
-// Shared-memory view of the rows r0-2..r0+TH of the three word columns
-// tx-1, tx, tx+1 around a tile: RD bits, f<0 bits and compact starts.
-template <int TH>
-struct TileMeta {
-    uint32_t act[TH + 3][3];
-    uint32_t fg[TH + 3][3];
-    int ws[TH + 3][3];
-};
-
-// (active, compact index, fixed v) of local pixel (r, c), r in [-2, TH],
-// c in [-32, 63] relative to the tile origin.
-template <int TH>
-__device__ __forceinline__ bool meta_lookup(const TileMeta<TH>& M, int r, int c, int& idx, float& vfix) {
-    int wc = (c + 32) >> 5;
-    int b = c & 31;
-    uint32_t a = M.act[r + 2][wc];
-    if ((a >> b) & 1u) {
-        idx = M.ws[r + 2][wc] + __popc(a & lanemask_lt(b));
-        return true;
-    }
-    vfix = ((M.fg[r + 2][wc] >> b) & 1u) ? 1.f : 0.f;
-    return false;
+// Compact index of pixel (i, j) when it is in RD, else its code.
+__device__ __forceinline__ int nb_code(const IterParams& P, const uint32_t* __restrict__ act,
+                                       const uint32_t* __restrict__ fgm,
+                                       const int32_t* __restrict__ wstart, int i, int j) {
+    if (i < 0 || i >= P.H || j < 0 || j >= P.W) return kNbOut;
+    const int64_t o = (int64_t)i * P.nw + (j >> 5);
+    const int b = j & 31;
+    const uint32_t a = act[o];
+    if ((a >> b) & 1u) return wstart[o] + __popc(a & lanemask_lt(b));
+    return ((fgm[o] >> b) & 1u) ? kNbFg : kNbBg;
 }
 
-template <typename T, int TH>
-__device__ __forceinline__ void nb_p1(const TileMeta<TH>& M, const T* P1, int r, int c, float& p1) {
-    int idx; float vf;
-    p1 = meta_lookup<TH>(M, r, c, idx, vf) ? Store<T>::ld(P1, idx) : 0.f;
-}
-template <typename T, int TH>
-__device__ __forceinline__ void nb_p2(const TileMeta<TH>& M, const T* P2, int r, int c, float& p2) {
-    int idx; float vf;
-    p2 = meta_lookup<TH>(M, r, c, idx, vf) ? Store<T>::ld(P2, idx) : 0.f;
-}
-template <typename T, int TH>
-__device__ __forceinline__ void nb_all(const TileMeta<TH>& M, const T* P1, const T* P2, const T* V,
-                                       int r, int c, float& p1, float& p2, float& v) {
-    int idx; float vf;
-    if (meta_lookup<TH>(M, r, c, idx, vf)) {
-        p1 = Store<T>::ld(P1, idx); p2 = Store<T>::ld(P2, idx); v = Store<T>::ld(V, idx);
-    } else {
-        p1 = 0.f; p2 = 0.f; v = vf;
-    }
-}
-
-// item encoding: local row r in [-1, TH-1], column c in [-1, 31]
-__device__ __forceinline__ uint16_t pack_rc(int r, int c) { return (uint16_t)(((r + 2) << 8) | (c + 2)); }
-__device__ __forceinline__ void unpack_rc(uint16_t e, int& r, int& c) { r = (e >> 8) - 2; c = (e & 255) - 2; }
-
-template <typename T, int TH, bool PONLY>
-__global__ void __launch_bounds__(kCompactThreads)
-k_step_compact(IterParams P, const int32_t* __restrict__ tiles, const int32_t* __restrict__ counts,
-               const uint32_t* __restrict__ act, const uint32_t* __restrict__ fgm,
-               const int32_t* __restrict__ wstart, const T* __restrict__ P1i,
-               const T* __restrict__ P2i, const T* __restrict__ Vi, T* __restrict__ P1o,
-               T* __restrict__ P2o, T* __restrict__ Vo, const float* __restrict__ F,
-               float* __restrict__ U, double* __restrict__ partials, WsHeader* h) {
-    constexpr int kMaxItems = TH * 32 + 32 + TH;
-    __shared__ TileMeta<TH> M;
-    __shared__ int s_lp[TH + 1];       // exclusive prefix of RD counts of the tile rows
-    __shared__ int s_hcp[TH + 1];      // exclusive prefix of the halo-column RD bits
-    __shared__ int s_cnt[3];           // n_own, halo-row count, halo-column count
-    __shared__ uint16_t s_item[kMaxItems];
-    __shared__ float s_q1[kMaxItems], s_q2[kMaxItems];
-    __shared__ double s_red[2 * (kCompactThreads / 32)];
-    if (*(volatile int*)&h->done) return;
-    const int n_tiles = counts[0];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = blockIdx.x; k < n_tiles; k += gridDim.x) {
-        const int t = tiles[k];
-        const int ty = t / P.ntx, tx = t - ty * P.ntx;
-        const int r0 = ty * TH, c0 = tx * 32;
-        // ---- word metadata of rows r0-2..r0+TH, word columns tx-1..tx+1
-        for (int e = tid; e < (TH + 3) * 3; e += kCompactThreads) {
-            int rr = e / 3, wc = e - rr * 3;
-            int i = r0 + rr - 2, wx = tx - 1 + wc;
-            uint32_t a = 0u, g = 0u;
-            int s = 0;
-            if (i >= 0 && i < P.H && wx >= 0 && wx < P.ntx) {
-                int64_t o = (int64_t)i * P.nw + wx;
-                a = act[o]; g = fgm[o]; s = wstart[o];
-            }
-            M.act[rr][wc] = a; M.fg[rr][wc] = g; M.ws[rr][wc] = s;
-        }
-        __syncthreads();
-        if (wid == 0) {
-            uint32_t a = lane < TH ? M.act[lane + 2][1] : 0u;
-            int c = __popc(a);
-            int hb = lane < TH ? (int)(M.act[lane + 2][0] >> 31) : 0;
-            int ic = c, ih = hb;
-            for (int d = 1; d < 32; d <<= 1) {
-                int o1 = __shfl_up_sync(0xffffffffu, ic, d);
-                int o2 = __shfl_up_sync(0xffffffffu, ih, d);
-                if (lane >= d) { ic += o1; ih += o2; }
-            }
-            if (lane < TH) { s_lp[lane] = ic - c; s_hcp[lane] = ih - hb; }
-            if (lane == TH - 1) { s_lp[TH] = ic; s_hcp[TH] = ih; s_cnt[0] = ic; s_cnt[2] = PONLY ? 0 : ih; }
-            if (lane == 0) s_cnt[1] = PONLY ? 0 : __popc(M.act[1][1]);
-        }
-        __syncthreads();
-        const int n_own = s_cnt[0], n_hr = s_cnt[1], n_hc = s_cnt[2];
-        const int n_items = n_own + n_hr + n_hc;
-        const int tstart = M.ws[2][1];   // compact index of the tile's first RD pixel
-        // ---- enumerate items: own pixels (row-major), halo row, halo column
-        for (int rr = wid; rr < TH + (PONLY ? 0 : 1); rr += kCompactThreads / 32) {
-            if (rr < TH) {
-                uint32_t a = M.act[rr + 2][1];
-                if ((a >> lane) & 1u) s_item[s_lp[rr] + __popc(a & lanemask_lt(lane))] = pack_rc(rr, lane);
-            } else {
-                uint32_t a = M.act[1][1];
-                if ((a >> lane) & 1u) s_item[n_own + __popc(a & lanemask_lt(lane))] = pack_rc(-1, lane);
-            }
-        }
-        if (!PONLY && tid < TH && ((M.act[tid + 2][0] >> 31) & 1u))
-            s_item[n_own + n_hr + s_hcp[tid]] = pack_rc(tid, -1);
-        __syncthreads();
-        // ---- phase 1: p' at every item
-        for (int e = tid; e < n_items; e += kCompactThreads) {
-            int r, c;
-            unpack_rc(s_item[e], r, c);
-            const int i = r0 + r, j = c0 + c;
-            float p1y, p2y, vy;
-            if (e < n_own) {
-                int idx = tstart + e;
-                p1y = Store<T>::ld(P1i, idx); p2y = Store<T>::ld(P2i, idx); vy = Store<T>::ld(Vi, idx);
-            } else {
-                nb_all<T, TH>(M, P1i, P2i, Vi, r, c, p1y, p2y, vy);
-            }
-            float p1_um, p2_lm, p1_d, p2_d, v_d, p1_r, p2_r, v_r, p2_dl, p1_ur;
-            nb_p1<T, TH>(M, P1i, r - 1, c, p1_um);        // y - e1
-            nb_p2<T, TH>(M, P2i, r, c - 1, p2_lm);        // y - e2
-            nb_all<T, TH>(M, P1i, P2i, Vi, r + 1, c, p1_d, p2_d, v_d);   // y + e1
-            nb_all<T, TH>(M, P1i, P2i, Vi, r, c + 1, p1_r, p2_r, v_r);   // y + e2
-            nb_p2<T, TH>(M, P2i, r + 1, c - 1, p2_dl);    // y + e1 - e2
-            nb_p1<T, TH>(M, P1i, r - 1, c + 1, p1_ur);    // y + e2 - e1
-            const bool lr = i < P.H - 1, lc = j < P.W - 1;
-            float w0 = ((lr ? p1y : 0.f) - p1_um) + ((lc ? p2y : 0.f) - p2_lm) - vy * P.inv_theta;
-            float g1 = 0.f, g2 = 0.f;
-            if (lr) {
-                float wd = ((i + 1 < P.H - 1 ? p1_d : 0.f) - p1y) + ((lc ? p2_d : 0.f) - p2_dl) -
-                           v_d * P.inv_theta;
-                g1 = wd - w0;
-            }
-            if (lc) {
-                float wr = ((lr ? p1_r : 0.f) - p1_ur) + ((j + 1 < P.W - 1 ? p2_r : 0.f) - p2y) -
-                           v_r * P.inv_theta;
-                g2 = wr - w0;
-            }
-            float a, b;
-            chambolle_update(p1y, p2y, g1, g2, P.tau, a, b);
-            s_q1[e] = a;
-            s_q2[e] = b;
-        }
-        __syncthreads();
-        // ---- phase 2: u', v' for own pixels, write back
-        double du2 = 0.0, dv2 = 0.0;
-        for (int e = tid; e < n_own; e += kCompactThreads) {
-            int r, c;
-            unpack_rc(s_item[e], r, c);
-            const int i = r0 + r, j = c0 + c;
-            const int idx = tstart + e;
-            float q1 = s_q1[e], q2 = s_q2[e];
-            Store<T>::st(P1o, idx, q1);
-            Store<T>::st(P2o, idx, q2);
-            if (PONLY) continue;
-            float q1u = 0.f, q2l = 0.f;
-            if (r > 0) {
-                uint32_t a = M.act[r + 1][1];
-                if ((a >> c) & 1u) q1u = s_q1[s_lp[r - 1] + __popc(a & lanemask_lt(c))];
-            } else {
-                uint32_t a = M.act[1][1];
-                if ((a >> c) & 1u) q1u = s_q1[n_own + __popc(a & lanemask_lt(c))];
-            }
-            if (c > 0) {
-                if ((M.act[r + 2][1] >> (c - 1)) & 1u) q2l = s_q2[e - 1];
-            } else {
-                if ((M.act[r + 2][0] >> 31) & 1u) q2l = s_q2[n_own + n_hr + s_hcp[r]];
-            }
-            float div = ((i < P.H - 1 ? q1 : 0.f) - q1u) + ((j < P.W - 1 ? q2 : 0.f) - q2l);
-            float vv = Store<T>::ld(Vi, idx);
-            float un = fmaf(-P.theta, div, vv);
-            float vn = clamp01(fmaf(-P.theta_lambda, __ldg(F + idx), un));
-            Store<T>::st(Vo, idx, vn);
-            if (P.check) {
-                float da = un - U[idx], db = vn - vv;
-                du2 += (double)(da * da);
-                dv2 += (double)(db * db);
-            }
-            if (P.write_u) U[idx] = un;
-        }
-        if (!PONLY && P.check) {
-            double ra, rb;
-            block_sum2<kCompactThreads>(du2, dv2, s_red, ra, rb);
-            if (tid == 0) { partials[2 * k] = ra; partials[2 * k + 1] = rb; }
-        } else {
-            __syncthreads();
-        }
-    }
-}
-
-// One warp per mask word: lane b is pixel (i, 32 wx + b).
+// One warp per mask word (lane b is pixel (i, 32 wx + b)): gathers f and the
+// start iterate of every RD pixel into compact order and fills its row of the
+// neighbour table.
 template <typename T>
 __global__ void k_compact_gather(IterParams P, const uint32_t* __restrict__ act,
                                  const uint32_t* __restrict__ fgm, const int32_t* __restrict__ wstart,
@@ -460,30 +272,139 @@ __global__ void k_compact_gather(IterParams P, const uint32_t* __restrict__ act,
         }
         return;
     }
-    int lane = threadIdx.x & 31;
-    int64_t word = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    int64_t nwords = (int64_t)P.H * P.ntx;
+    const int lane = threadIdx.x & 31;
+    const int64_t word = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t nwords = (int64_t)P.H * P.ntx;
     if (word >= nwords) return;
-    int64_t i = word / P.ntx;
-    int wx = (int)(word - i * P.ntx);
-    int64_t wo = i * P.nw + wx;
-    uint32_t a = act[wo];
+    const int i = (int)(word / P.ntx);
+    const int wx = (int)(word - (int64_t)i * P.ntx);
+    const int j = wx * 32 + lane;
+    const int64_t wo = (int64_t)i * P.nw + wx;
+    const uint32_t a = act[wo];
     if (!((a >> lane) & 1u)) return;
-    int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
-    int64_t o = i * P.ld + wx * 32 + lane;
-    float fv = f[o];
-    float hh = ((fgm[wo] >> lane) & 1u) ? 1.f : 0.f;
+    const int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
+    const int64_t o = (int64_t)i * P.ld + j;
+    const float fv = f[o];
+    const float hh = ((fgm[wo] >> lane) & 1u) ? 1.f : 0.f;
     S.f[idx] = fv;
     T* P1 = static_cast<T*>(S.p1[0]);
     T* P2 = static_cast<T*>(S.p2[0]);
-    T* V = static_cast<T*>(S.v[0]);
+    T* V = static_cast<T*>(S.v);
     if (warm) {
-        Store<T>::st(P1, idx, p1[o]); Store<T>::st(P2, idx, p2[o]); Store<T>::st(V, idx, v[o]);
+        // p1 on the last row and p2 on the last column never enter div p;
+        // they are held at 0 (where a cold start keeps them)
+        Store<T>::st(P1, idx, i < P.H - 1 ? p1[o] : 0.f);
+        Store<T>::st(P2, idx, j < P.W - 1 ? p2[o] : 0.f);
+        Store<T>::st(V, idx, v[o]);
         S.u[idx] = u[o];
     } else {
-        Store<T>::st(P1, idx, 0.f); Store<T>::st(P2, idx, 0.f);
+        Store<T>::st(P1, idx, 0.f);
+        Store<T>::st(P2, idx, 0.f);
         Store<T>::st(V, idx, clamp01(fmaf(-P.theta_lambda, fv, hh)));
         S.u[idx] = hh;
+    }
+    int32_t* nb = S.nb;
+    const int64_t cap = S.cap;
+    nb[NB_UP * cap + idx] = nb_code(P, act, fgm, wstart, i - 1, j);
+    nb[NB_LEFT * cap + idx] = nb_code(P, act, fgm, wstart, i, j - 1);
+    nb[NB_DOWN * cap + idx] = nb_code(P, act, fgm, wstart, i + 1, j);
+    nb[NB_RIGHT * cap + idx] = nb_code(P, act, fgm, wstart, i, j + 1);
+    nb[NB_DOWNLEFT * cap + idx] = nb_code(P, act, fgm, wstart, i + 1, j - 1);
+    nb[NB_UPRIGHT * cap + idx] = nb_code(P, act, fgm, wstart, i - 1, j + 1);
+}
+
+template <typename T>
+__device__ __forceinline__ float nb_ld(const T* __restrict__ X, int n) {
+    return n >= 0 ? Store<T>::ld(X, n) : 0.f;
+}
+__device__ __forceinline__ float nb_vfix(int n) { return n == kNbFg ? 1.f : 0.f; }
+
+// Dual step on every RD pixel a (grid-stride):
+//   w(y) = (p1(y) - p1(y-e1)) + (p2(y) - p2(y-e2)) - v(y)/theta at y = x,
+//   x+e1, x+e2; g = (w(x+e1) - w(x), w(x+e2) - w(x)) (0 across the image
+//   border); p'(x) = (p(x) + tau g) / (1 + tau |g|).
+// p1 vanishes on the last row and p2 on the last column (their gradient
+// component is 0 there and they start at 0), so no border masks are needed
+// in w.
+template <typename T>
+__global__ void __launch_bounds__(kCompactThreads)
+k_dual_compact(IterParams P, const int32_t* __restrict__ counts, const int32_t* __restrict__ nb,
+               int64_t cap, const T* __restrict__ P1i, const T* __restrict__ P2i,
+               const T* __restrict__ Vi, T* __restrict__ P1o, T* __restrict__ P2o, WsHeader* h) {
+    if (*(volatile int*)&h->done) return;
+    const int n = counts[1];
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const int n_up = __ldg(nb + NB_UP * cap + a);
+        const int n_left = __ldg(nb + NB_LEFT * cap + a);
+        const int n_down = __ldg(nb + NB_DOWN * cap + a);
+        const int n_right = __ldg(nb + NB_RIGHT * cap + a);
+        const int n_dl = __ldg(nb + NB_DOWNLEFT * cap + a);
+        const int n_ur = __ldg(nb + NB_UPRIGHT * cap + a);
+        const float p1 = Store<T>::ld(P1i, a), p2 = Store<T>::ld(P2i, a), v = Store<T>::ld(Vi, a);
+        const float p1_up = nb_ld(P1i, n_up);
+        const float p2_left = nb_ld(P2i, n_left);
+        const float p1_d = nb_ld(P1i, n_down), p2_d = nb_ld(P2i, n_down);
+        const float v_d = n_down >= 0 ? Store<T>::ld(Vi, n_down) : nb_vfix(n_down);
+        const float p1_r = nb_ld(P1i, n_right), p2_r = nb_ld(P2i, n_right);
+        const float v_r = n_right >= 0 ? Store<T>::ld(Vi, n_right) : nb_vfix(n_right);
+        const float p2_dl = nb_ld(P2i, n_dl);
+        const float p1_ur = nb_ld(P1i, n_ur);
+        const float w0 = (p1 - p1_up) + (p2 - p2_left) - v * P.inv_theta;
+        const float g1 = n_down != kNbOut ? ((p1_d - p1) + (p2_d - p2_dl) - v_d * P.inv_theta) - w0 : 0.f;
+        const float g2 = n_right != kNbOut ? ((p1_r - p1_ur) + (p2_r - p2) - v_r * P.inv_theta) - w0 : 0.f;
+        float q1, q2;
+        chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
+        const uint32_t rnd = mix32((uint32_t)a * 3u + P.seed);
+        Store<T>::st_sr(P1o, a, q1, rnd);
+        Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
+    }
+}
+
+// Primal step on every RD pixel: u' = v - theta div p', v' = clip(u' - theta
+// lambda f) (v updated in place), with per-block FP64 partials of |du|^2 and
+// |dv|^2 for the stopping test.
+template <typename T>
+__global__ void __launch_bounds__(kCompactThreads)
+k_primal_compact(IterParams P, const int32_t* __restrict__ counts, const int32_t* __restrict__ nb,
+                 int64_t cap, const T* __restrict__ P1n, const T* __restrict__ P2n, T* __restrict__ V,
+                 const float* __restrict__ F, float* __restrict__ U, double* __restrict__ partials,
+                 WsHeader* h) {
+    __shared__ double s_red[2 * (kCompactThreads / 32)];
+    if (*(volatile int*)&h->done) return;
+    const int n = counts[1];
+    float du2 = 0.f, dv2 = 0.f;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const int n_up = __ldg(nb + NB_UP * cap + a);
+        const int n_left = __ldg(nb + NB_LEFT * cap + a);
+        const float q1 = Store<T>::ld(P1n, a), q2 = Store<T>::ld(P2n, a);
+        const float q1u = nb_ld(P1n, n_up), q2l = nb_ld(P2n, n_left);
+        const float div = (q1 - q1u) + (q2 - q2l);
+        const float vv = Store<T>::ld_rw(V, a);
+        const float un = fmaf(-P.theta, div, vv);
+        const float vn = clamp01(fmaf(-P.theta_lambda, __ldg(F + a), un));
+        Store<T>::st_sr(V, a, vn, mix32((uint32_t)a * 5u + P.seed));
+        if (P.check) {
+            const float da = un - U[a], db = vn - vv;
+            du2 = fmaf(da, da, du2);
+            dv2 = fmaf(db, db, dv2);
+        }
+        if (P.write_u) U[a] = un;
+    }
+    if (P.check) {
+        double a = du2, b = dv2;
+        for (int d = 16; d > 0; d >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, d);
+            b += __shfl_down_sync(0xffffffffu, b, d);
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) { s_red[2 * wid] = a; s_red[2 * wid + 1] = b; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double x = 0.0, y = 0.0;
+            for (int w = 0; w < kCompactThreads / 32; ++w) { x += s_red[2 * w]; y += s_red[2 * w + 1]; }
+            partials[2 * blockIdx.x] = x;
+            partials[2 * blockIdx.x + 1] = y;
+        }
     }
 }
 
@@ -495,25 +416,25 @@ __global__ void k_compact_scatter(IterParams P, const uint32_t* __restrict__ act
                                   const int32_t* __restrict__ counts, int iters, int n_inner,
                                   CompactState S, const WsHeader* __restrict__ h, float* u, float* v,
                                   float* p1, float* p2) {
-    int lane = threadIdx.x & 31;
-    int64_t word = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    int64_t nwords = (int64_t)P.H * P.ntx;
+    const int lane = threadIdx.x & 31;
+    const int64_t word = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t nwords = (int64_t)P.H * P.ntx;
     if (word >= nwords) return;
-    int64_t i = word / P.ntx;
-    int wx = (int)(word - i * P.ntx);
-    int j = wx * 32 + lane;
+    const int64_t i = word / P.ntx;
+    const int wx = (int)(word - i * P.ntx);
+    const int j = wx * 32 + lane;
     if (j >= P.W) return;
-    int64_t wo = i * P.nw + wx;
-    int64_t o = i * P.ld + j;
-    uint32_t a = act[wo];
-    float hh = ((fgm[wo] >> lane) & 1u) ? 1.f : 0.f;
-    bool ok = counts[1] <= S.cap;
+    const int64_t wo = i * P.nw + wx;
+    const int64_t o = i * P.ld + j;
+    const uint32_t a = act[wo];
+    const float hh = ((fgm[wo] >> lane) & 1u) ? 1.f : 0.f;
+    const bool ok = counts[1] <= S.cap;
     if (ok && ((a >> lane) & 1u)) {
-        int l = h->done ? h->iters_done : iters;
-        int vb = l & 1, pb = (int)(((long long)l * n_inner) & 1);
-        int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
+        const int l = h->done ? h->iters_done : iters;
+        const int pb = (int)(((long long)l * n_inner) & 1);
+        const int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
         u[o] = S.u[idx];
-        v[o] = Store<T>::ld_rw(static_cast<const T*>(S.v[vb]), idx);
+        v[o] = Store<T>::ld_rw(static_cast<const T*>(S.v), idx);
         p1[o] = Store<T>::ld_rw(static_cast<const T*>(S.p1[pb]), idx);
         p2[o] = Store<T>::ld_rw(static_cast<const T*>(S.p2[pb]), idx);
     } else {
@@ -531,19 +452,20 @@ __global__ void k_solve_begin(WsHeader* h) {
     h->dv = 0.0;
 }
 
-// Section 4 stopping test after iteration l: sums the per-tile partials in a
-// fixed order, records the norms and raises the done flag when both are <= tol.
-__global__ void k_check(const double* __restrict__ partials, const int32_t* __restrict__ counts,
-                        int l, double tol, WsHeader* h) {
-    __shared__ double sa[256], sb[256];
+// Section 4 stopping test after iteration l: sums the n partial pairs in a
+// fixed order (thread t owns pairs t, t+1024, ...; then a fixed tree),
+// records the norms and raises the done flag when both are <= tol.
+constexpr int kCheckThreads = 1024;
+__global__ void __launch_bounds__(kCheckThreads)
+k_check(const double* __restrict__ partials, int n, int l, double tol, WsHeader* h) {
+    __shared__ double sa[kCheckThreads], sb[kCheckThreads];
     if (*(volatile int*)&h->done) return;
-    int n = counts[0];
     double a = 0.0, b = 0.0;
-    for (int k = threadIdx.x; k < n; k += 256) { a += partials[2 * k]; b += partials[2 * k + 1]; }
+    for (int k = threadIdx.x; k < n; k += kCheckThreads) { a += partials[2 * k]; b += partials[2 * k + 1]; }
     sa[threadIdx.x] = a;
     sb[threadIdx.x] = b;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
+    for (int w = kCheckThreads / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) { sa[threadIdx.x] += sa[threadIdx.x + w]; sb[threadIdx.x] += sb[threadIdx.x + w]; }
         __syncthreads();
     }
@@ -573,6 +495,13 @@ __global__ void k_solve_end(const WsHeader* __restrict__ h, const int32_t* __res
 
 // ================================================================== host
 
+static uint32_t mix32_host(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352du;
+    x ^= x >> 15; x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
 static int sm_count() {
     static int n = 0;
     if (!n) {
@@ -585,12 +514,12 @@ static int sm_count() {
 }
 
 template <typename K>
-static int grid_for(K kernel, int threads, int64_t max_tiles) {
+static int grid_for(K kernel, int threads, int64_t max_blocks) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
     if (per_sm <= 0) per_sm = 1;
     int64_t g = (int64_t)per_sm * sm_count();
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, max_tiles));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, max_blocks));
 }
 
 struct CompactLayout {
@@ -598,31 +527,36 @@ struct CompactLayout {
     int64_t cap;
 };
 
+// compact state: p1[2], p2[2], v (storage type), f, u (float32), neighbour
+// table (int32 x 6), each array 256-byte aligned
+constexpr int kCompactArrays = 8;
 static CompactLayout compact_layout(size_t state_bytes, int storage) {
     CompactLayout C{};
     size_t sz = storage_size(storage);
-    size_t per = 6 * sz + 8;
-    C.cap = state_bytes > 8 * 256 ? (int64_t)((state_bytes - 8 * 256) / per) : 0;
+    size_t per = 5 * sz + 8 + 4 * NB_COUNT;
+    C.cap = state_bytes > kCompactArrays * 256 ? (int64_t)((state_bytes - kCompactArrays * 256) / per) : 0;
     size_t o = 0;
-    for (int a = 0; a < 6; ++a) { C.off[a] = o; o = align_up(o + sz * (size_t)C.cap, 256); }
-    C.off[6] = o; o = align_up(o + 4 * (size_t)C.cap, 256);
-    C.off[7] = o;
+    for (int a = 0; a < 5; ++a) { C.off[a] = o; o = align_up(o + sz * (size_t)C.cap, 256); }
+    C.off[5] = o; o = align_up(o + 4 * (size_t)C.cap, 256);   // f
+    C.off[6] = o; o = align_up(o + 4 * (size_t)C.cap, 256);   // u
+    C.off[7] = o;                                             // neighbour table
     return C;
 }
 
-template <int TH, bool MASKED>
-static seg_status run_dense(const IterParams& P0, const seg_params* prm, const int32_t* tiles,
-                            const int32_t* counts, const uint32_t* act, const float* f, float* u,
-                            float* st, double* partials, WsHeader* h, int64_t max_tiles,
-                            cudaStream_t s) {
+static seg_status run_dense(const IterParams& P0, const seg_params* prm, const int32_t* counts,
+                            const uint32_t* act, const float* f, float* u, float* st,
+                            double* partials, WsHeader* h, cudaStream_t s) {
     int64_t plane = (int64_t)P0.H * P0.ld;
     float* P1[2] = {st, st + plane};
     float* P2[2] = {st + 2 * plane, st + 3 * plane};
     float* V[2] = {st + 4 * plane, st + 5 * plane};
-    auto kfull = k_step_dense<TH, MASKED, false>;
-    auto kp = k_step_dense<TH, MASKED, true>;
-    int grid = grid_for(kfull, kDenseThreads, max_tiles);
-    int gridp = grid_for(kp, kDenseThreads, max_tiles);
+    auto kfull = k_step_dense<false>;
+    auto kp = k_step_dense<true>;
+    const int n_strips = (P0.W + kStripOut - 1) / kStripOut;
+    const int n_tasks = n_strips * ((P0.H + kDenseBand - 1) / kDenseBand);
+    const int64_t max_blocks = (n_tasks + kDenseWarps - 1) / kDenseWarps;
+    const int grid = grid_for(kfull, kDenseWarps * 32, max_blocks);
+    const int gridp = grid_for(kp, kDenseWarps * 32, max_blocks);
     int pb = 0, vb = 0;
     const int C = std::max(1, prm->check_every);
     for (int it = 0; it < prm->iters; ++it) {
@@ -630,63 +564,21 @@ static seg_status run_dense(const IterParams& P0, const seg_params* prm, const i
         for (int sw = 1; sw < prm->n_inner; ++sw) {
             IterParams P = P0;
             P.check = 0; P.write_u = 0;
-            kp<<<gridp, kDenseThreads, 0, s>>>(P, tiles, counts, act, f, P1[pb], P2[pb], V[vb],
-                                               P1[pb ^ 1], P2[pb ^ 1], V[vb], u, partials, h);
+            kp<<<gridp, kDenseWarps * 32, 0, s>>>(P, n_strips, n_tasks, counts, act, f, P1[pb], P2[pb],
+                                                  V[vb], P1[pb ^ 1], P2[pb ^ 1], V[vb], u, partials, h);
             SEG_LAUNCHED("k_step_dense<p-only>");
             pb ^= 1;
         }
         IterParams P = P0;
         P.check = (l % C == 0) || l == prm->iters;
         P.write_u = P.check || ((l + 1) % C == 0) || l == prm->iters;
-        kfull<<<grid, kDenseThreads, 0, s>>>(P, tiles, counts, act, f, P1[pb], P2[pb], V[vb],
-                                             P1[pb ^ 1], P2[pb ^ 1], V[vb ^ 1], u, partials, h);
+        kfull<<<grid, kDenseWarps * 32, 0, s>>>(P, n_strips, n_tasks, counts, act, f, P1[pb], P2[pb],
+                                                V[vb], P1[pb ^ 1], P2[pb ^ 1], V[vb ^ 1], u, partials, h);
         SEG_LAUNCHED("k_step_dense");
         pb ^= 1;
         vb ^= 1;
         if (P.check) {
-            k_check<<<1, 256, 0, s>>>(partials, counts, l, prm->tol, h);
-            SEG_LAUNCHED("k_check");
-        }
-    }
-    return SEG_OK;
-}
-
-template <typename T, int TH>
-static seg_status run_compact(const IterParams& P0, const seg_params* prm, const int32_t* tiles,
-                              const int32_t* counts, const uint32_t* act, const uint32_t* fgm,
-                              const int32_t* wstart, const CompactState& S, double* partials,
-                              WsHeader* h, int64_t max_tiles, cudaStream_t s) {
-    T* P1[2] = {static_cast<T*>(S.p1[0]), static_cast<T*>(S.p1[1])};
-    T* P2[2] = {static_cast<T*>(S.p2[0]), static_cast<T*>(S.p2[1])};
-    T* V[2] = {static_cast<T*>(S.v[0]), static_cast<T*>(S.v[1])};
-    auto kfull = k_step_compact<T, TH, false>;
-    auto kp = k_step_compact<T, TH, true>;
-    int grid = grid_for(kfull, kCompactThreads, max_tiles);
-    int gridp = grid_for(kp, kCompactThreads, max_tiles);
-    int pb = 0, vb = 0;
-    const int C = std::max(1, prm->check_every);
-    for (int it = 0; it < prm->iters; ++it) {
-        const int l = it + 1;
-        for (int sw = 1; sw < prm->n_inner; ++sw) {
-            IterParams P = P0;
-            P.check = 0; P.write_u = 0;
-            kp<<<gridp, kCompactThreads, 0, s>>>(P, tiles, counts, act, fgm, wstart, P1[pb], P2[pb],
-                                                 V[vb], P1[pb ^ 1], P2[pb ^ 1], V[vb], S.f, S.u,
-                                                 partials, h);
-            SEG_LAUNCHED("k_step_compact<p-only>");
-            pb ^= 1;
-        }
-        IterParams P = P0;
-        P.check = (l % C == 0) || l == prm->iters;
-        P.write_u = P.check || ((l + 1) % C == 0) || l == prm->iters;
-        kfull<<<grid, kCompactThreads, 0, s>>>(P, tiles, counts, act, fgm, wstart, P1[pb], P2[pb],
-                                               V[vb], P1[pb ^ 1], P2[pb ^ 1], V[vb ^ 1], S.f, S.u,
-                                               partials, h);
-        SEG_LAUNCHED("k_step_compact");
-        pb ^= 1;
-        vb ^= 1;
-        if (P.check) {
-            k_check<<<1, 256, 0, s>>>(partials, counts, l, prm->tol, h);
+            k_check<<<1, kCheckThreads, 0, s>>>(partials, n_tasks, l, prm->tol, h);
             SEG_LAUNCHED("k_check");
         }
     }
@@ -694,34 +586,65 @@ static seg_status run_compact(const IterParams& P0, const seg_params* prm, const
 }
 
 template <typename T>
-static seg_status solve_compact_typed(const IterParams& P, const seg_params* prm, const float* f,
+static seg_status solve_compact_typed(const IterParams& P0, const seg_params* prm, const float* f,
                                       const uint32_t* act, const uint32_t* fgm, const int32_t* wstart,
-                                      const int32_t* tiles, const int32_t* counts, float* u, float* v,
-                                      float* p1, float* p2, void* state, size_t state_bytes,
-                                      double* partials, WsHeader* h, int64_t max_tiles, cudaStream_t s) {
+                                      const int32_t* counts, float* u, float* v, float* p1, float* p2,
+                                      void* state, size_t state_bytes, double* partials,
+                                      int64_t max_partials, WsHeader* h, cudaStream_t s) {
     CompactLayout C = compact_layout(state_bytes, prm->storage);
     CompactState S{};
     char* base = static_cast<char*>(state);
-    for (int b = 0; b < 2; ++b) {
-        S.p1[b] = base + C.off[0 + b];
-        S.p2[b] = base + C.off[2 + b];
-        S.v[b] = base + C.off[4 + b];
-    }
-    S.f = reinterpret_cast<float*>(base + C.off[6]);
-    S.u = reinterpret_cast<float*>(base + C.off[7]);
+    S.p1[0] = base + C.off[0];
+    S.p1[1] = base + C.off[1];
+    S.p2[0] = base + C.off[2];
+    S.p2[1] = base + C.off[3];
+    S.v = base + C.off[4];
+    S.f = reinterpret_cast<float*>(base + C.off[5]);
+    S.u = reinterpret_cast<float*>(base + C.off[6]);
+    S.nb = reinterpret_cast<int32_t*>(base + C.off[7]);
     S.cap = C.cap;
-    int64_t nwords = (int64_t)P.H * P.ntx;
-    unsigned gblocks = (unsigned)((nwords + 7) / 8);
-    k_compact_gather<T><<<gblocks, 256, 0, s>>>(P, act, fgm, wstart, counts, f, prm->warm_start, u, v,
+    const int64_t nwords = (int64_t)P0.H * P0.ntx;
+    const unsigned gblocks = (unsigned)((nwords + 7) / 8);
+    k_compact_gather<T><<<gblocks, 256, 0, s>>>(P0, act, fgm, wstart, counts, f, prm->warm_start, u, v,
                                                 p1, p2, S, h);
     SEG_LAUNCHED("k_compact_gather");
-    switch (prm->tile_h) {
-        case 4:  SEG_TRY((run_compact<T, 4>(P, prm, tiles, counts, act, fgm, wstart, S, partials, h, max_tiles, s))); break;
-        case 8:  SEG_TRY((run_compact<T, 8>(P, prm, tiles, counts, act, fgm, wstart, S, partials, h, max_tiles, s))); break;
-        case 16: SEG_TRY((run_compact<T, 16>(P, prm, tiles, counts, act, fgm, wstart, S, partials, h, max_tiles, s))); break;
-        default: SEG_TRY((run_compact<T, 32>(P, prm, tiles, counts, act, fgm, wstart, S, partials, h, max_tiles, s))); break;
+
+    T* P1[2] = {static_cast<T*>(S.p1[0]), static_cast<T*>(S.p1[1])};
+    T* P2[2] = {static_cast<T*>(S.p2[0]), static_cast<T*>(S.p2[1])};
+    T* V = static_cast<T*>(S.v);
+    auto kd = k_dual_compact<T>;
+    auto kq = k_primal_compact<T>;
+    // the grids are fixed for the whole solve (the RD size stays on the
+    // device); the primal grid is also the number of stopping-test partials
+    const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)P0.H * P0.W));
+    const int64_t need = (most + kCompactThreads - 1) / kCompactThreads;
+    const int gd = grid_for(kd, kCompactThreads, need);
+    const int gq = (int)std::min<int64_t>(grid_for(kq, kCompactThreads, need), max_partials);
+    int pb = 0;
+    const int Cc = std::max(1, prm->check_every);
+    for (int it = 0; it < prm->iters; ++it) {
+        const int l = it + 1;
+        for (int sw = 0; sw < prm->n_inner; ++sw) {
+            IterParams P = P0;
+            P.seed = mix32_host(0x51ed270bu ^ (uint32_t)(it * 131 + sw));
+            kd<<<gd, kCompactThreads, 0, s>>>(P, counts, S.nb, S.cap, P1[pb], P2[pb], V, P1[pb ^ 1],
+                                              P2[pb ^ 1], h);
+            SEG_LAUNCHED("k_dual_compact");
+            pb ^= 1;
+        }
+        IterParams P = P0;
+        P.check = (l % Cc == 0) || l == prm->iters;
+        P.write_u = P.check || ((l + 1) % Cc == 0) || l == prm->iters;
+        P.seed = mix32_host(0x2545f491u ^ (uint32_t)it);
+        kq<<<gq, kCompactThreads, 0, s>>>(P, counts, S.nb, S.cap, P1[pb], P2[pb], V, S.f, S.u,
+                                          partials, h);
+        SEG_LAUNCHED("k_primal_compact");
+        if (P.check) {
+            k_check<<<1, kCheckThreads, 0, s>>>(partials, gq, l, prm->tol, h);
+            SEG_LAUNCHED("k_check");
+        }
     }
-    k_compact_scatter<T><<<gblocks, 256, 0, s>>>(P, act, fgm, wstart, counts, prm->iters,
+    k_compact_scatter<T><<<gblocks, 256, 0, s>>>(P0, act, fgm, wstart, counts, prm->iters,
                                                  std::max(1, prm->n_inner), S, h, u, v, p1, p2);
     SEG_LAUNCHED("k_compact_scatter");
     return SEG_OK;
@@ -734,7 +657,7 @@ using namespace seg;
 extern "C" size_t seg_state_bytes(int H, int ld, int64_t capacity, int mode, int storage) {
     if (mode == SEG_MODE_DENSE) return 6 * 4 * (size_t)std::max(H, 0) * (size_t)std::max(ld, 0) + 256;
     size_t sz = storage_size(storage);
-    return 8 * 256 + (size_t)std::max<int64_t>(capacity, 1) * (6 * sz + 8);
+    return kCompactArrays * 256 + (size_t)std::max<int64_t>(capacity, 1) * (5 * sz + 8 + 4 * NB_COUNT);
 }
 
 extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint32_t* act,
@@ -746,8 +669,8 @@ extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint
     if (!prm) return fail(SEG_ERR_INVALID_ARG, "params must be non-NULL");
     if (!f || !act || !fgm || !wstart || !tiles || !counts || !u || !v || !p1 || !p2 || !state || !stats)
         return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
-    if (H <= 0 || W <= 0 || ld < W || (int64_t)H * W >= (1ll << 31))
-        return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d", H, W, ld);
+    if (H <= 0 || W <= 0 || ld < W || (int64_t)H * ld >= (1ll << 31))
+        return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d (H*ld < 2^31)", H, W, ld);
     if (ld % 32) return fail(SEG_ERR_ALIGN, "ld=%d is not a multiple of 32", ld);
     const int th = prm->tile_h;
     if (th != 4 && th != 8 && th != 16 && th != 32)
@@ -788,27 +711,23 @@ extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint
         int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
         k_init_dense<<<blocks, 256, 0, s>>>(P, act, fgm, f, prm->warm_start, p1, p2, v, u, st);
         SEG_LAUNCHED("k_init_dense");
-        switch (th) {
-            case 4:  SEG_TRY((run_dense<4, true>(P, prm, tiles, counts, act, f, u, st, partials, h, L.ntiles, s))); break;
-            case 8:  SEG_TRY((run_dense<8, true>(P, prm, tiles, counts, act, f, u, st, partials, h, L.ntiles, s))); break;
-            case 16: SEG_TRY((run_dense<16, true>(P, prm, tiles, counts, act, f, u, st, partials, h, L.ntiles, s))); break;
-            default: SEG_TRY((run_dense<32, true>(P, prm, tiles, counts, act, f, u, st, partials, h, L.ntiles, s))); break;
-        }
+        SEG_TRY(run_dense(P, prm, counts, act, f, u, st, partials, h, s));
         k_final_dense<<<blocks, 256, 0, s>>>(P, h, prm->iters, prm->n_inner, st, v, p1, p2);
         SEG_LAUNCHED("k_final_dense");
     } else {
         switch (prm->storage) {
             case SEG_STORE_F32:
-                SEG_TRY(solve_compact_typed<float>(P, prm, f, act, fgm, wstart, tiles, counts, u, v, p1, p2,
-                                                   state, state_bytes, partials, h, L.ntiles, s));
+                SEG_TRY(solve_compact_typed<float>(P, prm, f, act, fgm, wstart, counts, u, v, p1, p2,
+                                                   state, state_bytes, partials, L.npartials, h, s));
                 break;
             case SEG_STORE_BF16:
-                SEG_TRY(solve_compact_typed<__nv_bfloat16>(P, prm, f, act, fgm, wstart, tiles, counts, u, v,
-                                                           p1, p2, state, state_bytes, partials, h, L.ntiles, s));
+                SEG_TRY(solve_compact_typed<__nv_bfloat16>(P, prm, f, act, fgm, wstart, counts, u, v, p1,
+                                                           p2, state, state_bytes, partials,
+                                                           L.npartials, h, s));
                 break;
             default:
-                SEG_TRY(solve_compact_typed<__half>(P, prm, f, act, fgm, wstart, tiles, counts, u, v, p1, p2,
-                                                    state, state_bytes, partials, h, L.ntiles, s));
+                SEG_TRY(solve_compact_typed<__half>(P, prm, f, act, fgm, wstart, counts, u, v, p1, p2,
+                                                    state, state_bytes, partials, L.npartials, h, s));
                 break;
         }
     }

@@ -163,7 +163,7 @@ def _problem(shape, seed=0):
 @pytest.mark.parametrize("mode", ["dense", "compact"])
 @pytest.mark.parametrize("delta", [0.05, 0.15, 0.25, math.inf])
 @pytest.mark.parametrize("shape,tile_h", [((67, 131), 8), ((256, 256), 16), ((90, 45), 32),
-                                          ((33, 200), 4)])
+                                          ((33, 200), 4), ((300, 29), 8), ((1, 97), 4)])
 def test_solve_matches_oracle(orc, mode, delta, shape, tile_h):
     P = _problem(shape, seed=shape[1])
     _, f = orc.fitting(P.z, 0.3, 0.7)
