@@ -62,9 +62,23 @@ struct WsHeader {
     long long qk;        // rank still to find (quantile mode)
     long long qk0;       // rank asked for, k = ceil(q n)
     int n_fg;            // fixed foreground pixels
-    int pad[7];
+    // grid barrier of the persistent solver: arrival counter and generation,
+    // on separate cache lines so that polling does not contend with arrivals
+    alignas(128) unsigned bar_count;
+    alignas(64) unsigned bar_gen;
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
+
+__device__ __forceinline__ unsigned atom_add_release_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 constexpr int kScanItems = 1024;        // items per block of the exclusive scan
 constexpr int kHistBins = 256;          // radix-select digit bins (8 bits per pass)
@@ -113,10 +127,10 @@ inline WsLayout ws_layout(int H, int W, int tile_h) {
     L.tile_start = o; o = align_up(o + 4 * (size_t)(L.ntiles + 1), 256);
     L.tile_pos = o;   o = align_up(o + 4 * (size_t)(L.ntiles + 1), 256);
     L.scan_tmp = o;   o = align_up(o + 4 * (size_t)L.scan_tmp_items, 256);
-    // stopping-test partials: one pair per 29-column x 32-row warp task
-    // (dense mode) or per block of the primal step (compact mode, at most
-    // 4096 blocks)
-    int64_t dense_tasks = (int64_t)((W + 28) / 29) * ((H + 31) / 32);
+    // stopping-test partials: one pair per 60-column x (8 or more)-row warp
+    // task (dense mode) or per block of the primal step (compact mode, at
+    // most 4096 blocks)
+    int64_t dense_tasks = (int64_t)((W + 59) / 60) * ((H + 7) / 8);
     L.npartials = dense_tasks > 4096 ? dense_tasks : 4096;
     L.partials = o;   o = align_up(o + 2 * 8 * (size_t)(L.npartials + 1), 256);
     L.total = o;
@@ -150,41 +164,114 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 // unbiased stochastic rounding with the random word `r`: a round-to-nearest
 // store would drop every update smaller than half a unit in the last place,
 // which stalls the fixed-point iteration long before it converges.
+//
+// vbias: v in [0, 1] is stored as v - vbias.  For the 16-bit types vbias = 0.5
+// maps v to [-0.5, 0.5], where the unit in the last place is at most 2^-9
+// (bf16) instead of up to 2^-7 near v = 1, and 0 and 1 stay exact.
 template <typename T> struct Store;
 template <> struct Store<float> {
+    static constexpr float vbias = 0.0f;
     static __device__ __forceinline__ float ld(const float* p, int64_t i) { return __ldg(p + i); }
     static __device__ __forceinline__ float ld_rw(const float* p, int64_t i) { return p[i]; }
     static __device__ __forceinline__ void st(float* p, int64_t i, float x) { p[i] = x; }
-    static __device__ __forceinline__ void st_sr(float* p, int64_t i, float x, uint32_t) { p[i] = x; }
+    // stores x (stochastically rounded for 16-bit types) and returns the
+    // value stored
+    static __device__ __forceinline__ float st_sr(float* p, int64_t i, float x, uint32_t) { p[i] = x; return x; }
 };
 template <> struct Store<__nv_bfloat16> {
+    static constexpr float vbias = 0.5f;
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(__ldg(p + i)); }
     static __device__ __forceinline__ float ld_rw(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float x) { p[i] = __float2bfloat16_rn(x); }
     // bf16 keeps the top 16 bits of the float: adding a uniform 16-bit word to
     // the discarded bits before truncating rounds up with probability equal
     // to the discarded fraction (finite values; |x| <= 1 here)
-    static __device__ __forceinline__ void st_sr(__nv_bfloat16* p, int64_t i, float x, uint32_t r) {
+    static __device__ __forceinline__ float st_sr(__nv_bfloat16* p, int64_t i, float x, uint32_t r) {
         uint32_t b = __float_as_uint(x);
         b += r & 0xffffu;
-        p[i] = __ushort_as_bfloat16((unsigned short)(b >> 16));
+        const __nv_bfloat16 y = __ushort_as_bfloat16((unsigned short)(b >> 16));
+        p[i] = y;
+        return __bfloat162float(y);
     }
 };
 template <> struct Store<__half> {
+    static constexpr float vbias = 0.5f;
     static __device__ __forceinline__ float ld(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
     static __device__ __forceinline__ float ld_rw(const __half* p, int64_t i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void st(__half* p, int64_t i, float x) { p[i] = __float2half_rn(x); }
     // round to one of the two neighbouring halves with probabilities given by
     // the distance to each
-    static __device__ __forceinline__ void st_sr(__half* p, int64_t i, float x, uint32_t r) {
+    static __device__ __forceinline__ float st_sr(__half* p, int64_t i, float x, uint32_t r) {
         __half lo = __float2half_rd(x), hi = __float2half_ru(x);
         float fl = __half2float(lo), fh = __half2float(hi);
         float u = (float)(r >> 8) * (1.0f / 16777216.0f);
-        p[i] = (fh > fl && u * (fh - fl) < x - fl) ? hi : lo;
+        const bool up = fh > fl && u * (fh - fl) < x - fl;
+        p[i] = up ? hi : lo;
+        return up ? fh : fl;
     }
 };
 
 inline size_t storage_size(int storage) { return storage == SEG_STORE_F32 ? 4 : 2; }
+
+// ------------------------------------------- TMA bulk copies and mbarriers
+
+// Shared-memory address of a generic pointer into this CTA's shared memory.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes the barrier initialisation visible to the asynchronous (TMA) proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic shared-memory accesses before later
+// asynchronous-proxy accesses (a bulk copy refilling a buffer).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One arrival on `bar` that also expects `bytes` of transaction completions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// Bulk (non-tensor) TMA copy global -> shared, completing on `bar`.  dst, src
+// and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of `bar` for at most ~1 s of SM clock; returns
+// false (after recording SEG_ERR_TIMEOUT) when the wait runs out.
+constexpr long long kWaitCycles = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, WsHeader* h) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            record_status(h, SEG_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
 
 // ---------------------------------------------------- internal launchers
 

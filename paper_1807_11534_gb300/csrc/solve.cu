@@ -22,7 +22,9 @@
 //              for each RD pixel the compact index of the six pixels the
 //              fixed-point step reads (or a code for a fixed / outside pixel).
 //              Each iteration is two fully parallel passes over the RD pixels:
-//              the dual step (p') and the primal step (u', v').
+//              the dual step (p') and the primal step (u', v'); the primal
+//              step also stores w = div p - v/theta for the next dual step,
+//              which then reads w at three pixels instead of p and v at seven.
 // Per-block FP64 partial sums of |du|^2, |dv|^2 feed a fixed-order reduction,
 // so the stopping test is deterministic.  Once it fires, a device flag makes
 // every later launch of the solve return immediately.
@@ -36,7 +38,6 @@ namespace seg {
 struct IterParams {
     float theta, inv_theta, tau, theta_lambda;
     int H, W, ld, nw, ntx, th;
-    int check, write_u;
     uint32_t seed;   // per-launch seed of the stochastic rounding of 16-bit stores
 };
 
@@ -56,45 +57,47 @@ __device__ __forceinline__ void chambolle_update(float p1, float p2, float g1, f
 
 // ============================================================ dense stencil
 
-// One warp walks down a strip of 32 image columns (lanes) and a band of
-// kDenseBand output rows, keeping the previous row of p1, p2, v, w and p1' in
-// registers.  Per step i it has row i (loaded one step ahead), forms
-// w(i) = div p - v/theta, then p'(i-1) from w(i-1), w(i) and w(i-1) one
-// column right, then u', v' of row i-1 from p'(i-1), p1'(i-2) and p2'(i-1)
-// one column left.  Lane 0 lacks its left neighbour and lane 31 its right
-// one, so p' is exact on lanes 1..30 and u', v' on lanes 2..30: strips
-// overlap by 3 columns and each warp writes kStripOut = 29 columns.
-constexpr int kStripOut = 29;
-constexpr int kDenseBand = 32;
+// One warp walks down a strip of 64 image columns (two per lane, loaded as
+// float2) and a band of band_h output rows, keeping the previous row of
+// p1, p2, v, f, u, w and p1' in registers.  Per step i it has row i (loaded
+// one step ahead), forms w(i) = div p - v/theta, then p'(i-1) from w(i-1),
+// w(i) and w(i-1) one column right, then u', v' of row i-1 from p'(i-1),
+// p1'(i-2) and p2'(i-1) one column left; neighbours across the lane pair come
+// from warp shuffles.  Lane 0 lacks a left and lane 31 a right neighbour, so
+// lanes 1..30 write: strips overlap by 4 columns and each warp writes
+// kStripOut = 60 columns.  No shared memory, no block barriers.
+constexpr int kStripOut = 60;
 constexpr int kDenseWarps = 4;
 
 struct RowVals {
-    float p1, p2, v, f, u;
-    uint32_t act;
+    float2 p1, p2, v, f, u;
+    uint32_t act;   // bit 0: column a in RD, bit 1: column b in RD
 };
 
-template <bool PONLY>
+template <bool PONLY, bool CHECK>
 __device__ __forceinline__ void load_row(RowVals& r, bool valid, int off, int moff, int bit,
-                                         bool need_u, bool full, const uint32_t* __restrict__ act,
+                                         uint32_t inimg, bool full, const uint32_t* __restrict__ act,
                                          const float* __restrict__ f, const float* __restrict__ p1i,
                                          const float* __restrict__ p2i, const float* __restrict__ vi,
                                          const float* u) {
+    const float2 z = make_float2(0.f, 0.f);
     if (valid) {
-        r.p1 = __ldg(p1i + off);
-        r.p2 = __ldg(p2i + off);
-        r.v = __ldg(vi + off);
-        r.f = PONLY ? 0.f : __ldg(f + off);
-        r.u = need_u ? u[off] : 0.f;
-        r.act = full ? 1u : ((__ldg(act + moff) >> bit) & 1u);
+        r.p1 = __ldg(reinterpret_cast<const float2*>(p1i + off));
+        r.p2 = __ldg(reinterpret_cast<const float2*>(p2i + off));
+        r.v = __ldg(reinterpret_cast<const float2*>(vi + off));
+        r.f = PONLY ? z : __ldg(reinterpret_cast<const float2*>(f + off));
+        r.u = CHECK ? *reinterpret_cast<const float2*>(u + off) : z;
+        r.act = full ? inimg : ((__ldg(act + moff) >> bit) & inimg);
     } else {
-        r.p1 = 0.f; r.p2 = 0.f; r.v = 0.f; r.f = 0.f; r.u = 0.f; r.act = 0u;
+        r.p1 = z; r.p2 = z; r.v = z; r.f = z; r.u = z; r.act = 0u;
     }
 }
 
 // PONLY: fixed-point sweep for p only (extra inner sweeps), v unchanged.
-template <bool PONLY>
+// CHECK: accumulate |du|^2, |dv|^2 for the stopping test.  WRITEU: store u'.
+template <bool PONLY, bool CHECK, bool WRITEU>
 __global__ void __launch_bounds__(kDenseWarps * 32)
-k_step_dense(IterParams P, int n_strips, int n_tasks, const int32_t* __restrict__ counts,
+k_step_dense(IterParams P, int n_strips, int n_tasks, int band_h, const int32_t* __restrict__ counts,
              const uint32_t* __restrict__ act, const float* __restrict__ f,
              const float* __restrict__ p1i, const float* __restrict__ p2i, const float* __restrict__ vi,
              float* __restrict__ p1o, float* __restrict__ p2o, float* __restrict__ vo,
@@ -103,64 +106,79 @@ k_step_dense(IterParams P, int n_strips, int n_tasks, const int32_t* __restrict_
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool full = counts[1] == P.H * P.W;     // every pixel in RD: no mask loads
-    const bool need_u = !PONLY && P.check;
     for (int task = blockIdx.x * kDenseWarps + warp; task < n_tasks;
          task += gridDim.x * kDenseWarps) {
         const int strip = task % n_strips, band = task / n_strips;
-        const int j = strip * kStripOut - 2 + lane;
-        const bool jin = j >= 0 && j < P.W;
-        const bool notlastc = j < P.W - 1;
-        const bool hasleft = j > 0;
-        const bool outl = lane >= 2 && lane <= 30 && jin;
-        const int rb = band * kDenseBand;
-        const int re = min(rb + kDenseBand, P.H);
-        const int jc = jin ? j : 0;
-        const int bit = jc & 31;
+        const int ja = strip * kStripOut - 2 + 2 * lane;   // columns ja, ja + 1 (ja even)
+        const int jb = ja + 1;
+        const bool lvalid = ja >= 0 && ja < P.ld;           // the float2 lies inside the pitch
+        const uint32_t inimg = (ja >= 0 && ja < P.W ? 1u : 0u) | (jb >= 0 && jb < P.W ? 2u : 0u);
+        const bool a_nl = ja < P.W - 1, b_nl = jb < P.W - 1;   // not on the last column
+        const bool a_hl = ja > 0;                               // has a left neighbour
+        const bool outl = lane >= 1 && lane <= 30;
+        const int rb = band * band_h;
+        const int re = min(rb + band_h, P.H);
+        const int jc = lvalid ? ja : 0;
+        const int bit = jc & 31;                                // ja even: bits ja, ja+1 in one word
         int off = (rb - 2) * P.ld + jc;          // H * ld < 2^31 (checked by the caller)
         int moff = (rb - 2) * P.nw + (jc >> 5);
-        float p1m = 0.f, p2m = 0.f, vm = 0.f, fm = 0.f, um = 0.f, wm = 0.f, q1m = 0.f;
+        float2 p1m = make_float2(0.f, 0.f), p2m = p1m, vm = p1m, fm = p1m, um = p1m, wm = p1m, q1m = p1m;
         uint32_t am = 0u;
         float du2 = 0.f, dv2 = 0.f;
         RowVals cur, nxt;
         int i = rb - 2;
-        load_row<PONLY>(cur, jin && i >= 0 && i < P.H, off, moff, bit, need_u, full, act, f, p1i,
-                        p2i, vi, u);
+        load_row<PONLY, CHECK>(cur, lvalid && i >= 0 && i < P.H, off, moff, bit, inimg, full, act, f,
+                               p1i, p2i, vi, u);
         for (; i <= re; ++i) {
             const int offn = off + P.ld, moffn = moff + P.nw;
-            load_row<PONLY>(nxt, jin && i + 1 >= 0 && i + 1 < P.H && i + 1 <= re, offn, moffn, bit,
-                            need_u, full, act, f, p1i, p2i, vi, u);
-            // w at row i
-            const float a2l = __shfl_up_sync(FULL, cur.p2, 1);
-            const float d1 = (i < P.H - 1 ? cur.p1 : 0.f) - p1m;
-            const float d2 = (notlastc ? cur.p2 : 0.f) - (hasleft ? a2l : 0.f);
-            const float w = (d1 + d2) - cur.v * P.inv_theta;
+            load_row<PONLY, CHECK>(nxt, lvalid && i + 1 >= 0 && i + 1 < P.H && i + 1 <= re, offn,
+                                   moffn, bit, inimg, full, act, f, p1i, p2i, vi, u);
+            const bool rl = i < P.H - 1;         // row i is not the last row
+            // w at row i (columns a, b)
+            const float p2_la = __shfl_up_sync(FULL, cur.p2.y, 1);
+            float2 w;
+            w.x = ((rl ? cur.p1.x : 0.f) - p1m.x) + ((a_nl ? cur.p2.x : 0.f) - (a_hl ? p2_la : 0.f)) -
+                  cur.v.x * P.inv_theta;
+            w.y = ((rl ? cur.p1.y : 0.f) - p1m.y) + ((b_nl ? cur.p2.y : 0.f) - cur.p2.x) -
+                  cur.v.y * P.inv_theta;
             // p' at row i-1
-            const int im = i - 1;
-            const float wr = __shfl_down_sync(FULL, wm, 1);
-            float q1 = 0.f, q2 = 0.f;
-            if (am) {
-                const float g1 = im < P.H - 1 ? w - wm : 0.f;
-                const float g2 = notlastc ? wr - wm : 0.f;
-                chambolle_update(p1m, p2m, g1, g2, P.tau, q1, q2);
-            }
-            const float q2l = __shfl_up_sync(FULL, q2, 1);
+            const bool rlm = i - 1 < P.H - 1;
+            const float w_rb = __shfl_down_sync(FULL, wm.x, 1);
+            float2 q1, q2;
+            chambolle_update(p1m.x, p2m.x, rlm ? w.x - wm.x : 0.f, a_nl ? wm.y - wm.x : 0.f, P.tau,
+                             q1.x, q2.x);
+            chambolle_update(p1m.y, p2m.y, rlm ? w.y - wm.y : 0.f, b_nl ? w_rb - wm.y : 0.f, P.tau,
+                             q1.y, q2.y);
+            if (!(am & 1u)) { q1.x = 0.f; q2.x = 0.f; }
+            if (!(am & 2u)) { q1.y = 0.f; q2.y = 0.f; }
+            const float q2_la = __shfl_up_sync(FULL, q2.y, 1);
             // u', v' at row i-1
-            if (am && outl && im >= rb) {
+            if (outl && i - 1 >= rb && am) {
                 const int o = off - P.ld;
-                p1o[o] = q1;
-                p2o[o] = q2;
-                if (!PONLY) {
-                    const float div = ((im < P.H - 1 ? q1 : 0.f) - q1m) +
-                                      ((notlastc ? q2 : 0.f) - (hasleft ? q2l : 0.f));
-                    const float un = fmaf(-P.theta, div, vm);
-                    const float vn = clamp01(fmaf(-P.theta_lambda, fm, un));
-                    vo[o] = vn;
-                    if (P.check) {
-                        const float da = un - um, db = vn - vm;
-                        du2 = fmaf(da, da, du2);
-                        dv2 = fmaf(db, db, dv2);
-                    }
-                    if (P.write_u) u[o] = un;
+                float2 un, vn;
+                un.x = fmaf(-P.theta, ((rlm ? q1.x : 0.f) - q1m.x) + ((a_nl ? q2.x : 0.f) - (a_hl ? q2_la : 0.f)), vm.x);
+                un.y = fmaf(-P.theta, ((rlm ? q1.y : 0.f) - q1m.y) + ((b_nl ? q2.y : 0.f) - q2.x), vm.y);
+                vn.x = clamp01(fmaf(-P.theta_lambda, fm.x, un.x));
+                vn.y = clamp01(fmaf(-P.theta_lambda, fm.y, un.y));
+                if (am == 3u) {
+                    *reinterpret_cast<float2*>(p1o + o) = q1;
+                    *reinterpret_cast<float2*>(p2o + o) = q2;
+                    if (!PONLY) *reinterpret_cast<float2*>(vo + o) = vn;
+                    if (!PONLY && WRITEU) *reinterpret_cast<float2*>(u + o) = un;
+                } else if (am & 1u) {
+                    p1o[o] = q1.x; p2o[o] = q2.x;
+                    if (!PONLY) vo[o] = vn.x;
+                    if (!PONLY && WRITEU) u[o] = un.x;
+                } else {
+                    p1o[o + 1] = q1.y; p2o[o + 1] = q2.y;
+                    if (!PONLY) vo[o + 1] = vn.y;
+                    if (!PONLY && WRITEU) u[o + 1] = un.y;
+                }
+                if (!PONLY && CHECK) {
+                    const float dax = (am & 1u) ? un.x - um.x : 0.f, day = (am & 2u) ? un.y - um.y : 0.f;
+                    const float dbx = (am & 1u) ? vn.x - vm.x : 0.f, dby = (am & 2u) ? vn.y - vm.y : 0.f;
+                    du2 = fmaf(dax, dax, fmaf(day, day, du2));
+                    dv2 = fmaf(dbx, dbx, fmaf(dby, dby, dv2));
                 }
             }
             p1m = cur.p1; p2m = cur.p2; vm = cur.v; fm = cur.f; um = cur.u; am = cur.act;
@@ -169,7 +187,7 @@ k_step_dense(IterParams P, int n_strips, int n_tasks, const int32_t* __restrict_
             off = offn;
             moff = moffn;
         }
-        if (!PONLY && P.check) {
+        if (!PONLY && CHECK) {
             double a = du2, b = dv2;
             for (int d = 16; d > 0; d >>= 1) {
                 a += __shfl_down_sync(FULL, a, d);
@@ -238,8 +256,10 @@ struct CompactState {
     void *p1[2], *p2[2], *v;
     float* f;
     float* u;
-    int32_t* nb;     // [NB_COUNT][cap]
+    float* w;        // div p - v/theta of the current iterate
+    int32_t* nb;     // [NB_COUNT][stride]
     int64_t cap;
+    int64_t stride;
 };
 
 // Compact index of pixel (i, j) when it is in RD, else its code.
@@ -295,16 +315,19 @@ __global__ void k_compact_gather(IterParams P, const uint32_t* __restrict__ act,
         // they are held at 0 (where a cold start keeps them)
         Store<T>::st(P1, idx, i < P.H - 1 ? p1[o] : 0.f);
         Store<T>::st(P2, idx, j < P.W - 1 ? p2[o] : 0.f);
-        Store<T>::st(V, idx, v[o]);
+        Store<T>::st(V, idx, v[o] - Store<T>::vbias);
         S.u[idx] = u[o];
     } else {
         Store<T>::st(P1, idx, 0.f);
         Store<T>::st(P2, idx, 0.f);
-        Store<T>::st(V, idx, clamp01(fmaf(-P.theta_lambda, fv, hh)));
+        Store<T>::st(V, idx, clamp01(fmaf(-P.theta_lambda, fv, hh)) - Store<T>::vbias);
         S.u[idx] = hh;
     }
+    // w = div p - v/theta; with p = 0 (cold start) it is -v/theta, else it
+    // is filled by k_w_refresh once the table is complete
+    S.w[idx] = warm ? 0.f : -(Store<T>::ld_rw(V, idx) + Store<T>::vbias) * P.inv_theta;
     int32_t* nb = S.nb;
-    const int64_t cap = S.cap;
+    const int64_t cap = S.stride;
     nb[NB_UP * cap + idx] = nb_code(P, act, fgm, wstart, i - 1, j);
     nb[NB_LEFT * cap + idx] = nb_code(P, act, fgm, wstart, i, j - 1);
     nb[NB_DOWN * cap + idx] = nb_code(P, act, fgm, wstart, i + 1, j);
@@ -314,96 +337,240 @@ __global__ void k_compact_gather(IterParams P, const uint32_t* __restrict__ act,
 }
 
 template <typename T>
+__device__ __forceinline__ float to_f(T x) { return (float)x; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ float to_f<__half>(__half x) { return __half2float(x); }
+
+template <typename T>
 __device__ __forceinline__ float nb_ld(const T* __restrict__ X, int n) {
     return n >= 0 ? Store<T>::ld(X, n) : 0.f;
 }
 __device__ __forceinline__ float nb_vfix(int n) { return n == kNbFg ? 1.f : 0.f; }
 
-// Dual step on every RD pixel a (grid-stride):
-//   w(y) = (p1(y) - p1(y-e1)) + (p2(y) - p2(y-e2)) - v(y)/theta at y = x,
-//   x+e1, x+e2; g = (w(x+e1) - w(x), w(x+e2) - w(x)) (0 across the image
-//   border); p'(x) = (p(x) + tau g) / (1 + tau |g|).
-// p1 vanishes on the last row and p2 on the last column (their gradient
-// component is 0 there and they start at 0), so no border masks are needed
-// in w.
-template <typename T>
-__global__ void __launch_bounds__(kCompactThreads)
-k_dual_compact(IterParams P, const int32_t* __restrict__ counts, const int32_t* __restrict__ nb,
-               int64_t cap, const T* __restrict__ P1i, const T* __restrict__ P2i,
-               const T* __restrict__ Vi, T* __restrict__ P1o, T* __restrict__ P2o, WsHeader* h) {
-    if (*(volatile int*)&h->done) return;
-    const int n = counts[1];
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        const int n_up = __ldg(nb + NB_UP * cap + a);
-        const int n_left = __ldg(nb + NB_LEFT * cap + a);
-        const int n_down = __ldg(nb + NB_DOWN * cap + a);
-        const int n_right = __ldg(nb + NB_RIGHT * cap + a);
-        const int n_dl = __ldg(nb + NB_DOWNLEFT * cap + a);
-        const int n_ur = __ldg(nb + NB_UPRIGHT * cap + a);
-        const float p1 = Store<T>::ld(P1i, a), p2 = Store<T>::ld(P2i, a), v = Store<T>::ld(Vi, a);
-        const float p1_up = nb_ld(P1i, n_up);
-        const float p2_left = nb_ld(P2i, n_left);
-        const float p1_d = nb_ld(P1i, n_down), p2_d = nb_ld(P2i, n_down);
-        const float v_d = n_down >= 0 ? Store<T>::ld(Vi, n_down) : nb_vfix(n_down);
-        const float p1_r = nb_ld(P1i, n_right), p2_r = nb_ld(P2i, n_right);
-        const float v_r = n_right >= 0 ? Store<T>::ld(Vi, n_right) : nb_vfix(n_right);
-        const float p2_dl = nb_ld(P2i, n_dl);
-        const float p1_ur = nb_ld(P1i, n_ur);
-        const float w0 = (p1 - p1_up) + (p2 - p2_left) - v * P.inv_theta;
-        const float g1 = n_down != kNbOut ? ((p1_d - p1) + (p2_d - p2_dl) - v_d * P.inv_theta) - w0 : 0.f;
-        const float g2 = n_right != kNbOut ? ((p1_r - p1_ur) + (p2_r - p2) - v_r * P.inv_theta) - w0 : 0.f;
-        float q1, q2;
-        chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
-        const uint32_t rnd = mix32((uint32_t)a * 3u + P.seed);
-        Store<T>::st_sr(P1o, a, q1, rnd);
-        Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
-    }
+// w at a fixed (non-RD) neighbour y: p(y) = 0, so div p(y) is minus the two
+// p components that flow into y, and v(y) is its fixed value.
+__device__ __forceinline__ float w_fixed(float p_in_1, float p_in_2, int code, float inv_theta) {
+    return -(p_in_1 + p_in_2) - (code == kNbFg ? inv_theta : 0.f);
 }
 
-// Primal step on every RD pixel: u' = v - theta div p', v' = clip(u' - theta
-// lambda f) (v updated in place), with per-block FP64 partials of |du|^2 and
-// |dv|^2 for the stopping test.
-template <typename T>
-__global__ void __launch_bounds__(kCompactThreads)
-k_primal_compact(IterParams P, const int32_t* __restrict__ counts, const int32_t* __restrict__ nb,
-                 int64_t cap, const T* __restrict__ P1n, const T* __restrict__ P2n, T* __restrict__ V,
-                 const float* __restrict__ F, float* __restrict__ U, double* __restrict__ partials,
-                 WsHeader* h) {
-    __shared__ double s_red[2 * (kCompactThreads / 32)];
-    if (*(volatile int*)&h->done) return;
-    const int n = counts[1];
-    float du2 = 0.f, dv2 = 0.f;
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        const int n_up = __ldg(nb + NB_UP * cap + a);
-        const int n_left = __ldg(nb + NB_LEFT * cap + a);
-        const float q1 = Store<T>::ld(P1n, a), q2 = Store<T>::ld(P2n, a);
-        const float q1u = nb_ld(P1n, n_up), q2l = nb_ld(P2n, n_left);
-        const float div = (q1 - q1u) + (q2 - q2l);
-        const float vv = Store<T>::ld_rw(V, a);
-        const float un = fmaf(-P.theta, div, vv);
-        const float vn = clamp01(fmaf(-P.theta_lambda, __ldg(F + a), un));
-        Store<T>::st_sr(V, a, vn, mix32((uint32_t)a * 5u + P.seed));
-        if (P.check) {
-            const float da = un - U[a], db = vn - vv;
-            du2 = fmaf(da, da, du2);
-            dv2 = fmaf(db, db, dv2);
+// ------------------------------------------------ persistent compact solver
+//
+// All iterations of a compact solve run in one cooperative launch: every
+// block owns a contiguous range of compact indices for the whole solve and
+// the passes are separated by grid-wide barriers (all blocks are resident, as
+// the cooperative launch guarantees).  One iteration:
+//   dual phase   p'(x) from w at x, x+e1, x+e2           -> barrier
+//   primal phase u', v', w', stop-test partials          -> barrier
+//   (check iterations) block 0 sums the partials in a fixed order and raises
+//   the done flag, which every block reads after the next barrier.
+constexpr int kPersistThreads = 512;
+
+// Grid-wide barrier (arrival counter + generation), with a bounded wait:
+// thread 0 of each block arrives with a release add and polls the generation
+// with acquire loads until it passes `gen` (the block's count of barriers
+// passed, which every block tracks in a register); the last arrival resets
+// the counter and releases the generation.  Returns false after recording
+// SEG_ERR_TIMEOUT (and raising the done flag) if the others do not arrive
+// within ~1 s.
+__device__ __forceinline__ bool grid_sync(WsHeader* h, unsigned nblocks, unsigned& gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    ++gen;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (atom_add_release_gpu(&h->bar_count, 1u) == nblocks - 1) {
+            h->bar_count = 0u;
+            atom_add_release_gpu(&h->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while ((int)(ld_acquire_gpu(&h->bar_gen) - gen) < 0) {
+                if (clock64() - t0 > kWaitCycles) {
+                    record_status(h, SEG_ERR_TIMEOUT);
+                    h->done = 1;
+                    ok = 0;
+                    break;
+                }
+            }
         }
-        if (P.write_u) U[a] = un;
+        s_ok = ok;
     }
-    if (P.check) {
-        double a = du2, b = dv2;
-        for (int d = 16; d > 0; d >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, d);
-            b += __shfl_down_sync(0xffffffffu, b, d);
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Dual step on the RD pixels [a0, a1) (two per thread in flight):
+//   g = (w(x+e1) - w(x), w(x+e2) - w(x))   (a component is 0 across the
+//       image border), p'(x) = (p(x) + tau g) / (1 + tau |g|),
+// with w = div p - v/theta taken from the primal step's output where the
+// neighbour is in RD, and formed from p(x) and p(x+e1-e2) (resp. p(x+e2-e1))
+// where it is fixed.  p1 vanishes on the last row and p2 on the last column
+// (their gradient component is 0 there and they start at 0).
+template <typename T>
+__device__ __forceinline__ void dual_one(const IterParams& P, int a, const int32_t* __restrict__ nb,
+                                         int64_t stride, const T* __restrict__ P1i,
+                                         const T* __restrict__ P2i, const float* __restrict__ Wc,
+                                         T* __restrict__ P1o, T* __restrict__ P2o, uint32_t seed) {
+    const int n_down = __ldg(nb + NB_DOWN * stride + a);
+    const int n_right = __ldg(nb + NB_RIGHT * stride + a);
+    const int n_dl = __ldg(nb + NB_DOWNLEFT * stride + a);
+    const int n_ur = __ldg(nb + NB_UPRIGHT * stride + a);
+    const float p1 = Store<T>::ld(P1i, a), p2 = Store<T>::ld(P2i, a);
+    const float w0 = __ldg(Wc + a);
+    const float wd = n_down >= 0 ? __ldg(Wc + n_down) : 0.f;
+    const float wr = n_right >= 0 ? __ldg(Wc + n_right) : 0.f;
+    const float p2dl = nb_ld(P2i, n_dl);
+    const float p1ur = nb_ld(P1i, n_ur);
+    float g1 = 0.f, g2 = 0.f;
+    if (n_down != kNbOut) g1 = (n_down >= 0 ? wd : w_fixed(p1, p2dl, n_down, P.inv_theta)) - w0;
+    if (n_right != kNbOut) g2 = (n_right >= 0 ? wr : w_fixed(p1ur, p2, n_right, P.inv_theta)) - w0;
+    float q1, q2;
+    chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
+    const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
+    Store<T>::st_sr(P1o, a, q1, rnd);
+    Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
+}
+
+// Primal step on one RD pixel: u' = v - theta div p', v' = clip(u' - theta
+// lambda f) (v updated in place), w' = div p' - v'/theta for the next dual
+// step.  wonly: just w = div p' - v/theta (between extra fixed-point sweeps,
+// or for a warm start).
+template <typename T>
+__device__ __forceinline__ void primal_one(const IterParams& P, int a, const int32_t* __restrict__ nb,
+                                           int64_t stride, const T* __restrict__ P1n,
+                                           const T* __restrict__ P2n, T* __restrict__ V,
+                                           const float* __restrict__ F, float* __restrict__ U,
+                                           float* __restrict__ Wc, bool wonly, bool check, bool write_u,
+                                           uint32_t seed, float& du2, float& dv2) {
+    const int n_up = __ldg(nb + NB_UP * stride + a);
+    const int n_left = __ldg(nb + NB_LEFT * stride + a);
+    const float q1 = Store<T>::ld(P1n, a), q2 = Store<T>::ld(P2n, a);
+    const float vv = Store<T>::ld_rw(V, a) + Store<T>::vbias;
+    const float q1u = nb_ld(P1n, n_up), q2l = nb_ld(P2n, n_left);
+    const float div = (q1 - q1u) + (q2 - q2l);
+    if (wonly) {
+        Wc[a] = div - vv * P.inv_theta;
+        return;
+    }
+    const float un = fmaf(-P.theta, div, vv);
+    const float vn = clamp01(fmaf(-P.theta_lambda, __ldg(F + a), un));
+    const float vs = Store<T>::st_sr(V, a, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
+                     Store<T>::vbias;
+    Wc[a] = div - vs * P.inv_theta;
+    if (check) {
+        const float da = un - U[a], db = vn - vv;
+        du2 = fmaf(da, da, du2);
+        dv2 = fmaf(db, db, dv2);
+    }
+    if (write_u) U[a] = un;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPersistThreads)
+k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
+                const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
+                T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
+                float* Wc, double* partials, WsHeader* h) {
+    __shared__ double s_red[2 * (kPersistThreads / 32)];
+    // set before the launch (capacity overflow): the same for every block
+    if (*(volatile int*)&h->done) return;
+    const unsigned nblocks = gridDim.x;
+    const int n = counts[1];
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int pb = 0;
+    unsigned gen = 0u;   // barriers passed (the generation counter starts at 0 each solve)
+    float dummy0 = 0.f, dummy1 = 0.f;
+    // current / other ping-pong buffers of p, selected without indexing
+    auto p1c = [&]() { return pb ? P1b : P1a; };
+    auto p2c = [&]() { return pb ? P2b : P2a; };
+    auto p1o = [&]() { return pb ? P1a : P1b; };
+    auto p2o = [&]() { return pb ? P2a : P2b; };
+    if (warm) {   // w of the warm-start iterate
+        for (int a = a0 + tid; a < a1; a += nt)
+            primal_one(P, a, nb, stride, P1a, P2a, V, F, U, Wc, true, false, false, 0u, dummy0, dummy1);
+        if (!grid_sync(h, nblocks, gen)) return;
+    }
+    const int C = check_every;
+    for (int it = 0; it < iters; ++it) {
+        const int l = it + 1;
+        for (int sw = 0; sw < n_inner; ++sw) {
+            const uint32_t seed = mix32(0x51ed270bu ^ (uint32_t)(it * 131 + sw));
+            const T* pi1 = p1c(); const T* pi2 = p2c();
+            T* po1 = p1o(); T* po2 = p2o();
+            int a = a0 + tid;
+            for (; a + nt < a1; a += 2 * nt) {
+                dual_one(P, a, nb, stride, pi1, pi2, Wc, po1, po2, seed);
+                dual_one(P, a + nt, nb, stride, pi1, pi2, Wc, po1, po2, seed);
+            }
+            if (a < a1) dual_one(P, a, nb, stride, pi1, pi2, Wc, po1, po2, seed);
+            pb ^= 1;
+            if (!grid_sync(h, nblocks, gen)) return;
+            // the previous iteration's stopping test may have fired
+            if (sw == 0 && it > 0 && (it % C == 0) && *(volatile int*)&h->done) return;
+            if (sw + 1 < n_inner) {
+                for (int b = a0 + tid; b < a1; b += nt)
+                    primal_one(P, b, nb, stride, p1c(), p2c(), V, F, U, Wc, true, false, false, 0u,
+                               dummy0, dummy1);
+                if (!grid_sync(h, nblocks, gen)) return;
+            }
         }
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) { s_red[2 * wid] = a; s_red[2 * wid + 1] = b; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        const bool check = (l % C == 0) || l == iters;
+        const bool write_u = check || ((l + 1) % C == 0) || l == iters;
+        const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
+        float du2 = 0.f, dv2 = 0.f;
+        const T* q1s = p1c(); const T* q2s = p2c();
+        int a = a0 + tid;
+        for (; a + nt < a1; a += 2 * nt) {
+            primal_one(P, a, nb, stride, q1s, q2s, V, F, U, Wc, false, check, write_u, seed, du2, dv2);
+            primal_one(P, a + nt, nb, stride, q1s, q2s, V, F, U, Wc, false, check, write_u, seed, du2, dv2);
+        }
+        if (a < a1)
+            primal_one(P, a, nb, stride, q1s, q2s, V, F, U, Wc, false, check, write_u, seed, du2, dv2);
+        if (check) {
+            double x = du2, y = dv2;
+            for (int d = 16; d > 0; d >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, d);
+                y += __shfl_down_sync(0xffffffffu, y, d);
+            }
+            const int lane = tid & 31, wid = tid >> 5;
+            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
+            __syncthreads();
+            if (tid == 0) {
+                double sx = 0.0, sy = 0.0;
+                for (int w = 0; w < kPersistThreads / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
+                partials[2 * blockIdx.x] = sx;
+                partials[2 * blockIdx.x + 1] = sy;
+            }
+        }
+        if (!grid_sync(h, nblocks, gen)) return;
+        if (check && blockIdx.x == 0) {
+            // Section 4 stopping test: fixed-order FP64 sum of the block partials
             double x = 0.0, y = 0.0;
-            for (int w = 0; w < kCompactThreads / 32; ++w) { x += s_red[2 * w]; y += s_red[2 * w + 1]; }
-            partials[2 * blockIdx.x] = x;
-            partials[2 * blockIdx.x + 1] = y;
+            for (int k = tid; k < (int)nblocks; k += nt) { x += partials[2 * k]; y += partials[2 * k + 1]; }
+            for (int d = 16; d > 0; d >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, d);
+                y += __shfl_down_sync(0xffffffffu, y, d);
+            }
+            const int lane = tid & 31, wid = tid >> 5;
+            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
+            __syncthreads();
+            if (tid == 0) {
+                double sx = 0.0, sy = 0.0;
+                for (int w = 0; w < kPersistThreads / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
+                const double du = sqrt(sx), dv = sqrt(sy);
+                h->du = du;
+                h->dv = dv;
+                h->last_check = l;
+                if (tol > 0.0 && fmax(du, dv) <= tol) {
+                    h->iters_done = l;
+                    __threadfence();
+                    h->done = 1;
+                }
+            }
+            __syncthreads();
         }
     }
 }
@@ -434,7 +601,7 @@ __global__ void k_compact_scatter(IterParams P, const uint32_t* __restrict__ act
         const int pb = (int)(((long long)l * n_inner) & 1);
         const int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
         u[o] = S.u[idx];
-        v[o] = Store<T>::ld_rw(static_cast<const T*>(S.v), idx);
+        v[o] = Store<T>::ld_rw(static_cast<const T*>(S.v), idx) + Store<T>::vbias;
         p1[o] = Store<T>::ld_rw(static_cast<const T*>(S.p1[pb]), idx);
         p2[o] = Store<T>::ld_rw(static_cast<const T*>(S.p2[pb]), idx);
     } else {
@@ -445,6 +612,8 @@ __global__ void k_compact_scatter(IterParams P, const uint32_t* __restrict__ act
 // =================================================== stopping test, stats
 
 __global__ void k_solve_begin(WsHeader* h) {
+    h->bar_count = 0u;
+    h->bar_gen = 0u;
     h->done = 0;
     h->iters_done = 0;
     h->last_check = 0;
@@ -523,25 +692,40 @@ static int grid_for(K kernel, int threads, int64_t max_blocks) {
 }
 
 struct CompactLayout {
-    size_t off[8];
-    int64_t cap;
+    size_t off[9];
+    int64_t cap;       // RD pixels the state can hold
+    int64_t stride;    // elements allocated per array (cap + a chunk of slack, multiple of 64)
 };
 
-// compact state: p1[2], p2[2], v (storage type), f, u (float32), neighbour
-// table (int32 x 6), each array 256-byte aligned
-constexpr int kCompactArrays = 8;
+// compact state: p1[2], p2[2], v (storage type), f, u, w (float32),
+// neighbour table (int32 x 6 rows), each array 256-byte aligned and `stride`
+// elements long
+constexpr int kCompactArrays = 9;
+constexpr int kSlack = 256;   // spare elements past the capacity in every array
+constexpr size_t compact_per_element(size_t sz) { return 5 * sz + 12 + 4 * NB_COUNT; }
+static int64_t compact_stride(int64_t capacity) {
+    return (int64_t)align_up((size_t)std::max<int64_t>(capacity, 1) + kSlack, 64);
+}
 static CompactLayout compact_layout(size_t state_bytes, int storage) {
     CompactLayout C{};
-    size_t sz = storage_size(storage);
-    size_t per = 5 * sz + 8 + 4 * NB_COUNT;
-    C.cap = state_bytes > kCompactArrays * 256 ? (int64_t)((state_bytes - kCompactArrays * 256) / per) : 0;
+    const size_t sz = storage_size(storage);
+    const size_t per = compact_per_element(sz);
+    int64_t stride = state_bytes > kCompactArrays * 256
+                         ? (int64_t)((state_bytes - kCompactArrays * 256) / per) / 64 * 64 : 0;
+    C.stride = stride;
+    C.cap = std::max<int64_t>(0, stride - kSlack);
     size_t o = 0;
-    for (int a = 0; a < 5; ++a) { C.off[a] = o; o = align_up(o + sz * (size_t)C.cap, 256); }
-    C.off[5] = o; o = align_up(o + 4 * (size_t)C.cap, 256);   // f
-    C.off[6] = o; o = align_up(o + 4 * (size_t)C.cap, 256);   // u
-    C.off[7] = o;                                             // neighbour table
+    for (int a = 0; a < 5; ++a) { C.off[a] = o; o = align_up(o + sz * (size_t)stride, 256); }
+    C.off[5] = o; o = align_up(o + 4 * (size_t)stride, 256);   // f
+    C.off[6] = o; o = align_up(o + 4 * (size_t)stride, 256);   // u
+    C.off[7] = o; o = align_up(o + 4 * (size_t)stride, 256);   // w
+    C.off[8] = o;                                              // neighbour table
     return C;
 }
+
+using DenseKernel = void (*)(IterParams, int, int, int, const int32_t*, const uint32_t*, const float*,
+                             const float*, const float*, const float*, float*, float*, float*, float*,
+                             double*, WsHeader*);
 
 static seg_status run_dense(const IterParams& P0, const seg_params* prm, const int32_t* counts,
                             const uint32_t* act, const float* f, float* u, float* st,
@@ -550,34 +734,38 @@ static seg_status run_dense(const IterParams& P0, const seg_params* prm, const i
     float* P1[2] = {st, st + plane};
     float* P2[2] = {st + 2 * plane, st + 3 * plane};
     float* V[2] = {st + 4 * plane, st + 5 * plane};
-    auto kfull = k_step_dense<false>;
-    auto kp = k_step_dense<true>;
+    // variants: [check][write_u]; p-only sweeps neither check nor write u
+    DenseKernel kv[2][2] = {{k_step_dense<false, false, false>, k_step_dense<false, false, true>},
+                            {k_step_dense<false, true, false>, k_step_dense<false, true, true>}};
+    DenseKernel kp = k_step_dense<true, false, false>;
+    // band height: 32 rows (3 halo rows per band) unless that leaves fewer
+    // than ~48 warps per SM of work, then 16 or 8
     const int n_strips = (P0.W + kStripOut - 1) / kStripOut;
-    const int n_tasks = n_strips * ((P0.H + kDenseBand - 1) / kDenseBand);
+    int band_h = 32;
+    while (band_h > 8 && (int64_t)n_strips * ((P0.H + band_h - 1) / band_h) < 48LL * sm_count())
+        band_h /= 2;
+    const int n_tasks = n_strips * ((P0.H + band_h - 1) / band_h);
     const int64_t max_blocks = (n_tasks + kDenseWarps - 1) / kDenseWarps;
-    const int grid = grid_for(kfull, kDenseWarps * 32, max_blocks);
-    const int gridp = grid_for(kp, kDenseWarps * 32, max_blocks);
+    const int grid = grid_for(kv[1][1], kDenseWarps * 32, max_blocks);
     int pb = 0, vb = 0;
     const int C = std::max(1, prm->check_every);
     for (int it = 0; it < prm->iters; ++it) {
         const int l = it + 1;
         for (int sw = 1; sw < prm->n_inner; ++sw) {
-            IterParams P = P0;
-            P.check = 0; P.write_u = 0;
-            kp<<<gridp, kDenseWarps * 32, 0, s>>>(P, n_strips, n_tasks, counts, act, f, P1[pb], P2[pb],
-                                                  V[vb], P1[pb ^ 1], P2[pb ^ 1], V[vb], u, partials, h);
+            kp<<<grid, kDenseWarps * 32, 0, s>>>(P0, n_strips, n_tasks, band_h, counts, act, f, P1[pb], P2[pb],
+                                                 V[vb], P1[pb ^ 1], P2[pb ^ 1], V[vb], u, partials, h);
             SEG_LAUNCHED("k_step_dense<p-only>");
             pb ^= 1;
         }
-        IterParams P = P0;
-        P.check = (l % C == 0) || l == prm->iters;
-        P.write_u = P.check || ((l + 1) % C == 0) || l == prm->iters;
-        kfull<<<grid, kDenseWarps * 32, 0, s>>>(P, n_strips, n_tasks, counts, act, f, P1[pb], P2[pb],
-                                                V[vb], P1[pb ^ 1], P2[pb ^ 1], V[vb ^ 1], u, partials, h);
+        const bool check = (l % C == 0) || l == prm->iters;
+        const bool write_u = check || ((l + 1) % C == 0) || l == prm->iters;
+        kv[check][write_u]<<<grid, kDenseWarps * 32, 0, s>>>(P0, n_strips, n_tasks, band_h, counts, act, f,
+                                                             P1[pb], P2[pb], V[vb], P1[pb ^ 1],
+                                                             P2[pb ^ 1], V[vb ^ 1], u, partials, h);
         SEG_LAUNCHED("k_step_dense");
         pb ^= 1;
         vb ^= 1;
-        if (P.check) {
+        if (check) {
             k_check<<<1, kCheckThreads, 0, s>>>(partials, n_tasks, l, prm->tol, h);
             SEG_LAUNCHED("k_check");
         }
@@ -601,8 +789,10 @@ static seg_status solve_compact_typed(const IterParams& P0, const seg_params* pr
     S.v = base + C.off[4];
     S.f = reinterpret_cast<float*>(base + C.off[5]);
     S.u = reinterpret_cast<float*>(base + C.off[6]);
-    S.nb = reinterpret_cast<int32_t*>(base + C.off[7]);
+    S.w = reinterpret_cast<float*>(base + C.off[7]);
+    S.nb = reinterpret_cast<int32_t*>(base + C.off[8]);
     S.cap = C.cap;
+    S.stride = C.stride;
     const int64_t nwords = (int64_t)P0.H * P0.ntx;
     const unsigned gblocks = (unsigned)((nwords + 7) / 8);
     k_compact_gather<T><<<gblocks, 256, 0, s>>>(P0, act, fgm, wstart, counts, f, prm->warm_start, u, v,
@@ -612,37 +802,31 @@ static seg_status solve_compact_typed(const IterParams& P0, const seg_params* pr
     T* P1[2] = {static_cast<T*>(S.p1[0]), static_cast<T*>(S.p1[1])};
     T* P2[2] = {static_cast<T*>(S.p2[0]), static_cast<T*>(S.p2[1])};
     T* V = static_cast<T*>(S.v);
-    auto kd = k_dual_compact<T>;
-    auto kq = k_primal_compact<T>;
-    // the grids are fixed for the whole solve (the RD size stays on the
-    // device); the primal grid is also the number of stopping-test partials
+    auto kern = k_solve_compact<T>;
+    // one cooperative launch for the whole solve: the grid is what can be
+    // resident at once (at most one block per 512 RD pixels of capacity)
+    int per_sm = 0;
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, 0));
+    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_compact cannot be resident");
     const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)P0.H * P0.W));
-    const int64_t need = (most + kCompactThreads - 1) / kCompactThreads;
-    const int gd = grid_for(kd, kCompactThreads, need);
-    const int gq = (int)std::min<int64_t>(grid_for(kq, kCompactThreads, need), max_partials);
-    int pb = 0;
-    const int Cc = std::max(1, prm->check_every);
-    for (int it = 0; it < prm->iters; ++it) {
-        const int l = it + 1;
-        for (int sw = 0; sw < prm->n_inner; ++sw) {
-            IterParams P = P0;
-            P.seed = mix32_host(0x51ed270bu ^ (uint32_t)(it * 131 + sw));
-            kd<<<gd, kCompactThreads, 0, s>>>(P, counts, S.nb, S.cap, P1[pb], P2[pb], V, P1[pb ^ 1],
-                                              P2[pb ^ 1], h);
-            SEG_LAUNCHED("k_dual_compact");
-            pb ^= 1;
-        }
-        IterParams P = P0;
-        P.check = (l % Cc == 0) || l == prm->iters;
-        P.write_u = P.check || ((l + 1) % Cc == 0) || l == prm->iters;
-        P.seed = mix32_host(0x2545f491u ^ (uint32_t)it);
-        kq<<<gq, kCompactThreads, 0, s>>>(P, counts, S.nb, S.cap, P1[pb], P2[pb], V, S.f, S.u,
-                                          partials, h);
-        SEG_LAUNCHED("k_primal_compact");
-        if (P.check) {
-            k_check<<<1, kCheckThreads, 0, s>>>(partials, gq, l, prm->tol, h);
-            SEG_LAUNCHED("k_check");
-        }
+    int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
+                                      std::max<int64_t>(1, (most + kPersistThreads - 1) / kPersistThreads));
+    grid = (int)std::min<int64_t>(grid, max_partials);
+    int iters = prm->iters, n_inner = std::max(1, prm->n_inner), check_every = std::max(1, prm->check_every);
+    double tol = prm->tol;
+    int warm = prm->warm_start;
+    int64_t stride = S.stride;
+    const int32_t* nbp = S.nb;
+    float* F = S.f;
+    float* U = S.u;
+    float* Wc = S.w;
+    IterParams P = P0;
+    void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&counts, (void*)&nbp, &stride,
+                    &P1[0], &P1[1], &P2[0], &P2[1], &V, &F, &U, &Wc, &partials, &h};
+    if (iters > 0 || warm) {
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPersistThreads),
+                                                 args, 0, s));
+        count_launch();
     }
     k_compact_scatter<T><<<gblocks, 256, 0, s>>>(P0, act, fgm, wstart, counts, prm->iters,
                                                  std::max(1, prm->n_inner), S, h, u, v, p1, p2);
@@ -657,7 +841,7 @@ using namespace seg;
 extern "C" size_t seg_state_bytes(int H, int ld, int64_t capacity, int mode, int storage) {
     if (mode == SEG_MODE_DENSE) return 6 * 4 * (size_t)std::max(H, 0) * (size_t)std::max(ld, 0) + 256;
     size_t sz = storage_size(storage);
-    return kCompactArrays * 256 + (size_t)std::max<int64_t>(capacity, 1) * (5 * sz + 8 + 4 * NB_COUNT);
+    return kCompactArrays * 256 + (size_t)compact_stride(capacity) * compact_per_element(sz);
 }
 
 extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint32_t* act,

@@ -296,6 +296,22 @@ def state_buffer(H, W, capacity, mode="compact", storage="f32", device="cuda"):
     return torch.empty((nb + 15) // 16 * 16, dtype=torch.uint8, device=device)
 
 
+def capture_graph(fn, warmup=1):
+    """Record the libseg launches that `fn()` issues on the current stream into
+    a CUDA graph (torch's capture API); returns the graph, to be replayed with
+    ``g.replay()``.  The buffers `fn` uses must stay alive and in place."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
 class Solver:
     """Buffers for one H x W image and the chain fitting -> domain -> solve ->
     energy through the C ABI.  Allocation only (torch); every step runs in
