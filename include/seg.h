@@ -168,6 +168,38 @@ seg_status seg_solve(const float* f, int H, int W, int ld,
                      void* state, size_t state_bytes, double* stats,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* One image of a batch for seg_solve_batch (host struct holding device
+ * pointers): the fitting term and the domain of seg_build_domain for it,
+ * its u, v, p1, p2 [H][ld] (warm start in, result out) and its lambda. */
+typedef struct seg_image {
+    const float* f;
+    int H, W, ld;
+    const uint32_t* act;
+    const uint32_t* fg;
+    const int32_t* wstart;
+    const int32_t* counts;
+    float* u;
+    float* v;
+    float* p1;
+    float* p2;
+    double lambda;
+} seg_image;
+
+/* Workspace bytes for seg_solve_batch (independent of the image sizes). */
+size_t seg_batch_workspace_bytes(int n_images, int64_t max_pixels);
+
+/* The iteration of seg_solve for up to 128 images at once, in one persistent
+ * launch (Section 3 per image; the images are independent problems whose RD
+ * pixels are concatenated).  Compact mode only; theta, tau, the iteration
+ * count, n_inner, storage and the stopping test (Euclidean norms over the
+ * whole batch) are shared, lambda is per image.  state: seg_state_bytes(0, 0,
+ * capacity, SEG_MODE_COMPACT, storage) with capacity >= the total RD pixels
+ * (else SEG_ERR_CAPACITY in the status word).  stats as for seg_solve
+ * (stats[3] = total RD pixels).  Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA. */
+seg_status seg_solve_batch(const seg_image* images, int n_images, const seg_params* prm,
+                           void* state, size_t state_bytes, double* stats,
+                           void* ws, size_t ws_bytes, void* stream);
+
 /* Energies of an iterate (FP64 reductions over the image):
  *   out[0] TV(u) (isotropic, forward differences), out[1] E_CR(u) = TV(u) +
  *   lambda sum f u (Eq. CR), out[2] E_CR(v), out[3] E_DF(u, v) (Eq. DF with

@@ -111,7 +111,8 @@ inline int64_t scan_tmp_items_for(int64_t n) {
 constexpr size_t kWsHeaderOff = 0;
 constexpr size_t kWsRedOff = 256;
 constexpr size_t kWsHistOff = kWsRedOff + 8 * (size_t)kReduceBlocks * kEnergyTerms;
-constexpr size_t kWsFixedBytes = kWsHistOff + 4 * (size_t)kHistBins;
+constexpr size_t kWsBatchOff = kWsHistOff + 4 * (size_t)kHistBins;   // compact bases of a batch
+constexpr size_t kWsFixedBytes = kWsBatchOff + 4 * (size_t)(128 + 2 + 2);
 
 inline WsLayout ws_layout(int H, int W, int tile_h) {
     WsLayout L{};

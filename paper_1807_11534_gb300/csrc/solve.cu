@@ -274,66 +274,120 @@ __device__ __forceinline__ int nb_code(const IterParams& P, const uint32_t* __re
     return ((fgm[o] >> b) & 1u) ? kNbFg : kNbBg;
 }
 
-// One warp per mask word (lane b is pixel (i, 32 wx + b)): gathers f and the
-// start iterate of every RD pixel into compact order and fills its row of the
-// neighbour table.
-template <typename T>
-__global__ void k_compact_gather(IterParams P, const uint32_t* __restrict__ act,
-                                 const uint32_t* __restrict__ fgm, const int32_t* __restrict__ wstart,
-                                 const int32_t* __restrict__ counts, const float* __restrict__ f,
-                                 int warm, const float* __restrict__ u, const float* __restrict__ v,
-                                 const float* __restrict__ p1, const float* __restrict__ p2,
-                                 CompactState S, WsHeader* h) {
-    if (counts[1] > S.cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            record_status(h, SEG_ERR_CAPACITY);
-            h->done = 1;
-            h->iters_done = 0;
-        }
-        return;
+// A batch of images solved together in compact form: their RD pixels are
+// concatenated (image k's compact index i becomes base[k] + i), the
+// neighbour table holds concatenated indices, and f is stored premultiplied
+// by theta * lambda_k, so the persistent solver needs no per-image data.  A
+// single image is a batch of one.
+constexpr int kMaxBatch = 128;
+
+struct BatchImage {
+    const float* f;
+    const uint32_t* act;
+    const uint32_t* fg;
+    const int32_t* wstart;
+    const int32_t* counts;
+    float *u, *v, *p1, *p2;
+    long long word_off;      // first flattened word of this image
+    int H, W, ld, nw, ntx;
+    float theta_lambda;      // theta * lambda of this image
+};
+
+struct BatchDesc {
+    int n;
+    long long total_words;   // sum over images of H * ceil(W/32)
+    BatchImage img[kMaxBatch];
+};
+
+// Image of a flattened word index (binary search over the word offsets).
+__device__ __forceinline__ int batch_image_of(const BatchDesc& B, long long word) {
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.img[mid].word_off <= word) lo = mid; else hi = mid - 1;
     }
+    return lo;
+}
+
+// Compact bases of the images (exclusive prefix of their RD counts) and the
+// batch total; a total above the capacity records SEG_ERR_CAPACITY and stops
+// the solve before it starts.
+__global__ void k_batch_bases(BatchDesc B, int32_t* base, int32_t* totals, int64_t cap, WsHeader* h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long run = 0, tiles = 0;
+    for (int k = 0; k < B.n; ++k) {
+        base[k] = (int32_t)run;
+        run += B.img[k].counts[1];
+        tiles += B.img[k].counts[0];
+    }
+    base[B.n] = (int32_t)run;
+    totals[0] = (int32_t)tiles;
+    totals[1] = run > cap ? 0 : (int32_t)run;
+    if (run > cap) {
+        record_status(h, SEG_ERR_CAPACITY);
+        h->done = 1;
+        h->iters_done = 0;
+    }
+}
+
+// One warp per mask word of the batch (lane b is pixel (i, 32 wx + b) of its
+// image): gathers f (times theta lambda) and the start iterate of every RD
+// pixel into compact order and fills its row of the neighbour table.
+template <typename T>
+__global__ void k_compact_gather(IterParams P, BatchDesc B, const int32_t* __restrict__ base,
+                                 int warm, CompactState S, const WsHeader* __restrict__ h) {
+    if (*(volatile const int*)&h->done) return;
     const int lane = threadIdx.x & 31;
-    const int64_t word = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int64_t nwords = (int64_t)P.H * P.ntx;
-    if (word >= nwords) return;
-    const int i = (int)(word / P.ntx);
-    const int wx = (int)(word - (int64_t)i * P.ntx);
+    const long long word = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (word >= B.total_words) return;
+    const int k = batch_image_of(B, word);
+    const BatchImage& I = B.img[k];
+    const long long lw = word - I.word_off;
+    const int i = (int)(lw / I.ntx);
+    const int wx = (int)(lw - (long long)i * I.ntx);
     const int j = wx * 32 + lane;
-    const int64_t wo = (int64_t)i * P.nw + wx;
-    const uint32_t a = act[wo];
+    const int64_t wo = (int64_t)i * I.nw + wx;
+    const uint32_t a = I.act[wo];
     if (!((a >> lane) & 1u)) return;
-    const int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
-    const int64_t o = (int64_t)i * P.ld + j;
-    const float fv = f[o];
-    const float hh = ((fgm[wo] >> lane) & 1u) ? 1.f : 0.f;
-    S.f[idx] = fv;
+    const int b0 = base[k];
+    const int64_t idx = b0 + I.wstart[wo] + __popc(a & lanemask_lt(lane));
+    const int64_t o = (int64_t)i * I.ld + j;
+    const float fv = I.f[o];
+    const float hh = ((I.fg[wo] >> lane) & 1u) ? 1.f : 0.f;
+    S.f[idx] = I.theta_lambda * fv;
     T* P1 = static_cast<T*>(S.p1[0]);
     T* P2 = static_cast<T*>(S.p2[0]);
     T* V = static_cast<T*>(S.v);
     if (warm) {
         // p1 on the last row and p2 on the last column never enter div p;
         // they are held at 0 (where a cold start keeps them)
-        Store<T>::st(P1, idx, i < P.H - 1 ? p1[o] : 0.f);
-        Store<T>::st(P2, idx, j < P.W - 1 ? p2[o] : 0.f);
-        Store<T>::st(V, idx, v[o] - Store<T>::vbias);
-        S.u[idx] = u[o];
+        Store<T>::st(P1, idx, i < I.H - 1 ? I.p1[o] : 0.f);
+        Store<T>::st(P2, idx, j < I.W - 1 ? I.p2[o] : 0.f);
+        Store<T>::st(V, idx, I.v[o] - Store<T>::vbias);
+        S.u[idx] = I.u[o];
     } else {
         Store<T>::st(P1, idx, 0.f);
         Store<T>::st(P2, idx, 0.f);
-        Store<T>::st(V, idx, clamp01(fmaf(-P.theta_lambda, fv, hh)) - Store<T>::vbias);
+        Store<T>::st(V, idx, clamp01(fmaf(-I.theta_lambda, fv, hh)) - Store<T>::vbias);
         S.u[idx] = hh;
     }
-    // w = div p - v/theta; with p = 0 (cold start) it is -v/theta, else it
-    // is filled by k_w_refresh once the table is complete
+    // w = div p - v/theta; with p = 0 (cold start) it is -v/theta, else the
+    // solver forms it once the table is complete
     S.w[idx] = warm ? 0.f : -(Store<T>::ld_rw(V, idx) + Store<T>::vbias) * P.inv_theta;
+    IterParams Q = P;
+    Q.H = I.H; Q.W = I.W; Q.nw = I.nw;
+    auto code = [&](int ii, int jj) {
+        const int c = nb_code(Q, I.act, I.fg, I.wstart, ii, jj);
+        return c >= 0 ? c + b0 : c;
+    };
     int32_t* nb = S.nb;
-    const int64_t cap = S.stride;
-    nb[NB_UP * cap + idx] = nb_code(P, act, fgm, wstart, i - 1, j);
-    nb[NB_LEFT * cap + idx] = nb_code(P, act, fgm, wstart, i, j - 1);
-    nb[NB_DOWN * cap + idx] = nb_code(P, act, fgm, wstart, i + 1, j);
-    nb[NB_RIGHT * cap + idx] = nb_code(P, act, fgm, wstart, i, j + 1);
-    nb[NB_DOWNLEFT * cap + idx] = nb_code(P, act, fgm, wstart, i + 1, j - 1);
-    nb[NB_UPRIGHT * cap + idx] = nb_code(P, act, fgm, wstart, i - 1, j + 1);
+    const int64_t st = S.stride;
+    nb[NB_UP * st + idx] = code(i - 1, j);
+    nb[NB_LEFT * st + idx] = code(i, j - 1);
+    nb[NB_DOWN * st + idx] = code(i + 1, j);
+    nb[NB_RIGHT * st + idx] = code(i, j + 1);
+    nb[NB_DOWNLEFT * st + idx] = code(i + 1, j - 1);
+    nb[NB_UPRIGHT * st + idx] = code(i - 1, j + 1);
 }
 
 template <typename T>
@@ -454,7 +508,7 @@ __device__ __forceinline__ void primal_one(const IterParams& P, int a, const int
         return;
     }
     const float un = fmaf(-P.theta, div, vv);
-    const float vn = clamp01(fmaf(-P.theta_lambda, __ldg(F + a), un));
+    const float vn = clamp01(un - __ldg(F + a));   // F = theta lambda f
     const float vs = Store<T>::st_sr(V, a, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
                      Store<T>::vbias;
     Wc[a] = div - vs * P.inv_theta;
@@ -575,37 +629,37 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
     }
 }
 
-// Dense u, v, p1, p2 of the final iterate: compact values on RD, the fixed
-// values elsewhere.
+// Dense u, v, p1, p2 of the final iterate of every image of the batch:
+// compact values on RD, the fixed values elsewhere.
 template <typename T>
-__global__ void k_compact_scatter(IterParams P, const uint32_t* __restrict__ act,
-                                  const uint32_t* __restrict__ fgm, const int32_t* __restrict__ wstart,
-                                  const int32_t* __restrict__ counts, int iters, int n_inner,
-                                  CompactState S, const WsHeader* __restrict__ h, float* u, float* v,
-                                  float* p1, float* p2) {
+__global__ void k_compact_scatter(BatchDesc B, const int32_t* __restrict__ base,
+                                  const int32_t* __restrict__ totals, int iters, int n_inner,
+                                  CompactState S, const WsHeader* __restrict__ h) {
     const int lane = threadIdx.x & 31;
-    const int64_t word = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int64_t nwords = (int64_t)P.H * P.ntx;
-    if (word >= nwords) return;
-    const int64_t i = word / P.ntx;
-    const int wx = (int)(word - i * P.ntx);
+    const long long word = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (word >= B.total_words) return;
+    const int k = batch_image_of(B, word);
+    const BatchImage& I = B.img[k];
+    const long long lw = word - I.word_off;
+    const int i = (int)(lw / I.ntx);
+    const int wx = (int)(lw - (long long)i * I.ntx);
     const int j = wx * 32 + lane;
-    if (j >= P.W) return;
-    const int64_t wo = i * P.nw + wx;
-    const int64_t o = i * P.ld + j;
-    const uint32_t a = act[wo];
-    const float hh = ((fgm[wo] >> lane) & 1u) ? 1.f : 0.f;
-    const bool ok = counts[1] <= S.cap;
+    if (j >= I.W) return;
+    const int64_t wo = (int64_t)i * I.nw + wx;
+    const int64_t o = (int64_t)i * I.ld + j;
+    const uint32_t a = I.act[wo];
+    const float hh = ((I.fg[wo] >> lane) & 1u) ? 1.f : 0.f;
+    const bool ok = base[B.n] <= S.cap && totals[1] == base[B.n];
     if (ok && ((a >> lane) & 1u)) {
         const int l = h->done ? h->iters_done : iters;
         const int pb = (int)(((long long)l * n_inner) & 1);
-        const int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
-        u[o] = S.u[idx];
-        v[o] = Store<T>::ld_rw(static_cast<const T*>(S.v), idx) + Store<T>::vbias;
-        p1[o] = Store<T>::ld_rw(static_cast<const T*>(S.p1[pb]), idx);
-        p2[o] = Store<T>::ld_rw(static_cast<const T*>(S.p2[pb]), idx);
+        const int64_t idx = base[k] + I.wstart[wo] + __popc(a & lanemask_lt(lane));
+        I.u[o] = S.u[idx];
+        I.v[o] = Store<T>::ld_rw(static_cast<const T*>(S.v), idx) + Store<T>::vbias;
+        I.p1[o] = Store<T>::ld_rw(static_cast<const T*>(S.p1[pb]), idx);
+        I.p2[o] = Store<T>::ld_rw(static_cast<const T*>(S.p2[pb]), idx);
     } else {
-        u[o] = hh; v[o] = hh; p1[o] = 0.f; p2[o] = 0.f;
+        I.u[o] = hh; I.v[o] = hh; I.p1[o] = 0.f; I.p2[o] = 0.f;
     }
 }
 
@@ -773,34 +827,38 @@ static seg_status run_dense(const IterParams& P0, const seg_params* prm, const i
     return SEG_OK;
 }
 
+// Compact solve of a batch (a single image is a batch of one): bases of the
+// images, gather + neighbour table, one cooperative launch for all the
+// iterations, scatter.
 template <typename T>
-static seg_status solve_compact_typed(const IterParams& P0, const seg_params* prm, const float* f,
-                                      const uint32_t* act, const uint32_t* fgm, const int32_t* wstart,
-                                      const int32_t* counts, float* u, float* v, float* p1, float* p2,
-                                      void* state, size_t state_bytes, double* partials,
+static seg_status solve_compact_batch(const IterParams& P0, const seg_params* prm, const BatchDesc& B,
+                                      int64_t max_pixels, void* state, size_t state_bytes,
+                                      int32_t* base, int32_t* totals, double* partials,
                                       int64_t max_partials, WsHeader* h, cudaStream_t s) {
     CompactLayout C = compact_layout(state_bytes, prm->storage);
     CompactState S{};
-    char* base = static_cast<char*>(state);
-    S.p1[0] = base + C.off[0];
-    S.p1[1] = base + C.off[1];
-    S.p2[0] = base + C.off[2];
-    S.p2[1] = base + C.off[3];
-    S.v = base + C.off[4];
-    S.f = reinterpret_cast<float*>(base + C.off[5]);
-    S.u = reinterpret_cast<float*>(base + C.off[6]);
-    S.w = reinterpret_cast<float*>(base + C.off[7]);
-    S.nb = reinterpret_cast<int32_t*>(base + C.off[8]);
+    char* sb = static_cast<char*>(state);
+    S.p1[0] = sb + C.off[0];
+    S.p1[1] = sb + C.off[1];
+    S.p2[0] = sb + C.off[2];
+    S.p2[1] = sb + C.off[3];
+    S.v = sb + C.off[4];
+    S.f = reinterpret_cast<float*>(sb + C.off[5]);
+    S.u = reinterpret_cast<float*>(sb + C.off[6]);
+    S.w = reinterpret_cast<float*>(sb + C.off[7]);
+    S.nb = reinterpret_cast<int32_t*>(sb + C.off[8]);
     S.cap = C.cap;
     S.stride = C.stride;
-    const int64_t nwords = (int64_t)P0.H * P0.ntx;
-    const unsigned gblocks = (unsigned)((nwords + 7) / 8);
-    k_compact_gather<T><<<gblocks, 256, 0, s>>>(P0, act, fgm, wstart, counts, f, prm->warm_start, u, v,
-                                                p1, p2, S, h);
+    k_batch_bases<<<1, 1, 0, s>>>(B, base, totals, C.cap, h);
+    SEG_LAUNCHED("k_batch_bases");
+    const unsigned gblocks = (unsigned)std::max<long long>(1, (B.total_words + 7) / 8);
+    k_compact_gather<T><<<gblocks, 256, 0, s>>>(P0, B, base, prm->warm_start, S, h);
     SEG_LAUNCHED("k_compact_gather");
 
-    T* P1[2] = {static_cast<T*>(S.p1[0]), static_cast<T*>(S.p1[1])};
-    T* P2[2] = {static_cast<T*>(S.p2[0]), static_cast<T*>(S.p2[1])};
+    T* P1a = static_cast<T*>(S.p1[0]);
+    T* P1b = static_cast<T*>(S.p1[1]);
+    T* P2a = static_cast<T*>(S.p2[0]);
+    T* P2b = static_cast<T*>(S.p2[1]);
     T* V = static_cast<T*>(S.v);
     auto kern = k_solve_compact<T>;
     // one cooperative launch for the whole solve: the grid is what can be
@@ -808,7 +866,7 @@ static seg_status solve_compact_typed(const IterParams& P0, const seg_params* pr
     int per_sm = 0;
     SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, 0));
     if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_compact cannot be resident");
-    const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)P0.H * P0.W));
+    const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, max_pixels));
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
                                       std::max<int64_t>(1, (most + kPersistThreads - 1) / kPersistThreads));
     grid = (int)std::min<int64_t>(grid, max_partials);
@@ -817,21 +875,67 @@ static seg_status solve_compact_typed(const IterParams& P0, const seg_params* pr
     int warm = prm->warm_start;
     int64_t stride = S.stride;
     const int32_t* nbp = S.nb;
+    const int32_t* cnt = totals;
     float* F = S.f;
     float* U = S.u;
     float* Wc = S.w;
     IterParams P = P0;
-    void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&counts, (void*)&nbp, &stride,
-                    &P1[0], &P1[1], &P2[0], &P2[1], &V, &F, &U, &Wc, &partials, &h};
+    void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&cnt, (void*)&nbp, &stride,
+                    &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Wc, &partials, &h};
     if (iters > 0 || warm) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPersistThreads),
                                                  args, 0, s));
         count_launch();
     }
-    k_compact_scatter<T><<<gblocks, 256, 0, s>>>(P0, act, fgm, wstart, counts, prm->iters,
-                                                 std::max(1, prm->n_inner), S, h, u, v, p1, p2);
+    k_compact_scatter<T><<<gblocks, 256, 0, s>>>(B, base, totals, prm->iters, std::max(1, prm->n_inner),
+                                                 S, h);
     SEG_LAUNCHED("k_compact_scatter");
     return SEG_OK;
+}
+
+static seg_status solve_compact_any(const IterParams& P, const seg_params* prm, const BatchDesc& B,
+                                    int64_t max_pixels, void* state, size_t state_bytes, int32_t* base,
+                                    int32_t* totals, double* partials, int64_t max_partials, WsHeader* h,
+                                    cudaStream_t s) {
+    switch (prm->storage) {
+        case SEG_STORE_F32:
+            return solve_compact_batch<float>(P, prm, B, max_pixels, state, state_bytes, base, totals,
+                                              partials, max_partials, h, s);
+        case SEG_STORE_BF16:
+            return solve_compact_batch<__nv_bfloat16>(P, prm, B, max_pixels, state, state_bytes, base,
+                                                      totals, partials, max_partials, h, s);
+        default:
+            return solve_compact_batch<__half>(P, prm, B, max_pixels, state, state_bytes, base, totals,
+                                               partials, max_partials, h, s);
+    }
+}
+
+static seg_status check_params(const seg_params* prm) {
+    if (!prm) return fail(SEG_ERR_INVALID_ARG, "params must be non-NULL");
+    const int th = prm->tile_h;
+    if (th != 4 && th != 8 && th != 16 && th != 32)
+        return fail(SEG_ERR_INVALID_ARG, "tile_h=%d not in {4, 8, 16, 32}", th);
+    if (prm->iters < 0 || prm->n_inner < 1 || prm->check_every < 1)
+        return fail(SEG_ERR_INVALID_ARG, "iters >= 0, n_inner >= 1, check_every >= 1 required");
+    if (!(prm->theta > 0) || !(prm->tau > 0) || !std::isfinite(prm->lambda) || std::isnan(prm->tol))
+        return fail(SEG_ERR_INVALID_ARG, "theta, tau must be > 0 and lambda finite");
+    if (prm->mode != SEG_MODE_DENSE && prm->mode != SEG_MODE_COMPACT)
+        return fail(SEG_ERR_INVALID_ARG, "unknown mode %d", prm->mode);
+    if (prm->storage < 0 || prm->storage > 2)
+        return fail(SEG_ERR_INVALID_ARG, "unknown storage %d", prm->storage);
+    if (prm->mode == SEG_MODE_DENSE && prm->storage != SEG_STORE_F32)
+        return fail(SEG_ERR_INVALID_ARG, "16-bit storage needs SEG_MODE_COMPACT");
+    return SEG_OK;
+}
+
+static IterParams iter_params(const seg_params* prm, int H, int W, int ld) {
+    IterParams P{};
+    P.theta = (float)prm->theta;
+    P.inv_theta = (float)(1.0 / prm->theta);
+    P.tau = (float)prm->tau;
+    P.theta_lambda = (float)(prm->theta * prm->lambda);
+    P.H = H; P.W = W; P.ld = ld; P.nw = ld / 32; P.ntx = (W + 31) / 32; P.th = prm->tile_h;
+    return P;
 }
 
 }  // namespace seg
@@ -850,39 +954,20 @@ extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint
                                 float* p1, float* p2, void* state, size_t state_bytes, double* stats,
                                 void* ws, size_t ws_bytes, void* stream) {
     clear_error();
-    if (!prm) return fail(SEG_ERR_INVALID_ARG, "params must be non-NULL");
+    SEG_TRY(check_params(prm));
     if (!f || !act || !fgm || !wstart || !tiles || !counts || !u || !v || !p1 || !p2 || !state || !stats)
         return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
     if (H <= 0 || W <= 0 || ld < W || (int64_t)H * ld >= (1ll << 31))
         return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d (H*ld < 2^31)", H, W, ld);
     if (ld % 32) return fail(SEG_ERR_ALIGN, "ld=%d is not a multiple of 32", ld);
-    const int th = prm->tile_h;
-    if (th != 4 && th != 8 && th != 16 && th != 32)
-        return fail(SEG_ERR_INVALID_ARG, "tile_h=%d not in {4, 8, 16, 32}", th);
-    if (prm->iters < 0 || prm->n_inner < 1 || prm->check_every < 1)
-        return fail(SEG_ERR_INVALID_ARG, "iters >= 0, n_inner >= 1, check_every >= 1 required");
-    if (!(prm->theta > 0) || !(prm->tau > 0) || !std::isfinite(prm->lambda) || std::isnan(prm->tol))
-        return fail(SEG_ERR_INVALID_ARG, "theta, tau must be > 0 and lambda finite");
-    if (prm->mode != SEG_MODE_DENSE && prm->mode != SEG_MODE_COMPACT)
-        return fail(SEG_ERR_INVALID_ARG, "unknown mode %d", prm->mode);
-    if (prm->storage < 0 || prm->storage > 2)
-        return fail(SEG_ERR_INVALID_ARG, "unknown storage %d", prm->storage);
-    if (prm->mode == SEG_MODE_DENSE && prm->storage != SEG_STORE_F32)
-        return fail(SEG_ERR_INVALID_ARG, "16-bit storage needs SEG_MODE_COMPACT");
     if (reinterpret_cast<uintptr_t>(state) % 16)
         return fail(SEG_ERR_ALIGN, "state buffer not 16-byte aligned");
-    WsLayout L = ws_layout(H, W, th);
+    WsLayout L = ws_layout(H, W, prm->tile_h);
     SEG_TRY(check_ws(ws, ws_bytes, L));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     WsHeader* h = ws_at<WsHeader>(ws, L.header);
     double* partials = ws_at<double>(ws, L.partials);
-
-    IterParams P{};
-    P.theta = (float)prm->theta;
-    P.inv_theta = (float)(1.0 / prm->theta);
-    P.tau = (float)prm->tau;
-    P.theta_lambda = (float)(prm->theta * prm->lambda);
-    P.H = H; P.W = W; P.ld = ld; P.nw = ld / 32; P.ntx = (W + 31) / 32; P.th = th;
+    IterParams P = iter_params(prm, H, W, ld);
 
     k_solve_begin<<<1, 1, 0, s>>>(h);
     SEG_LAUNCHED("k_solve_begin");
@@ -899,23 +984,77 @@ extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint
         k_final_dense<<<blocks, 256, 0, s>>>(P, h, prm->iters, prm->n_inner, st, v, p1, p2);
         SEG_LAUNCHED("k_final_dense");
     } else {
-        switch (prm->storage) {
-            case SEG_STORE_F32:
-                SEG_TRY(solve_compact_typed<float>(P, prm, f, act, fgm, wstart, counts, u, v, p1, p2,
-                                                   state, state_bytes, partials, L.npartials, h, s));
-                break;
-            case SEG_STORE_BF16:
-                SEG_TRY(solve_compact_typed<__nv_bfloat16>(P, prm, f, act, fgm, wstart, counts, u, v, p1,
-                                                           p2, state, state_bytes, partials,
-                                                           L.npartials, h, s));
-                break;
-            default:
-                SEG_TRY(solve_compact_typed<__half>(P, prm, f, act, fgm, wstart, counts, u, v, p1, p2,
-                                                    state, state_bytes, partials, L.npartials, h, s));
-                break;
-        }
+        BatchDesc B{};
+        B.n = 1;
+        B.total_words = (long long)H * P.ntx;
+        BatchImage& I = B.img[0];
+        I.f = f; I.act = act; I.fg = fgm; I.wstart = wstart; I.counts = counts;
+        I.u = u; I.v = v; I.p1 = p1; I.p2 = p2;
+        I.word_off = 0; I.H = H; I.W = W; I.ld = ld; I.nw = ld / 32; I.ntx = P.ntx;
+        I.theta_lambda = P.theta_lambda;
+        int32_t* base = ws_at<int32_t>(ws, kWsBatchOff);
+        SEG_TRY(solve_compact_any(P, prm, B, (int64_t)H * W, state, state_bytes, base, base + kMaxBatch + 2,
+                                  partials, L.npartials, h, s));
+        k_solve_end<<<1, 1, 0, s>>>(h, base + kMaxBatch + 2, prm->iters, stats);
+        SEG_LAUNCHED("k_solve_end");
+        return SEG_OK;
     }
     k_solve_end<<<1, 1, 0, s>>>(h, counts, prm->iters, stats);
+    SEG_LAUNCHED("k_solve_end");
+    return SEG_OK;
+}
+
+extern "C" size_t seg_batch_workspace_bytes(int n_images, int64_t max_pixels) {
+    (void)n_images;
+    // the fixed regions plus stopping-test partials for the persistent grid
+    return align_up(kWsFixedBytes, 256) + 2 * 8 * (size_t)(4096 + 1) + 256 + 0 * (size_t)max_pixels;
+}
+
+extern "C" seg_status seg_solve_batch(const seg_image* images, int n_images, const seg_params* prm,
+                                      void* state, size_t state_bytes, double* stats, void* ws,
+                                      size_t ws_bytes, void* stream) {
+    clear_error();
+    SEG_TRY(check_params(prm));
+    if (prm->mode != SEG_MODE_COMPACT)
+        return fail(SEG_ERR_INVALID_ARG, "seg_solve_batch runs SEG_MODE_COMPACT only");
+    if (!images || n_images <= 0 || n_images > kMaxBatch)
+        return fail(SEG_ERR_INVALID_ARG, "n_images=%d not in [1, %d]", n_images, kMaxBatch);
+    if (!state || !stats) return fail(SEG_ERR_INVALID_ARG, "state and stats must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(state) % 16 || reinterpret_cast<uintptr_t>(ws) % 16)
+        return fail(SEG_ERR_ALIGN, "state / workspace not 16-byte aligned");
+    if (!ws || ws_bytes < seg_batch_workspace_bytes(n_images, 0))
+        return fail(SEG_ERR_WORKSPACE, "batch workspace needs %zu bytes", seg_batch_workspace_bytes(n_images, 0));
+    BatchDesc B{};
+    B.n = n_images;
+    long long words = 0, pixels = 0;
+    for (int k = 0; k < n_images; ++k) {
+        const seg_image& X = images[k];
+        if (!X.f || !X.act || !X.fg || !X.wstart || !X.counts || !X.u || !X.v || !X.p1 || !X.p2)
+            return fail(SEG_ERR_INVALID_ARG, "image %d: a required pointer is NULL", k);
+        if (X.H <= 0 || X.W <= 0 || X.ld < X.W || (int64_t)X.H * X.ld >= (1ll << 31))
+            return fail(SEG_ERR_INVALID_ARG, "image %d: bad size H=%d W=%d ld=%d", k, X.H, X.W, X.ld);
+        if (X.ld % 32) return fail(SEG_ERR_ALIGN, "image %d: ld=%d is not a multiple of 32", k, X.ld);
+        if (!std::isfinite(X.lambda)) return fail(SEG_ERR_INVALID_ARG, "image %d: lambda not finite", k);
+        BatchImage& I = B.img[k];
+        I.f = X.f; I.act = X.act; I.fg = X.fg; I.wstart = X.wstart; I.counts = X.counts;
+        I.u = X.u; I.v = X.v; I.p1 = X.p1; I.p2 = X.p2;
+        I.word_off = words; I.H = X.H; I.W = X.W; I.ld = X.ld; I.nw = X.ld / 32; I.ntx = (X.W + 31) / 32;
+        I.theta_lambda = (float)(prm->theta * X.lambda);
+        words += (long long)X.H * I.ntx;
+        pixels += (long long)X.H * X.W;
+    }
+    B.total_words = words;
+    if (pixels >= (1ll << 31)) return fail(SEG_ERR_INVALID_ARG, "batch holds %lld pixels (< 2^31)", pixels);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader* h = ws_at<WsHeader>(ws, kWsHeaderOff);
+    int32_t* base = ws_at<int32_t>(ws, kWsBatchOff);
+    double* partials = ws_at<double>(ws, align_up(kWsFixedBytes, 256));
+    IterParams P = iter_params(prm, images[0].H, images[0].W, images[0].ld);
+    k_solve_begin<<<1, 1, 0, s>>>(h);
+    SEG_LAUNCHED("k_solve_begin");
+    SEG_TRY(solve_compact_any(P, prm, B, pixels, state, state_bytes, base, base + kMaxBatch + 2, partials,
+                              4096, h, s));
+    k_solve_end<<<1, 1, 0, s>>>(h, base + kMaxBatch + 2, prm->iters, stats);
     SEG_LAUNCHED("k_solve_end");
     return SEG_OK;
 }

@@ -54,6 +54,14 @@ class seg_params(ctypes.Structure):
                 ("tile_h", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class seg_image(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("ld", ctypes.c_int), ("act", ctypes.c_void_p), ("fg", ctypes.c_void_p),
+                ("wstart", ctypes.c_void_p), ("counts", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("p1", ctypes.c_void_p), ("p2", ctypes.c_void_p),
+                ("lambda_", ctypes.c_double)]
+
+
 _lib = None
 
 # exported entry points and their C signatures (include/seg.h)
@@ -73,6 +81,9 @@ SIGNATURES = {
     "seg_energy": ([_P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _P, _P, _Z, _P], _I),
     "seg_errors": ([_P, _P, _I, _I, _I, _D, _P, _P, _Z, _P], _I),
     "seg_energy_noalloc": ([_P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _P, _P], _I),
+    "seg_batch_workspace_bytes": ([_I, _L], _Z),
+    "seg_solve_batch": ([ctypes.POINTER(seg_image), _I, ctypes.POINTER(seg_params), _P, _Z, _P, _P, _Z,
+                         _P], _I),
 }
 
 
@@ -187,6 +198,17 @@ def seg_energy_noalloc(f, u, v, p1, p2, lam, theta, out, stream=None):
     _check(lib.seg_energy_noalloc(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(u), _ptr(v),
                                   _ptr(p1), _ptr(p2), float(lam), float(theta), _ptr(out),
                                   _stream(stream)))
+
+
+def seg_batch_workspace_bytes(n_images, max_pixels=0):
+    return load().seg_batch_workspace_bytes(int(n_images), int(max_pixels))
+
+
+def seg_solve_batch(images, params: seg_params, state, stats, ws, stream=None):
+    """`images`: a ctypes array of seg_image (device pointers)."""
+    lib = load()
+    _check(lib.seg_solve_batch(images, len(images), ctypes.byref(params), _ptr(state),
+                               _nbytes(state), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)))
 
 
 def seg_errors(u_star, u_gt, eps, out, ws, stream=None):
@@ -373,3 +395,62 @@ class Solver:
 
     def check_status(self):
         seg_read_status(self.ws, self.stream)
+
+
+class BatchSolver:
+    """Buffers for a batch of images (one Solver per image for the fitting
+    term and the domain) and one shared compact state: the iteration of all
+    images runs in one persistent launch (seg_solve_batch)."""
+
+    def __init__(self, shapes, tile_h=16, storage="f32", capacity=None, device="cuda", stream=None):
+        self.device = torch.device(device)
+        self.stream = stream
+        self.tile_h, self.storage = tile_h, storage
+        Hm = max(h for h, _ in shapes)
+        Wm = max(w for _, w in shapes)
+        # one workspace large enough for the largest image serves every image
+        self.ws_img = workspace(Hm, Wm, tile_h, self.device)
+        self.solvers = []
+        for (H, W) in shapes:
+            S = Solver.__new__(Solver)
+            S.H, S.W, S.tile_h, S.mode, S.storage = H, W, tile_h, "compact", storage
+            S.device, S.stream, S.ws = self.device, stream, self.ws_img
+            S.capacity, S.state = 0, None
+            S.f = image(H, W, device=self.device)
+            S.u = image(H, W, device=self.device)
+            S.v = image(H, W, device=self.device)
+            S.p1 = image(H, W, device=self.device)
+            S.p2 = image(H, W, device=self.device)
+            S.stats = torch.zeros(8, dtype=torch.float64, device=self.device)
+            S.c = torch.zeros(2, dtype=torch.float64, device=self.device)
+            S.energy_out = torch.zeros(6, dtype=torch.float64, device=self.device)
+            S.err_out = torch.zeros(2, dtype=torch.float64, device=self.device)
+            S.dom = None
+            self.solvers.append(S)
+        total = sum(h * w for h, w in shapes)
+        self.capacity = total if capacity is None else int(capacity)
+        self.state = state_buffer(0, 32, self.capacity, "compact", storage, self.device)
+        nb = seg_batch_workspace_bytes(len(shapes), total)
+        self.ws = torch.zeros((nb + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        self.stats = torch.zeros(8, dtype=torch.float64, device=self.device)
+
+    def images(self, lams):
+        arr = (seg_image * len(self.solvers))()
+        for k, (S, lam) in enumerate(zip(self.solvers, lams)):
+            d = S.dom
+            arr[k] = seg_image(S.f.data_ptr(), S.H, S.W, S.f.stride(0), d.act.data_ptr(),
+                               d.fg.data_ptr(), d.wstart.data_ptr(), d.counts.data_ptr(),
+                               S.u.data_ptr(), S.v.data_ptr(), S.p1.data_ptr(), S.p2.data_ptr(),
+                               float(lam))
+        return arr
+
+    def solve(self, lams, theta=0.2, tau=0.125, iters=100, tol=0.0, n_inner=1, check_every=10,
+              warm_start=False):
+        prm = make_params(1.0, theta, tau, iters, tol, n_inner, check_every, warm_start, "compact",
+                          self.storage, self.tile_h)
+        seg_solve_batch(self.images(lams), prm, self.state, self.stats, self.ws, self.stream)
+        return self.stats
+
+    def check_status(self):
+        seg_read_status(self.ws, self.stream)
+        seg_read_status(self.ws_img, self.stream)
