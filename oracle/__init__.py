@@ -73,6 +73,8 @@ def _load():
         lib.oracle_div.restype = None
         lib.oracle_solve.argtypes = [P, I, I, P, D, D, D, I, I, D, I, P, P, P, P, P]
         lib.oracle_solve.restype = I
+        lib.oracle_solve_grad.argtypes = [P, I, I, P, D, D, D, I, P, P, P, P]
+        lib.oracle_solve_grad.restype = None
         lib.oracle_energy.argtypes = [P, P, P, P, P, I, I, D, D, P]
         lib.oracle_energy.restype = None
         lib.oracle_errors.argtypes = [P, P, L, D, P]
@@ -206,6 +208,21 @@ def solve(f32, region, lam, theta=0.2, tau=0.125, iters=100, n_inner=1, tol=0.0,
                             int(iters), int(n_inner), float(tol), warm,
                             _ptr(u), _ptr(v), _ptr(p1), _ptr(p2), _ptr(hist))
     return State(u, v, p1, p2, done, hist[:done])
+
+
+def solve_grad(f32, region, lam, gu, gv=None, theta=0.2, tau=0.125, iters=20):
+    """(dL/df, dL/dlambda) for L = <gu, u^K> + <gv, v^K> (reverse mode)."""
+    lib = _load()
+    f = _c(f32, np.float32)
+    reg = _c(region, np.uint8)
+    H, W = f.shape
+    gu = _c(gu, np.float64)
+    gvv = _c(gv, np.float64) if gv is not None else None
+    gf = np.zeros((H, W))
+    glam = ctypes.c_double()
+    lib.oracle_solve_grad(_ptr(f), H, W, _ptr(reg), float(lam), float(theta), float(tau), int(iters),
+                          _ptr(gu), _ptr(gvv), _ptr(gf), ctypes.byref(glam))
+    return gf, glam.value
 
 
 def energy(u, v, p1, p2, f32, lam, theta=0.2):

@@ -295,6 +295,165 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
     return done;
 }
 
+/* ------------------------------------------------------- reverse mode */
+
+/* Gradient of L = <gu, u^K> + <gv, v^K> through the unrolled iteration of
+ * oracle_solve (cold start, n_inner = 1, `iters` = K iterations, no stopping
+ * test), with respect to f on RD (gf; 0 elsewhere) and lambda (*glam).  The
+ * partition is held fixed (no derivative through the threshold), u0 = H(-f)
+ * is piecewise constant, and the clip has derivative 1 strictly inside (0,1)
+ * and 0 elsewhere; d|g| is taken as 0 at g = 0.  Plain reverse-mode
+ * differentiation of the same steps, storing every iterate:
+ *   v = clip(s), s = u - theta lambda f:  sbar = vbar [0 < s < 1],
+ *       fbar -= theta lambda sbar, lambdabar -= theta sum f sbar
+ *   u = v_prev - theta div p:            v_prevbar += ubar, pbar += theta grad ubar
+ *   p = (p_prev + tau g) / d, d = 1 + tau |g|:
+ *       p_prevbar += pbar / d,  gbar = (tau / d) (pbar - (pbar . p) g/|g|)
+ *   g = grad w:                          wbar = -div gbar
+ *   w = div p_prev - v_prev / theta:      p_prevbar -= grad wbar, v_prevbar -= wbar / theta
+ * (div^T = -grad, so grad^T = -div.) */
+void oracle_solve_grad(const float* f32, int H, int W, const uint8_t* region,
+                       double lambda, double theta, double tau, int iters,
+                       const double* gu, const double* gv, double* gf, double* glam)
+{
+    int64_t n = (int64_t)H * W;
+    size_t sz = sizeof(double) * (size_t)n;
+    int K = iters;
+    double* P1 = (double*)malloc(sz * (size_t)(K + 1));
+    double* P2 = (double*)malloc(sz * (size_t)(K + 1));
+    double* V = (double*)malloc(sz * (size_t)(K + 1));
+    double* U = (double*)malloc(sz * (size_t)(K + 1));
+    double* d = (double*)malloc(sz);
+    double* w = (double*)malloc(sz);
+    double* g1 = (double*)malloc(sz);
+    double* g2 = (double*)malloc(sz);
+    double* ub = (double*)malloc(sz);
+    double* vb = (double*)malloc(sz);
+    double* p1b = (double*)malloc(sz);
+    double* p2b = (double*)malloc(sz);
+    double* gb1 = (double*)malloc(sz);
+    double* gb2 = (double*)malloc(sz);
+    double* wb = (double*)malloc(sz);
+    double* t1 = (double*)malloc(sz);
+    double* t2 = (double*)malloc(sz);
+
+    /* forward, every iterate kept */
+    for (int64_t x = 0; x < n; ++x) {
+        double f = (double)f32[x];
+        double h = (f < 0.0) ? 1.0 : 0.0;
+        if (region[x] != 2) h = (region[x] == 1) ? 1.0 : 0.0;
+        U[x] = h;
+        P1[x] = 0.0;
+        P2[x] = 0.0;
+        V[x] = (region[x] == 2) ? clamp01(h - theta * lambda * f) : h;
+    }
+    for (int k = 0; k < K; ++k) {
+        double *p1 = P1 + (int64_t)k * n, *p2 = P2 + (int64_t)k * n, *v = V + (int64_t)k * n;
+        double *q1 = P1 + (int64_t)(k + 1) * n, *q2 = P2 + (int64_t)(k + 1) * n;
+        double *un = U + (int64_t)(k + 1) * n, *vn = V + (int64_t)(k + 1) * n;
+        oracle_div(p1, p2, H, W, d);
+        for (int64_t x = 0; x < n; ++x) w[x] = d[x] - v[x] / theta;
+        oracle_grad(w, H, W, g1, g2);
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] == 2) {
+                double den = 1.0 + tau * sqrt(g1[x] * g1[x] + g2[x] * g2[x]);
+                q1[x] = (p1[x] + tau * g1[x]) / den;
+                q2[x] = (p2[x] + tau * g2[x]) / den;
+            } else {
+                q1[x] = 0.0;
+                q2[x] = 0.0;
+            }
+        }
+        oracle_div(q1, q2, H, W, d);
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] == 2) {
+                un[x] = v[x] - theta * d[x];
+                vn[x] = clamp01(un[x] - theta * lambda * (double)f32[x]);
+            } else {
+                un[x] = U[x];
+                vn[x] = V[x];
+            }
+        }
+    }
+
+    /* reverse */
+    double lb = 0.0;
+    for (int64_t x = 0; x < n; ++x) {
+        gf[x] = 0.0;
+        vb[x] = (region[x] == 2 && gv) ? gv[x] : 0.0;
+        p1b[x] = 0.0;
+        p2b[x] = 0.0;
+    }
+    for (int k = K - 1; k >= 0; --k) {
+        double *p1 = P1 + (int64_t)k * n, *p2 = P2 + (int64_t)k * n, *v = V + (int64_t)k * n;
+        double *q1 = P1 + (int64_t)(k + 1) * n, *q2 = P2 + (int64_t)(k + 1) * n;
+        double *un = U + (int64_t)(k + 1) * n;
+        /* v^{k+1} = clip(u^{k+1} - theta lambda f) */
+        for (int64_t x = 0; x < n; ++x) {
+            ub[x] = 0.0;
+            if (region[x] != 2) continue;
+            double f = (double)f32[x];
+            double sv = un[x] - theta * lambda * f;
+            double sb = (sv > 0.0 && sv < 1.0) ? vb[x] : 0.0;
+            ub[x] = sb + ((k == K - 1) ? gu[x] : 0.0);
+            gf[x] -= theta * lambda * sb;
+            lb -= theta * f * sb;
+        }
+        /* u^{k+1} = v^k - theta div p^{k+1}: pbar += theta grad ubar on RD */
+        oracle_grad(ub, H, W, t1, t2);
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] != 2) continue;
+            p1b[x] += theta * t1[x];
+            p2b[x] += theta * t2[x];
+        }
+        /* p^{k+1} = (p^k + tau g^k) / d */
+        oracle_div(p1, p2, H, W, d);
+        for (int64_t x = 0; x < n; ++x) w[x] = d[x] - v[x] / theta;
+        oracle_grad(w, H, W, g1, g2);
+        for (int64_t x = 0; x < n; ++x) {
+            gb1[x] = 0.0;
+            gb2[x] = 0.0;
+            if (region[x] != 2) { p1b[x] = 0.0; p2b[x] = 0.0; continue; }
+            double nrm = sqrt(g1[x] * g1[x] + g2[x] * g2[x]);
+            double den = 1.0 + tau * nrm;
+            double dot = p1b[x] * q1[x] + p2b[x] * q2[x];
+            double h1 = nrm > 0.0 ? g1[x] / nrm : 0.0, h2 = nrm > 0.0 ? g2[x] / nrm : 0.0;
+            gb1[x] = (tau / den) * (p1b[x] - dot * h1);
+            gb2[x] = (tau / den) * (p2b[x] - dot * h2);
+            p1b[x] = p1b[x] / den;
+            p2b[x] = p2b[x] / den;
+        }
+        /* g = grad w (zero components carry no adjoint) */
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                if (i == H - 1) gb1[IDX(i, j)] = 0.0;
+                if (j == W - 1) gb2[IDX(i, j)] = 0.0;
+            }
+        oracle_div(gb1, gb2, H, W, d);
+        for (int64_t x = 0; x < n; ++x) wb[x] = -d[x];
+        /* w = div p^k - v^k / theta */
+        oracle_grad(wb, H, W, t1, t2);
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] != 2) { vb[x] = 0.0; continue; }
+            p1b[x] -= t1[x];
+            p2b[x] -= t2[x];
+            vb[x] = ub[x] - wb[x] / theta;
+        }
+    }
+    /* v^0 = clip(u^0 - theta lambda f) */
+    for (int64_t x = 0; x < n; ++x) {
+        if (region[x] != 2) continue;
+        double f = (double)f32[x];
+        double sv = U[x] - theta * lambda * f;
+        double sb = (sv > 0.0 && sv < 1.0) ? vb[x] : 0.0;
+        gf[x] -= theta * lambda * sb;
+        lb -= theta * f * sb;
+    }
+    *glam = lb;
+    free(P1); free(P2); free(V); free(U); free(d); free(w); free(g1); free(g2);
+    free(ub); free(vb); free(p1b); free(p2b); free(gb1); free(gb2); free(wb); free(t1); free(t2);
+}
+
 /* ------------------------------------------------------------- energies */
 
 static double tv(const double* u, int H, int W)

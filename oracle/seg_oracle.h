@@ -62,6 +62,13 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
                  int iters, int n_inner, double tol, int warm,
                  double* u, double* v, double* p1, double* p2, double* hist);
 
+/* Reverse mode of the unrolled iteration (cold start, n_inner = 1, no stop):
+ * gradient of <gu, u^K> + <gv, v^K> (gv nullable) with respect to f (gf,
+ * nonzero on RD only) and lambda (*glam), the partition held fixed. */
+void oracle_solve_grad(const float* f32, int H, int W, const uint8_t* region,
+                       double lambda, double theta, double tau, int iters,
+                       const double* gu, const double* gv, double* gf, double* glam);
+
 /* out[0] = TV(u), out[1] = E_CR(u), out[2] = E_CR(v), out[3] = E_DF(u, v),
  * out[4] = D(p) (dual lower bound), out[5] = E_CR(v) - D(p) (duality gap). */
 void oracle_energy(const double* u, const double* v, const double* p1,
