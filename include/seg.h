@@ -200,6 +200,47 @@ seg_status seg_solve_batch(const seg_image* images, int n_images, const seg_para
                            void* state, size_t state_bytes, double* stats,
                            void* ws, size_t ws_bytes, void* stream);
 
+/* Bytes of the checkpoints of seg_solve_diff: (p1, p2, v) as float32 for
+ * ceil(iters / ckpt_every) iterates, for a state of `capacity` RD pixels. */
+size_t seg_ckpt_bytes(int64_t capacity, int iters, int ckpt_every);
+
+/* Scratch bytes of seg_backward (adjoint fields and one segment of
+ * ckpt_every + 1 recomputed iterates). */
+size_t seg_backward_scratch_bytes(int64_t capacity, int ckpt_every);
+
+/* Differentiable forward (not in the paper): seg_solve in compact mode with
+ * float32 storage, n_inner = 1, cold start and a fixed number of iterations
+ * (tol <= 0), which also writes the iterate (p1, p2, v) every ckpt_every
+ * iterations into `ckpt` (seg_ckpt_bytes).  Arguments otherwise as
+ * seg_solve.  Errors: INVALID_ARG, ALIGN, CAPACITY, WORKSPACE, CUDA. */
+seg_status seg_solve_diff(const float* f, int H, int W, int ld,
+                          const uint32_t* act, const uint32_t* fg, const int32_t* wstart,
+                          const int32_t* tiles, const int32_t* counts,
+                          const seg_params* prm,
+                          float* u, float* v, float* p1, float* p2,
+                          void* state, size_t state_bytes,
+                          int ckpt_every, void* ckpt, size_t ckpt_bytes, double* stats,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* Reverse mode of the unrolled iteration run by seg_solve_diff (not in the
+ * paper): given dL/du^K (grad_u, [H][ld]) and optionally dL/dv^K (grad_v),
+ * returns dL/df (grad_f, [H][ld], 0 outside RD) and grad_out = {dL/dlambda,
+ * dL/dc1, dL/dc2} (device double[3]; the c terms need z and c = {c1, c2},
+ * device double[2], else they are 0).  The partition is held fixed; the
+ * clip's derivative is 1 strictly inside (0, 1).  The forward iterates are
+ * recomputed segment by segment from the checkpoints (state and ckpt must be
+ * those of the seg_solve_diff call, unmodified).  scratch:
+ * seg_backward_scratch_bytes bytes, caller-owned.  Errors: INVALID_ARG,
+ * ALIGN, CAPACITY, WORKSPACE, CUDA. */
+seg_status seg_backward(const float* f, int H, int W, int ld,
+                        const uint32_t* act, const uint32_t* fg, const int32_t* wstart,
+                        const int32_t* counts, const seg_params* prm,
+                        const void* state, size_t state_bytes,
+                        const void* ckpt, size_t ckpt_bytes, int ckpt_every,
+                        const float* grad_u, const float* grad_v, const float* z, const double* c,
+                        float* grad_f, double* grad_out, void* scratch, size_t scratch_bytes,
+                        void* ws, size_t ws_bytes, void* stream);
+
 /* Energies of an iterate (FP64 reductions over the image):
  *   out[0] TV(u) (isotropic, forward differences), out[1] E_CR(u) = TV(u) +
  *   lambda sum f u (Eq. CR), out[2] E_CR(v), out[3] E_DF(u, v) (Eq. DF with

@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kPersistThreads)
 k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
                 const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
                 T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
-                float* Wc, double* partials, WsHeader* h) {
+                float* Wc, double* partials, WsHeader* h, float* ckpt, int ckpt_every) {
     __shared__ double s_red[2 * (kPersistThreads / 32)];
     // set before the launch (capacity overflow): the same for every block
     if (*(volatile int*)&h->done) return;
@@ -548,6 +548,18 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
         if (!grid_sync(h, nblocks, gen)) return;
     }
     const int C = check_every;
+    // checkpoint m holds (p1, p2, v) of iterate m * ckpt_every, as float32
+    auto save = [&](int m) {
+        float* c = ckpt + (int64_t)m * 3 * stride;
+        const T* q1 = p1c();
+        const T* q2 = p2c();
+        for (int a = a0 + tid; a < a1; a += nt) {
+            c[a] = to_f(q1[a]);
+            c[stride + a] = to_f(q2[a]);
+            c[2 * stride + a] = to_f(V[a]) + Store<T>::vbias;
+        }
+    };
+    if (ckpt) save(0);
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
         for (int sw = 0; sw < n_inner; ++sw) {
@@ -583,6 +595,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
         }
         if (a < a1)
             primal_one(P, a, nb, stride, q1s, q2s, V, F, U, Wc, false, check, write_u, seed, du2, dv2);
+        if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);
         if (check) {
             double x = du2, y = dv2;
             for (int d = 16; d > 0; d >>= 1) {
@@ -834,7 +847,8 @@ template <typename T>
 static seg_status solve_compact_batch(const IterParams& P0, const seg_params* prm, const BatchDesc& B,
                                       int64_t max_pixels, void* state, size_t state_bytes,
                                       int32_t* base, int32_t* totals, double* partials,
-                                      int64_t max_partials, WsHeader* h, cudaStream_t s) {
+                                      int64_t max_partials, WsHeader* h, cudaStream_t s,
+                                      float* ckpt = nullptr, int ckpt_every = 1) {
     CompactLayout C = compact_layout(state_bytes, prm->storage);
     CompactState S{};
     char* sb = static_cast<char*>(state);
@@ -881,7 +895,7 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     float* Wc = S.w;
     IterParams P = P0;
     void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&cnt, (void*)&nbp, &stride,
-                    &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Wc, &partials, &h};
+                    &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Wc, &partials, &h, &ckpt, &ckpt_every};
     if (iters > 0 || warm) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPersistThreads),
                                                  args, 0, s));
@@ -937,6 +951,228 @@ static IterParams iter_params(const seg_params* prm, int H, int W, int ld) {
     P.H = H; P.W = W; P.ld = ld; P.nw = ld / 32; P.ntx = (W + 31) / 32; P.th = prm->tile_h;
     return P;
 }
+
+// ============================================================ adjoint
+//
+// Reverse mode of the unrolled compact iteration (float32 state, n_inner =
+// 1, a fixed number of iterations), for L with given dL/du^K (and dL/dv^K):
+// the partition is held fixed, u0 = H(-f) is piecewise constant, the clip has
+// derivative 1 strictly inside (0, 1) -- i.e. where the clipped value lies in
+// (0, 1) -- and 0 elsewhere, and d|g| is 0 at g = 0.  For each segment of C
+// iterations, from the last to the first, the forward iterates are recomputed
+// from the segment's checkpoint into a segment buffer, then the adjoint walks
+// back through them:
+//   A  sbar = vbar [0 < v^{n+1} < 1];  ubar = sbar (+ dL/du^K at n+1 = K);
+//      Fbar -= sbar  (F = theta lambda f)
+//   B  qbar = pbar + theta grad ubar;  with d = 1 + tau |g^n|, q = p^{n+1}:
+//      gbar = (tau / d) (qbar - (qbar . q) g/|g|),  pbar_direct = qbar / d
+//   C  wbar = -div gbar at x, x+e1, x+e2;  pbar = pbar_direct - grad wbar;
+//      vbar = ubar - wbar / theta
+// (div^T = -grad), then the v0 = clip(u0 - F) term.  Finally df = theta
+// lambda Fbar, dlambda = theta sum f Fbar, dc1 = sum df (-2)(z - c1),
+// dc2 = sum df 2 (z - c2).
+
+struct AdjArrays {
+    float *p1b, *p2b, *vb, *ub, *gb1, *gb2, *pd1, *pd2, *fb, *gu, *gv;   // [stride] each
+    float* seg;        // segment buffer: [(C + 1)][4][stride]  (p1, p2, v, w)
+};
+
+// gathers dL/du^K, dL/dv^K into compact order and clears the adjoint
+__global__ void k_adj_gather(IterParams P, const uint32_t* __restrict__ act,
+                             const int32_t* __restrict__ wstart, const int32_t* __restrict__ counts,
+                             const float* __restrict__ grad_u, const float* __restrict__ grad_v,
+                             AdjArrays A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t word = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t nwords = (int64_t)P.H * P.ntx;
+    if (word >= nwords) return;
+    const int i = (int)(word / P.ntx);
+    const int wx = (int)(word - (int64_t)i * P.ntx);
+    const int64_t wo = (int64_t)i * P.nw + wx;
+    const uint32_t a = act[wo];
+    if (!((a >> lane) & 1u)) return;
+    const int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
+    const int64_t o = (int64_t)i * P.ld + wx * 32 + lane;
+    A.gu[idx] = grad_u[o];
+    A.gv[idx] = grad_v ? grad_v[o] : 0.f;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum1(double x, double* s_red) {
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) s_red[wid] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) t += s_red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(kPersistThreads)
+k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
+                   const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
+                   const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
+    if (*(volatile int*)&h->done) return;
+    const unsigned nblocks = gridDim.x;
+    const int n = counts[1];
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    unsigned gen = 0u;
+    const int64_t S4 = 4 * stride;   // one state of the segment buffer
+    auto segp1 = [&](int m) { return A.seg + m * S4; };
+    auto segp2 = [&](int m) { return A.seg + m * S4 + stride; };
+    auto segv = [&](int m) { return A.seg + m * S4 + 2 * stride; };
+    auto segw = [&](int m) { return A.seg + m * S4 + 3 * stride; };
+    // adjoint of the final iterate
+    for (int a = a0 + tid; a < a1; a += nt) {
+        A.p1b[a] = 0.f; A.p2b[a] = 0.f; A.vb[a] = A.gv[a]; A.fb[a] = 0.f;
+    }
+    const int nseg = (iters + ckpt_every - 1) / ckpt_every;
+    for (int k = nseg - 1; k >= 0; --k) {
+        const int n0 = k * ckpt_every;
+        const int M = min(ckpt_every, iters - n0);
+        // ---- replay the segment from its checkpoint
+        const float* c = ckpt + (int64_t)k * 3 * stride;
+        for (int a = a0 + tid; a < a1; a += nt) {
+            segp1(0)[a] = c[a]; segp2(0)[a] = c[stride + a]; segv(0)[a] = c[2 * stride + a];
+        }
+        if (!grid_sync(h, nblocks, gen)) return;
+        float d0 = 0.f, d1 = 0.f;
+        for (int a = a0 + tid; a < a1; a += nt)
+            primal_one<float>(P, a, nb, stride, segp1(0), segp2(0), segv(0), F, nullptr, segw(0), true,
+                              false, false, 0u, d0, d1);
+        if (!grid_sync(h, nblocks, gen)) return;
+        for (int m = 0; m < M; ++m) {
+            for (int a = a0 + tid; a < a1; a += nt)
+                dual_one<float>(P, a, nb, stride, segp1(m), segp2(m), segw(m), segp1(m + 1), segp2(m + 1), 0u);
+            if (!grid_sync(h, nblocks, gen)) return;
+            for (int a = a0 + tid; a < a1; a += nt) {
+                segv(m + 1)[a] = segv(m)[a];    // primal_one updates v in place
+            }
+            for (int a = a0 + tid; a < a1; a += nt)
+                primal_one<float>(P, a, nb, stride, segp1(m + 1), segp2(m + 1), segv(m + 1), F, nullptr,
+                                  segw(m + 1), false, false, false, 0u, d0, d1);
+            if (!grid_sync(h, nblocks, gen)) return;
+        }
+        // ---- walk back through the segment
+        for (int m = M - 1; m >= 0; --m) {
+            const bool last = n0 + m + 1 == iters;
+            // A: clip, u^{n+1}
+            for (int a = a0 + tid; a < a1; a += nt) {
+                const float vn = segv(m + 1)[a];
+                const float sb = (vn > 0.f && vn < 1.f) ? A.vb[a] : 0.f;
+                A.ub[a] = sb + (last ? A.gu[a] : 0.f);
+                A.fb[a] -= sb;
+            }
+            if (!grid_sync(h, nblocks, gen)) return;
+            // B: qbar = pbar + theta grad ubar, the fixed-point step
+            for (int a = a0 + tid; a < a1; a += nt) {
+                const int n_down = __ldg(nb + NB_DOWN * stride + a);
+                const int n_right = __ldg(nb + NB_RIGHT * stride + a);
+                const int n_dl = __ldg(nb + NB_DOWNLEFT * stride + a);
+                const int n_ur = __ldg(nb + NB_UPRIGHT * stride + a);
+                const float ua = A.ub[a];
+                const float ud = n_down >= 0 ? A.ub[n_down] : 0.f;
+                const float ur = n_right >= 0 ? A.ub[n_right] : 0.f;
+                float qb1 = A.p1b[a] + (n_down != kNbOut ? P.theta * (ud - ua) : 0.f);
+                float qb2 = A.p2b[a] + (n_right != kNbOut ? P.theta * (ur - ua) : 0.f);
+                // g^n as in the forward dual step
+                const float* p1s = segp1(m);
+                const float* p2s = segp2(m);
+                const float* ws = segw(m);
+                const float p1 = p1s[a], p2 = p2s[a], w0 = ws[a];
+                float g1 = 0.f, g2 = 0.f;
+                if (n_down != kNbOut)
+                    g1 = (n_down >= 0 ? ws[n_down] : w_fixed(p1, n_dl >= 0 ? p2s[n_dl] : 0.f, n_down, P.inv_theta)) - w0;
+                if (n_right != kNbOut)
+                    g2 = (n_right >= 0 ? ws[n_right] : w_fixed(n_ur >= 0 ? p1s[n_ur] : 0.f, p2, n_right, P.inv_theta)) - w0;
+                const float nrm = sqrtf(g1 * g1 + g2 * g2);
+                const float den = 1.f + P.tau * nrm;
+                const float q1 = segp1(m + 1)[a], q2 = segp2(m + 1)[a];
+                const float dot = qb1 * q1 + qb2 * q2;
+                const float h1 = nrm > 0.f ? g1 / nrm : 0.f, h2 = nrm > 0.f ? g2 / nrm : 0.f;
+                float gb1 = (P.tau / den) * (qb1 - dot * h1);
+                float gb2 = (P.tau / den) * (qb2 - dot * h2);
+                if (n_down == kNbOut) gb1 = 0.f;
+                if (n_right == kNbOut) gb2 = 0.f;
+                A.gb1[a] = gb1;
+                A.gb2[a] = gb2;
+                A.pd1[a] = qb1 / den;
+                A.pd2[a] = qb2 / den;
+            }
+            if (!grid_sync(h, nblocks, gen)) return;
+            // C: wbar = -div gbar at x, x+e1, x+e2; pbar, vbar of iterate n
+            for (int a = a0 + tid; a < a1; a += nt) {
+                const int n_up = __ldg(nb + NB_UP * stride + a);
+                const int n_left = __ldg(nb + NB_LEFT * stride + a);
+                const int n_down = __ldg(nb + NB_DOWN * stride + a);
+                const int n_right = __ldg(nb + NB_RIGHT * stride + a);
+                const int n_dl = __ldg(nb + NB_DOWNLEFT * stride + a);
+                const int n_ur = __ldg(nb + NB_UPRIGHT * stride + a);
+                const float g1 = A.gb1[a], g2 = A.gb2[a];
+                auto G1 = [&](int c2) { return c2 >= 0 ? A.gb1[c2] : 0.f; };
+                auto G2 = [&](int c2) { return c2 >= 0 ? A.gb2[c2] : 0.f; };
+                const float wb0 = -((g1 - G1(n_up)) + (g2 - G2(n_left)));
+                const float wbd = -((G1(n_down) - g1) + (G2(n_down) - G2(n_dl)));
+                const float wbr = -((G1(n_right) - G1(n_ur)) + (G2(n_right) - g2));
+                A.p1b[a] = A.pd1[a] - (n_down != kNbOut ? wbd - wb0 : 0.f);
+                A.p2b[a] = A.pd2[a] - (n_right != kNbOut ? wbr - wb0 : 0.f);
+                A.vb[a] = A.ub[a] - wb0 * P.inv_theta;
+            }
+            if (!grid_sync(h, nblocks, gen)) return;
+        }
+    }
+    // v0 = clip(u0 - F): its clipped value is in checkpoint 0
+    for (int a = a0 + tid; a < a1; a += nt) {
+        const float v0 = ckpt[2 * stride + a];
+        if (v0 > 0.f && v0 < 1.f) A.fb[a] -= A.vb[a];
+    }
+}
+
+// dL/df on the image (0 outside RD) and the FP64 sums for lambda, c1, c2
+// (fixed grid of kReduceBlocks blocks: deterministic).
+__global__ void __launch_bounds__(256)
+k_adj_scatter(IterParams P, const float* __restrict__ f, const uint32_t* __restrict__ act,
+              const int32_t* __restrict__ wstart, const float* __restrict__ Fbar,
+              const float* __restrict__ z, const double* __restrict__ c, float theta_lambda,
+              float* __restrict__ grad_f, double* __restrict__ red) {
+    __shared__ double s_red[8];
+    double sl = 0.0, s1 = 0.0, s2 = 0.0;
+    const int64_t n = (int64_t)P.H * P.W;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = x / P.W, j = x - i * P.W;
+        const int64_t wo = i * P.nw + (j >> 5);
+        const int64_t o = i * P.ld + j;
+        const uint32_t a = act[wo];
+        float gfv = 0.f;
+        if ((a >> (j & 31)) & 1u) {
+            const int64_t idx = wstart[wo] + __popc(a & lanemask_lt((int)(j & 31)));
+            const double fb = Fbar[idx];
+            gfv = (float)(theta_lambda * fb);
+            sl += (double)P.theta * (double)f[o] * fb;
+            if (z) {
+                const double zz = z[o];
+                s1 += (double)gfv * (-2.0 * (zz - c[0]));
+                s2 += (double)gfv * (2.0 * (zz - c[1]));
+            }
+        }
+        grad_f[o] = gfv;
+    }
+    const double a = block_sum1<256>(sl, s_red);
+    const double b = block_sum1<256>(s1, s_red);
+    const double d = block_sum1<256>(s2, s_red);
+    if (threadIdx.x == 0) {
+        red[3 * blockIdx.x] = a;
+        red[3 * blockIdx.x + 1] = b;
+        red[3 * blockIdx.x + 2] = d;
+    }
+}
+
+static size_t adj_float_arrays() { return 11; }
 
 }  // namespace seg
 
@@ -1056,5 +1292,135 @@ extern "C" seg_status seg_solve_batch(const seg_image* images, int n_images, con
                               4096, h, s));
     k_solve_end<<<1, 1, 0, s>>>(h, base + kMaxBatch + 2, prm->iters, stats);
     SEG_LAUNCHED("k_solve_end");
+    return SEG_OK;
+}
+
+
+// ----------------------------------------------------- differentiable solve
+
+extern "C" size_t seg_ckpt_bytes(int64_t capacity, int iters, int ckpt_every) {
+    if (ckpt_every < 1 || iters < 0) return 0;
+    const int64_t m = std::max(1, (iters + ckpt_every - 1) / ckpt_every);
+    return (size_t)m * 3 * 4 * (size_t)compact_stride(capacity) + 256;
+}
+
+extern "C" size_t seg_backward_scratch_bytes(int64_t capacity, int ckpt_every) {
+    const int64_t st = compact_stride(capacity);
+    return (adj_float_arrays() + 4 * (size_t)(std::max(ckpt_every, 1) + 1)) * 4 * (size_t)st + 16 * 256;
+}
+
+extern "C" seg_status seg_solve_diff(const float* f, int H, int W, int ld, const uint32_t* act,
+                                     const uint32_t* fgm, const int32_t* wstart, const int32_t* tiles,
+                                     const int32_t* counts, const seg_params* prm, float* u, float* v,
+                                     float* p1, float* p2, void* state, size_t state_bytes,
+                                     int ckpt_every, void* ckpt, size_t ckpt_bytes, double* stats,
+                                     void* ws, size_t ws_bytes, void* stream) {
+    clear_error();
+    SEG_TRY(check_params(prm));
+    if (prm->mode != SEG_MODE_COMPACT || prm->storage != SEG_STORE_F32 || prm->n_inner != 1 ||
+        prm->warm_start || prm->tol > 0)
+        return fail(SEG_ERR_INVALID_ARG,
+                    "seg_solve_diff: compact mode, float32 storage, n_inner = 1, cold start, tol <= 0");
+    if (!f || !act || !fgm || !wstart || !tiles || !counts || !u || !v || !p1 || !p2 || !state || !stats ||
+        !ckpt)
+        return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
+    if (H <= 0 || W <= 0 || ld < W || (int64_t)H * ld >= (1ll << 31))
+        return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d", H, W, ld);
+    if (ld % 32) return fail(SEG_ERR_ALIGN, "ld=%d is not a multiple of 32", ld);
+    if (ckpt_every < 1) return fail(SEG_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+    CompactLayout C = compact_layout(state_bytes, prm->storage);
+    if (ckpt_bytes < seg_ckpt_bytes(C.cap, prm->iters, ckpt_every))
+        return fail(SEG_ERR_CAPACITY, "checkpoints need %zu bytes", seg_ckpt_bytes(C.cap, prm->iters, ckpt_every));
+    WsLayout L = ws_layout(H, W, prm->tile_h);
+    SEG_TRY(check_ws(ws, ws_bytes, L));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader* h = ws_at<WsHeader>(ws, L.header);
+    double* partials = ws_at<double>(ws, L.partials);
+    IterParams P = iter_params(prm, H, W, ld);
+    BatchDesc B{};
+    B.n = 1;
+    B.total_words = (long long)H * P.ntx;
+    BatchImage& I = B.img[0];
+    I.f = f; I.act = act; I.fg = fgm; I.wstart = wstart; I.counts = counts;
+    I.u = u; I.v = v; I.p1 = p1; I.p2 = p2;
+    I.word_off = 0; I.H = H; I.W = W; I.ld = ld; I.nw = ld / 32; I.ntx = P.ntx;
+    I.theta_lambda = P.theta_lambda;
+    int32_t* base = ws_at<int32_t>(ws, kWsBatchOff);
+    k_solve_begin<<<1, 1, 0, s>>>(h);
+    SEG_LAUNCHED("k_solve_begin");
+    SEG_TRY(solve_compact_batch<float>(P, prm, B, (int64_t)H * W, state, state_bytes, base,
+                                       base + kMaxBatch + 2, partials, L.npartials, h, s,
+                                       static_cast<float*>(ckpt), ckpt_every));
+    k_solve_end<<<1, 1, 0, s>>>(h, base + kMaxBatch + 2, prm->iters, stats);
+    SEG_LAUNCHED("k_solve_end");
+    return SEG_OK;
+}
+
+extern "C" seg_status seg_backward(const float* f, int H, int W, int ld, const uint32_t* act,
+                                   const uint32_t* fgm, const int32_t* wstart, const int32_t* counts,
+                                   const seg_params* prm, const void* state, size_t state_bytes,
+                                   const void* ckpt, size_t ckpt_bytes, int ckpt_every,
+                                   const float* grad_u, const float* grad_v, const float* z,
+                                   const double* c, float* grad_f, double* grad_out, void* scratch,
+                                   size_t scratch_bytes, void* ws, size_t ws_bytes, void* stream) {
+    clear_error();
+    SEG_TRY(check_params(prm));
+    if (prm->mode != SEG_MODE_COMPACT || prm->storage != SEG_STORE_F32 || prm->n_inner != 1)
+        return fail(SEG_ERR_INVALID_ARG, "seg_backward: compact mode, float32 storage, n_inner = 1");
+    if (!f || !act || !fgm || !wstart || !counts || !state || !ckpt || !grad_u || !grad_f || !grad_out ||
+        !scratch || (z && !c))
+        return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
+    if (H <= 0 || W <= 0 || ld < W || (int64_t)H * ld >= (1ll << 31))
+        return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d", H, W, ld);
+    if (ld % 32) return fail(SEG_ERR_ALIGN, "ld=%d is not a multiple of 32", ld);
+    if (ckpt_every < 1) return fail(SEG_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+    CompactLayout C = compact_layout(state_bytes, prm->storage);
+    if (ckpt_bytes < seg_ckpt_bytes(C.cap, prm->iters, ckpt_every))
+        return fail(SEG_ERR_CAPACITY, "checkpoint buffer smaller than the forward wrote");
+    if (scratch_bytes < seg_backward_scratch_bytes(C.cap, ckpt_every))
+        return fail(SEG_ERR_WORKSPACE, "backward scratch needs %zu bytes",
+                    seg_backward_scratch_bytes(C.cap, ckpt_every));
+    if (reinterpret_cast<uintptr_t>(scratch) % 16)
+        return fail(SEG_ERR_ALIGN, "scratch not 16-byte aligned");
+    WsLayout L = ws_layout(H, W, prm->tile_h);
+    SEG_TRY(check_ws(ws, ws_bytes, L));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader* h = ws_at<WsHeader>(ws, L.header);
+    IterParams P = iter_params(prm, H, W, ld);
+    const char* sb = static_cast<const char*>(state);
+    const float* F = reinterpret_cast<const float*>(sb + C.off[5]);
+    const int32_t* nbp = reinterpret_cast<const int32_t*>(sb + C.off[8]);
+    int64_t stride = C.stride;
+    AdjArrays A{};
+    float* sc = static_cast<float*>(scratch);
+    float** fields[] = {&A.p1b, &A.p2b, &A.vb, &A.ub, &A.gb1, &A.gb2, &A.pd1, &A.pd2, &A.fb, &A.gu, &A.gv};
+    for (size_t k = 0; k < adj_float_arrays(); ++k) *fields[k] = sc + k * stride;
+    A.seg = sc + adj_float_arrays() * stride;
+
+    k_solve_begin<<<1, 1, 0, s>>>(h);
+    SEG_LAUNCHED("k_solve_begin");
+    const int64_t nwords = (int64_t)H * P.ntx;
+    const unsigned gblocks = (unsigned)((nwords + 7) / 8);
+    k_adj_gather<<<gblocks, 256, 0, s>>>(P, act, wstart, counts, grad_u, grad_v, A);
+    SEG_LAUNCHED("k_adj_gather");
+    auto kern = k_backward_compact;
+    int per_sm = 0;
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, 0));
+    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_backward_compact cannot be resident");
+    const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)H * W));
+    int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
+                                      std::max<int64_t>(1, (most + kPersistThreads - 1) / kPersistThreads));
+    int iters = prm->iters, ce = ckpt_every;
+    const float* ck = static_cast<const float*>(ckpt);
+    void* args[] = {&P, &iters, &ce, (void*)&counts, (void*)&nbp, &stride, (void*)&F, (void*)&ck, &A, &h};
+    if (iters > 0) {
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPersistThreads), args,
+                                                 0, s));
+        count_launch();
+    }
+    double* red = ws_at<double>(ws, kWsRedOff);
+    k_adj_scatter<<<kReduceBlocks, 256, 0, s>>>(P, f, act, wstart, A.fb, z, c, P.theta_lambda, grad_f, red);
+    SEG_LAUNCHED("k_adj_scatter");
+    SEG_TRY(reduce_partials(red, kReduceBlocks, 3, grad_out, s));
     return SEG_OK;
 }

@@ -82,6 +82,12 @@ SIGNATURES = {
     "seg_errors": ([_P, _P, _I, _I, _I, _D, _P, _P, _Z, _P], _I),
     "seg_energy_noalloc": ([_P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _P, _P], _I),
     "seg_batch_workspace_bytes": ([_I, _L], _Z),
+    "seg_ckpt_bytes": ([_L, _I, _I], _Z),
+    "seg_backward_scratch_bytes": ([_L, _I], _Z),
+    "seg_solve_diff": ([_P, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(seg_params), _P, _P, _P, _P,
+                        _P, _Z, _I, _P, _Z, _P, _P, _Z, _P], _I),
+    "seg_backward": ([_P, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(seg_params), _P, _Z, _P, _Z, _I,
+                      _P, _P, _P, _P, _P, _P, _P, _Z, _P, _Z, _P], _I),
     "seg_solve_batch": ([ctypes.POINTER(seg_image), _I, ctypes.POINTER(seg_params), _P, _Z, _P, _P, _Z,
                          _P], _I),
 }
@@ -209,6 +215,35 @@ def seg_solve_batch(images, params: seg_params, state, stats, ws, stream=None):
     lib = load()
     _check(lib.seg_solve_batch(images, len(images), ctypes.byref(params), _ptr(state),
                                _nbytes(state), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def seg_ckpt_bytes(capacity, iters, ckpt_every):
+    return load().seg_ckpt_bytes(int(capacity), int(iters), int(ckpt_every))
+
+
+def seg_backward_scratch_bytes(capacity, ckpt_every):
+    return load().seg_backward_scratch_bytes(int(capacity), int(ckpt_every))
+
+
+def seg_solve_diff(f, act, fg, wstart, tiles, counts, params: seg_params, u, v, p1, p2, state,
+                   ckpt_every, ckpt, stats, ws, stream=None):
+    lib = load()
+    _check(lib.seg_solve_diff(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(act), _ptr(fg),
+                              _ptr(wstart), _ptr(tiles), _ptr(counts), ctypes.byref(params), _ptr(u),
+                              _ptr(v), _ptr(p1), _ptr(p2), _ptr(state), _nbytes(state),
+                              int(ckpt_every), _ptr(ckpt), _nbytes(ckpt), _ptr(stats), _ptr(ws),
+                              _nbytes(ws), _stream(stream)))
+
+
+def seg_backward(f, act, fg, wstart, counts, params: seg_params, state, ckpt, ckpt_every, grad_u,
+                 grad_v, z, c, grad_f, grad_out, scratch, ws, stream=None):
+    lib = load()
+    _check(lib.seg_backward(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(act), _ptr(fg),
+                            _ptr(wstart), _ptr(counts), ctypes.byref(params), _ptr(state),
+                            _nbytes(state), _ptr(ckpt), _nbytes(ckpt), int(ckpt_every),
+                            _ptr(grad_u), _ptr(grad_v), _ptr(z), _ptr(c), _ptr(grad_f),
+                            _ptr(grad_out), _ptr(scratch), _nbytes(scratch), _ptr(ws), _nbytes(ws),
+                            _stream(stream)))
 
 
 def seg_errors(u_star, u_gt, eps, out, ws, stream=None):
@@ -454,3 +489,87 @@ class BatchSolver:
     def check_status(self):
         seg_read_status(self.ws, self.stream)
         seg_read_status(self.ws_img, self.stream)
+
+
+class DiffSolver(Solver):
+    """A compact float32 Solver whose solve can be differentiated: the forward
+    (seg_solve_diff) keeps checkpoints every `ckpt_every` iterations and
+    `backward` runs the adjoint (seg_backward)."""
+
+    def __init__(self, H, W, iters, ckpt_every=20, tile_h=16, capacity=None, device="cuda",
+                 stream=None):
+        super().__init__(H, W, tile_h=tile_h, mode="compact", storage="f32", capacity=capacity,
+                         device=device, stream=stream)
+        self.iters, self.ckpt_every = int(iters), int(ckpt_every)
+        cap = self.capacity
+        nb = seg_ckpt_bytes(cap, self.iters, self.ckpt_every)
+        self.ckpt = torch.empty((nb + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        nb = seg_backward_scratch_bytes(cap, self.ckpt_every)
+        self.scratch = torch.empty((nb + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        self.grad_f = image(H, W, device=self.device)
+        self.grad_out = torch.zeros(3, dtype=torch.float64, device=self.device)
+        self._prm = None
+
+    def solve_diff(self, lam, theta=0.2, tau=0.125, f=None):
+        f = self.f if f is None else f
+        d = self.dom
+        self._prm = make_params(lam, theta, tau, self.iters, 0.0, 1, self.iters, False, "compact",
+                                "f32", self.tile_h)
+        seg_solve_diff(f, d.act, d.fg, d.wstart, d.tiles, d.counts, self._prm, self.u, self.v,
+                       self.p1, self.p2, self.state, self.ckpt_every, self.ckpt, self.stats, self.ws,
+                       self.stream)
+        return self.u
+
+    def backward(self, grad_u, grad_v=None, z=None, c=None, f=None):
+        f = self.f if f is None else f
+        d = self.dom
+        seg_backward(f, d.act, d.fg, d.wstart, d.counts, self._prm, self.state, self.ckpt,
+                     self.ckpt_every, grad_u, grad_v, z, c, self.grad_f, self.grad_out,
+                     self.scratch, self.ws, self.stream)
+        return self.grad_f, self.grad_out
+
+
+class SegSolveFn(torch.autograd.Function):
+    """u^K = solve(f, lambda) through the unrolled restricted iteration, with
+    the hand-written adjoint as its backward.  f is a [H, ld] image tensor
+    (its domain must already be built in `solver` with solver.domain), lam a
+    0-d float64 tensor; returns u^K ([H, ld])."""
+
+    @staticmethod
+    def forward(ctx, f, lam, solver: DiffSolver, theta=0.2, tau=0.125):
+        solver.f.copy_(f)
+        solver.solve_diff(float(lam.item()), theta, tau)
+        ctx.solver = solver
+        return solver.u.clone()
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        S = ctx.solver
+        g = image(S.H, S.W, device=S.device)
+        g.copy_(grad_u)
+        gf, gout = S.backward(g)
+        return gf.clone(), gout[0].clone(), None, None, None
+
+
+class SegFitSolveFn(torch.autograd.Function):
+    """u^K = solve(f(z; c1, c2), lambda) with f the piecewise-constant fitting
+    term (Eq. CV); gradients for c1, c2 and lambda.  z: [H, ld] image tensor;
+    c1, c2, lam: 0-d float64 tensors.  The domain is built from f at delta
+    (and held fixed in the backward)."""
+
+    @staticmethod
+    def forward(ctx, z, c1, c2, lam, solver: DiffSolver, delta, theta=0.2, tau=0.125):
+        seg_make_fitting(z, float(c1.item()), float(c2.item()), None, None, 0.0, solver.f, solver.c,
+                         solver.ws, solver.stream)
+        solver.domain(delta=delta)
+        solver.solve_diff(float(lam.item()), theta, tau)
+        ctx.solver, ctx.z = solver, z
+        return solver.u.clone()
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        S = ctx.solver
+        g = image(S.H, S.W, device=S.device)
+        g.copy_(grad_u)
+        _, gout = S.backward(g, z=ctx.z, c=S.c)
+        return None, gout[1].clone(), gout[2].clone(), gout[0].clone(), None, None, None, None

@@ -1,0 +1,146 @@
+"""The hand-written adjoint (seg_solve_diff + seg_backward, and the
+torch.autograd.Function around them) against the FP64 oracle's reverse mode
+(itself pinned by central finite differences) and against finite
+differences of the CUDA forward."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1807_11534_gb300 import synth
+from tests.gpu_helpers import require_gpu, seg_mod
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    seg_mod()
+
+
+def _gpu_grad(f, delta, lam, gu, gv, iters, ckpt_every, z=None, c=None):
+    seg = seg_mod()
+    H, W = f.shape
+    S = seg.DiffSolver(H, W, iters, ckpt_every)
+    S.f[:, :W].copy_(torch.from_numpy(f))
+    S.domain(delta=delta)
+    S.solve_diff(lam)
+    g = seg.upload(gu.astype(np.float32))
+    gvt = seg.upload(gv.astype(np.float32)) if gv is not None else None
+    zt = seg.upload(z) if z is not None else None
+    ct = torch.tensor(c, dtype=torch.float64, device="cuda") if c is not None else None
+    gf, gout = S.backward(g, gvt, zt, ct)
+    torch.cuda.synchronize()
+    S.check_status()
+    return seg.download(gf).astype(np.float64), gout.cpu().numpy(), S
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12))
+
+
+@pytest.mark.parametrize("shape,delta,iters,ce", [((40, 50), np.inf, 30, 7), ((64, 64), 0.25, 60, 20),
+                                                  ((33, 70), 0.12, 25, 25), ((20, 31), 0.3, 9, 1)])
+def test_backward_matches_oracle_reverse_mode(orc, shape, delta, iters, ce):
+    rng = np.random.default_rng(sum(shape))
+    P = synth.small_example(seed=shape[0], H=shape[0], W=shape[1])
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    gu = rng.normal(size=shape)
+    gv = rng.normal(size=shape)
+    lam = 1.3
+    gf, gout, _ = _gpu_grad(f, delta, lam, gu, gv, iters, ce)
+    reg = orc.domain(f, delta)
+    gf_o, gl_o = orc.solve_grad(f, reg, lam, gu, gv, iters=iters)
+    assert np.all(gf[reg != 2] == 0)
+    assert _rel(gf, gf_o) <= 1e-3, _rel(gf, gf_o)
+    assert abs(gout[0] - gl_o) <= 1e-3 * max(1.0, abs(gl_o)), (gout[0], gl_o)
+
+
+def test_c_gradients_through_the_fitting_term(orc):
+    """dL/dc1 = sum dL/df (-2)(z - c1), dL/dc2 = sum dL/df 2(z - c2) (Eq. CV)."""
+    rng = np.random.default_rng(5)
+    P = synth.small_example(seed=9, H=48, W=64)
+    c1, c2 = 0.32, 0.69
+    _, f = orc.fitting(P.z, c1, c2)
+    gu = rng.normal(size=f.shape)
+    gf, gout, _ = _gpu_grad(f, 0.2, 1.0, gu, None, 40, 10, z=P.z, c=[c1, c2])
+    reg = orc.domain(f, 0.2)
+    gf_o, _ = orc.solve_grad(f, reg, 1.0, gu, None, iters=40)
+    z = P.z.astype(np.float64)
+    e1 = float(np.sum(gf_o * (-2.0) * (z - c1)))
+    e2 = float(np.sum(gf_o * 2.0 * (z - c2)))
+    assert abs(gout[1] - e1) <= 1e-3 * max(1.0, abs(e1)) and abs(gout[2] - e2) <= 1e-3 * max(1.0, abs(e2))
+
+
+@pytest.mark.slow
+def test_crops_of_the_differentiation_workload(orc):
+    """1024x1024 random-shape images with generator masks, BCE(u_K, mask) on
+    clip(u_K, 1e-4, 1 - 1e-4), K = 200 unrolled iterations, checkpoints every
+    20; the gradient of 64x64 crops (each an independent problem) against the
+    oracle's reverse mode, and against central differences of the CUDA
+    forward with h = 1e-3 along a random direction."""
+    rng = np.random.default_rng(11)
+    probs = synth.training_batch(seed=0, n_images=2, side=1024)
+    for P in probs:
+        _, f_full = orc.fitting(P.z, 0.3, 0.7)
+        i0, j0 = rng.integers(0, 1024 - 64, 2)
+        f = np.ascontiguousarray(f_full[i0:i0 + 64, j0:j0 + 64])
+        m = P.label[i0:i0 + 64, j0:j0 + 64].astype(np.float64)
+        K, lam, delta = 200, 1.0, 0.2
+        # BCE gradient at the oracle's u_K
+        reg = orc.domain(f, delta)
+        u = orc.solve(f, reg, lam, iters=K).u
+        uc = np.clip(u, 1e-4, 1 - 1e-4)
+        gu = np.where((u > 1e-4) & (u < 1 - 1e-4), (uc - m) / (uc * (1 - uc)), 0.0) / u.size
+        gf, gout, S = _gpu_grad(f, delta, lam, gu, None, K, 20)
+        gf_o, gl_o = orc.solve_grad(f, reg, lam, gu, None, iters=K)
+        assert _rel(gf, gf_o) <= 1e-3, _rel(gf, gf_o)
+        assert abs(gout[0] - gl_o) <= 1e-3 * max(1e-3, abs(gl_o))
+        # finite differences of the CUDA forward (linear loss <gu, u_K>)
+        seg = seg_mod()
+        d = np.where(reg == 2, rng.normal(size=f.shape), 0.0)
+        h = 1e-3
+
+        def loss(ff):
+            T = seg.DiffSolver(64, 64, K, 20)
+            T.f[:, :64].copy_(torch.from_numpy(ff.astype(np.float32)))
+            T.dom = S.dom     # the partition of the unperturbed f stays fixed
+            T.solve_diff(lam)
+            return float(np.sum(gu * seg.download(T.u)))
+
+        fd = (loss(f + h * d) - loss(f - h * d)) / (2 * h)
+        an = float(np.sum(gf * d))
+        assert abs(fd - an) <= 2e-2 * max(abs(an), 1e-3), (fd, an)
+
+
+def test_autograd_function(orc):
+    seg = seg_mod()
+    rng = np.random.default_rng(3)
+    P = synth.small_example(seed=3, H=50, W=70)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    S = seg.DiffSolver(50, 70, 40, 10)
+    S.f[:, :70].copy_(torch.from_numpy(f))
+    S.domain(delta=0.2)
+    ft = S.f.clone().requires_grad_(True)
+    lam = torch.tensor(1.2, dtype=torch.float64, device="cuda", requires_grad=True)
+    wgt = torch.zeros_like(S.f)
+    wgt[:, :70] = torch.from_numpy(rng.normal(size=(50, 70)).astype(np.float32))
+    u = seg.SegSolveFn.apply(ft, lam, S)
+    (u * wgt).sum().backward()
+    reg = orc.domain(f, 0.2)
+    gf_o, gl_o = orc.solve_grad(f, reg, 1.2, wgt[:, :70].cpu().numpy().astype(np.float64), None, iters=40)
+    assert _rel(ft.grad[:, :70].cpu().numpy().astype(np.float64), gf_o) <= 1e-3
+    assert abs(lam.grad.item() - gl_o) <= 1e-3 * max(1.0, abs(gl_o))
+    # c1, c2 through the fitting term
+    z = seg.upload(P.z)
+    c1 = torch.tensor(0.3, dtype=torch.float64, device="cuda", requires_grad=True)
+    c2 = torch.tensor(0.7, dtype=torch.float64, device="cuda", requires_grad=True)
+    lam2 = torch.tensor(1.2, dtype=torch.float64, device="cuda", requires_grad=True)
+    u2 = seg.SegFitSolveFn.apply(z, c1, c2, lam2, S, 0.2)
+    (u2 * wgt).sum().backward()
+    zz = P.z.astype(np.float64)
+    assert abs(c1.grad.item() - np.sum(gf_o * -2 * (zz - 0.3))) <= 1e-3 * max(1.0, abs(c1.grad.item()))
+    assert abs(c2.grad.item() - np.sum(gf_o * 2 * (zz - 0.7))) <= 1e-3 * max(1.0, abs(c2.grad.item()))
+    assert abs(lam2.grad.item() - gl_o) <= 1e-3 * max(1.0, abs(gl_o))
