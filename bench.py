@@ -35,6 +35,12 @@ sys.path.insert(0, ROOT)
 
 DELTA_SWEEP = (0.02, 0.05, 0.1, 0.2, 0.3, 0.5)
 BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + write p1,p2,v
+# DRAM bytes (read + write) per iteration of k_solve_compact, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum over a 50-iteration
+# launch / 50) of `bench.py --profile --iters 50` (2048x2048, delta = 0.2,
+# float32), summarised in profiles/k_solve_compact_ds2048.md.  The compacted
+# state stays in L2, so this is far below the algorithmic bytes.
+COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (46336 + 21832192) / 50}
 
 
 def parse():
@@ -46,7 +52,7 @@ def parse():
     ap.add_argument("--workload", default="ds2048", choices=["ds2048", "small", "batch"])
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--lam", type=float, default=2.0)
-    ap.add_argument("--tile-h", type=int, default=16)
+    ap.add_argument("--tile-h", type=int, default=0, help="0: autotune")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -68,7 +74,7 @@ def make_problem(args):
     return P
 
 
-def workload_config(args, P, delta, A):
+def workload_config(args, P, delta, A, tile_h):
     H, W = P.z.shape
     return {"workload": f"{'ds2048' if args.workload == 'ds2048' else 'ds256'}: {H}x{W} image, "
                         f"40 ellipses + N(0,0.1), distance-selective term (20 markers, gamma=0.5), "
@@ -76,7 +82,7 @@ def workload_config(args, P, delta, A):
                         f"(smallest of the sweep with E1>=0.98 vs full domain) vs full domain",
             "H": H, "W": W, "iters": P.iters, "delta": delta, "active_pixels": int(A),
             "active_fraction": round(A / (H * W), 4), "storage": args.storage,
-            "tile_h": args.tile_h, "l2": "flushed between steps (256 MiB write)"}
+            "tile_h": tile_h, "l2": "flushed between steps (256 MiB write)"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -155,15 +161,14 @@ def run_ours(args, rank, world):
     z = seg.upload(P.z, dev)
     label = seg.upload(P.label, dev)
     markers = torch.from_numpy(P.markers.astype(np.int32)).to(dev)
-    th = args.tile_h
-    R = seg.Solver(H, W, tile_h=th, mode="compact", storage=args.storage, device=dev)
-    F = seg.Solver(H, W, tile_h=th, mode="dense", storage="f32", device=dev)
+    F = seg.Solver(H, W, tile_h=16, mode="dense", storage="f32", device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     # ---- calibration (untimed): full-domain result and the equal-error delta
     F.fitting(z, label=label, markers=markers, gamma=P.gamma)
     F.domain(delta=math.inf)
     F.solve(args.lam, iters=iters, check_every=iters)
+    R = seg.Solver(H, W, tile_h=16, mode="compact", storage=args.storage, device=dev)
     R.fitting(z, label=label, markers=markers, gamma=P.gamma)
     chosen, e1s = None, {}
     for d in DELTA_SWEEP:
@@ -176,6 +181,17 @@ def run_ours(args, rank, world):
             break
     if chosen is None:
         chosen = DELTA_SWEEP[-1]
+
+    def make_run(th):
+        Rt = seg.Solver(H, W, tile_h=th, mode="compact", storage=args.storage, device=dev)
+        Rt.fitting(z, label=label, markers=markers, gamma=P.gamma)
+        Rt.domain(delta=chosen)
+        return lambda: Rt.solve(args.lam, iters=50, check_every=50)
+
+    th = args.tile_h if args.tile_h > 0 else seg.autotune(("ds", H, W, chosen, args.storage), make_run,
+                                                          (8, 16, 32))
+    R = seg.Solver(H, W, tile_h=th, mode="compact", storage=args.storage, device=dev)
+    R.fitting(z, label=label, markers=markers, gamma=P.gamma)
     R.domain(delta=chosen)
     R.check_status()
     A = int(R.dom.counts[1].item())
@@ -287,7 +303,7 @@ def run_ours(args, rank, world):
                iters=iters, delta=chosen, e1s=e1s, e1=e1_final, e2=e2_final,
                launches=int(launches), clocks=clk.summary(), t_iter_r=t_iter_r,
                t_iter_f=t_iter_f, ach_r=ach_r, ach_f=ach_f, e2e_ms=float(np.mean(t_e2e)),
-               h2d=h2d, d2h=d2h, P=P)
+               h2d=h2d, d2h=d2h, P=P, tile_h=th)
     return res
 
 
@@ -303,7 +319,7 @@ def run_profile(args):
     label = seg.upload(P.label, dev)
     markers = torch.from_numpy(P.markers.astype(np.int32)).to(dev)
     for mode, delta in (("compact", args.delta), ("dense", math.inf)):
-        S = seg.Solver(H, W, tile_h=args.tile_h, mode=mode,
+        S = seg.Solver(H, W, tile_h=args.tile_h or 16, mode=mode,
                        storage=args.storage if mode == "compact" else "f32", device=dev)
         S.fitting(z, label=label, markers=markers, gamma=P.gamma)
         S.domain(delta=delta)
@@ -328,9 +344,20 @@ def run_batch(args, rank, world):
     probs = synth.batch(seed=0, iters=args.iters or 500)
     iters = probs[0].iters
     shapes = [p.z.shape for p in probs]
-    B = seg.BatchSolver(shapes, tile_h=args.tile_h, storage=args.storage, device=dev)
     zs = [seg.upload(p.z, dev) for p in probs]
     lams = [p.lam for p in probs]
+
+    # autotune the tile height (it sets the compact order, hence locality)
+    def make_run(th):
+        Bt = seg.BatchSolver(shapes, tile_h=th, storage=args.storage, device=dev)
+        for P, S, z in zip(probs, Bt.solvers, zs):
+            S.fitting(z, P.c1, P.c2)
+            S.domain(q=P.q)
+        return lambda: Bt.solve(lams, iters=20, check_every=20)
+
+    tile_h = args.tile_h if args.tile_h > 0 else seg.autotune(("batch", args.storage), make_run,
+                                                              (8, 16, 32))
+    B = seg.BatchSolver(shapes, tile_h=tile_h, storage=args.storage, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
@@ -377,7 +404,7 @@ def run_batch(args, rank, world):
     t_iter = (solve_ms(iters) - solve_ms(0)) / iters
     bpa = BYTES_PER_ACTIVE_ITER[args.storage]
     ach = bpa * A / (t_iter * 1e-3) / 1e9
-    return dict(ms=float(np.mean(ms)), A=A, N=sum(h * w for h, w in shapes), iters=iters,
+    return dict(ms=float(np.mean(ms)), A=A, N=sum(h * w for h, w in shapes), iters=iters, tile_h=tile_h,
                 launches=per_step * args.steps, clocks=clk.summary(), t_iter=t_iter, ach=ach,
                 probs=probs)
 
@@ -463,7 +490,7 @@ def main():
                 "config": {"workload": "batch: 64 images, sides U{128..1024}, shapes + N(0,0.05), "
                                        f"q~U[0.02,0.4] quantile delta, {r['iters']} iters, one "
                                        "persistent launch, CUDA graph",
-                           "pixels": r["N"], "active_pixels": r["A"],
+                           "pixels": r["N"], "active_pixels": r["A"], "tile_h": r["tile_h"],
                            "l2": "flushed between steps (256 MiB write)"},
                 "roofline": {"bound": "hbm", "kernel": "k_solve_compact (one iteration)",
                              "achieved": r["ach"], "peak": peak, "unit": "GB/s",
@@ -498,10 +525,13 @@ def main():
         "value": value, "unit": "active Mpixel-iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_r, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.storage if args.storage != "f32" else "f32",
-        "data": "synthetic", "config": workload_config(args, r["P"], r["delta"], r["A"]),
-        "roofline": {"bound": "hbm", "kernel": "k_dual_compact + k_primal_compact (one iteration)",
+        "data": "synthetic", "config": workload_config(args, r["P"], r["delta"], r["A"], r["tile_h"]),
+        "roofline": {"bound": "hbm", "kernel": "k_solve_compact (one iteration)",
                      "achieved": r["ach_r"],
-                     "peak": peak, "unit": "GB/s", "frac": r["ach_r"] / peak, "traffic": None,
+                     "peak": peak, "unit": "GB/s", "frac": r["ach_r"] / peak,
+                     "traffic": COMPACT_DRAM_BYTES_PER_ITER.get((args.workload, args.storage)),
+                     "traffic_note": "ncu DRAM bytes per iteration; the compacted state is "
+                                     "L2-resident across iterations",
                      "bytes_per_active_iter": BYTES_PER_ACTIVE_ITER[args.storage],
                      "us_per_iter": r["t_iter_r"] * 1e3, "peak_source": peak_src},
         "full_domain": {"value": full_value, "unit": "active Mpixel-iter/s", "ms_per_step": r["ms_f"],

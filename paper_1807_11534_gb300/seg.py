@@ -573,3 +573,34 @@ class SegFitSolveFn(torch.autograd.Function):
         g.copy_(grad_u)
         _, gout = S.backward(g, z=ctx.z, c=S.c)
         return None, gout[1].clone(), gout[2].clone(), gout[0].clone(), None, None, None, None
+
+
+_TUNE_CACHE = {}
+
+
+def autotune(key, make_run, candidates, reps=3):
+    """Project autotuner: `make_run(c)` prepares the work for candidate c (for
+    example a solver whose domain uses tile height c) and returns a callable
+    that runs a short solve on the current stream; each candidate is timed
+    with CUDA events (best of `reps` after one warm-up) and the fastest is
+    returned and cached under `key`."""
+    if key in _TUNE_CACHE:
+        return _TUNE_CACHE[key]
+    best, best_t = None, None
+    for c in candidates:
+        run = make_run(c)
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t = None
+        for _ in range(reps):
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            dt = e0.elapsed_time(e1)
+            t = dt if t is None else min(t, dt)
+        if best_t is None or t < best_t:
+            best, best_t = c, t
+    _TUNE_CACHE[key] = best
+    return best
