@@ -54,6 +54,10 @@ typedef int seg_status;
 /* solve modes */
 #define SEG_MODE_DENSE 0        /* dense [H][ld] state, tile list of the domain, fused stencil */
 #define SEG_MODE_COMPACT 1      /* state stored only for RD pixels (tile-major compact order) */
+#define SEG_MODE_TILED 2        /* dense [H][ld] state, several iterations per pass: each
+                                   60 x 68 window (own region + a halo as wide as the
+                                   iterations it runs) is iterated in shared memory over
+                                   its RD pixels; float32 storage only */
 
 /* storage types of the iteration state (p1, p2, v); arithmetic is float32 */
 #define SEG_STORE_F32 0
@@ -70,10 +74,11 @@ typedef struct seg_params {
     int n_inner;        /* fixed-point sweeps for p per outer iteration (>= 1; default 1) */
     int check_every;    /* evaluate the stopping test every this many iterations (>= 1) */
     int warm_start;     /* 0: start from u = H(-f), p = 0, v = v-step(u); 1: from the u, v, p1, p2 given */
-    int mode;           /* SEG_MODE_DENSE or SEG_MODE_COMPACT */
+    int mode;           /* SEG_MODE_DENSE, SEG_MODE_COMPACT or SEG_MODE_TILED */
     int storage;        /* SEG_STORE_*; 16-bit storage is SEG_MODE_COMPACT only */
     int tile_h;         /* tile height used by seg_build_domain for this domain */
-    int reserved;
+    int sweep;          /* SEG_MODE_TILED: outer iterations per window pass (0: 4);
+                           sweep * n_inner <= 8.  Ignored by the other modes. */
 } seg_params;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -91,7 +96,8 @@ unsigned long long seg_launch_count(void);
 size_t seg_workspace_bytes(int H, int W, int ld, int tile_h);
 
 /* Bytes of iteration state for seg_solve: dense mode 6*H*ld float32
- * (ping-pong p1, p2, v); compact mode room for `capacity` RD pixels
+ * (ping-pong p1, p2, v); tiled mode the same planes plus the RD pixel list of
+ * every window (about 4 bytes per pixel); compact mode room for `capacity` RD pixels
  * (ping-pong p1, p2, v in the storage type, plus f, u and the pixel list). */
 size_t seg_state_bytes(int H, int ld, int64_t capacity, int mode, int storage);
 
@@ -155,6 +161,8 @@ seg_status seg_build_domain(const float* f, int H, int W, int ld,
  *                 prm->warm_start, and the final iterate on output.
  *   state         seg_state_bytes(H, ld, capacity, mode, storage) bytes
  *                 (compact mode: capacity >= n_active).
+ * SEG_MODE_TILED additionally needs f 16-byte aligned (it is read by TMA)
+ * and returns INVALID_ARG when sweep * n_inner > 8.
  *   stats         out double[8] (device): [0] iterations run, [1] last
  *                 ||du||, [2] last ||dv|| (from the last check), [3] n_active,
  *                 [4] n_tiles, [5] iteration of the last check.

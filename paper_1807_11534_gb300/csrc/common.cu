@@ -21,6 +21,17 @@ seg_status fail(seg_status st, const char* fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, m = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+        n = m > 0 ? m : 1;
+    }
+    return n;
+}
+
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 

@@ -1,0 +1,83 @@
+// iterate.cuh -- pieces of one outer iteration of Sections 2.1 and 3 shared
+// by the solvers of solve.cu (dense, compact) and tiled.cu (temporally
+// blocked): the scalar parameters, the fixed-point update of p, and the
+// bounded grid-wide barrier of the persistent kernels.
+#pragma once
+
+#include "seg_internal.cuh"
+
+namespace seg {
+
+struct IterParams {
+    float theta, inv_theta, tau, theta_lambda;
+    int H, W, ld, nw, ntx, th;
+    uint32_t seed;   // per-launch seed of the stochastic rounding of 16-bit stores
+};
+
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
+
+// p' = (p + tau g) / (1 + tau |g|); |g| through the hardware reciprocal square
+// root and the quotient through the fast divide (a few ulp; the iteration is
+// checked against the FP64 oracle to 1e-4).
+__device__ __forceinline__ void chambolle_update(float p1, float p2, float g1, float g2, float tau,
+                                                 float& q1, float& q2) {
+    const float s = fmaf(g1, g1, g2 * g2);
+    const float nrm = s > 0.f ? s * rsqrtf(s) : 0.f;
+    const float r = __fdividef(1.0f, fmaf(tau, nrm, 1.0f));
+    q1 = fmaf(tau, g1, p1) * r;
+    q2 = fmaf(tau, g2, p2) * r;
+}
+
+// ------------------------------------------------ persistent kernels
+
+// Grid-wide barrier (arrival counter + generation), with a bounded wait:
+// thread 0 of each block arrives with a release add and polls the generation
+// with acquire loads until it passes `gen` (the block's count of barriers
+// passed, which every block tracks in a register); the last arrival resets
+// the counter and releases the generation.  Returns false after recording
+// SEG_ERR_TIMEOUT (and raising the done flag) if the others do not arrive
+// within ~1 s.
+__device__ __forceinline__ bool grid_sync(WsHeader* h, unsigned nblocks, unsigned& gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    ++gen;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (atom_add_release_gpu(&h->bar_count, 1u) == nblocks - 1) {
+            h->bar_count = 0u;
+            atom_add_release_gpu(&h->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while ((int)(ld_acquire_gpu(&h->bar_gen) - gen) < 0) {
+                if (clock64() - t0 > kWaitCycles) {
+                    record_status(h, SEG_ERR_TIMEOUT);
+                    h->done = 1;
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ------------------------------------------------ host entry of tiled.cu
+
+// Temporally blocked solve on the dense ping-pong state `st` (initialised by
+// the dense init kernel): all iterations in one cooperative launch, then the
+// final p1, p2, v copied out (u is written by the solve itself).
+seg_status run_tiled(const IterParams& P, const seg_params* prm, const uint32_t* act, const float* f,
+                     float* u, float* v, float* p1, float* p2, float* st, double* partials, int64_t npartials,
+                     WsHeader* h, cudaStream_t s);
+
+// Number of windows of the tiled solve for an H x W image (validates sweep
+// and n_inner).
+seg_status tiled_geometry(int H, int W, int sweep, int n_inner, int* nwin);
+
+// State bytes of the tiled solve: the six dense planes and the per-window
+// RD lists.
+size_t tiled_state_bytes(int H, int ld);
+
+}  // namespace seg

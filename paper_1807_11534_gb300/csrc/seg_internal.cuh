@@ -36,6 +36,9 @@ void clear_error();
 // Host-side count of kernel launches issued by the library (diagnostics).
 void count_launch();
 
+// Streaming multiprocessors of the current device (queried once).
+int sm_count();
+
 // Checks the launch that was just issued.
 #define SEG_LAUNCHED(name)                                                           \
     do {                                                                             \
@@ -62,6 +65,10 @@ struct WsHeader {
     long long qk;        // rank still to find (quantile mode)
     long long qk0;       // rank asked for, k = ceil(q n)
     int n_fg;            // fixed foreground pixels
+    // temporally blocked solver: window tickets of the last four sweeps and
+    // the ping-pong buffer that holds the final state
+    int tb_ticket[4];
+    int tb_buf;
     // grid barrier of the persistent solver: arrival counter and generation,
     // on separate cache lines so that polling does not contend with arrivals
     alignas(128) unsigned bar_count;
@@ -248,6 +255,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Tiled TMA load of one 2-D box at (x, y) = (column, row) of the tensor
+// described by `map` (a kernel parameter or global-memory descriptor) into
+// shared memory, completing on `bar`.  x times the element size must be a
+// multiple of 16 bytes; coordinates outside the tensor read as zero.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)) : "memory");
+}
+
+// Orders this thread's earlier generic-proxy global accesses (and those it
+// has acquired from other threads) before its later TMA accesses.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {

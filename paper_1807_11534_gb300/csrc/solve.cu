@@ -31,29 +31,9 @@
 #include <algorithm>
 #include <cmath>
 
-#include "seg_internal.cuh"
+#include "iterate.cuh"
 
 namespace seg {
-
-struct IterParams {
-    float theta, inv_theta, tau, theta_lambda;
-    int H, W, ld, nw, ntx, th;
-    uint32_t seed;   // per-launch seed of the stochastic rounding of 16-bit stores
-};
-
-__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
-
-// p' = (p + tau g) / (1 + tau |g|); |g| through the hardware reciprocal square
-// root and the quotient through the fast divide (a few ulp; the iteration is
-// checked against the FP64 oracle to 1e-4).
-__device__ __forceinline__ void chambolle_update(float p1, float p2, float g1, float g2, float tau,
-                                                 float& q1, float& q2) {
-    const float s = fmaf(g1, g1, g2 * g2);
-    const float nrm = s > 0.f ? s * rsqrtf(s) : 0.f;
-    const float r = __fdividef(1.0f, fmaf(tau, nrm, 1.0f));
-    q1 = fmaf(tau, g1, p1) * r;
-    q2 = fmaf(tau, g2, p2) * r;
-}
 
 // ============================================================ dense stencil
 
@@ -244,8 +224,6 @@ __global__ void k_final_dense(IterParams P, const WsHeader* __restrict__ h, int 
 
 // ========================================================== compact stencil
 
-constexpr int kCompactThreads = 256;
-
 // neighbour slots of the table and the codes for pixels that are not in RD
 enum { NB_UP = 0, NB_LEFT = 1, NB_DOWN = 2, NB_RIGHT = 3, NB_DOWNLEFT = 4, NB_UPRIGHT = 5, NB_COUNT = 6 };
 constexpr int kNbBg = -1;    // fixed background: p = 0, v = 0
@@ -420,39 +398,6 @@ __device__ __forceinline__ float w_fixed(float p_in_1, float p_in_2, int code, f
 //   (check iterations) block 0 sums the partials in a fixed order and raises
 //   the done flag, which every block reads after the next barrier.
 constexpr int kPersistThreads = 512;
-
-// Grid-wide barrier (arrival counter + generation), with a bounded wait:
-// thread 0 of each block arrives with a release add and polls the generation
-// with acquire loads until it passes `gen` (the block's count of barriers
-// passed, which every block tracks in a register); the last arrival resets
-// the counter and releases the generation.  Returns false after recording
-// SEG_ERR_TIMEOUT (and raising the done flag) if the others do not arrive
-// within ~1 s.
-__device__ __forceinline__ bool grid_sync(WsHeader* h, unsigned nblocks, unsigned& gen) {
-    __shared__ int s_ok;
-    __syncthreads();
-    ++gen;
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        if (atom_add_release_gpu(&h->bar_count, 1u) == nblocks - 1) {
-            h->bar_count = 0u;
-            atom_add_release_gpu(&h->bar_gen, 1u);
-        } else {
-            const long long t0 = clock64();
-            while ((int)(ld_acquire_gpu(&h->bar_gen) - gen) < 0) {
-                if (clock64() - t0 > kWaitCycles) {
-                    record_status(h, SEG_ERR_TIMEOUT);
-                    h->done = 1;
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 // Dual step on the RD pixels [a0, a1) (two per thread in flight):
 //   g = (w(x+e1) - w(x), w(x+e2) - w(x))   (a component is 0 across the
@@ -686,6 +631,8 @@ __global__ void k_solve_begin(WsHeader* h) {
     h->last_check = 0;
     h->du = 0.0;
     h->dv = 0.0;
+    for (int k = 0; k < 4; ++k) h->tb_ticket[k] = 0;
+    h->tb_buf = 0;
 }
 
 // Section 4 stopping test after iteration l: sums the n partial pairs in a
@@ -731,23 +678,6 @@ __global__ void k_solve_end(const WsHeader* __restrict__ h, const int32_t* __res
 
 // ================================================================== host
 
-static uint32_t mix32_host(uint32_t x) {
-    x ^= x >> 16; x *= 0x7feb352du;
-    x ^= x >> 15; x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
-}
-
-static int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
 
 template <typename K>
 static int grid_for(K kernel, int threads, int64_t max_blocks) {
@@ -933,12 +863,13 @@ static seg_status check_params(const seg_params* prm) {
         return fail(SEG_ERR_INVALID_ARG, "iters >= 0, n_inner >= 1, check_every >= 1 required");
     if (!(prm->theta > 0) || !(prm->tau > 0) || !std::isfinite(prm->lambda) || std::isnan(prm->tol))
         return fail(SEG_ERR_INVALID_ARG, "theta, tau must be > 0 and lambda finite");
-    if (prm->mode != SEG_MODE_DENSE && prm->mode != SEG_MODE_COMPACT)
+    if (prm->mode != SEG_MODE_DENSE && prm->mode != SEG_MODE_COMPACT && prm->mode != SEG_MODE_TILED)
         return fail(SEG_ERR_INVALID_ARG, "unknown mode %d", prm->mode);
     if (prm->storage < 0 || prm->storage > 2)
         return fail(SEG_ERR_INVALID_ARG, "unknown storage %d", prm->storage);
-    if (prm->mode == SEG_MODE_DENSE && prm->storage != SEG_STORE_F32)
+    if (prm->mode != SEG_MODE_COMPACT && prm->storage != SEG_STORE_F32)
         return fail(SEG_ERR_INVALID_ARG, "16-bit storage needs SEG_MODE_COMPACT");
+    if (prm->sweep < 0) return fail(SEG_ERR_INVALID_ARG, "sweep must be >= 0");
     return SEG_OK;
 }
 
@@ -1180,6 +1111,7 @@ using namespace seg;
 
 extern "C" size_t seg_state_bytes(int H, int ld, int64_t capacity, int mode, int storage) {
     if (mode == SEG_MODE_DENSE) return 6 * 4 * (size_t)std::max(H, 0) * (size_t)std::max(ld, 0) + 256;
+    if (mode == SEG_MODE_TILED) return tiled_state_bytes(H, ld);
     size_t sz = storage_size(storage);
     return kCompactArrays * 256 + (size_t)compact_stride(capacity) * compact_per_element(sz);
 }
@@ -1198,6 +1130,11 @@ extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint
     if (ld % 32) return fail(SEG_ERR_ALIGN, "ld=%d is not a multiple of 32", ld);
     if (reinterpret_cast<uintptr_t>(state) % 16)
         return fail(SEG_ERR_ALIGN, "state buffer not 16-byte aligned");
+    if (prm->mode == SEG_MODE_TILED) {
+        int nwin = 0;
+        SEG_TRY(tiled_geometry(H, W, prm->sweep, prm->n_inner, &nwin));
+        if (reinterpret_cast<uintptr_t>(f) % 16) return fail(SEG_ERR_ALIGN, "f not 16-byte aligned");
+    }
     WsLayout L = ws_layout(H, W, prm->tile_h);
     SEG_TRY(check_ws(ws, ws_bytes, L));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1207,18 +1144,22 @@ extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint
 
     k_solve_begin<<<1, 1, 0, s>>>(h);
     SEG_LAUNCHED("k_solve_begin");
-    if (prm->mode == SEG_MODE_DENSE) {
-        if (state_bytes < seg_state_bytes(H, ld, 0, SEG_MODE_DENSE, SEG_STORE_F32))
-            return fail(SEG_ERR_CAPACITY, "dense state needs %zu bytes, got %zu",
-                        seg_state_bytes(H, ld, 0, SEG_MODE_DENSE, SEG_STORE_F32), state_bytes);
+    if (prm->mode == SEG_MODE_DENSE || prm->mode == SEG_MODE_TILED) {
+        const size_t need = seg_state_bytes(H, ld, 0, prm->mode, SEG_STORE_F32);
+        if (state_bytes < need)
+            return fail(SEG_ERR_CAPACITY, "dense state needs %zu bytes, got %zu", need, state_bytes);
         float* st = static_cast<float*>(state);
         int64_t n = (int64_t)H * W;
-        int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+        int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
         k_init_dense<<<blocks, 256, 0, s>>>(P, act, fgm, f, prm->warm_start, p1, p2, v, u, st);
         SEG_LAUNCHED("k_init_dense");
-        SEG_TRY(run_dense(P, prm, counts, act, f, u, st, partials, h, s));
-        k_final_dense<<<blocks, 256, 0, s>>>(P, h, prm->iters, prm->n_inner, st, v, p1, p2);
-        SEG_LAUNCHED("k_final_dense");
+        if (prm->mode == SEG_MODE_TILED) {
+            SEG_TRY(run_tiled(P, prm, act, f, u, v, p1, p2, st, partials, L.npartials, h, s));
+        } else {
+            SEG_TRY(run_dense(P, prm, counts, act, f, u, st, partials, h, s));
+            k_final_dense<<<blocks, 256, 0, s>>>(P, h, prm->iters, prm->n_inner, st, v, p1, p2);
+            SEG_LAUNCHED("k_final_dense");
+        }
     } else {
         BatchDesc B{};
         B.n = 1;

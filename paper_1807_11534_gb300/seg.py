@@ -31,6 +31,8 @@ SEG_ERR_WORKSPACE = 7
 
 SEG_MODE_DENSE = 0
 SEG_MODE_COMPACT = 1
+SEG_MODE_TILED = 2
+_MODE_BY_NAME = {"dense": SEG_MODE_DENSE, "compact": SEG_MODE_COMPACT, "tiled": SEG_MODE_TILED}
 SEG_STORE_F32 = 0
 SEG_STORE_BF16 = 1
 SEG_STORE_F16 = 2
@@ -51,7 +53,7 @@ class seg_params(ctypes.Structure):
                 ("iters", ctypes.c_int), ("n_inner", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("warm_start", ctypes.c_int),
                 ("mode", ctypes.c_int), ("storage", ctypes.c_int),
-                ("tile_h", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("tile_h", ctypes.c_int), ("sweep", ctypes.c_int)]
 
 
 class seg_image(ctypes.Structure):
@@ -337,17 +339,20 @@ def build_domain(f, delta=math.inf, q=-1.0, tile_h=16, ws=None, with_pixels=True
     return dom
 
 
+def _mode(mode):
+    return _MODE_BY_NAME[mode] if isinstance(mode, str) else int(mode)
+
+
 def make_params(lam, theta=0.2, tau=0.125, iters=100, tol=0.0, n_inner=1, check_every=10,
-                warm_start=False, mode="compact", storage="f32", tile_h=16) -> seg_params:
+                warm_start=False, mode="compact", storage="f32", tile_h=16, sweep=0) -> seg_params:
     return seg_params(float(lam), float(theta), float(tau), float(tol), int(iters), int(n_inner),
-                      int(check_every), int(bool(warm_start)),
-                      SEG_MODE_COMPACT if mode == "compact" else SEG_MODE_DENSE,
+                      int(check_every), int(bool(warm_start)), _mode(mode),
                       _STORE_BY_NAME[storage] if isinstance(storage, str) else int(storage),
-                      int(tile_h), 0)
+                      int(tile_h), int(sweep))
 
 
 def state_buffer(H, W, capacity, mode="compact", storage="f32", device="cuda"):
-    m = SEG_MODE_COMPACT if mode == "compact" else SEG_MODE_DENSE
+    m = _mode(mode)
     s = _STORE_BY_NAME[storage] if isinstance(storage, str) else int(storage)
     nb = seg_state_bytes(H, pitch(W), int(capacity), m, s)
     return torch.empty((nb + 15) // 16 * 16, dtype=torch.uint8, device=device)
@@ -409,11 +414,11 @@ class Solver:
         return self.dom
 
     def solve(self, lam, theta=0.2, tau=0.125, iters=100, tol=0.0, n_inner=1, check_every=10,
-              warm_start=False, f=None):
+              warm_start=False, f=None, sweep=0):
         f = self.f if f is None else f
         d = self.dom
         prm = make_params(lam, theta, tau, iters, tol, n_inner, check_every, warm_start,
-                          self.mode, self.storage, self.tile_h)
+                          self.mode, self.storage, self.tile_h, sweep)
         seg_solve(f, d.act, d.fg, d.wstart, d.tiles, d.counts, prm, self.u, self.v, self.p1,
                   self.p2, self.state, self.stats, self.ws, self.stream)
         return self.stats

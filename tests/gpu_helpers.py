@@ -27,7 +27,7 @@ def bits_to_mask(words, W):
 
 
 def run_gpu(f32, delta=math.inf, q=-1.0, lam=1.0, theta=0.2, tau=0.125, iters=100, tol=0.0,
-            n_inner=1, check_every=10, mode="compact", storage="f32", tile_h=16, warm=None):
+            n_inner=1, check_every=10, mode="compact", storage="f32", tile_h=16, warm=None, sweep=0):
     """Domain + solve for a float32 fitting term; returns a dict of numpy
     outputs (u, v, p1, p2 as float64) and the solver."""
     seg = seg_mod()
@@ -38,7 +38,8 @@ def run_gpu(f32, delta=math.inf, q=-1.0, lam=1.0, theta=0.2, tau=0.125, iters=10
     if warm is not None:
         for name in ("u", "v", "p1", "p2"):
             getattr(S, name)[:, :W].copy_(torch.from_numpy(np.asarray(getattr(warm, name), np.float32)))
-    S.solve(lam, theta, tau, iters, tol, n_inner, check_every, warm_start=warm is not None)
+    S.solve(lam, theta, tau, iters, tol, n_inner, check_every, warm_start=warm is not None,
+            sweep=sweep)
     torch.cuda.synchronize()
     S.check_status()
     out = {k: seg.download(getattr(S, k)).astype(np.float64) for k in ("u", "v", "p1", "p2")}

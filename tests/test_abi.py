@@ -42,6 +42,9 @@ def test_sizes(lib):
     big = seg.seg_workspace_bytes(4096, 4096, 4096, 4)
     assert 0 < small < big
     assert seg.seg_state_bytes(100, 128, 0, seg.SEG_MODE_DENSE, 0) >= 6 * 4 * 100 * 128
+    dense = seg.seg_state_bytes(100, 128, 0, seg.SEG_MODE_DENSE, 0)
+    tiled = seg.seg_state_bytes(100, 128, 0, seg.SEG_MODE_TILED, 0)
+    assert dense < tiled < dense + 8 * 100 * 128 + 65536
     s32 = seg.seg_state_bytes(100, 128, 5000, seg.SEG_MODE_COMPACT, seg.SEG_STORE_F32)
     s16 = seg.seg_state_bytes(100, 128, 5000, seg.SEG_MODE_COMPACT, seg.SEG_STORE_BF16)
     assert s32 >= 5000 * (6 * 4 + 8) and s16 >= 5000 * (6 * 2 + 8) and s16 < s32
@@ -97,6 +100,11 @@ def test_host_side_argument_errors(lib):
     p3 = seg.make_params(1.0, iters=10, tile_h=16, mode="dense", storage="bf16")
     sargs[9] = ctypes.byref(p3)
     assert lib.seg_solve(*sargs) == seg.SEG_ERR_INVALID_ARG
+    # temporally blocked mode: float32 only, sweep * n_inner <= 8, sweep >= 0
+    for kw in (dict(storage="f16"), dict(sweep=9), dict(sweep=3, n_inner=3), dict(sweep=-1)):
+        p4 = seg.make_params(1.0, iters=10, tile_h=16, mode="tiled", **kw)
+        sargs[9] = ctypes.byref(p4)
+        assert lib.seg_solve(*sargs) == seg.SEG_ERR_INVALID_ARG, kw
     sargs[9] = None
     assert lib.seg_solve(*sargs) == seg.SEG_ERR_INVALID_ARG
     # energy / errors

@@ -160,7 +160,7 @@ def _problem(shape, seed=0):
     return P
 
 
-@pytest.mark.parametrize("mode", ["dense", "compact"])
+@pytest.mark.parametrize("mode", ["dense", "compact", "tiled"])
 @pytest.mark.parametrize("delta", [0.05, 0.15, 0.25, math.inf])
 @pytest.mark.parametrize("shape,tile_h", [((67, 131), 8), ((256, 256), 16), ((90, 45), 32),
                                           ((33, 200), 4), ((300, 29), 8), ((1, 97), 4)])
@@ -176,7 +176,7 @@ def test_solve_matches_oracle(orc, mode, delta, shape, tile_h):
     np.testing.assert_allclose(out["stats"][1:3], st.hist[-1], rtol=2e-3, atol=1e-5)
 
 
-@pytest.mark.parametrize("mode", ["dense", "compact"])
+@pytest.mark.parametrize("mode", ["dense", "compact", "tiled"])
 def test_solve_stops_like_the_oracle(orc, mode):
     P = _problem((96, 160), seed=4)
     _, f = orc.fitting(P.z, 0.3, 0.7)
@@ -195,12 +195,13 @@ def test_solve_stops_like_the_oracle(orc, mode):
     assert l_o < 2000 and crit[-1] <= tol
 
 
-@pytest.mark.parametrize("mode", ["dense", "compact"])
+@pytest.mark.parametrize("mode", ["dense", "compact", "tiled"])
 def test_inner_sweeps_and_warm_start(orc, mode):
     P = _problem((70, 100), seed=6)
     _, f = orc.fitting(P.z, 0.3, 0.7)
     reg = orc.domain(f, 0.2)
-    out = run_gpu(f, delta=0.2, lam=2.0, iters=30, n_inner=3, mode=mode, tile_h=8)
+    out = run_gpu(f, delta=0.2, lam=2.0, iters=30, n_inner=3, mode=mode, tile_h=8,
+                  sweep=2 if mode == "tiled" else 0)
     st = orc.solve(f, reg, 2.0, iters=30, n_inner=3)
     _cmp_state(out, st, TOL_U32, TOL_P32)
     # continue from the oracle state on the GPU: 25 more iterations
@@ -209,10 +210,41 @@ def test_inner_sweeps_and_warm_start(orc, mode):
     _cmp_state(out2, st2, TOL_U32, TOL_P32)
 
 
+@pytest.mark.parametrize("sweep,n_inner,check_every", [(1, 1, 7), (2, 1, 5), (3, 2, 10), (4, 1, 6),
+                                                      (8, 1, 8), (5, 1, 100)])
+@pytest.mark.parametrize("shape", [(200, 301), (61, 69), (123, 57)])
+def test_tiled_sweeps_and_windows(orc, sweep, n_inner, check_every, shape):
+    """Temporally blocked solve: several window rows and columns with ragged
+    last windows, sweeps of 1 to 8 iterations, inner fixed-point sweeps, and
+    stopping tests that split sweeps (check_every not a multiple of sweep)."""
+    P = _problem(shape, seed=sum(shape))
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    iters = 47
+    for delta in (0.2, math.inf):
+        out = run_gpu(f, delta=delta, lam=1.2, iters=iters, n_inner=n_inner,
+                      check_every=check_every, mode="tiled", sweep=sweep)
+        st = orc.solve(f, orc.domain(f, delta), 1.2, 0.2, 0.125, iters, n_inner=n_inner)
+        _cmp_state(out, st, TOL_U32, TOL_P32)
+        assert out["stats"][0] == iters
+        np.testing.assert_allclose(out["stats"][1:3], st.hist[-1], rtol=2e-3, atol=1e-5)
+
+
+def test_tiled_rejects_bad_sweeps():
+    seg = seg_mod()
+    f = np.random.default_rng(3).normal(0, 0.2, (40, 40)).astype(np.float32)
+    S = seg.Solver(40, 40, mode="tiled")
+    S.f[:, :40].copy_(torch.from_numpy(f))
+    S.domain(delta=0.2)
+    for sweep, n_inner in ((9, 1), (3, 3)):
+        with pytest.raises(seg.SegError) as e:
+            S.solve(1.0, iters=5, n_inner=n_inner, sweep=sweep)
+        assert e.value.status == seg.SEG_ERR_INVALID_ARG
+
+
 def test_empty_and_full_domain_edges(orc):
     P = _problem((50, 70), seed=7)
     _, f = orc.fitting(P.z, 0.3, 0.7)
-    for mode in ("dense", "compact"):
+    for mode in ("dense", "compact", "tiled"):
         out = run_gpu(f, delta=0.0, iters=10, tol=1e-9, check_every=1, mode=mode)
         h = (f < 0).astype(np.float64)
         np.testing.assert_array_equal(out["u"], h)
@@ -223,7 +255,7 @@ def test_empty_and_full_domain_edges(orc):
     for shape in ((1, 40), (40, 1)):
         rng = np.random.default_rng(1)
         f1 = rng.normal(0, 0.3, shape).astype(np.float32)
-        for mode in ("dense", "compact"):
+        for mode in ("dense", "compact", "tiled"):
             out = run_gpu(f1, iters=50, mode=mode, tile_h=4)
             st = orc.solve(f1, orc.domain(f1, math.inf), 1.0, iters=50)
             _cmp_state(out, st, TOL_U32, TOL_P32)
@@ -295,7 +327,7 @@ def _crop_check(orc, f_full, out_u, delta, lam, K, centres):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("mode", ["compact", "dense"])
+@pytest.mark.parametrize("mode", ["compact", "dense", "tiled"])
 def test_full_size_2048_ds_sampled(orc, mode):
     """2048x2048 distance-selective workload in the benchmark's launch
     configuration: K iterations on the GPU, then the oracle on crops of
