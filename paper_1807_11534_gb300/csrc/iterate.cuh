@@ -30,31 +30,32 @@ __device__ __forceinline__ void chambolle_update(float p1, float p2, float g1, f
 
 // ------------------------------------------------ persistent kernels
 
-// Grid-wide barrier (arrival counter + generation), with a bounded wait:
-// thread 0 of each block arrives with a release add and polls the generation
-// with acquire loads until it passes `gen` (the block's count of barriers
-// passed, which every block tracks in a register); the last arrival resets
-// the counter and releases the generation.  Returns false after recording
+// Grid-wide barrier on a monotonic arrival counter, with a bounded wait:
+// thread 0 of each block adds 1 with a release reduction (no round trip) and
+// polls the counter with acquire loads until it reaches nblocks x `gen` (the
+// block's count of barriers passed, tracked in a register; the counter is
+// reset before each persistent launch).  Returns false after recording
 // SEG_ERR_TIMEOUT (and raising the done flag) if the others do not arrive
 // within ~1 s.
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_sync(WsHeader* h, unsigned nblocks, unsigned& gen) {
     __shared__ int s_ok;
     __syncthreads();
     ++gen;
     if (threadIdx.x == 0) {
         int ok = 1;
-        if (atom_add_release_gpu(&h->bar_count, 1u) == nblocks - 1) {
-            h->bar_count = 0u;
-            atom_add_release_gpu(&h->bar_gen, 1u);
-        } else {
-            const long long t0 = clock64();
-            while ((int)(ld_acquire_gpu(&h->bar_gen) - gen) < 0) {
-                if (clock64() - t0 > kWaitCycles) {
-                    record_status(h, SEG_ERR_TIMEOUT);
-                    h->done = 1;
-                    ok = 0;
-                    break;
-                }
+        red_add_release_gpu(&h->bar_count, 1u);
+        const unsigned target = nblocks * gen;
+        const long long t0 = clock64();
+        while ((int)(ld_acquire_gpu(&h->bar_count) - target) < 0) {
+            if (clock64() - t0 > kWaitCycles) {
+                record_status(h, SEG_ERR_TIMEOUT);
+                h->done = 1;
+                ok = 0;
+                break;
             }
         }
         s_ok = ok;

@@ -69,10 +69,9 @@ struct WsHeader {
     // the ping-pong buffer that holds the final state
     int tb_ticket[4];
     int tb_buf;
-    // grid barrier of the persistent solver: arrival counter and generation,
-    // on separate cache lines so that polling does not contend with arrivals
+    // grid barrier of the persistent solvers: monotonic arrival counter, on
+    // its own cache line
     alignas(128) unsigned bar_count;
-    alignas(64) unsigned bar_gen;
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
@@ -180,8 +179,13 @@ template <typename T> struct Store;
 template <> struct Store<float> {
     static constexpr float vbias = 0.0f;
     static __device__ __forceinline__ float ld(const float* p, int64_t i) { return __ldg(p + i); }
+    // coherent load (L2) of state that other blocks write during the kernel
+    static __device__ __forceinline__ float ldc(const float* p, int64_t i) { return __ldcg(p + i); }
     static __device__ __forceinline__ float ld_rw(const float* p, int64_t i) { return p[i]; }
     static __device__ __forceinline__ void st(float* p, int64_t i, float x) { p[i] = x; }
+    // x rounded to the storage type (stochastically for 16-bit types, with
+    // the random word r), as a float
+    static __device__ __forceinline__ float sr(float x, uint32_t) { return x; }
     // stores x (stochastically rounded for 16-bit types) and returns the
     // value stored
     static __device__ __forceinline__ float st_sr(float* p, int64_t i, float x, uint32_t) { p[i] = x; return x; }
@@ -189,15 +193,22 @@ template <> struct Store<float> {
 template <> struct Store<__nv_bfloat16> {
     static constexpr float vbias = 0.5f;
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(__ldg(p + i)); }
+    static __device__ __forceinline__ float ldc(const __nv_bfloat16* p, int64_t i) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p) + i)));
+    }
     static __device__ __forceinline__ float ld_rw(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float x) { p[i] = __float2bfloat16_rn(x); }
     // bf16 keeps the top 16 bits of the float: adding a uniform 16-bit word to
     // the discarded bits before truncating rounds up with probability equal
     // to the discarded fraction (finite values; |x| <= 1 here)
-    static __device__ __forceinline__ float st_sr(__nv_bfloat16* p, int64_t i, float x, uint32_t r) {
+    static __device__ __forceinline__ __nv_bfloat16 sr_t(float x, uint32_t r) {
         uint32_t b = __float_as_uint(x);
         b += r & 0xffffu;
-        const __nv_bfloat16 y = __ushort_as_bfloat16((unsigned short)(b >> 16));
+        return __ushort_as_bfloat16((unsigned short)(b >> 16));
+    }
+    static __device__ __forceinline__ float sr(float x, uint32_t r) { return __bfloat162float(sr_t(x, r)); }
+    static __device__ __forceinline__ float st_sr(__nv_bfloat16* p, int64_t i, float x, uint32_t r) {
+        const __nv_bfloat16 y = sr_t(x, r);
         p[i] = y;
         return __bfloat162float(y);
     }
@@ -205,17 +216,25 @@ template <> struct Store<__nv_bfloat16> {
 template <> struct Store<__half> {
     static constexpr float vbias = 0.5f;
     static __device__ __forceinline__ float ld(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
+    static __device__ __forceinline__ float ldc(const __half* p, int64_t i) {
+        return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p) + i)));
+    }
     static __device__ __forceinline__ float ld_rw(const __half* p, int64_t i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void st(__half* p, int64_t i, float x) { p[i] = __float2half_rn(x); }
     // round to one of the two neighbouring halves with probabilities given by
     // the distance to each
-    static __device__ __forceinline__ float st_sr(__half* p, int64_t i, float x, uint32_t r) {
+    static __device__ __forceinline__ __half sr_t(float x, uint32_t r) {
         __half lo = __float2half_rd(x), hi = __float2half_ru(x);
         float fl = __half2float(lo), fh = __half2float(hi);
         float u = (float)(r >> 8) * (1.0f / 16777216.0f);
         const bool up = fh > fl && u * (fh - fl) < x - fl;
-        p[i] = up ? hi : lo;
-        return up ? fh : fl;
+        return up ? hi : lo;
+    }
+    static __device__ __forceinline__ float sr(float x, uint32_t r) { return __half2float(sr_t(x, r)); }
+    static __device__ __forceinline__ float st_sr(__half* p, int64_t i, float x, uint32_t r) {
+        const __half y = sr_t(x, r);
+        p[i] = y;
+        return __half2float(y);
     }
 };
 

@@ -225,7 +225,10 @@ __global__ void k_final_dense(IterParams P, const WsHeader* __restrict__ h, int 
 // ========================================================== compact stencil
 
 // neighbour slots of the table and the codes for pixels that are not in RD
-enum { NB_UP = 0, NB_LEFT = 1, NB_DOWN = 2, NB_RIGHT = 3, NB_DOWNLEFT = 4, NB_UPRIGHT = 5, NB_COUNT = 6 };
+// (NB_UUR = (i-2, j+1) and NB_LLD = (i+1, j-2) are the neighbours of x - e1
+// and x - e2 that the fused iteration needs when it redoes their dual step)
+enum { NB_UP = 0, NB_LEFT = 1, NB_DOWN = 2, NB_RIGHT = 3, NB_DOWNLEFT = 4, NB_UPRIGHT = 5, NB_UUR = 6,
+       NB_LLD = 7, NB_COUNT = 8 };
 constexpr int kNbBg = -1;    // fixed background: p = 0, v = 0
 constexpr int kNbFg = -2;    // fixed foreground: p = 0, v = 1
 constexpr int kNbOut = -3;   // outside the image (the gradient there is 0)
@@ -236,6 +239,7 @@ struct CompactState {
     float* u;
     float* w;        // div p - v/theta of the current iterate
     int32_t* nb;     // [NB_COUNT][stride]
+    float* w2;       // the other w buffer of the fused iteration
     int64_t cap;
     int64_t stride;
 };
@@ -366,6 +370,8 @@ __global__ void k_compact_gather(IterParams P, BatchDesc B, const int32_t* __res
     nb[NB_RIGHT * st + idx] = code(i, j + 1);
     nb[NB_DOWNLEFT * st + idx] = code(i + 1, j - 1);
     nb[NB_UPRIGHT * st + idx] = code(i - 1, j + 1);
+    nb[NB_UUR * st + idx] = code(i - 2, j + 1);
+    nb[NB_LLD * st + idx] = code(i + 1, j - 2);
 }
 
 template <typename T>
@@ -375,11 +381,12 @@ __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return _
 template <>
 __device__ __forceinline__ float to_f<__half>(__half x) { return __half2float(x); }
 
+// state at a neighbour (0 where it is fixed or outside): coherent loads, the
+// state is rewritten by other blocks between the phases of a persistent solve
 template <typename T>
-__device__ __forceinline__ float nb_ld(const T* __restrict__ X, int n) {
-    return n >= 0 ? Store<T>::ld(X, n) : 0.f;
+__device__ __forceinline__ float nb_ld(const T* X, int n) {
+    return n >= 0 ? Store<T>::ldc(X, n) : 0.f;
 }
-__device__ __forceinline__ float nb_vfix(int n) { return n == kNbFg ? 1.f : 0.f; }
 
 // w at a fixed (non-RD) neighbour y: p(y) = 0, so div p(y) is minus the two
 // p components that flow into y, and v(y) is its fixed value.
@@ -397,28 +404,58 @@ __device__ __forceinline__ float w_fixed(float p_in_1, float p_in_2, int code, f
 //   primal phase u', v', w', stop-test partials          -> barrier
 //   (check iterations) block 0 sums the partials in a fixed order and raises
 //   the done flag, which every block reads after the next barrier.
+// With one fixed-point sweep per iteration (n_inner = 1) the two phases are
+// fused into one, with one barrier per iteration: the thread of x also redoes
+// the dual steps of x - e1 and x - e2 (same inputs, same arithmetic, same
+// rounding as their owners), which is all the v-step of x needs, and w is
+// ping-ponged.  The iterates are bit-identical to the two-phase ones.
+// Only the owner reads the neighbour-table rows and v of a pixel, so when a
+// block's range fits, those are copied into its shared memory once per solve:
+// every neighbour load then depends on a shared-memory read instead of an L2
+// read, and v is written back at the end.
 constexpr int kPersistThreads = 512;
+// dynamic shared memory of the persistent solver: one or two blocks per SM
+constexpr size_t compact_smem(int nt) { return nt == 1024 ? 220 * 1024 : 110 * 1024; }
+constexpr int kCompactThreads = 1024;   // one block per SM
+constexpr int kCompactUnroll = 4;       // pixels per thread in flight in the two-phase iteration
+constexpr int kFusePerThread = 3;       // fused iteration up to this many pixels per thread
 
-// Dual step on the RD pixels [a0, a1) (two per thread in flight):
+// Own-pixel arrays (neighbour-table rows, v) of the pixels a block updates:
+// SH, copies in shared memory indexed from the block's first pixel a0; else
+// the global arrays (a0 = 0).  theta lambda f is read from its global array.
+template <typename T, bool SH>
+struct Own {
+    const int32_t* nb;   // [NB_COUNT][ns]
+    int64_t ns;
+    T* v;
+    const float* f;      // global, indexed by a
+    int a0;
+    __device__ __forceinline__ int nbr(int k, int a) const {
+        const int64_t i = (int64_t)k * ns + (a - a0);
+        return SH ? nb[i] : __ldg(nb + i);
+    }
+    __device__ __forceinline__ float fv(int a) const { return __ldg(f + a); }
+    __device__ __forceinline__ int vi(int a) const { return a - a0; }
+};
+
+// Dual step on one RD pixel:
 //   g = (w(x+e1) - w(x), w(x+e2) - w(x))   (a component is 0 across the
 //       image border), p'(x) = (p(x) + tau g) / (1 + tau |g|),
 // with w = div p - v/theta taken from the primal step's output where the
 // neighbour is in RD, and formed from p(x) and p(x+e1-e2) (resp. p(x+e2-e1))
 // where it is fixed.  p1 vanishes on the last row and p2 on the last column
 // (their gradient component is 0 there and they start at 0).
-template <typename T>
-__device__ __forceinline__ void dual_one(const IterParams& P, int a, const int32_t* __restrict__ nb,
-                                         int64_t stride, const T* __restrict__ P1i,
-                                         const T* __restrict__ P2i, const float* __restrict__ Wc,
-                                         T* __restrict__ P1o, T* __restrict__ P2o, uint32_t seed) {
-    const int n_down = __ldg(nb + NB_DOWN * stride + a);
-    const int n_right = __ldg(nb + NB_RIGHT * stride + a);
-    const int n_dl = __ldg(nb + NB_DOWNLEFT * stride + a);
-    const int n_ur = __ldg(nb + NB_UPRIGHT * stride + a);
-    const float p1 = Store<T>::ld(P1i, a), p2 = Store<T>::ld(P2i, a);
-    const float w0 = __ldg(Wc + a);
-    const float wd = n_down >= 0 ? __ldg(Wc + n_down) : 0.f;
-    const float wr = n_right >= 0 ? __ldg(Wc + n_right) : 0.f;
+template <typename T, bool SH>
+__device__ __forceinline__ void dual_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1i,
+                                         const T* P2i, const float* Wc, T* P1o, T* P2o, uint32_t seed) {
+    const int n_down = O.nbr(NB_DOWN, a);
+    const int n_right = O.nbr(NB_RIGHT, a);
+    const int n_dl = O.nbr(NB_DOWNLEFT, a);
+    const int n_ur = O.nbr(NB_UPRIGHT, a);
+    const float p1 = Store<T>::ldc(P1i, a), p2 = Store<T>::ldc(P2i, a);
+    const float w0 = __ldcg(Wc + a);
+    const float wd = n_down >= 0 ? __ldcg(Wc + n_down) : 0.f;
+    const float wr = n_right >= 0 ? __ldcg(Wc + n_right) : 0.f;
     const float p2dl = nb_ld(P2i, n_dl);
     const float p1ur = nb_ld(P1i, n_ur);
     float g1 = 0.f, g2 = 0.f;
@@ -435,17 +472,14 @@ __device__ __forceinline__ void dual_one(const IterParams& P, int a, const int32
 // lambda f) (v updated in place), w' = div p' - v'/theta for the next dual
 // step.  wonly: just w = div p' - v/theta (between extra fixed-point sweeps,
 // or for a warm start).
-template <typename T>
-__device__ __forceinline__ void primal_one(const IterParams& P, int a, const int32_t* __restrict__ nb,
-                                           int64_t stride, const T* __restrict__ P1n,
-                                           const T* __restrict__ P2n, T* __restrict__ V,
-                                           const float* __restrict__ F, float* __restrict__ U,
-                                           float* __restrict__ Wc, bool wonly, bool check, bool write_u,
-                                           uint32_t seed, float& du2, float& dv2) {
-    const int n_up = __ldg(nb + NB_UP * stride + a);
-    const int n_left = __ldg(nb + NB_LEFT * stride + a);
-    const float q1 = Store<T>::ld(P1n, a), q2 = Store<T>::ld(P2n, a);
-    const float vv = Store<T>::ld_rw(V, a) + Store<T>::vbias;
+template <typename T, bool SH>
+__device__ __forceinline__ void primal_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1n,
+                                           const T* P2n, float* U, float* Wc, bool wonly, bool check,
+                                           bool write_u, uint32_t seed, float& du2, float& dv2) {
+    const int n_up = O.nbr(NB_UP, a);
+    const int n_left = O.nbr(NB_LEFT, a);
+    const float q1 = Store<T>::ldc(P1n, a), q2 = Store<T>::ldc(P2n, a);
+    const float vv = Store<T>::ld_rw(O.v, O.vi(a)) + Store<T>::vbias;
     const float q1u = nb_ld(P1n, n_up), q2l = nb_ld(P2n, n_left);
     const float div = (q1 - q1u) + (q2 - q2l);
     if (wonly) {
@@ -453,8 +487,8 @@ __device__ __forceinline__ void primal_one(const IterParams& P, int a, const int
         return;
     }
     const float un = fmaf(-P.theta, div, vv);
-    const float vn = clamp01(un - __ldg(F + a));   // F = theta lambda f
-    const float vs = Store<T>::st_sr(V, a, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
+    const float vn = clamp01(un - O.fv(a));   // F = theta lambda f
+    const float vs = Store<T>::st_sr(O.v, O.vi(a), vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
                      Store<T>::vbias;
     Wc[a] = div - vs * P.inv_theta;
     if (check) {
@@ -465,22 +499,105 @@ __device__ __forceinline__ void primal_one(const IterParams& P, int a, const int
     if (write_u) U[a] = un;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kPersistThreads)
-k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
-                const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
-                T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
-                float* Wc, double* partials, WsHeader* h, float* ckpt, int ckpt_every) {
-    __shared__ double s_red[2 * (kPersistThreads / 32)];
-    // set before the launch (capacity overflow): the same for every block
-    if (*(volatile int*)&h->done) return;
+// One fused iteration at one RD pixel (n_inner = 1): p'(x) as the dual step
+// computes it, p1'(x - e1) and p2'(x - e2) as the dual steps of x - e1 and
+// x - e2 compute them (their neighbours below / right are x, x - e1 + e2 and
+// x + e1 - e2, x; a fixed one of those needs p at (i-2, j+1) resp.
+// (i+1, j-2)), each rounded as its owner stores it; then the primal step of
+// x.  Reads p, w of the current iterate (P1i, P2i, Wi), writes p', w' to the
+// other buffers and v in place.
+template <typename T, bool SH>
+__device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1i,
+                                          const T* P2i, const float* Wi, T* P1o, T* P2o, float* Wo, float* U,
+                                          bool check, bool write_u, uint32_t seed_d, uint32_t seed_p, float& du2,
+                                          float& dv2) {
+    const int n_up = O.nbr(NB_UP, a), n_left = O.nbr(NB_LEFT, a);
+    const int n_down = O.nbr(NB_DOWN, a), n_right = O.nbr(NB_RIGHT, a);
+    const int n_dl = O.nbr(NB_DOWNLEFT, a), n_ur = O.nbr(NB_UPRIGHT, a);
+    const int n_uur = n_up >= 0 ? O.nbr(NB_UUR, a) : kNbOut;
+    const int n_lld = n_left >= 0 ? O.nbr(NB_LLD, a) : kNbOut;
+    // every load of the step, independent of one another
+    const float p1 = Store<T>::ldc(P1i, a), p2 = Store<T>::ldc(P2i, a);
+    const float w0 = __ldcg(Wi + a);
+    const float wd = n_down >= 0 ? __ldcg(Wi + n_down) : 0.f;
+    const float wr = n_right >= 0 ? __ldcg(Wi + n_right) : 0.f;
+    const float p2dl = nb_ld(P2i, n_dl), p1ur = nb_ld(P1i, n_ur);
+    const float p1U = nb_ld(P1i, n_up), p2U = nb_ld(P2i, n_up);
+    const float wU = n_up >= 0 ? __ldcg(Wi + n_up) : 0.f;
+    const float wur = n_ur >= 0 ? __ldcg(Wi + n_ur) : 0.f;
+    const float p1uur = nb_ld(P1i, n_uur);
+    const float p1L = nb_ld(P1i, n_left), p2L = nb_ld(P2i, n_left);
+    const float wL = n_left >= 0 ? __ldcg(Wi + n_left) : 0.f;
+    const float wdl = n_dl >= 0 ? __ldcg(Wi + n_dl) : 0.f;
+    const float p2lld = nb_ld(P2i, n_lld);
+    // p'(x)
+    float g1 = 0.f, g2 = 0.f;
+    if (n_down != kNbOut) g1 = (n_down >= 0 ? wd : w_fixed(p1, p2dl, n_down, P.inv_theta)) - w0;
+    if (n_right != kNbOut) g2 = (n_right >= 0 ? wr : w_fixed(p1ur, p2, n_right, P.inv_theta)) - w0;
+    float q1, q2;
+    chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
+    const uint32_t rnd = mix32((uint32_t)a * 3u + seed_d);
+    q1 = Store<T>::st_sr(P1o, a, q1, rnd);
+    q2 = Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
+    // p1'(x - e1)
+    float q1u = 0.f;
+    if (n_up >= 0) {
+        float gu2 = 0.f;
+        if (n_ur != kNbOut) gu2 = (n_ur >= 0 ? wur : w_fixed(p1uur, p2U, n_ur, P.inv_theta)) - wU;
+        float b1, b2;
+        chambolle_update(p1U, p2U, w0 - wU, gu2, P.tau, b1, b2);
+        q1u = Store<T>::sr(b1, mix32((uint32_t)n_up * 3u + seed_d));
+    }
+    // p2'(x - e2)
+    float q2l = 0.f;
+    if (n_left >= 0) {
+        float gl1 = 0.f;
+        if (n_dl != kNbOut) gl1 = (n_dl >= 0 ? wdl : w_fixed(p1L, p2lld, n_dl, P.inv_theta)) - wL;
+        float b1, b2;
+        chambolle_update(p1L, p2L, gl1, w0 - wL, P.tau, b1, b2);
+        q2l = Store<T>::sr(b2, mix32(mix32((uint32_t)n_left * 3u + seed_d) ^ 0x9e3779b9u));
+    }
+    // primal step of x
+    const float div = (q1 - q1u) + (q2 - q2l);
+    const float vv = Store<T>::ld_rw(O.v, O.vi(a)) + Store<T>::vbias;
+    const float un = fmaf(-P.theta, div, vv);
+    const float vn = clamp01(un - O.fv(a));   // F = theta lambda f
+    const float vs = Store<T>::st_sr(O.v, O.vi(a), vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed_p)) +
+                     Store<T>::vbias;
+    Wo[a] = div - vs * P.inv_theta;
+    if (check) {
+        const float da = un - U[a], db = vn - vv;
+        du2 = fmaf(da, da, du2);
+        dv2 = fmaf(db, db, dv2);
+    }
+    if (write_u) U[a] = un;
+}
+
+// The iterations of one block of the persistent compact solver (see above);
+// false when a grid barrier timed out.
+template <typename T, bool SH, int NT, int UNROLL>
+__device__ __forceinline__ bool compact_iterations(const IterParams& P, const Own<T, SH>& O, int a0, int a1,
+                                                   int iters, int n_inner, int check_every, double tol, int warm,
+                                                   int64_t stride, T* P1a, T* P1b, T* P2a, T* P2b, float* Uu,
+                                                   float* Wc, float* Wc2, double* partials, WsHeader* h,
+                                                   float* ckpt, int ckpt_every, double* s_red, int fuse) {
     const unsigned nblocks = gridDim.x;
-    const int n = counts[1];
-    const int per = (n + (int)nblocks - 1) / (int)nblocks;
-    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = NT;
     int pb = 0;
-    unsigned gen = 0u;   // barriers passed (the generation counter starts at 0 each solve)
+    unsigned gen = 0u;   // barriers passed (the arrival counter starts at 0 each solve)
+    // the block's pixels, UNROLL per thread in flight (one in the fused
+    // step, which keeps about three times as many values live)
+    auto each = [&](auto&& op) {
+        int a = a0 + tid;
+        for (; a + (UNROLL - 1) * nt < a1; a += UNROLL * nt) {
+#pragma unroll
+            for (int k = 0; k < UNROLL; ++k) op(a + k * nt);
+        }
+        for (; a < a1; a += nt) op(a);
+    };
+    auto each1 = [&](auto&& op) {
+        for (int a = a0 + tid; a < a1; a += nt) op(a);
+    };
     float dummy0 = 0.f, dummy1 = 0.f;
     // current / other ping-pong buffers of p, selected without indexing
     auto p1c = [&]() { return pb ? P1b : P1a; };
@@ -489,8 +606,8 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
     auto p2o = [&]() { return pb ? P2a : P2b; };
     if (warm) {   // w of the warm-start iterate
         for (int a = a0 + tid; a < a1; a += nt)
-            primal_one(P, a, nb, stride, P1a, P2a, V, F, U, Wc, true, false, false, 0u, dummy0, dummy1);
-        if (!grid_sync(h, nblocks, gen)) return;
+            primal_one(P, a, O, P1a, P2a, Uu, Wc, true, false, false, 0u, dummy0, dummy1);
+        if (!grid_sync(h, nblocks, gen)) return false;
     }
     const int C = check_every;
     // checkpoint m holds (p1, p2, v) of iterate m * ckpt_every, as float32
@@ -501,31 +618,97 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
         for (int a = a0 + tid; a < a1; a += nt) {
             c[a] = to_f(q1[a]);
             c[stride + a] = to_f(q2[a]);
-            c[2 * stride + a] = to_f(V[a]) + Store<T>::vbias;
+            c[2 * stride + a] = to_f(O.v[O.vi(a)]) + Store<T>::vbias;
         }
     };
     if (ckpt) save(0);
+    if (fuse) {   // fused: one phase and one barrier per iteration
+        int wb = 0, chk = 0;
+        for (int it = 0; it < iters; ++it) {
+            const int l = it + 1;
+            const bool check = (l % C == 0) || l == iters;
+            const bool write_u = check || ((l + 1) % C == 0) || l == iters;
+            const uint32_t seed_d = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
+            const uint32_t seed_p = mix32(0x2545f491u ^ (uint32_t)it);
+            const T* pi1 = p1c(); const T* pi2 = p2c();
+            T* po1 = p1o(); T* po2 = p2o();
+            const float* wi = wb ? Wc2 : Wc;
+            float* wo = wb ? Wc : Wc2;
+            float du2 = 0.f, dv2 = 0.f;
+            each1([&](int a) {
+                fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, check, write_u, seed_d, seed_p, du2, dv2);
+            });
+            pb ^= 1;
+            wb ^= 1;
+            if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);   // own pixels: no barrier
+            // stopping-test partials, double-buffered by check so that a fast
+            // block cannot overwrite those a slow block is still summing
+            double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
+            if (check) {
+                double x = du2, y = dv2;
+                for (int d = 16; d > 0; d >>= 1) {
+                    x += __shfl_down_sync(0xffffffffu, x, d);
+                    y += __shfl_down_sync(0xffffffffu, y, d);
+                }
+                const int lane = tid & 31, wid = tid >> 5;
+                if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
+                __syncthreads();
+                if (tid == 0) {
+                    double sx = 0.0, sy = 0.0;
+                    for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
+                    part[2 * blockIdx.x] = sx;
+                    part[2 * blockIdx.x + 1] = sy;
+                }
+            }
+            if (!grid_sync(h, nblocks, gen)) return false;
+            if (check) {
+                // Section 4 stopping test: every block sums the block partials
+                // in the same fixed order, so all stop at the same iteration
+                double x = 0.0, y = 0.0;
+                for (int k = tid; k < (int)nblocks; k += nt) { x += __ldcg(part + 2 * k); y += __ldcg(part + 2 * k + 1); }
+                for (int d = 16; d > 0; d >>= 1) {
+                    x += __shfl_down_sync(0xffffffffu, x, d);
+                    y += __shfl_down_sync(0xffffffffu, y, d);
+                }
+                const int lane = tid & 31, wid = tid >> 5;
+                __syncthreads();
+                if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
+                __syncthreads();
+                double sx = 0.0, sy = 0.0;
+                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
+                const double du = sqrt(sx), dv = sqrt(sy);
+                const bool stop = tol > 0.0 && fmax(du, dv) <= tol;
+                if (blockIdx.x == 0 && tid == 0) {
+                    h->du = du;
+                    h->dv = dv;
+                    h->last_check = l;
+                    if (stop) {
+                        h->iters_done = l;
+                        h->done = 1;
+                    }
+                }
+                ++chk;
+                __syncthreads();
+                if (stop) return true;
+            }
+        }
+        return true;
+    }
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
         for (int sw = 0; sw < n_inner; ++sw) {
             const uint32_t seed = mix32(0x51ed270bu ^ (uint32_t)(it * 131 + sw));
             const T* pi1 = p1c(); const T* pi2 = p2c();
             T* po1 = p1o(); T* po2 = p2o();
-            int a = a0 + tid;
-            for (; a + nt < a1; a += 2 * nt) {
-                dual_one(P, a, nb, stride, pi1, pi2, Wc, po1, po2, seed);
-                dual_one(P, a + nt, nb, stride, pi1, pi2, Wc, po1, po2, seed);
-            }
-            if (a < a1) dual_one(P, a, nb, stride, pi1, pi2, Wc, po1, po2, seed);
+            each([&](int a) { dual_one(P, a, O, pi1, pi2, Wc, po1, po2, seed); });
             pb ^= 1;
-            if (!grid_sync(h, nblocks, gen)) return;
+            if (!grid_sync(h, nblocks, gen)) return false;
             // the previous iteration's stopping test may have fired
-            if (sw == 0 && it > 0 && (it % C == 0) && *(volatile int*)&h->done) return;
+            if (sw == 0 && it > 0 && (it % C == 0) && *(volatile int*)&h->done) return true;
             if (sw + 1 < n_inner) {
                 for (int b = a0 + tid; b < a1; b += nt)
-                    primal_one(P, b, nb, stride, p1c(), p2c(), V, F, U, Wc, true, false, false, 0u,
-                               dummy0, dummy1);
-                if (!grid_sync(h, nblocks, gen)) return;
+                    primal_one(P, b, O, p1c(), p2c(), Uu, Wc, true, false, false, 0u, dummy0, dummy1);
+                if (!grid_sync(h, nblocks, gen)) return false;
             }
         }
         const bool check = (l % C == 0) || l == iters;
@@ -533,13 +716,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
         const T* q1s = p1c(); const T* q2s = p2c();
-        int a = a0 + tid;
-        for (; a + nt < a1; a += 2 * nt) {
-            primal_one(P, a, nb, stride, q1s, q2s, V, F, U, Wc, false, check, write_u, seed, du2, dv2);
-            primal_one(P, a + nt, nb, stride, q1s, q2s, V, F, U, Wc, false, check, write_u, seed, du2, dv2);
-        }
-        if (a < a1)
-            primal_one(P, a, nb, stride, q1s, q2s, V, F, U, Wc, false, check, write_u, seed, du2, dv2);
+        each([&](int a) { primal_one(P, a, O, q1s, q2s, Uu, Wc, false, check, write_u, seed, du2, dv2); });
         if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);
         if (check) {
             double x = du2, y = dv2;
@@ -552,16 +729,16 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
             __syncthreads();
             if (tid == 0) {
                 double sx = 0.0, sy = 0.0;
-                for (int w = 0; w < kPersistThreads / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
+                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
                 partials[2 * blockIdx.x] = sx;
                 partials[2 * blockIdx.x + 1] = sy;
             }
         }
-        if (!grid_sync(h, nblocks, gen)) return;
+        if (!grid_sync(h, nblocks, gen)) return false;
         if (check && blockIdx.x == 0) {
             // Section 4 stopping test: fixed-order FP64 sum of the block partials
             double x = 0.0, y = 0.0;
-            for (int k = tid; k < (int)nblocks; k += nt) { x += partials[2 * k]; y += partials[2 * k + 1]; }
+            for (int k = tid; k < (int)nblocks; k += nt) { x += __ldcg(partials + 2 * k); y += __ldcg(partials + 2 * k + 1); }
             for (int d = 16; d > 0; d >>= 1) {
                 x += __shfl_down_sync(0xffffffffu, x, d);
                 y += __shfl_down_sync(0xffffffffu, y, d);
@@ -571,7 +748,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
             __syncthreads();
             if (tid == 0) {
                 double sx = 0.0, sy = 0.0;
-                for (int w = 0; w < kPersistThreads / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
+                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
                 const double du = sqrt(sx), dv = sqrt(sy);
                 h->du = du;
                 h->dv = dv;
@@ -584,6 +761,48 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
             }
             __syncthreads();
         }
+    }
+    return true;
+}
+
+template <typename T, int NT, int UNROLL>
+__global__ void __launch_bounds__(NT, 1024 / NT)
+k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
+                const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
+                T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
+                float* Wc, float* Wc2, double* partials, WsHeader* h, float* ckpt, int ckpt_every) {
+    __shared__ double s_red[2 * (NT / 32)];
+    extern __shared__ __align__(16) unsigned char c_smem[];
+    // set before the launch (capacity overflow): the same for every block
+    if (*(volatile int*)&h->done) return;
+    const unsigned nblocks = gridDim.x;
+    const int n = counts[1];
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    const int tid = threadIdx.x, nt = NT;
+    // the fused iteration pays off while barriers dominate, i.e. with few
+    // pixels per thread; the two-phase one reads six table rows, not eight
+    const int fuse = n_inner == 1 && per <= kFusePerThread * NT;
+    const int rows = fuse ? NB_COUNT : NB_UUR;
+    if ((size_t)per * (4 * rows + sizeof(T)) <= compact_smem(NT)) {   // the same in every block
+        int32_t* nb_s = reinterpret_cast<int32_t*>(c_smem);
+        T* v_s = reinterpret_cast<T*>(c_smem + (size_t)4 * rows * per);
+        for (int i = tid; i < a1 - a0; i += nt) {
+            for (int k = 0; k < rows; ++k) nb_s[k * per + i] = __ldg(nb + k * stride + a0 + i);
+            v_s[i] = V[a0 + i];
+        }
+        __syncthreads();
+        const Own<T, true> O{nb_s, per, v_s, F, a0};
+        if (!compact_iterations<T, true, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
+                                                     stride, P1a, P1b, P2a, P2b, U, Wc, Wc2, partials, h,
+                                                     ckpt, ckpt_every, s_red, fuse))
+            return;
+        for (int i = tid; i < a1 - a0; i += nt) V[a0 + i] = v_s[i];
+    } else {
+        const Own<T, false> O{nb, stride, V, F, 0};
+        compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm, stride,
+                                                 P1a, P1b, P2a, P2b, U, Wc, Wc2, partials, h, ckpt,
+                                                 ckpt_every, s_red, fuse);
     }
 }
 
@@ -625,7 +844,6 @@ __global__ void k_compact_scatter(BatchDesc B, const int32_t* __restrict__ base,
 
 __global__ void k_solve_begin(WsHeader* h) {
     h->bar_count = 0u;
-    h->bar_gen = 0u;
     h->done = 0;
     h->iters_done = 0;
     h->last_check = 0;
@@ -689,17 +907,17 @@ static int grid_for(K kernel, int threads, int64_t max_blocks) {
 }
 
 struct CompactLayout {
-    size_t off[9];
+    size_t off[10];
     int64_t cap;       // RD pixels the state can hold
     int64_t stride;    // elements allocated per array (cap + a chunk of slack, multiple of 64)
 };
 
 // compact state: p1[2], p2[2], v (storage type), f, u, w (float32),
-// neighbour table (int32 x 6 rows), each array 256-byte aligned and `stride`
-// elements long
-constexpr int kCompactArrays = 9;
+// neighbour table (int32 x NB_COUNT rows), w2 (float32), each array 256-byte
+// aligned and `stride` elements long
+constexpr int kCompactArrays = 10;
 constexpr int kSlack = 256;   // spare elements past the capacity in every array
-constexpr size_t compact_per_element(size_t sz) { return 5 * sz + 12 + 4 * NB_COUNT; }
+constexpr size_t compact_per_element(size_t sz) { return 5 * sz + 16 + 4 * NB_COUNT; }
 static int64_t compact_stride(int64_t capacity) {
     return (int64_t)align_up((size_t)std::max<int64_t>(capacity, 1) + kSlack, 64);
 }
@@ -716,7 +934,8 @@ static CompactLayout compact_layout(size_t state_bytes, int storage) {
     C.off[5] = o; o = align_up(o + 4 * (size_t)stride, 256);   // f
     C.off[6] = o; o = align_up(o + 4 * (size_t)stride, 256);   // u
     C.off[7] = o; o = align_up(o + 4 * (size_t)stride, 256);   // w
-    C.off[8] = o;                                              // neighbour table
+    C.off[8] = o; o = align_up(o + 4 * (size_t)NB_COUNT * stride, 256);   // neighbour table
+    C.off[9] = o;                                              // w2
     return C;
 }
 
@@ -791,6 +1010,7 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     S.u = reinterpret_cast<float*>(sb + C.off[6]);
     S.w = reinterpret_cast<float*>(sb + C.off[7]);
     S.nb = reinterpret_cast<int32_t*>(sb + C.off[8]);
+    S.w2 = reinterpret_cast<float*>(sb + C.off[9]);
     S.cap = C.cap;
     S.stride = C.stride;
     k_batch_bases<<<1, 1, 0, s>>>(B, base, totals, C.cap, h);
@@ -804,16 +1024,19 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     T* P2a = static_cast<T*>(S.p2[0]);
     T* P2b = static_cast<T*>(S.p2[1]);
     T* V = static_cast<T*>(S.v);
-    auto kern = k_solve_compact<T>;
+    const int NTs = kCompactThreads;
+    const void* kern = (const void*)k_solve_compact<T, kCompactThreads, kCompactUnroll>;
+    const size_t smem = compact_smem(NTs);
     // one cooperative launch for the whole solve: the grid is what can be
-    // resident at once (at most one block per 512 RD pixels of capacity)
+    // resident at once (at most one block per NT RD pixels of capacity)
+    SEG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, 0));
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTs, smem));
     if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_compact cannot be resident");
     const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, max_pixels));
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
-                                      std::max<int64_t>(1, (most + kPersistThreads - 1) / kPersistThreads));
-    grid = (int)std::min<int64_t>(grid, max_partials);
+                                      std::max<int64_t>(1, (most + NTs - 1) / NTs));
+    grid = (int)std::min<int64_t>(grid, max_partials / 2);   // partials are double-buffered
     int iters = prm->iters, n_inner = std::max(1, prm->n_inner), check_every = std::max(1, prm->check_every);
     double tol = prm->tol;
     int warm = prm->warm_start;
@@ -823,12 +1046,12 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     float* F = S.f;
     float* U = S.u;
     float* Wc = S.w;
+    float* Wc2 = S.w2;
     IterParams P = P0;
     void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&cnt, (void*)&nbp, &stride,
-                    &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Wc, &partials, &h, &ckpt, &ckpt_every};
+                    &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Wc, &Wc2, &partials, &h, &ckpt, &ckpt_every};
     if (iters > 0 || warm) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPersistThreads),
-                                                 args, 0, s));
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NTs), args, smem, s));
         count_launch();
     }
     k_compact_scatter<T><<<gblocks, 256, 0, s>>>(B, base, totals, prm->iters, std::max(1, prm->n_inner),
@@ -973,19 +1196,20 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
         if (!grid_sync(h, nblocks, gen)) return;
         float d0 = 0.f, d1 = 0.f;
         for (int a = a0 + tid; a < a1; a += nt)
-            primal_one<float>(P, a, nb, stride, segp1(0), segp2(0), segv(0), F, nullptr, segw(0), true,
-                              false, false, 0u, d0, d1);
+            primal_one(P, a, Own<float, false>{nb, stride, segv(0), F, 0}, segp1(0), segp2(0), nullptr,
+                       segw(0), true, false, false, 0u, d0, d1);
         if (!grid_sync(h, nblocks, gen)) return;
         for (int m = 0; m < M; ++m) {
             for (int a = a0 + tid; a < a1; a += nt)
-                dual_one<float>(P, a, nb, stride, segp1(m), segp2(m), segw(m), segp1(m + 1), segp2(m + 1), 0u);
+                dual_one(P, a, Own<float, false>{nb, stride, nullptr, F, 0}, segp1(m), segp2(m), segw(m),
+                         segp1(m + 1), segp2(m + 1), 0u);
             if (!grid_sync(h, nblocks, gen)) return;
             for (int a = a0 + tid; a < a1; a += nt) {
                 segv(m + 1)[a] = segv(m)[a];    // primal_one updates v in place
             }
             for (int a = a0 + tid; a < a1; a += nt)
-                primal_one<float>(P, a, nb, stride, segp1(m + 1), segp2(m + 1), segv(m + 1), F, nullptr,
-                                  segw(m + 1), false, false, false, 0u, d0, d1);
+                primal_one(P, a, Own<float, false>{nb, stride, segv(m + 1), F, 0}, segp1(m + 1), segp2(m + 1),
+                           nullptr, segw(m + 1), false, false, false, 0u, d0, d1);
             if (!grid_sync(h, nblocks, gen)) return;
         }
         // ---- walk back through the segment
