@@ -40,7 +40,7 @@ BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + 
 # launch / 50) of `bench.py --profile --iters 50` (2048x2048, delta = 0.2,
 # float32), summarised in profiles/k_solve_compact_ds2048.md.  The compacted
 # state stays in L2, so this is far below the algorithmic bytes.
-COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (46336 + 21832192) / 50}
+COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (136960 + 14904320) / 50}
 
 
 def parse():
@@ -60,6 +60,8 @@ def parse():
                     help="no timing: one restricted step (delta given by --delta) and one "
                          "full-domain step, for ncu captures")
     ap.add_argument("--delta", type=float, default=0.2)
+    ap.add_argument("--profile-tiled", action="store_true",
+                    help="with --profile: also the temporally blocked solver, restricted and full")
     return ap.parse_args()
 
 
@@ -318,9 +320,13 @@ def run_profile(args):
     z = seg.upload(P.z, dev)
     label = seg.upload(P.label, dev)
     markers = torch.from_numpy(P.markers.astype(np.int32)).to(dev)
-    for mode, delta in (("compact", args.delta), ("dense", math.inf)):
+    runs = [("compact", args.delta), ("dense", math.inf)]
+    if args.profile_tiled:
+        runs += [("tiled", args.delta), ("tiled", math.inf)]
+    for mode, delta in runs:
         S = seg.Solver(H, W, tile_h=args.tile_h or 16, mode=mode,
                        storage=args.storage if mode == "compact" else "f32", device=dev)
+        print(f"{mode}: solving", flush=True)
         S.fitting(z, label=label, markers=markers, gamma=P.gamma)
         S.domain(delta=delta)
         S.solve(args.lam, iters=P.iters, check_every=10)
