@@ -41,13 +41,20 @@ __device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync(WsHeader* h, unsigned nblocks, unsigned& gen) {
-    __shared__ int s_ok;
+// Split form of the barrier: grid_arrive after the block's writes (a block
+// barrier, then thread 0's release reduction; returns the new generation),
+// grid_wait before reading what other blocks wrote.  Work that only reads
+// this block's own writes may run in between.
+__device__ __forceinline__ void grid_arrive(WsHeader* h, unsigned& gen) {
     __syncthreads();
     ++gen;
+    if (threadIdx.x == 0) red_add_release_gpu(&h->bar_count, 1u);
+}
+
+__device__ __forceinline__ bool grid_wait(WsHeader* h, unsigned nblocks, unsigned gen) {
+    __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        red_add_release_gpu(&h->bar_count, 1u);
         const unsigned target = nblocks * gen;
         const long long t0 = clock64();
         while ((int)(ld_acquire_gpu(&h->bar_count) - target) < 0) {
@@ -62,6 +69,11 @@ __device__ __forceinline__ bool grid_sync(WsHeader* h, unsigned nblocks, unsigne
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(WsHeader* h, unsigned nblocks, unsigned& gen) {
+    grid_arrive(h, gen);
+    return grid_wait(h, nblocks, gen);
 }
 
 // ------------------------------------------------ host entry of tiled.cu

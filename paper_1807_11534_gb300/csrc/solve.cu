@@ -765,6 +765,189 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
     return true;
 }
 
+// ---- shared-memory-resident block state (two-phase iteration, n_inner = 1)
+//
+// When a block's pixels fit, p (both ping-pong copies), w and v of its own
+// pixels live in shared memory for the whole solve, and its neighbour table
+// is re-encoded as int16: a local index (>= 0) for a neighbour the block
+// owns, the fixed-pixel codes (-1..-3), or kNbRemote - r for the r-th entry
+// of a per-block list of the compact indices of neighbours other blocks own.
+// Neighbours the block owns are read from shared memory; only the others go
+// to L2.  Every update is still written to the global arrays, which the
+// other blocks read.  The barrier and stopping-test protocol is the one of
+// compact_iterations, so blocks on either path interleave correctly.
+constexpr int kNbRemote = -4;
+
+template <typename T>
+struct SmState {
+    const int16_t* nb;   // [NB_UUR][per]
+    const int32_t* rem;  // remote compact indices
+    float* p1;           // [2][per]
+    float* p2;           // [2][per]
+    float* w;            // [per]
+    T* v;                // [per]
+    int per;
+    __device__ __forceinline__ int code(int k, int i) const { return nb[k * per + i]; }
+    __device__ __forceinline__ static bool in_rd(int c) { return c >= 0 || c <= kNbRemote; }
+    // w at a neighbour in RD
+    __device__ __forceinline__ float wn(int c, const float* Wg) const {
+        return c >= 0 ? w[c] : __ldcg(Wg + rem[kNbRemote - c]);
+    }
+    // p component at a neighbour (0 where it is fixed or outside)
+    __device__ __forceinline__ float pn(const float* ps, const T* pg, int c) const {
+        return c >= 0 ? ps[c] : (c <= kNbRemote ? Store<T>::ldc(pg, rem[kNbRemote - c]) : 0.f);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void dual_sm(const IterParams& P, int i, int a, const SmState<T>& S, int pb,
+                                        const T* P1g, const T* P2g, const float* Wg, T* P1o, T* P2o,
+                                        uint32_t seed) {
+    const int per = S.per;
+    const int c_down = S.code(NB_DOWN, i), c_right = S.code(NB_RIGHT, i);
+    const int c_dl = S.code(NB_DOWNLEFT, i), c_ur = S.code(NB_UPRIGHT, i);
+    const float* p1c = S.p1 + pb * per;
+    const float* p2c = S.p2 + pb * per;
+    const float p1 = p1c[i], p2 = p2c[i], w0 = S.w[i];
+    const float wd = SmState<T>::in_rd(c_down) ? S.wn(c_down, Wg) : 0.f;
+    const float wr = SmState<T>::in_rd(c_right) ? S.wn(c_right, Wg) : 0.f;
+    const float p2dl = S.pn(p2c, P2g, c_dl);
+    const float p1ur = S.pn(p1c, P1g, c_ur);
+    float g1 = 0.f, g2 = 0.f;
+    if (c_down != kNbOut) g1 = (SmState<T>::in_rd(c_down) ? wd : w_fixed(p1, p2dl, c_down, P.inv_theta)) - w0;
+    if (c_right != kNbOut) g2 = (SmState<T>::in_rd(c_right) ? wr : w_fixed(p1ur, p2, c_right, P.inv_theta)) - w0;
+    float q1, q2;
+    chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
+    const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
+    S.p1[(pb ^ 1) * per + i] = Store<T>::st_sr(P1o, a, q1, rnd);
+    S.p2[(pb ^ 1) * per + i] = Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
+}
+
+template <typename T>
+__device__ __forceinline__ void primal_sm(const IterParams& P, int i, int a, const SmState<T>& S, int pb,
+                                          const T* P1g, const T* P2g, const float* F, float* U, float* Wg,
+                                          bool check, bool write_u, uint32_t seed, float& du2, float& dv2) {
+    const int per = S.per;
+    const int c_up = S.code(NB_UP, i), c_left = S.code(NB_LEFT, i);
+    const float* q1c = S.p1 + pb * per;
+    const float* q2c = S.p2 + pb * per;
+    const float q1 = q1c[i], q2 = q2c[i];
+    const float vv = Store<T>::ld_rw(S.v, i) + Store<T>::vbias;
+    const float q1u = S.pn(q1c, P1g, c_up), q2l = S.pn(q2c, P2g, c_left);
+    const float div = (q1 - q1u) + (q2 - q2l);
+    const float un = fmaf(-P.theta, div, vv);
+    const float vn = clamp01(un - __ldg(F + a));   // F = theta lambda f
+    const float vs = Store<T>::st_sr(S.v, i, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
+                     Store<T>::vbias;
+    const float wv = div - vs * P.inv_theta;
+    S.w[i] = wv;
+    Wg[a] = wv;
+    if (check) {
+        const float da = un - U[a], db = vn - vv;
+        du2 = fmaf(da, da, du2);
+        dv2 = fmaf(db, db, dv2);
+    }
+    if (write_u) U[a] = un;
+}
+
+// The iterations with shared-memory-resident state (n_inner = 1, after the
+// warm-start pass); same barriers and stopping test as compact_iterations.
+template <typename T, int NT, int UNROLL>
+__device__ __forceinline__ bool compact_iterations_sm(const IterParams& P, const SmState<T>& S, int a0, int a1,
+                                                      int iters, int check_every, double tol, int64_t stride,
+                                                      T* P1a, T* P1b, T* P2a, T* P2b, const float* F,
+                                                      float* U, float* Wc, double* partials, WsHeader* h,
+                                                      float* ckpt, int ckpt_every, double* s_red,
+                                                      unsigned gen) {
+    const unsigned nblocks = gridDim.x;
+    const int tid = threadIdx.x, nt = NT;
+    int pb = 0;
+    auto each = [&](auto&& op) {
+        int a = a0 + tid;
+        for (; a + (UNROLL - 1) * nt < a1; a += UNROLL * nt) {
+#pragma unroll
+            for (int k = 0; k < UNROLL; ++k) op(a + k * nt);
+        }
+        for (; a < a1; a += nt) op(a);
+    };
+    auto save = [&](int m) {
+        float* c = ckpt + (int64_t)m * 3 * stride;
+        for (int a = a0 + tid; a < a1; a += nt) {
+            const int i = a - a0;
+            c[a] = S.p1[pb * S.per + i];
+            c[stride + a] = S.p2[pb * S.per + i];
+            c[2 * stride + a] = to_f(S.v[i]) + Store<T>::vbias;
+        }
+    };
+    if (ckpt) save(0);
+    const int C = check_every;
+    for (int it = 0; it < iters; ++it) {
+        const int l = it + 1;
+        {
+            const uint32_t seed = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
+            const T* g1 = pb ? P1b : P1a;
+            const T* g2 = pb ? P2b : P2a;
+            T* o1 = pb ? P1a : P1b;
+            T* o2 = pb ? P2a : P2b;
+            each([&](int a) { dual_sm(P, a - a0, a, S, pb, g1, g2, Wc, o1, o2, seed); });
+            pb ^= 1;
+            if (!grid_sync(h, nblocks, gen)) return false;
+            if (it > 0 && (it % C == 0) && *(volatile int*)&h->done) return true;
+        }
+        const bool check = (l % C == 0) || l == iters;
+        const bool write_u = check || ((l + 1) % C == 0) || l == iters;
+        const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
+        float du2 = 0.f, dv2 = 0.f;
+        const T* g1 = pb ? P1b : P1a;
+        const T* g2 = pb ? P2b : P2a;
+        each([&](int a) { primal_sm(P, a - a0, a, S, pb, g1, g2, F, U, Wc, check, write_u, seed, du2, dv2); });
+        if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);
+        if (check) {
+            double x = du2, y = dv2;
+            for (int d = 16; d > 0; d >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, d);
+                y += __shfl_down_sync(0xffffffffu, y, d);
+            }
+            const int lane = tid & 31, wid = tid >> 5;
+            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
+            __syncthreads();
+            if (tid == 0) {
+                double sx = 0.0, sy = 0.0;
+                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
+                partials[2 * blockIdx.x] = sx;
+                partials[2 * blockIdx.x + 1] = sy;
+            }
+        }
+        if (!grid_sync(h, nblocks, gen)) return false;
+        if (check && blockIdx.x == 0) {
+            double x = 0.0, y = 0.0;
+            for (int k = tid; k < (int)nblocks; k += nt) { x += __ldcg(partials + 2 * k); y += __ldcg(partials + 2 * k + 1); }
+            for (int d = 16; d > 0; d >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, d);
+                y += __shfl_down_sync(0xffffffffu, y, d);
+            }
+            const int lane = tid & 31, wid = tid >> 5;
+            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
+            __syncthreads();
+            if (tid == 0) {
+                double sx = 0.0, sy = 0.0;
+                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
+                const double du = sqrt(sx), dv = sqrt(sy);
+                h->du = du;
+                h->dv = dv;
+                h->last_check = l;
+                if (tol > 0.0 && fmax(du, dv) <= tol) {
+                    h->iters_done = l;
+                    __threadfence();
+                    h->done = 1;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    return true;
+}
+
 template <typename T, int NT, int UNROLL>
 __global__ void __launch_bounds__(NT, 1024 / NT)
 k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
@@ -784,6 +967,74 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
     // pixels per thread; the two-phase one reads six table rows, not eight
     const int fuse = n_inner == 1 && per <= kFusePerThread * NT;
     const int rows = fuse ? NB_COUNT : NB_UUR;
+    if (n_inner == 1 && !fuse) {
+        // shared-memory-resident state if this block's pixels and its list of
+        // neighbours owned by other blocks fit (decided per block: both paths
+        // keep the global arrays current and pass the same barriers)
+        __shared__ int s_r;
+        if (tid == 0) s_r = 0;
+        __syncthreads();
+        int r = 0;
+        for (int i = tid; i < a1 - a0; i += nt)
+            for (int k = 0; k < NB_UUR; ++k) {
+                const int m = __ldg(nb + k * stride + a0 + i);
+                r += (m >= 0 && (m < a0 || m >= a1)) ? 1 : 0;
+            }
+        atomicAdd(&s_r, r);
+        __syncthreads();
+        const int nrem = s_r;
+        const size_t off_p1 = ((size_t)2 * NB_UUR * per + 15) & ~(size_t)15;
+        const size_t off_p2 = off_p1 + (size_t)8 * per;
+        const size_t off_w = off_p2 + (size_t)8 * per;
+        const size_t off_v = off_w + (size_t)4 * per;
+        const size_t off_rem = off_v + (size_t)4 * per;
+        if (off_rem + (size_t)4 * nrem <= compact_smem(NT) && nrem <= 32000) {
+            int16_t* nb16 = reinterpret_cast<int16_t*>(c_smem);
+            float* p1s = reinterpret_cast<float*>(c_smem + off_p1);
+            float* p2s = reinterpret_cast<float*>(c_smem + off_p2);
+            float* ws = reinterpret_cast<float*>(c_smem + off_w);
+            T* vs = reinterpret_cast<T*>(c_smem + off_v);
+            int32_t* rem = reinterpret_cast<int32_t*>(c_smem + off_rem);
+            unsigned gen0 = 0u;
+            if (warm) {   // w of the warm-start iterate, from the global arrays (as the other path)
+                float d0 = 0.f, d1 = 0.f;
+                const Own<T, false> O{nb, stride, V, F, 0};
+                for (int a = a0 + tid; a < a1; a += nt)
+                    primal_one(P, a, O, P1a, P2a, U, Wc, true, false, false, 0u, d0, d1);
+                if (!grid_sync(h, nblocks, gen0)) return;
+            }
+            if (tid == 0) s_r = 0;
+            __syncthreads();
+            for (int i = tid; i < a1 - a0; i += nt) {
+                for (int k = 0; k < NB_UUR; ++k) {
+                    const int m = __ldg(nb + k * stride + a0 + i);
+                    int c = m;
+                    if (m >= a0 && m < a1) {
+                        c = m - a0;
+                    } else if (m >= 0) {
+                        const int slot = atomicAdd(&s_r, 1);
+                        rem[slot] = m;
+                        c = kNbRemote - slot;
+                    }
+                    nb16[k * per + i] = (int16_t)c;
+                }
+                p1s[i] = Store<T>::ldc(P1a, a0 + i);
+                p2s[i] = Store<T>::ldc(P2a, a0 + i);
+                ws[i] = __ldcg(Wc + a0 + i);
+                vs[i] = V[a0 + i];
+            }
+            __syncthreads();
+            const SmState<T> S{nb16, rem, p1s, p2s, ws, vs, per};
+            // the barrier generation continues from the warm-start barrier
+            if (!compact_iterations_sm<T, NT, UNROLL>(P, S, a0, a1, iters, check_every, tol, stride, P1a, P1b,
+                                                       P2a, P2b, F, U, Wc, partials, h, ckpt, ckpt_every,
+                                                       s_red, gen0))
+                return;
+            __syncthreads();
+            for (int i = tid; i < a1 - a0; i += nt) V[a0 + i] = vs[i];
+            return;
+        }
+    }
     if ((size_t)per * (4 * rows + sizeof(T)) <= compact_smem(NT)) {   // the same in every block
         int32_t* nb_s = reinterpret_cast<int32_t*>(c_smem);
         T* v_s = reinterpret_cast<T*>(c_smem + (size_t)4 * rows * per);
