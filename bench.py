@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--tile-h", type=int, default=0, help="0: autotune")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the adjoint, 16-bit storage and batch measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile", action="store_true",
                     help="no timing: one restricted step (delta given by --delta) and one "
@@ -415,6 +417,107 @@ def run_batch(args, rank, world):
                 probs=probs)
 
 
+# ------------------------------------------------------------------ other rows
+
+def _graph_ms(g, stream, flush, reps=3):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(reps):
+        flush.fill_(1)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def row_adjoint(dev, flush):
+    """Differentiation workload: 8 images of 1024x1024 (random shapes, CV term
+    c1 = 0.3, c2 = 0.7, lambda = 1, delta = 0.2), K = 200 unrolled iterations
+    with checkpoints every 20, forward (seg_solve_diff) and hand-written
+    adjoint (seg_backward) of every image in one CUDA graph each; the BCE
+    gradient on u_K is formed once, its values do not change the work."""
+    import torch
+    from paper_1807_11534_gb300 import seg, synth
+    stream = torch.cuda.current_stream()
+    probs = synth.training_batch(seed=0, n_images=8, side=1024, iters=200)
+    sols, grads, A = [], [], 0
+    for P in probs:
+        S = seg.DiffSolver(1024, 1024, 200, 20, device=dev)
+        S.fitting(seg.upload(P.z, dev), 0.3, 0.7)
+        S.domain(delta=0.2)
+        S.solve_diff(1.0)
+        u = S.u[:, :1024].clamp(1e-4, 1 - 1e-4)
+        m = seg.upload(P.label.astype(np.float32), dev)[:, :1024]
+        g = seg.image(1024, 1024, device=dev)
+        g[:, :1024] = (u - m) / (u * (1 - u)) / u.numel()
+        torch.cuda.synchronize()
+        A += int(S.dom.counts[1].item())
+        sols.append(S)
+        grads.append(g)
+    gf = seg.capture_graph(lambda: [S.solve_diff(1.0) for S in sols])
+    gb = seg.capture_graph(lambda: [S.backward(g) for S, g in zip(sols, grads)])
+    tf, tb = _graph_ms(gf, stream, flush), _graph_ms(gb, stream, flush)
+    for S in sols:
+        S.check_status()
+    return {"config": "8 x 1024^2, K=200, C=20, lambda=1, delta=0.2 (BCE on u_K)",
+            "active_pixels": A, "forward_ms": tf, "backward_ms": tb, "backward_over_forward": tb / tf,
+            "active_Mpixel_iter_per_s": A * 200 / ((tf + tb) * 1e-3) / 1e6}
+
+
+def row_storage(dev, flush):
+    """Precision variants: 4096x4096 image of 200 polygons + N(0, 0.08), CV
+    term, delta = 0.1, p and v stored as float32, bf16 and fp16 with float32
+    arithmetic: time per iteration (graphs of 200 iterations minus 0) and,
+    after 2000 iterations, the max and mean |u - u_f32| and the disagreement
+    of the masks u > 0.5."""
+    import torch
+    from paper_1807_11534_gb300 import seg, synth
+    stream = torch.cuda.current_stream()
+    P = synth.polygons(seed=0, H=4096, W=4096)
+    z = seg.upload(P.z, dev)
+    out, u32 = {}, None
+    for st in ("f32", "bf16", "f16"):
+        S = seg.Solver(4096, 4096, tile_h=16, mode="compact", storage=st, device=dev)
+        S.fitting(z, 0.3, 0.7)
+        S.domain(delta=0.1)
+        A = int(S.dom.counts[1].item())
+        g = {n: seg.capture_graph(lambda n=n: S.solve(1.0, iters=n, check_every=max(n, 1)))
+             for n in (0, 200)}
+        t = (_graph_ms(g[200], stream, flush) - _graph_ms(g[0], stream, flush)) / 200
+        S.solve(1.0, iters=2000, check_every=2000)
+        torch.cuda.synchronize()
+        S.check_status()
+        u = S.u[:, :4096].double()
+        if u32 is None:
+            u32 = u
+        d = (u - u32).abs()
+        bpa = BYTES_PER_ACTIVE_ITER[st]
+        out[st] = {"us_per_iter": t * 1e3, "active_pixels": A,
+                   "achieved_gbs": bpa * A / (t * 1e-3) / 1e9,
+                   "max_abs_du_vs_f32": float(d.max()), "mean_abs_du_vs_f32": float(d.mean()),
+                   "mask_disagreement_vs_f32": float(((u > 0.5) != (u32 > 0.5)).double().mean())}
+    return {"config": "4096^2 polygons, CV, lambda=1, delta=0.1, 2000 iterations", **out}
+
+
+def run_rows(args, dev):
+    """The hot-path rows beside the headline: adjoint (differentiation
+    workload), 16-bit storage (precision workload), batched solve."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rows = {"a7_adjoint": row_adjoint(dev, flush), "a8_storage": row_storage(dev, flush)}
+    b = run_batch(argparse.Namespace(**{**vars(args), "iters": None}), 0, 1)
+    rows["a6_batch"] = {"config": "64 images, sides U{128..1024}, q ~ U[0.02, 0.4], 500 iterations, "
+                                  "one persistent launch",
+                        "active_pixels": b["A"], "ms_per_step": b["ms"], "us_per_iter": b["t_iter"] * 1e3,
+                        "active_Mpixel_iter_per_s": b["A"] * b["iters"] / (b["ms"] * 1e-3) / 1e6,
+                        "frac_of_measured_hbm": b["ach"] / 6689.8, "tile_h": b["tile_h"]}
+    return rows
+
+
 def cpu_baseline(P, delta, seconds):
     """The FP64 oracle (single thread) on a bounded sample of the workload:
     fitting + domain on the full image, then as many restricted iterations as
@@ -454,7 +557,9 @@ def main():
         if rank != 0:
             return
         P = make_problem(args)
-        delta = 0.1
+        # the equal-error delta the GPU arm's calibration selects on this
+        # workload (its E1 sweep reaches 0.98 first at 0.2)
+        delta = 0.2 if args.workload == "ds2048" else 0.1
         times, vals = [], []
         for k in range(args.warmup + args.steps):
             cb, A, n, dt = cpu_baseline(P, delta, max(2.0, args.cpu_seconds / max(args.steps, 1)))
@@ -467,7 +572,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": "ds2048 restricted solve, bounded sample (oracle)"},
+                "config": {"workload": f"{args.workload}: restricted solve at delta={delta:g}, bounded "
+                                       "sample of the iterations (FP64 oracle, one core)"},
                 "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "active Mpixel-iter/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -552,6 +658,8 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
+    if rank == 0 and not args.no_rows and args.workload == "ds2048":
+        line["rows"] = run_rows(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
     if rank == 0 and not args.no_cpu_baseline:
         cb, *_ = cpu_baseline(r["P"], r["delta"], args.cpu_seconds)
         line["cpu_baseline"] = cb

@@ -179,8 +179,10 @@ template <typename T> struct Store;
 template <> struct Store<float> {
     static constexpr float vbias = 0.0f;
     static __device__ __forceinline__ float ld(const float* p, int64_t i) { return __ldg(p + i); }
-    // coherent load (L2) of state that other blocks write during the kernel
-    static __device__ __forceinline__ float ldc(const float* p, int64_t i) { return __ldcg(p + i); }
+    // load of state that other blocks write during the kernel: a plain
+    // (not read-only-path) load, ordered after their writes by the grid
+    // barrier's acquire, which also discards stale L1 lines
+    static __device__ __forceinline__ float ldc(const float* p, int64_t i) { return p[i]; }
     static __device__ __forceinline__ float ld_rw(const float* p, int64_t i) { return p[i]; }
     static __device__ __forceinline__ void st(float* p, int64_t i, float x) { p[i] = x; }
     // x rounded to the storage type (stochastically for 16-bit types, with
@@ -193,9 +195,7 @@ template <> struct Store<float> {
 template <> struct Store<__nv_bfloat16> {
     static constexpr float vbias = 0.5f;
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(__ldg(p + i)); }
-    static __device__ __forceinline__ float ldc(const __nv_bfloat16* p, int64_t i) {
-        return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p) + i)));
-    }
+    static __device__ __forceinline__ float ldc(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ float ld_rw(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float x) { p[i] = __float2bfloat16_rn(x); }
     // bf16 keeps the top 16 bits of the float: adding a uniform 16-bit word to
@@ -216,9 +216,7 @@ template <> struct Store<__nv_bfloat16> {
 template <> struct Store<__half> {
     static constexpr float vbias = 0.5f;
     static __device__ __forceinline__ float ld(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
-    static __device__ __forceinline__ float ldc(const __half* p, int64_t i) {
-        return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p) + i)));
-    }
+    static __device__ __forceinline__ float ldc(const __half* p, int64_t i) { return __half2float(p[i]); }
     static __device__ __forceinline__ float ld_rw(const __half* p, int64_t i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void st(__half* p, int64_t i, float x) { p[i] = __float2half_rn(x); }
     // round to one of the two neighbouring halves with probabilities given by

@@ -381,8 +381,11 @@ __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return _
 template <>
 __device__ __forceinline__ float to_f<__half>(__half x) { return __half2float(x); }
 
-// state at a neighbour (0 where it is fixed or outside): coherent loads, the
-// state is rewritten by other blocks between the phases of a persistent solve
+// w written by other blocks earlier in a persistent solve (see Store::ldc)
+__device__ __forceinline__ float ldw(const float* p) { return *p; }
+
+// state at a neighbour (0 where it is fixed or outside); the state is
+// rewritten by other blocks between the phases of a persistent solve
 template <typename T>
 __device__ __forceinline__ float nb_ld(const T* X, int n) {
     return n >= 0 ? Store<T>::ldc(X, n) : 0.f;
@@ -453,9 +456,9 @@ __device__ __forceinline__ void dual_one(const IterParams& P, int a, const Own<T
     const int n_dl = O.nbr(NB_DOWNLEFT, a);
     const int n_ur = O.nbr(NB_UPRIGHT, a);
     const float p1 = Store<T>::ldc(P1i, a), p2 = Store<T>::ldc(P2i, a);
-    const float w0 = __ldcg(Wc + a);
-    const float wd = n_down >= 0 ? __ldcg(Wc + n_down) : 0.f;
-    const float wr = n_right >= 0 ? __ldcg(Wc + n_right) : 0.f;
+    const float w0 = ldw(Wc + a);
+    const float wd = n_down >= 0 ? ldw(Wc + n_down) : 0.f;
+    const float wr = n_right >= 0 ? ldw(Wc + n_right) : 0.f;
     const float p2dl = nb_ld(P2i, n_dl);
     const float p1ur = nb_ld(P1i, n_ur);
     float g1 = 0.f, g2 = 0.f;
@@ -518,17 +521,17 @@ __device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<
     const int n_lld = n_left >= 0 ? O.nbr(NB_LLD, a) : kNbOut;
     // every load of the step, independent of one another
     const float p1 = Store<T>::ldc(P1i, a), p2 = Store<T>::ldc(P2i, a);
-    const float w0 = __ldcg(Wi + a);
-    const float wd = n_down >= 0 ? __ldcg(Wi + n_down) : 0.f;
-    const float wr = n_right >= 0 ? __ldcg(Wi + n_right) : 0.f;
+    const float w0 = ldw(Wi + a);
+    const float wd = n_down >= 0 ? ldw(Wi + n_down) : 0.f;
+    const float wr = n_right >= 0 ? ldw(Wi + n_right) : 0.f;
     const float p2dl = nb_ld(P2i, n_dl), p1ur = nb_ld(P1i, n_ur);
     const float p1U = nb_ld(P1i, n_up), p2U = nb_ld(P2i, n_up);
-    const float wU = n_up >= 0 ? __ldcg(Wi + n_up) : 0.f;
-    const float wur = n_ur >= 0 ? __ldcg(Wi + n_ur) : 0.f;
+    const float wU = n_up >= 0 ? ldw(Wi + n_up) : 0.f;
+    const float wur = n_ur >= 0 ? ldw(Wi + n_ur) : 0.f;
     const float p1uur = nb_ld(P1i, n_uur);
     const float p1L = nb_ld(P1i, n_left), p2L = nb_ld(P2i, n_left);
-    const float wL = n_left >= 0 ? __ldcg(Wi + n_left) : 0.f;
-    const float wdl = n_dl >= 0 ? __ldcg(Wi + n_dl) : 0.f;
+    const float wL = n_left >= 0 ? ldw(Wi + n_left) : 0.f;
+    const float wdl = n_dl >= 0 ? ldw(Wi + n_dl) : 0.f;
     const float p2lld = nb_ld(P2i, n_lld);
     // p'(x)
     float g1 = 0.f, g2 = 0.f;
@@ -791,7 +794,7 @@ struct SmState {
     __device__ __forceinline__ static bool in_rd(int c) { return c >= 0 || c <= kNbRemote; }
     // w at a neighbour in RD
     __device__ __forceinline__ float wn(int c, const float* Wg) const {
-        return c >= 0 ? w[c] : __ldcg(Wg + rem[kNbRemote - c]);
+        return c >= 0 ? w[c] : ldw(Wg + rem[kNbRemote - c]);
     }
     // p component at a neighbour (0 where it is fixed or outside)
     __device__ __forceinline__ float pn(const float* ps, const T* pg, int c) const {
@@ -1020,7 +1023,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
                 }
                 p1s[i] = Store<T>::ldc(P1a, a0 + i);
                 p2s[i] = Store<T>::ldc(P2a, a0 + i);
-                ws[i] = __ldcg(Wc + a0 + i);
+                ws[i] = ldw(Wc + a0 + i);
                 vs[i] = V[a0 + i];
             }
             __syncthreads();
