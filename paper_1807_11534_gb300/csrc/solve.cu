@@ -770,81 +770,94 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
 
 // ---- shared-memory-resident block state (two-phase iteration, n_inner = 1)
 //
-// When a block's pixels fit, p (both ping-pong copies), w and v of its own
-// pixels live in shared memory for the whole solve, and its neighbour table
-// is re-encoded as int16: a local index (>= 0) for a neighbour the block
-// owns, the fixed-pixel codes (-1..-3), or kNbRemote - r for the r-th entry
-// of a per-block list of the compact indices of neighbours other blocks own.
-// Neighbours the block owns are read from shared memory; only the others go
-// to L2.  Every update is still written to the global arrays, which the
-// other blocks read.  The barrier and stopping-test protocol is the one of
-// compact_iterations, so blocks on either path interleave correctly.
-constexpr int kNbRemote = -4;
+// When a block's pixels fit, the whole state of its own pixels lives in
+// shared memory for the solve, as float words:
+//   P1, P2   two regions each (the ping-pong buffers b = 0, 1) of
+//            [own pixels | one zero word | ghost words]
+//   W        [own pixels | zero word | ghost words], V [own pixels]
+// and every neighbour read is one shared-memory load at a word offset fixed
+// at the start: a neighbour the block owns is its own word, a fixed (or
+// outside) one the zero word, and one another block owns a ghost word, which
+// the block refills from the global arrays (an L2 read) at the start of the
+// phase that reads it.  p of buffer b is at offset + b x (region size), so
+// the ping-pong needs no branch.  A per-pixel byte holds the class of the
+// neighbours below and right (RD / fixed background / fixed foreground /
+// outside), whether other blocks read the pixel (then its p' and w' are also
+// written to the global arrays), and is otherwise the same arithmetic and
+// rounding as dual_one / primal_one.  The barrier and stopping-test protocol
+// is the one of compact_iterations, so blocks on either path interleave.
+enum { GK_DOWN = 0, GK_RIGHT, GK_DL, GK_UR, GK_UP, GK_LEFT };   // ghost kinds = table slots used
+constexpr uint8_t kFlExport = 16;
 
-template <typename T>
-struct SmState {
-    const int16_t* nb;   // [NB_UUR][per]
-    const int32_t* rem;  // remote compact indices
-    float* p1;           // [2][per]
-    float* p2;           // [2][per]
-    float* w;            // [per]
-    T* v;                // [per]
-    int per;
-    __device__ __forceinline__ int code(int k, int i) const { return nb[k * per + i]; }
-    __device__ __forceinline__ static bool in_rd(int c) { return c >= 0 || c <= kNbRemote; }
-    // w at a neighbour in RD
-    __device__ __forceinline__ float wn(int c, const float* Wg) const {
-        return c >= 0 ? w[c] : ldw(Wg + rem[kNbRemote - c]);
-    }
-    // p component at a neighbour (0 where it is fixed or outside)
-    __device__ __forceinline__ float pn(const float* ps, const T* pg, int c) const {
-        return c >= 0 ? ps[c] : (c <= kNbRemote ? Store<T>::ldc(pg, rem[kNbRemote - c]) : 0.f);
-    }
+struct GhostLayout {
+    int n;                 // own pixels
+    int ns1, ns2, nsw;     // region sizes (words) of P1, P2 (per buffer) and W
+    int p1, p2, w, v;      // word offsets of the regions
+    int gd, gp;            // ghosts read by the dual / by the primal
+    size_t off16, offfl, offgs, offgd, bytes;   // byte offsets of the tables
 };
 
 template <typename T>
-__device__ __forceinline__ void dual_sm(const IterParams& P, int i, int a, const SmState<T>& S, int pb,
-                                        const T* P1g, const T* P2g, const float* Wg, T* P1o, T* P2o,
-                                        uint32_t seed) {
-    const int per = S.per;
-    const int c_down = S.code(NB_DOWN, i), c_right = S.code(NB_RIGHT, i);
-    const int c_dl = S.code(NB_DOWNLEFT, i), c_ur = S.code(NB_UPRIGHT, i);
-    const float* p1c = S.p1 + pb * per;
-    const float* p2c = S.p2 + pb * per;
-    const float p1 = p1c[i], p2 = p2c[i], w0 = S.w[i];
-    const float wd = SmState<T>::in_rd(c_down) ? S.wn(c_down, Wg) : 0.f;
-    const float wr = SmState<T>::in_rd(c_right) ? S.wn(c_right, Wg) : 0.f;
-    const float p2dl = S.pn(p2c, P2g, c_dl);
-    const float p1ur = S.pn(p1c, P1g, c_ur);
+struct GhostState {
+    float* sm;             // the shared-memory words
+    const uint16_t* off;   // [6][n] word offsets (DOWN, RIGHT, DL, UR into buffer 0; UP, LEFT into buffer 0)
+    const uint8_t* fl;     // [n]
+    const int32_t* gsrc;   // [gd + gp] compact index of each ghost's pixel
+    const uint16_t* gdst;  // [gd + gp] word offset of each ghost (buffer 0 for p kinds)
+    GhostLayout L;
+    __device__ __forceinline__ T* v() const { return reinterpret_cast<T*>(sm + L.v); }
+};
+
+template <typename T>
+__device__ __forceinline__ void dual_gh(const IterParams& P, int i, int a, const GhostState<T>& S, int pb,
+                                        T* P1o, T* P2o, uint32_t seed) {
+    const GhostLayout& L = S.L;
+    float* sm = S.sm;
+    const int n = L.n;
+    const uint8_t fl = S.fl[i];
+    const int b1 = pb * L.ns1, b2 = pb * L.ns2;
+    const float p1 = sm[L.p1 + b1 + i], p2 = sm[L.p2 + b2 + i], w0 = sm[L.w + i];
+    const float wdv = sm[S.off[GK_DOWN * n + i]], wrv = sm[S.off[GK_RIGHT * n + i]];
+    const float p2dl = sm[S.off[GK_DL * n + i] + b2], p1ur = sm[S.off[GK_UR * n + i] + b1];
+    const int cd = fl & 3, cr = (fl >> 2) & 3;   // 0 RD, 1 fixed Bg, 2 fixed Fg, 3 outside
     float g1 = 0.f, g2 = 0.f;
-    if (c_down != kNbOut) g1 = (SmState<T>::in_rd(c_down) ? wd : w_fixed(p1, p2dl, c_down, P.inv_theta)) - w0;
-    if (c_right != kNbOut) g2 = (SmState<T>::in_rd(c_right) ? wr : w_fixed(p1ur, p2, c_right, P.inv_theta)) - w0;
+    if (cd != 3) g1 = (cd == 0 ? wdv : w_fixed(p1, p2dl, cd == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
+    if (cr != 3) g2 = (cr == 0 ? wrv : w_fixed(p1ur, p2, cr == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
     float q1, q2;
     chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
     const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
-    S.p1[(pb ^ 1) * per + i] = Store<T>::st_sr(P1o, a, q1, rnd);
-    S.p2[(pb ^ 1) * per + i] = Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
+    const uint32_t rnd2 = mix32(rnd ^ 0x9e3779b9u);
+    if (fl & kFlExport) {
+        q1 = Store<T>::st_sr(P1o, a, q1, rnd);
+        q2 = Store<T>::st_sr(P2o, a, q2, rnd2);
+    } else {
+        q1 = Store<T>::sr(q1, rnd);
+        q2 = Store<T>::sr(q2, rnd2);
+    }
+    sm[L.p1 + (L.ns1 - b1) + i] = q1;   // the other buffer: (1 - pb) x ns1
+    sm[L.p2 + (L.ns2 - b2) + i] = q2;
 }
 
 template <typename T>
-__device__ __forceinline__ void primal_sm(const IterParams& P, int i, int a, const SmState<T>& S, int pb,
-                                          const T* P1g, const T* P2g, const float* F, float* U, float* Wg,
-                                          bool check, bool write_u, uint32_t seed, float& du2, float& dv2) {
-    const int per = S.per;
-    const int c_up = S.code(NB_UP, i), c_left = S.code(NB_LEFT, i);
-    const float* q1c = S.p1 + pb * per;
-    const float* q2c = S.p2 + pb * per;
-    const float q1 = q1c[i], q2 = q2c[i];
-    const float vv = Store<T>::ld_rw(S.v, i) + Store<T>::vbias;
-    const float q1u = S.pn(q1c, P1g, c_up), q2l = S.pn(q2c, P2g, c_left);
+__device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, const GhostState<T>& S, int pb,
+                                          const float* F, float* U, float* Wg, bool check, bool write_u,
+                                          uint32_t seed, float& du2, float& dv2) {
+    const GhostLayout& L = S.L;
+    float* sm = S.sm;
+    const int n = L.n;
+    const int b1 = pb * L.ns1, b2 = pb * L.ns2;
+    const float q1 = sm[L.p1 + b1 + i], q2 = sm[L.p2 + b2 + i];
+    const float q1u = sm[S.off[GK_UP * n + i] + b1], q2l = sm[S.off[GK_LEFT * n + i] + b2];
+    T* V = S.v();
+    const float vv = Store<T>::ld_rw(V, i) + Store<T>::vbias;
     const float div = (q1 - q1u) + (q2 - q2l);
     const float un = fmaf(-P.theta, div, vv);
     const float vn = clamp01(un - __ldg(F + a));   // F = theta lambda f
-    const float vs = Store<T>::st_sr(S.v, i, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
+    const float vs = Store<T>::st_sr(V, i, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
                      Store<T>::vbias;
     const float wv = div - vs * P.inv_theta;
-    S.w[i] = wv;
-    Wg[a] = wv;
+    sm[L.w + i] = wv;
+    if (S.fl[i] & kFlExport) Wg[a] = wv;
     if (check) {
         const float da = un - U[a], db = vn - vv;
         du2 = fmaf(da, da, du2);
@@ -853,17 +866,33 @@ __device__ __forceinline__ void primal_sm(const IterParams& P, int i, int a, con
     if (write_u) U[a] = un;
 }
 
-// The iterations with shared-memory-resident state (n_inner = 1, after the
-// warm-start pass); same barriers and stopping test as compact_iterations.
+// Refills ghosts [g0, g1) from the global arrays: w for the neighbours below /
+// right, p of buffer pb for the others.
+template <typename T>
+__device__ __forceinline__ void fill_ghosts(const GhostState<T>& S, int g0, int g1, int pb, const T* P1g,
+                                            const T* P2g, const float* Wg, int nt) {
+    const GhostLayout& L = S.L;
+    for (int g = g0 + (int)threadIdx.x; g < g1; g += nt) {
+        const int src = S.gsrc[g], dst = S.gdst[g];
+        if (dst >= L.w) S.sm[dst] = ldw(Wg + src);
+        else if (dst >= L.p2) S.sm[dst + pb * L.ns2] = Store<T>::ldc(P2g, src);
+        else S.sm[dst + pb * L.ns1] = Store<T>::ldc(P1g, src);
+    }
+}
+
+// The iterations with shared-memory-resident state; returns false when a
+// barrier timed out, else the final iterate's buffer in *fb and iteration
+// count in *lf.
 template <typename T, int NT, int UNROLL>
-__device__ __forceinline__ bool compact_iterations_sm(const IterParams& P, const SmState<T>& S, int a0, int a1,
+__device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const GhostState<T>& S, int a0, int a1,
                                                       int iters, int check_every, double tol, int64_t stride,
                                                       T* P1a, T* P1b, T* P2a, T* P2b, const float* F,
                                                       float* U, float* Wc, double* partials, WsHeader* h,
                                                       float* ckpt, int ckpt_every, double* s_red,
-                                                      unsigned gen) {
+                                                      unsigned gen, int* fb, int* lf) {
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = NT;
+    const GhostLayout& L = S.L;
     int pb = 0;
     auto each = [&](auto&& op) {
         int a = a0 + tid;
@@ -875,35 +904,42 @@ __device__ __forceinline__ bool compact_iterations_sm(const IterParams& P, const
     };
     auto save = [&](int m) {
         float* c = ckpt + (int64_t)m * 3 * stride;
+        const T* V = S.v();
         for (int a = a0 + tid; a < a1; a += nt) {
             const int i = a - a0;
-            c[a] = S.p1[pb * S.per + i];
-            c[stride + a] = S.p2[pb * S.per + i];
-            c[2 * stride + a] = to_f(S.v[i]) + Store<T>::vbias;
+            c[a] = S.sm[L.p1 + pb * L.ns1 + i];
+            c[stride + a] = S.sm[L.p2 + pb * L.ns2 + i];
+            c[2 * stride + a] = to_f(V[i]) + Store<T>::vbias;
         }
     };
     if (ckpt) save(0);
     const int C = check_every;
+    *fb = 0;
+    *lf = iters;
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
         {
             const uint32_t seed = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
-            const T* g1 = pb ? P1b : P1a;
-            const T* g2 = pb ? P2b : P2a;
+            fill_ghosts(S, 0, L.gd, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
+            __syncthreads();
             T* o1 = pb ? P1a : P1b;
             T* o2 = pb ? P2a : P2b;
-            each([&](int a) { dual_sm(P, a - a0, a, S, pb, g1, g2, Wc, o1, o2, seed); });
+            each([&](int a) { dual_gh(P, a - a0, a, S, pb, o1, o2, seed); });
             pb ^= 1;
             if (!grid_sync(h, nblocks, gen)) return false;
-            if (it > 0 && (it % C == 0) && *(volatile int*)&h->done) return true;
+            if (it > 0 && (it % C == 0) && *(volatile int*)&h->done) {
+                *fb = pb ^ 1;   // the dual step after the stopping test wrote the other buffer
+                *lf = it;
+                return true;
+            }
         }
         const bool check = (l % C == 0) || l == iters;
         const bool write_u = check || ((l + 1) % C == 0) || l == iters;
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
-        const T* g1 = pb ? P1b : P1a;
-        const T* g2 = pb ? P2b : P2a;
-        each([&](int a) { primal_sm(P, a - a0, a, S, pb, g1, g2, F, U, Wc, check, write_u, seed, du2, dv2); });
+        fill_ghosts(S, L.gd, L.gd + L.gp, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
+        __syncthreads();
+        each([&](int a) { primal_gh(P, a - a0, a, S, pb, F, U, Wc, check, write_u, seed, du2, dv2); });
         if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);
         if (check) {
             double x = du2, y = dv2;
@@ -948,6 +984,7 @@ __device__ __forceinline__ bool compact_iterations_sm(const IterParams& P, const
             __syncthreads();
         }
     }
+    *fb = pb;
     return true;
 }
 
@@ -971,33 +1008,55 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
     const int fuse = n_inner == 1 && per <= kFusePerThread * NT;
     const int rows = fuse ? NB_COUNT : NB_UUR;
     if (n_inner == 1 && !fuse) {
-        // shared-memory-resident state if this block's pixels and its list of
-        // neighbours owned by other blocks fit (decided per block: both paths
-        // keep the global arrays current and pass the same barriers)
-        __shared__ int s_r;
-        if (tid == 0) s_r = 0;
+        // shared-memory-resident state if this block's pixels and its ghosts
+        // fit (decided per block: both paths keep the global arrays that
+        // other blocks read current and pass the same barriers)
+        __shared__ int s_cnt[8];   // ghosts per kind, then running slots
+        if (tid < 8) s_cnt[tid] = 0;
         __syncthreads();
-        int r = 0;
-        for (int i = tid; i < a1 - a0; i += nt)
-            for (int k = 0; k < NB_UUR; ++k) {
-                const int m = __ldg(nb + k * stride + a0 + i);
-                r += (m >= 0 && (m < a0 || m >= a1)) ? 1 : 0;
-            }
-        atomicAdd(&s_r, r);
+        const int nown = max(a1 - a0, 0);
+        // table slots in ghost-kind order
+        const int slot_of[6] = {NB_DOWN, NB_RIGHT, NB_DOWNLEFT, NB_UPRIGHT, NB_UP, NB_LEFT};
+        {
+            int c[6] = {0, 0, 0, 0, 0, 0};
+            for (int i = tid; i < nown; i += nt)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const int m = __ldg(nb + slot_of[k] * stride + a0 + i);
+                    c[k] += (m >= 0 && (m < a0 || m >= a1)) ? 1 : 0;
+                }
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if (c[k]) atomicAdd(&s_cnt[k], c[k]);
+        }
         __syncthreads();
-        const int nrem = s_r;
-        const size_t off_p1 = ((size_t)2 * NB_UUR * per + 15) & ~(size_t)15;
-        const size_t off_p2 = off_p1 + (size_t)8 * per;
-        const size_t off_w = off_p2 + (size_t)8 * per;
-        const size_t off_v = off_w + (size_t)4 * per;
-        const size_t off_rem = off_v + (size_t)4 * per;
-        if (off_rem + (size_t)4 * nrem <= compact_smem(NT) && nrem <= 32000) {
-            int16_t* nb16 = reinterpret_cast<int16_t*>(c_smem);
-            float* p1s = reinterpret_cast<float*>(c_smem + off_p1);
-            float* p2s = reinterpret_cast<float*>(c_smem + off_p2);
-            float* ws = reinterpret_cast<float*>(c_smem + off_w);
-            T* vs = reinterpret_cast<T*>(c_smem + off_v);
-            int32_t* rem = reinterpret_cast<int32_t*>(c_smem + off_rem);
+        GhostLayout L{};
+        L.n = nown;
+        const int g_w = s_cnt[GK_DOWN] + s_cnt[GK_RIGHT];
+        const int g_p1 = s_cnt[GK_UR] + s_cnt[GK_UP];
+        const int g_p2 = s_cnt[GK_DL] + s_cnt[GK_LEFT];
+        L.gd = s_cnt[GK_DOWN] + s_cnt[GK_RIGHT] + s_cnt[GK_DL] + s_cnt[GK_UR];
+        L.gp = s_cnt[GK_UP] + s_cnt[GK_LEFT];
+        L.ns1 = nown + 1 + g_p1;
+        L.ns2 = nown + 1 + g_p2;
+        L.nsw = nown + 1 + g_w;
+        L.p1 = 0;
+        L.p2 = 2 * L.ns1;
+        L.w = L.p2 + 2 * L.ns2;
+        L.v = L.w + L.nsw;
+        const int words = L.v + (int)((sizeof(T) * nown + 3) / 4);
+        L.off16 = (size_t)4 * words;
+        L.offfl = L.off16 + (size_t)2 * 6 * nown;
+        L.offgs = (L.offfl + nown + 3) & ~(size_t)3;
+        L.offgd = L.offgs + (size_t)4 * (L.gd + L.gp);
+        L.bytes = L.offgd + (size_t)2 * (L.gd + L.gp);
+        __syncthreads();   // every thread has read the counts before they become slot cursors
+        if (L.bytes <= compact_smem(NT) && words < 65536) {
+            float* sm = reinterpret_cast<float*>(c_smem);
+            uint16_t* off = reinterpret_cast<uint16_t*>(c_smem + L.off16);
+            uint8_t* flg = reinterpret_cast<uint8_t*>(c_smem + L.offfl);
+            int32_t* gsrc = reinterpret_cast<int32_t*>(c_smem + L.offgs);
+            uint16_t* gdst = reinterpret_cast<uint16_t*>(c_smem + L.offgd);
             unsigned gen0 = 0u;
             if (warm) {   // w of the warm-start iterate, from the global arrays (as the other path)
                 float d0 = 0.f, d1 = 0.f;
@@ -1006,35 +1065,74 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
                     primal_one(P, a, O, P1a, P2a, U, Wc, true, false, false, 0u, d0, d1);
                 if (!grid_sync(h, nblocks, gen0)) return;
             }
-            if (tid == 0) s_r = 0;
-            __syncthreads();
-            for (int i = tid; i < a1 - a0; i += nt) {
-                for (int k = 0; k < NB_UUR; ++k) {
-                    const int m = __ldg(nb + k * stride + a0 + i);
-                    int c = m;
-                    if (m >= a0 && m < a1) {
-                        c = m - a0;
-                    } else if (m >= 0) {
-                        const int slot = atomicAdd(&s_r, 1);
-                        rem[slot] = m;
-                        c = kNbRemote - slot;
-                    }
-                    nb16[k * per + i] = (int16_t)c;
-                }
-                p1s[i] = Store<T>::ldc(P1a, a0 + i);
-                p2s[i] = Store<T>::ldc(P2a, a0 + i);
-                ws[i] = ldw(Wc + a0 + i);
-                vs[i] = V[a0 + i];
+            // ghost slots: dual kinds first (down, right, dl, ur), then primal (up, left)
+            if (tid == 0) {
+                int acc = 0;
+                for (int k = 0; k < 6; ++k) { const int c = s_cnt[k]; s_cnt[k] = acc; acc += c; }
+            }
+            // zero words
+            if (tid == 0) {
+                sm[L.p1 + nown] = 0.f; sm[L.p1 + L.ns1 + nown] = 0.f;
+                sm[L.p2 + nown] = 0.f; sm[L.p2 + L.ns2 + nown] = 0.f;
+                sm[L.w + nown] = 0.f;
             }
             __syncthreads();
-            const SmState<T> S{nb16, rem, p1s, p2s, ws, vs, per};
+            // per-kind region base (buffer 0) and running ghost index within the region
+            __shared__ int s_reg[3];   // ghosts placed so far in the W, P1, P2 ghost areas
+            if (tid < 3) s_reg[tid] = 0;
+            __syncthreads();
+            T* Vs = reinterpret_cast<T*>(sm + L.v);
+            for (int i = tid; i < nown; i += nt) {
+                const int a = a0 + i;
+                uint8_t f = 0;
+                bool exported = false;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const int m = __ldg(nb + slot_of[k] * stride + a);
+                    // region of this kind: W (down, right), P1 (ur, up), P2 (dl, left)
+                    const int reg = (k == GK_DOWN || k == GK_RIGHT) ? 0 : (k == GK_UR || k == GK_UP) ? 1 : 2;
+                    const int base = reg == 0 ? L.w : reg == 1 ? L.p1 : L.p2;
+                    int o;
+                    if (m >= a0 && m < a1) {
+                        o = base + (m - a0);
+                    } else if (m >= 0) {
+                        exported = true;
+                        const int slot = atomicAdd(&s_cnt[k], 1);          // position in the ghost lists
+                        const int gi = atomicAdd(&s_reg[reg], 1);          // word in the region's ghost area
+                        o = base + nown + 1 + gi;
+                        gsrc[slot] = m;
+                        gdst[slot] = (uint16_t)o;
+                    } else {
+                        o = base + nown;                                   // the zero word
+                    }
+                    off[k * nown + i] = (uint16_t)o;
+                    if (k == GK_DOWN) f |= (uint8_t)(m >= 0 ? 0 : m == kNbBg ? 1 : m == kNbFg ? 2 : 3);
+                    if (k == GK_RIGHT) f |= (uint8_t)((m >= 0 ? 0 : m == kNbBg ? 1 : m == kNbFg ? 2 : 3) << 2);
+                }
+                flg[i] = (uint8_t)(f | (exported ? kFlExport : 0));
+                sm[L.p1 + i] = Store<T>::ldc(P1a, a);
+                sm[L.p2 + i] = Store<T>::ldc(P2a, a);
+                sm[L.w + i] = ldw(Wc + a);
+                Vs[i] = V[a];
+            }
+            __syncthreads();
+            const GhostState<T> S{sm, off, flg, gsrc, gdst, L};
+            int fb = 0, lf = iters;
             // the barrier generation continues from the warm-start barrier
-            if (!compact_iterations_sm<T, NT, UNROLL>(P, S, a0, a1, iters, check_every, tol, stride, P1a, P1b,
+            if (!compact_iterations_gh<T, NT, UNROLL>(P, S, a0, a1, iters, check_every, tol, stride, P1a, P1b,
                                                        P2a, P2b, F, U, Wc, partials, h, ckpt, ckpt_every,
-                                                       s_red, gen0))
+                                                       s_red, gen0, &fb, &lf))
                 return;
             __syncthreads();
-            for (int i = tid; i < a1 - a0; i += nt) V[a0 + i] = vs[i];
+            // the final iterate: v, and p of every own pixel (only exported
+            // pixels were kept current in the global arrays)
+            T* G1 = (lf & 1) ? P1b : P1a;
+            T* G2 = (lf & 1) ? P2b : P2a;
+            for (int i = tid; i < nown; i += nt) {
+                V[a0 + i] = Vs[i];
+                Store<T>::st(G1, a0 + i, sm[L.p1 + fb * L.ns1 + i]);
+                Store<T>::st(G2, a0 + i, sm[L.p2 + fb * L.ns2 + i]);
+            }
             return;
         }
     }
