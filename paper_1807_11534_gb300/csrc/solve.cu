@@ -1557,24 +1557,25 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
                          segp1(m + 1), segp2(m + 1), 0u);
             if (!grid_sync(h, nblocks, gen)) return;
             for (int a = a0 + tid; a < a1; a += nt) {
-                segv(m + 1)[a] = segv(m)[a];    // primal_one updates v in place
-            }
-            for (int a = a0 + tid; a < a1; a += nt)
+                segv(m + 1)[a] = segv(m)[a];    // primal_one updates v in place (same thread, no barrier)
                 primal_one(P, a, Own<float, false>{nb, stride, segv(m + 1), F, 0}, segp1(m + 1), segp2(m + 1),
                            nullptr, segw(m + 1), false, false, false, 0u, d0, d1);
-            if (!grid_sync(h, nblocks, gen)) return;
-        }
-        // ---- walk back through the segment
-        for (int m = M - 1; m >= 0; --m) {
-            const bool last = n0 + m + 1 == iters;
-            // A: clip, u^{n+1}
-            for (int a = a0 + tid; a < a1; a += nt) {
-                const float vn = segv(m + 1)[a];
-                const float sb = (vn > 0.f && vn < 1.f) ? A.vb[a] : 0.f;
-                A.ub[a] = sb + (last ? A.gu[a] : 0.f);
-                A.fb[a] -= sb;
             }
             if (!grid_sync(h, nblocks, gen)) return;
+        }
+        // ---- walk back through the segment.  Phase A (clip, u^{n+1}) only
+        // touches the pixel itself, so it runs at the end of phase C of the
+        // step before (and here for the first step of the segment).
+        auto phase_a = [&](int m, int a) {
+            const bool last = n0 + m + 1 == iters;
+            const float vn = segv(m + 1)[a];
+            const float sb = (vn > 0.f && vn < 1.f) ? A.vb[a] : 0.f;
+            A.ub[a] = sb + (last ? A.gu[a] : 0.f);
+            A.fb[a] -= sb;
+        };
+        for (int a = a0 + tid; a < a1; a += nt) phase_a(M - 1, a);
+        if (!grid_sync(h, nblocks, gen)) return;
+        for (int m = M - 1; m >= 0; --m) {
             // B: qbar = pbar + theta grad ubar, the fixed-point step
             for (int a = a0 + tid; a < a1; a += nt) {
                 const int n_down = __ldg(nb + NB_DOWN * stride + a);
@@ -1628,6 +1629,8 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
                 A.p1b[a] = A.pd1[a] - (n_down != kNbOut ? wbd - wb0 : 0.f);
                 A.p2b[a] = A.pd2[a] - (n_right != kNbOut ? wbr - wb0 : 0.f);
                 A.vb[a] = A.ub[a] - wb0 * P.inv_theta;
+                // the next step's phase A: no other pixel's phase C reads ub
+                if (m > 0) phase_a(m - 1, a);
             }
             if (!grid_sync(h, nblocks, gen)) return;
         }

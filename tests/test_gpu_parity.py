@@ -327,22 +327,27 @@ def _crop_check(orc, f_full, out_u, delta, lam, K, centres):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("mode", ["compact", "dense", "tiled"])
-def test_full_size_2048_ds_sampled(orc, mode):
+@pytest.mark.parametrize("mode,delta", [("compact", 0.1), ("compact", 0.2), ("dense", 0.1), ("tiled", 0.1),
+                                        ("tiled", 0.2)])
+def test_full_size_2048_ds_sampled(orc, mode, delta):
     """2048x2048 distance-selective workload in the benchmark's launch
     configuration: K iterations on the GPU, then the oracle on crops of
     radius 2K+4 around sampled pixels (the iteration's domain of dependence
-    grows by 2 pixels per iteration, so the crop centre is exact)."""
+    grows by 2 pixels per iteration, so the crop centre is exact).  At
+    delta = 0.1 (237K RD pixels) the compact solver takes its fused
+    iteration, at 0.2 (863K, the benchmark's delta) the two-phase iteration
+    with shared-memory state, ghost words at block borders, and the final
+    write-back of pixels no other block reads."""
     seg = seg_mod()
     P = synth.ellipses_ds(seed=0, H=2048, W=2048)
     c1, c2 = orc.class_means(P.z, P.label)
     _, f = orc.fitting(P.z, c1, c2, P.markers, P.gamma)
-    K, delta, lam = 30, 0.1, 2.0
+    K, lam = 30, 2.0
     out = run_gpu(f, delta=delta, lam=lam, iters=K, mode=mode, tile_h=16)
     reg = orc.domain(f, delta)
     rng = np.random.default_rng(0)
     act = np.argwhere(reg == 2)
-    pick = act[rng.choice(len(act), 12, replace=False)]
+    pick = act[rng.choice(len(act), 32, replace=False)]
     centres = [tuple(x) for x in pick] + [(0, 0), (2047, 2047), (0, 1500), (2047, 3)]
     assert _crop_check(orc, f, out["u"], delta, lam, K, centres) <= TOL_U32
     # invariants over the whole image
@@ -350,6 +355,25 @@ def test_full_size_2048_ds_sampled(orc, mode):
     assert out["v"].min() >= 0 and out["v"].max() <= 1
     fixed = reg != 2
     np.testing.assert_array_equal(out["u"][fixed], (reg[fixed] == 1).astype(np.float64))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("delta", [0.1, 0.2, 0.3])
+def test_compact_matches_dense_on_the_whole_image(orc, delta):
+    """Every pixel of the 2048x2048 workload: the compact solver (fused
+    iteration at delta = 0.1, shared-memory state with ghost words at 0.2,
+    global-memory neighbour table at 0.3) against the dense solver run on the
+    same restricted domain, itself checked against the oracle above; both
+    are float32 iterations of the same steps."""
+    P = synth.ellipses_ds(seed=0, H=2048, W=2048)
+    c1, c2 = orc.class_means(P.z, P.label)
+    _, f = orc.fitting(P.z, c1, c2, P.markers, P.gamma)
+    K, lam = 40, 2.0
+    oc = run_gpu(f, delta=delta, lam=lam, iters=K, mode="compact", tile_h=16)
+    od = run_gpu(f, delta=delta, lam=lam, iters=K, mode="dense", tile_h=16)
+    for k in ("u", "v", "p1", "p2"):
+        assert np.max(np.abs(oc[k] - od[k])) <= TOL_U32, k
+    np.testing.assert_allclose(oc["stats"][1:3], od["stats"][1:3], rtol=1e-3)
 
 
 @pytest.mark.slow
