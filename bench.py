@@ -89,6 +89,25 @@ def workload_config(args, P, delta, A, tile_h):
             "tile_h": tile_h, "l2": "flushed between steps (256 MiB write)"}
 
 
+# ------------------------------------------------------------------ ranks
+
+def aggregate(units, ms, world):
+    """Whole-job figures over the ranks (replicas, no collective on the data
+    path): the units all ranks processed, divided by the slowest rank's time.
+    Returns (value in units per second / 1e6, max time in ms)."""
+    if world <= 1:
+        return units / (ms * 1e-3) / 1e6, ms
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return float(u.item()) / (ms_max * 1e-3) / 1e6, ms_max
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -589,13 +608,9 @@ def main():
         except OSError:
             pass
         peak = float(peaks.get("hbm_gbs", 6800.0))
-        ms = r["ms"]
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        value, ms = aggregate(r["A"] * r["iters"], r["ms"], world)
         line = {"metric": "active Mpixel-iters/s and % HBM roofline (batched restricted solve)",
-                "value": r["A"] * r["iters"] * world / (ms * 1e-3) / 1e6,
+                "value": value,
                 "unit": "active Mpixel-iter/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
@@ -618,12 +633,7 @@ def main():
 
     r = run_ours(args, rank, world)
     import torch
-    ms_r = r["ms_r"]
-    if world > 1:
-        t = torch.tensor([ms_r], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_r = float(t.item())
-    value = r["A"] * r["iters"] * world / (ms_r * 1e-3) / 1e6
+    value, ms_r = aggregate(r["A"] * r["iters"], r["ms_r"], world)
     full_value = r["A_full"] * r["iters"] / (r["ms_f"] * 1e-3) / 1e6
     peaks = {}
     try:

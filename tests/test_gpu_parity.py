@@ -377,6 +377,25 @@ def test_compact_matches_dense_on_the_whole_image(orc, delta):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_16bit_storage_on_the_shared_memory_path(orc, storage):
+    """16-bit p, v on the benchmark image at its delta (0.2: the two-phase
+    iteration with shared-memory state) against float32 storage, with the
+    bounds of the small-image 16-bit test."""
+    P = synth.ellipses_ds(seed=0, H=2048, W=2048)
+    c1, c2 = orc.class_means(P.z, P.label)
+    _, f = orc.fitting(P.z, c1, c2, P.markers, P.gamma)
+    K, lam = 200, 2.0
+    o32 = run_gpu(f, delta=0.2, lam=lam, iters=K, mode="compact", tile_h=16)
+    o16 = run_gpu(f, delta=0.2, lam=lam, iters=K, mode="compact", tile_h=16, storage=storage)
+    d = np.abs(o16["u"] - o32["u"])
+    assert d.max() <= (1e-2 if storage == "f16" else 4e-2), d.max()
+    assert d.mean() <= 2e-3
+    assert np.mean((o16["u"] > 0.5) != (o32["u"] > 0.5)) <= 1e-3
+    assert o16["v"].min() >= 0 and o16["v"].max() <= 1
+
+
+@pytest.mark.slow
 def test_full_size_4096_storage_sampled(orc):
     """4096x4096 polygons, 16-bit storage against float32 storage and the
     oracle on crops."""
