@@ -265,6 +265,7 @@ def run_ours(args, rank, world):
     ms_f = timed(g_f)
     R.check_status()
     F.check_status()
+    smem_blocks = int(R.stats[6].item())   # blocks of the timed solve that held their state in shared memory
     e1_final = float(R.errors(R.u, F.u)[0].item())
     e2_final = float(R.err_out[1].item())
 
@@ -324,7 +325,7 @@ def run_ours(args, rank, world):
 
     res = dict(ms_r=float(np.mean(ms_r)), ms_f=float(np.mean(ms_f)), A=A, A_full=A_full,
                iters=iters, delta=chosen, e1s=e1s, e1=e1_final, e2=e2_final,
-               launches=int(launches), clocks=clk.summary(), t_iter_r=t_iter_r,
+               launches=int(launches), clocks=clk.summary(), t_iter_r=t_iter_r, smem_blocks=smem_blocks,
                t_iter_f=t_iter_f, ach_r=ach_r, ach_f=ach_f, e2e_ms=float(np.mean(t_e2e)),
                h2d=h2d, d2h=d2h, P=P, tile_h=th)
     return res
@@ -655,7 +656,8 @@ def main():
                      "traffic_note": "ncu DRAM bytes per iteration; the compacted state is "
                                      "L2-resident across iterations",
                      "bytes_per_active_iter": BYTES_PER_ACTIVE_ITER[args.storage],
-                     "us_per_iter": r["t_iter_r"] * 1e3, "peak_source": peak_src},
+                     "us_per_iter": r["t_iter_r"] * 1e3, "peak_source": peak_src,
+                     "blocks_with_state_in_shared_memory": r["smem_blocks"]},
         "full_domain": {"value": full_value, "unit": "active Mpixel-iter/s", "ms_per_step": r["ms_f"],
                         "kernel": "k_step_dense", "us_per_iter": r["t_iter_f"] * 1e3,
                         "achieved_gbs": r["ach_f"], "frac": r["ach_f"] / peak},

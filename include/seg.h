@@ -165,7 +165,9 @@ seg_status seg_build_domain(const float* f, int H, int W, int ld,
  * and returns INVALID_ARG when sweep * n_inner > 8.
  *   stats         out double[8] (device): [0] iterations run, [1] last
  *                 ||du||, [2] last ||dv|| (from the last check), [3] n_active,
- *                 [4] n_tiles, [5] iteration of the last check.
+ *                 [4] n_tiles, [5] iteration of the last check, [6] compact
+ *                 mode: blocks of the persistent solver that kept their
+ *                 pixels' state in shared memory (diagnostic).
  * Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA on the host; CAPACITY (compact
  * state too small) in the status word. */
 seg_status seg_solve(const float* f, int H, int W, int ld,

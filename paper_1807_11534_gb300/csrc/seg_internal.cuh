@@ -69,6 +69,7 @@ struct WsHeader {
     // the ping-pong buffer that holds the final state
     int tb_ticket[4];
     int tb_buf;
+    int n_smem_blocks;   // compact solver: blocks that held their state in shared memory
     // grid barrier of the persistent solvers: monotonic arrival counter, on
     // its own cache line
     alignas(128) unsigned bar_count;

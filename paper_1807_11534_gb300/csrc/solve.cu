@@ -418,7 +418,7 @@ __device__ __forceinline__ float w_fixed(float p_in_1, float p_in_2, int code, f
 // read, and v is written back at the end.
 constexpr int kPersistThreads = 512;
 // dynamic shared memory of the persistent solver: one or two blocks per SM
-constexpr size_t compact_smem(int nt) { return nt == 1024 ? 220 * 1024 : 110 * 1024; }
+constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 110 * 1024; }
 constexpr int kCompactThreads = 1024;   // one block per SM
 constexpr int kCompactUnroll = 4;       // pixels per thread in flight in the two-phase iteration
 constexpr int kFusePerThread = 3;       // fused iteration up to this many pixels per thread
@@ -787,14 +787,18 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
 // rounding as dual_one / primal_one.  The barrier and stopping-test protocol
 // is the one of compact_iterations, so blocks on either path interleave.
 enum { GK_DOWN = 0, GK_RIGHT, GK_DL, GK_UR, GK_UP, GK_LEFT };   // ghost kinds = table slots used
-constexpr uint8_t kFlExport = 16;
+constexpr uint8_t kFlExport = 16;       // other blocks read this pixel
+constexpr uint8_t kFlDualGhost = 32;    // its dual step reads a ghost word
+constexpr uint8_t kFlPrimalGhost = 64;  // its primal step reads a ghost word
+constexpr int kGhostRegs = 2;           // ghosts per thread carried in registers while the interior runs
 
 struct GhostLayout {
     int n;                 // own pixels
     int ns1, ns2, nsw;     // region sizes (words) of P1, P2 (per buffer) and W
     int p1, p2, w, v;      // word offsets of the regions
     int gd, gp;            // ghosts read by the dual / by the primal
-    size_t off16, offfl, offgs, offgd, bytes;   // byte offsets of the tables
+    int nbd, nbp;          // pixels whose dual / primal step reads a ghost
+    size_t off16, offfl, offgs, offgd, offbd, offbp, bytes;   // byte offsets of the tables
 };
 
 template <typename T>
@@ -804,6 +808,8 @@ struct GhostState {
     const uint8_t* fl;     // [n]
     const int32_t* gsrc;   // [gd + gp] compact index of each ghost's pixel
     const uint16_t* gdst;  // [gd + gp] word offset of each ghost (buffer 0 for p kinds)
+    const uint16_t* bd;    // [nbd] pixels whose dual step reads a ghost
+    const uint16_t* bp;    // [nbp] pixels whose primal step reads a ghost
     GhostLayout L;
     __device__ __forceinline__ T* v() const { return reinterpret_cast<T*>(sm + L.v); }
 };
@@ -880,6 +886,38 @@ __device__ __forceinline__ void fill_ghosts(const GhostState<T>& S, int g0, int 
     }
 }
 
+// Overlapped refill: each thread loads up to kGhostRegs ghosts of [g0, g1)
+// into registers (the loads stay in flight), and stores them once the
+// interior pixels are done.
+template <typename T>
+struct GhostRegs {
+    float x[kGhostRegs];
+    __device__ __forceinline__ void load(const GhostState<T>& S, int g0, int g1, int pb, const T* P1g,
+                                         const T* P2g, const float* Wg, int nt) {
+        const GhostLayout& L = S.L;
+#pragma unroll
+        for (int j = 0; j < kGhostRegs; ++j) {
+            const int g = g0 + (int)threadIdx.x + j * nt;
+            x[j] = 0.f;
+            if (g < g1) {
+                const int src = S.gsrc[g], dst = S.gdst[g];
+                x[j] = dst >= L.w ? ldw(Wg + src) : dst >= L.p2 ? Store<T>::ldc(P2g, src) : Store<T>::ldc(P1g, src);
+            }
+        }
+    }
+    __device__ __forceinline__ void store(const GhostState<T>& S, int g0, int g1, int pb, int nt) const {
+        const GhostLayout& L = S.L;
+#pragma unroll
+        for (int j = 0; j < kGhostRegs; ++j) {
+            const int g = g0 + (int)threadIdx.x + j * nt;
+            if (g < g1) {
+                const int dst = S.gdst[g];
+                S.sm[dst >= L.w ? dst : dst >= L.p2 ? dst + pb * L.ns2 : dst + pb * L.ns1] = x[j];
+            }
+        }
+    }
+};
+
 // The iterations with shared-memory-resident state; returns false when a
 // barrier timed out, else the final iterate's buffer in *fb and iteration
 // count in *lf.
@@ -893,6 +931,8 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = NT;
     const GhostLayout& L = S.L;
+    // every ghost of a phase fits in the threads' registers (uniform in the block)
+    const bool overlap = L.gd <= kGhostRegs * NT && L.gp <= kGhostRegs * NT;
     int pb = 0;
     auto each = [&](auto&& op) {
         int a = a0 + tid;
@@ -920,11 +960,22 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
         const int l = it + 1;
         {
             const uint32_t seed = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
-            fill_ghosts(S, 0, L.gd, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
-            __syncthreads();
             T* o1 = pb ? P1a : P1b;
             T* o2 = pb ? P2a : P2b;
-            each([&](int a) { dual_gh(P, a - a0, a, S, pb, o1, o2, seed); });
+            if (overlap) {   // ghosts in flight while the interior pixels update
+                GhostRegs<T> R;
+                R.load(S, 0, L.gd, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
+                each([&](int a) {
+                    if (!(S.fl[a - a0] & kFlDualGhost)) dual_gh(P, a - a0, a, S, pb, o1, o2, seed);
+                });
+                R.store(S, 0, L.gd, pb, nt);
+                __syncthreads();
+                for (int e = tid; e < L.nbd; e += nt) dual_gh(P, S.bd[e], a0 + S.bd[e], S, pb, o1, o2, seed);
+            } else {
+                fill_ghosts(S, 0, L.gd, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
+                __syncthreads();
+                each([&](int a) { dual_gh(P, a - a0, a, S, pb, o1, o2, seed); });
+            }
             pb ^= 1;
             if (!grid_sync(h, nblocks, gen)) return false;
             if (it > 0 && (it % C == 0) && *(volatile int*)&h->done) {
@@ -937,10 +988,26 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
         const bool write_u = check || ((l + 1) % C == 0) || l == iters;
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
-        fill_ghosts(S, L.gd, L.gd + L.gp, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
-        __syncthreads();
-        each([&](int a) { primal_gh(P, a - a0, a, S, pb, F, U, Wc, check, write_u, seed, du2, dv2); });
-        if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);
+        if (overlap) {
+            GhostRegs<T> R;
+            R.load(S, L.gd, L.gd + L.gp, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
+            each([&](int a) {
+                if (!(S.fl[a - a0] & kFlPrimalGhost))
+                    primal_gh(P, a - a0, a, S, pb, F, U, Wc, check, write_u, seed, du2, dv2);
+            });
+            R.store(S, L.gd, L.gd + L.gp, pb, nt);
+            __syncthreads();
+            for (int e = tid; e < L.nbp; e += nt)
+                primal_gh(P, S.bp[e], a0 + S.bp[e], S, pb, F, U, Wc, check, write_u, seed, du2, dv2);
+        } else {
+            fill_ghosts(S, L.gd, L.gd + L.gp, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
+            __syncthreads();
+            each([&](int a) { primal_gh(P, a - a0, a, S, pb, F, U, Wc, check, write_u, seed, du2, dv2); });
+        }
+        if (ckpt && l % ckpt_every == 0 && l < iters) {
+            __syncthreads();   // boundary pixels were updated by other threads
+            save(l / ckpt_every);
+        }
         if (check) {
             double x = du2, y = dv2;
             for (int d = 16; d > 0; d >>= 1) {
@@ -1049,7 +1116,10 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
         L.offfl = L.off16 + (size_t)2 * 6 * nown;
         L.offgs = (L.offfl + nown + 3) & ~(size_t)3;
         L.offgd = L.offgs + (size_t)4 * (L.gd + L.gp);
-        L.bytes = L.offgd + (size_t)2 * (L.gd + L.gp);
+        // pixels whose dual / primal step reads a ghost: at most one per ghost
+        L.offbd = L.offgd + (size_t)2 * (L.gd + L.gp);
+        L.offbp = L.offbd + (size_t)2 * L.gd;
+        L.bytes = L.offbp + (size_t)2 * L.gp;
         __syncthreads();   // every thread has read the counts before they become slot cursors
         if (L.bytes <= compact_smem(NT) && words < 65536) {
             float* sm = reinterpret_cast<float*>(c_smem);
@@ -1057,6 +1127,8 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
             uint8_t* flg = reinterpret_cast<uint8_t*>(c_smem + L.offfl);
             int32_t* gsrc = reinterpret_cast<int32_t*>(c_smem + L.offgs);
             uint16_t* gdst = reinterpret_cast<uint16_t*>(c_smem + L.offgd);
+            uint16_t* lbd = reinterpret_cast<uint16_t*>(c_smem + L.offbd);
+            uint16_t* lbp = reinterpret_cast<uint16_t*>(c_smem + L.offbp);
             unsigned gen0 = 0u;
             if (warm) {   // w of the warm-start iterate, from the global arrays (as the other path)
                 float d0 = 0.f, d1 = 0.f;
@@ -1085,7 +1157,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
             for (int i = tid; i < nown; i += nt) {
                 const int a = a0 + i;
                 uint8_t f = 0;
-                bool exported = false;
+                bool exported = false, gdual = false, gprimal = false;
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
                     const int m = __ldg(nb + slot_of[k] * stride + a);
@@ -1097,6 +1169,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
                         o = base + (m - a0);
                     } else if (m >= 0) {
                         exported = true;
+                        if (k < GK_UP) gdual = true; else gprimal = true;
                         const int slot = atomicAdd(&s_cnt[k], 1);          // position in the ghost lists
                         const int gi = atomicAdd(&s_reg[reg], 1);          // word in the region's ghost area
                         o = base + nown + 1 + gi;
@@ -1109,14 +1182,38 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
                     if (k == GK_DOWN) f |= (uint8_t)(m >= 0 ? 0 : m == kNbBg ? 1 : m == kNbFg ? 2 : 3);
                     if (k == GK_RIGHT) f |= (uint8_t)((m >= 0 ? 0 : m == kNbBg ? 1 : m == kNbFg ? 2 : 3) << 2);
                 }
-                flg[i] = (uint8_t)(f | (exported ? kFlExport : 0));
+                flg[i] = (uint8_t)(f | (exported ? kFlExport : 0) | (gdual ? kFlDualGhost : 0) |
+                                   (gprimal ? kFlPrimalGhost : 0));
                 sm[L.p1 + i] = Store<T>::ldc(P1a, a);
                 sm[L.p2 + i] = Store<T>::ldc(P2a, a);
                 sm[L.w + i] = ldw(Wc + a);
                 Vs[i] = V[a];
             }
             __syncthreads();
-            const GhostState<T> S{sm, off, flg, gsrc, gdst, L};
+            // stable lists of the pixels that read ghosts
+            __shared__ int s_nb[2];
+            if (tid < 32) {
+                int cd = 0, cp = 0;
+                for (int b = 0; b < nown; b += 32) {
+                    const int i = b + tid;
+                    const unsigned f = i < nown ? flg[i] : 0u;
+                    const unsigned md = __ballot_sync(0xffffffffu, f & kFlDualGhost);
+                    const unsigned mp = __ballot_sync(0xffffffffu, f & kFlPrimalGhost);
+                    if (f & kFlDualGhost) lbd[cd + __popc(md & lanemask_lt(tid))] = (uint16_t)i;
+                    if (f & kFlPrimalGhost) lbp[cp + __popc(mp & lanemask_lt(tid))] = (uint16_t)i;
+                    cd += __popc(md);
+                    cp += __popc(mp);
+                }
+                if (tid == 0) {
+                    s_nb[0] = cd;
+                    s_nb[1] = cp;
+                    atomicAdd(&h->n_smem_blocks, 1);
+                }
+            }
+            __syncthreads();
+            L.nbd = s_nb[0];
+            L.nbp = s_nb[1];
+            const GhostState<T> S{sm, off, flg, gsrc, gdst, lbd, lbp, L};
             int fb = 0, lf = iters;
             // the barrier generation continues from the warm-start barrier
             if (!compact_iterations_gh<T, NT, UNROLL>(P, S, a0, a1, iters, check_every, tol, stride, P1a, P1b,
@@ -1203,6 +1300,7 @@ __global__ void k_solve_begin(WsHeader* h) {
     h->dv = 0.0;
     for (int k = 0; k < 4; ++k) h->tb_ticket[k] = 0;
     h->tb_buf = 0;
+    h->n_smem_blocks = 0;
 }
 
 // Section 4 stopping test after iteration l: sums the n partial pairs in a
@@ -1242,7 +1340,7 @@ __global__ void k_solve_end(const WsHeader* __restrict__ h, const int32_t* __res
     stats[3] = counts[1];
     stats[4] = counts[0];
     stats[5] = h->last_check;
-    stats[6] = 0.0;
+    stats[6] = h->n_smem_blocks;
     stats[7] = 0.0;
 }
 
