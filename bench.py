@@ -37,10 +37,11 @@ DELTA_SWEEP = (0.02, 0.05, 0.1, 0.2, 0.3, 0.5)
 BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + write p1,p2,v
 # DRAM bytes (read + write) per iteration of k_solve_compact, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a 50-iteration
-# launch / 50) of `bench.py --profile --iters 50` (2048x2048, delta = 0.2,
-# float32), summarised in profiles/k_solve_compact_ds2048.md.  The compacted
-# state stays in L2, so this is far below the algorithmic bytes.
-COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (136960 + 14904320) / 50}
+# launch / 50) of `bench.py --profile --profile-tiled --iters 50` (2048x2048,
+# delta = 0.2, float32), summarised in profiles/k_solve_compact_ds2048.md.
+# The iteration state is held on chip, so this is far below the algorithmic
+# bytes.
+COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (1281280 + 5902080) / 50}
 
 
 def parse():
@@ -653,8 +654,8 @@ def main():
                      "achieved": r["ach_r"],
                      "peak": peak, "unit": "GB/s", "frac": r["ach_r"] / peak,
                      "traffic": COMPACT_DRAM_BYTES_PER_ITER.get((args.workload, args.storage)),
-                     "traffic_note": "ncu DRAM bytes per iteration; the compacted state is "
-                                     "L2-resident across iterations",
+                     "traffic_note": "ncu DRAM bytes per iteration; the iteration state is held "
+                                     "in shared memory and L2 across iterations",
                      "bytes_per_active_iter": BYTES_PER_ACTIVE_ITER[args.storage],
                      "us_per_iter": r["t_iter_r"] * 1e3, "peak_source": peak_src,
                      "blocks_with_state_in_shared_memory": r["smem_blocks"]},
