@@ -10,21 +10,24 @@
 // row / column; div = -grad^T).  The stopping test of Section 4 compares
 // max(||u'-u||, ||v'-v||) with tol every check_every iterations.
 //
-// Two implementations:
+// Two implementations (SEG_MODE_TILED, temporal blocking, is in tiled.cu):
 //  * dense   : state in [H][ld] float32 ping-pong images.  One warp walks down
-//              a strip of 32 columns with the previous row in registers and
-//              its horizontal neighbours from shuffles; one pass per
-//              iteration, no shared memory.  RD is given by the RD bit plane
-//              (every pixel when RD is the whole image: the original method).
+//              a strip of 64 columns (two per lane) with the previous row in
+//              registers and its horizontal neighbours from shuffles; one pass
+//              per iteration, no shared memory.  RD is given by the RD bit
+//              plane (every pixel when RD is the whole image: the original
+//              method).
 //  * compact : state stored only for RD pixels, in the tile-major compact order
 //              of the domain (float32, bf16 or fp16 storage, float32
 //              arithmetic).  A neighbour table, built once per solve, holds
-//              for each RD pixel the compact index of the six pixels the
-//              fixed-point step reads (or a code for a fixed / outside pixel).
-//              Each iteration is two fully parallel passes over the RD pixels:
-//              the dual step (p') and the primal step (u', v'); the primal
-//              step also stores w = div p - v/theta for the next dual step,
-//              which then reads w at three pixels instead of p and v at seven.
+//              for each RD pixel the compact index of the eight pixels the
+//              iteration reads (or a code for a fixed / outside pixel).  One
+//              persistent cooperative launch runs every iteration: a dual
+//              phase (p') and a primal phase (u', v', and w = div p - v/theta
+//              for the next dual phase) separated by grid barriers, or one
+//              fused phase per iteration when each thread holds few pixels;
+//              each block keeps what it can of its pixels' state in shared
+//              memory (see the persistent compact solver below).
 // Per-block FP64 partial sums of |du|^2, |dv|^2 feed a fixed-order reduction,
 // so the stopping test is deterministic.  Once it fires, a device flag makes
 // every later launch of the solve return immediately.
@@ -407,16 +410,19 @@ __device__ __forceinline__ float w_fixed(float p_in_1, float p_in_2, int code, f
 //   primal phase u', v', w', stop-test partials          -> barrier
 //   (check iterations) block 0 sums the partials in a fixed order and raises
 //   the done flag, which every block reads after the next barrier.
-// With one fixed-point sweep per iteration (n_inner = 1) the two phases are
-// fused into one, with one barrier per iteration: the thread of x also redoes
-// the dual steps of x - e1 and x - e2 (same inputs, same arithmetic, same
-// rounding as their owners), which is all the v-step of x needs, and w is
-// ping-ponged.  The iterates are bit-identical to the two-phase ones.
-// Only the owner reads the neighbour-table rows and v of a pixel, so when a
-// block's range fits, those are copied into its shared memory once per solve:
-// every neighbour load then depends on a shared-memory read instead of an L2
-// read, and v is written back at the end.
-constexpr int kPersistThreads = 512;
+// Each block takes the first of these that applies (blocks may differ; all
+// keep the same barrier protocol and the same global arrays current):
+//  * fused (n_inner = 1, few pixels per thread): one phase and one barrier
+//    per iteration; the thread of x also redoes the dual steps of x - e1 and
+//    x - e2 (same inputs, same arithmetic, same rounding as their owners),
+//    which is all the v-step of x needs, and w is ping-ponged.  The iterates
+//    are bit-identical to the two-phase ones.
+//  * shared-memory state (n_inner = 1, the block's pixels fit): see
+//    compact_iterations_gh below.
+//  * neighbour-table rows and v in shared memory, neighbour values from the
+//    global arrays (only the owner reads a pixel's rows and v).
+//  * everything in global memory.
+constexpr int kBackwardThreads = 512;   // block size of the persistent reverse sweep
 // dynamic shared memory of the persistent solver: one or two blocks per SM
 constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 110 * 1024; }
 constexpr int kCompactThreads = 1024;   // one block per SM
@@ -814,17 +820,27 @@ struct GhostState {
     __device__ __forceinline__ T* v() const { return reinterpret_cast<T*>(sm + L.v); }
 };
 
+// Per-phase views of the shared-memory state (pointers fixed for a phase).
+struct DualView {
+    const float *p1, *p2, *w;     // own p (buffer pb) and w, by own index
+    float *q1, *q2;               // own p' (the other buffer)
+    const float *n1, *n2;         // neighbour p words of buffer pb (offsets are buffer 0)
+    const float* nw;              // neighbour w words
+    const uint16_t *od, *orr, *odl, *our;   // offsets of the neighbours below, right, x+e1-e2, x-e1+e2
+};
+struct PrimalView {
+    const float *q1, *q2;         // own p' (buffer pb)
+    const float *n1, *n2;         // neighbour p' words of buffer pb
+    float* w;                     // own w
+    const uint16_t *ou, *ol;      // offsets of the neighbours above, left
+};
+
 template <typename T>
-__device__ __forceinline__ void dual_gh(const IterParams& P, int i, int a, const GhostState<T>& S, int pb,
+__device__ __forceinline__ void dual_gh(const IterParams& P, int i, int a, uint8_t fl, const DualView& D,
                                         T* P1o, T* P2o, uint32_t seed) {
-    const GhostLayout& L = S.L;
-    float* sm = S.sm;
-    const int n = L.n;
-    const uint8_t fl = S.fl[i];
-    const int b1 = pb * L.ns1, b2 = pb * L.ns2;
-    const float p1 = sm[L.p1 + b1 + i], p2 = sm[L.p2 + b2 + i], w0 = sm[L.w + i];
-    const float wdv = sm[S.off[GK_DOWN * n + i]], wrv = sm[S.off[GK_RIGHT * n + i]];
-    const float p2dl = sm[S.off[GK_DL * n + i] + b2], p1ur = sm[S.off[GK_UR * n + i] + b1];
+    const float p1 = D.p1[i], p2 = D.p2[i], w0 = D.w[i];
+    const float wdv = D.nw[D.od[i]], wrv = D.nw[D.orr[i]];
+    const float p2dl = D.n2[D.odl[i]], p1ur = D.n1[D.our[i]];
     const int cd = fl & 3, cr = (fl >> 2) & 3;   // 0 RD, 1 fixed Bg, 2 fixed Fg, 3 outside
     float g1 = 0.f, g2 = 0.f;
     if (cd != 3) g1 = (cd == 0 ? wdv : w_fixed(p1, p2dl, cd == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
@@ -840,21 +856,16 @@ __device__ __forceinline__ void dual_gh(const IterParams& P, int i, int a, const
         q1 = Store<T>::sr(q1, rnd);
         q2 = Store<T>::sr(q2, rnd2);
     }
-    sm[L.p1 + (L.ns1 - b1) + i] = q1;   // the other buffer: (1 - pb) x ns1
-    sm[L.p2 + (L.ns2 - b2) + i] = q2;
+    D.q1[i] = q1;
+    D.q2[i] = q2;
 }
 
 template <typename T>
-__device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, const GhostState<T>& S, int pb,
-                                          const float* F, float* U, float* Wg, bool check, bool write_u,
+__device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, uint8_t fl, const PrimalView& Q,
+                                          T* V, const float* F, float* U, float* Wg, bool check, bool write_u,
                                           uint32_t seed, float& du2, float& dv2) {
-    const GhostLayout& L = S.L;
-    float* sm = S.sm;
-    const int n = L.n;
-    const int b1 = pb * L.ns1, b2 = pb * L.ns2;
-    const float q1 = sm[L.p1 + b1 + i], q2 = sm[L.p2 + b2 + i];
-    const float q1u = sm[S.off[GK_UP * n + i] + b1], q2l = sm[S.off[GK_LEFT * n + i] + b2];
-    T* V = S.v();
+    const float q1 = Q.q1[i], q2 = Q.q2[i];
+    const float q1u = Q.n1[Q.ou[i]], q2l = Q.n2[Q.ol[i]];
     const float vv = Store<T>::ld_rw(V, i) + Store<T>::vbias;
     const float div = (q1 - q1u) + (q2 - q2l);
     const float un = fmaf(-P.theta, div, vv);
@@ -862,8 +873,8 @@ __device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, con
     const float vs = Store<T>::st_sr(V, i, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
                      Store<T>::vbias;
     const float wv = div - vs * P.inv_theta;
-    sm[L.w + i] = wv;
-    if (S.fl[i] & kFlExport) Wg[a] = wv;
+    Q.w[i] = wv;
+    if (fl & kFlExport) Wg[a] = wv;
     if (check) {
         const float da = un - U[a], db = vn - vv;
         du2 = fmaf(da, da, du2);
@@ -962,19 +973,36 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
             const uint32_t seed = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
             T* o1 = pb ? P1a : P1b;
             T* o2 = pb ? P2a : P2b;
+            DualView D;
+            D.p1 = S.sm + L.p1 + pb * L.ns1;
+            D.p2 = S.sm + L.p2 + pb * L.ns2;
+            D.w = S.sm + L.w;
+            D.q1 = S.sm + L.p1 + (1 - pb) * L.ns1;
+            D.q2 = S.sm + L.p2 + (1 - pb) * L.ns2;
+            D.n1 = S.sm + pb * L.ns1;
+            D.n2 = S.sm + pb * L.ns2;
+            D.nw = S.sm;
+            D.od = S.off + GK_DOWN * L.n;
+            D.orr = S.off + GK_RIGHT * L.n;
+            D.odl = S.off + GK_DL * L.n;
+            D.our = S.off + GK_UR * L.n;
             if (overlap) {   // ghosts in flight while the interior pixels update
                 GhostRegs<T> R;
                 R.load(S, 0, L.gd, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
                 each([&](int a) {
-                    if (!(S.fl[a - a0] & kFlDualGhost)) dual_gh(P, a - a0, a, S, pb, o1, o2, seed);
+                    const uint8_t f = S.fl[a - a0];
+                    if (!(f & kFlDualGhost)) dual_gh(P, a - a0, a, f, D, o1, o2, seed);
                 });
                 R.store(S, 0, L.gd, pb, nt);
                 __syncthreads();
-                for (int e = tid; e < L.nbd; e += nt) dual_gh(P, S.bd[e], a0 + S.bd[e], S, pb, o1, o2, seed);
+                for (int e = tid; e < L.nbd; e += nt) {
+                    const int i = S.bd[e];
+                    dual_gh(P, i, a0 + i, S.fl[i], D, o1, o2, seed);
+                }
             } else {
                 fill_ghosts(S, 0, L.gd, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
                 __syncthreads();
-                each([&](int a) { dual_gh(P, a - a0, a, S, pb, o1, o2, seed); });
+                each([&](int a) { dual_gh(P, a - a0, a, S.fl[a - a0], D, o1, o2, seed); });
             }
             pb ^= 1;
             if (!grid_sync(h, nblocks, gen)) return false;
@@ -988,21 +1016,35 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
         const bool write_u = check || ((l + 1) % C == 0) || l == iters;
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
+        PrimalView Q;
+        Q.q1 = S.sm + L.p1 + pb * L.ns1;
+        Q.q2 = S.sm + L.p2 + pb * L.ns2;
+        Q.n1 = S.sm + pb * L.ns1;
+        Q.n2 = S.sm + pb * L.ns2;
+        Q.w = S.sm + L.w;
+        Q.ou = S.off + GK_UP * L.n;
+        Q.ol = S.off + GK_LEFT * L.n;
+        T* Vs = S.v();
         if (overlap) {
             GhostRegs<T> R;
             R.load(S, L.gd, L.gd + L.gp, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
             each([&](int a) {
-                if (!(S.fl[a - a0] & kFlPrimalGhost))
-                    primal_gh(P, a - a0, a, S, pb, F, U, Wc, check, write_u, seed, du2, dv2);
+                const uint8_t f = S.fl[a - a0];
+                if (!(f & kFlPrimalGhost))
+                    primal_gh(P, a - a0, a, f, Q, Vs, F, U, Wc, check, write_u, seed, du2, dv2);
             });
             R.store(S, L.gd, L.gd + L.gp, pb, nt);
             __syncthreads();
-            for (int e = tid; e < L.nbp; e += nt)
-                primal_gh(P, S.bp[e], a0 + S.bp[e], S, pb, F, U, Wc, check, write_u, seed, du2, dv2);
+            for (int e = tid; e < L.nbp; e += nt) {
+                const int i = S.bp[e];
+                primal_gh(P, i, a0 + i, S.fl[i], Q, Vs, F, U, Wc, check, write_u, seed, du2, dv2);
+            }
         } else {
             fill_ghosts(S, L.gd, L.gd + L.gp, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
             __syncthreads();
-            each([&](int a) { primal_gh(P, a - a0, a, S, pb, F, U, Wc, check, write_u, seed, du2, dv2); });
+            each([&](int a) {
+                primal_gh(P, a - a0, a, S.fl[a - a0], Q, Vs, F, U, Wc, check, write_u, seed, du2, dv2);
+            });
         }
         if (ckpt && l % ckpt_every == 0 && l < iters) {
             __syncthreads();   // boundary pixels were updated by other threads
@@ -1614,7 +1656,7 @@ __device__ __forceinline__ double block_sum1(double x, double* s_red) {
     return t;
 }
 
-__global__ void __launch_bounds__(kPersistThreads)
+__global__ void __launch_bounds__(kBackwardThreads)
 k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
                    const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
                    const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
@@ -2023,16 +2065,16 @@ extern "C" seg_status seg_backward(const float* f, int H, int W, int ld, const u
     SEG_LAUNCHED("k_adj_gather");
     auto kern = k_backward_compact;
     int per_sm = 0;
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, 0));
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBackwardThreads, 0));
     if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_backward_compact cannot be resident");
     const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)H * W));
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
-                                      std::max<int64_t>(1, (most + kPersistThreads - 1) / kPersistThreads));
+                                      std::max<int64_t>(1, (most + kBackwardThreads - 1) / kBackwardThreads));
     int iters = prm->iters, ce = ckpt_every;
     const float* ck = static_cast<const float*>(ckpt);
     void* args[] = {&P, &iters, &ce, (void*)&counts, (void*)&nbp, &stride, (void*)&F, (void*)&ck, &A, &h};
     if (iters > 0) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPersistThreads), args,
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kBackwardThreads), args,
                                                  0, s));
         count_launch();
     }
