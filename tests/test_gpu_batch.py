@@ -137,3 +137,26 @@ def test_full_size_batch_of_64(orc):
             fc = np.ascontiguousarray(f[a:b, c:d])
             st = orc.solve(fc, orc.domain(fc, delta), probs[k].lam, iters=K)
             assert abs(st.u[i - a, j - c] - u[i, j]) <= 1e-4
+
+
+def test_largest_batch_and_one_more(orc):
+    """128 images (the most one launch takes) of sizes 1x1 .. 48x48, each
+    against the oracle; 129 images are refused before any device work."""
+    seg = seg_mod()
+    rng = np.random.default_rng(12)
+    shapes = [(int(rng.integers(1, 49)), int(rng.integers(1, 49))) for _ in range(128)]
+    lams = [float(x) for x in rng.uniform(0.5, 3.0, 128)]
+    qs = [float(x) for x in rng.uniform(0.0, 1.0, 128)]
+    B, fs = _batch(orc, shapes, lams, qs, 40)
+    B.check_status()
+    for k, S in enumerate(B.solvers):
+        delta = float(S.dom.delta.cpu().numpy()[0])
+        st = orc.solve(fs[k], orc.domain(fs[k], delta), lams[k], 0.2, 0.125, 40)
+        assert np.max(np.abs(seg.download(S.u).astype(np.float64) - st.u)) <= 1e-4, k
+    B129 = seg.BatchSolver(shapes + [(8, 8)], tile_h=16)
+    for S in B129.solvers:
+        S.f.zero_()
+        S.domain(delta=0.1)
+    with pytest.raises(seg.SegError) as e:
+        B129.solve([1.0] * 129, iters=5)
+    assert e.value.status == seg.SEG_ERR_INVALID_ARG

@@ -396,6 +396,33 @@ def test_16bit_storage_on_the_shared_memory_path(orc, storage):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("mode", ["compact", "tiled"])
+def test_largest_image_sampled(orc, mode):
+    """A 16384 x 16384 image (268 M pixels; H * ld must stay below 2^31):
+    random fitting term, delta = 0.1, 20 iterations, oracle crops around
+    sampled RD pixels and the four corners."""
+    seg = seg_mod()
+    rng = np.random.default_rng(21)
+    H = W = 16384
+    f = rng.normal(0.0, 0.3, (H, W)).astype(np.float32)
+    K, delta, lam = 20, 0.1, 1.0
+    S = seg.Solver(H, W, tile_h=16, mode=mode)
+    S.f[:, :W].copy_(torch.from_numpy(f))
+    S.domain(delta=delta)
+    S.solve(lam, iters=K, check_every=K)
+    torch.cuda.synchronize()
+    S.check_status()
+    inrd = np.abs(f) < np.float32(delta)
+    assert int(S.dom.counts[1].item()) == int(np.count_nonzero(inrd))
+    u = S.u[:, :W].cpu().numpy()      # float32, 1 GB
+    del S
+    act = np.argwhere(inrd)
+    pick = act[rng.choice(len(act), 12, replace=False)]
+    centres = [tuple(x) for x in pick] + [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0)]
+    assert _crop_check(orc, f, u, delta, lam, K, centres) <= TOL_U32
+
+
+@pytest.mark.slow
 def test_full_size_4096_storage_sampled(orc):
     """4096x4096 polygons, 16-bit storage against float32 storage and the
     oracle on crops."""
