@@ -110,7 +110,9 @@ seg_status seg_read_status(void* ws, size_t ws_bytes, void* stream);
  * the nearest marker pixel divided by its maximum over the image.
  *   z        [H][ld] float32 image.
  *   c1, c2   foreground / background intensities (host doubles), used when
- *            label == NULL.
+ *            label == NULL; both NaN: the c1, c2 the workspace holds from the
+ *            last seg_make_fitting or seg_update_means on it (so a Chan-Vese
+ *            loop needs no host round trip).
  *   label    NULL, or uint8 [H][ld] class mask: c1 = mean of z where label != 0,
  *            c2 = mean where label == 0 (FP64 on the device).
  *   markers  NULL or int32 [n_markers][2] (row, col) device array.
@@ -122,6 +124,20 @@ seg_status seg_make_fitting(const float* z, int H, int W, int ld,
                             double c1, double c2, const uint8_t* label,
                             const int32_t* markers, int n_markers, double gamma,
                             float* f, double* c_out,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* Chan-Vese update of the intensities of Eq. CV (the alternating step of the
+ * piecewise-constant model the fitting term of Section 1 comes from [ACWE],
+ * with the relaxed u thresholded): c1 = mean of z over {u > thresh}, c2 =
+ * mean of z over {u <= thresh}, in FP64 with a fixed-order reduction.  A
+ * class with no pixel keeps the value the workspace held.  The result is
+ * stored in the workspace (for seg_make_fitting with c1 = c2 = NaN) and, if
+ * c_out is not NULL, in c_out (device double[2]).
+ *   z, u     [H][ld] float32 image and relaxed indicator.
+ * Errors: INVALID_ARG (sizes, NULL z/u, non-finite thresh), ALIGN, WORKSPACE,
+ * CUDA. */
+seg_status seg_update_means(const float* z, const float* u, int H, int W, int ld,
+                            double thresh, double* c_out,
                             void* ws, size_t ws_bytes, void* stream);
 
 /* Restricted domain (Section 3): RD = {|f| < delta}, Fg = {f < 0} \ RD,

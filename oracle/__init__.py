@@ -57,6 +57,8 @@ def _load():
         lib.oracle_fitting.restype = None
         lib.oracle_class_means.argtypes = [P, P, L, P, P]
         lib.oracle_class_means.restype = None
+        lib.oracle_update_means.argtypes = [P, P, L, D, P, P]
+        lib.oracle_update_means.restype = None
         lib.oracle_quantile_delta.argtypes = [P, L, D]
         lib.oracle_quantile_delta.restype = F
         lib.oracle_domain.argtypes = [P, L, F, P]
@@ -113,6 +115,35 @@ def class_means(z, label):
     c1, c2 = ctypes.c_double(), ctypes.c_double()
     lib.oracle_class_means(_ptr(z), _ptr(lab), z.size, ctypes.byref(c1), ctypes.byref(c2))
     return c1.value, c2.value
+
+
+def update_means(z, u, thresh, c1, c2):
+    """Chan-Vese intensity update: (mean of z over u > thresh, mean over
+    u <= thresh); a class without pixels keeps c1 resp. c2."""
+    lib = _load()
+    z = _c(z, np.float32)
+    uu = _c(u, np.float64)
+    a, b = ctypes.c_double(c1), ctypes.c_double(c2)
+    lib.oracle_update_means(_ptr(z), _ptr(uu), z.size, float(thresh), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def chan_vese(z, c1, c2, lam, outer, iters, delta=float("inf"), q=-1.0, thresh=0.5, theta=0.2,
+              tau=0.125):
+    """Chan-Vese loop on the restricted solve: for t = 0 .. outer-1, the
+    fitting term of Eq. CV with (c1, c2), its domain (delta, or quantile q),
+    `iters` iterations warm-started from the previous solve, then the
+    intensity update from u.  Returns (state of the last solve, the (c1, c2)
+    that solve used, the list of (c1, c2) per outer step)."""
+    st, used = None, []
+    for t in range(outer):
+        if t > 0:
+            c1, c2 = update_means(z, st.u, thresh, c1, c2)
+        used.append((c1, c2))
+        _, f = fitting(z, c1, c2)
+        d = quantile_delta(f, q) if q >= 0 else delta
+        st = solve(f, domain(f, d), lam, theta, tau, iters, state=st)
+    return st, (c1, c2), used
 
 
 def quantile_delta(f32, q):

@@ -98,6 +98,25 @@ void oracle_class_means(const float* z, const uint8_t* label, int64_t n,
     *c2 = n0 ? s0 / (double)n0 : 0.0;
 }
 
+/* Chan-Vese update of the intensities: the alternating step of the
+ * piecewise-constant model ([ACWE], cited in Section 1 for Eq. CV) with the
+ * relaxed u thresholded.  For fixed u the fitting energy
+ * sum (z-c1)^2 [u > thresh] + (z-c2)^2 [u <= thresh] is minimised by the
+ * class means; a class without pixels keeps its previous value (c1, c2 are
+ * in / out).  Sums in FP64 in index order. */
+void oracle_update_means(const float* z, const double* u, int64_t n, double thresh,
+                         double* c1, double* c2)
+{
+    double s1 = 0.0, s0 = 0.0;
+    int64_t n1 = 0, n0 = 0;
+    for (int64_t x = 0; x < n; ++x) {
+        if (u[x] > thresh) { s1 += (double)z[x]; ++n1; }
+        else               { s0 += (double)z[x]; ++n0; }
+    }
+    if (n1) *c1 = s1 / (double)n1;
+    if (n0) *c2 = s0 / (double)n0;
+}
+
 /* --------------------------------------------------------------- domain */
 
 static int cmp_float(const void* a, const void* b)

@@ -27,6 +27,10 @@ void oracle_fitting(const float* z, int H, int W, double c1, double c2,
                     double* f64_out, float* f32_out);
 
 /* Class means of z over label==1 (c1, foreground) and label==0 (c2). */
+/* Chan-Vese update of c1, c2 from the thresholded relaxed u (in / out). */
+void oracle_update_means(const float* z, const double* u, int64_t n, double thresh,
+                         double* c1, double* c2);
+
 void oracle_class_means(const float* z, const uint8_t* label, int64_t n,
                         double* c1, double* c2);
 

@@ -6,6 +6,7 @@
 // markers and gamma.  c1, c2 may come from a label mask (class means, FP64,
 // fixed-order reduction).
 #include <algorithm>
+#include <cmath>
 
 #include "seg_internal.cuh"
 
@@ -51,6 +52,44 @@ __global__ void k_set_c(WsHeader* h, double c1, double c2, double* c_out) {
     h->c[1] = c2;
     h->d2max = 0ull;
     if (c_out) { c_out[0] = c1; c_out[1] = c2; }
+}
+
+// Keeps the c1, c2 already in the header (set by the last fitting term or
+// class-mean update).
+__global__ void k_keep_c(WsHeader* h, double* c_out) {
+    h->d2max = 0ull;
+    if (c_out) { c_out[0] = h->c[0]; c_out[1] = h->c[1]; }
+}
+
+// Per-block FP64 sums of z over u > thresh (foreground) and u <= thresh and
+// their counts; red[b*4 + {0,1,2,3}] = {sum1, sum0, n1, n0}.
+__global__ void k_class_sums(const float* __restrict__ z, const float* __restrict__ u, float thresh,
+                             int H, int W, int ld, double* __restrict__ red) {
+    __shared__ double s[4][kFitThreads];
+    double s1 = 0, s0 = 0, n1 = 0, n0 = 0;
+    int64_t n = (int64_t)H * W;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = x / W, j = x - i * W;
+        double zz = (double)z[i * ld + j];
+        if (u[i * ld + j] > thresh) { s1 = __dadd_rn(s1, zz); n1 += 1.0; }
+        else                        { s0 = __dadd_rn(s0, zz); n0 += 1.0; }
+    }
+    s[0][threadIdx.x] = s1; s[1][threadIdx.x] = s0; s[2][threadIdx.x] = n1; s[3][threadIdx.x] = n0;
+    __syncthreads();
+    for (int w = kFitThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int t = 0; t < 4; ++t) s[t][threadIdx.x] = __dadd_rn(s[t][threadIdx.x], s[t][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) red[(int64_t)blockIdx.x * 4 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// c1, c2 = the class means; a class without pixels keeps its previous value.
+__global__ void k_update_means(const double* __restrict__ sums, WsHeader* h, double* c_out) {
+    if (sums[2] > 0) h->c[0] = __ddiv_rn(sums[0], sums[2]);
+    if (sums[3] > 0) h->c[1] = __ddiv_rn(sums[1], sums[3]);
+    if (c_out) { c_out[0] = h->c[0]; c_out[1] = h->c[1]; }
 }
 
 // Smallest squared distance (exact integer) from pixel (i, j) to a marker.
@@ -166,8 +205,13 @@ extern "C" seg_status seg_make_fitting(const float* z, int H, int W, int ld, dou
     WsLayout L = ws_layout(H, W, 32);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     WsHeader* h = ws_at<WsHeader>(ws, L.header);
-    k_set_c<<<1, 1, 0, s>>>(h, c1, c2, label ? nullptr : c_out);
-    SEG_LAUNCHED("k_set_c");
+    if (!label && std::isnan(c1) && std::isnan(c2)) {   // the c1, c2 already in the workspace
+        k_keep_c<<<1, 1, 0, s>>>(h, c_out);
+        SEG_LAUNCHED("k_keep_c");
+    } else {
+        k_set_c<<<1, 1, 0, s>>>(h, c1, c2, label ? nullptr : c_out);
+        SEG_LAUNCHED("k_set_c");
+    }
     if (label) {
         double* red = ws_at<double>(ws, L.red);
         k_label_sums<<<kReduceBlocks, kFitThreads, 0, s>>>(z, label, H, W, ld, red);
@@ -185,5 +229,35 @@ extern "C" seg_status seg_make_fitting(const float* z, int H, int W, int ld, dou
     }
     k_fitting<<<blocks, kFitThreads, 0, s>>>(z, H, W, ld, markers, n_markers, gamma, h, f);
     SEG_LAUNCHED("k_fitting");
+    return SEG_OK;
+}
+
+// Chan-Vese update of the intensities (the alternating step of the
+// piecewise-constant model of Section 1's [ACWE] fitting term, with the
+// relaxed u thresholded): c1 = mean of z over u > thresh, c2 = mean over
+// u <= thresh, FP64 with a fixed-order reduction, stored in the workspace for
+// the next seg_make_fitting (called with c1 = c2 = NaN) and in c_out.
+extern "C" seg_status seg_update_means(const float* z, const float* u, int H, int W, int ld, double thresh,
+                                       double* c_out, void* ws, size_t ws_bytes, void* stream) {
+    using namespace seg;
+    clear_error();
+    if (!z || !u) return fail(SEG_ERR_INVALID_ARG, "z and u must be non-NULL");
+    if (H <= 0 || W <= 0 || ld < W || (int64_t)H * W >= (1ll << 31))
+        return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d", H, W, ld);
+    if (ld % 32) return fail(SEG_ERR_ALIGN, "ld=%d is not a multiple of 32", ld);
+    if (!std::isfinite(thresh)) return fail(SEG_ERR_INVALID_ARG, "thresh must be finite");
+    if (!ws || ws_bytes < kWsFixedBytes)
+        return fail(SEG_ERR_WORKSPACE, "workspace too small for seg_update_means");
+    if (reinterpret_cast<uintptr_t>(ws) % 16) return fail(SEG_ERR_ALIGN, "workspace not 16-byte aligned");
+    WsLayout L = ws_layout(H, W, 32);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader* h = ws_at<WsHeader>(ws, L.header);
+    double* red = ws_at<double>(ws, L.red);
+    k_class_sums<<<kReduceBlocks, kFitThreads, 0, s>>>(z, u, (float)thresh, H, W, ld, red);
+    SEG_LAUNCHED("k_class_sums");
+    double* sums = red + (size_t)kReduceBlocks * 4;
+    SEG_TRY(reduce_partials(red, kReduceBlocks, 4, sums, s));
+    k_update_means<<<1, 1, 0, s>>>(sums, h, c_out);
+    SEG_LAUNCHED("k_update_means");
     return SEG_OK;
 }

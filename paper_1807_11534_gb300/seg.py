@@ -78,6 +78,7 @@ SIGNATURES = {
     "seg_read_status": ([_P, _Z, _P], _I),
     "seg_make_fitting": ([_P, _I, _I, _I, _D, _D, _P, _P, _I, _D, _P, _P, _P, _Z, _P], _I),
     "seg_build_domain": ([_P, _I, _I, _I, _D, _D, _I, _P, _P, _P, _P, _I, _P, _L, _P, _P, _P, _Z, _P], _I),
+    "seg_update_means": ([_P, _P, _I, _I, _I, _D, _P, _P, _Z, _P], _I),
     "seg_solve": ([_P, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(seg_params),
                    _P, _P, _P, _P, _P, _Z, _P, _P, _Z, _P], _I),
     "seg_energy": ([_P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _P, _P, _Z, _P], _I),
@@ -171,6 +172,11 @@ def seg_make_fitting(z, c1, c2, label, markers, gamma, f, c_out, ws, stream=None
     _check(lib.seg_make_fitting(_ptr(z), z.shape[0], _W(z), z.stride(0), float(c1), float(c2), _ptr(label),
                                 _ptr(markers), n_markers, float(gamma), _ptr(f), _ptr(c_out),
                                 _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def seg_update_means(z, u, thresh, c_out, ws, stream=None):
+    _check(load().seg_update_means(_ptr(z), _ptr(u), z.shape[0], _W(z), z.stride(0), float(thresh),
+                                   _ptr(c_out), _ptr(ws), _nbytes(ws), _stream(stream)))
 
 
 def seg_build_domain(f, delta, q, tile_h, act, fg, wstart, tiles, pixels, counts, delta_out, ws,
@@ -422,6 +428,29 @@ class Solver:
         seg_solve(f, d.act, d.fg, d.wstart, d.tiles, d.counts, prm, self.u, self.v, self.p1,
                   self.p2, self.state, self.stats, self.ws, self.stream)
         return self.stats
+
+    def update_means(self, z, thresh=0.5):
+        """Chan-Vese intensity update from this solver's u (into self.c and
+        the workspace, for fitting with c1 = c2 = NaN)."""
+        seg_update_means(z, self.u, thresh, self.c, self.ws, self.stream)
+        return self.c
+
+    def chan_vese(self, z, lam, c1=0.3, c2=0.7, outer=5, iters=100, delta=math.inf, q=-1.0,
+                  thresh=0.5, theta=0.2, tau=0.125, check_every=None):
+        """Chan-Vese loop on the restricted solve, all on the device: for
+        t = 0 .. outer-1 the fitting term of Eq. CV with the current (c1, c2)
+        (the given ones, then the class means of z over u > thresh and
+        u <= thresh), its domain, and `iters` iterations warm-started from the
+        previous solve.  Returns self.c, the (c1, c2) of the last solve."""
+        for t in range(outer):
+            if t == 0:
+                self.fitting(z, c1, c2)
+            else:
+                self.update_means(z, thresh)
+                self.fitting(z, math.nan, math.nan)
+            self.domain(delta=delta, q=q)
+            self.solve(lam, theta, tau, iters, 0.0, 1, check_every or iters, warm_start=t > 0)
+        return self.c
 
     def energy(self, lam, theta=0.2, f=None):
         f = self.f if f is None else f

@@ -510,3 +510,60 @@ def test_reverse_mode_matches_central_differences(orc, delta, seed):
     el = 1e-6
     fd = (_loss(orc, f, reg, lam + el, gu, gv, K) - _loss(orc, f, reg, lam - el, gu, gv, K)) / (2 * el)
     assert abs(fd - glam) <= 1e-5 * max(1.0, abs(glam)), (fd, glam)
+
+
+# ------------------------------------------------------------ Chan-Vese loop
+
+def test_update_means_is_the_class_mean_and_keeps_empty_classes(orc):
+    rng = np.random.default_rng(41)
+    z = rng.uniform(0, 1, (37, 53)).astype(np.float32)
+    u = rng.uniform(-0.2, 1.2, (37, 53))
+    c1, c2 = orc.update_means(z, u, 0.5, -7.0, -8.0)
+    m = u > 0.5
+    assert c1 == pytest.approx(float(np.sum(z[m].astype(np.float64))) / m.sum(), rel=1e-14)
+    assert c2 == pytest.approx(float(np.sum(z[~m].astype(np.float64))) / (~m).sum(), rel=1e-14)
+    # one class empty: it keeps the value it had
+    c1, c2 = orc.update_means(z, np.zeros_like(u), 0.5, 0.25, 0.75)
+    assert c1 == 0.25 and c2 == pytest.approx(float(np.mean(z.astype(np.float64))), rel=1e-14)
+
+
+def test_update_means_minimises_the_fitting_energy_for_the_mask(orc):
+    """For a fixed thresholded u the updated c1, c2 minimise
+    sum (z-c1)^2 [u > 0.5] + (z-c2)^2 [u <= 0.5]: any other pair is worse."""
+    rng = np.random.default_rng(42)
+    z = rng.normal(0.5, 0.2, (40, 40)).astype(np.float32)
+    u = rng.uniform(0, 1, (40, 40))
+    c1, c2 = orc.update_means(z, u, 0.5, 0.3, 0.7)
+    m = u > 0.5
+    zz = z.astype(np.float64)
+
+    def energy(a, b):
+        return float(np.sum((zz[m] - a) ** 2) + np.sum((zz[~m] - b) ** 2))
+
+    e0 = energy(c1, c2)
+    for da, db in ((1e-3, 0), (-1e-3, 0), (0, 1e-3), (0, -1e-3), (0.05, -0.05)):
+        assert energy(c1 + da, c2 + db) > e0
+
+
+def test_chan_vese_one_outer_step_is_the_plain_solve(orc):
+    P = synth.small_example(seed=5, H=48, W=64)
+    st, used, _ = orc.chan_vese(P.z, 0.3, 0.7, 1.0, outer=1, iters=30, delta=0.2)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    ref = orc.solve(f, orc.domain(f, 0.2), 1.0, iters=30)
+    assert used == (0.3, 0.7)
+    np.testing.assert_array_equal(st.u, ref.u)
+    np.testing.assert_array_equal(st.p1, ref.p1)
+
+
+def test_chan_vese_finds_the_levels_of_a_noiseless_two_level_image(orc):
+    """A disk at 0.3 on 0.7, starting from c = (0.35, 0.65): with lambda large
+    enough the first solve segments the disk exactly, after which the class
+    means are the two float32 levels and stay there."""
+    H = W = 64
+    yy, xx = np.mgrid[0:H, 0:W]
+    disk = (yy - 31.5) ** 2 + (xx - 30.0) ** 2 < 18.0 ** 2
+    z = np.where(disk, 0.3, 0.7).astype(np.float32)
+    st, used, hist = orc.chan_vese(z, 0.35, 0.65, 40.0, outer=4, iters=60, delta=np.inf)
+    assert np.array_equal(st.u > 0.5, disk)
+    assert hist[1] == (float(np.float32(0.3)), float(np.float32(0.7)))
+    assert used == hist[1] == hist[3]
