@@ -51,8 +51,12 @@ __device__ __forceinline__ void grid_arrive(WsHeader* h, unsigned& gen) {
     if (threadIdx.x == 0) red_add_release_gpu(&h->bar_count, 1u);
 }
 
-__device__ __forceinline__ bool grid_wait(WsHeader* h, unsigned nblocks, unsigned gen) {
-    __shared__ int s_ok;
+// poll: thread 0 also reads the done flag after the barrier and the block
+// gets it in `done` (one load per block instead of one per warp on a single
+// line).
+__device__ __forceinline__ bool grid_wait(WsHeader* h, unsigned nblocks, unsigned gen, bool poll,
+                                          bool& done) {
+    __shared__ int s_ok, s_done;
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned target = nblocks * gen;
@@ -66,14 +70,77 @@ __device__ __forceinline__ bool grid_wait(WsHeader* h, unsigned nblocks, unsigne
             }
         }
         s_ok = ok;
+        if (poll) s_done = *(volatile int*)&h->done;
     }
     __syncthreads();
+    done = poll && s_done != 0;
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_wait(WsHeader* h, unsigned nblocks, unsigned gen) {
+    bool d;
+    return grid_wait(h, nblocks, gen, false, d);
 }
 
 __device__ __forceinline__ bool grid_sync(WsHeader* h, unsigned nblocks, unsigned& gen) {
     grid_arrive(h, gen);
     return grid_wait(h, nblocks, gen);
+}
+
+__device__ __forceinline__ bool grid_sync_poll(WsHeader* h, unsigned nblocks, unsigned& gen, bool poll,
+                                               bool& done) {
+    grid_arrive(h, gen);
+    return grid_wait(h, nblocks, gen, poll, done);
+}
+
+// Stopping-test sums (Section 4), deterministic and with no FP64 work in the
+// block (FP64 is a narrow pipe on this part, and every block reduces at every
+// test):
+//  * block_sum2f: the FP32 sums of (x, y) over a block of NT threads, a warp
+//    shuffle tree, the warp sums staged in shared memory (s_red, 64 floats),
+//    then one shuffle tree over them; the totals land in every thread;
+//  * sum_partials_warp0: the FP64 sum of n (x, y) pairs written by the
+//    blocks, in a fixed order by warp 0 (lane l adds pairs l, l + 32, ...,
+//    then a shuffle tree); returns the totals in lane 0 of warp 0.
+// All threads of the block must call block_sum2f.
+template <int NT>
+__device__ __forceinline__ void block_sum2f(float& x, float& y, float* s_red) {
+    const unsigned FULL = 0xffffffffu;
+    for (int d = 16; d > 0; d >>= 1) {
+        x += __shfl_down_sync(FULL, x, d);
+        y += __shfl_down_sync(FULL, y, d);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();   // s_red may still be read from an earlier use
+    if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
+    __syncthreads();
+    if (wid == 0) {
+        x = lane < NT / 32 ? s_red[2 * lane] : 0.f;
+        y = lane < NT / 32 ? s_red[2 * lane + 1] : 0.f;
+        for (int d = 16; d > 0; d >>= 1) {
+            x += __shfl_down_sync(FULL, x, d);
+            y += __shfl_down_sync(FULL, y, d);
+        }
+        if (lane == 0) { s_red[64] = x; s_red[65] = y; }
+    }
+    __syncthreads();
+    x = s_red[64];
+    y = s_red[65];
+}
+
+__device__ __forceinline__ void sum_partials_warp0(const double* part, int n, double& x, double& y) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    x = 0.0;
+    y = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        x += __ldcg(part + 2 * k);
+        y += __ldcg(part + 2 * k + 1);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        x += __shfl_down_sync(FULL, x, d);
+        y += __shfl_down_sync(FULL, y, d);
+    }
 }
 
 // ------------------------------------------------ host entry of tiled.cu

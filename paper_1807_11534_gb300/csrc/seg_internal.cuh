@@ -58,7 +58,7 @@ struct WsHeader {
     int iters_done;      // iteration at which the stopping test fired
     int last_check;      // iteration of the last stopping test
     double c[2];         // c1, c2 used by the fitting term
-    double du, dv;       // last ||u^l - u^(l-1)||, ||v^l - v^(l-1)||
+    double du2, dv2;     // last ||u^l - u^(l-1)||^2, ||v^l - v^(l-1)||^2
     unsigned long long d2max;   // largest squared marker distance (Eq. DS)
     float delta;         // domain threshold in use
     unsigned int qprefix;       // radix-select prefix (quantile mode)

@@ -243,6 +243,7 @@ struct CompactState {
     float* w;        // div p - v/theta of the current iterate
     int32_t* nb;     // [NB_COUNT][stride]
     float* w2;       // the other w buffer of the fused iteration
+    float* up;       // u of the iteration before a stopping test
     int64_t cap;
     int64_t stride;
 };
@@ -350,11 +351,13 @@ __global__ void k_compact_gather(IterParams P, BatchDesc B, const int32_t* __res
         Store<T>::st(P2, idx, j < I.W - 1 ? I.p2[o] : 0.f);
         Store<T>::st(V, idx, I.v[o] - Store<T>::vbias);
         S.u[idx] = I.u[o];
+        S.up[idx] = I.u[o];
     } else {
         Store<T>::st(P1, idx, 0.f);
         Store<T>::st(P2, idx, 0.f);
         Store<T>::st(V, idx, clamp01(fmaf(-I.theta_lambda, fv, hh)) - Store<T>::vbias);
         S.u[idx] = hh;
+        S.up[idx] = hh;
     }
     // w = div p - v/theta; with p = 0 (cold start) it is -v/theta, else the
     // solver forms it once the table is complete
@@ -483,8 +486,9 @@ __device__ __forceinline__ void dual_one(const IterParams& P, int a, const Own<T
 // or for a warm start).
 template <typename T, bool SH>
 __device__ __forceinline__ void primal_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1n,
-                                           const T* P2n, float* U, float* Wc, bool wonly, bool check,
-                                           bool write_u, uint32_t seed, float& du2, float& dv2) {
+                                           const T* P2n, float* U, float* Up, float* Wc, bool wonly,
+                                           bool check, bool write_u, bool write_prev, uint32_t seed,
+                                           float& du2, float& dv2) {
     const int n_up = O.nbr(NB_UP, a);
     const int n_left = O.nbr(NB_LEFT, a);
     const float q1 = Store<T>::ldc(P1n, a), q2 = Store<T>::ldc(P2n, a);
@@ -501,10 +505,11 @@ __device__ __forceinline__ void primal_one(const IterParams& P, int a, const Own
                      Store<T>::vbias;
     Wc[a] = div - vs * P.inv_theta;
     if (check) {
-        const float da = un - U[a], db = vn - vv;
+        const float da = un - Up[a], db = vn - vv;
         du2 = fmaf(da, da, du2);
         dv2 = fmaf(db, db, dv2);
     }
+    if (write_prev) Up[a] = un;
     if (write_u) U[a] = un;
 }
 
@@ -518,8 +523,8 @@ __device__ __forceinline__ void primal_one(const IterParams& P, int a, const Own
 template <typename T, bool SH>
 __device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1i,
                                           const T* P2i, const float* Wi, T* P1o, T* P2o, float* Wo, float* U,
-                                          bool check, bool write_u, uint32_t seed_d, uint32_t seed_p, float& du2,
-                                          float& dv2) {
+                                          float* Up, bool check, bool write_u, bool write_prev, uint32_t seed_d,
+                                          uint32_t seed_p, float& du2, float& dv2) {
     const int n_up = O.nbr(NB_UP, a), n_left = O.nbr(NB_LEFT, a);
     const int n_down = O.nbr(NB_DOWN, a), n_right = O.nbr(NB_RIGHT, a);
     const int n_dl = O.nbr(NB_DOWNLEFT, a), n_ur = O.nbr(NB_UPRIGHT, a);
@@ -575,10 +580,11 @@ __device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<
                      Store<T>::vbias;
     Wo[a] = div - vs * P.inv_theta;
     if (check) {
-        const float da = un - U[a], db = vn - vv;
+        const float da = un - Up[a], db = vn - vv;
         du2 = fmaf(da, da, du2);
         dv2 = fmaf(db, db, dv2);
     }
+    if (write_prev) Up[a] = un;
     if (write_u) U[a] = un;
 }
 
@@ -588,7 +594,7 @@ template <typename T, bool SH, int NT, int UNROLL>
 __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Own<T, SH>& O, int a0, int a1,
                                                    int iters, int n_inner, int check_every, double tol, int warm,
                                                    int64_t stride, T* P1a, T* P1b, T* P2a, T* P2b, float* Uu,
-                                                   float* Wc, float* Wc2, double* partials, WsHeader* h,
+                                                   float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h,
                                                    float* ckpt, int ckpt_every, double* s_red, int fuse) {
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = NT;
@@ -615,7 +621,7 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
     auto p2o = [&]() { return pb ? P2a : P2b; };
     if (warm) {   // w of the warm-start iterate
         for (int a = a0 + tid; a < a1; a += nt)
-            primal_one(P, a, O, P1a, P2a, Uu, Wc, true, false, false, 0u, dummy0, dummy1);
+            primal_one(P, a, O, P1a, P2a, Uu, Up, Wc, true, false, false, false, 0u, dummy0, dummy1);
         if (!grid_sync(h, nblocks, gen)) return false;
     }
     const int C = check_every;
@@ -636,7 +642,8 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
         for (int it = 0; it < iters; ++it) {
             const int l = it + 1;
             const bool check = (l % C == 0) || l == iters;
-            const bool write_u = check || ((l + 1) % C == 0) || l == iters;
+            const bool write_u = check;   // the output u and the stopped iterate
+        const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
             const uint32_t seed_d = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
             const uint32_t seed_p = mix32(0x2545f491u ^ (uint32_t)it);
             const T* pi1 = p1c(); const T* pi2 = p2c();
@@ -645,7 +652,8 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
             float* wo = wb ? Wc : Wc2;
             float du2 = 0.f, dv2 = 0.f;
             each1([&](int a) {
-                fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, check, write_u, seed_d, seed_p, du2, dv2);
+                fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, Up, check, write_u, write_prev, seed_d, seed_p,
+                          du2, dv2);
             });
             pb ^= 1;
             wb ^= 1;
@@ -654,48 +662,38 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
             // block cannot overwrite those a slow block is still summing
             double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
             if (check) {
-                double x = du2, y = dv2;
-                for (int d = 16; d > 0; d >>= 1) {
-                    x += __shfl_down_sync(0xffffffffu, x, d);
-                    y += __shfl_down_sync(0xffffffffu, y, d);
-                }
-                const int lane = tid & 31, wid = tid >> 5;
-                if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
-                __syncthreads();
+                float x = du2, y = dv2;
+                block_sum2f<NT>(x, y, reinterpret_cast<float*>(s_red));
                 if (tid == 0) {
-                    double sx = 0.0, sy = 0.0;
-                    for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
-                    part[2 * blockIdx.x] = sx;
-                    part[2 * blockIdx.x + 1] = sy;
+                    part[2 * blockIdx.x] = x;
+                    part[2 * blockIdx.x + 1] = y;
                 }
             }
             if (!grid_sync(h, nblocks, gen)) return false;
             if (check) {
                 // Section 4 stopping test: every block sums the block partials
                 // in the same fixed order, so all stop at the same iteration
-                double x = 0.0, y = 0.0;
-                for (int k = tid; k < (int)nblocks; k += nt) { x += __ldcg(part + 2 * k); y += __ldcg(part + 2 * k + 1); }
-                for (int d = 16; d > 0; d >>= 1) {
-                    x += __shfl_down_sync(0xffffffffu, x, d);
-                    y += __shfl_down_sync(0xffffffffu, y, d);
-                }
-                const int lane = tid & 31, wid = tid >> 5;
-                __syncthreads();
-                if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
-                __syncthreads();
-                double sx = 0.0, sy = 0.0;
-                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
-                const double du = sqrt(sx), dv = sqrt(sy);
-                const bool stop = tol > 0.0 && fmax(du, dv) <= tol;
-                if (blockIdx.x == 0 && tid == 0) {
-                    h->du = du;
-                    h->dv = dv;
-                    h->last_check = l;
-                    if (stop) {
-                        h->iters_done = l;
-                        h->done = 1;
+                // (squared norms against tol^2: the square roots are taken
+                // once, for the stats)
+                if (tid < 32) {
+                    double sx, sy;
+                    sum_partials_warp0(part, (int)nblocks, sx, sy);
+                    if (tid == 0) {
+                        const bool stop = tol > 0.0 && fmax(sx, sy) <= tol * tol;
+                        s_red[0] = stop ? 1.0 : 0.0;
+                        if (blockIdx.x == 0) {
+                            h->du2 = sx;
+                            h->dv2 = sy;
+                            h->last_check = l;
+                            if (stop) {
+                                h->iters_done = l;
+                                h->done = 1;
+                            }
+                        }
                     }
                 }
+                __syncthreads();
+                const bool stop = s_red[0] != 0.0;
                 ++chk;
                 __syncthreads();
                 if (stop) return true;
@@ -711,58 +709,42 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
             T* po1 = p1o(); T* po2 = p2o();
             each([&](int a) { dual_one(P, a, O, pi1, pi2, Wc, po1, po2, seed); });
             pb ^= 1;
-            if (!grid_sync(h, nblocks, gen)) return false;
-            // the previous iteration's stopping test may have fired
-            if (sw == 0 && it > 0 && (it % C == 0) && *(volatile int*)&h->done) return true;
+            bool done;
+            if (!grid_sync_poll(h, nblocks, gen, sw == 0 && it > 0 && (it % C == 0), done)) return false;
+            if (done) return true;   // the previous iteration's stopping test fired
             if (sw + 1 < n_inner) {
                 for (int b = a0 + tid; b < a1; b += nt)
-                    primal_one(P, b, O, p1c(), p2c(), Uu, Wc, true, false, false, 0u, dummy0, dummy1);
+                    primal_one(P, b, O, p1c(), p2c(), Uu, Up, Wc, true, false, false, false, 0u, dummy0, dummy1);
                 if (!grid_sync(h, nblocks, gen)) return false;
             }
         }
         const bool check = (l % C == 0) || l == iters;
-        const bool write_u = check || ((l + 1) % C == 0) || l == iters;
+        const bool write_u = check;   // the output u and the stopped iterate
+        const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
         const T* q1s = p1c(); const T* q2s = p2c();
-        each([&](int a) { primal_one(P, a, O, q1s, q2s, Uu, Wc, false, check, write_u, seed, du2, dv2); });
+        each([&](int a) { primal_one(P, a, O, q1s, q2s, Uu, Up, Wc, false, check, write_u, write_prev, seed, du2, dv2); });
         if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);
         if (check) {
-            double x = du2, y = dv2;
-            for (int d = 16; d > 0; d >>= 1) {
-                x += __shfl_down_sync(0xffffffffu, x, d);
-                y += __shfl_down_sync(0xffffffffu, y, d);
-            }
-            const int lane = tid & 31, wid = tid >> 5;
-            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
-            __syncthreads();
+            float x = du2, y = dv2;
+            block_sum2f<NT>(x, y, reinterpret_cast<float*>(s_red));
             if (tid == 0) {
-                double sx = 0.0, sy = 0.0;
-                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
-                partials[2 * blockIdx.x] = sx;
-                partials[2 * blockIdx.x + 1] = sy;
+                partials[2 * blockIdx.x] = x;
+                partials[2 * blockIdx.x + 1] = y;
             }
         }
         if (!grid_sync(h, nblocks, gen)) return false;
         if (check && blockIdx.x == 0) {
-            // Section 4 stopping test: fixed-order FP64 sum of the block partials
-            double x = 0.0, y = 0.0;
-            for (int k = tid; k < (int)nblocks; k += nt) { x += __ldcg(partials + 2 * k); y += __ldcg(partials + 2 * k + 1); }
-            for (int d = 16; d > 0; d >>= 1) {
-                x += __shfl_down_sync(0xffffffffu, x, d);
-                y += __shfl_down_sync(0xffffffffu, y, d);
-            }
-            const int lane = tid & 31, wid = tid >> 5;
-            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
-            __syncthreads();
+            // Section 4 stopping test: fixed-order FP64 sum of the block partials,
+            // squared norms against tol^2 (square roots taken once, for the stats)
+            double sx = 0.0, sy = 0.0;
+            if (tid < 32) sum_partials_warp0(partials, (int)nblocks, sx, sy);
             if (tid == 0) {
-                double sx = 0.0, sy = 0.0;
-                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
-                const double du = sqrt(sx), dv = sqrt(sy);
-                h->du = du;
-                h->dv = dv;
+                h->du2 = sx;
+                h->dv2 = sy;
                 h->last_check = l;
-                if (tol > 0.0 && fmax(du, dv) <= tol) {
+                if (tol > 0.0 && fmax(sx, sy) <= tol * tol) {
                     h->iters_done = l;
                     __threadfence();
                     h->done = 1;
@@ -862,8 +844,9 @@ __device__ __forceinline__ void dual_gh(const IterParams& P, int i, int a, uint8
 
 template <typename T>
 __device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, uint8_t fl, const PrimalView& Q,
-                                          T* V, const float* F, float* U, float* Wg, bool check, bool write_u,
-                                          uint32_t seed, float& du2, float& dv2) {
+                                          T* V, const float* F, float* U, float* Up, float* Wg, bool check,
+                                          bool write_u, bool write_prev, uint32_t seed, float& du2,
+                                          float& dv2) {
     const float q1 = Q.q1[i], q2 = Q.q2[i];
     const float q1u = Q.n1[Q.ou[i]], q2l = Q.n2[Q.ol[i]];
     const float vv = Store<T>::ld_rw(V, i) + Store<T>::vbias;
@@ -876,10 +859,11 @@ __device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, uin
     Q.w[i] = wv;
     if (fl & kFlExport) Wg[a] = wv;
     if (check) {
-        const float da = un - U[a], db = vn - vv;
+        const float da = un - Up[a], db = vn - vv;
         du2 = fmaf(da, da, du2);
         dv2 = fmaf(db, db, dv2);
     }
+    if (write_prev) Up[a] = un;
     if (write_u) U[a] = un;
 }
 
@@ -936,8 +920,8 @@ template <typename T, int NT, int UNROLL>
 __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const GhostState<T>& S, int a0, int a1,
                                                       int iters, int check_every, double tol, int64_t stride,
                                                       T* P1a, T* P1b, T* P2a, T* P2b, const float* F,
-                                                      float* U, float* Wc, double* partials, WsHeader* h,
-                                                      float* ckpt, int ckpt_every, double* s_red,
+                                                      float* U, float* Up, float* Wc, double* partials,
+                                                      WsHeader* h, float* ckpt, int ckpt_every, double* s_red,
                                                       unsigned gen, int* fb, int* lf) {
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = NT;
@@ -1005,15 +989,17 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
                 each([&](int a) { dual_gh(P, a - a0, a, S.fl[a - a0], D, o1, o2, seed); });
             }
             pb ^= 1;
-            if (!grid_sync(h, nblocks, gen)) return false;
-            if (it > 0 && (it % C == 0) && *(volatile int*)&h->done) {
+            bool done;
+            if (!grid_sync_poll(h, nblocks, gen, it > 0 && (it % C == 0), done)) return false;
+            if (done) {
                 *fb = pb ^ 1;   // the dual step after the stopping test wrote the other buffer
                 *lf = it;
                 return true;
             }
         }
         const bool check = (l % C == 0) || l == iters;
-        const bool write_u = check || ((l + 1) % C == 0) || l == iters;
+        const bool write_u = check;   // the output u and the stopped iterate
+        const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
         PrimalView Q;
@@ -1031,19 +1017,19 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
             each([&](int a) {
                 const uint8_t f = S.fl[a - a0];
                 if (!(f & kFlPrimalGhost))
-                    primal_gh(P, a - a0, a, f, Q, Vs, F, U, Wc, check, write_u, seed, du2, dv2);
+                    primal_gh(P, a - a0, a, f, Q, Vs, F, U, Up, Wc, check, write_u, write_prev, seed, du2, dv2);
             });
             R.store(S, L.gd, L.gd + L.gp, pb, nt);
             __syncthreads();
             for (int e = tid; e < L.nbp; e += nt) {
                 const int i = S.bp[e];
-                primal_gh(P, i, a0 + i, S.fl[i], Q, Vs, F, U, Wc, check, write_u, seed, du2, dv2);
+                primal_gh(P, i, a0 + i, S.fl[i], Q, Vs, F, U, Up, Wc, check, write_u, write_prev, seed, du2, dv2);
             }
         } else {
             fill_ghosts(S, L.gd, L.gd + L.gp, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
             __syncthreads();
             each([&](int a) {
-                primal_gh(P, a - a0, a, S.fl[a - a0], Q, Vs, F, U, Wc, check, write_u, seed, du2, dv2);
+                primal_gh(P, a - a0, a, S.fl[a - a0], Q, Vs, F, U, Up, Wc, check, write_u, write_prev, seed, du2, dv2);
             });
         }
         if (ckpt && l % ckpt_every == 0 && l < iters) {
@@ -1051,40 +1037,24 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
             save(l / ckpt_every);
         }
         if (check) {
-            double x = du2, y = dv2;
-            for (int d = 16; d > 0; d >>= 1) {
-                x += __shfl_down_sync(0xffffffffu, x, d);
-                y += __shfl_down_sync(0xffffffffu, y, d);
-            }
-            const int lane = tid & 31, wid = tid >> 5;
-            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
-            __syncthreads();
+            float x = du2, y = dv2;
+            block_sum2f<NT>(x, y, reinterpret_cast<float*>(s_red));
             if (tid == 0) {
-                double sx = 0.0, sy = 0.0;
-                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
-                partials[2 * blockIdx.x] = sx;
-                partials[2 * blockIdx.x + 1] = sy;
+                partials[2 * blockIdx.x] = x;
+                partials[2 * blockIdx.x + 1] = y;
             }
         }
         if (!grid_sync(h, nblocks, gen)) return false;
         if (check && blockIdx.x == 0) {
-            double x = 0.0, y = 0.0;
-            for (int k = tid; k < (int)nblocks; k += nt) { x += __ldcg(partials + 2 * k); y += __ldcg(partials + 2 * k + 1); }
-            for (int d = 16; d > 0; d >>= 1) {
-                x += __shfl_down_sync(0xffffffffu, x, d);
-                y += __shfl_down_sync(0xffffffffu, y, d);
-            }
-            const int lane = tid & 31, wid = tid >> 5;
-            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
-            __syncthreads();
+            // Section 4 stopping test: fixed-order FP64 sum of the block partials,
+            // squared norms against tol^2 (square roots taken once, for the stats)
+            double sx = 0.0, sy = 0.0;
+            if (tid < 32) sum_partials_warp0(partials, (int)nblocks, sx, sy);
             if (tid == 0) {
-                double sx = 0.0, sy = 0.0;
-                for (int w = 0; w < NT / 32; ++w) { sx += s_red[2 * w]; sy += s_red[2 * w + 1]; }
-                const double du = sqrt(sx), dv = sqrt(sy);
-                h->du = du;
-                h->dv = dv;
+                h->du2 = sx;
+                h->dv2 = sy;
                 h->last_check = l;
-                if (tol > 0.0 && fmax(du, dv) <= tol) {
+                if (tol > 0.0 && fmax(sx, sy) <= tol * tol) {
                     h->iters_done = l;
                     __threadfence();
                     h->done = 1;
@@ -1102,8 +1072,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
 k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
                 const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
                 T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
-                float* Wc, float* Wc2, double* partials, WsHeader* h, float* ckpt, int ckpt_every) {
-    __shared__ double s_red[2 * (NT / 32)];
+                float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h, float* ckpt,
+                int ckpt_every) {
+    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
     extern __shared__ __align__(16) unsigned char c_smem[];
     // set before the launch (capacity overflow): the same for every block
     if (*(volatile int*)&h->done) return;
@@ -1176,7 +1147,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
                 float d0 = 0.f, d1 = 0.f;
                 const Own<T, false> O{nb, stride, V, F, 0};
                 for (int a = a0 + tid; a < a1; a += nt)
-                    primal_one(P, a, O, P1a, P2a, U, Wc, true, false, false, 0u, d0, d1);
+                    primal_one(P, a, O, P1a, P2a, U, Up, Wc, true, false, false, false, 0u, d0, d1);
                 if (!grid_sync(h, nblocks, gen0)) return;
             }
             // ghost slots: dual kinds first (down, right, dl, ur), then primal (up, left)
@@ -1259,7 +1230,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
             int fb = 0, lf = iters;
             // the barrier generation continues from the warm-start barrier
             if (!compact_iterations_gh<T, NT, UNROLL>(P, S, a0, a1, iters, check_every, tol, stride, P1a, P1b,
-                                                       P2a, P2b, F, U, Wc, partials, h, ckpt, ckpt_every,
+                                                       P2a, P2b, F, U, Up, Wc, partials, h, ckpt, ckpt_every,
                                                        s_red, gen0, &fb, &lf))
                 return;
             __syncthreads();
@@ -1285,14 +1256,14 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
         __syncthreads();
         const Own<T, true> O{nb_s, per, v_s, F, a0};
         if (!compact_iterations<T, true, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
-                                                     stride, P1a, P1b, P2a, P2b, U, Wc, Wc2, partials, h,
+                                                     stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
                                                      ckpt, ckpt_every, s_red, fuse))
             return;
         for (int i = tid; i < a1 - a0; i += nt) V[a0 + i] = v_s[i];
     } else {
         const Own<T, false> O{nb, stride, V, F, 0};
         compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm, stride,
-                                                 P1a, P1b, P2a, P2b, U, Wc, Wc2, partials, h, ckpt,
+                                                 P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h, ckpt,
                                                  ckpt_every, s_red, fuse);
     }
 }
@@ -1338,8 +1309,8 @@ __global__ void k_solve_begin(WsHeader* h) {
     h->done = 0;
     h->iters_done = 0;
     h->last_check = 0;
-    h->du = 0.0;
-    h->dv = 0.0;
+    h->du2 = 0.0;
+    h->dv2 = 0.0;
     for (int k = 0; k < 4; ++k) h->tb_ticket[k] = 0;
     h->tb_buf = 0;
     h->n_smem_blocks = 0;
@@ -1363,11 +1334,10 @@ k_check(const double* __restrict__ partials, int n, int l, double tol, WsHeader*
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double du = sqrt(sa[0]), dv = sqrt(sb[0]);
-        h->du = du;
-        h->dv = dv;
+        h->du2 = sa[0];
+        h->dv2 = sb[0];
         h->last_check = l;
-        if (tol > 0.0 && fmax(du, dv) <= tol) {
+        if (tol > 0.0 && fmax(sa[0], sb[0]) <= tol * tol) {
             h->iters_done = l;
             h->done = 1;
         }
@@ -1377,8 +1347,8 @@ k_check(const double* __restrict__ partials, int n, int l, double tol, WsHeader*
 __global__ void k_solve_end(const WsHeader* __restrict__ h, const int32_t* __restrict__ counts,
                             int iters, double* stats) {
     stats[0] = h->done ? h->iters_done : iters;
-    stats[1] = h->du;
-    stats[2] = h->dv;
+    stats[1] = sqrt(h->du2);
+    stats[2] = sqrt(h->dv2);
     stats[3] = counts[1];
     stats[4] = counts[0];
     stats[5] = h->last_check;
@@ -1399,17 +1369,17 @@ static int grid_for(K kernel, int threads, int64_t max_blocks) {
 }
 
 struct CompactLayout {
-    size_t off[10];
+    size_t off[11];
     int64_t cap;       // RD pixels the state can hold
     int64_t stride;    // elements allocated per array (cap + a chunk of slack, multiple of 64)
 };
 
 // compact state: p1[2], p2[2], v (storage type), f, u, w (float32),
-// neighbour table (int32 x NB_COUNT rows), w2 (float32), each array 256-byte
-// aligned and `stride` elements long
-constexpr int kCompactArrays = 10;
+// neighbour table (int32 x NB_COUNT rows), w2, up (float32), each array
+// 256-byte aligned and `stride` elements long
+constexpr int kCompactArrays = 11;
 constexpr int kSlack = 256;   // spare elements past the capacity in every array
-constexpr size_t compact_per_element(size_t sz) { return 5 * sz + 16 + 4 * NB_COUNT; }
+constexpr size_t compact_per_element(size_t sz) { return 5 * sz + 20 + 4 * NB_COUNT; }
 static int64_t compact_stride(int64_t capacity) {
     return (int64_t)align_up((size_t)std::max<int64_t>(capacity, 1) + kSlack, 64);
 }
@@ -1427,7 +1397,8 @@ static CompactLayout compact_layout(size_t state_bytes, int storage) {
     C.off[6] = o; o = align_up(o + 4 * (size_t)stride, 256);   // u
     C.off[7] = o; o = align_up(o + 4 * (size_t)stride, 256);   // w
     C.off[8] = o; o = align_up(o + 4 * (size_t)NB_COUNT * stride, 256);   // neighbour table
-    C.off[9] = o;                                              // w2
+    C.off[9] = o; o = align_up(o + 4 * (size_t)stride, 256);   // w2
+    C.off[10] = o;                                             // up
     return C;
 }
 
@@ -1503,6 +1474,7 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     S.w = reinterpret_cast<float*>(sb + C.off[7]);
     S.nb = reinterpret_cast<int32_t*>(sb + C.off[8]);
     S.w2 = reinterpret_cast<float*>(sb + C.off[9]);
+    S.up = reinterpret_cast<float*>(sb + C.off[10]);
     S.cap = C.cap;
     S.stride = C.stride;
     k_batch_bases<<<1, 1, 0, s>>>(B, base, totals, C.cap, h);
@@ -1537,11 +1509,13 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     const int32_t* cnt = totals;
     float* F = S.f;
     float* U = S.u;
+    float* Up = S.up;
     float* Wc = S.w;
     float* Wc2 = S.w2;
     IterParams P = P0;
     void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&cnt, (void*)&nbp, &stride,
-                    &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Wc, &Wc2, &partials, &h, &ckpt, &ckpt_every};
+                    &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Up, &Wc, &Wc2, &partials, &h, &ckpt,
+                    &ckpt_every};
     if (iters > 0 || warm) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NTs), args, smem, s));
         count_launch();
@@ -1689,7 +1663,7 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
         float d0 = 0.f, d1 = 0.f;
         for (int a = a0 + tid; a < a1; a += nt)
             primal_one(P, a, Own<float, false>{nb, stride, segv(0), F, 0}, segp1(0), segp2(0), nullptr,
-                       segw(0), true, false, false, 0u, d0, d1);
+                       nullptr, segw(0), true, false, false, false, 0u, d0, d1);
         if (!grid_sync(h, nblocks, gen)) return;
         for (int m = 0; m < M; ++m) {
             for (int a = a0 + tid; a < a1; a += nt)
@@ -1699,7 +1673,7 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
             for (int a = a0 + tid; a < a1; a += nt) {
                 segv(m + 1)[a] = segv(m)[a];    // primal_one updates v in place (same thread, no barrier)
                 primal_one(P, a, Own<float, false>{nb, stride, segv(m + 1), F, 0}, segp1(m + 1), segp2(m + 1),
-                           nullptr, segw(m + 1), false, false, false, 0u, d0, d1);
+                           nullptr, nullptr, segw(m + 1), false, false, false, false, 0u, d0, d1);
             }
             if (!grid_sync(h, nblocks, gen)) return;
         }

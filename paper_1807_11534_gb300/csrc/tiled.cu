@@ -183,11 +183,10 @@ k_solve_tiled(IterParams P, TbGeom G, int iters, int n_inner, int kmax, int chec
     int* const s_n = reinterpret_cast<int*>(misc + 32);                  // [2] RD pixels per buffer
     int* const s_first = reinterpret_cast<int*>(misc + 40);              // first ticket of a sweep
     int* const s_next = reinterpret_cast<int*>(misc + 44);               // next ticket (NBUF = 1)
-    double* const s_red = reinterpret_cast<double*>(misc + 64);          // [2 * 32]
+    double* const s_red = reinterpret_cast<double*>(misc + 64);          // [66]: block_sum2f (as floats), stop flag
 
     if (*(volatile int*)&h->done) return;
-    const unsigned FULL = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x;
     const unsigned nblocks = gridDim.x;
     const int64_t plane = (int64_t)P.H * P.ld;
     const int nact = *nact_p;
@@ -350,18 +349,11 @@ k_solve_tiled(IterParams P, TbGeom G, int iters, int n_inner, int kmax, int chec
                 }
             }
             if (is_check) {   // per-window partials of the stopping test, fixed order
-                double x = du2, y = dv2;
-                for (int d = 16; d > 0; d >>= 1) {
-                    x += __shfl_down_sync(FULL, x, d);
-                    y += __shfl_down_sync(FULL, y, d);
-                }
-                if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
-                __syncthreads();
+                float x = du2, y = dv2;
+                block_sum2f<kTbThreads>(x, y, reinterpret_cast<float*>(s_red));
                 if (tid == 0) {
-                    double sa = 0.0, sb = 0.0;
-                    for (int k = 0; k < kTbThreads / 32; ++k) { sa += s_red[2 * k]; sb += s_red[2 * k + 1]; }
-                    __stcg(part + 2 * a, sa);
-                    __stcg(part + 2 * a + 1, sb);
+                    __stcg(part + 2 * a, (double)x);
+                    __stcg(part + 2 * a + 1, (double)y);
                 }
             }
             if (NBUF == 1) {   // the buffer is free again: load the next window
@@ -383,31 +375,27 @@ k_solve_tiled(IterParams P, TbGeom G, int iters, int n_inner, int kmax, int chec
         cur_g ^= 1;
         ++sweep;
         if (is_check) {
-            // every block sums the window partials in window order
-            double x = 0.0, y = 0.0;
-            for (int k = tid; k < nact; k += kTbThreads) {
-                x += __ldcg(part + 2 * k);
-                y += __ldcg(part + 2 * k + 1);
-            }
-            for (int d = 16; d > 0; d >>= 1) {
-                x += __shfl_down_sync(FULL, x, d);
-                y += __shfl_down_sync(FULL, y, d);
-            }
-            if (lane == 0) { s_red[2 * wid] = x; s_red[2 * wid + 1] = y; }
-            __syncthreads();
-            double sx = 0.0, sy = 0.0;
-            for (int k = 0; k < kTbThreads / 32; ++k) { sx += s_red[2 * k]; sy += s_red[2 * k + 1]; }
-            const double du = sqrt(sx), dv = sqrt(sy);
-            const bool stop = tol > 0.0 && fmax(du, dv) <= tol;
-            if (blockIdx.x == 0 && tid == 0) {
-                h->du = du;
-                h->dv = dv;
-                h->last_check = l0;
-                if (stop) {
-                    h->iters_done = l0;
-                    h->done = 1;
+            // every block sums the window partials in window order (squared
+            // norms against tol^2; the square roots are taken once, for the stats)
+            if (tid < 32) {
+                double x, y;
+                sum_partials_warp0(part, nact, x, y);
+                if (tid == 0) {
+                    const bool stop = tol > 0.0 && fmax(x, y) <= tol * tol;
+                    s_red[0] = stop ? 1.0 : 0.0;
+                    if (blockIdx.x == 0) {
+                        h->du2 = x;
+                        h->dv2 = y;
+                        h->last_check = l0;
+                        if (stop) {
+                            h->iters_done = l0;
+                            h->done = 1;
+                        }
+                    }
                 }
             }
+            __syncthreads();
+            const bool stop = s_red[0] != 0.0;
             ++chk;
             __syncthreads();
             if (stop) break;
