@@ -166,6 +166,43 @@ seg_status seg_build_domain(const float* f, int H, int W, int ld,
                             int32_t* counts, float* delta_out,
                             void* ws, size_t ws_bytes, void* stream);
 
+/* Robust restriction (the Conclusion leaves open how to restrict the domain
+ * robustly when f is noisy; this is the reading used here).  As
+ * seg_build_domain, with two optional changes:
+ *   fbar     NULL (or f): RD = {|f| < delta}.  Otherwise a device [H][ld]
+ *            float32 field, normally the local mean of f from seg_box_mean:
+ *            RD = {|fbar| < delta} united with the pixels where f and fbar
+ *            have different signs ((f < 0) != (fbar < 0)), i.e. the pixels
+ *            whose fixed value H(-f) their neighbourhood contradicts; in
+ *            quantile mode delta is the quantile of |fbar|.
+ *   radius   RD is then grown by every pixel within Chebyshev distance radius
+ *            of an RD pixel (a (2r+1) x (2r+1) square dilation clipped to the
+ *            image); 0 = no growth.
+ * Fg = {f < 0} outside the final RD (the fixed values stay H(-f) of the raw
+ * f), Bg = the rest; counts and lists describe the final RD.  With fbar NULL
+ * and radius 0 the outputs equal seg_build_domain's.  wstart is used as
+ * scratch before it is written.
+ * Errors: as seg_build_domain (NaN/Inf in fbar too), and INVALID_ARG for
+ * radius outside [0, 32]. */
+seg_status seg_build_domain_robust(const float* f, const float* fbar, int H, int W, int ld,
+                                   double delta, double q, int radius, int tile_h,
+                                   uint32_t* act, uint32_t* fg, int32_t* wstart,
+                                   int32_t* tiles, int tiles_cap,
+                                   int32_t* pixels, int64_t pixels_cap,
+                                   int32_t* counts, float* delta_out,
+                                   void* ws, size_t ws_bytes, void* stream);
+
+/* Local mean for the robust restriction: out[i][j] = the mean of f over the
+ * (2r+1) x (2r+1) square around (i, j) clipped to the image, the window's
+ * values summed in FP64 in row-major order, divided by their count and
+ * rounded once to float32 (a bit-exact function of f).  Columns >= W of out
+ * are not written.
+ *   f, out   device [H][ld] float32, not aliased.
+ * Errors: INVALID_ARG (sizes, NULL, aliasing, radius outside [0, 16]), ALIGN,
+ * CUDA. */
+seg_status seg_box_mean(const float* f, int H, int W, int ld, int radius, float* out,
+                        void* stream);
+
 /* Restricted dual iteration (Sections 2.1 and 3) on the domain built by
  * seg_build_domain for the same f and tile_h:
  *   p <- (p + tau g) / (1 + tau |g|),  g = grad(div p - v/theta)   on RD

@@ -63,6 +63,12 @@ def _load():
         lib.oracle_quantile_delta.restype = F
         lib.oracle_domain.argtypes = [P, L, F, P]
         lib.oracle_domain.restype = None
+        lib.oracle_box_mean.argtypes = [P, I, I, I, P]
+        lib.oracle_box_mean.restype = None
+        lib.oracle_domain_robust.argtypes = [P, P, L, F, P]
+        lib.oracle_domain_robust.restype = None
+        lib.oracle_dilate.argtypes = [P, I, I, I, P]
+        lib.oracle_dilate.restype = None
         lib.oracle_pixel_list.argtypes = [P, L, P]
         lib.oracle_pixel_list.restype = L
         lib.oracle_tile_list.argtypes = [P, I, I, I, I, P]
@@ -159,6 +165,45 @@ def domain(f32, delta):
     reg = np.empty(f.shape, np.uint8)
     lib.oracle_domain(_ptr(f), f.size, float(np.float32(delta)), _ptr(reg))
     return reg
+
+
+def box_mean(f32, r):
+    """Local mean of f over (2r+1)^2 squares clipped to the image (float32)."""
+    lib = _load()
+    f = _c(f32, np.float32)
+    H, W = f.shape
+    out = np.empty_like(f)
+    lib.oracle_box_mean(_ptr(f), H, W, int(r), _ptr(out))
+    return out
+
+
+def domain_robust(f32, fbar, delta):
+    """Robust partition: RD = {|fbar| < delta} plus sign disagreements of f and fbar."""
+    lib = _load()
+    f = _c(f32, np.float32)
+    m = _c(fbar, np.float32)
+    reg = np.empty(f.shape, np.uint8)
+    lib.oracle_domain_robust(_ptr(f), _ptr(m), f.size, float(np.float32(delta)), _ptr(reg))
+    return reg
+
+
+def robust_region(f32, delta=None, q=-1.0, smooth=0, radius=0):
+    """The partition seg_build_domain_robust builds: threshold on the local mean
+    (smooth > 0) or on f, delta from q's quantile when q >= 0, then dilation."""
+    fbar = box_mean(f32, smooth) if smooth else _c(f32, np.float32)
+    d = quantile_delta(fbar, q) if q >= 0 else delta
+    reg = domain_robust(f32, fbar, d) if smooth else domain(f32, d)
+    return dilate(reg, radius) if radius else reg
+
+
+def dilate(region, r):
+    """RD grown by Chebyshev distance r (robust restriction, Conclusion)."""
+    lib = _load()
+    reg = _c(region, np.uint8)
+    H, W = reg.shape
+    out = np.empty_like(reg)
+    lib.oracle_dilate(_ptr(reg), H, W, int(r), _ptr(out))
+    return out
 
 
 def pixel_list(region):

@@ -154,6 +154,59 @@ void oracle_domain(const float* f32, int64_t n, float delta, uint8_t* region)
     }
 }
 
+/* Local mean for the robust restriction: the mean of f over the
+ * (2r+1) x (2r+1) square around each pixel, clipped to the image, summed in
+ * FP64 in row-major window order, divided by the count, rounded to float32. */
+void oracle_box_mean(const float* f, int H, int W, int r, float* out)
+{
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double sum = 0.0;
+            int cnt = 0;
+            for (int a = i - r; a <= i + r; ++a)
+                for (int b = j - r; b <= j + r; ++b)
+                    if (a >= 0 && a < H && b >= 0 && b < W) {
+                        sum += (double)f[(int64_t)a * W + b];
+                        ++cnt;
+                    }
+            out[(int64_t)i * W + j] = (float)(sum / (double)cnt);
+        }
+}
+
+/* Robust partition (the Conclusion's noisy-f case, as read here): RD =
+ * {|fbar| < delta} plus the pixels where f and its local mean fbar disagree
+ * in sign (their fixed value H(-f) is contradicted by the neighbourhood);
+ * outside RD the codes follow the raw f as in oracle_domain. */
+void oracle_domain_robust(const float* f32, const float* fbar, int64_t n, float delta,
+                          uint8_t* region)
+{
+    for (int64_t x = 0; x < n; ++x) {
+        float f = f32[x], m = fbar[x];
+        if (fabsf(m) < delta || ((f < 0.0f) != (m < 0.0f))) region[x] = 2;
+        else if (f < 0.0f) region[x] = 1;
+        else region[x] = 0;
+    }
+}
+
+/* Robust restriction (Conclusion: a robust restriction for noisy f is left
+ * open; the reading here grows RD by its neighbourhood): a pixel joins RD if
+ * some RD pixel lies within Chebyshev distance r, i.e. in the (2r+1) x (2r+1)
+ * square around it, clipped to the image.  Other pixels keep their code. */
+void oracle_dilate(const uint8_t* region, int H, int W, int r, uint8_t* out)
+{
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            uint8_t c = region[(int64_t)i * W + j];
+            for (int a = i - r; a <= i + r && c != 2; ++a)
+                for (int b = j - r; b <= j + r; ++b)
+                    if (a >= 0 && a < H && b >= 0 && b < W && region[(int64_t)a * W + b] == 2) {
+                        c = 2;
+                        break;
+                    }
+            out[(int64_t)i * W + j] = c;
+        }
+}
+
 int64_t oracle_pixel_list(const uint8_t* region, int64_t n, int32_t* list)
 {
     int64_t c = 0;

@@ -41,6 +41,19 @@ float oracle_quantile_delta(const float* f32, int64_t n, double q);
 /* Fg / Bg / RD partition of Section 3, decided in float32. */
 void oracle_domain(const float* f32, int64_t n, float delta, uint8_t* region);
 
+/* Local mean of f over (2r+1)^2 squares clipped to the image (FP64 sum in
+ * row-major window order, one rounding to float32). */
+void oracle_box_mean(const float* f, int H, int W, int r, float* out);
+
+/* Robust partition: RD = {|fbar| < delta} plus the pixels where f and fbar
+ * differ in sign; Fg / Bg from the raw f outside RD. */
+void oracle_domain_robust(const float* f32, const float* fbar, int64_t n, float delta,
+                          uint8_t* region);
+
+/* Robust restriction (Conclusion): RD grown by every pixel within Chebyshev
+ * distance r of an RD pixel; the other codes are kept. */
+void oracle_dilate(const uint8_t* region, int H, int W, int r, uint8_t* out);
+
 /* Row-major linear indices of RD pixels; returns the count. */
 int64_t oracle_pixel_list(const uint8_t* region, int64_t n, int32_t* list);
 

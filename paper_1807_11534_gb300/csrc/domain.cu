@@ -11,6 +11,11 @@
 // pixel (i, j) is wstart[i][j/32] + popc(act[i][j/32] & lanemask_lt(j%32)).
 // Integer scans only: the outputs are bit-exact functions of f and delta.
 //
+// Robust restriction (the Conclusion's open point for noisy f): RD may be
+// grown by every pixel within Chebyshev distance r of an RD pixel (a square
+// dilation of the RD bit plane, rows then columns), before the lists are
+// built; the grown pixels start from u0 = H(-f) like any RD pixel.
+//
 // Quantile mode (Section 3: q-hat grows from 0 until |RD| / n reaches q):
 // delta is the float just above the k-th smallest |f|, k = ceil(q n), found
 // by an exact 4-pass radix select on the bit patterns of |f| (for
@@ -83,8 +88,11 @@ __global__ void k_q_finish(WsHeader* h) {
 }
 
 // One warp per mask word: lane b classifies pixel (i, 32k + b).
-__global__ void k_classify(const float* __restrict__ f, int H, int W, int ld, int nw,
-                           WsHeader* h, uint32_t* __restrict__ act, uint32_t* __restrict__ fg) {
+// fsel: the field thresholded (f, or its local mean fbar for the robust
+// restriction, which also admits the pixels whose sign differs from fbar's).
+__global__ void k_classify(const float* __restrict__ f, const float* __restrict__ fsel, int H,
+                           int W, int ld, int nw, WsHeader* h, uint32_t* __restrict__ act,
+                           uint32_t* __restrict__ fg) {
     __shared__ int s_fg[kDomThreads / 32];
     const float delta = h->delta;
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -96,9 +104,10 @@ __global__ void k_classify(const float* __restrict__ f, int H, int W, int ld, in
         int j = (int)(word - i * nw) * 32 + lane;
         bool a = false, g = false, bad = false;
         if (j < W) {
-            float fv = f[i * ld + j];
-            bad = !isfinite(fv);
-            a = fabsf(fv) < delta;
+            const float fv = f[i * ld + j];
+            const float fs = fsel[i * ld + j];
+            bad = !isfinite(fv) || !isfinite(fs);
+            a = fabsf(fs) < delta || ((fv < 0.0f) != (fs < 0.0f));
             g = fv < 0.0f;
         }
         unsigned wa = __ballot_sync(0xffffffffu, a);
@@ -118,6 +127,78 @@ __global__ void k_classify(const float* __restrict__ f, int H, int W, int ld, in
         for (int w = 0; w < kDomThreads / 32; ++w) t += s_fg[w];
         if (t) atomicAdd(&h->n_fg, t);
     }
+}
+
+// Square dilation, horizontal half: one thread per word; bit b of word k is
+// column 32k + b, and a column joins if a column within r of it is in RD
+// (r <= 32: the neighbour words suffice).  Columns >= W stay clear.
+__global__ void k_dilate_rows(const uint32_t* __restrict__ act, int H, int W, int nw, int r,
+                              uint32_t* __restrict__ out, WsHeader* h) {
+    const int64_t word = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (word == 0) h->n_fg = 0;   // recounted by k_dilate_cols
+    if (word >= (int64_t)H * nw) return;
+    const int64_t i = word / nw;
+    const int k = (int)(word - i * nw);
+    const int ntx = (W + 31) / 32;
+    if (k >= ntx) {
+        out[word] = 0u;
+        return;
+    }
+    const uint32_t c = act[word];
+    const uint32_t pv = k > 0 ? act[word - 1] : 0u;
+    const uint32_t nx = k + 1 < ntx ? act[word + 1] : 0u;
+    uint32_t d = c;
+    for (int s = 1; s <= r; ++s) {
+        if (s < 32) d |= (c >> s) | (nx << (32 - s)) | (c << s) | (pv >> (32 - s));
+        else d |= nx | pv;
+    }
+    const int rem = W - 32 * k;
+    if (rem < 32) d &= (1u << rem) - 1u;
+    out[word] = d;
+}
+
+// Square dilation, vertical half: OR of the rows within r; recounts the
+// fixed foreground pixels (f < 0 outside the grown RD).
+__global__ void k_dilate_cols(const uint32_t* __restrict__ rows, int H, int nw, int r,
+                              const uint32_t* __restrict__ fg, uint32_t* __restrict__ act,
+                              WsHeader* h) {
+    __shared__ int s_fg[kDomThreads / 32];
+    const int64_t word = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int cnt = 0;
+    if (word < (int64_t)H * nw) {
+        const int i = (int)(word / nw);
+        const int k = (int)(word - (int64_t)i * nw);
+        const int i0 = i - r < 0 ? 0 : i - r, i1 = i + r >= H ? H - 1 : i + r;
+        uint32_t d = 0u;
+        for (int ii = i0; ii <= i1; ++ii) d |= rows[(int64_t)ii * nw + k];
+        act[word] = d;
+        cnt = __popc(fg[word] & ~d);
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) s_fg[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kDomThreads / 32; ++w) t += s_fg[w];
+        if (t) atomicAdd(&h->n_fg, t);
+    }
+}
+
+// Local mean of f over the (2r+1) x (2r+1) square clipped to the image: the
+// window's values summed in FP64 in row-major order, divided by the count
+// and rounded once to float32 (the rounding order is fixed, so the result is
+// a bit-exact function of f).
+__global__ void k_box_mean(const float* __restrict__ f, int H, int W, int ld, int r,
+                           float* __restrict__ out) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (int64_t)H * W) return;
+    const int i = (int)(x / W), j = (int)(x - (int64_t)i * W);
+    const int i0 = max(i - r, 0), i1 = min(i + r, H - 1), j0 = max(j - r, 0), j1 = min(j + r, W - 1);
+    double sum = 0.0;
+    for (int a = i0; a <= i1; ++a)
+        for (int b = j0; b <= j1; ++b) sum = __dadd_rn(sum, (double)f[(int64_t)a * ld + b]);
+    const double cnt = (double)((i1 - i0 + 1) * (j1 - j0 + 1));
+    out[(int64_t)i * ld + j] = __double2float_rn(__ddiv_rn(sum, cnt));
 }
 
 __global__ void k_tile_count(const uint32_t* __restrict__ act, int H, int nw, int ntx, int th,
@@ -189,12 +270,14 @@ __global__ void k_domain_finish(const WsHeader* __restrict__ h, int32_t* counts,
 
 using namespace seg;
 
-extern "C" seg_status seg_build_domain(const float* f, int H, int W, int ld, double delta, double q,
-                                       int tile_h, uint32_t* act, uint32_t* fg, int32_t* wstart,
-                                       int32_t* tiles, int tiles_cap, int32_t* pixels,
-                                       int64_t pixels_cap, int32_t* counts, float* delta_out,
-                                       void* ws, size_t ws_bytes, void* stream) {
+static seg_status build_domain(const float* f, const float* fbar, int H, int W, int ld,
+                               double delta, double q, int radius, int tile_h, uint32_t* act, uint32_t* fg,
+                               int32_t* wstart, int32_t* tiles, int tiles_cap, int32_t* pixels,
+                               int64_t pixels_cap, int32_t* counts, float* delta_out, void* ws,
+                               size_t ws_bytes, void* stream) {
     clear_error();
+    if (radius < 0 || radius > 32)
+        return fail(SEG_ERR_INVALID_ARG, "radius=%d not in [0, 32]", radius);
     if (!f || !act || !fg || !wstart || !tiles || !counts)
         return fail(SEG_ERR_INVALID_ARG, "f, act, fg, wstart, tiles and counts must be non-NULL");
     if (H <= 0 || W <= 0 || ld < W || (int64_t)H * W >= (1ll << 31))
@@ -207,6 +290,7 @@ extern "C" seg_status seg_build_domain(const float* f, int H, int W, int ld, dou
     if (!(q <= 1.0)) return fail(SEG_ERR_INVALID_ARG, "q=%g > 1", q);
     WsLayout L = ws_layout(H, W, tile_h);
     SEG_TRY(check_ws(ws, ws_bytes, L));
+    const float* fsel = fbar ? fbar : f;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     WsHeader* h = ws_at<WsHeader>(ws, L.header);
     int64_t n = (int64_t)H * W;
@@ -225,7 +309,7 @@ extern "C" seg_status seg_build_domain(const float* f, int H, int W, int ld, dou
             int blocks = (int)std::min<int64_t>((n + kDomThreads - 1) / kDomThreads, 152 * 8);
             for (int shift = 24; shift >= 0; shift -= 8) {
                 SEG_TRY_CUDA(cudaMemsetAsync(hist, 0, 4 * kHistBins, s));
-                k_q_hist<<<blocks, kDomThreads, 0, s>>>(f, H, W, ld, shift, h, hist);
+                k_q_hist<<<blocks, kDomThreads, 0, s>>>(fsel, H, W, ld, shift, h, hist);
                 SEG_LAUNCHED("k_q_hist");
                 k_q_select<<<1, 1, 0, s>>>(h, hist, shift);
                 SEG_LAUNCHED("k_q_select");
@@ -240,8 +324,17 @@ extern "C" seg_status seg_build_domain(const float* f, int H, int W, int ld, dou
     }
 
     int64_t nwords = (int64_t)H * nw;
-    k_classify<<<(unsigned)((nwords + 7) / 8), kDomThreads, 0, s>>>(f, H, W, ld, nw, h, act, fg);
+    k_classify<<<(unsigned)((nwords + 7) / 8), kDomThreads, 0, s>>>(f, fsel, H, W, ld, nw, h, act,
+                                                                    fg);
     SEG_LAUNCHED("k_classify");
+    if (radius > 0) {   // wstart (same shape, written later) holds the row pass
+        uint32_t* rows = reinterpret_cast<uint32_t*>(wstart);
+        const unsigned nb = (unsigned)((nwords + kDomThreads - 1) / kDomThreads);
+        k_dilate_rows<<<nb, kDomThreads, 0, s>>>(act, H, W, nw, radius, rows, h);
+        SEG_LAUNCHED("k_dilate_rows");
+        k_dilate_cols<<<nb, kDomThreads, 0, s>>>(rows, H, nw, radius, fg, act, h);
+        SEG_LAUNCHED("k_dilate_cols");
+    }
 
     int* cnt = ws_at<int>(ws, L.tile_cnt);
     int* flag = ws_at<int>(ws, L.tile_flag);
@@ -261,5 +354,43 @@ extern "C" seg_status seg_build_domain(const float* f, int H, int W, int ld, dou
     SEG_LAUNCHED("k_tile_emit");
     k_domain_finish<<<1, 1, 0, s>>>(h, counts, delta_out, n_tiles_dev, n_act_dev);
     SEG_LAUNCHED("k_domain_finish");
+    return SEG_OK;
+}
+
+extern "C" seg_status seg_build_domain(const float* f, int H, int W, int ld, double delta, double q,
+                                       int tile_h, uint32_t* act, uint32_t* fg, int32_t* wstart,
+                                       int32_t* tiles, int tiles_cap, int32_t* pixels,
+                                       int64_t pixels_cap, int32_t* counts, float* delta_out,
+                                       void* ws, size_t ws_bytes, void* stream) {
+    return build_domain(f, nullptr, H, W, ld, delta, q, 0, tile_h, act, fg, wstart, tiles,
+                        tiles_cap, pixels, pixels_cap, counts, delta_out, ws, ws_bytes, stream);
+}
+
+extern "C" seg_status seg_build_domain_robust(const float* f, const float* fbar, int H, int W,
+                                              int ld, double delta, double q, int radius,
+                                              int tile_h, uint32_t* act, uint32_t* fg,
+                                              int32_t* wstart, int32_t* tiles, int tiles_cap,
+                                              int32_t* pixels, int64_t pixels_cap,
+                                              int32_t* counts, float* delta_out, void* ws,
+                                              size_t ws_bytes, void* stream) {
+    if (fbar == f) fbar = nullptr;
+    return build_domain(f, fbar, H, W, ld, delta, q, radius, tile_h, act, fg, wstart, tiles,
+                        tiles_cap, pixels, pixels_cap, counts, delta_out, ws, ws_bytes, stream);
+}
+
+extern "C" seg_status seg_box_mean(const float* f, int H, int W, int ld, int radius, float* out,
+                                   void* stream) {
+    clear_error();
+    if (!f || !out) return fail(SEG_ERR_INVALID_ARG, "f and out must be non-NULL");
+    if (H <= 0 || W <= 0 || ld < W || (int64_t)H * W >= (1ll << 31))
+        return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d", H, W, ld);
+    if (ld % 32) return fail(SEG_ERR_ALIGN, "ld=%d is not a multiple of 32", ld);
+    if (radius < 0 || radius > 16)
+        return fail(SEG_ERR_INVALID_ARG, "radius=%d not in [0, 16]", radius);
+    if (f == out) return fail(SEG_ERR_INVALID_ARG, "out must not alias f");
+    const int64_t n = (int64_t)H * W;
+    k_box_mean<<<(unsigned)((n + kDomThreads - 1) / kDomThreads), kDomThreads, 0,
+                 static_cast<cudaStream_t>(stream)>>>(f, H, W, ld, radius, out);
+    SEG_LAUNCHED("k_box_mean");
     return SEG_OK;
 }

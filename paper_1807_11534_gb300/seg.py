@@ -78,6 +78,9 @@ SIGNATURES = {
     "seg_read_status": ([_P, _Z, _P], _I),
     "seg_make_fitting": ([_P, _I, _I, _I, _D, _D, _P, _P, _I, _D, _P, _P, _P, _Z, _P], _I),
     "seg_build_domain": ([_P, _I, _I, _I, _D, _D, _I, _P, _P, _P, _P, _I, _P, _L, _P, _P, _P, _Z, _P], _I),
+    "seg_build_domain_robust": ([_P, _P, _I, _I, _I, _D, _D, _I, _I, _P, _P, _P, _P, _I, _P, _L, _P,
+                                 _P, _P, _Z, _P], _I),
+    "seg_box_mean": ([_P, _I, _I, _I, _I, _P, _P], _I),
     "seg_update_means": ([_P, _P, _I, _I, _I, _D, _P, _P, _Z, _P], _I),
     "seg_solve": ([_P, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(seg_params),
                    _P, _P, _P, _P, _P, _Z, _P, _P, _Z, _P], _I),
@@ -187,6 +190,31 @@ def seg_build_domain(f, delta, q, tile_h, act, fg, wstart, tiles, pixels, counts
                                 tiles.numel(), _ptr(pixels),
                                 0 if pixels is None else pixels.numel(), _ptr(counts),
                                 _ptr(delta_out), _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def seg_build_domain_robust(f, fbar, delta, q, radius, tile_h, act, fg, wstart, tiles, pixels,
+                            counts, delta_out, ws, stream=None):
+    lib = load()
+    _check(lib.seg_build_domain_robust(_ptr(f), _ptr(fbar), f.shape[0], _W(f), f.stride(0),
+                                       float(delta), float(q), int(radius), int(tile_h), _ptr(act),
+                                       _ptr(fg), _ptr(wstart), _ptr(tiles), tiles.numel(),
+                                       _ptr(pixels), 0 if pixels is None else pixels.numel(),
+                                       _ptr(counts), _ptr(delta_out), _ptr(ws), _nbytes(ws),
+                                       _stream(stream)))
+
+
+def seg_box_mean(f, radius, out, stream=None):
+    _check(load().seg_box_mean(_ptr(f), f.shape[0], _W(f), f.stride(0), int(radius), _ptr(out),
+                               _stream(stream)))
+
+
+def _build_into(f, delta, q, radius, tile_h, d, ws, stream, fbar=None):
+    if radius or fbar is not None:
+        seg_build_domain_robust(f, fbar, delta, q, radius, tile_h, d.act, d.fg, d.wstart, d.tiles,
+                                d.pixels, d.counts, d.delta, ws, stream)
+    else:
+        seg_build_domain(f, delta, q, tile_h, d.act, d.fg, d.wstart, d.tiles, d.pixels, d.counts,
+                         d.delta, ws, stream)
 
 
 def seg_solve(f, act, fg, wstart, tiles, counts, params: seg_params, u, v, p1, p2, state, stats,
@@ -324,7 +352,8 @@ class Domain:
         return -(-self.H // self.tile_h) * -(-self.W // 32)
 
 
-def build_domain(f, delta=math.inf, q=-1.0, tile_h=16, ws=None, with_pixels=True, stream=None):
+def build_domain(f, delta=math.inf, q=-1.0, tile_h=16, ws=None, with_pixels=True, stream=None,
+                 radius=0, fbar=None):
     H, W = f.shape[0], _W(f)
     ld = f.stride(0)
     dev = f.device
@@ -340,8 +369,7 @@ def build_domain(f, delta=math.inf, q=-1.0, tile_h=16, ws=None, with_pixels=True
                  delta=torch.zeros(1, dtype=torch.float32, device=dev))
     if ws is None:
         ws = workspace(H, W, tile_h, dev)
-    seg_build_domain(f, delta, q, tile_h, dom.act, dom.fg, dom.wstart, dom.tiles, dom.pixels,
-                     dom.counts, dom.delta, ws, stream)
+    _build_into(f, delta, q, radius, tile_h, dom, ws, stream, fbar)
     return dom
 
 
@@ -409,14 +437,22 @@ class Solver:
         seg_make_fitting(z, c1, c2, label, markers, gamma, self.f, self.c, self.ws, self.stream)
         return self.f
 
-    def domain(self, f=None, delta=math.inf, q=-1.0, with_pixels=True):
+    def domain(self, f=None, delta=math.inf, q=-1.0, with_pixels=True, radius=0, smooth=0):
+        """RD = {|f| < delta} (or q's quantile).  smooth > 0: the robust
+        restriction on the local mean of f over (2 smooth + 1)^2 squares;
+        radius > 0: RD grown by that many pixels (seg_build_domain_robust)."""
         f = self.f if f is None else f
+        fbar = None
+        if smooth:
+            if getattr(self, "fbar", None) is None:
+                self.fbar = image(self.H, self.W, device=self.device)
+            seg_box_mean(f, smooth, self.fbar, self.stream)
+            fbar = self.fbar
         if self.dom is None or (self.dom.pixels is None) == with_pixels:
-            self.dom = build_domain(f, delta, q, self.tile_h, self.ws, with_pixels, self.stream)
+            self.dom = build_domain(f, delta, q, self.tile_h, self.ws, with_pixels, self.stream,
+                                    radius, fbar)
         else:
-            d = self.dom
-            seg_build_domain(f, delta, q, self.tile_h, d.act, d.fg, d.wstart, d.tiles, d.pixels,
-                             d.counts, d.delta, self.ws, self.stream)
+            _build_into(f, delta, q, radius, self.tile_h, self.dom, self.ws, self.stream, fbar)
         return self.dom
 
     def solve(self, lam, theta=0.2, tau=0.125, iters=100, tol=0.0, n_inner=1, check_every=10,

@@ -124,6 +124,16 @@ def small_example(seed=0, H=256, W=256, iters=500, delta=float("inf")) -> Proble
                    name=f"shapes{H}x{W}_s{seed}")
 
 
+def noisy_example(seed=0, H=96, W=96, sigma=0.25, iters=600) -> Problem:
+    """Strong-noise case for the robust restriction: 3 disks/rectangles of
+    size H/6..H/2 at 0.3 on 0.7 + N(0, sigma) (sigma = 0.25 flips the sign of
+    the Chan-Vese term on about a fifth of the pixels); c1 = 0.3, c2 = 0.7,
+    lambda = 2."""
+    z, lab = shapes_image(H, W, 3, max(H // 6, 2), max(H // 2, 3), 0.3, 0.7, sigma, seed)
+    return Problem(z=z, label=lab, c1=0.3, c2=0.7, lam=2.0, iters=iters, delta=float("inf"),
+                   name=f"noisy{H}x{W}_s{seed}")
+
+
 def ellipses_ds(seed=0, H=2048, W=2048, n_ell=40, n_markers=20, lam=2.0, gamma=0.5,
                 iters=1000, delta=float("inf")) -> Problem:
     """2048x2048 image: `n_ell` ellipses with semi-axes U[10, 120] (scaled with

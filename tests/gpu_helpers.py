@@ -27,14 +27,15 @@ def bits_to_mask(words, W):
 
 
 def run_gpu(f32, delta=math.inf, q=-1.0, lam=1.0, theta=0.2, tau=0.125, iters=100, tol=0.0,
-            n_inner=1, check_every=10, mode="compact", storage="f32", tile_h=16, warm=None, sweep=0):
+            n_inner=1, check_every=10, mode="compact", storage="f32", tile_h=16, warm=None, sweep=0,
+            radius=0, smooth=0):
     """Domain + solve for a float32 fitting term; returns a dict of numpy
     outputs (u, v, p1, p2 as float64) and the solver."""
     seg = seg_mod()
     H, W = f32.shape
     S = seg.Solver(H, W, tile_h=tile_h, mode=mode, storage=storage)
     S.f[:, :W].copy_(torch.from_numpy(np.ascontiguousarray(f32)))
-    S.domain(delta=delta, q=q)
+    S.domain(delta=delta, q=q, radius=radius, smooth=smooth)
     if warm is not None:
         for name in ("u", "v", "p1", "p2"):
             getattr(S, name)[:, :W].copy_(torch.from_numpy(np.asarray(getattr(warm, name), np.float32)))

@@ -567,3 +567,86 @@ def test_chan_vese_finds_the_levels_of_a_noiseless_two_level_image(orc):
     assert np.array_equal(st.u > 0.5, disk)
     assert hist[1] == (float(np.float32(0.3)), float(np.float32(0.7)))
     assert used == hist[1] == hist[3]
+
+
+# ------------------------------------------------- robust restriction (Conclusion)
+
+@pytest.mark.parametrize("r", [0, 1, 2, 5])
+def test_dilation_is_the_square_binary_dilation(orc, r):
+    """RD grown by Chebyshev distance r = binary dilation of the RD mask by a
+    (2r+1) x (2r+1) square (scipy.ndimage, zero outside the image); the other
+    pixels keep their Fg / Bg code."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(40 + r)
+    reg = rng.choice(np.array([0, 1, 2], np.uint8), size=(37, 53), p=[0.5, 0.45, 0.05])
+    out = orc.dilate(reg, r)
+    want = ndimage.binary_dilation(reg == 2, structure=np.ones((2 * r + 1, 2 * r + 1), bool))
+    np.testing.assert_array_equal(out == 2, want)
+    np.testing.assert_array_equal(out[~want], reg[~want])
+
+
+def test_dilation_of_one_pixel_is_a_clipped_square(orc):
+    reg = np.zeros((9, 12), np.uint8)
+    reg[1, 10] = 2
+    out = orc.dilate(reg, 3)
+    want = np.zeros((9, 12), bool)
+    want[0:5, 7:12] = True
+    np.testing.assert_array_equal(out == 2, want)
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_box_mean_is_the_clipped_window_mean(orc, r):
+    """Inside the image the local mean equals scipy's uniform filter (a
+    running-sum implementation, so within float32 rounding); at a corner it
+    is the mean of the (r+1) x (r+1) window that remains; a constant field is
+    kept exactly."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(7 + r)
+    f = rng.normal(0, 0.4, (30, 41)).astype(np.float32)
+    m = orc.box_mean(f, r)
+    ref = ndimage.uniform_filter(f.astype(np.float64), 2 * r + 1, mode="constant")
+    inner = (slice(r, -r), slice(r, -r))
+    np.testing.assert_allclose(m[inner], ref[inner], rtol=0, atol=2e-7)
+    assert m[0, 0] == np.float32(np.mean(f[: r + 1, : r + 1].astype(np.float64)))
+    assert m[-1, -1] == np.float32(np.mean(f[-r - 1:, -r - 1:].astype(np.float64)))
+    c = np.full((11, 13), 0.3125, np.float32)
+    assert np.all(orc.box_mean(c, r) == np.float32(0.3125))
+    np.testing.assert_array_equal(orc.box_mean(f, 0), f)
+
+
+def test_robust_partition_reduces_to_the_plain_one(orc):
+    """With fbar = f there is no sign disagreement: the Section 3 partition."""
+    f = np.random.default_rng(3).normal(0, 0.3, (25, 33)).astype(np.float32)
+    f[2, 2] = 0.0
+    np.testing.assert_array_equal(orc.domain_robust(f, f, 0.1), orc.domain(f, 0.1))
+    m = orc.box_mean(f, 1)
+    reg = orc.domain_robust(f, m, 0.0)   # empty threshold: only the sign disagreements
+    np.testing.assert_array_equal(reg == 2, (f < 0) != (m < 0))
+    np.testing.assert_array_equal(reg[reg != 2], np.where(f < 0, 1, 0)[reg != 2])
+
+
+def test_robust_restriction_trend_with_strong_noise(orc):
+    """The Conclusion expects noisy f to need a more robust restriction.  With
+    N(0, 0.25) noise (a fifth of the pixels have the wrong sign of f):
+    restricting on the local mean of f (plus the sign disagreements) at
+    |RD|/N ~ 0.25 agrees with the full-domain result much better than the
+    plain |f| threshold at the same size, and better than the plain one at
+    twice the size; growing the plain RD by one pixel also helps."""
+    P = synth.noisy_example(seed=0)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    full = orc.solve(f, orc.domain(f, math.inf), 2.0, iters=600).u > 0.5
+
+    def e1(**kw):
+        reg = orc.robust_region(f, **kw)
+        m = orc.solve(f, reg, 2.0, iters=600).u > 0.5
+        return float(np.mean(m == full)), float(np.mean(reg == 2))
+
+    e_plain, a_plain = e1(q=0.25)
+    e_half, _ = e1(q=0.5)
+    e_rob, a_rob = e1(q=0.05, smooth=1)
+    e_q1, _ = e1(q=0.1)
+    e_dil, _ = e1(q=0.1, radius=1)
+    assert abs(a_rob - a_plain) < 0.03
+    assert e_rob > e_plain + 0.08
+    assert e_rob > e_half
+    assert e_dil > e_q1
