@@ -524,12 +524,38 @@ def row_storage(dev, flush):
     return {"config": "4096^2 polygons, CV, lambda=1, delta=0.1, 2000 iterations", **out}
 
 
+def row_chan_vese(dev, flush):
+    """Chan-Vese loop (the intensities re-estimated from u between solves):
+    the 2048x2048 ellipse image with the piecewise-constant term only, start
+    (c1, c2) = (0.35, 0.65), delta = 0.2, 5 outer steps of 200 warm-started
+    iterations, all on the device in one CUDA graph."""
+    import torch
+    from paper_1807_11534_gb300 import seg, synth
+    stream = torch.cuda.current_stream()
+    P = synth.ellipses_ds(seed=0, H=2048, W=2048)
+    z = seg.upload(P.z, dev)
+    S = seg.Solver(2048, 2048, tile_h=32, mode="compact", device=dev)
+    run = lambda: S.chan_vese(z, 2.0, 0.35, 0.65, outer=5, iters=200, delta=0.2)
+    run()
+    torch.cuda.synchronize()
+    g = seg.capture_graph(run)
+    ms = _graph_ms(g, stream, flush)
+    S.check_status()
+    A = int(S.dom.counts[1].item())
+    c = S.c.cpu().numpy().tolist()
+    return {"config": "2048^2 ellipses, CV term, lambda=2, delta=0.2, 5 outer x 200 iterations",
+            "ms": ms, "ms_per_outer_step": ms / 5, "c_final": c, "active_pixels_last": A,
+            "active_Mpixel_iter_per_s": A * 1000 / (ms * 1e-3) / 1e6}
+
+
 def run_rows(args, dev):
     """The hot-path rows beside the headline: adjoint (differentiation
-    workload), 16-bit storage (precision workload), batched solve."""
+    workload), 16-bit storage (precision workload), batched solve, and the
+    Chan-Vese loop."""
     import torch
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    rows = {"a7_adjoint": row_adjoint(dev, flush), "a8_storage": row_storage(dev, flush)}
+    rows = {"a7_adjoint": row_adjoint(dev, flush), "a8_storage": row_storage(dev, flush),
+            "next_chan_vese": row_chan_vese(dev, flush)}
     b = run_batch(argparse.Namespace(**{**vars(args), "iters": None}), 0, 1)
     rows["a6_batch"] = {"config": "64 images, sides U{128..1024}, q ~ U[0.02, 0.4], 500 iterations, "
                                   "one persistent launch",
