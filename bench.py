@@ -440,6 +440,18 @@ def run_batch(args, rank, world):
 
 # ------------------------------------------------------------------ other rows
 
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of MEASURED_PEAKS.json, else
+    the 6.8 TB/s fallback of an earlier GB300 measurement."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    if "hbm_gbs" in peaks:
+        return float(peaks["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
 def _graph_ms(g, stream, flush, reps=3):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -548,6 +560,43 @@ def row_chan_vese(dev, flush):
             "active_Mpixel_iter_per_s": A * 1000 / (ms * 1e-3) / 1e6}
 
 
+PD_BYTES_PER_ACTIVE_ITER = 36   # read p1, p2, ubar, u, f; write p1, p2, u, ubar (float32)
+
+
+def row_pd(dev, flush):
+    """Restricted primal-dual (Chambolle-Pock) solve of Eq. CR on the
+    2048x2048 distance-selective image at delta = 0.2: time per iteration
+    (graph of 1000 iterations minus graph of 0, a test every 10), and the
+    agreement of its thresholded u with the dual iteration's on the same
+    domain after 1000 iterations each."""
+    import torch
+    from paper_1807_11534_gb300 import seg, synth
+    stream = torch.cuda.current_stream()
+    P = synth.ellipses_ds(seed=0, H=2048, W=2048)
+    z = seg.upload(P.z, dev)
+    label = seg.upload(P.label, dev)
+    markers = torch.from_numpy(P.markers.astype(np.int32)).to(dev)
+    S = seg.Solver(2048, 2048, tile_h=32, mode="compact", device=dev)
+    S.fitting(z, label=label, markers=markers, gamma=P.gamma)
+    S.domain(delta=0.2)
+    A = int(S.dom.counts[1].item())
+    g = {n: seg.capture_graph(lambda n=n: S.solve_pd(2.0, iters=n, check_every=10)) for n in (0, 1000)}
+    ms = {n: _graph_ms(gr, stream, flush) for n, gr in g.items()}
+    S.check_status()
+    u_pd = S.u.clone()
+    S.solve(2.0, iters=1000, check_every=1000)
+    torch.cuda.synchronize()
+    agree = float(((u_pd > 0.5) == (S.u > 0.5))[:, :2048].float().mean().item())
+    us = (ms[1000] - ms[0]) * 1000 / 1000
+    gbs = PD_BYTES_PER_ACTIVE_ITER * A / (us * 1e-6) / 1e9
+    return {"config": "2048^2 ellipses, DS term, lambda=2, delta=0.2, 1000 iterations, sigma=tau=1/sqrt(8)",
+            "active_pixels": A, "us_per_iter": us, "ms_1000": ms[1000],
+            "active_Mpixel_iter_per_s": A / (us * 1e-6) / 1e6,
+            "bytes_per_active_iter": PD_BYTES_PER_ACTIVE_ITER, "achieved_gbs": gbs,
+            "frac_of_measured_hbm": gbs / hbm_peak()[0],
+            "mask_agreement_with_dual_iteration": agree}
+
+
 def run_rows(args, dev):
     """The hot-path rows beside the headline: adjoint (differentiation
     workload), 16-bit storage (precision workload), batched solve, and the
@@ -555,7 +604,7 @@ def run_rows(args, dev):
     import torch
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     rows = {"a7_adjoint": row_adjoint(dev, flush), "a8_storage": row_storage(dev, flush),
-            "next_chan_vese": row_chan_vese(dev, flush)}
+            "next_chan_vese": row_chan_vese(dev, flush), "next_primal_dual": row_pd(dev, flush)}
     b = run_batch(argparse.Namespace(**{**vars(args), "iters": None}), 0, 1)
     rows["a6_batch"] = {"config": "64 images, sides U{128..1024}, q ~ U[0.02, 0.4], 500 iterations, "
                                   "one persistent launch",
@@ -630,12 +679,7 @@ def main():
     if args.workload == "batch":
         r = run_batch(args, rank, world)
         import torch
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except OSError:
-            pass
-        peak = float(peaks.get("hbm_gbs", 6800.0))
+        peak, _ = hbm_peak()
         value, ms = aggregate(r["A"] * r["iters"], r["ms"], world)
         line = {"metric": "active Mpixel-iters/s and % HBM roofline (batched restricted solve)",
                 "value": value,
@@ -663,13 +707,7 @@ def main():
     import torch
     value, ms_r = aggregate(r["A"] * r["iters"], r["ms_r"], world)
     full_value = r["A_full"] * r["iters"] / (r["ms_f"] * 1e-3) / 1e6
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peak, peak_src = hbm_peak()
     line = {
         "metric": "active Mpixel-iters/s and % HBM roofline, restricted vs full domain at equal error",
         "value": value, "unit": "active Mpixel-iter/s", "n_gpus": world, "steps": args.steps,

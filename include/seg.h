@@ -231,6 +231,44 @@ seg_status seg_solve(const float* f, int H, int W, int ld,
                      void* state, size_t state_bytes, double* stats,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* Parameters of a restricted primal-dual solve (host struct, read during the
+ * call only). */
+typedef struct seg_pd_params {
+    double lambda;      /* weight of the fitting term, Eq. CR */
+    double sigma;       /* dual step (default 1/sqrt(8)) */
+    double tau;         /* primal step (default 1/sqrt(8)); sigma tau <= 1/8 converges */
+    double tol;         /* stop when max(||du||, ||dp||) <= tol; <= 0: run `iters` */
+    int iters;          /* maximum number of iterations */
+    int check_every;    /* evaluate the stopping test every this many iterations (>= 1) */
+    int warm_start;     /* 0: start from u = H(-f), p = 0; 1: from the u, p1, p2 given */
+    int tile_h;         /* tile height used by seg_build_domain for this domain */
+} seg_pd_params;
+
+/* Restricted primal-dual solver of Eq. CR (the Conclusion proposes carrying
+ * the restriction over to other solvers of Eq. CR; this is the first-order
+ * primal-dual method of Chambolle and Pock, 2011) on the domain built by
+ * seg_build_domain, with Section 3's restriction (p = 0 and u = H(-f)
+ * outside RD):
+ *   p <- P(p + sigma grad ubar),  P the projection onto |p| <= 1    on RD
+ *   u' = clip(u + tau (div p - lambda f), 0, 1),  ubar = 2 u' - u    on RD
+ * from ubar = u, alternated prm->iters times or until max(||u' - u||,
+ * ||p' - p||) <= tol (Section 4's test with p in the place of v, checked every
+ * check_every iterations).  Unlike seg_solve it minimises Eq. CR itself (no
+ * theta coupling); grad/div are the same discrete operators.
+ *   u, p1, p2     [H][ld] float32: warm start in (prm->warm_start; the
+ *                 extrapolation restarts there, ubar = u), result out.
+ *   state         seg_state_bytes(H, ld, capacity, SEG_MODE_COMPACT,
+ *                 SEG_STORE_F32) bytes (capacity >= n_active).
+ *   stats         out double[8] (device): as seg_solve, [2] = last ||dp||.
+ * Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA on the host; CAPACITY in the
+ * status word. */
+seg_status seg_solve_pd(const float* f, int H, int W, int ld,
+                        const uint32_t* act, const uint32_t* fg, const int32_t* wstart,
+                        const int32_t* counts, const seg_pd_params* prm,
+                        float* u, float* p1, float* p2,
+                        void* state, size_t state_bytes, double* stats,
+                        void* ws, size_t ws_bytes, void* stream);
+
 /* One image of a batch for seg_solve_batch (host struct holding device
  * pointers): the fitting term and the domain of seg_build_domain for it,
  * its u, v, p1, p2 [H][ld] (warm start in, result out) and its lambda. */

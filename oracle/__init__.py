@@ -11,6 +11,7 @@ only compiles it and marshals numpy arrays in and out.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -82,6 +83,8 @@ def _load():
         lib.oracle_solve.argtypes = [P, I, I, P, D, D, D, I, I, D, I, P, P, P, P, P]
         lib.oracle_solve.restype = I
         lib.oracle_solve_grad.argtypes = [P, I, I, P, D, D, D, I, P, P, P, P]
+        lib.oracle_solve_pd.argtypes = [P, I, I, P, D, D, D, I, D, I, P, P, P, P]
+        lib.oracle_solve_pd.restype = ctypes.c_int
         lib.oracle_solve_grad.restype = None
         lib.oracle_energy.argtypes = [P, P, P, P, P, I, I, D, D, P]
         lib.oracle_energy.restype = None
@@ -284,6 +287,29 @@ def solve(f32, region, lam, theta=0.2, tau=0.125, iters=100, n_inner=1, tol=0.0,
                             int(iters), int(n_inner), float(tol), warm,
                             _ptr(u), _ptr(v), _ptr(p1), _ptr(p2), _ptr(hist))
     return State(u, v, p1, p2, done, hist[:done])
+
+
+PD_STEP = 1.0 / math.sqrt(8.0)   # sigma = tau = 1/sqrt(8): sigma tau ||grad||^2 <= 1
+
+
+def solve_pd(f32, region, lam, sigma=PD_STEP, tau=PD_STEP, iters=100, tol=0.0,
+             state: State | None = None) -> State:
+    """Restricted primal-dual (Chambolle-Pock) solve of Eq. CR on the same
+    partition; v of the returned state is u (the method has no v)."""
+    lib = _load()
+    f = _c(f32, np.float32)
+    reg = _c(region, np.uint8)
+    H, W = f.shape
+    if state is None:
+        u = np.zeros((H, W)); p1 = np.zeros((H, W)); p2 = np.zeros((H, W))
+        warm = 0
+    else:
+        u, p1, p2 = (_c(a, np.float64).copy() for a in (state.u, state.p1, state.p2))
+        warm = 1
+    hist = np.zeros((max(iters, 1), 2))
+    done = lib.oracle_solve_pd(_ptr(f), H, W, _ptr(reg), float(lam), float(sigma), float(tau),
+                               int(iters), float(tol), warm, _ptr(u), _ptr(p1), _ptr(p2), _ptr(hist))
+    return State(u, u, p1, p2, done, hist[:done])
 
 
 def solve_grad(f32, region, lam, gu, gv=None, theta=0.2, tau=0.125, iters=20):

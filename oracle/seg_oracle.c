@@ -367,6 +367,79 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
     return done;
 }
 
+/* ------------------------------------------ restricted primal-dual solver */
+
+/* The Conclusion proposes carrying the restriction over to other solvers of
+ * Eq. CR.  This is the first-order primal-dual method of Chambolle and Pock
+ * (2011) on the same partition, with the same restriction as Section 3 (the
+ * dual variable is 0 outside RD, u fixed to H(-f) there):
+ *   p <- P(p + sigma grad ubar)      on RD, P the projection onto |p| <= 1
+ *   u' = clip(u + tau (div p - lambda f), 0, 1)                      on RD
+ *   ubar = 2 u' - u
+ * from u0 = H(-f), ubar0 = u0, p0 = 0 (or the caller's u, p), sigma tau <= 1/8
+ * for convergence (||grad||^2 <= 8).  Stopping test (Section 4's, with p in
+ * the place of v): max(||u' - u||, ||p' - p||) <= tol, checked every
+ * iteration; hist gets the two norms.  Returns the iterations done. */
+int oracle_solve_pd(const float* f32, int H, int W, const uint8_t* region,
+                    double lambda, double sigma, double tau, int iters, double tol,
+                    int warm, double* u, double* p1, double* p2, double* hist)
+{
+    int64_t n = (int64_t)H * W;
+    size_t sz = sizeof(double) * (size_t)n;
+    double* ub = (double*)malloc(sz);
+    double* g1 = (double*)malloc(sz);
+    double* g2 = (double*)malloc(sz);
+    double* d = (double*)malloc(sz);
+
+    for (int64_t x = 0; x < n; ++x) {
+        if (!warm) {
+            u[x] = ((double)f32[x] < 0.0) ? 1.0 : 0.0;
+            p1[x] = 0.0;
+            p2[x] = 0.0;
+        }
+        if (region[x] != 2) {
+            u[x] = (region[x] == 1) ? 1.0 : 0.0;
+            p1[x] = 0.0;
+            p2[x] = 0.0;
+        }
+        ub[x] = u[x];
+    }
+    int done = 0;
+    for (int it = 0; it < iters; ++it) {
+        /* dual ascent step and projection */
+        oracle_grad(ub, H, W, g1, g2);
+        double sp = 0.0;
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] != 2) continue;
+            double a = p1[x] + sigma * g1[x];
+            double b = p2[x] + sigma * g2[x];
+            double nrm = sqrt(a * a + b * b);
+            double s = nrm > 1.0 ? nrm : 1.0;
+            a /= s;
+            b /= s;
+            sp += (a - p1[x]) * (a - p1[x]) + (b - p2[x]) * (b - p2[x]);
+            p1[x] = a;
+            p2[x] = b;
+        }
+        /* primal descent step, clip, extrapolation */
+        oracle_div(p1, p2, H, W, d);
+        double su = 0.0;
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] != 2) continue;
+            double un = clamp01(u[x] + tau * (d[x] - lambda * (double)f32[x]));
+            su += (un - u[x]) * (un - u[x]);
+            ub[x] = 2.0 * un - u[x];
+            u[x] = un;
+        }
+        double du = sqrt(su), dp = sqrt(sp);
+        if (hist) { hist[2 * it] = du; hist[2 * it + 1] = dp; }
+        done = it + 1;
+        if (tol > 0.0 && (du > dp ? du : dp) <= tol) break;
+    }
+    free(ub); free(g1); free(g2); free(d);
+    return done;
+}
+
 /* ------------------------------------------------------- reverse mode */
 
 /* Gradient of L = <gu, u^K> + <gv, v^K> through the unrolled iteration of

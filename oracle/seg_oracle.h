@@ -79,6 +79,14 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
                  int iters, int n_inner, double tol, int warm,
                  double* u, double* v, double* p1, double* p2, double* hist);
 
+/* Restricted primal-dual (Chambolle-Pock) solver of Eq. CR on the same
+ * partition (the Conclusion's extension to other solvers): p on RD only, u
+ * fixed to H(-f) outside RD; u, p1, p2 in/out (warm start when warm != 0);
+ * hist[2 it] = ||u' - u||, hist[2 it + 1] = ||p' - p||.  Returns iterations done. */
+int oracle_solve_pd(const float* f32, int H, int W, const uint8_t* region,
+                    double lambda, double sigma, double tau, int iters, double tol,
+                    int warm, double* u, double* p1, double* p2, double* hist);
+
 /* Reverse mode of the unrolled iteration (cold start, n_inner = 1, no stop):
  * gradient of <gu, u^K> + <gv, v^K> (gv nullable) with respect to f (gf,
  * nonzero on RD only) and lambda (*glam), the partition held fixed. */

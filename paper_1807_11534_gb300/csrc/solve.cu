@@ -2058,3 +2058,262 @@ extern "C" seg_status seg_backward(const float* f, int H, int W, int ld, const u
     SEG_TRY(reduce_partials(red, kReduceBlocks, 3, grad_out, s));
     return SEG_OK;
 }
+
+// ================================================== restricted primal-dual
+//
+// The Conclusion proposes carrying the domain restriction over to other
+// solvers of Eq. CR.  This is the primal-dual method of Chambolle and Pock
+// (2011) on the same compact RD machinery, with Section 3's restriction (p =
+// 0 outside RD, u fixed to H(-f) there):
+//   dual    p <- P(p + sigma grad ubar),  P the projection onto |p| <= 1
+//   primal  u' = clip(u + tau div p - tau lambda f, 0, 1),  ubar = 2 u' - u
+// from u0 = H(-f) (or the caller's u, p), ubar0 = u0.  Every step reads its
+// own pixel's old value from one buffer and writes the new value to the
+// other (p and u are ping-ponged; ubar is written only by the primal step
+// and read only by the dual one), two grid barriers per iteration, and the
+// Section 4 test on max(||u' - u||, ||p' - p||) every check_every iterations.
+// The neighbour table, f (premultiplied by tau lambda) and the start
+// iterate come from k_compact_gather; the state is the compact state's
+// arrays: p1[0..1], p2[0..1], u (U0), w (U1), up (ubar), f.
+
+constexpr int kPdThreads = 1024;
+
+__device__ __forceinline__ float pd_fixed(int code) { return code == kNbFg ? 1.f : 0.f; }
+
+__global__ void __launch_bounds__(kPdThreads, 1)
+k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
+           const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
+           float* P1a, float* P1b, float* P2a, float* P2b, float* U0, float* U1, float* Ub,
+           const float* __restrict__ F, double* partials, WsHeader* h) {
+    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
+    if (*(volatile int*)&h->done) return;
+    const unsigned nblocks = gridDim.x;
+    const int n = counts[1];
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    const int tid = threadIdx.x;
+    const int C = check_every;
+    unsigned gen = 0;
+    int chk = 0;
+    for (int l = 1; l <= iters; ++l) {
+        const bool check = (l % C == 0) || l == iters;
+        // iterate l - 1 lives in buffer (l - 1) & 1
+        const float* P1i = (l & 1) ? P1a : P1b;
+        const float* P2i = (l & 1) ? P2a : P2b;
+        float* P1o = (l & 1) ? P1b : P1a;
+        float* P2o = (l & 1) ? P2b : P2a;
+        const float* Ui = (l & 1) ? U0 : U1;
+        float* Uo = (l & 1) ? U1 : U0;
+        float du2 = 0.f, dp2 = 0.f;
+        for (int a = a0 + tid; a < a1; a += kPdThreads) {
+            const int nd = __ldg(nb + NB_DOWN * stride + a), nr = __ldg(nb + NB_RIGHT * stride + a);
+            const float ub = Ub[a];
+            float g1 = 0.f, g2 = 0.f;
+            if (nd != kNbOut) g1 = (nd >= 0 ? Ub[nd] : pd_fixed(nd)) - ub;
+            if (nr != kNbOut) g2 = (nr >= 0 ? Ub[nr] : pd_fixed(nr)) - ub;
+            const float p1 = P1i[a], p2 = P2i[a];
+            float q1 = fmaf(sigma, g1, p1), q2 = fmaf(sigma, g2, p2);
+            const float s2 = fmaf(q1, q1, q2 * q2);
+            if (s2 > 1.f) {
+                const float r = rsqrtf(s2);
+                q1 *= r;
+                q2 *= r;
+            }
+            P1o[a] = q1;
+            P2o[a] = q2;
+            if (check) {
+                const float d1 = q1 - p1, d2 = q2 - p2;
+                dp2 = fmaf(d1, d1, fmaf(d2, d2, dp2));
+            }
+        }
+        if (!grid_sync(h, nblocks, gen)) return;
+        for (int a = a0 + tid; a < a1; a += kPdThreads) {
+            const int nu = __ldg(nb + NB_UP * stride + a), nl = __ldg(nb + NB_LEFT * stride + a);
+            const float q1 = P1o[a], q2 = P2o[a];
+            const float q1u = nu >= 0 ? P1o[nu] : 0.f, q2l = nl >= 0 ? P2o[nl] : 0.f;
+            const float div = (q1 - q1u) + (q2 - q2l);
+            const float uo = Ui[a];
+            const float un = clamp01(fmaf(tau, div, uo) - __ldg(F + a));   // F = tau lambda f
+            Uo[a] = un;
+            Ub[a] = fmaf(2.f, un, -uo);
+            if (check) {
+                const float d = un - uo;
+                du2 = fmaf(d, d, du2);
+            }
+        }
+        double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
+        if (check) {
+            float x = du2, y = dp2;
+            block_sum2f<kPdThreads>(x, y, reinterpret_cast<float*>(s_red));
+            if (tid == 0) {
+                part[2 * blockIdx.x] = x;
+                part[2 * blockIdx.x + 1] = y;
+            }
+        }
+        if (!grid_sync(h, nblocks, gen)) return;
+        if (check) {
+            // every block sums the partials in the same order and stops at
+            // the same iteration
+            if (tid < 32) {
+                double sx, sy;
+                sum_partials_warp0(part, (int)nblocks, sx, sy);
+                if (tid == 0) {
+                    const bool stop = tol > 0.0 && fmax(sx, sy) <= tol * tol;
+                    s_red[0] = stop ? 1.0 : 0.0;
+                    if (blockIdx.x == 0) {
+                        h->du2 = sx;
+                        h->dv2 = sy;
+                        h->last_check = l;
+                        if (stop) {
+                            h->iters_done = l;
+                            h->done = 1;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            const bool stop = s_red[0] != 0.0;
+            ++chk;
+            __syncthreads();
+            if (stop) return;
+        }
+    }
+}
+
+// Dense u, p1, p2 of the final primal-dual iterate (fixed values outside RD).
+__global__ void k_pd_scatter(BatchDesc B, const int32_t* __restrict__ base,
+                             const int32_t* __restrict__ totals, int iters, CompactState S,
+                             const WsHeader* __restrict__ h) {
+    const int lane = threadIdx.x & 31;
+    const long long word = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (word >= B.total_words) return;
+    const BatchImage& I = B.img[0];
+    const int i = (int)(word / I.ntx);
+    const int wx = (int)(word - (long long)i * I.ntx);
+    const int j = wx * 32 + lane;
+    if (j >= I.W) return;
+    const int64_t wo = (int64_t)i * I.nw + wx;
+    const int64_t o = (int64_t)i * I.ld + j;
+    const uint32_t a = I.act[wo];
+    const float hh = ((I.fg[wo] >> lane) & 1u) ? 1.f : 0.f;
+    const bool ok = base[1] <= S.cap && totals[1] == base[1];
+    if (ok && ((a >> lane) & 1u)) {
+        const int l = h->done ? h->iters_done : iters;
+        const int pb = l & 1;
+        const int64_t idx = I.wstart[wo] + __popc(a & lanemask_lt(lane));
+        I.u[o] = pb ? S.w[idx] : S.u[idx];
+        I.p1[o] = static_cast<const float*>(S.p1[pb])[idx];
+        I.p2[o] = static_cast<const float*>(S.p2[pb])[idx];
+    } else {
+        I.u[o] = hh;
+        I.p1[o] = 0.f;
+        I.p2[o] = 0.f;
+    }
+}
+
+extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const uint32_t* act,
+                                   const uint32_t* fgm, const int32_t* wstart, const int32_t* counts,
+                                   const seg_pd_params* prm, float* u, float* p1, float* p2,
+                                   void* state, size_t state_bytes, double* stats, void* ws,
+                                   size_t ws_bytes, void* stream) {
+    clear_error();
+    if (!prm) return fail(SEG_ERR_INVALID_ARG, "params must be non-NULL");
+    if (!f || !act || !fgm || !wstart || !counts || !u || !p1 || !p2 || !state || !stats)
+        return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
+    if (H <= 0 || W <= 0 || ld < W || (int64_t)H * ld >= (1ll << 31))
+        return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d (H*ld < 2^31)", H, W, ld);
+    if (ld % 32) return fail(SEG_ERR_ALIGN, "ld=%d is not a multiple of 32", ld);
+    if (reinterpret_cast<uintptr_t>(state) % 16)
+        return fail(SEG_ERR_ALIGN, "state buffer not 16-byte aligned");
+    const int th = prm->tile_h;
+    if (th != 4 && th != 8 && th != 16 && th != 32)
+        return fail(SEG_ERR_INVALID_ARG, "tile_h=%d not in {4, 8, 16, 32}", th);
+    if (prm->iters < 0 || prm->check_every < 1)
+        return fail(SEG_ERR_INVALID_ARG, "iters >= 0 and check_every >= 1 required");
+    if (!(prm->sigma > 0) || !(prm->tau > 0) || !std::isfinite(prm->sigma) || !std::isfinite(prm->tau) ||
+        !std::isfinite(prm->lambda) || std::isnan(prm->tol))
+        return fail(SEG_ERR_INVALID_ARG, "sigma, tau must be finite and > 0, lambda finite");
+    WsLayout L = ws_layout(H, W, th);
+    SEG_TRY(check_ws(ws, ws_bytes, L));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader* h = ws_at<WsHeader>(ws, L.header);
+    double* partials = ws_at<double>(ws, L.partials);
+
+    // the compact state of the DF solver, float32 storage, gathered with
+    // F = tau lambda f
+    IterParams P{};
+    P.theta = 1.f;
+    P.inv_theta = 1.f;
+    P.tau = (float)prm->tau;
+    P.theta_lambda = (float)(prm->tau * prm->lambda);
+    P.H = H; P.W = W; P.ld = ld; P.nw = ld / 32; P.ntx = (W + 31) / 32; P.th = th;
+    BatchDesc B{};
+    B.n = 1;
+    B.total_words = (long long)H * P.ntx;
+    BatchImage& I = B.img[0];
+    I.f = f; I.act = act; I.fg = fgm; I.wstart = wstart; I.counts = counts;
+    I.u = u; I.v = u; I.p1 = p1; I.p2 = p2;
+    I.word_off = 0; I.H = H; I.W = W; I.ld = ld; I.nw = ld / 32; I.ntx = P.ntx;
+    I.theta_lambda = P.theta_lambda;
+    int32_t* base = ws_at<int32_t>(ws, kWsBatchOff);
+    int32_t* totals = base + kMaxBatch + 2;
+
+    CompactLayout C = compact_layout(state_bytes, SEG_STORE_F32);
+    CompactState S{};
+    char* sb = static_cast<char*>(state);
+    S.p1[0] = sb + C.off[0];
+    S.p1[1] = sb + C.off[1];
+    S.p2[0] = sb + C.off[2];
+    S.p2[1] = sb + C.off[3];
+    S.v = sb + C.off[4];
+    S.f = reinterpret_cast<float*>(sb + C.off[5]);
+    S.u = reinterpret_cast<float*>(sb + C.off[6]);
+    S.w = reinterpret_cast<float*>(sb + C.off[7]);
+    S.nb = reinterpret_cast<int32_t*>(sb + C.off[8]);
+    S.w2 = reinterpret_cast<float*>(sb + C.off[9]);
+    S.up = reinterpret_cast<float*>(sb + C.off[10]);
+    S.cap = C.cap;
+    S.stride = C.stride;
+
+    k_solve_begin<<<1, 1, 0, s>>>(h);
+    SEG_LAUNCHED("k_solve_begin");
+    k_batch_bases<<<1, 1, 0, s>>>(B, base, totals, C.cap, h);
+    SEG_LAUNCHED("k_batch_bases");
+    const unsigned gblocks = (unsigned)std::max<long long>(1, (B.total_words + 7) / 8);
+    k_compact_gather<float><<<gblocks, 256, 0, s>>>(P, B, base, prm->warm_start, S, h);
+    SEG_LAUNCHED("k_compact_gather");
+
+    const void* kern = (const void*)k_solve_pd;
+    int per_sm = 0;
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPdThreads, 0));
+    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_pd cannot be resident");
+    const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)H * W));
+    int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
+                                      std::max<int64_t>(1, (most + kPdThreads - 1) / kPdThreads));
+    grid = (int)std::min<int64_t>(grid, L.npartials / 2);
+    int iters = prm->iters, ce = prm->check_every;
+    double tol = prm->tol;
+    float sigma = (float)prm->sigma, tau = (float)prm->tau;
+    const int32_t* cnt = totals;
+    const int32_t* nbp = S.nb;
+    int64_t stride = S.stride;
+    float* P1a = static_cast<float*>(S.p1[0]);
+    float* P1b = static_cast<float*>(S.p1[1]);
+    float* P2a = static_cast<float*>(S.p2[0]);
+    float* P2b = static_cast<float*>(S.p2[1]);
+    float* U0 = S.u;
+    float* U1 = S.w;
+    float* Ub = S.up;
+    const float* F = S.f;
+    void* args[] = {&iters, &ce, &tol, &sigma, &tau, (void*)&cnt, (void*)&nbp, &stride, &P1a, &P1b,
+                    &P2a, &P2b, &U0, &U1, &Ub, (void*)&F, &partials, &h};
+    if (iters > 0) {
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kPdThreads), args, 0, s));
+        count_launch();
+    }
+    k_pd_scatter<<<gblocks, 256, 0, s>>>(B, base, totals, prm->iters, S, h);
+    SEG_LAUNCHED("k_pd_scatter");
+    k_solve_end<<<1, 1, 0, s>>>(h, totals, prm->iters, stats);
+    SEG_LAUNCHED("k_solve_end");
+    return SEG_OK;
+}

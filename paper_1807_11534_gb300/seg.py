@@ -56,6 +56,16 @@ class seg_params(ctypes.Structure):
                 ("tile_h", ctypes.c_int), ("sweep", ctypes.c_int)]
 
 
+class seg_pd_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("tau", ctypes.c_double), ("tol", ctypes.c_double),
+                ("iters", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("tile_h", ctypes.c_int)]
+
+
+PD_STEP = 1.0 / math.sqrt(8.0)   # sigma = tau = 1/sqrt(8): sigma tau ||grad||^2 <= 1
+
+
 class seg_image(ctypes.Structure):
     _fields_ = [("f", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
                 ("ld", ctypes.c_int), ("act", ctypes.c_void_p), ("fg", ctypes.c_void_p),
@@ -94,6 +104,8 @@ SIGNATURES = {
                         _P, _Z, _I, _P, _Z, _P, _P, _Z, _P], _I),
     "seg_backward": ([_P, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(seg_params), _P, _Z, _P, _Z, _I,
                       _P, _P, _P, _P, _P, _P, _P, _Z, _P, _Z, _P], _I),
+    "seg_solve_pd": ([_P, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(seg_pd_params), _P, _P, _P, _P,
+                      _Z, _P, _P, _Z, _P], _I),
     "seg_solve_batch": ([ctypes.POINTER(seg_image), _I, ctypes.POINTER(seg_params), _P, _Z, _P, _P, _Z,
                          _P], _I),
 }
@@ -190,6 +202,14 @@ def seg_build_domain(f, delta, q, tile_h, act, fg, wstart, tiles, pixels, counts
                                 tiles.numel(), _ptr(pixels),
                                 0 if pixels is None else pixels.numel(), _ptr(counts),
                                 _ptr(delta_out), _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def seg_solve_pd(f, act, fg, wstart, counts, params: seg_pd_params, u, p1, p2, state, stats, ws,
+                 stream=None):
+    lib = load()
+    _check(lib.seg_solve_pd(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(act), _ptr(fg), _ptr(wstart),
+                            _ptr(counts), ctypes.byref(params), _ptr(u), _ptr(p1), _ptr(p2), _ptr(state),
+                            _nbytes(state), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)))
 
 
 def seg_build_domain_robust(f, fbar, delta, q, radius, tile_h, act, fg, wstart, tiles, pixels,
@@ -463,6 +483,26 @@ class Solver:
                           self.mode, self.storage, self.tile_h, sweep)
         seg_solve(f, d.act, d.fg, d.wstart, d.tiles, d.counts, prm, self.u, self.v, self.p1,
                   self.p2, self.state, self.stats, self.ws, self.stream)
+        return self.stats
+
+    def solve_pd(self, lam, sigma=PD_STEP, tau=PD_STEP, iters=100, tol=0.0, check_every=10,
+                 warm_start=False, f=None):
+        """Restricted primal-dual (Chambolle-Pock) solve of Eq. CR on the
+        current domain (seg_solve_pd); writes self.u, self.p1, self.p2 (v is
+        not part of this method and is left as it was)."""
+        f = self.f if f is None else f
+        d = self.dom
+        if self.mode == "compact" and self.storage == "f32":
+            state = self.state
+        else:   # the primal-dual solver keeps a float32 compact state
+            if getattr(self, "_pd_state", None) is None:
+                self._pd_state = state_buffer(self.H, self.W, self.capacity, "compact", "f32",
+                                              self.device)
+            state = self._pd_state
+        prm = seg_pd_params(float(lam), float(sigma), float(tau), float(tol), int(iters),
+                            int(check_every), int(bool(warm_start)), int(self.tile_h))
+        seg_solve_pd(f, d.act, d.fg, d.wstart, d.counts, prm, self.u, self.p1, self.p2, state,
+                     self.stats, self.ws, self.stream)
         return self.stats
 
     def update_means(self, z, thresh=0.5):

@@ -650,3 +650,126 @@ def test_robust_restriction_trend_with_strong_noise(orc):
     assert e_rob > e_plain + 0.08
     assert e_rob > e_half
     assert e_dil > e_q1
+
+
+# ------------------------------------- restricted primal-dual solver (Conclusion)
+
+def _tv_lp_1d(f, lam, region):
+    """The 1-D restricted problem as a linear program (scipy's HiGHS): the
+    unknowns are u at the RD pixels; for every RD pixel j < W-1 a term
+    |u_{j+1} - u_j| (u fixed to H(-f) outside RD); plus lam * f_j u_j over RD."""
+    opt = pytest.importorskip("scipy.optimize")
+    W = f.shape[0]
+    rd = np.flatnonzero(region == 2)
+    col = {j: k for k, j in enumerate(rd)}
+    fixed = np.where(region == 1, 1.0, 0.0)
+    edges = [j for j in rd if j < W - 1]
+    nu, ne = len(rd), len(edges)
+    c = np.concatenate([lam * f[rd].astype(np.float64), np.ones(ne)])
+    A, b = [], []
+    for e, j in enumerate(edges):
+        for sgn in (1.0, -1.0):   # t_e >= sgn (u_{j+1} - u_j)
+            r = np.zeros(nu + ne)
+            rhs = 0.0
+            r[nu + e] = -1.0
+            r[col[j]] -= sgn
+            if (j + 1) in col:
+                r[col[j + 1]] += sgn
+            else:
+                rhs -= sgn * fixed[j + 1]
+            A.append(r)
+            b.append(rhs)
+    res = opt.linprog(c, A_ub=np.array(A) if A else None, b_ub=np.array(b) if b else None,
+                      bounds=[(0, 1)] * nu + [(0, None)] * ne, method="highs")
+    assert res.status == 0
+    return res.fun
+
+
+def _restricted_objective_1d(u, f, lam, region):
+    rd = region == 2
+    W = f.shape[0]
+    tv = sum(abs(u[j + 1] - u[j]) for j in range(W - 1) if rd[j])
+    return tv + lam * float(np.sum(f[rd].astype(np.float64) * u[rd]))
+
+
+@pytest.mark.parametrize("delta", [math.inf, 0.4, 0.15])
+def test_pd_reaches_the_linear_programming_minimum_in_1d(orc, delta):
+    """With one row, the restricted Eq. CR is a linear program; the
+    primal-dual iterate reaches its optimum (scipy HiGHS, an independent
+    solver) on the full domain and on restricted ones."""
+    rng = np.random.default_rng(11)
+    f = rng.normal(0, 0.5, (1, 70)).astype(np.float32)
+    lam = 1.3
+    reg = orc.domain(f, delta)
+    st = orc.solve_pd(f, reg, lam, iters=20000)
+    got = _restricted_objective_1d(st.u[0], f[0], lam, reg[0])
+    want = _tv_lp_1d(f[0], lam, reg[0])
+    assert got == pytest.approx(want, abs=1e-6)
+    assert np.all(st.u[reg != 2] == np.where(reg[reg != 2] == 1, 1.0, 0.0))
+
+
+def test_pd_duality_gap_closes_on_a_noisy_image(orc):
+    """Weak duality (gap >= 0 for every |p| <= 1) and the gap shrinking to ~0
+    (strong duality of Eq. CR); the primal-dual p is the negative of the dual
+    variable in the energy's convention (TV(u) = max <u, div p>)."""
+    P = synth.noisy_example(seed=0, H=40, W=48)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    reg = orc.domain(f, math.inf)
+    gaps = []
+    for it in (100, 2000, 8000):
+        st = orc.solve_pd(f, reg, 2.0, iters=it)
+        assert np.max(np.hypot(st.p1, st.p2)) <= 1 + 1e-12
+        e = orc.energy(st.u, st.u, -st.p1, -st.p2, f, 2.0)
+        gaps.append(e["ecr_u"] - e["dual"])
+        assert gaps[-1] >= -1e-9
+    assert gaps[1] < 0.05 * gaps[0]
+    assert gaps[2] < 2e-5 * abs(e["ecr_u"])
+
+
+def test_pd_is_at_least_as_low_as_the_dual_iteration_on_eq_cr(orc):
+    """Both methods work on the same restricted Eq. CR; the DF iteration
+    minimises its theta-relaxation, so its v is feasible but not optimal for
+    Eq. CR, while the primal-dual iterate converges to the minimum."""
+    P = synth.noisy_example(seed=2, H=40, W=48)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    reg = orc.domain(f, math.inf)
+    pd = orc.solve_pd(f, reg, 2.0, iters=6000)
+    df = orc.solve(f, reg, 2.0, iters=3000)
+    e_pd = orc.energy(pd.u, pd.u, pd.p1, pd.p2, f, 2.0)["ecr_u"]
+    e_df = orc.energy(df.u, df.v, df.p1, df.p2, f, 2.0)["ecr_v"]
+    assert e_pd <= e_df + 1e-4
+
+
+def test_pd_special_cases(orc):
+    """Empty RD keeps u = H(-f) and p = 0; large lambda gives u = H(-f) on RD
+    too (the fitting term dominates every TV change)."""
+    f = np.random.default_rng(5).normal(0, 0.3, (20, 24)).astype(np.float32)
+    f[f == 0] = 0.1
+    st = orc.solve_pd(f, orc.domain(f, 0.0), 1.0, iters=50)
+    np.testing.assert_array_equal(st.u, (f < 0).astype(float))
+    assert not st.p1.any() and not st.p2.any()
+    g = np.where(np.abs(f) < 0.05, np.sign(f) * 0.05, f).astype(np.float32)
+    st = orc.solve_pd(g, orc.domain(g, 0.2), 1e4, iters=50)
+    np.testing.assert_array_equal(st.u, (g < 0).astype(float))
+
+
+def test_pd_two_pixel_worked_example(orc):
+    """Two pixels in one row, f = (-0.5, 0.5), lambda = 0.1, sigma = tau =
+    s = 1/sqrt(8), worked by hand through Chambolle and Pock's Algorithm 1
+    (extrapolation ubar = 2u' - u):
+      u0 = (1, 0) = ubar0, p = 0.  Only p2 at the first pixel is free (the
+      last column's p2 never enters div).
+      it 1: p2 = -s (|.| < 1); div p = (-s, s);
+            u = (1 - s (s - 0.05), s (s - 0.05)) = (0.892678, 0.107322);
+            ubar = 2u - u0 = (0.785355, 0.214645)
+      it 2: p2 = -s + s (0.214645 - 0.785355) = -0.555330;
+            u1 = 0.892678 + s (-0.555330 + 0.05) = 0.714016
+    (without the extrapolation step it would be 0.687156)."""
+    f = np.array([[-0.5, 0.5]], np.float32)
+    reg = orc.domain(f, math.inf)
+    st = orc.solve_pd(f, reg, 0.1, iters=1)
+    assert st.u[0] == pytest.approx([0.892678, 0.107322], abs=1e-6)
+    assert st.p2[0, 0] == pytest.approx(-0.353553, abs=1e-6)
+    st = orc.solve_pd(f, reg, 0.1, iters=2)
+    assert st.p2[0, 0] == pytest.approx(-0.555330, abs=1e-6)
+    assert st.u[0, 0] == pytest.approx(0.714016, abs=1e-6)
