@@ -597,6 +597,44 @@ def row_pd(dev, flush):
             "mask_agreement_with_dual_iteration": agree}
 
 
+VOL_BYTES_PER_ACTIVE_ITER = 36   # read p1, p2, p3, v, f; write p1, p2, p3, v (float32)
+
+
+def row_volume(dev, flush):
+    """3-D volume: 256^3 spheres (N(0, 0.1) noise), Chan-Vese term, lambda=2:
+    the restricted solve at delta = 0.1 against the full volume (delta = inf),
+    200 iterations each (graph of 200 minus graph of 0, a test every 10),
+    and the agreement of their thresholded u."""
+    import torch
+    from paper_1807_11534_gb300 import seg, synth
+    stream = torch.cuda.current_stream()
+    D = H = W = 256
+    P = synth.spheres_volume(seed=0, D=D, H=H, W=W, n_spheres=40)
+    out = {"config": "256^3 spheres + N(0,0.1), CV term, lambda=2, 200 iterations, delta=0.1 vs inf"}
+    us = {}
+    u_final = {}
+    for name, delta in (("restricted", 0.1), ("full", math.inf)):
+        S = seg.VolumeSolver(D, H, W, tile_h=8, device=dev)
+        z = S.upload(P.z)
+        S.fitting(z, 0.3, 0.7)
+        S.domain(delta=delta)
+        A = int(S.dom.counts[1].item())
+        g = {n: seg.capture_graph(lambda n=n: S.solve(2.0, iters=n, check_every=10)) for n in (0, 200)}
+        ms = {n: _graph_ms(gr, stream, flush) for n, gr in g.items()}
+        S.check_status()
+        us[name] = (ms[200] - ms[0]) * 1000 / 200
+        u_final[name] = S.u[:, :W] > 0.5
+        gbs = VOL_BYTES_PER_ACTIVE_ITER * A / (us[name] * 1e-6) / 1e9
+        out[name] = {"active_voxels": A, "active_fraction": A / (D * H * W), "us_per_iter": us[name],
+                     "active_Mvoxel_iter_per_s": A / (us[name] * 1e-6) / 1e6, "achieved_gbs": gbs,
+                     "frac_of_measured_hbm": gbs / hbm_peak()[0]}
+        del S, g
+    out["restricted_vs_full_per_iter"] = us["full"] / us["restricted"]
+    out["E1_vs_full"] = float((u_final["restricted"] == u_final["full"]).float().mean().item())
+    out["bytes_per_active_iter"] = VOL_BYTES_PER_ACTIVE_ITER
+    return out
+
+
 def run_rows(args, dev):
     """The hot-path rows beside the headline: adjoint (differentiation
     workload), 16-bit storage (precision workload), batched solve, and the
@@ -604,7 +642,8 @@ def run_rows(args, dev):
     import torch
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     rows = {"a7_adjoint": row_adjoint(dev, flush), "a8_storage": row_storage(dev, flush),
-            "next_chan_vese": row_chan_vese(dev, flush), "next_primal_dual": row_pd(dev, flush)}
+            "next_chan_vese": row_chan_vese(dev, flush), "next_primal_dual": row_pd(dev, flush),
+            "next_volume": row_volume(dev, flush)}
     b = run_batch(argparse.Namespace(**{**vars(args), "iters": None}), 0, 1)
     rows["a6_batch"] = {"config": "64 images, sides U{128..1024}, q ~ U[0.02, 0.4], 500 iterations, "
                                   "one persistent launch",

@@ -231,6 +231,36 @@ seg_status seg_solve(const float* f, int H, int W, int ld,
                      void* state, size_t state_bytes, double* stats,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* 3-D volumes (the Conclusion names 3-D problems as the next target): the
+ * same iteration as seg_solve with a third component of p and the slice
+ * neighbours.  A volume is [D][H][ld] float32 (slice z, row i, column j; the
+ * rows of all slices stacked), so seg_make_fitting (without markers) and
+ * seg_build_domain / seg_build_domain_robust apply to it as a (D*H) x W
+ * image, and their act, fg, pixels and counts are the partition of the
+ * volume; the iteration runs over its RD voxel list (seg_build_domain's
+ * `pixels`, linear ids (z*H + i)*W + j in tile-major order).  grad is the
+ * forward difference along rows, columns and slices (0
+ * on the last one), div = -grad^T:
+ *   p <- (p + tau g) / (1 + tau |g|),  g = grad(div p - v/theta)   on RD
+ *   u  = v - theta div p,  v = clip(u - theta lambda f, 0, 1)       on RD
+ * with p = 0 and u = v = H(-f) outside RD, the Section 4 test as seg_solve.
+ *   prm           lambda, theta, tau, tol, iters, check_every, warm_start,
+ *                 tile_h (as for seg_build_domain) are used; n_inner must be
+ *                 1 and storage SEG_STORE_F32; mode is ignored.
+ *   u, v, p1, p2, p3  [D][H][ld] float32: warm start in, result out (p1
+ *                 along rows, p2 along columns, p3 along slices).
+ *   state         seg_state_bytes3d(D, H, ld) bytes, 256-byte aligned.
+ *   stats         out double[8] (device), as seg_solve.
+ * Errors: INVALID_ARG, ALIGN, CAPACITY (state too small), WORKSPACE (a
+ * workspace for the (D*H) x W image), CUDA; TIMEOUT in the status word. */
+size_t seg_state_bytes3d(int D, int H, int ld);
+seg_status seg_solve3d(const float* f, int D, int H, int W, int ld,
+                       const uint32_t* act, const uint32_t* fg, const int32_t* voxels,
+                       const int32_t* counts, const seg_params* prm,
+                       float* u, float* v, float* p1, float* p2, float* p3,
+                       void* state, size_t state_bytes, double* stats,
+                       void* ws, size_t ws_bytes, void* stream);
+
 /* Parameters of a restricted primal-dual solve (host struct, read during the
  * call only). */
 typedef struct seg_pd_params {

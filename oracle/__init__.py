@@ -83,6 +83,12 @@ def _load():
         lib.oracle_solve.argtypes = [P, I, I, P, D, D, D, I, I, D, I, P, P, P, P, P]
         lib.oracle_solve.restype = I
         lib.oracle_solve_grad.argtypes = [P, I, I, P, D, D, D, I, P, P, P, P]
+        lib.oracle_grad3.argtypes = [P, I, I, I, P, P, P]
+        lib.oracle_grad3.restype = None
+        lib.oracle_div3.argtypes = [P, P, P, I, I, I, P]
+        lib.oracle_div3.restype = None
+        lib.oracle_solve3.argtypes = [P, I, I, I, P, D, D, D, I, D, I, P, P, P, P, P, P]
+        lib.oracle_solve3.restype = ctypes.c_int
         lib.oracle_solve_pd.argtypes = [P, I, I, P, D, D, D, I, D, I, P, P, P, P]
         lib.oracle_solve_pd.restype = ctypes.c_int
         lib.oracle_solve_grad.restype = None
@@ -287,6 +293,52 @@ def solve(f32, region, lam, theta=0.2, tau=0.125, iters=100, n_inner=1, tol=0.0,
                             int(iters), int(n_inner), float(tol), warm,
                             _ptr(u), _ptr(v), _ptr(p1), _ptr(p2), _ptr(hist))
     return State(u, v, p1, p2, done, hist[:done])
+
+
+def grad3(w):
+    lib = _load()
+    w = _c(w, np.float64)
+    D, H, W = w.shape
+    g = [np.empty_like(w) for _ in range(3)]
+    lib.oracle_grad3(_ptr(w), D, H, W, *(_ptr(x) for x in g))
+    return tuple(g)
+
+
+def div3(p1, p2, p3):
+    lib = _load()
+    ps = [_c(x, np.float64) for x in (p1, p2, p3)]
+    D, H, W = ps[0].shape
+    d = np.empty_like(ps[0])
+    lib.oracle_div3(*(_ptr(x) for x in ps), D, H, W, _ptr(d))
+    return d
+
+
+class State3:
+    """Oracle iterate of a volume: u, v, p1, p2, p3 (FP64) and the increments."""
+
+    def __init__(self, u, v, p1, p2, p3, iters_done, hist):
+        self.u, self.v, self.p1, self.p2, self.p3 = u, v, p1, p2, p3
+        self.iters_done = iters_done
+        self.hist = hist
+
+
+def solve3(f32, region, lam, theta=0.2, tau=0.125, iters=100, tol=0.0,
+           state: State3 | None = None) -> State3:
+    """Section 3's iteration on a [D][H][W] volume (region codes per voxel)."""
+    lib = _load()
+    f = _c(f32, np.float32)
+    reg = _c(region, np.uint8)
+    D, H, W = f.shape
+    if state is None:
+        arrs = [np.zeros((D, H, W)) for _ in range(5)]
+        warm = 0
+    else:
+        arrs = [_c(a, np.float64).copy() for a in (state.u, state.v, state.p1, state.p2, state.p3)]
+        warm = 1
+    hist = np.zeros((max(iters, 1), 2))
+    done = lib.oracle_solve3(_ptr(f), D, H, W, _ptr(reg), float(lam), float(theta), float(tau),
+                             int(iters), float(tol), warm, *(_ptr(a) for a in arrs), _ptr(hist))
+    return State3(*arrs, done, hist[:done])
 
 
 PD_STEP = 1.0 / math.sqrt(8.0)   # sigma = tau = 1/sqrt(8): sigma tau ||grad||^2 <= 1

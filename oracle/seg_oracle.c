@@ -367,6 +367,107 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
     return done;
 }
 
+/* ------------------------------------------------------- 3-D volumes */
+
+/* The Conclusion names 3-D problems as the next target; the method is the
+ * same with a third axis.  Volumes are [D][H][W] (slice z, row i, column j),
+ * grad has the components (i, j, z) as forward differences set to 0 on the
+ * last row / column / slice, and div = -grad^T (Chambolle's operators with
+ * one more axis). */
+#define IDX3(z, i, j) (((int64_t)(z) * H + (int64_t)(i)) * (int64_t)W + (int64_t)(j))
+
+void oracle_grad3(const double* w, int D, int H, int W, double* g1, double* g2, double* g3)
+{
+    for (int z = 0; z < D; ++z)
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                double c = w[IDX3(z, i, j)];
+                g1[IDX3(z, i, j)] = (i < H - 1) ? w[IDX3(z, i + 1, j)] - c : 0.0;
+                g2[IDX3(z, i, j)] = (j < W - 1) ? w[IDX3(z, i, j + 1)] - c : 0.0;
+                g3[IDX3(z, i, j)] = (z < D - 1) ? w[IDX3(z + 1, i, j)] - c : 0.0;
+            }
+}
+
+void oracle_div3(const double* p1, const double* p2, const double* p3, int D, int H, int W,
+                 double* d)
+{
+    for (int z = 0; z < D; ++z)
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                double a = (i < H - 1 ? p1[IDX3(z, i, j)] : 0.0) - (i > 0 ? p1[IDX3(z, i - 1, j)] : 0.0);
+                double b = (j < W - 1 ? p2[IDX3(z, i, j)] : 0.0) - (j > 0 ? p2[IDX3(z, i, j - 1)] : 0.0);
+                double c = (z < D - 1 ? p3[IDX3(z, i, j)] : 0.0) - (z > 0 ? p3[IDX3(z - 1, i, j)] : 0.0);
+                d[IDX3(z, i, j)] = a + b + c;
+            }
+}
+
+/* Section 3's iteration on a volume: the same steps as oracle_solve with
+ * three components of rho; region codes per voxel as oracle_domain gives
+ * them for the flattened volume. */
+int oracle_solve3(const float* f32, int D, int H, int W, const uint8_t* region,
+                  double lambda, double theta, double tau, int iters, double tol, int warm,
+                  double* u, double* v, double* p1, double* p2, double* p3, double* hist)
+{
+    int64_t n = (int64_t)D * H * W;
+    size_t sz = sizeof(double) * (size_t)n;
+    double* d = (double*)malloc(sz);
+    double* w = (double*)malloc(sz);
+    double* g1 = (double*)malloc(sz);
+    double* g2 = (double*)malloc(sz);
+    double* g3 = (double*)malloc(sz);
+
+    for (int64_t x = 0; x < n; ++x) {
+        double f = (double)f32[x];
+        if (!warm) {
+            double h = (f < 0.0) ? 1.0 : 0.0;
+            u[x] = h;
+            p1[x] = 0.0;
+            p2[x] = 0.0;
+            p3[x] = 0.0;
+            v[x] = (region[x] == 2) ? clamp01(h - theta * lambda * f) : h;
+        }
+        if (region[x] != 2) {
+            double h = (region[x] == 1) ? 1.0 : 0.0;
+            u[x] = h;
+            v[x] = h;
+            p1[x] = 0.0;
+            p2[x] = 0.0;
+            p3[x] = 0.0;
+        }
+    }
+    int done = 0;
+    for (int it = 0; it < iters; ++it) {
+        oracle_div3(p1, p2, p3, D, H, W, d);
+        for (int64_t x = 0; x < n; ++x) w[x] = d[x] - v[x] / theta;
+        oracle_grad3(w, D, H, W, g1, g2, g3);
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] != 2) continue;
+            double nrm = sqrt(g1[x] * g1[x] + g2[x] * g2[x] + g3[x] * g3[x]);
+            double den = 1.0 + tau * nrm;
+            p1[x] = (p1[x] + tau * g1[x]) / den;
+            p2[x] = (p2[x] + tau * g2[x]) / den;
+            p3[x] = (p3[x] + tau * g3[x]) / den;
+        }
+        oracle_div3(p1, p2, p3, D, H, W, d);
+        double su = 0.0, sv = 0.0;
+        for (int64_t x = 0; x < n; ++x) {
+            if (region[x] != 2) continue;
+            double un = v[x] - theta * d[x];
+            double vn = clamp01(un - theta * lambda * (double)f32[x]);
+            su += (un - u[x]) * (un - u[x]);
+            sv += (vn - v[x]) * (vn - v[x]);
+            u[x] = un;
+            v[x] = vn;
+        }
+        double du = sqrt(su), dv = sqrt(sv);
+        if (hist) { hist[2 * it] = du; hist[2 * it + 1] = dv; }
+        done = it + 1;
+        if (tol > 0.0 && (du > dv ? du : dv) <= tol) break;
+    }
+    free(d); free(w); free(g1); free(g2); free(g3);
+    return done;
+}
+
 /* ------------------------------------------ restricted primal-dual solver */
 
 /* The Conclusion proposes carrying the restriction over to other solvers of

@@ -79,6 +79,16 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
                  int iters, int n_inner, double tol, int warm,
                  double* u, double* v, double* p1, double* p2, double* hist);
 
+/* 3-D volumes [D][H][W]: forward-difference gradient (components along
+ * rows, columns, slices; 0 on the last one), div = -grad^T, and Section 3's
+ * iteration with three components of rho (region codes per voxel). */
+void oracle_grad3(const double* w, int D, int H, int W, double* g1, double* g2, double* g3);
+void oracle_div3(const double* p1, const double* p2, const double* p3, int D, int H, int W,
+                 double* d);
+int oracle_solve3(const float* f32, int D, int H, int W, const uint8_t* region,
+                  double lambda, double theta, double tau, int iters, double tol, int warm,
+                  double* u, double* v, double* p1, double* p2, double* p3, double* hist);
+
 /* Restricted primal-dual (Chambolle-Pock) solver of Eq. CR on the same
  * partition (the Conclusion's extension to other solvers): p on RD only, u
  * fixed to H(-f) outside RD; u, p1, p2 in/out (warm start when warm != 0);

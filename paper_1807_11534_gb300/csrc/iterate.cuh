@@ -143,6 +143,14 @@ __device__ __forceinline__ void sum_partials_warp0(const double* part, int n, do
     }
 }
 
+// ------------------------------------------------ host helpers of solve.cu
+
+// Reset of the solve's header words before a persistent solve, and the
+// stats of the finished solve (see seg_solve): launched on stream s.
+seg_status launch_solve_begin(WsHeader* h, cudaStream_t s);
+seg_status launch_solve_end(const WsHeader* h, const int32_t* counts, int iters, double* stats,
+                            cudaStream_t s);
+
 // ------------------------------------------------ host entry of tiled.cu
 
 // Temporally blocked solve on the dense ping-pong state `st` (initialised by

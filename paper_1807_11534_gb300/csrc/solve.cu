@@ -1358,6 +1358,19 @@ __global__ void k_solve_end(const WsHeader* __restrict__ h, const int32_t* __res
 
 // ================================================================== host
 
+seg_status launch_solve_begin(WsHeader* h, cudaStream_t s) {
+    k_solve_begin<<<1, 1, 0, s>>>(h);
+    SEG_LAUNCHED("k_solve_begin");
+    return SEG_OK;
+}
+
+seg_status launch_solve_end(const WsHeader* h, const int32_t* counts, int iters, double* stats,
+                            cudaStream_t s) {
+    k_solve_end<<<1, 1, 0, s>>>(h, counts, iters, stats);
+    SEG_LAUNCHED("k_solve_end");
+    return SEG_OK;
+}
+
 
 template <typename K>
 static int grid_for(K kernel, int threads, int64_t max_blocks) {

@@ -106,6 +106,9 @@ SIGNATURES = {
                       _P, _P, _P, _P, _P, _P, _P, _Z, _P, _Z, _P], _I),
     "seg_solve_pd": ([_P, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(seg_pd_params), _P, _P, _P, _P,
                       _Z, _P, _P, _Z, _P], _I),
+    "seg_state_bytes3d": ([_I, _I, _I], _Z),
+    "seg_solve3d": ([_P, _I, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(seg_params), _P, _P, _P, _P, _P,
+                     _P, _Z, _P, _P, _Z, _P], _I),
     "seg_solve_batch": ([ctypes.POINTER(seg_image), _I, ctypes.POINTER(seg_params), _P, _Z, _P, _P, _Z,
                          _P], _I),
 }
@@ -210,6 +213,21 @@ def seg_solve_pd(f, act, fg, wstart, counts, params: seg_pd_params, u, p1, p2, s
     _check(lib.seg_solve_pd(_ptr(f), f.shape[0], _W(f), f.stride(0), _ptr(act), _ptr(fg), _ptr(wstart),
                             _ptr(counts), ctypes.byref(params), _ptr(u), _ptr(p1), _ptr(p2), _ptr(state),
                             _nbytes(state), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def seg_state_bytes3d(D, H, ld):
+    return load().seg_state_bytes3d(int(D), int(H), int(ld))
+
+
+def seg_solve3d(f, D, H, act, fg, voxels, counts, params: seg_params, u, v, p1, p2, p3, state, stats,
+                ws, stream=None):
+    """f, u, v, p1, p2, p3: [D*H][ld] stacked volume images; voxels: the RD
+    voxel list of seg_build_domain on the stacked image."""
+    lib = load()
+    _check(lib.seg_solve3d(_ptr(f), int(D), int(H), _W(f), f.stride(0), _ptr(act), _ptr(fg), _ptr(voxels),
+                           _ptr(counts), ctypes.byref(params), _ptr(u), _ptr(v), _ptr(p1), _ptr(p2),
+                           _ptr(p3), _ptr(state), _nbytes(state), _ptr(stats), _ptr(ws), _nbytes(ws),
+                           _stream(stream)))
 
 
 def seg_build_domain_robust(f, fbar, delta, q, radius, tile_h, act, fg, wstart, tiles, pixels,
@@ -537,6 +555,64 @@ class Solver:
     def errors(self, u_star, u_gt, eps=0.5):
         seg_errors(u_star, u_gt, eps, self.err_out, self.ws, self.stream)
         return self.err_out
+
+    def check_status(self):
+        seg_read_status(self.ws, self.stream)
+
+
+class VolumeSolver:
+    """Buffers for one D x H x W volume, stored as its slices stacked into a
+    (D*H) x W image ([D][H][ld] float32), and the chain fitting -> domain ->
+    solve through the C ABI (seg_make_fitting and seg_build_domain on the
+    stacked image, seg_solve3d for the iteration)."""
+
+    def __init__(self, D, H, W, tile_h=16, device="cuda", stream=None):
+        self.D, self.H, self.W, self.tile_h = D, H, W, tile_h
+        self.device = torch.device(device)
+        self.stream = stream
+        R = D * H
+        self.ws = workspace(R, W, tile_h, self.device)
+        self.f = image(R, W, device=self.device)
+        self.u = image(R, W, device=self.device)
+        self.v = image(R, W, device=self.device)
+        self.p1 = image(R, W, device=self.device)
+        self.p2 = image(R, W, device=self.device)
+        self.p3 = image(R, W, device=self.device)
+        nb = seg_state_bytes3d(D, H, pitch(W))
+        self.state = torch.empty((nb + 255) // 256 * 256, dtype=torch.uint8, device=self.device)
+        self.stats = torch.zeros(8, dtype=torch.float64, device=self.device)
+        self.c = torch.zeros(2, dtype=torch.float64, device=self.device)
+        self.dom = None
+
+    def upload(self, a):
+        """Host volume [D, H, W] -> stacked device image."""
+        a = torch.as_tensor(a, dtype=torch.float32).reshape(self.D * self.H, self.W)
+        return upload(a, self.device)
+
+    def download(self, t):
+        """Stacked device image -> host volume [D, H, W]."""
+        return download(t).reshape(self.D, self.H, self.W)
+
+    def fitting(self, z, c1=0.3, c2=0.7, label=None):
+        seg_make_fitting(z, c1, c2, label, None, 0.0, self.f, self.c, self.ws, self.stream)
+        return self.f
+
+    def domain(self, delta=math.inf, q=-1.0):
+        if self.dom is None:
+            self.dom = build_domain(self.f, delta, q, self.tile_h, self.ws, True, self.stream)
+        else:
+            d = self.dom
+            seg_build_domain(self.f, delta, q, self.tile_h, d.act, d.fg, d.wstart, d.tiles, d.pixels,
+                             d.counts, d.delta, self.ws, self.stream)
+        return self.dom
+
+    def solve(self, lam, theta=0.2, tau=0.125, iters=100, tol=0.0, check_every=10, warm_start=False):
+        d = self.dom
+        prm = make_params(lam, theta, tau, iters, tol, 1, check_every, warm_start, "compact", "f32",
+                          self.tile_h)
+        seg_solve3d(self.f, self.D, self.H, d.act, d.fg, d.pixels, d.counts, prm, self.u, self.v,
+                    self.p1, self.p2, self.p3, self.state, self.stats, self.ws, self.stream)
+        return self.stats
 
     def check_status(self):
         seg_read_status(self.ws, self.stream)

@@ -134,6 +134,23 @@ def noisy_example(seed=0, H=96, W=96, sigma=0.25, iters=600) -> Problem:
                    name=f"noisy{H}x{W}_s{seed}")
 
 
+def spheres_volume(seed=0, D=64, H=64, W=64, n_spheres=12, sigma=0.1, lam=2.0, iters=200):
+    """Volume [D, H, W]: `n_spheres` balls of radius U[4, 24] (scaled with the
+    smallest side) at 0.3 on a 0.7 background, + N(0, sigma); label = the
+    balls; c1 = 0.3, c2 = 0.7."""
+    rng = np.random.default_rng(seed)
+    scale = min(D, H, W) / 64.0
+    zz, yy, xx = np.mgrid[:D, :H, :W]
+    lab = np.zeros((D, H, W), bool)
+    for _ in range(n_spheres):
+        r = rng.uniform(4, 24) * max(scale, 0.1)
+        cz, cy, cx = rng.uniform(0, D), rng.uniform(0, H), rng.uniform(0, W)
+        lab |= (zz - cz) ** 2 + (yy - cy) ** 2 + (xx - cx) ** 2 < r * r
+    z = np.where(lab, 0.3, 0.7) + rng.normal(0.0, sigma, size=(D, H, W))
+    return Problem(z=z.astype(np.float32), label=lab.astype(np.uint8), c1=0.3, c2=0.7, lam=lam,
+                   iters=iters, delta=float("inf"), name=f"spheres{D}x{H}x{W}_s{seed}")
+
+
 def ellipses_ds(seed=0, H=2048, W=2048, n_ell=40, n_markers=20, lam=2.0, gamma=0.5,
                 iters=1000, delta=float("inf")) -> Problem:
     """2048x2048 image: `n_ell` ellipses with semi-axes U[10, 120] (scaled with

@@ -1,0 +1,137 @@
+"""3-D volumes (seg_solve3d on the partition of the stacked volume) against
+the FP64 oracle's 3-D iteration: ragged volumes, restricted and full
+domains, early stop, warm start, a 160^3 volume through oracle crops, and
+the argument and capacity errors."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1807_11534_gb300 import synth
+from tests.gpu_helpers import require_gpu, seg_mod
+
+pytestmark = pytest.mark.gpu
+
+TOL_U, TOL_P = 1e-4, 2e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    seg_mod()
+
+
+def _run(f, lam, iters, delta=math.inf, q=-1.0, tile_h=8, tol=0.0, check_every=10, warm=None):
+    seg = seg_mod()
+    D, H, W = f.shape
+    S = seg.VolumeSolver(D, H, W, tile_h=tile_h)
+    S.f.copy_(S.upload(f))
+    S.domain(delta=delta, q=q)
+    if warm is not None:
+        for name in ("u", "v", "p1", "p2", "p3"):
+            getattr(S, name).copy_(S.upload(getattr(warm, name)))
+    S.solve(lam, iters=iters, tol=tol, check_every=check_every, warm_start=warm is not None)
+    torch.cuda.synchronize()
+    S.check_status()
+    out = {k: S.download(getattr(S, k)).astype(np.float64) for k in ("u", "v", "p1", "p2", "p3")}
+    out["stats"] = S.stats.cpu().numpy()
+    out["delta"] = float(S.dom.delta.cpu().numpy()[0])
+    out["counts"] = S.dom.counts.cpu().numpy()
+    return out
+
+
+def _cmp(out, st):
+    du = max(np.max(np.abs(out["u"] - st.u)), np.max(np.abs(out["v"] - st.v)))
+    dp = max(np.max(np.abs(out[k] - getattr(st, k))) for k in ("p1", "p2", "p3"))
+    assert du <= TOL_U and dp <= TOL_P, (du, dp)
+
+
+def _volume(shape, seed):
+    return synth.spheres_volume(seed=seed, D=shape[0], H=shape[1], W=shape[2], sigma=0.08).z
+
+
+@pytest.mark.parametrize("shape,tile_h", [((5, 17, 40), 8), ((1, 30, 33), 4), ((9, 8, 65), 16),
+                                          ((16, 16, 16), 4), ((3, 1, 50), 32), ((2, 40, 1), 8),
+                                          ((20, 23, 29), 16)])
+@pytest.mark.parametrize("dq", [dict(delta=math.inf), dict(delta=0.15), dict(q=0.3)])
+def test_volume_matches_oracle(orc, shape, tile_h, dq):
+    z = _volume(shape, sum(shape) + tile_h)
+    _, f = orc.fitting(z.reshape(-1, shape[2]), 0.3, 0.7)
+    f = f.reshape(shape)
+    out = _run(f, 1.0, 60, tile_h=tile_h, **dq)
+    reg = orc.domain(f, out["delta"])
+    assert out["counts"][1] == int(np.sum(reg == 2))
+    st = orc.solve3(f, reg, 1.0, iters=60)
+    _cmp(out, st)
+    assert out["stats"][0] == 60
+
+
+def test_volume_early_stop_and_warm_start(orc):
+    shape = (12, 30, 37)
+    z = _volume(shape, 4)
+    _, f = orc.fitting(z.reshape(-1, shape[2]), 0.3, 0.7)
+    f = f.reshape(shape)
+    reg = orc.domain(f, 0.12)
+    full = orc.solve3(f, reg, 1.0, iters=300)
+    # the Section 4 test every 5 iterations, tol put between a check past
+    # iteration 50 that sets a new low by more than 5 % and the lowest before
+    checks = np.max(full.hist, axis=1)[4::5]
+    k = next(k for k in range(10, len(checks)) if checks[:k].min() > 1.05 * checks[k])
+    tol = math.sqrt(checks[:k].min() * checks[k])
+    stop = 5 * (k + 1)
+    out = _run(f, 1.0, 300, delta=0.12, tol=tol, check_every=5)
+    assert int(out["stats"][0]) == stop
+    _cmp(out, orc.solve3(f, reg, 1.0, iters=stop))
+    # warm start: 30 + 30 iterations = 60 from cold (the iterate is the state)
+    a = orc.solve3(f, reg, 1.0, iters=30)
+    out = _run(f, 1.0, 30, delta=0.12, warm=a)
+    _cmp(out, orc.solve3(f, reg, 1.0, iters=60))
+
+
+def test_volume_160_sampled(orc):
+    """160^3 spheres volume (4.1 M voxels) at delta = 0.2: K iterations on the
+    GPU, the oracle on crops of radius 2K+4 around sampled voxels."""
+    D = H = W = 160
+    P = synth.spheres_volume(seed=1, D=D, H=H, W=W)
+    _, f = orc.fitting(P.z.reshape(-1, W), 0.3, 0.7)
+    f = f.reshape(D, H, W)
+    K, lam, delta = 10, 2.0, 0.2
+    out = _run(f, lam, K, delta=delta, tile_h=16)
+    reg = orc.domain(f, delta)
+    rng = np.random.default_rng(2)
+    act = np.argwhere(reg == 2)
+    centres = [tuple(x) for x in act[rng.choice(len(act), 16, replace=False)]] + [(0, 0, 0), (159, 159, 159)]
+    R = 2 * K + 4
+    worst = 0.0
+    for (z0, i0, j0) in centres:
+        sl = tuple(slice(max(0, c - R), min(n, c + R + 1)) for c, n in zip((z0, i0, j0), (D, H, W)))
+        fc = np.ascontiguousarray(f[sl])
+        st = orc.solve3(fc, orc.domain(fc, delta), lam, iters=K)
+        worst = max(worst, abs(st.u[z0 - sl[0].start, i0 - sl[1].start, j0 - sl[2].start] - out["u"][z0, i0, j0]))
+    assert worst <= TOL_U
+    assert np.all(np.sqrt(out["p1"] ** 2 + out["p2"] ** 2 + out["p3"] ** 2) <= 1 + 1e-6)
+    fixed = reg != 2
+    np.testing.assert_array_equal(out["u"][fixed], (reg[fixed] == 1).astype(np.float64))
+
+
+def test_volume_argument_and_capacity_errors():
+    seg = seg_mod()
+    S = seg.VolumeSolver(4, 10, 20)
+    S.f.copy_(S.upload(np.random.default_rng(0).normal(0, 0.3, (4, 10, 20))))
+    S.domain(delta=0.2)
+    d = S.dom
+    for kw in (dict(n_inner=2), dict(storage="bf16"), dict(check_every=0)):
+        base = dict(lam=1.0, theta=0.2, tau=0.125, iters=10, tol=0.0, n_inner=1, check_every=10,
+                    warm_start=False, mode="compact", storage="f32", tile_h=16)
+        base.update(kw)
+        prm = seg.make_params(*base.values())
+        with pytest.raises(seg.SegError) as e:
+            seg.seg_solve3d(S.f, 4, 10, d.act, d.fg, d.pixels, d.counts, prm, S.u, S.v, S.p1, S.p2, S.p3,
+                            S.state, S.stats, S.ws)
+        assert e.value.status == seg.SEG_ERR_INVALID_ARG
+    prm = seg.make_params(1.0)
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_solve3d(S.f, 4, 10, d.act, d.fg, d.pixels, d.counts, prm, S.u, S.v, S.p1, S.p2, S.p3,
+                        S.state[:1024], S.stats, S.ws)
+    assert e.value.status == seg.SEG_ERR_CAPACITY

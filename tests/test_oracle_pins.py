@@ -773,3 +773,76 @@ def test_pd_two_pixel_worked_example(orc):
     st = orc.solve_pd(f, reg, 0.1, iters=2)
     assert st.p2[0, 0] == pytest.approx(-0.555330, abs=1e-6)
     assert st.u[0, 0] == pytest.approx(0.714016, abs=1e-6)
+
+
+# ------------------------------------------------------------- 3-D volumes
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 7), (4, 1, 6), (3, 5, 1), (4, 6, 9)])
+def test_div3_is_minus_adjoint_of_grad3(orc, shape):
+    rng = np.random.default_rng(sum(shape))
+    w = rng.normal(size=shape)
+    p = [rng.normal(size=shape) for _ in range(3)]
+    g = orc.grad3(w)
+    lhs = float(sum(np.sum(a * b) for a, b in zip(g, p)))
+    rhs = -float(np.sum(w * orc.div3(*p)))
+    assert abs(lhs - rhs) <= 1e-12 * (1 + abs(lhs))
+
+
+def test_grad3_textbook_values(orc):
+    """A ramp along the slices has gradient (0, 0, 1) except on the last
+    slice; a unit field p3 has divergence +1 on the first slice, 0 inside,
+    -1 on the last."""
+    D, H, W = 5, 3, 4
+    ramp = np.broadcast_to(np.arange(D, dtype=float)[:, None, None], (D, H, W)).copy()
+    g1, g2, g3 = orc.grad3(ramp)
+    assert not g1.any() and not g2.any()
+    assert np.all(g3[:-1] == 1.0) and np.all(g3[-1] == 0.0)
+    d = orc.div3(np.zeros((D, H, W)), np.zeros((D, H, W)), np.ones((D, H, W)))
+    assert np.all(d[0] == 1.0) and np.all(d[1:-1] == 0.0) and np.all(d[-1] == -1.0)
+
+
+def test_volume_of_one_slice_is_the_image_solve(orc):
+    P = synth.small_example(seed=4, H=30, W=41)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    reg = orc.domain(f, 0.2)
+    a = orc.solve3(f[None], reg[None], 1.0, iters=80)
+    b = orc.solve(f, reg, 1.0, iters=80)
+    for k in ("u", "v", "p1", "p2"):
+        np.testing.assert_array_equal(getattr(a, k)[0], getattr(b, k))
+    assert not a.p3.any()
+
+
+def test_volume_constant_along_slices_solves_every_slice_as_the_image(orc):
+    """f repeated over the slices: the slice differences vanish, so every
+    slice follows the image iteration (p3 stays 0)."""
+    P = synth.small_example(seed=6, H=24, W=37)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    f3 = np.repeat(f[None], 5, axis=0)
+    a = orc.solve3(f3, orc.domain(f3, 0.25), 1.0, iters=60)
+    b = orc.solve(f, orc.domain(f, 0.25), 1.0, iters=60)
+    assert not a.p3.any()
+    for z in range(5):
+        np.testing.assert_allclose(a.u[z], b.u, atol=1e-13)
+        np.testing.assert_allclose(a.p1[z], b.p1, atol=1e-13)
+
+
+@pytest.mark.parametrize("perm", [(1, 0, 2), (2, 1, 0), (0, 2, 1)])
+def test_volume_solve_commutes_with_axis_permutations(orc, perm):
+    """The iteration treats the three axes alike (isotropic TV, the same
+    boundary rule on each), so permuting the axes of f permutes u, v and the
+    components of p."""
+    rng = np.random.default_rng(8)
+    f = rng.normal(0, 0.3, (6, 9, 11)).astype(np.float32)
+    reg = orc.domain(f, 0.25)
+    a = orc.solve3(f, reg, 1.5, iters=40)
+    fp = np.ascontiguousarray(f.transpose(perm))
+    b = orc.solve3(fp, np.ascontiguousarray(reg.transpose(perm)), 1.5, iters=40)
+    np.testing.assert_allclose(b.u, a.u.transpose(perm), atol=1e-12)
+    np.testing.assert_allclose(b.v, a.v.transpose(perm), atol=1e-12)
+    # component k of p belongs to axis (1, 2, 0)[k] of the array (rows, columns, slices)
+    comp_axis = {0: 2, 1: 0, 2: 1}   # array axis -> component index
+    pa = (a.p1, a.p2, a.p3)
+    pb = (b.p1, b.p2, b.p3)
+    for new_axis, old_axis in enumerate(perm):
+        np.testing.assert_allclose(pb[comp_axis[new_axis]], pa[comp_axis[old_axis]].transpose(perm),
+                                   atol=1e-12)
