@@ -11,8 +11,10 @@
 //   gap     = E_CR(v) - D(p) >= 0 for v in [0, 1], |p| <= 1
 //   E1, E2  : Section 4 (Tanimoto of the eps-thresholded masks; sum of
 //             squared differences)
-// Each block accumulates its pixels in FP64 in a fixed order; a fixed grid and
-// a fixed-order final reduction make the sums deterministic.
+// The energy terms are accumulated per thread in double-float arithmetic
+// (below) and combined across threads and blocks in FP64; the error terms
+// in FP64.  A fixed grid and fixed-order reductions make the sums
+// deterministic.
 #include "seg_internal.cuh"
 
 namespace seg {
@@ -37,33 +39,101 @@ __device__ __forceinline__ void block_store_terms(double (&acc)[NTERMS], double*
     }
 }
 
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi) / 2 (Dekker 1971).  The error-free sum is
+// Knuth's TwoSum, the error-free product uses the FMA, and the square root
+// takes one correction step of the float root (Karp and Markstein).  About 48
+// significant bits, all on the float pipes: the per-pixel energy terms cost a
+// handful of float operations instead of FP64 ones, which this part runs at a
+// small fraction of the float rate.
+struct DF {
+    float hi, lo;
+};
+
+// (explicitly rounded operations: the compiler must not fuse a product into
+// a following sum here, which would break the error-free steps)
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {   // |a| >= |b| or a = 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = df_two_sum(a.hi, b.hi);
+    const DF t = df_two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_sqrt(DF a) {
+    if (!(a.hi > 0.f)) return {0.f, 0.f};
+    const float r = __fsqrt_rn(a.hi);
+    const float rr = __fmul_rn(r, r);
+    // a - r^2 with r^2 split exactly by the FMA
+    const float e = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, rr), __fmaf_rn(r, r, -rr)), a.lo);
+    return df_fast_two_sum(r, __fdiv_rn(e, __fmul_rn(2.f, r)));
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+// |(a, b)| for a, b exact double-float differences
+__device__ __forceinline__ DF df_hypot(DF a, DF b) { return df_sqrt(df_add(df_mul(a, a), df_mul(b, b))); }
+
 // terms: 0 TV(u), 1 TV(v), 2 sum f u, 3 sum f v, 4 sum (u-v)^2, 5 sum min(0, lambda f + div p)
+// Differences of two floats and products of two floats are exact in
+// double-float; the rest carries ~2^-48 relative error per operation, and
+// each thread's sums are double-float too, so no FP64 work happens per pixel.
 __global__ void k_energy_terms(const float* __restrict__ f, int H, int W, int ld,
                                const float* __restrict__ u, const float* __restrict__ v,
                                const float* __restrict__ p1, const float* __restrict__ p2,
                                double lambda, double* __restrict__ red) {
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    int64_t n = (int64_t)H * W;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = x / W, j = x - i * W;
-        int64_t o = i * ld + j;
-        double uu = u[o], vv = v[o], ff = f[o];
-        double au = i < H - 1 ? (double)u[o + ld] - uu : 0.0;
-        double bu = j < W - 1 ? (double)u[o + 1] - uu : 0.0;
-        double av = i < H - 1 ? (double)v[o + ld] - vv : 0.0;
-        double bv = j < W - 1 ? (double)v[o + 1] - vv : 0.0;
-        acc[0] += sqrt(au * au + bu * bu);
-        acc[1] += sqrt(av * av + bv * bv);
-        acc[2] += ff * uu;
-        acc[3] += ff * vv;
-        acc[4] += (uu - vv) * (uu - vv);
-        double d = (i < H - 1 ? (double)p1[o] : 0.0) - (i > 0 ? (double)p1[o - ld] : 0.0) +
-                   (j < W - 1 ? (double)p2[o] : 0.0) - (j > 0 ? (double)p2[o - 1] : 0.0);
-        double c = lambda * ff + d;
-        acc[5] += c < 0.0 ? c : 0.0;
+    const DF zero{0.f, 0.f};
+    DF acc[6] = {zero, zero, zero, zero, zero, zero};
+    const float lam_hi = (float)lambda;
+    const DF lam{lam_hi, (float)(lambda - (double)lam_hi)};
+    const unsigned n = (unsigned)H * (unsigned)W;   // < 2^31 (checked by the callers)
+    for (unsigned x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const unsigned i = x / (unsigned)W, j = x - i * (unsigned)W;
+        const int64_t o = (int64_t)i * ld + j;
+        const float uu = u[o], vv = v[o], ff = f[o];
+        const bool dn = i + 1 < (unsigned)H, rt = j + 1 < (unsigned)W;
+        const DF au = dn ? df_two_sum(u[o + ld], -uu) : zero;
+        const DF bu = rt ? df_two_sum(u[o + 1], -uu) : zero;
+        const DF av = dn ? df_two_sum(v[o + ld], -vv) : zero;
+        const DF bv = rt ? df_two_sum(v[o + 1], -vv) : zero;
+        acc[0] = df_add(acc[0], df_hypot(au, bu));
+        acc[1] = df_add(acc[1], df_hypot(av, bv));
+        acc[2] = df_add(acc[2], df_mul({ff, 0.f}, {uu, 0.f}));
+        acc[3] = df_add(acc[3], df_mul({ff, 0.f}, {vv, 0.f}));
+        const DF d = df_two_sum(uu, -vv);
+        acc[4] = df_add(acc[4], df_mul(d, d));
+        // div p (Chambolle): the components that never enter it are skipped
+        DF dp = zero;
+        if (dn) dp = df_add(dp, {p1[o], 0.f});
+        if (i > 0) dp = df_add(dp, {-p1[o - ld], 0.f});
+        if (rt) dp = df_add(dp, {p2[o], 0.f});
+        if (j > 0) dp = df_add(dp, {-p2[o - 1], 0.f});
+        const DF c = df_add(df_mul(lam, {ff, 0.f}), dp);
+        if (c.hi < 0.f || (c.hi == 0.f && c.lo < 0.f)) acc[5] = df_add(acc[5], c);
     }
-    block_store_terms<6>(acc, red);
+    double out[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) out[t] = df_to_double(acc[t]);
+    block_store_terms<6>(out, red);
 }
 
 __global__ void k_energy_final(const double* __restrict__ sums, double lambda, double theta,
