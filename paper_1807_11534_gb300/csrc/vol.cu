@@ -37,7 +37,18 @@ struct VolState {
     float* p[2][3];     // buffer b, component k (along rows, columns, slices)
     float* w;           // div p - v/theta of the current iterate (RD voxels)
     float* up;          // u of the iteration before a stopping test
+    int32_t* off;       // per RD voxel (list order): its offset (z*H + i)*ld + j
+    uint16_t* flg;      // per RD voxel: kVf* bits below
 };
+
+// Per-voxel flags, computed once per solve: which backward / forward
+// neighbours exist, and the state of the three forward neighbours (2 bits
+// each: RD, fixed background, fixed foreground).
+enum : uint16_t {
+    kVfUp = 1, kVfDown = 2, kVfLeft = 4, kVfRight = 8, kVfBack = 16, kVfFront = 32,
+    kVfShiftDown = 6, kVfShiftRight = 8, kVfShiftFront = 10   // 2-bit neighbour codes
+};
+enum { kVnRd = 0, kVnBg = 1, kVnFg = 2 };
 
 // one p buffer (selected without indexing the state's array by a runtime
 // value, which would put it in local memory)
@@ -50,7 +61,7 @@ __device__ __forceinline__ VolBuf vol_buf(const VolState& S, int b) {
 }
 
 constexpr int kVolThreads = 1024;   // one block per SM
-constexpr int kVolPlanes = 8;       // p[2][3], w, up
+constexpr int kVolPlanes = 10;      // p[2][3], w, up, off, flg
 
 __device__ __forceinline__ uint32_t plane_bit(const uint32_t* __restrict__ plane, int nw, int64_t r,
                                               int j) {
@@ -114,85 +125,149 @@ __global__ void k_vol_w(VolGeom G, const uint32_t* __restrict__ act, const float
     }
 }
 
+// Offsets and flags of the RD voxels (one pass over the voxel list).
+__global__ void k_vol_setup(VolGeom G, const int32_t* __restrict__ vox, const int32_t* __restrict__ counts,
+                            const uint32_t* __restrict__ act, const uint32_t* __restrict__ fgm, VolState S) {
+    const int n = counts[1];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int id = vox[k];   // r * W + j
+        const int r = id / G.W, j = id - r * G.W;
+        const int z = r / G.H, i = r - z * G.H;
+        auto code = [&](int64_t rr, int jj) -> uint16_t {
+            if (plane_bit(act, G.nw, rr, jj)) return kVnRd;
+            return plane_bit(fgm, G.nw, rr, jj) ? kVnFg : kVnBg;
+        };
+        uint16_t fl = 0;
+        if (i > 0) fl |= kVfUp;
+        if (j > 0) fl |= kVfLeft;
+        if (z > 0) fl |= kVfBack;
+        if (i + 1 < G.H) fl |= kVfDown | (uint16_t)(code(r + 1, j) << kVfShiftDown);
+        if (j + 1 < G.W) fl |= kVfRight | (uint16_t)(code(r, j + 1) << kVfShiftRight);
+        if (z + 1 < G.D) fl |= kVfFront | (uint16_t)(code(r + G.H, j) << kVfShiftFront);
+        S.off[k] = (int32_t)((int64_t)r * G.ld + j);
+        S.flg[k] = fl;
+    }
+}
+
 // w at a fixed voxel y: p(y) = 0, so div p(y) is minus the backward
 // neighbours' components along the axes where y has one; v(y) = H(-f(y)).
-__device__ __forceinline__ float vol_wfixed(const VolGeom& G, const float* P1, const float* P2, const float* P3,
-                                            int64_t y, int zy, int iy, int jy, uint32_t fgy) {
-    const float s = (iy > 0 ? P1[y - G.ld] : 0.f) + (jy > 0 ? P2[y - 1] : 0.f) +
-                    (zy > 0 ? P3[y - G.slice] : 0.f);
-    return -s - (fgy ? G.inv_theta : 0.f);
+// hu, hl, hb: whether y has a neighbour above / left / behind.
+__device__ __forceinline__ float vol_wfixed(const VolGeom& G, const VolBuf& B, int64_t y, bool hu, bool hl,
+                                            bool hb, unsigned code) {
+    const float s = (hu ? B.p1[y - G.ld] : 0.f) + (hl ? B.p2[y - 1] : 0.f) + (hb ? B.p3[y - G.slice] : 0.f);
+    return -s - (code == kVnFg ? G.inv_theta : 0.f);
 }
 
-// Dual (fixed-point) step at RD voxel (r, j) from the previous p (Bi) into Bo.
-__device__ __forceinline__ void vol_dual(const VolGeom& G, const uint32_t* __restrict__ act,
-                                         const uint32_t* __restrict__ fgm, const VolState& S, const VolBuf& Bi,
-                                         const VolBuf& Bo, int r, int j) {
-    const int z = r / G.H, i = r - z * G.H;
-    const int64_t o = (int64_t)r * G.ld + j;
-    const float* P1 = Bi.p1;
-    const float* P2 = Bi.p2;
-    const float* P3 = Bi.p3;
-    const float w0 = S.w[o];
-    float g1 = 0.f, g2 = 0.f, g3 = 0.f;
-    if (i + 1 < G.H) {
-        const int64_t y = o + G.ld;
-        const float wy = plane_bit(act, G.nw, r + 1, j) ? S.w[y]
-                                                        : vol_wfixed(G, P1, P2, P3, y, z, i + 1, j,
-                                                                     plane_bit(fgm, G.nw, r + 1, j));
-        g1 = wy - w0;
+// The voxels of a thread are taken kVolUnroll at a time: first every load of
+// the group, then the arithmetic and the stores (loads ahead of the stores
+// let the compiler keep them in flight together).  One voxel at a time with
+// this order measured fastest (256^3 volume: 270 us per full-volume
+// iteration at 1, 326 at 2, 517 at 4 with 512 threads).
+constexpr int kVolUnroll = 1;
+
+// Dual (fixed-point) step at RD voxels (list entries k0 + u * stride) from the
+// previous p (Bi) into Bo.
+__device__ __forceinline__ void vol_dual(const VolGeom& G, const VolState& S, const VolBuf& Bi, const VolBuf& Bo,
+                                         int n, int k0, int stride) {
+    int64_t o[kVolUnroll];
+    unsigned fl[kVolUnroll];
+    float w0[kVolUnroll], wy[kVolUnroll][3], pp[kVolUnroll][3];
+#pragma unroll
+    for (int u = 0; u < kVolUnroll; ++u) {
+        const int k = k0 + u * stride;
+        o[u] = k < n ? (int64_t)__ldg(S.off + k) : 0;
+        fl[u] = k < n ? (unsigned)__ldg(S.flg + k) : 0u;
     }
-    if (j + 1 < G.W) {
-        const int64_t y = o + 1;
-        const float wy = plane_bit(act, G.nw, r, j + 1) ? S.w[y]
-                                                        : vol_wfixed(G, P1, P2, P3, y, z, i, j + 1,
-                                                                     plane_bit(fgm, G.nw, r, j + 1));
-        g2 = wy - w0;
+#pragma unroll
+    for (int u = 0; u < kVolUnroll; ++u) {
+        if (k0 + u * stride >= n) continue;
+        const int64_t x = o[u];
+        const unsigned f = fl[u];
+        const bool hu = f & kVfUp, hl = f & kVfLeft, hb = f & kVfBack;
+        w0[u] = S.w[x];
+        pp[u][0] = Bi.p1[x];
+        pp[u][1] = Bi.p2[x];
+        pp[u][2] = Bi.p3[x];
+        wy[u][0] = wy[u][1] = wy[u][2] = 0.f;
+        if (f & kVfDown) {
+            const unsigned c = (f >> kVfShiftDown) & 3u;
+            wy[u][0] = c == kVnRd ? S.w[x + G.ld] : vol_wfixed(G, Bi, x + G.ld, true, hl, hb, c);
+        }
+        if (f & kVfRight) {
+            const unsigned c = (f >> kVfShiftRight) & 3u;
+            wy[u][1] = c == kVnRd ? S.w[x + 1] : vol_wfixed(G, Bi, x + 1, hu, true, hb, c);
+        }
+        if (f & kVfFront) {
+            const unsigned c = (f >> kVfShiftFront) & 3u;
+            wy[u][2] = c == kVnRd ? S.w[x + G.slice] : vol_wfixed(G, Bi, x + G.slice, hu, hl, true, c);
+        }
     }
-    if (z + 1 < G.D) {
-        const int64_t y = o + G.slice;
-        const float wy = plane_bit(act, G.nw, r + G.H, j) ? S.w[y]
-                                                          : vol_wfixed(G, P1, P2, P3, y, z + 1, i, j,
-                                                                       plane_bit(fgm, G.nw, r + G.H, j));
-        g3 = wy - w0;
+#pragma unroll
+    for (int u = 0; u < kVolUnroll; ++u) {
+        if (k0 + u * stride >= n) continue;
+        const unsigned f = fl[u];
+        const float g1 = (f & kVfDown) ? wy[u][0] - w0[u] : 0.f;
+        const float g2 = (f & kVfRight) ? wy[u][1] - w0[u] : 0.f;
+        const float g3 = (f & kVfFront) ? wy[u][2] - w0[u] : 0.f;
+        const float s = fmaf(g1, g1, fmaf(g2, g2, g3 * g3));
+        const float nrm = s > 0.f ? s * rsqrtf(s) : 0.f;
+        const float rc = __fdividef(1.0f, fmaf(G.tau, nrm, 1.0f));
+        Bo.p1[o[u]] = fmaf(G.tau, g1, pp[u][0]) * rc;
+        Bo.p2[o[u]] = fmaf(G.tau, g2, pp[u][1]) * rc;
+        Bo.p3[o[u]] = fmaf(G.tau, g3, pp[u][2]) * rc;
     }
-    const float s = fmaf(g1, g1, fmaf(g2, g2, g3 * g3));
-    const float nrm = s > 0.f ? s * rsqrtf(s) : 0.f;
-    const float rc = __fdividef(1.0f, fmaf(G.tau, nrm, 1.0f));
-    Bo.p1[o] = fmaf(G.tau, g1, P1[o]) * rc;
-    Bo.p2[o] = fmaf(G.tau, g2, P2[o]) * rc;
-    Bo.p3[o] = fmaf(G.tau, g3, P3[o]) * rc;
 }
 
-// Primal step at RD voxel (r, j) with the new p (Bo): u, v in place, w for
-// the next dual step, the stopping-test sums.
+// Primal step at RD voxels (list entries k0 + u * stride) with the new p
+// (Bo): u, v in place, w for the next dual step, the stopping-test sums.
 __device__ __forceinline__ void vol_primal(const VolGeom& G, const float* __restrict__ f, float* U, float* V,
-                                           const VolState& S, const VolBuf& Bo, int r, int j, bool check,
-                                           bool write_u, bool write_prev, float& du2, float& dv2) {
-    const int z = r / G.H, i = r - z * G.H;
-    const int64_t o = (int64_t)r * G.ld + j;
-    const float div = vol_div(G, Bo.p1, Bo.p2, Bo.p3, o, z, i, j);
-    const float vv = V[o];
-    const float un = fmaf(-G.theta, div, vv);
-    const float vn = clamp01(un - G.theta_lambda * __ldg(f + o));
-    V[o] = vn;
-    S.w[o] = div - vn * G.inv_theta;
-    if (check) {
-        const float da = un - S.up[o], db = vn - vv;
-        du2 = fmaf(da, da, du2);
-        dv2 = fmaf(db, db, dv2);
+                                           const VolState& S, const VolBuf& Bo, int n, int k0, int stride,
+                                           bool check, bool write_u, bool write_prev, float& du2, float& dv2) {
+    int64_t o[kVolUnroll];
+    unsigned fl[kVolUnroll];
+    float dv[kVolUnroll], vv[kVolUnroll], ff[kVolUnroll], uo[kVolUnroll];
+#pragma unroll
+    for (int u = 0; u < kVolUnroll; ++u) {
+        const int k = k0 + u * stride;
+        o[u] = k < n ? (int64_t)__ldg(S.off + k) : 0;
+        fl[u] = k < n ? (unsigned)__ldg(S.flg + k) : 0u;
     }
-    if (write_prev) S.up[o] = un;
-    if (write_u) U[o] = un;
+#pragma unroll
+    for (int u = 0; u < kVolUnroll; ++u) {
+        if (k0 + u * stride >= n) continue;
+        const int64_t x = o[u];
+        const unsigned b = fl[u];
+        const float a1 = ((b & kVfDown) ? Bo.p1[x] : 0.f) - ((b & kVfUp) ? Bo.p1[x - G.ld] : 0.f);
+        const float a2 = ((b & kVfRight) ? Bo.p2[x] : 0.f) - ((b & kVfLeft) ? Bo.p2[x - 1] : 0.f);
+        const float a3 = ((b & kVfFront) ? Bo.p3[x] : 0.f) - ((b & kVfBack) ? Bo.p3[x - G.slice] : 0.f);
+        dv[u] = a1 + a2 + a3;
+        vv[u] = V[x];
+        ff[u] = __ldg(f + x);
+        uo[u] = check ? S.up[x] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kVolUnroll; ++u) {
+        if (k0 + u * stride >= n) continue;
+        const int64_t x = o[u];
+        const float un = fmaf(-G.theta, dv[u], vv[u]);
+        const float vn = clamp01(un - G.theta_lambda * ff[u]);
+        V[x] = vn;
+        S.w[x] = dv[u] - vn * G.inv_theta;
+        if (check) {
+            const float da = un - uo[u], db = vn - vv[u];
+            du2 = fmaf(da, da, du2);
+            dv2 = fmaf(db, db, dv2);
+        }
+        if (write_prev) S.up[x] = un;
+        if (write_u) U[x] = un;
+    }
 }
 
 template <typename Fn>
-__device__ __forceinline__ void vol_each(const VolGeom& G, const int32_t* __restrict__ vox, int n, Fn fn) {
+__device__ __forceinline__ void vol_each(int n, Fn fn) {
     const int stride = (int)gridDim.x * kVolThreads;
-    for (int k = (int)blockIdx.x * kVolThreads + (int)threadIdx.x; k < n; k += stride) {
-        const int id = __ldg(vox + k);   // r * W + j
-        const int r = id / G.W;
-        fn(r, id - r * G.W);
-    }
+    for (int k0 = (int)blockIdx.x * kVolThreads + (int)threadIdx.x; k0 < n; k0 += kVolUnroll * stride)
+        fn(k0, stride);
 }
 
 __global__ void __launch_bounds__(kVolThreads, 1)
@@ -212,11 +287,11 @@ k_solve_vol(VolGeom G, int iters, int check_every, double tol, const uint32_t* _
         const bool check = (l % C == 0) || l == iters;
         const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
         const VolBuf Bi = vol_buf(S, (l - 1) & 1), Bo = vol_buf(S, l & 1);
-        vol_each(G, vox, n, [&](int r, int j) { vol_dual(G, act, fgm, S, Bi, Bo, r, j); });
+        vol_each(n, [&](int k0, int stride) { vol_dual(G, S, Bi, Bo, n, k0, stride); });
         if (!grid_sync(h, nblocks, gen)) return;
         float du2 = 0.f, dv2 = 0.f;
-        vol_each(G, vox, n, [&](int r, int j) {
-            vol_primal(G, f, U, V, S, Bo, r, j, check, check, write_prev, du2, dv2);
+        vol_each(n, [&](int k0, int stride) {
+            vol_primal(G, f, U, V, S, Bo, n, k0, stride, check, check, write_prev, du2, dv2);
         });
         double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
         if (check) {
@@ -325,6 +400,8 @@ extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, c
         for (int k = 0; k < 3; ++k) S.p[b][k] = reinterpret_cast<float*>(sb + (size_t)(3 * b + k) * plane);
     S.w = reinterpret_cast<float*>(sb + 6 * plane);
     S.up = reinterpret_cast<float*>(sb + 7 * plane);
+    S.off = reinterpret_cast<int32_t*>(sb + 8 * plane);
+    S.flg = reinterpret_cast<uint16_t*>(sb + 9 * plane);
 
     SEG_TRY(launch_solve_begin(h, s));
     const int64_t n = (int64_t)R * W;
@@ -335,6 +412,8 @@ extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, c
         k_vol_w<<<eblocks, 256, 0, s>>>(G, act, v, S);
         SEG_LAUNCHED("k_vol_w");
     }
+    k_vol_setup<<<eblocks, 256, 0, s>>>(G, voxels, counts, act, fgm, S);
+    SEG_LAUNCHED("k_vol_setup");
     const void* kern = (const void*)k_solve_vol;
     int per_sm = 0;
     SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVolThreads, 0));
