@@ -249,13 +249,18 @@ seg_status seg_solve(const float* f, int H, int W, int ld,
  *                 1 and storage SEG_STORE_F32; mode is ignored.
  *   u, v, p1, p2, p3  [D][H][ld] float32: warm start in, result out (p1
  *                 along rows, p2 along columns, p3 along slices).
- *   state         seg_state_bytes3d(D, H, ld) bytes, 256-byte aligned.
+ *   wstart, voxels  seg_build_domain's compact starts and RD voxel list
+ *                 (`pixels`) for the stacked image.
+ *   state         seg_state_bytes3d(capacity) bytes, 256-byte aligned: the
+ *                 compact state of up to `capacity` RD voxels (92 bytes each).
  *   stats         out double[8] (device), as seg_solve.
- * Errors: INVALID_ARG, ALIGN, CAPACITY (state too small), WORKSPACE (a
- * workspace for the (D*H) x W image), CUDA; TIMEOUT in the status word. */
-size_t seg_state_bytes3d(int D, int H, int ld);
+ * Errors: INVALID_ARG, ALIGN, WORKSPACE (a workspace for the (D*H) x W
+ * image), CUDA on the host; CAPACITY (more RD voxels than the state holds)
+ * and TIMEOUT in the status word. */
+size_t seg_state_bytes3d(int64_t capacity);
 seg_status seg_solve3d(const float* f, int D, int H, int W, int ld,
-                       const uint32_t* act, const uint32_t* fg, const int32_t* voxels,
+                       const uint32_t* act, const uint32_t* fg, const int32_t* wstart,
+                       const int32_t* voxels,
                        const int32_t* counts, const seg_params* prm,
                        float* u, float* v, float* p1, float* p2, float* p3,
                        void* state, size_t state_bytes, double* stats,

@@ -5,19 +5,25 @@
 // A volume is [D][H][ld] float32 (slice z, row i, column j; the rows of all
 // slices stacked), so the fitting term and the partition of
 // seg_make_fitting / seg_build_domain apply to it unchanged as a (D*H) x W
-// image: RD bits, f<0 bits and the list of 32-column x tile_h-row tiles that
-// hold an RD voxel.  The iteration is the 2-D one with a third component of
-// p and the slice neighbours (grad: forward differences along rows, columns
-// and slices, 0 on the last one; div = -grad^T):
+// image: RD bits, f<0 bits, the compact starts of every mask word and the
+// RD voxel list in tile-major order.  The iteration is the 2-D one with a
+// third component of p and the slice neighbours (grad: forward differences
+// along rows, columns and slices, 0 on the last one; div = -grad^T):
 //   w = div p - v/theta,  p <- (p + tau grad w) / (1 + tau |grad w|)   on RD
 //   u = v - theta div p,  v = clip(u - theta lambda f, 0, 1)           on RD
-// The state is dense ([D][H][ld] planes, p = 0 outside RD), ping-pong for p
-// so that w at a fixed neighbour y (p(y) = 0, v(y) = H(-f(y))) can be formed
-// from the previous p of y's backward neighbours.  One persistent
-// cooperative launch runs every iteration over the RD voxel list of
-// seg_build_domain (linear ids in tile-major order, so consecutive threads
-// take neighbouring voxels and no lane idles on a fixed voxel), two grid
-// barriers per iteration, the Section 4 test every check_every iterations.
+//
+// The state is compact: one element per RD voxel in list order (p in two
+// ping-pong buffers, w, v, theta lambda f, u of the iteration before a
+// stopping test, the voxel's dense offset) plus a neighbour table of 12
+// entries per voxel (compact index, or a code for fixed background /
+// foreground / outside): the six axis neighbours, and for each forward
+// neighbour y the two backward neighbours of y other than the voxel itself,
+// which w at a fixed y needs (p(y) = 0 and v(y) = H(-f(y)), so w(y) is minus
+// the sum of those neighbours' previous p components, minus v(y)/theta).
+// Consecutive threads take consecutive voxels, so the voxel's own state is
+// read and written in full sectors however scattered RD is in the volume.
+// One persistent cooperative launch runs every iteration: two grid barriers
+// per iteration, the Section 4 test every check_every iterations.
 #include <algorithm>
 #include <cmath>
 
@@ -27,28 +33,31 @@
 namespace seg {
 
 struct VolGeom {
-    int D, H, W, ld, nw, ntx, th;
+    int D, H, W, ld, nw;
     int R;              // rows of the stacked volume, D * H
-    int64_t slice;      // H * ld
     float theta, inv_theta, tau, theta_lambda;
 };
 
-struct VolState {
-    float* p[2][3];     // buffer b, component k (along rows, columns, slices)
-    float* w;           // div p - v/theta of the current iterate (RD voxels)
-    float* up;          // u of the iteration before a stopping test
-    int32_t* off;       // per RD voxel (list order): its offset (z*H + i)*ld + j
-    uint16_t* flg;      // per RD voxel: kVf* bits below
+// neighbour slots: the six axis neighbours, then for y = x + e1, x + e2,
+// x + e3 (in that order) the two backward neighbours of y other than x
+enum {
+    VN_UP = 0, VN_DOWN, VN_LEFT, VN_RIGHT, VN_BACK, VN_FRONT,
+    VN_DOWN_LEFT, VN_DOWN_BACK,     // (x + e1) - e2, (x + e1) - e3
+    VN_RIGHT_UP, VN_RIGHT_BACK,     // (x + e2) - e1, (x + e2) - e3
+    VN_FRONT_UP, VN_FRONT_LEFT,     // (x + e3) - e1, (x + e3) - e2
+    VN_COUNT
 };
+constexpr int kVBg = -1;    // fixed background: p = 0, v = 0
+constexpr int kVFg = -2;    // fixed foreground: p = 0, v = 1
+constexpr int kVOut = -3;   // outside the volume
 
-// Per-voxel flags, computed once per solve: which backward / forward
-// neighbours exist, and the state of the three forward neighbours (2 bits
-// each: RD, fixed background, fixed foreground).
-enum : uint16_t {
-    kVfUp = 1, kVfDown = 2, kVfLeft = 4, kVfRight = 8, kVfBack = 16, kVfFront = 32,
-    kVfShiftDown = 6, kVfShiftRight = 8, kVfShiftFront = 10   // 2-bit neighbour codes
+struct VolState {           // compact arrays, `stride` elements each
+    float* p[2][3];         // buffer b, component k (along rows, columns, slices)
+    float *w, *v, *f, *up;  // w = div p - v/theta; f premultiplied by theta lambda
+    int32_t* off;           // dense offset (z*H + i)*ld + j of each RD voxel
+    int32_t* nb;            // [VN_COUNT][stride]
+    int64_t cap, stride;
 };
-enum { kVnRd = 0, kVnBg = 1, kVnFg = 2 };
 
 // one p buffer (selected without indexing the state's array by a runtime
 // value, which would put it in local memory)
@@ -61,225 +70,194 @@ __device__ __forceinline__ VolBuf vol_buf(const VolState& S, int b) {
 }
 
 constexpr int kVolThreads = 1024;   // one block per SM
-constexpr int kVolPlanes = 10;      // p[2][3], w, up, off, flg
+constexpr int kVolArrays = 11 + VN_COUNT;
+constexpr int64_t kVolSlack = 256;
+
+inline int64_t vol_stride(int64_t capacity) {
+    return (std::max<int64_t>(capacity, 1) + kVolSlack + 63) / 64 * 64;
+}
 
 __device__ __forceinline__ uint32_t plane_bit(const uint32_t* __restrict__ plane, int nw, int64_t r,
                                               int j) {
     return (__ldg(plane + r * nw + (j >> 5)) >> (j & 31)) & 1u;
 }
 
-// Start iterate: u0 = H(-f) (or the caller's u) and v0 = clip(u0 - theta
-// lambda f) on RD, the fixed values outside; p = 0 outside RD and on the
-// components that never enter div (last row / column / slice).
-__global__ void k_vol_init(VolGeom G, const uint32_t* __restrict__ act, const uint32_t* __restrict__ fgm,
-                           const float* __restrict__ f, int warm, float* u, float* v,
-                           const float* __restrict__ p1in, const float* __restrict__ p2in,
-                           const float* __restrict__ p3in, VolState S) {
+// Compact index of voxel (z, i, j) if it is in RD, else its code.
+__device__ __forceinline__ int vol_code(const VolGeom& G, const uint32_t* __restrict__ act,
+                                        const uint32_t* __restrict__ fgm, const int32_t* __restrict__ wstart,
+                                        int z, int i, int j) {
+    if (z < 0 || z >= G.D || i < 0 || i >= G.H || j < 0 || j >= G.W) return kVOut;
+    const int64_t wo = ((int64_t)z * G.H + i) * G.nw + (j >> 5);
+    const uint32_t a = __ldg(act + wo);
+    const int b = j & 31;
+    if ((a >> b) & 1u) return __ldg(wstart + wo) + __popc(a & lanemask_lt(b));
+    return ((__ldg(fgm + wo) >> b) & 1u) ? kVFg : kVBg;
+}
+
+// Fixed voxels of the dense outputs (u = v = H(-f), p = 0); RD voxels are
+// written by the solve and the scatter.
+__global__ void k_vol_fixed(VolGeom G, const uint32_t* __restrict__ act, const uint32_t* __restrict__ fgm,
+                            float* u, float* v, float* p1, float* p2, float* p3) {
     const int64_t n = (int64_t)G.R * G.W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(x / G.W), j = (int)(x - (int64_t)r * G.W);
-        const int z = r / G.H, i = r - z * G.H;
+        if (plane_bit(act, G.nw, r, j)) continue;
         const int64_t o = (int64_t)r * G.ld + j;
         const float hh = plane_bit(fgm, G.nw, r, j) ? 1.f : 0.f;
-        float uu = hh, vv = hh, q1 = 0.f, q2 = 0.f, q3 = 0.f, ww = 0.f;
-        if (plane_bit(act, G.nw, r, j)) {
-            if (warm) {
-                uu = u[o];
-                vv = v[o];
-                q1 = i < G.H - 1 ? p1in[o] : 0.f;
-                q2 = j < G.W - 1 ? p2in[o] : 0.f;
-                q3 = z < G.D - 1 ? p3in[o] : 0.f;
-            } else {
-                vv = clamp01(uu - G.theta_lambda * f[o]);
-                ww = -vv * G.inv_theta;   // div p = 0
-            }
-        }
-        u[o] = uu;
-        v[o] = vv;
-        S.p[0][0][o] = q1; S.p[0][1][o] = q2; S.p[0][2][o] = q3;
-        S.p[1][0][o] = 0.f; S.p[1][1][o] = 0.f; S.p[1][2][o] = 0.f;
-        S.w[o] = ww;
-        S.up[o] = uu;
+        u[o] = hh;
+        v[o] = hh;
+        p1[o] = 0.f;
+        p2[o] = 0.f;
+        p3[o] = 0.f;
     }
 }
 
-__device__ __forceinline__ float vol_div(const VolGeom& G, const float* Q1, const float* Q2, const float* Q3,
-                                         int64_t o, int z, int i, int j) {
-    const float a = (i < G.H - 1 ? Q1[o] : 0.f) - (i > 0 ? Q1[o - G.ld] : 0.f);
-    const float b = (j < G.W - 1 ? Q2[o] : 0.f) - (j > 0 ? Q2[o - 1] : 0.f);
-    const float c = (z < G.D - 1 ? Q3[o] : 0.f) - (z > 0 ? Q3[o - G.slice] : 0.f);
-    return a + b + c;
-}
-
-// w of a warm start (the caller's p): div p - v/theta on RD.
-__global__ void k_vol_w(VolGeom G, const uint32_t* __restrict__ act, const float* __restrict__ v, VolState S) {
-    const int64_t n = (int64_t)G.R * G.W;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(x / G.W), j = (int)(x - (int64_t)r * G.W);
-        if (!plane_bit(act, G.nw, r, j)) continue;
-        const int z = r / G.H, i = r - z * G.H;
-        const int64_t o = (int64_t)r * G.ld + j;
-        S.w[o] = vol_div(G, S.p[0][0], S.p[0][1], S.p[0][2], o, z, i, j) - v[o] * G.inv_theta;
-    }
-}
-
-// Offsets and flags of the RD voxels (one pass over the voxel list).
+// Compact state and neighbour table of every RD voxel (list entry k is
+// compact index k): start iterate u0 = H(-f) and v0 = clip(u0 - theta lambda
+// f) (or the caller's u, v, p, with the p components that never enter div
+// -- last row / column / slice -- held at 0), w = -v/theta for a cold start.
 __global__ void k_vol_setup(VolGeom G, const int32_t* __restrict__ vox, const int32_t* __restrict__ counts,
-                            const uint32_t* __restrict__ act, const uint32_t* __restrict__ fgm, VolState S) {
+                            const uint32_t* __restrict__ act, const uint32_t* __restrict__ fgm,
+                            const int32_t* __restrict__ wstart, const float* __restrict__ f, int warm,
+                            const float* u, const float* v, const float* p1in, const float* p2in,
+                            const float* p3in, VolState S, WsHeader* h) {
     const int n = counts[1];
+    if (n > S.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            record_status(h, SEG_ERR_CAPACITY);
+            h->done = 1;
+            h->iters_done = 0;
+        }
+        return;
+    }
+    const int64_t st = S.stride;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int id = vox[k];   // r * W + j
+        const int id = __ldg(vox + k);   // r * W + j
         const int r = id / G.W, j = id - r * G.W;
         const int z = r / G.H, i = r - z * G.H;
-        auto code = [&](int64_t rr, int jj) -> uint16_t {
-            if (plane_bit(act, G.nw, rr, jj)) return kVnRd;
-            return plane_bit(fgm, G.nw, rr, jj) ? kVnFg : kVnBg;
-        };
-        uint16_t fl = 0;
-        if (i > 0) fl |= kVfUp;
-        if (j > 0) fl |= kVfLeft;
-        if (z > 0) fl |= kVfBack;
-        if (i + 1 < G.H) fl |= kVfDown | (uint16_t)(code(r + 1, j) << kVfShiftDown);
-        if (j + 1 < G.W) fl |= kVfRight | (uint16_t)(code(r, j + 1) << kVfShiftRight);
-        if (z + 1 < G.D) fl |= kVfFront | (uint16_t)(code(r + G.H, j) << kVfShiftFront);
-        S.off[k] = (int32_t)((int64_t)r * G.ld + j);
-        S.flg[k] = fl;
+        const int64_t o = (int64_t)r * G.ld + j;
+        int32_t* nb = S.nb + k;
+        nb[VN_UP * st] = vol_code(G, act, fgm, wstart, z, i - 1, j);
+        nb[VN_DOWN * st] = vol_code(G, act, fgm, wstart, z, i + 1, j);
+        nb[VN_LEFT * st] = vol_code(G, act, fgm, wstart, z, i, j - 1);
+        nb[VN_RIGHT * st] = vol_code(G, act, fgm, wstart, z, i, j + 1);
+        nb[VN_BACK * st] = vol_code(G, act, fgm, wstart, z - 1, i, j);
+        nb[VN_FRONT * st] = vol_code(G, act, fgm, wstart, z + 1, i, j);
+        nb[VN_DOWN_LEFT * st] = vol_code(G, act, fgm, wstart, z, i + 1, j - 1);
+        nb[VN_DOWN_BACK * st] = vol_code(G, act, fgm, wstart, z - 1, i + 1, j);
+        nb[VN_RIGHT_UP * st] = vol_code(G, act, fgm, wstart, z, i - 1, j + 1);
+        nb[VN_RIGHT_BACK * st] = vol_code(G, act, fgm, wstart, z - 1, i, j + 1);
+        nb[VN_FRONT_UP * st] = vol_code(G, act, fgm, wstart, z + 1, i - 1, j);
+        nb[VN_FRONT_LEFT * st] = vol_code(G, act, fgm, wstart, z + 1, i, j - 1);
+        S.off[k] = (int32_t)o;
+        const float fv = f[o];
+        S.f[k] = G.theta_lambda * fv;
+        const float hh = plane_bit(fgm, G.nw, r, j) ? 1.f : 0.f;
+        float uu = hh, vv, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+        if (warm) {
+            uu = u[o];
+            vv = v[o];
+            q1 = i < G.H - 1 ? p1in[o] : 0.f;
+            q2 = j < G.W - 1 ? p2in[o] : 0.f;
+            q3 = z < G.D - 1 ? p3in[o] : 0.f;
+        } else {
+            vv = clamp01(uu - G.theta_lambda * fv);
+        }
+        S.p[0][0][k] = q1;
+        S.p[0][1][k] = q2;
+        S.p[0][2][k] = q3;
+        S.v[k] = vv;
+        S.up[k] = uu;
+        S.w[k] = -vv * G.inv_theta;   // div p = 0 (cold start); k_vol_warm_w otherwise
     }
 }
 
-// w at a fixed voxel y: p(y) = 0, so div p(y) is minus the backward
-// neighbours' components along the axes where y has one; v(y) = H(-f(y)).
-// hu, hl, hb: whether y has a neighbour above / left / behind.
-__device__ __forceinline__ float vol_wfixed(const VolGeom& G, const VolBuf& B, int64_t y, bool hu, bool hl,
-                                            bool hb, unsigned code) {
-    const float s = (hu ? B.p1[y - G.ld] : 0.f) + (hl ? B.p2[y - 1] : 0.f) + (hb ? B.p3[y - G.slice] : 0.f);
-    return -s - (code == kVnFg ? G.inv_theta : 0.f);
+// p component at a table entry (0 at fixed and outside voxels)
+__device__ __forceinline__ float vol_pat(const float* P, int c) { return c >= 0 ? P[c] : 0.f; }
+
+__device__ __forceinline__ float vol_div(const VolState& S, const VolBuf& B, int k) {
+    const int64_t st = S.stride;
+    const int nu = __ldg(S.nb + VN_UP * st + k), nl = __ldg(S.nb + VN_LEFT * st + k);
+    const int nbk = __ldg(S.nb + VN_BACK * st + k);
+    return (B.p1[k] - vol_pat(B.p1, nu)) + (B.p2[k] - vol_pat(B.p2, nl)) + (B.p3[k] - vol_pat(B.p3, nbk));
 }
 
-// The voxels of a thread are taken kVolUnroll at a time: first every load of
-// the group, then the arithmetic and the stores (loads ahead of the stores
-// let the compiler keep them in flight together).  One voxel at a time with
-// this order measured fastest (256^3 volume: 270 us per full-volume
-// iteration at 1, 326 at 2, 517 at 4 with 512 threads).
-constexpr int kVolUnroll = 1;
+// w = div p - v/theta of a warm start (after the whole table exists).
+__global__ void k_vol_warm_w(const int32_t* __restrict__ counts, VolGeom G, VolState S) {
+    const int n = counts[1];
+    if (n > S.cap) return;
+    const VolBuf B = vol_buf(S, 0);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        S.w[k] = vol_div(S, B, k) - S.v[k] * G.inv_theta;
+}
 
-// Dual (fixed-point) step at RD voxels (list entries k0 + u * stride) from the
-// previous p (Bi) into Bo.
+// Dual (fixed-point) step at compact voxel k from the previous p (Bi) into Bo.
 __device__ __forceinline__ void vol_dual(const VolGeom& G, const VolState& S, const VolBuf& Bi, const VolBuf& Bo,
-                                         int n, int k0, int stride) {
-    int64_t o[kVolUnroll];
-    unsigned fl[kVolUnroll];
-    float w0[kVolUnroll], wy[kVolUnroll][3], pp[kVolUnroll][3];
-#pragma unroll
-    for (int u = 0; u < kVolUnroll; ++u) {
-        const int k = k0 + u * stride;
-        o[u] = k < n ? (int64_t)__ldg(S.off + k) : 0;
-        fl[u] = k < n ? (unsigned)__ldg(S.flg + k) : 0u;
+                                         int k) {
+    const int64_t st = S.stride;
+    const int* nb = S.nb + k;
+    const int nd = __ldg(nb + VN_DOWN * st), nr = __ldg(nb + VN_RIGHT * st), nf = __ldg(nb + VN_FRONT * st);
+    const float w0 = S.w[k];
+    const float p1 = Bi.p1[k], p2 = Bi.p2[k], p3 = Bi.p3[k];
+    float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+    if (nd >= 0) {
+        g1 = S.w[nd] - w0;
+    } else if (nd != kVOut) {   // w at a fixed y = x + e1: its p1 backward neighbour is x itself
+        const float s = p1 + vol_pat(Bi.p2, __ldg(nb + VN_DOWN_LEFT * st)) +
+                        vol_pat(Bi.p3, __ldg(nb + VN_DOWN_BACK * st));
+        g1 = (-s - (nd == kVFg ? G.inv_theta : 0.f)) - w0;
     }
-#pragma unroll
-    for (int u = 0; u < kVolUnroll; ++u) {
-        if (k0 + u * stride >= n) continue;
-        const int64_t x = o[u];
-        const unsigned f = fl[u];
-        const bool hu = f & kVfUp, hl = f & kVfLeft, hb = f & kVfBack;
-        w0[u] = S.w[x];
-        pp[u][0] = Bi.p1[x];
-        pp[u][1] = Bi.p2[x];
-        pp[u][2] = Bi.p3[x];
-        wy[u][0] = wy[u][1] = wy[u][2] = 0.f;
-        if (f & kVfDown) {
-            const unsigned c = (f >> kVfShiftDown) & 3u;
-            wy[u][0] = c == kVnRd ? S.w[x + G.ld] : vol_wfixed(G, Bi, x + G.ld, true, hl, hb, c);
-        }
-        if (f & kVfRight) {
-            const unsigned c = (f >> kVfShiftRight) & 3u;
-            wy[u][1] = c == kVnRd ? S.w[x + 1] : vol_wfixed(G, Bi, x + 1, hu, true, hb, c);
-        }
-        if (f & kVfFront) {
-            const unsigned c = (f >> kVfShiftFront) & 3u;
-            wy[u][2] = c == kVnRd ? S.w[x + G.slice] : vol_wfixed(G, Bi, x + G.slice, hu, hl, true, c);
-        }
+    if (nr >= 0) {
+        g2 = S.w[nr] - w0;
+    } else if (nr != kVOut) {
+        const float s = vol_pat(Bi.p1, __ldg(nb + VN_RIGHT_UP * st)) + p2 +
+                        vol_pat(Bi.p3, __ldg(nb + VN_RIGHT_BACK * st));
+        g2 = (-s - (nr == kVFg ? G.inv_theta : 0.f)) - w0;
     }
-#pragma unroll
-    for (int u = 0; u < kVolUnroll; ++u) {
-        if (k0 + u * stride >= n) continue;
-        const unsigned f = fl[u];
-        const float g1 = (f & kVfDown) ? wy[u][0] - w0[u] : 0.f;
-        const float g2 = (f & kVfRight) ? wy[u][1] - w0[u] : 0.f;
-        const float g3 = (f & kVfFront) ? wy[u][2] - w0[u] : 0.f;
-        const float s = fmaf(g1, g1, fmaf(g2, g2, g3 * g3));
-        const float nrm = s > 0.f ? s * rsqrtf(s) : 0.f;
-        const float rc = __fdividef(1.0f, fmaf(G.tau, nrm, 1.0f));
-        Bo.p1[o[u]] = fmaf(G.tau, g1, pp[u][0]) * rc;
-        Bo.p2[o[u]] = fmaf(G.tau, g2, pp[u][1]) * rc;
-        Bo.p3[o[u]] = fmaf(G.tau, g3, pp[u][2]) * rc;
+    if (nf >= 0) {
+        g3 = S.w[nf] - w0;
+    } else if (nf != kVOut) {
+        const float s = vol_pat(Bi.p1, __ldg(nb + VN_FRONT_UP * st)) +
+                        vol_pat(Bi.p2, __ldg(nb + VN_FRONT_LEFT * st)) + p3;
+        g3 = (-s - (nf == kVFg ? G.inv_theta : 0.f)) - w0;
     }
+    const float s = fmaf(g1, g1, fmaf(g2, g2, g3 * g3));
+    const float nrm = s > 0.f ? s * rsqrtf(s) : 0.f;
+    const float rc = __fdividef(1.0f, fmaf(G.tau, nrm, 1.0f));
+    Bo.p1[k] = fmaf(G.tau, g1, p1) * rc;
+    Bo.p2[k] = fmaf(G.tau, g2, p2) * rc;
+    Bo.p3[k] = fmaf(G.tau, g3, p3) * rc;
 }
 
-// Primal step at RD voxels (list entries k0 + u * stride) with the new p
-// (Bo): u, v in place, w for the next dual step, the stopping-test sums.
-__device__ __forceinline__ void vol_primal(const VolGeom& G, const float* __restrict__ f, float* U, float* V,
-                                           const VolState& S, const VolBuf& Bo, int n, int k0, int stride,
+// Primal step at compact voxel k with the new p (Bo): v in place, w for the
+// next dual step, u to the dense output on a stopping-test iteration.
+__device__ __forceinline__ void vol_primal(const VolGeom& G, float* U, const VolState& S, const VolBuf& Bo, int k,
                                            bool check, bool write_u, bool write_prev, float& du2, float& dv2) {
-    int64_t o[kVolUnroll];
-    unsigned fl[kVolUnroll];
-    float dv[kVolUnroll], vv[kVolUnroll], ff[kVolUnroll], uo[kVolUnroll];
-#pragma unroll
-    for (int u = 0; u < kVolUnroll; ++u) {
-        const int k = k0 + u * stride;
-        o[u] = k < n ? (int64_t)__ldg(S.off + k) : 0;
-        fl[u] = k < n ? (unsigned)__ldg(S.flg + k) : 0u;
+    const float div = vol_div(S, Bo, k);
+    const float vv = S.v[k];
+    const float un = fmaf(-G.theta, div, vv);
+    const float vn = clamp01(un - __ldg(S.f + k));   // f premultiplied by theta lambda
+    S.v[k] = vn;
+    S.w[k] = div - vn * G.inv_theta;
+    if (check) {
+        const float da = un - S.up[k], db = vn - vv;
+        du2 = fmaf(da, da, du2);
+        dv2 = fmaf(db, db, dv2);
     }
-#pragma unroll
-    for (int u = 0; u < kVolUnroll; ++u) {
-        if (k0 + u * stride >= n) continue;
-        const int64_t x = o[u];
-        const unsigned b = fl[u];
-        const float a1 = ((b & kVfDown) ? Bo.p1[x] : 0.f) - ((b & kVfUp) ? Bo.p1[x - G.ld] : 0.f);
-        const float a2 = ((b & kVfRight) ? Bo.p2[x] : 0.f) - ((b & kVfLeft) ? Bo.p2[x - 1] : 0.f);
-        const float a3 = ((b & kVfFront) ? Bo.p3[x] : 0.f) - ((b & kVfBack) ? Bo.p3[x - G.slice] : 0.f);
-        dv[u] = a1 + a2 + a3;
-        vv[u] = V[x];
-        ff[u] = __ldg(f + x);
-        uo[u] = check ? S.up[x] : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < kVolUnroll; ++u) {
-        if (k0 + u * stride >= n) continue;
-        const int64_t x = o[u];
-        const float un = fmaf(-G.theta, dv[u], vv[u]);
-        const float vn = clamp01(un - G.theta_lambda * ff[u]);
-        V[x] = vn;
-        S.w[x] = dv[u] - vn * G.inv_theta;
-        if (check) {
-            const float da = un - uo[u], db = vn - vv[u];
-            du2 = fmaf(da, da, du2);
-            dv2 = fmaf(db, db, dv2);
-        }
-        if (write_prev) S.up[x] = un;
-        if (write_u) U[x] = un;
-    }
-}
-
-template <typename Fn>
-__device__ __forceinline__ void vol_each(int n, Fn fn) {
-    const int stride = (int)gridDim.x * kVolThreads;
-    for (int k0 = (int)blockIdx.x * kVolThreads + (int)threadIdx.x; k0 < n; k0 += kVolUnroll * stride)
-        fn(k0, stride);
+    if (write_prev) S.up[k] = un;
+    if (write_u) U[__ldg(S.off + k)] = un;
 }
 
 __global__ void __launch_bounds__(kVolThreads, 1)
-k_solve_vol(VolGeom G, int iters, int check_every, double tol, const uint32_t* __restrict__ act,
-            const uint32_t* __restrict__ fgm, const int32_t* __restrict__ vox,
-            const int32_t* __restrict__ counts, const float* __restrict__ f, float* U, float* V, VolState S,
-            double* partials, WsHeader* h) {
+k_solve_vol(VolGeom G, int iters, int check_every, double tol, const int32_t* __restrict__ counts, float* U,
+            VolState S, double* partials, WsHeader* h) {
     __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
     if (*(volatile int*)&h->done) return;
     const unsigned nblocks = gridDim.x;
     const int n = counts[1];
     const int tid = threadIdx.x;
+    const int k0 = (int)blockIdx.x * kVolThreads + tid, stride = (int)nblocks * kVolThreads;
     const int C = check_every;
     unsigned gen = 0;
     int chk = 0;
@@ -287,12 +265,10 @@ k_solve_vol(VolGeom G, int iters, int check_every, double tol, const uint32_t* _
         const bool check = (l % C == 0) || l == iters;
         const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
         const VolBuf Bi = vol_buf(S, (l - 1) & 1), Bo = vol_buf(S, l & 1);
-        vol_each(n, [&](int k0, int stride) { vol_dual(G, S, Bi, Bo, n, k0, stride); });
+        for (int k = k0; k < n; k += stride) vol_dual(G, S, Bi, Bo, k);
         if (!grid_sync(h, nblocks, gen)) return;
         float du2 = 0.f, dv2 = 0.f;
-        vol_each(n, [&](int k0, int stride) {
-            vol_primal(G, f, U, V, S, Bo, n, k0, stride, check, check, write_prev, du2, dv2);
-        });
+        for (int k = k0; k < n; k += stride) vol_primal(G, U, S, Bo, k, check, check, write_prev, du2, dv2);
         double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
         if (check) {
             float x = du2, y = dv2;
@@ -331,19 +307,21 @@ k_solve_vol(VolGeom G, int iters, int check_every, double tol, const uint32_t* _
     }
 }
 
-// p of the final iterate (buffer of its parity) to the caller's planes.
-__global__ void k_vol_final(VolGeom G, const WsHeader* __restrict__ h, int iters, VolState S, float* p1,
-                            float* p2, float* p3) {
+// v and p of the final iterate (p from the buffer of its parity) to the dense
+// outputs; u too when no iteration ran (iterations write it themselves).
+__global__ void k_vol_scatter(const int32_t* __restrict__ counts, const WsHeader* __restrict__ h, int iters,
+                              VolState S, float* u, float* v, float* p1, float* p2, float* p3) {
+    const int n = counts[1];
+    if (n > S.cap) return;
     const int l = h->done ? h->iters_done : iters;
     const VolBuf B = vol_buf(S, l & 1);
-    const int64_t n = (int64_t)G.R * G.W;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(x / G.W), j = (int)(x - (int64_t)r * G.W);
-        const int64_t o = (int64_t)r * G.ld + j;
-        p1[o] = B.p1[o];
-        p2[o] = B.p2[o];
-        p3[o] = B.p3[o];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int64_t o = S.off[k];
+        v[o] = S.v[k];
+        p1[o] = B.p1[k];
+        p2[o] = B.p2[k];
+        p3[o] = B.p3[k];
+        if (l == 0) u[o] = S.up[k];
     }
 }
 
@@ -351,19 +329,18 @@ __global__ void k_vol_final(VolGeom G, const WsHeader* __restrict__ h, int iters
 
 using namespace seg;
 
-extern "C" size_t seg_state_bytes3d(int D, int H, int ld) {
-    const size_t plane = (size_t)std::max(D, 0) * (size_t)std::max(H, 0) * (size_t)std::max(ld, 0);
-    return kVolPlanes * align_up(4 * plane, 256) + 256;
+extern "C" size_t seg_state_bytes3d(int64_t capacity) {
+    return (size_t)kVolArrays * align_up(4 * (size_t)vol_stride(capacity), 256) + 256;
 }
 
 extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, const uint32_t* act,
-                                  const uint32_t* fgm, const int32_t* voxels, const int32_t* counts,
-                                  const seg_params* prm, float* u, float* v, float* p1, float* p2, float* p3,
-                                  void* state, size_t state_bytes, double* stats, void* ws,
+                                  const uint32_t* fgm, const int32_t* wstart, const int32_t* voxels,
+                                  const int32_t* counts, const seg_params* prm, float* u, float* v, float* p1,
+                                  float* p2, float* p3, void* state, size_t state_bytes, double* stats, void* ws,
                                   size_t ws_bytes, void* stream) {
     clear_error();
     if (!prm) return fail(SEG_ERR_INVALID_ARG, "params must be non-NULL");
-    if (!f || !act || !fgm || !voxels || !counts || !u || !v || !p1 || !p2 || !p3 || !state || !stats)
+    if (!f || !act || !fgm || !wstart || !voxels || !counts || !u || !v || !p1 || !p2 || !p3 || !state || !stats)
         return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
     if (D <= 0 || H <= 0 || W <= 0 || ld < W || (int64_t)D * H * ld >= (1ll << 31))
         return fail(SEG_ERR_INVALID_ARG, "bad volume size D=%d H=%d W=%d ld=%d (D*H*ld < 2^31)", D, H, W, ld);
@@ -376,8 +353,6 @@ extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, c
     if (!(prm->theta > 0) || !(prm->tau > 0) || !std::isfinite(prm->lambda) || std::isnan(prm->tol))
         return fail(SEG_ERR_INVALID_ARG, "theta, tau must be > 0 and lambda finite");
     if (prm->storage != SEG_STORE_F32) return fail(SEG_ERR_INVALID_ARG, "volumes use float32 storage");
-    const size_t need = seg_state_bytes3d(D, H, ld);
-    if (state_bytes < need) return fail(SEG_ERR_CAPACITY, "volume state needs %zu bytes, got %zu", need, state_bytes);
     if (reinterpret_cast<uintptr_t>(state) % 256) return fail(SEG_ERR_ALIGN, "state not 256-byte aligned");
     const int R = D * H;
     WsLayout L = ws_layout(R, W, th);
@@ -387,48 +362,54 @@ extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, c
     double* partials = ws_at<double>(ws, L.partials);
 
     VolGeom G{};
-    G.D = D; G.H = H; G.W = W; G.ld = ld; G.nw = ld / 32; G.ntx = (W + 31) / 32; G.th = th; G.R = R;
-    G.slice = (int64_t)H * ld;
+    G.D = D; G.H = H; G.W = W; G.ld = ld; G.nw = ld / 32; G.R = R;
     G.theta = (float)prm->theta;
     G.inv_theta = (float)(1.0 / prm->theta);
     G.tau = (float)prm->tau;
     G.theta_lambda = (float)(prm->theta * prm->lambda);
+    // the largest array length (a multiple of 64) whose arrays fit in state_bytes
     VolState S{};
-    const size_t plane = align_up(4 * (size_t)R * ld, 256);
+    const size_t per_array = state_bytes > 256 ? (state_bytes - 256) / kVolArrays / 256 * 256 : 0;
+    S.stride = (int64_t)(per_array / 4) / 64 * 64;
+    S.cap = std::max<int64_t>(0, S.stride - kVolSlack);
     char* sb = static_cast<char*>(state);
     for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < 3; ++k) S.p[b][k] = reinterpret_cast<float*>(sb + (size_t)(3 * b + k) * plane);
-    S.w = reinterpret_cast<float*>(sb + 6 * plane);
-    S.up = reinterpret_cast<float*>(sb + 7 * plane);
-    S.off = reinterpret_cast<int32_t*>(sb + 8 * plane);
-    S.flg = reinterpret_cast<uint16_t*>(sb + 9 * plane);
+        for (int k = 0; k < 3; ++k) S.p[b][k] = reinterpret_cast<float*>(sb + (size_t)(3 * b + k) * per_array);
+    S.w = reinterpret_cast<float*>(sb + 6 * per_array);
+    S.v = reinterpret_cast<float*>(sb + 7 * per_array);
+    S.f = reinterpret_cast<float*>(sb + 8 * per_array);
+    S.up = reinterpret_cast<float*>(sb + 9 * per_array);
+    S.off = reinterpret_cast<int32_t*>(sb + 10 * per_array);
+    S.nb = reinterpret_cast<int32_t*>(sb + 11 * per_array);   // VN_COUNT arrays of stride
 
     SEG_TRY(launch_solve_begin(h, s));
-    const int64_t n = (int64_t)R * W;
-    const int eblocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
-    k_vol_init<<<eblocks, 256, 0, s>>>(G, act, fgm, f, prm->warm_start, u, v, p1, p2, p3, S);
-    SEG_LAUNCHED("k_vol_init");
-    if (prm->warm_start) {
-        k_vol_w<<<eblocks, 256, 0, s>>>(G, act, v, S);
-        SEG_LAUNCHED("k_vol_w");
-    }
-    k_vol_setup<<<eblocks, 256, 0, s>>>(G, voxels, counts, act, fgm, S);
+    const int64_t nvox = (int64_t)R * W;
+    const int eblocks = (int)std::min<int64_t>((nvox + 255) / 256, (int64_t)sm_count() * 16);
+    k_vol_setup<<<eblocks, 256, 0, s>>>(G, voxels, counts, act, fgm, wstart, f, prm->warm_start, u, v, p1, p2,
+                                        p3, S, h);
     SEG_LAUNCHED("k_vol_setup");
+    if (prm->warm_start) {
+        k_vol_warm_w<<<eblocks, 256, 0, s>>>(counts, G, S);
+        SEG_LAUNCHED("k_vol_warm_w");
+    }
+    k_vol_fixed<<<eblocks, 256, 0, s>>>(G, act, fgm, u, v, p1, p2, p3);
+    SEG_LAUNCHED("k_vol_fixed");
     const void* kern = (const void*)k_solve_vol;
     int per_sm = 0;
     SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVolThreads, 0));
     if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_vol cannot be resident");
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), L.npartials / 2);
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (std::max<int64_t>(S.cap, 1) + kVolThreads - 1) /
+                                                                  kVolThreads));
     int iters = prm->iters, ce = prm->check_every;
     double tol = prm->tol;
-    void* args[] = {&G, &iters, &ce, &tol, (void*)&act, (void*)&fgm, (void*)&voxels, (void*)&counts,
-                    (void*)&f, &u, &v, &S, &partials, &h};
+    void* args[] = {&G, &iters, &ce, &tol, (void*)&counts, &u, &S, &partials, &h};
     if (iters > 0) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kVolThreads), args, 0, s));
         count_launch();
     }
-    k_vol_final<<<eblocks, 256, 0, s>>>(G, h, prm->iters, S, p1, p2, p3);
-    SEG_LAUNCHED("k_vol_final");
+    k_vol_scatter<<<eblocks, 256, 0, s>>>(counts, h, prm->iters, S, u, v, p1, p2, p3);
+    SEG_LAUNCHED("k_vol_scatter");
     SEG_TRY(launch_solve_end(h, counts, prm->iters, stats, s));
     return SEG_OK;
 }

@@ -106,9 +106,9 @@ SIGNATURES = {
                       _P, _P, _P, _P, _P, _P, _P, _Z, _P, _Z, _P], _I),
     "seg_solve_pd": ([_P, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(seg_pd_params), _P, _P, _P, _P,
                       _Z, _P, _P, _Z, _P], _I),
-    "seg_state_bytes3d": ([_I, _I, _I], _Z),
-    "seg_solve3d": ([_P, _I, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(seg_params), _P, _P, _P, _P, _P,
-                     _P, _Z, _P, _P, _Z, _P], _I),
+    "seg_state_bytes3d": ([_L], _Z),
+    "seg_solve3d": ([_P, _I, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(seg_params), _P, _P, _P, _P,
+                     _P, _P, _Z, _P, _P, _Z, _P], _I),
     "seg_solve_batch": ([ctypes.POINTER(seg_image), _I, ctypes.POINTER(seg_params), _P, _Z, _P, _P, _Z,
                          _P], _I),
 }
@@ -215,16 +215,17 @@ def seg_solve_pd(f, act, fg, wstart, counts, params: seg_pd_params, u, p1, p2, s
                             _nbytes(state), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)))
 
 
-def seg_state_bytes3d(D, H, ld):
-    return load().seg_state_bytes3d(int(D), int(H), int(ld))
+def seg_state_bytes3d(capacity):
+    return load().seg_state_bytes3d(int(capacity))
 
 
-def seg_solve3d(f, D, H, act, fg, voxels, counts, params: seg_params, u, v, p1, p2, p3, state, stats,
-                ws, stream=None):
-    """f, u, v, p1, p2, p3: [D*H][ld] stacked volume images; voxels: the RD
-    voxel list of seg_build_domain on the stacked image."""
+def seg_solve3d(f, D, H, act, fg, wstart, voxels, counts, params: seg_params, u, v, p1, p2, p3, state,
+                stats, ws, stream=None):
+    """f, u, v, p1, p2, p3: [D*H][ld] stacked volume images; wstart, voxels:
+    seg_build_domain's compact starts and RD voxel list for the stacked image."""
     lib = load()
-    _check(lib.seg_solve3d(_ptr(f), int(D), int(H), _W(f), f.stride(0), _ptr(act), _ptr(fg), _ptr(voxels),
+    _check(lib.seg_solve3d(_ptr(f), int(D), int(H), _W(f), f.stride(0), _ptr(act), _ptr(fg), _ptr(wstart),
+                           _ptr(voxels),
                            _ptr(counts), ctypes.byref(params), _ptr(u), _ptr(v), _ptr(p1), _ptr(p2),
                            _ptr(p3), _ptr(state), _nbytes(state), _ptr(stats), _ptr(ws), _nbytes(ws),
                            _stream(stream)))
@@ -566,7 +567,7 @@ class VolumeSolver:
     solve through the C ABI (seg_make_fitting and seg_build_domain on the
     stacked image, seg_solve3d for the iteration)."""
 
-    def __init__(self, D, H, W, tile_h=16, device="cuda", stream=None):
+    def __init__(self, D, H, W, tile_h=16, capacity=None, device="cuda", stream=None):
         self.D, self.H, self.W, self.tile_h = D, H, W, tile_h
         self.device = torch.device(device)
         self.stream = stream
@@ -578,7 +579,8 @@ class VolumeSolver:
         self.p1 = image(R, W, device=self.device)
         self.p2 = image(R, W, device=self.device)
         self.p3 = image(R, W, device=self.device)
-        nb = seg_state_bytes3d(D, H, pitch(W))
+        self.capacity = D * H * W if capacity is None else int(capacity)
+        nb = seg_state_bytes3d(self.capacity)
         self.state = torch.empty((nb + 255) // 256 * 256, dtype=torch.uint8, device=self.device)
         self.stats = torch.zeros(8, dtype=torch.float64, device=self.device)
         self.c = torch.zeros(2, dtype=torch.float64, device=self.device)
@@ -610,7 +612,7 @@ class VolumeSolver:
         d = self.dom
         prm = make_params(lam, theta, tau, iters, tol, 1, check_every, warm_start, "compact", "f32",
                           self.tile_h)
-        seg_solve3d(self.f, self.D, self.H, d.act, d.fg, d.pixels, d.counts, prm, self.u, self.v,
+        seg_solve3d(self.f, self.D, self.H, d.act, d.fg, d.wstart, d.pixels, d.counts, prm, self.u, self.v,
                     self.p1, self.p2, self.p3, self.state, self.stats, self.ws, self.stream)
         return self.stats
 

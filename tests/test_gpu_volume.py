@@ -127,11 +127,14 @@ def test_volume_argument_and_capacity_errors():
         base.update(kw)
         prm = seg.make_params(*base.values())
         with pytest.raises(seg.SegError) as e:
-            seg.seg_solve3d(S.f, 4, 10, d.act, d.fg, d.pixels, d.counts, prm, S.u, S.v, S.p1, S.p2, S.p3,
+            seg.seg_solve3d(S.f, 4, 10, d.act, d.fg, d.wstart, d.pixels, d.counts, prm, S.u, S.v, S.p1, S.p2, S.p3,
                             S.state, S.stats, S.ws)
         assert e.value.status == seg.SEG_ERR_INVALID_ARG
-    prm = seg.make_params(1.0)
+    # a state for 10 RD voxels: the solve records CAPACITY and does not run
+    small = seg.VolumeSolver(4, 10, 20, capacity=10)
+    small.f.copy_(S.f)
+    small.domain(delta=0.2)
+    small.solve(1.0, iters=10)
     with pytest.raises(seg.SegError) as e:
-        seg.seg_solve3d(S.f, 4, 10, d.act, d.fg, d.pixels, d.counts, prm, S.u, S.v, S.p1, S.p2, S.p3,
-                        S.state[:1024], S.stats, S.ws)
+        small.check_status()
     assert e.value.status == seg.SEG_ERR_CAPACITY
