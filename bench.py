@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--delta", type=float, default=0.2)
     ap.add_argument("--profile-tiled", action="store_true",
                     help="with --profile: also the temporally blocked solver, restricted and full")
+    ap.add_argument("--profile-next", action="store_true",
+                    help="with --profile: also the primal-dual solve of the same image and a "
+                         "128^3 spheres volume (restricted delta = 0.1), --iters iterations each")
     return ap.parse_args()
 
 
@@ -358,6 +361,21 @@ def run_profile(args):
         S.check_status()
         print(f"{mode}: delta={delta} active={int(S.dom.counts[1])} tiles={int(S.dom.counts[0])} "
               f"iters={int(S.stats[0])}")
+        if args.profile_next and mode == "compact":
+            S.solve_pd(args.lam, iters=P.iters, check_every=10)
+            torch.cuda.synchronize()
+            S.check_status()
+            print(f"primal-dual: iters={int(S.stats[0])}")
+    if args.profile_next:
+        from paper_1807_11534_gb300 import synth
+        V = synth.spheres_volume(seed=0, D=128, H=128, W=128, n_spheres=20)
+        VS = seg.VolumeSolver(128, 128, 128, tile_h=8, device=dev)
+        VS.fitting(VS.upload(V.z), 0.3, 0.7)
+        VS.domain(delta=0.1)
+        VS.solve(args.lam, iters=P.iters, check_every=10)
+        torch.cuda.synchronize()
+        VS.check_status()
+        print(f"volume: active={int(VS.dom.counts[1])} iters={int(VS.stats[0])}")
 
 
 def run_batch(args, rank, world):
