@@ -6,8 +6,9 @@ taken from torch tensors and the current torch CUDA stream; all arithmetic runs
 in the CUDA kernels of libseg.  There is no CPU fallback: if the library cannot
 be loaded the import raises.
 
-Higher up, ``Domain`` and ``solve_image`` only allocate buffers (through
-torch) and chain the entry points.
+Higher up, ``Solver`` (one image), ``BatchSolver``, ``DiffSolver`` (with
+the adjoint), ``VolumeSolver`` (3-D) and ``capture_graph`` only allocate
+buffers (through torch), chain the entry points and record their launches.
 """
 from __future__ import annotations
 
