@@ -126,3 +126,70 @@ def test_oracle_and_library_share_no_code():
     for fn in os.listdir(os.path.join(ROOT, "oracle")):
         if fn.endswith((".py", ".c", ".h")):
             assert not bad_orc.search(open(os.path.join(ROOT, "oracle", fn)).read()), fn
+
+
+def test_host_side_argument_errors_of_the_next_rows(lib):
+    """The robust restriction, the primal-dual solver, the volume solver and
+    the Chan-Vese update reject bad arguments before any device work."""
+    from paper_1807_11534_gb300 import seg
+    fake = 1 << 20
+    ws_ok = 1 << 30
+    # robust domain: radius range, then the checks of seg_build_domain
+    rargs = [fake, None, 8, 8, 32, 0.1, -1.0, 0, 16, fake, fake, fake, fake, 10, None, 0, fake, None,
+             fake, ws_ok, None]
+    for r in (-1, 33):
+        rargs[7] = r
+        assert lib.seg_build_domain_robust(*rargs) == seg.SEG_ERR_INVALID_ARG
+    rargs[7] = 2
+    rargs[8] = 12
+    assert lib.seg_build_domain_robust(*rargs) == seg.SEG_ERR_INVALID_ARG
+    # box mean: radius, aliasing, NULL, pitch
+    assert lib.seg_box_mean(fake, 8, 8, 32, 17, fake + 4096, None) == seg.SEG_ERR_INVALID_ARG
+    assert lib.seg_box_mean(fake, 8, 8, 32, 1, fake, None) == seg.SEG_ERR_INVALID_ARG
+    assert lib.seg_box_mean(None, 8, 8, 32, 1, fake, None) == seg.SEG_ERR_INVALID_ARG
+    assert lib.seg_box_mean(fake, 8, 8, 33, 1, fake + 4096, None) == seg.SEG_ERR_ALIGN
+    # primal-dual parameters
+    base = dict(sigma=seg.PD_STEP, tau=seg.PD_STEP, tol=0.0, iters=10, check_every=10, warm_start=0,
+                tile_h=16)
+    pargs = [fake, 8, 8, 32, fake, fake, fake, fake, None, fake, fake, fake, fake, 1 << 20, fake, fake,
+             ws_ok, None]
+    assert lib.seg_solve_pd(*pargs) == seg.SEG_ERR_INVALID_ARG
+    for field, bad in (("sigma", 0.0), ("tau", -1.0), ("sigma", math.inf), ("check_every", 0),
+                       ("iters", -1), ("tile_h", 5)):
+        kw = dict(base)
+        kw[field] = bad
+        prm = seg.seg_pd_params(1.0, kw["sigma"], kw["tau"], kw["tol"], kw["iters"], kw["check_every"],
+                                kw["warm_start"], kw["tile_h"])
+        pargs[8] = ctypes.byref(prm)
+        assert lib.seg_solve_pd(*pargs) == seg.SEG_ERR_INVALID_ARG, field
+    prm = seg.seg_pd_params(1.0, seg.PD_STEP, seg.PD_STEP, 0.0, 10, 10, 0, 16)
+    pargs[8] = ctypes.byref(prm)
+    pargs[3] = 33
+    assert lib.seg_solve_pd(*pargs) == seg.SEG_ERR_ALIGN
+    # volumes: parameters, sizes, state alignment
+    vargs = [fake, 4, 8, 8, 32, fake, fake, fake, fake, fake, None, fake, fake, fake, fake, fake, fake,
+             1 << 20, fake, fake, ws_ok, None]
+    for kw in (dict(n_inner=2), dict(storage="bf16"), dict(check_every=0), dict(tile_h=5)):
+        p = dict(lam=1.0, theta=0.2, tau=0.125, iters=10, tol=0.0, n_inner=1, check_every=10,
+                 warm_start=False, mode="compact", storage="f32", tile_h=16)
+        p.update(kw)
+        prm3 = seg.make_params(*p.values())
+        vargs[10] = ctypes.byref(prm3)
+        assert lib.seg_solve3d(*vargs) == seg.SEG_ERR_INVALID_ARG, kw
+    prm3 = seg.make_params(1.0, iters=10, tile_h=16)
+    vargs[10] = ctypes.byref(prm3)
+    vargs[1] = 0
+    assert lib.seg_solve3d(*vargs) == seg.SEG_ERR_INVALID_ARG
+    vargs[1] = 4
+    vargs[16] = fake + 16   # the state
+    assert lib.seg_solve3d(*vargs) == seg.SEG_ERR_ALIGN
+    # Chan-Vese update
+    assert lib.seg_update_means(fake, fake, 8, 8, 32, math.nan, None, fake, ws_ok, None) == \
+        seg.SEG_ERR_INVALID_ARG
+    assert lib.seg_update_means(fake, None, 8, 8, 32, 0.5, None, fake, ws_ok, None) == seg.SEG_ERR_INVALID_ARG
+
+
+def test_state_sizes_of_the_next_rows(lib):
+    from paper_1807_11534_gb300 import seg
+    a, b = seg.seg_state_bytes3d(1000), seg.seg_state_bytes3d(100000)
+    assert a < b and b >= 100000 * 92
