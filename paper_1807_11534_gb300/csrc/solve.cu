@@ -429,6 +429,7 @@ constexpr int kBackwardThreads = 512;   // block size of the persistent reverse 
 // dynamic shared memory of the persistent solver: one or two blocks per SM
 constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 110 * 1024; }
 constexpr int kCompactThreads = 1024;   // one block per SM
+constexpr int kCompactWideUnroll = 2;   // pixels per thread in flight in k_solve_compact_wide
 constexpr int kCompactUnroll = 4;       // pixels per thread in flight in the two-phase iteration
 constexpr int kFusePerThread = 3;       // fused iteration up to this many pixels per thread
 
@@ -1067,19 +1068,32 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
     return true;
 }
 
+// Which of the two persistent compact kernels runs a solve (both are
+// launched; the other returns at once).  The shared-memory kernel (one
+// block per SM, grid1 blocks) unless even its table rows would not fit in
+// shared memory -- then every block would take the global-memory path, and
+// k_solve_compact_wide, the same path at two blocks per SM (twice the warps
+// to hide the latency of the table and neighbour loads), runs instead.
+template <typename T>
+__device__ __forceinline__ bool compact_wide(int n, int grid1) {
+    const int64_t per1 = ((int64_t)n + grid1 - 1) / grid1;
+    return (size_t)per1 * (4 * NB_UUR + sizeof(T)) > compact_smem(1024);
+}
+
 template <typename T, int NT, int UNROLL>
 __global__ void __launch_bounds__(NT, 1024 / NT)
 k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
                 const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
                 T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
                 float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h, float* ckpt,
-                int ckpt_every) {
+                int ckpt_every, int grid1) {
     __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
     extern __shared__ __align__(16) unsigned char c_smem[];
     // set before the launch (capacity overflow): the same for every block
     if (*(volatile int*)&h->done) return;
     const unsigned nblocks = gridDim.x;
     const int n = counts[1];
+    if (compact_wide<T>(n, grid1)) return;
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
     const int tid = threadIdx.x, nt = NT;
@@ -1266,6 +1280,31 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
                                                  P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h, ckpt,
                                                  ckpt_every, s_red, fuse);
     }
+}
+
+// The global-memory path of k_solve_compact at two blocks per SM (32
+// registers a thread), for solves too large for the shared-memory paths.
+template <typename T, int NT, int UNROLL>
+__global__ void __launch_bounds__(NT, 2048 / NT)
+k_solve_compact_wide(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
+                     const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
+                     T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
+                     float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h, float* ckpt,
+                     int ckpt_every, int grid1) {
+    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
+    if (*(volatile int*)&h->done) return;
+    const int n = counts[1];
+    if (!compact_wide<T>(n, grid1)) return;
+    const unsigned nblocks = gridDim.x;
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    // (never the fused iteration: this kernel runs only when the one-block
+    // kernel's blocks would hold more than 8,000 pixels each, so with at
+    // most twice its blocks each block holds more than 3 x NT)
+    const Own<T, false> O{nb, stride, V, F, 0};
+    compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm, stride, P1a,
+                                             P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h, ckpt, ckpt_every,
+                                             s_red, 0);
 }
 
 // Dense u, v, p1, p2 of the final iterate of every image of the batch:
@@ -1526,11 +1565,23 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     float* Wc = S.w;
     float* Wc2 = S.w2;
     IterParams P = P0;
+    // the global-memory kernel for solves too large for shared memory (the
+    // kernels decide on the device which of them runs)
+    const void* kern2 = (const void*)k_solve_compact_wide<T, kCompactThreads, kCompactWideUnroll>;
+    int per_sm2 = 0;
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kern2, NTs, 0));
+    if (per_sm2 <= 0) return fail(SEG_ERR_CUDA, "k_solve_compact_wide cannot be resident");
+    int grid2 = (int)std::min<int64_t>((int64_t)per_sm2 * sm_count(),
+                                       std::max<int64_t>(1, (most + NTs - 1) / NTs));
+    grid2 = (int)std::min<int64_t>(grid2, max_partials / 2);
+    int grid1 = grid;
     void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&cnt, (void*)&nbp, &stride,
                     &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Up, &Wc, &Wc2, &partials, &h, &ckpt,
-                    &ckpt_every};
+                    &ckpt_every, &grid1};
     if (iters > 0 || warm) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NTs), args, smem, s));
+        count_launch();
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern2, dim3(grid2), dim3(NTs), args, 0, s));
         count_launch();
     }
     k_compact_scatter<T><<<gblocks, 256, 0, s>>>(B, base, totals, prm->iters, std::max(1, prm->n_inner),
