@@ -425,7 +425,7 @@ __device__ __forceinline__ float w_fixed(float p_in_1, float p_in_2, int code, f
 //  * neighbour-table rows and v in shared memory, neighbour values from the
 //    global arrays (only the owner reads a pixel's rows and v).
 //  * everything in global memory.
-constexpr int kBackwardThreads = 512;   // block size of the persistent reverse sweep
+constexpr int kBackwardThreads = 512;   // block size of the persistent reverse sweep (4 per SM)
 // dynamic shared memory of the persistent solver: one or two blocks per SM
 constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 110 * 1024; }
 constexpr int kCompactThreads = 1024;   // one block per SM
@@ -1694,7 +1694,7 @@ __device__ __forceinline__ double block_sum1(double x, double* s_red) {
     return t;
 }
 
-__global__ void __launch_bounds__(kBackwardThreads)
+__global__ void __launch_bounds__(kBackwardThreads, 4)
 k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
                    const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
                    const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
@@ -2140,11 +2140,11 @@ extern "C" seg_status seg_backward(const float* f, int H, int W, int ld, const u
 // iterate come from k_compact_gather; the state is the compact state's
 // arrays: p1[0..1], p2[0..1], u (U0), w (U1), up (ubar), f.
 
-constexpr int kPdThreads = 1024;
+constexpr int kPdThreads = 1024;   // two blocks per SM (32 registers): latency-bound loads
 
 __device__ __forceinline__ float pd_fixed(int code) { return code == kNbFg ? 1.f : 0.f; }
 
-__global__ void __launch_bounds__(kPdThreads, 1)
+__global__ void __launch_bounds__(kPdThreads, 2)
 k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
            const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
            float* P1a, float* P1b, float* P2a, float* P2b, float* U0, float* U1, float* Ub,
