@@ -54,7 +54,7 @@ __global__ void k_q_hist(const float* __restrict__ f, int H, int W, int ld, int 
     int64_t n = (int64_t)H * W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = x / W, j = x - i * W;
+        int64_t i = (int64_t)((uint32_t)x / (uint32_t)W), j = x - i * W;   // x < 2^31
         unsigned key = __float_as_uint(f[i * ld + j]) & 0x7fffffffu;
         bool match = hi >= 32 ? true : ((key >> hi) == (prefix >> hi));
         if (match) atomicAdd(&sh[(key >> shift) & 255u], 1u);
@@ -192,7 +192,7 @@ __global__ void k_box_mean(const float* __restrict__ f, int H, int W, int ld, in
                            float* __restrict__ out) {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= (int64_t)H * W) return;
-    const int i = (int)(x / W), j = (int)(x - (int64_t)i * W);
+    const int i = (int)((uint32_t)x / (uint32_t)W), j = (int)(x - (int64_t)i * W);   // x < 2^31
     const int i0 = max(i - r, 0), i1 = min(i + r, H - 1), j0 = max(j - r, 0), j1 = min(j + r, W - 1);
     double sum = 0.0;
     for (int a = i0; a <= i1; ++a)

@@ -154,7 +154,7 @@ __global__ void k_error_terms(const float* __restrict__ us, const float* __restr
     int64_t n = (int64_t)H * W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = x / W, j = x - i * W;
+        int64_t i = (int64_t)((uint32_t)x / (uint32_t)W), j = x - i * W;   // x < 2^31
         int64_t o = i * ld + j;
         float a = us[o], b = ug[o];
         bool A = b > eps, B = a > eps;

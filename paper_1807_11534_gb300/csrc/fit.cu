@@ -24,7 +24,7 @@ __global__ void k_label_sums(const float* __restrict__ z, const uint8_t* __restr
     int64_t n = (int64_t)H * W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = x / W, j = x - i * W;
+        int64_t i = (int64_t)((uint32_t)x / (uint32_t)W), j = x - i * W;   // x < 2^31
         double zz = (double)z[i * ld + j];
         if (label[i * ld + j]) { s1 = __dadd_rn(s1, zz); n1 += 1.0; }
         else                   { s0 = __dadd_rn(s0, zz); n0 += 1.0; }
@@ -70,7 +70,7 @@ __global__ void k_class_sums(const float* __restrict__ z, const float* __restric
     int64_t n = (int64_t)H * W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = x / W, j = x - i * W;
+        int64_t i = (int64_t)((uint32_t)x / (uint32_t)W), j = x - i * W;   // x < 2^31
         double zz = (double)z[i * ld + j];
         if (u[i * ld + j] > thresh) { s1 = __dadd_rn(s1, zz); n1 += 1.0; }
         else                        { s0 = __dadd_rn(s0, zz); n0 += 1.0; }
@@ -117,7 +117,7 @@ __global__ void k_marker_dmax(const int32_t* __restrict__ markers, int n_markers
     int64_t rounds = (n + stride - 1) / stride;
     for (int64_t r = 0; r < rounds; ++r) {
         int64_t x = x0 + r * stride;
-        int i = (int)(x / W), j = (int)(x - (int64_t)(x / W) * W);
+        const int i = (int)((uint32_t)x / (uint32_t)W), j = (int)(x - (int64_t)i * W);   // x < 2^31
         unsigned long long best = ~0ull;
         for (int c0 = 0; c0 < n_markers; c0 += kMarkerChunk) {
             int m = min(kMarkerChunk, n_markers - c0);
@@ -157,7 +157,7 @@ __global__ void k_fitting(const float* __restrict__ z, int H, int W, int ld,
     int64_t rounds = (n + stride - 1) / stride;
     for (int64_t r = 0; r < rounds; ++r) {
         int64_t x = x0 + r * stride;
-        int i = (int)(x / W), j = (int)(x - (int64_t)(x / W) * W);
+        const int i = (int)((uint32_t)x / (uint32_t)W), j = (int)(x - (int64_t)i * W);   // x < 2^31
         unsigned long long best = ~0ull;
         for (int c0 = 0; c0 < n_markers; c0 += kMarkerChunk) {
             int m = min(kMarkerChunk, n_markers - c0);

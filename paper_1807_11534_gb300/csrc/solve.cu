@@ -194,7 +194,7 @@ __global__ void k_init_dense(IterParams P, const uint32_t* __restrict__ act,
     int64_t n = (int64_t)P.H * P.W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = x / P.W, j = x - i * P.W;
+        int64_t i = (int64_t)((uint32_t)x / (uint32_t)P.W), j = x - i * P.W;   // x < 2^31
         int64_t o = i * P.ld + j, wo = i * P.nw + (j >> 5);
         bool a = (act[wo] >> (j & 31)) & 1u;
         float hh = ((fgm[wo] >> (j & 31)) & 1u) ? 1.f : 0.f;
@@ -219,7 +219,7 @@ __global__ void k_final_dense(IterParams P, const WsHeader* __restrict__ h, int 
     int64_t n = (int64_t)P.H * P.W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = x / P.W, j = x - i * P.W;
+        int64_t i = (int64_t)((uint32_t)x / (uint32_t)P.W), j = x - i * P.W;   // x < 2^31
         int64_t o = i * P.ld + j;
         p1[o] = P1[o]; p2[o] = P2[o]; v[o] = V[o];
     }
@@ -1832,7 +1832,7 @@ k_adj_scatter(IterParams P, const float* __restrict__ f, const uint32_t* __restr
     const int64_t n = (int64_t)P.H * P.W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = x / P.W, j = x - i * P.W;
+        const int64_t i = (int64_t)((uint32_t)x / (uint32_t)P.W), j = x - i * P.W;   // x < 2^31
         const int64_t wo = i * P.nw + (j >> 5);
         const int64_t o = i * P.ld + j;
         const uint32_t a = act[wo];

@@ -415,7 +415,7 @@ __global__ void k_final_tiled(IterParams P, const WsHeader* __restrict__ h, cons
     const int64_t n = (int64_t)P.H * P.W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = x / P.W, j = x - i * P.W;
+        const int64_t i = (int64_t)((uint32_t)x / (uint32_t)P.W), j = x - i * P.W;   // x < 2^31
         const int64_t o = i * P.ld + j;
         p1[o] = S1[o];
         p2[o] = S2[o];
