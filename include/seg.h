@@ -331,7 +331,11 @@ size_t seg_batch_workspace_bytes(int n_images, int64_t max_pixels);
  * whole batch) are shared, lambda is per image.  state: seg_state_bytes(0, 0,
  * capacity, SEG_MODE_COMPACT, storage) with capacity >= the total RD pixels
  * (else SEG_ERR_CAPACITY in the status word).  stats as for seg_solve
- * (stats[3] = total RD pixels).  Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA. */
+ * (stats[3] = total RD pixels).  With tol <= 0 and n_inner = 1 the launch
+ * may solve the images in consecutive waves of whole images (each small
+ * enough for shared memory); the iterates are the same (the images are
+ * independent) and stats[1..2] are summed over the waves.
+ * Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA. */
 seg_status seg_solve_batch(const seg_image* images, int n_images, const seg_params* prm,
                            void* state, size_t state_bytes, double* stats,
                            void* ws, size_t ws_bytes, void* stream);

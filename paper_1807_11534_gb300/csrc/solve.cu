@@ -596,11 +596,13 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
                                                    int iters, int n_inner, int check_every, double tol, int warm,
                                                    int64_t stride, T* P1a, T* P1b, T* P2a, T* P2b, float* Uu,
                                                    float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h,
-                                                   float* ckpt, int ckpt_every, double* s_red, int fuse) {
+                                                   float* ckpt, int ckpt_every, double* s_red, int fuse,
+                                                   unsigned& gen) {
+    // gen: barriers passed (the arrival counter starts at 0 each solve and
+    // runs on across the waves of a batch)
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = NT;
     int pb = 0;
-    unsigned gen = 0u;   // barriers passed (the arrival counter starts at 0 each solve)
     // the block's pixels, UNROLL per thread in flight (one in the fused
     // step, which keeps about three times as many values live)
     auto each = [&](auto&& op) {
@@ -923,7 +925,7 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
                                                       T* P1a, T* P1b, T* P2a, T* P2b, const float* F,
                                                       float* U, float* Up, float* Wc, double* partials,
                                                       WsHeader* h, float* ckpt, int ckpt_every, double* s_red,
-                                                      unsigned gen, int* fb, int* lf) {
+                                                      unsigned& gen, int* fb, int* lf) {
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = NT;
     const GhostLayout& L = S.L;
@@ -1080,22 +1082,18 @@ __device__ __forceinline__ bool compact_wide(int n, int grid1) {
     return (size_t)per1 * (4 * NB_UUR + sizeof(T)) > compact_smem(1024);
 }
 
+// All iterations of the compact solve over the RD pixels [w0, w0 + n) (the
+// whole problem, or one wave of whole images of a batch); false when a grid
+// barrier timed out.  gen: barriers passed so far in the launch.
 template <typename T, int NT, int UNROLL>
-__global__ void __launch_bounds__(NT, 1024 / NT)
-k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
-                const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
-                T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
-                float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h, float* ckpt,
-                int ckpt_every, int grid1) {
-    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
-    extern __shared__ __align__(16) unsigned char c_smem[];
-    // set before the launch (capacity overflow): the same for every block
-    if (*(volatile int*)&h->done) return;
+__device__ __forceinline__ bool compact_solve_range(
+    const IterParams& P, int iters, int n_inner, int check_every, double tol, int warm, int w0, int n,
+    const int32_t* __restrict__ nb, int64_t stride, T* P1a, T* P1b, T* P2a, T* P2b, T* V,
+    const float* __restrict__ F, float* U, float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h,
+    float* ckpt, int ckpt_every, unsigned& gen, double* s_red, unsigned char* c_smem) {
     const unsigned nblocks = gridDim.x;
-    const int n = counts[1];
-    if (compact_wide<T>(n, grid1)) return;
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
-    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    const int a0 = w0 + (int)blockIdx.x * per, a1 = min(w0 + n, a0 + per);
     const int tid = threadIdx.x, nt = NT;
     // the fused iteration pays off while barriers dominate, i.e. with few
     // pixels per thread; the two-phase one reads six table rows, not eight
@@ -1156,13 +1154,12 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
             uint16_t* gdst = reinterpret_cast<uint16_t*>(c_smem + L.offgd);
             uint16_t* lbd = reinterpret_cast<uint16_t*>(c_smem + L.offbd);
             uint16_t* lbp = reinterpret_cast<uint16_t*>(c_smem + L.offbp);
-            unsigned gen0 = 0u;
             if (warm) {   // w of the warm-start iterate, from the global arrays (as the other path)
                 float d0 = 0.f, d1 = 0.f;
                 const Own<T, false> O{nb, stride, V, F, 0};
                 for (int a = a0 + tid; a < a1; a += nt)
                     primal_one(P, a, O, P1a, P2a, U, Up, Wc, true, false, false, false, 0u, d0, d1);
-                if (!grid_sync(h, nblocks, gen0)) return;
+                if (!grid_sync(h, nblocks, gen)) return false;
             }
             // ghost slots: dual kinds first (down, right, dl, ur), then primal (up, left)
             if (tid == 0) {
@@ -1245,8 +1242,8 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
             // the barrier generation continues from the warm-start barrier
             if (!compact_iterations_gh<T, NT, UNROLL>(P, S, a0, a1, iters, check_every, tol, stride, P1a, P1b,
                                                        P2a, P2b, F, U, Up, Wc, partials, h, ckpt, ckpt_every,
-                                                       s_red, gen0, &fb, &lf))
-                return;
+                                                       s_red, gen, &fb, &lf))
+                return false;
             __syncthreads();
             // the final iterate: v, and p of every own pixel (only exported
             // pixels were kept current in the global arrays)
@@ -1257,7 +1254,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
                 Store<T>::st(G1, a0 + i, sm[L.p1 + fb * L.ns1 + i]);
                 Store<T>::st(G2, a0 + i, sm[L.p2 + fb * L.ns2 + i]);
             }
-            return;
+            return true;
         }
     }
     if ((size_t)per * (4 * rows + sizeof(T)) <= compact_smem(NT)) {   // the same in every block
@@ -1271,14 +1268,72 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
         const Own<T, true> O{nb_s, per, v_s, F, a0};
         if (!compact_iterations<T, true, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
                                                      stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
-                                                     ckpt, ckpt_every, s_red, fuse))
-            return;
+                                                     ckpt, ckpt_every, s_red, fuse, gen))
+            return false;
         for (int i = tid; i < a1 - a0; i += nt) V[a0 + i] = v_s[i];
-    } else {
-        const Own<T, false> O{nb, stride, V, F, 0};
-        compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm, stride,
-                                                 P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h, ckpt,
-                                                 ckpt_every, s_red, fuse);
+        return true;
+    }
+    const Own<T, false> O{nb, stride, V, F, 0};
+    return compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
+                                                    stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
+                                                    ckpt, ckpt_every, s_red, fuse, gen);
+}
+
+// Batches solved in waves: with a fixed iteration count (tol <= 0, so no
+// test decides anything across images) and n_inner = 1, a batch larger than
+// the shared-memory paths hold is solved as consecutive waves of whole
+// images, each at most kWavePerBlock pixels per block (images are
+// independent problems, so their iterates do not depend on the grouping);
+// stats then hold the norms of the last test summed over the waves, i.e.
+// over the whole batch, as without waves.
+constexpr int kWavePerBlock = 5000;
+
+inline bool compact_waves(int nimg, double tol, int n_inner, const float* ckpt) {
+    return nimg > 1 && !(tol > 0.0) && n_inner == 1 && ckpt == nullptr;
+}
+
+// WAVES: the batch's images in waves (see above); otherwise one range, and
+// this kernel returns at once when k_solve_compact_wide is the one to run.
+template <typename T, int NT, int UNROLL, bool WAVES>
+__global__ void __launch_bounds__(NT, 1024 / NT)
+k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double tol, int warm,
+                const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
+                T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
+                float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h, float* ckpt,
+                int ckpt_every, int grid1, const int32_t* __restrict__ base, int nimg) {
+    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
+    extern __shared__ __align__(16) unsigned char c_smem[];
+    // set before the launch (capacity overflow): the same for every block
+    if (*(volatile int*)&h->done) return;
+    const int n = counts[1];
+    unsigned gen = 0u;
+    if (!WAVES) {
+        if (compact_wide<T>(n, grid1)) return;
+        compact_solve_range<T, NT, UNROLL>(P, iters, n_inner, check_every, tol, warm, 0, n, nb, stride, P1a, P1b,
+                                           P2a, P2b, V, F, U, Up, Wc, Wc2, partials, h, ckpt, ckpt_every, gen,
+                                           s_red, c_smem);
+        return;
+    }
+    const int cap = (int)gridDim.x * kWavePerBlock;
+    double su = 0.0, sv = 0.0;   // block 0, thread 0: the last test's sums over the waves
+    for (int k0 = 0; k0 < nimg;) {
+        int k1 = k0 + 1;
+        while (k1 < nimg && __ldg(base + k1 + 1) - __ldg(base + k0) <= cap) ++k1;
+        const int w0 = __ldg(base + k0), wn = __ldg(base + k1) - w0;
+        k0 = k1;
+        if (wn == 0) continue;
+        if (!compact_solve_range<T, NT, UNROLL>(P, iters, n_inner, check_every, tol, warm, w0, wn, nb, stride,
+                                                P1a, P1b, P2a, P2b, V, F, U, Up, Wc, Wc2, partials, h, ckpt,
+                                                ckpt_every, gen, s_red, c_smem))
+            return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            su += h->du2;
+            sv += h->dv2;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        h->du2 = su;
+        h->dv2 = sv;
     }
 }
 
@@ -1290,7 +1345,7 @@ k_solve_compact_wide(IterParams P, int iters, int n_inner, int check_every, doub
                      const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
                      T* P1a, T* P1b, T* P2a, T* P2b, T* V, const float* __restrict__ F, float* U,
                      float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h, float* ckpt,
-                     int ckpt_every, int grid1) {
+                     int ckpt_every, int grid1, const int32_t* __restrict__ base, int nimg) {
     __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
     if (*(volatile int*)&h->done) return;
     const int n = counts[1];
@@ -1302,9 +1357,10 @@ k_solve_compact_wide(IterParams P, int iters, int n_inner, int check_every, doub
     // kernel's blocks would hold more than 8,000 pixels each, so with at
     // most twice its blocks each block holds more than 3 x NT)
     const Own<T, false> O{nb, stride, V, F, 0};
+    unsigned gen = 0u;
     compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm, stride, P1a,
                                              P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h, ckpt, ckpt_every,
-                                             s_red, 0);
+                                             s_red, 0, gen);
 }
 
 // Dense u, v, p1, p2 of the final iterate of every image of the batch:
@@ -1541,7 +1597,9 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     T* P2b = static_cast<T*>(S.p2[1]);
     T* V = static_cast<T*>(S.v);
     const int NTs = kCompactThreads;
-    const void* kern = (const void*)k_solve_compact<T, kCompactThreads, kCompactUnroll>;
+    const bool waves = compact_waves(B.n, prm->tol, std::max(1, prm->n_inner), ckpt);
+    const void* kern = waves ? (const void*)k_solve_compact<T, kCompactThreads, kCompactUnroll, true>
+                             : (const void*)k_solve_compact<T, kCompactThreads, kCompactUnroll, false>;
     const size_t smem = compact_smem(NTs);
     // one cooperative launch for the whole solve: the grid is what can be
     // resident at once (at most one block per NT RD pixels of capacity)
@@ -1575,14 +1633,18 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
                                        std::max<int64_t>(1, (most + NTs - 1) / NTs));
     grid2 = (int)std::min<int64_t>(grid2, max_partials / 2);
     int grid1 = grid;
+    const int32_t* bases = base;
+    int nimg = B.n;
     void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&cnt, (void*)&nbp, &stride,
                     &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Up, &Wc, &Wc2, &partials, &h, &ckpt,
-                    &ckpt_every, &grid1};
+                    &ckpt_every, &grid1, &bases, &nimg};
     if (iters > 0 || warm) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NTs), args, smem, s));
         count_launch();
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern2, dim3(grid2), dim3(NTs), args, 0, s));
-        count_launch();
+        if (!waves) {
+            SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern2, dim3(grid2), dim3(NTs), args, 0, s));
+            count_launch();
+        }
     }
     k_compact_scatter<T><<<gblocks, 256, 0, s>>>(B, base, totals, prm->iters, std::max(1, prm->n_inner),
                                                  S, h);
