@@ -160,3 +160,29 @@ def test_largest_batch_and_one_more(orc):
     with pytest.raises(seg.SegError) as e:
         B129.solve([1.0] * 129, iters=5)
     assert e.value.status == seg.SEG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_batch_waves_give_the_same_iterates(orc, storage):
+    """A batch with a fixed iteration count larger than one wave (5,000
+    pixels per block) runs in waves of whole images; with a stopping test
+    (never met) it runs as one range.  The images are independent and every
+    path rounds alike, so both give the same bits."""
+    seg = seg_mod()
+    shapes = [(600, 640), (512, 700), (640, 480), (700, 600), (480, 512), (620, 600), (500, 500)]
+    lams = [1.0, 1.5, 2.0, 0.7, 1.2, 1.8, 1.1]
+    qs = [0.4, 0.35, 0.4, 0.3, 0.4, 0.38, 0.4]
+    outs = []
+    for tol in (0.0, 1e-30):
+        B, _ = _batch(orc, shapes, lams, qs, 40, storage=storage, tol=tol)
+        B.check_status()
+        assert int(B.stats[3].item()) > 152 * 5000   # more than one wave
+        outs.append([{k: seg.download(getattr(S, k)) for k in ("u", "v", "p1", "p2")} for S in B.solvers])
+        outs[-1].append(B.stats.cpu().numpy().copy())
+    for a, b in zip(outs[0][:-1], outs[1][:-1]):
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k])
+    sa, sb = outs[0][-1], outs[1][-1]
+    assert sa[0] == sb[0] == 40 and sa[3] == sb[3]
+    # the last test's norms: summed over the waves vs over the one range
+    assert sa[1] == pytest.approx(sb[1], rel=1e-5) and sa[2] == pytest.approx(sb[2], rel=1e-5)
