@@ -138,3 +138,37 @@ def test_pd_argument_and_capacity_errors():
     with pytest.raises(seg.SegError) as e:
         S.check_status()
     assert e.value.status == seg.SEG_ERR_CAPACITY
+
+
+@pytest.mark.slow
+def test_pd_largest_image_sampled(orc):
+    """A 16384 x 16384 image (268 M pixels, H * ld just below 2^31) with the
+    primal-dual solver: random fitting term, delta = 0.1, 12 iterations,
+    oracle crops around sampled RD pixels and the corners."""
+    seg = seg_mod()
+    rng = np.random.default_rng(31)
+    H = W = 16384
+    f = rng.normal(0.0, 0.3, (H, W)).astype(np.float32)
+    K, delta, lam = 12, 0.1, 1.0
+    S = seg.Solver(H, W, tile_h=16, mode="compact")
+    S.f[:, :W].copy_(torch.from_numpy(f))
+    S.domain(delta=delta)
+    S.solve_pd(lam, iters=K, check_every=K)
+    torch.cuda.synchronize()
+    S.check_status()
+    inrd = np.abs(f) < np.float32(delta)
+    assert int(S.dom.counts[1].item()) == int(np.count_nonzero(inrd))
+    u = S.u[:, :W].cpu().numpy()
+    del S
+    act = np.argwhere(inrd)
+    centres = [tuple(x) for x in act[rng.choice(len(act), 10, replace=False)]]
+    centres += [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0)]
+    R = 2 * K + 4
+    worst = 0.0
+    for (i, j) in centres:
+        a, b = max(0, i - R), min(H, i + R + 1)
+        c, d = max(0, j - R), min(W, j + R + 1)
+        fc = np.ascontiguousarray(f[a:b, c:d])
+        st = orc.solve_pd(fc, orc.domain(fc, delta), lam, iters=K)
+        worst = max(worst, abs(st.u[i - a, j - c] - u[i, j]))
+    assert worst <= TOL_U

@@ -138,3 +138,34 @@ def test_volume_argument_and_capacity_errors():
     with pytest.raises(seg.SegError) as e:
         small.check_status()
     assert e.value.status == seg.SEG_ERR_CAPACITY
+
+
+@pytest.mark.slow
+def test_largest_volume_sampled(orc):
+    """A 512^3 volume (134 M voxels, 12 GB of compact state) at delta = 0.1:
+    K iterations, oracle crops around sampled voxels and two corners."""
+    D = H = W = 512
+    rng = np.random.default_rng(41)
+    f = rng.normal(0.0, 0.3, (D, H, W)).astype(np.float32)
+    K, lam, delta = 6, 1.0, 0.1
+    seg = seg_mod()
+    S = seg.VolumeSolver(D, H, W, tile_h=8)
+    S.f.copy_(S.upload(f))
+    S.domain(delta=delta)
+    S.solve(lam, iters=K, check_every=K)
+    torch.cuda.synchronize()
+    S.check_status()
+    inrd = np.abs(f) < np.float32(delta)
+    assert int(S.dom.counts[1].item()) == int(np.count_nonzero(inrd))
+    u = S.download(S.u)
+    del S
+    act = np.argwhere(inrd)
+    centres = [tuple(x) for x in act[rng.choice(len(act), 8, replace=False)]] + [(0, 0, 0), (511, 511, 511)]
+    R = 2 * K + 4
+    worst = 0.0
+    for (z0, i0, j0) in centres:
+        sl = tuple(slice(max(0, c - R), min(n, c + R + 1)) for c, n in zip((z0, i0, j0), (D, H, W)))
+        fc = np.ascontiguousarray(f[sl])
+        st = orc.solve3(fc, orc.domain(fc, delta), lam, iters=K)
+        worst = max(worst, abs(st.u[z0 - sl[0].start, i0 - sl[1].start, j0 - sl[2].start] - u[z0, i0, j0]))
+    assert worst <= TOL_U
