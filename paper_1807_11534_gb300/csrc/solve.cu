@@ -770,14 +770,18 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
 // at the start: a neighbour the block owns is its own word, a fixed (or
 // outside) one the zero word, and one another block owns a ghost word, which
 // the block refills from the global arrays (an L2 read) at the start of the
-// phase that reads it.  p of buffer b is at offset + b x (region size), so
+// phase that reads it.  The dual step reads w below x when that neighbour is
+// in RD and p2 at x + e1 - e2 when it is fixed (never both), so one offset
+// slot serves the two; likewise w right of x and p1 at x - e1 + e2.  p of buffer b is at offset + b x (region size), so
 // the ping-pong needs no branch.  A per-pixel byte holds the class of the
 // neighbours below and right (RD / fixed background / fixed foreground /
 // outside), whether other blocks read the pixel (then its p' and w' are also
 // written to the global arrays), and is otherwise the same arithmetic and
 // rounding as dual_one / primal_one.  The barrier and stopping-test protocol
 // is the one of compact_iterations, so blocks on either path interleave.
-enum { GK_DOWN = 0, GK_RIGHT, GK_DL, GK_UR, GK_UP, GK_LEFT };   // ghost kinds = table slots used
+// ghost kinds: below (w, or p2 at x + e1 - e2 when below is fixed), right (w,
+// or p1 at x - e1 + e2), above (p1'), left (p2')
+enum { GK_D = 0, GK_R, GK_UP, GK_LEFT, GK_KINDS };
 constexpr uint8_t kFlExport = 16;       // other blocks read this pixel
 constexpr uint8_t kFlDualGhost = 32;    // its dual step reads a ghost word
 constexpr uint8_t kFlPrimalGhost = 64;  // its primal step reads a ghost word
@@ -795,7 +799,7 @@ struct GhostLayout {
 template <typename T>
 struct GhostState {
     float* sm;             // the shared-memory words
-    const uint16_t* off;   // [6][n] word offsets (DOWN, RIGHT, DL, UR into buffer 0; UP, LEFT into buffer 0)
+    const uint16_t* off;   // [4][n] word offsets of the kinds D, R, UP, LEFT (p words: buffer 0)
     const uint8_t* fl;     // [n]
     const int32_t* gsrc;   // [gd + gp] compact index of each ghost's pixel
     const uint16_t* gdst;  // [gd + gp] word offset of each ghost (buffer 0 for p kinds)
@@ -809,9 +813,9 @@ struct GhostState {
 struct DualView {
     const float *p1, *p2, *w;     // own p (buffer pb) and w, by own index
     float *q1, *q2;               // own p' (the other buffer)
-    const float *n1, *n2;         // neighbour p words of buffer pb (offsets are buffer 0)
-    const float* nw;              // neighbour w words
-    const uint16_t *od, *orr, *odl, *our;   // offsets of the neighbours below, right, x+e1-e2, x-e1+e2
+    const float* sm;              // all shared words (offsets: p words of buffer 0)
+    int sh1, sh2;                 // shift of buffer pb in the P1 / P2 regions
+    const uint16_t *od, *orr;     // offsets of the kinds D and R
 };
 struct PrimalView {
     const float *q1, *q2;         // own p' (buffer pb)
@@ -824,12 +828,13 @@ template <typename T>
 __device__ __forceinline__ void dual_gh(const IterParams& P, int i, int a, uint8_t fl, const DualView& D,
                                         T* P1o, T* P2o, uint32_t seed) {
     const float p1 = D.p1[i], p2 = D.p2[i], w0 = D.w[i];
-    const float wdv = D.nw[D.od[i]], wrv = D.nw[D.orr[i]];
-    const float p2dl = D.n2[D.odl[i]], p1ur = D.n1[D.our[i]];
     const int cd = fl & 3, cr = (fl >> 2) & 3;   // 0 RD, 1 fixed Bg, 2 fixed Fg, 3 outside
+    // w below (RD) or p2 at x + e1 - e2 (below fixed; a p word of buffer pb)
+    const float xd = D.sm[D.od[i] + (cd ? D.sh2 : 0)];
+    const float xr = D.sm[D.orr[i] + (cr ? D.sh1 : 0)];
     float g1 = 0.f, g2 = 0.f;
-    if (cd != 3) g1 = (cd == 0 ? wdv : w_fixed(p1, p2dl, cd == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
-    if (cr != 3) g2 = (cr == 0 ? wrv : w_fixed(p1ur, p2, cr == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
+    if (cd != 3) g1 = (cd == 0 ? xd : w_fixed(p1, xd, cd == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
+    if (cr != 3) g2 = (cr == 0 ? xr : w_fixed(xr, p2, cr == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
     float q1, q2;
     chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
     const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
@@ -966,13 +971,11 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
             D.w = S.sm + L.w;
             D.q1 = S.sm + L.p1 + (1 - pb) * L.ns1;
             D.q2 = S.sm + L.p2 + (1 - pb) * L.ns2;
-            D.n1 = S.sm + pb * L.ns1;
-            D.n2 = S.sm + pb * L.ns2;
-            D.nw = S.sm;
-            D.od = S.off + GK_DOWN * L.n;
-            D.orr = S.off + GK_RIGHT * L.n;
-            D.odl = S.off + GK_DL * L.n;
-            D.our = S.off + GK_UR * L.n;
+            D.sm = S.sm;
+            D.sh1 = pb * L.ns1;
+            D.sh2 = pb * L.ns2;
+            D.od = S.off + GK_D * L.n;
+            D.orr = S.off + GK_R * L.n;
             if (overlap) {   // ghosts in flight while the interior pixels update
                 GhostRegs<T> R;
                 R.load(S, 0, L.gd, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
@@ -1103,31 +1106,48 @@ __device__ __forceinline__ bool compact_solve_range(
         // shared-memory-resident state if this block's pixels and its ghosts
         // fit (decided per block: both paths keep the global arrays that
         // other blocks read current and pass the same barriers)
-        __shared__ int s_cnt[8];   // ghosts per kind, then running slots
+        __shared__ int s_cnt[8];   // ghosts per kind, then running slots; ghosts per region
         if (tid < 8) s_cnt[tid] = 0;
         __syncthreads();
         const int nown = max(a1 - a0, 0);
-        // table slots in ghost-kind order
-        const int slot_of[6] = {NB_DOWN, NB_RIGHT, NB_DOWNLEFT, NB_UPRIGHT, NB_UP, NB_LEFT};
+        // the source pixel and region (0 W, 1 P1, 2 P2) of each kind's read
+        // (source < 0: nothing to read, the zero word)
+        auto kind_src = [&](int a, int k, int& reg) {
+            if (k == GK_D || k == GK_R) {
+                const int m = __ldg(nb + (k == GK_D ? NB_DOWN : NB_RIGHT) * stride + a);
+                if (m >= 0) { reg = 0; return m; }
+                reg = k == GK_D ? 2 : 1;
+                if (m == kNbOut) return -1;
+                return __ldg(nb + (k == GK_D ? NB_DOWNLEFT : NB_UPRIGHT) * stride + a);
+            }
+            reg = k == GK_UP ? 1 : 2;
+            return __ldg(nb + (k == GK_UP ? NB_UP : NB_LEFT) * stride + a);
+        };
         {
-            int c[6] = {0, 0, 0, 0, 0, 0};
+            int c[GK_KINDS] = {0, 0, 0, 0}, c_w = 0, c_p1 = 0, c_p2 = 0;
             for (int i = tid; i < nown; i += nt)
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const int m = __ldg(nb + slot_of[k] * stride + a0 + i);
-                    c[k] += (m >= 0 && (m < a0 || m >= a1)) ? 1 : 0;
+                for (int k = 0; k < GK_KINDS; ++k) {
+                    int reg;
+                    const int m = kind_src(a0 + i, k, reg);
+                    const int g = (m >= 0 && (m < a0 || m >= a1)) ? 1 : 0;
+                    c[k] += g;
+                    c_w += reg == 0 ? g : 0;
+                    c_p1 += reg == 1 ? g : 0;
+                    c_p2 += reg == 2 ? g : 0;
                 }
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
+            for (int k = 0; k < GK_KINDS; ++k)
                 if (c[k]) atomicAdd(&s_cnt[k], c[k]);
+            if (c_w) atomicAdd(&s_cnt[4], c_w);
+            if (c_p1) atomicAdd(&s_cnt[5], c_p1);
+            if (c_p2) atomicAdd(&s_cnt[6], c_p2);
         }
         __syncthreads();
         GhostLayout L{};
         L.n = nown;
-        const int g_w = s_cnt[GK_DOWN] + s_cnt[GK_RIGHT];
-        const int g_p1 = s_cnt[GK_UR] + s_cnt[GK_UP];
-        const int g_p2 = s_cnt[GK_DL] + s_cnt[GK_LEFT];
-        L.gd = s_cnt[GK_DOWN] + s_cnt[GK_RIGHT] + s_cnt[GK_DL] + s_cnt[GK_UR];
+        const int g_w = s_cnt[4], g_p1 = s_cnt[5], g_p2 = s_cnt[6];
+        L.gd = s_cnt[GK_D] + s_cnt[GK_R];
         L.gp = s_cnt[GK_UP] + s_cnt[GK_LEFT];
         L.ns1 = nown + 1 + g_p1;
         L.ns2 = nown + 1 + g_p2;
@@ -1138,7 +1158,7 @@ __device__ __forceinline__ bool compact_solve_range(
         L.v = L.w + L.nsw;
         const int words = L.v + (int)((sizeof(T) * nown + 3) / 4);
         L.off16 = (size_t)4 * words;
-        L.offfl = L.off16 + (size_t)2 * 6 * nown;
+        L.offfl = L.off16 + (size_t)2 * GK_KINDS * nown;
         L.offgs = (L.offfl + nown + 3) & ~(size_t)3;
         L.offgd = L.offgs + (size_t)4 * (L.gd + L.gp);
         // pixels whose dual / primal step reads a ghost: at most one per ghost
@@ -1161,10 +1181,10 @@ __device__ __forceinline__ bool compact_solve_range(
                     primal_one(P, a, O, P1a, P2a, U, Up, Wc, true, false, false, false, 0u, d0, d1);
                 if (!grid_sync(h, nblocks, gen)) return false;
             }
-            // ghost slots: dual kinds first (down, right, dl, ur), then primal (up, left)
+            // ghost slots: dual kinds first (D, R), then primal (up, left)
             if (tid == 0) {
                 int acc = 0;
-                for (int k = 0; k < 6; ++k) { const int c = s_cnt[k]; s_cnt[k] = acc; acc += c; }
+                for (int k = 0; k < GK_KINDS; ++k) { const int c = s_cnt[k]; s_cnt[k] = acc; acc += c; }
             }
             // zero words
             if (tid == 0) {
@@ -1182,17 +1202,24 @@ __device__ __forceinline__ bool compact_solve_range(
                 const int a = a0 + i;
                 uint8_t f = 0;
                 bool exported = false, gdual = false, gprimal = false;
+                // other blocks read this pixel if one of its neighbours is theirs
+                {
+                    const int sl[6] = {NB_UP, NB_LEFT, NB_DOWN, NB_RIGHT, NB_DOWNLEFT, NB_UPRIGHT};
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const int m = __ldg(nb + slot_of[k] * stride + a);
-                    // region of this kind: W (down, right), P1 (ur, up), P2 (dl, left)
-                    const int reg = (k == GK_DOWN || k == GK_RIGHT) ? 0 : (k == GK_UR || k == GK_UP) ? 1 : 2;
+                    for (int k = 0; k < 6; ++k) {
+                        const int m = __ldg(nb + sl[k] * stride + a);
+                        if (m >= 0 && (m < a0 || m >= a1)) exported = true;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < GK_KINDS; ++k) {
+                    int reg;
+                    const int m = kind_src(a, k, reg);
                     const int base = reg == 0 ? L.w : reg == 1 ? L.p1 : L.p2;
                     int o;
                     if (m >= a0 && m < a1) {
                         o = base + (m - a0);
                     } else if (m >= 0) {
-                        exported = true;
                         if (k < GK_UP) gdual = true; else gprimal = true;
                         const int slot = atomicAdd(&s_cnt[k], 1);          // position in the ghost lists
                         const int gi = atomicAdd(&s_reg[reg], 1);          // word in the region's ghost area
@@ -1203,8 +1230,11 @@ __device__ __forceinline__ bool compact_solve_range(
                         o = base + nown;                                   // the zero word
                     }
                     off[k * nown + i] = (uint16_t)o;
-                    if (k == GK_DOWN) f |= (uint8_t)(m >= 0 ? 0 : m == kNbBg ? 1 : m == kNbFg ? 2 : 3);
-                    if (k == GK_RIGHT) f |= (uint8_t)((m >= 0 ? 0 : m == kNbBg ? 1 : m == kNbFg ? 2 : 3) << 2);
+                }
+                {
+                    const int md = __ldg(nb + NB_DOWN * stride + a), mr = __ldg(nb + NB_RIGHT * stride + a);
+                    f |= (uint8_t)(md >= 0 ? 0 : md == kNbBg ? 1 : md == kNbFg ? 2 : 3);
+                    f |= (uint8_t)((mr >= 0 ? 0 : mr == kNbBg ? 1 : mr == kNbFg ? 2 : 3) << 2);
                 }
                 flg[i] = (uint8_t)(f | (exported ? kFlExport : 0) | (gdual ? kFlDualGhost : 0) |
                                    (gprimal ? kFlPrimalGhost : 0));
