@@ -70,6 +70,8 @@ struct WsHeader {
     int tb_ticket[4];
     int tb_buf;
     int n_smem_blocks;   // compact solver: blocks that held their state in shared memory
+    int n_h1_blocks;     // compact solver: blocks that ran one grid barrier per iteration
+    unsigned h1_vote;    // compact solver: blocks whose one-barrier state did not fit (a vote)
     // grid barrier of the persistent solvers: monotonic arrival counter, on
     // its own cache line
     alignas(128) unsigned bar_count;

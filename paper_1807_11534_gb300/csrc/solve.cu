@@ -809,6 +809,28 @@ struct GhostState {
     __device__ __forceinline__ T* v() const { return reinterpret_cast<T*>(sm + L.v); }
 };
 
+// The source pixel and region (0 W, 1 P1, 2 P2) of the ghost-path read of
+// kind k at compact pixel a; a source < 0 reads the zero word.
+__device__ __forceinline__ int gk_src(const int32_t* __restrict__ nb, int64_t stride, int a, int k, int& reg) {
+    if (k == GK_D || k == GK_R) {
+        const int m = __ldg(nb + (k == GK_D ? NB_DOWN : NB_RIGHT) * stride + a);
+        if (m >= 0) { reg = 0; return m; }
+        reg = k == GK_D ? 2 : 1;
+        if (m == kNbOut) return -1;
+        return __ldg(nb + (k == GK_D ? NB_DOWNLEFT : NB_UPRIGHT) * stride + a);
+    }
+    reg = k == GK_UP ? 1 : 2;
+    return __ldg(nb + (k == GK_UP ? NB_UP : NB_LEFT) * stride + a);
+}
+
+// The class byte of the neighbours below and right of pixel a (bits 0-1 and
+// 2-3: 0 RD, 1 fixed Bg, 2 fixed Fg, 3 outside).
+__device__ __forceinline__ uint8_t gk_codes(const int32_t* __restrict__ nb, int64_t stride, int a) {
+    const int md = __ldg(nb + NB_DOWN * stride + a), mr = __ldg(nb + NB_RIGHT * stride + a);
+    return (uint8_t)((md >= 0 ? 0 : md == kNbBg ? 1 : md == kNbFg ? 2 : 3) |
+                     ((mr >= 0 ? 0 : mr == kNbBg ? 1 : mr == kNbFg ? 2 : 3) << 2));
+}
+
 // Per-phase views of the shared-memory state (pointers fixed for a phase).
 struct DualView {
     const float *p1, *p2, *w;     // own p (buffer pb) and w, by own index
@@ -1073,6 +1095,402 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
     return true;
 }
 
+// ---- one grid barrier per iteration
+//
+// The two-phase iteration needs its second grid barrier only because the
+// primal step of x reads p' at x - e1 and x - e2, which another block may
+// compute.  When every block's state fits with it, a block also runs the dual
+// step of its ring -- the pixels other blocks own directly above or left of
+// its own -- from the same inputs and with the same arithmetic and rounding
+// as their owners, so its primal step follows its dual step after a block
+// barrier, and one grid barrier ends the iteration.  What the dual steps read
+// that the block does not compute (w below / right, or p at the diagonal
+// neighbour, of its pixels and of its ring, and w of the ring) are ghost
+// words refilled at the start of each iteration from the previous iterate,
+// whose p and w the global arrays hold in ping-pong buffers, written for the
+// pixels some other block reads (marked once, before the iterations).  p' of
+// the ring stays in the block's own words, so the ring's p is read once.
+// The iterates are bit-identical to the two-barrier ones.
+struct H1Layout {
+    int n, r, nE;          // own pixels, ring pixels, n + r
+    int ns1, ns2, nsw;     // region sizes (words) of P1, P2 (per buffer) and W: [own | ring | zero | ghosts]
+    int p1, p2, w, v;      // word offsets of the regions
+    int ng, nbd;           // ghost words refilled per iteration; own pixels whose dual step reads one
+    size_t off16, offfl, offr1, offgs, offgd, offbd, bytes;   // byte offsets of the tables
+};
+
+template <typename T>
+struct H1State {
+    float* sm;             // the shared-memory words
+    const uint16_t* off;   // [D: nE][R: nE][UP: n][LEFT: n] word offsets (p words: buffer 0)
+    const uint8_t* fl;     // [nE]
+    const int32_t* r1;     // [r] compact index of each ring pixel
+    const int32_t* gsrc;   // [ng] compact index of each ghost's pixel
+    const uint16_t* gdst;  // [ng] word offset of each ghost (p words: buffer 0)
+    const uint16_t* bd;    // [nbd] own pixels whose dual step reads a ghost
+    H1Layout L;
+    __device__ __forceinline__ T* v() const { return reinterpret_cast<T*>(sm + L.v); }
+};
+
+// The iterations; returns false when a barrier timed out, else the final
+// iterate's count in *lf (its p is in buffer lf & 1).
+template <typename T, int NT, int UNROLL>
+__device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const H1State<T>& S, int a0, int a1,
+                                                      int iters, int check_every, double tol, int64_t stride,
+                                                      T* P1a, T* P1b, T* P2a, T* P2b, const float* F,
+                                                      float* U, float* Up, float* Wc, float* Wc2,
+                                                      double* partials, WsHeader* h, float* ckpt, int ckpt_every,
+                                                      double* s_red, unsigned& gen, int* lf) {
+    const unsigned nblocks = gridDim.x;
+    const int tid = threadIdx.x, nt = NT;
+    const H1Layout& L = S.L;
+    int pb = 0, chk = 0;
+    auto each = [&](auto&& op) {
+        int a = a0 + tid;
+        for (; a + (UNROLL - 1) * nt < a1; a += UNROLL * nt) {
+#pragma unroll
+            for (int k = 0; k < UNROLL; ++k) op(a + k * nt);
+        }
+        for (; a < a1; a += nt) op(a);
+    };
+    auto save = [&](int m) {
+        float* c = ckpt + (int64_t)m * 3 * stride;
+        const T* V = S.v();
+        for (int a = a0 + tid; a < a1; a += nt) {
+            const int i = a - a0;
+            c[a] = S.sm[L.p1 + pb * L.ns1 + i];
+            c[stride + a] = S.sm[L.p2 + pb * L.ns2 + i];
+            c[2 * stride + a] = to_f(V[i]) + Store<T>::vbias;
+        }
+    };
+    if (ckpt) save(0);
+    const int C = check_every;
+    *lf = iters;
+    for (int it = 0; it < iters; ++it) {
+        const int l = it + 1;
+        const float* Wi = (it & 1) ? Wc2 : Wc;   // w of iterate it
+        float* Wo = (it & 1) ? Wc : Wc2;         // w of iterate l (pixels other blocks read)
+        {
+            const uint32_t seed = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
+            T* o1 = pb ? P1a : P1b;
+            T* o2 = pb ? P2a : P2b;
+            const T* i1 = pb ? P1b : P1a;
+            const T* i2 = pb ? P2b : P2a;
+            DualView D;
+            D.p1 = S.sm + L.p1 + pb * L.ns1;
+            D.p2 = S.sm + L.p2 + pb * L.ns2;
+            D.w = S.sm + L.w;
+            D.q1 = S.sm + L.p1 + (1 - pb) * L.ns1;
+            D.q2 = S.sm + L.p2 + (1 - pb) * L.ns2;
+            D.sm = S.sm;
+            D.sh1 = pb * L.ns1;
+            D.sh2 = pb * L.ns2;
+            D.od = S.off;
+            D.orr = S.off + L.nE;
+            // ghosts in flight (kGhostRegs per thread) while the pixels that
+            // read none update
+            float x[kGhostRegs];
+#pragma unroll
+            for (int j = 0; j < kGhostRegs; ++j) {
+                const int g = tid + j * nt;
+                x[j] = 0.f;
+                if (g < L.ng) {
+                    const int src = S.gsrc[g], dst = S.gdst[g];
+                    x[j] = dst >= L.w ? ldw(Wi + src) : dst >= L.p2 ? Store<T>::ldc(i2, src) : Store<T>::ldc(i1, src);
+                }
+            }
+            each([&](int a) {
+                const uint8_t f = S.fl[a - a0];
+                if (!(f & kFlDualGhost)) dual_gh(P, a - a0, a, f, D, o1, o2, seed);
+            });
+#pragma unroll
+            for (int j = 0; j < kGhostRegs; ++j) {
+                const int g = tid + j * nt;
+                if (g < L.ng) {
+                    const int dst = S.gdst[g];
+                    S.sm[dst >= L.w ? dst : dst >= L.p2 ? dst + D.sh2 : dst + D.sh1] = x[j];
+                }
+            }
+            __syncthreads();
+            // own pixels that read ghosts, then the ring
+            for (int e = tid; e < L.nbd + L.r; e += nt) {
+                const bool own = e < L.nbd;
+                const int i = own ? S.bd[e] : L.n + (e - L.nbd);
+                const int a = own ? a0 + i : S.r1[e - L.nbd];
+                dual_gh(P, i, a, S.fl[i], D, o1, o2, seed);
+            }
+            pb ^= 1;
+            __syncthreads();
+        }
+        const bool check = (l % C == 0) || l == iters;
+        const bool write_u = check;   // the output u and the stopped iterate
+        const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
+        const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
+        float du2 = 0.f, dv2 = 0.f;
+        PrimalView Q;
+        Q.q1 = S.sm + L.p1 + pb * L.ns1;
+        Q.q2 = S.sm + L.p2 + pb * L.ns2;
+        Q.n1 = S.sm + pb * L.ns1;
+        Q.n2 = S.sm + pb * L.ns2;
+        Q.w = S.sm + L.w;
+        Q.ou = S.off + 2 * L.nE;
+        Q.ol = S.off + 2 * L.nE + L.n;
+        T* Vs = S.v();
+        each([&](int a) {
+            primal_gh(P, a - a0, a, S.fl[a - a0], Q, Vs, F, U, Up, Wo, check, write_u, write_prev, seed, du2, dv2);
+        });
+        if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);   // own pixels, same threads
+        // stopping-test partials, double-buffered by check so that a fast
+        // block cannot overwrite those a slow block is still summing
+        double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
+        if (check) {
+            float x = du2, y = dv2;
+            block_sum2f<NT>(x, y, reinterpret_cast<float*>(s_red));
+            if (tid == 0) {
+                part[2 * blockIdx.x] = x;
+                part[2 * blockIdx.x + 1] = y;
+            }
+        }
+        if (!grid_sync(h, nblocks, gen)) return false;
+        if (check) {
+            // Section 4 stopping test: with a tolerance every block sums the
+            // block partials in the same fixed order, so all stop after the
+            // same iteration (squared norms against tol^2); block 0 records
+            // the norms
+            if (tol > 0.0 || blockIdx.x == 0) {
+                if (tid < 32) {
+                    double sx, sy;
+                    sum_partials_warp0(part, (int)nblocks, sx, sy);
+                    if (tid == 0) {
+                        const bool stop = tol > 0.0 && fmax(sx, sy) <= tol * tol;
+                        s_red[0] = stop ? 1.0 : 0.0;
+                        if (blockIdx.x == 0) {
+                            h->du2 = sx;
+                            h->dv2 = sy;
+                            h->last_check = l;
+                            if (stop) {
+                                h->iters_done = l;
+                                h->done = 1;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                const bool stop = s_red[0] != 0.0;
+                __syncthreads();
+                if (stop) {
+                    *lf = l;
+                    return true;
+                }
+            }
+            ++chk;
+        }
+    }
+    return true;
+}
+
+// Sets up and runs the one-barrier iteration when every block's state fits
+// (a grid-wide vote; `votes`, the vote count seen so far, runs on across the
+// waves of a batch).  Returns 1 when it ran the solve, 0 when some block does
+// not fit (nothing changed; the caller takes the two-barrier paths), -1 when
+// a barrier timed out.
+template <typename T, int NT, int UNROLL>
+__device__ __forceinline__ int compact_solve_h1(
+    const IterParams& P, int iters, int check_every, double tol, int a0, int a1,
+    const int32_t* __restrict__ nb, int64_t stride, T* P1a, T* P1b, T* P2a, T* P2b, T* V,
+    const float* __restrict__ F, float* U, float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h,
+    float* ckpt, int ckpt_every, unsigned& gen, unsigned& votes, double* s_red, unsigned char* c_smem) {
+    const unsigned nblocks = gridDim.x;
+    const int tid = threadIdx.x, nt = NT;
+    const int nown = max(a1 - a0, 0);
+    auto other = [&](int m) { return m >= 0 && (m < a0 || m >= a1); };
+    // counts: [0] ring pixels, [1..3] ghost words of the W / P1 / P2 areas,
+    // [4] ghosts read by own pixels' dual steps; then running slots
+    __shared__ int s_h[8];
+    if (tid < 8) s_h[tid] = 0;
+    __syncthreads();
+    {
+        int r = 0, gw = 0, g1 = 0, g2 = 0, go = 0;
+        for (int i = tid; i < nown; i += nt) {
+            const int a = a0 + i;
+#pragma unroll
+            for (int k = GK_D; k <= GK_R; ++k) {
+                int reg;
+                const int m = gk_src(nb, stride, a, k, reg);
+                if (other(m)) {
+                    ++go;
+                    gw += reg == 0; g1 += reg == 1; g2 += reg == 2;
+                }
+            }
+#pragma unroll
+            for (int k = GK_UP; k <= GK_LEFT; ++k) {
+                int reg;
+                const int y = gk_src(nb, stride, a, k, reg);
+                if (!other(y)) continue;
+                ++r;
+#pragma unroll
+                for (int k2 = GK_D; k2 <= GK_R; ++k2) {
+                    int reg2;
+                    const int m = gk_src(nb, stride, y, k2, reg2);
+                    if (other(m)) { gw += reg2 == 0; g1 += reg2 == 1; g2 += reg2 == 2; }
+                }
+            }
+        }
+        if (r) atomicAdd(&s_h[0], r);
+        if (gw) atomicAdd(&s_h[1], gw);
+        if (g1) atomicAdd(&s_h[2], g1);
+        if (g2) atomicAdd(&s_h[3], g2);
+        if (go) atomicAdd(&s_h[4], go);
+    }
+    __syncthreads();
+    H1Layout L{};
+    L.n = nown;
+    L.r = s_h[0];
+    L.nE = nown + L.r;
+    const int gwx = s_h[1], g1x = s_h[2], g2x = s_h[3];
+    L.ng = gwx + g1x + g2x + L.r;   // plus w of every ring pixel
+    L.ns1 = L.nE + 1 + g1x;
+    L.ns2 = L.nE + 1 + g2x;
+    L.nsw = L.nE + 1 + gwx;
+    L.p1 = 0;
+    L.p2 = 2 * L.ns1;
+    L.w = L.p2 + 2 * L.ns2;
+    L.v = L.w + L.nsw;
+    const int words = L.v + (int)((sizeof(T) * nown + 3) / 4);
+    L.off16 = (size_t)4 * words;
+    L.offfl = L.off16 + (size_t)2 * (2 * L.nE + 2 * nown);
+    L.offr1 = (L.offfl + L.nE + 3) & ~(size_t)3;
+    L.offgs = L.offr1 + (size_t)4 * L.r;
+    L.offgd = L.offgs + (size_t)4 * L.ng;
+    L.offbd = L.offgd + (size_t)2 * L.ng;
+    L.bytes = L.offbd + (size_t)2 * min(nown, s_h[4]);
+    const bool fits = L.bytes <= compact_smem(NT) && words < 65536 && L.ng <= kGhostRegs * NT;
+    // the vote: every block adds 1 when it does not fit
+    __shared__ unsigned s_vote;
+    if (tid == 0 && !fits) atomicAdd(&h->h1_vote, 1u);
+    if (!grid_sync(h, nblocks, gen)) return -1;
+    if (tid == 0) s_vote = *(volatile unsigned*)&h->h1_vote;
+    __syncthreads();
+    const bool all_fit = s_vote == votes;
+    votes = s_vote;
+    __syncthreads();   // s_vote and s_h are read by every thread before they change
+    if (!all_fit) return 0;
+
+    // export marks (1 = another block reads the pixel), cleared before any block marks
+    unsigned* mark = reinterpret_cast<unsigned*>(Wc2);
+    for (int i = tid; i < nown; i += nt) mark[a0 + i] = 0u;
+    float* sm = reinterpret_cast<float*>(c_smem);
+    uint16_t* off = reinterpret_cast<uint16_t*>(c_smem + L.off16);
+    uint8_t* flg = reinterpret_cast<uint8_t*>(c_smem + L.offfl);
+    int32_t* r1 = reinterpret_cast<int32_t*>(c_smem + L.offr1);
+    int32_t* gsrc = reinterpret_cast<int32_t*>(c_smem + L.offgs);
+    uint16_t* gdst = reinterpret_cast<uint16_t*>(c_smem + L.offgd);
+    uint16_t* lbd = reinterpret_cast<uint16_t*>(c_smem + L.offbd);
+    if (tid < 8) s_h[tid] = 0;   // [0] ring slots, [1..3] area words, [4] ghost slots
+    if (tid == 0) {
+        sm[L.p1 + L.nE] = 0.f; sm[L.p1 + L.ns1 + L.nE] = 0.f;
+        sm[L.p2 + L.nE] = 0.f; sm[L.p2 + L.ns2 + L.nE] = 0.f;
+        sm[L.w + L.nE] = 0.f;
+    }
+    __syncthreads();
+    // the offset of a D / R read of pixel a (a ghost word when another block owns its source)
+    auto dr_off = [&](int a, int k, bool& ghost) {
+        int reg;
+        const int m = gk_src(nb, stride, a, k, reg);
+        const int base = reg == 0 ? L.w : reg == 1 ? L.p1 : L.p2;
+        ghost = false;
+        if (m >= a0 && m < a1) return base + (m - a0);
+        if (m < 0) return base + L.nE;   // the zero word
+        ghost = true;
+        const int gi = atomicAdd(&s_h[1 + reg], 1);
+        const int o = base + L.nE + 1 + gi;
+        const int slot = atomicAdd(&s_h[4], 1);
+        gsrc[slot] = m;
+        gdst[slot] = (uint16_t)o;
+        return o;
+    };
+    T* Vs = reinterpret_cast<T*>(sm + L.v);
+    for (int i = tid; i < nown; i += nt) {
+        const int a = a0 + i;
+        bool gd = false, g;
+        off[i] = (uint16_t)dr_off(a, GK_D, g);
+        gd |= g;
+        off[L.nE + i] = (uint16_t)dr_off(a, GK_R, g);
+        gd |= g;
+        flg[i] = (uint8_t)(gk_codes(nb, stride, a) | (gd ? kFlDualGhost : 0));
+#pragma unroll
+        for (int k = GK_UP; k <= GK_LEFT; ++k) {
+            int reg;
+            const int y = gk_src(nb, stride, a, k, reg);
+            const int base = k == GK_UP ? L.p1 : L.p2;
+            int o;
+            if (y >= a0 && y < a1) {
+                o = base + (y - a0);
+            } else if (y < 0) {
+                o = base + L.nE;
+            } else {   // a ring pixel: its own words, p read once, w a ghost
+                const int j = atomicAdd(&s_h[0], 1);
+                const int e = nown + j;
+                o = base + e;
+                r1[j] = y;
+                off[e] = (uint16_t)dr_off(y, GK_D, g);
+                off[L.nE + e] = (uint16_t)dr_off(y, GK_R, g);
+                flg[e] = gk_codes(nb, stride, y);
+                sm[L.p1 + e] = Store<T>::ldc(P1a, y);
+                sm[L.p2 + e] = Store<T>::ldc(P2a, y);
+                const int slot = atomicAdd(&s_h[4], 1);
+                gsrc[slot] = y;
+                gdst[slot] = (uint16_t)(L.w + e);
+            }
+            off[2 * L.nE + (k - GK_UP) * nown + i] = (uint16_t)o;
+        }
+        sm[L.p1 + i] = Store<T>::ldc(P1a, a);
+        sm[L.p2 + i] = Store<T>::ldc(P2a, a);
+        sm[L.w + i] = ldw(Wc + a);
+        Vs[i] = V[a];
+    }
+    if (!grid_sync(h, nblocks, gen)) return -1;   // every mark cleared, every table built
+    for (int g = tid; g < L.ng; g += nt) mark[gsrc[g]] = 1u;
+    // stable list of the own pixels whose dual step reads a ghost
+    __shared__ int s_nbd;
+    if (tid < 32) {
+        int cd = 0;
+        for (int b = 0; b < nown; b += 32) {
+            const int i = b + tid;
+            const unsigned f = i < nown ? flg[i] : 0u;
+            const unsigned md = __ballot_sync(0xffffffffu, f & kFlDualGhost);
+            if (f & kFlDualGhost) lbd[cd + __popc(md & lanemask_lt(tid))] = (uint16_t)i;
+            cd += __popc(md);
+        }
+        if (tid == 0) {
+            s_nbd = cd;
+            atomicAdd(&h->n_smem_blocks, 1);
+            atomicAdd(&h->n_h1_blocks, 1);
+        }
+    }
+    if (!grid_sync(h, nblocks, gen)) return -1;   // every mark set
+    for (int i = tid; i < nown; i += nt)
+        if (__ldcg(mark + a0 + i)) flg[i] |= kFlExport;
+    __syncthreads();
+    L.nbd = s_nbd;
+    const H1State<T> S{sm, off, flg, r1, gsrc, gdst, lbd, L};
+    int lf = iters;
+    if (!compact_iterations_h1<T, NT, UNROLL>(P, S, a0, a1, iters, check_every, tol, stride, P1a, P1b, P2a, P2b,
+                                              F, U, Up, Wc, Wc2, partials, h, ckpt, ckpt_every, s_red, gen, &lf))
+        return -1;
+    __syncthreads();
+    // the final iterate: v, and p of every own pixel
+    const int fb = lf & 1;
+    T* G1 = fb ? P1b : P1a;
+    T* G2 = fb ? P2b : P2a;
+    for (int i = tid; i < nown; i += nt) {
+        V[a0 + i] = Vs[i];
+        Store<T>::st(G1, a0 + i, sm[L.p1 + fb * L.ns1 + i]);
+        Store<T>::st(G2, a0 + i, sm[L.p2 + fb * L.ns2 + i]);
+    }
+    return 1;
+}
+
 // Which of the two persistent compact kernels runs a solve (both are
 // launched; the other returns at once).  The shared-memory kernel (one
 // block per SM, grid1 blocks) unless even its table rows would not fit in
@@ -1093,7 +1511,7 @@ __device__ __forceinline__ bool compact_solve_range(
     const IterParams& P, int iters, int n_inner, int check_every, double tol, int warm, int w0, int n,
     const int32_t* __restrict__ nb, int64_t stride, T* P1a, T* P1b, T* P2a, T* P2b, T* V,
     const float* __restrict__ F, float* U, float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h,
-    float* ckpt, int ckpt_every, unsigned& gen, double* s_red, unsigned char* c_smem) {
+    float* ckpt, int ckpt_every, unsigned& gen, unsigned& votes, double* s_red, unsigned char* c_smem) {
     const unsigned nblocks = gridDim.x;
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = w0 + (int)blockIdx.x * per, a1 = min(w0 + n, a0 + per);
@@ -1103,6 +1521,19 @@ __device__ __forceinline__ bool compact_solve_range(
     const int fuse = n_inner == 1 && per <= kFusePerThread * NT;
     const int rows = fuse ? NB_COUNT : NB_UUR;
     if (n_inner == 1 && !fuse) {
+        // w of the warm-start iterate first, from the global arrays (every
+        // path below then starts from it)
+        if (warm) {
+            float d0 = 0.f, d1 = 0.f;
+            const Own<T, false> O{nb, stride, V, F, 0};
+            for (int a = a0 + tid; a < a1; a += nt)
+                primal_one(P, a, O, P1a, P2a, U, Up, Wc, true, false, false, false, 0u, d0, d1);
+            warm = 0;   // the vote's barrier below orders these writes before any read
+        }
+        const int h1 = compact_solve_h1<T, NT, UNROLL>(P, iters, check_every, tol, a0, a1, nb, stride, P1a, P1b,
+                                                      P2a, P2b, V, F, U, Up, Wc, Wc2, partials, h, ckpt,
+                                                      ckpt_every, gen, votes, s_red, c_smem);
+        if (h1 != 0) return h1 > 0;
         // shared-memory-resident state if this block's pixels and its ghosts
         // fit (decided per block: both paths keep the global arrays that
         // other blocks read current and pass the same barriers)
@@ -1110,26 +1541,13 @@ __device__ __forceinline__ bool compact_solve_range(
         if (tid < 8) s_cnt[tid] = 0;
         __syncthreads();
         const int nown = max(a1 - a0, 0);
-        // the source pixel and region (0 W, 1 P1, 2 P2) of each kind's read
-        // (source < 0: nothing to read, the zero word)
-        auto kind_src = [&](int a, int k, int& reg) {
-            if (k == GK_D || k == GK_R) {
-                const int m = __ldg(nb + (k == GK_D ? NB_DOWN : NB_RIGHT) * stride + a);
-                if (m >= 0) { reg = 0; return m; }
-                reg = k == GK_D ? 2 : 1;
-                if (m == kNbOut) return -1;
-                return __ldg(nb + (k == GK_D ? NB_DOWNLEFT : NB_UPRIGHT) * stride + a);
-            }
-            reg = k == GK_UP ? 1 : 2;
-            return __ldg(nb + (k == GK_UP ? NB_UP : NB_LEFT) * stride + a);
-        };
         {
             int c[GK_KINDS] = {0, 0, 0, 0}, c_w = 0, c_p1 = 0, c_p2 = 0;
             for (int i = tid; i < nown; i += nt)
 #pragma unroll
                 for (int k = 0; k < GK_KINDS; ++k) {
                     int reg;
-                    const int m = kind_src(a0 + i, k, reg);
+                    const int m = gk_src(nb, stride, a0 + i, k, reg);
                     const int g = (m >= 0 && (m < a0 || m >= a1)) ? 1 : 0;
                     c[k] += g;
                     c_w += reg == 0 ? g : 0;
@@ -1214,7 +1632,7 @@ __device__ __forceinline__ bool compact_solve_range(
 #pragma unroll
                 for (int k = 0; k < GK_KINDS; ++k) {
                     int reg;
-                    const int m = kind_src(a, k, reg);
+                    const int m = gk_src(nb, stride, a, k, reg);
                     const int base = reg == 0 ? L.w : reg == 1 ? L.p1 : L.p2;
                     int o;
                     if (m >= a0 && m < a1) {
@@ -1231,11 +1649,7 @@ __device__ __forceinline__ bool compact_solve_range(
                     }
                     off[k * nown + i] = (uint16_t)o;
                 }
-                {
-                    const int md = __ldg(nb + NB_DOWN * stride + a), mr = __ldg(nb + NB_RIGHT * stride + a);
-                    f |= (uint8_t)(md >= 0 ? 0 : md == kNbBg ? 1 : md == kNbFg ? 2 : 3);
-                    f |= (uint8_t)((mr >= 0 ? 0 : mr == kNbBg ? 1 : mr == kNbFg ? 2 : 3) << 2);
-                }
+                f |= gk_codes(nb, stride, a);
                 flg[i] = (uint8_t)(f | (exported ? kFlExport : 0) | (gdual ? kFlDualGhost : 0) |
                                    (gprimal ? kFlPrimalGhost : 0));
                 sm[L.p1 + i] = Store<T>::ldc(P1a, a);
@@ -1336,12 +1750,12 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
     // set before the launch (capacity overflow): the same for every block
     if (*(volatile int*)&h->done) return;
     const int n = counts[1];
-    unsigned gen = 0u;
+    unsigned gen = 0u, votes = 0u;
     if (!WAVES) {
         if (compact_wide<T>(n, grid1)) return;
         compact_solve_range<T, NT, UNROLL>(P, iters, n_inner, check_every, tol, warm, 0, n, nb, stride, P1a, P1b,
                                            P2a, P2b, V, F, U, Up, Wc, Wc2, partials, h, ckpt, ckpt_every, gen,
-                                           s_red, c_smem);
+                                           votes, s_red, c_smem);
         return;
     }
     const int cap = (int)gridDim.x * kWavePerBlock;
@@ -1354,7 +1768,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
         if (wn == 0) continue;
         if (!compact_solve_range<T, NT, UNROLL>(P, iters, n_inner, check_every, tol, warm, w0, wn, nb, stride,
                                                 P1a, P1b, P2a, P2b, V, F, U, Up, Wc, Wc2, partials, h, ckpt,
-                                                ckpt_every, gen, s_red, c_smem))
+                                                ckpt_every, gen, votes, s_red, c_smem))
             return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             su += h->du2;
@@ -1439,6 +1853,8 @@ __global__ void k_solve_begin(WsHeader* h) {
     for (int k = 0; k < 4; ++k) h->tb_ticket[k] = 0;
     h->tb_buf = 0;
     h->n_smem_blocks = 0;
+    h->n_h1_blocks = 0;
+    h->h1_vote = 0u;
 }
 
 // Section 4 stopping test after iteration l: sums the n partial pairs in a
@@ -1478,7 +1894,7 @@ __global__ void k_solve_end(const WsHeader* __restrict__ h, const int32_t* __res
     stats[4] = counts[0];
     stats[5] = h->last_check;
     stats[6] = h->n_smem_blocks;
-    stats[7] = 0.0;
+    stats[7] = h->n_h1_blocks;
 }
 
 // ================================================================== host
