@@ -220,7 +220,8 @@ seg_status seg_box_mean(const float* f, int H, int W, int ld, int radius, float*
  *                 ||du||, [2] last ||dv|| (from the last check), [3] n_active,
  *                 [4] n_tiles, [5] iteration of the last check, [6] compact
  *                 mode: blocks of the persistent solver that kept their
- *                 pixels' state in shared memory (diagnostic).
+ *                 pixels' state in shared memory, [7] compact mode: blocks
+ *                 that ran one grid barrier per iteration (diagnostics).
  * Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA on the host; CAPACITY (compact
  * state too small) in the status word. */
 seg_status seg_solve(const float* f, int H, int W, int ld,
