@@ -403,6 +403,15 @@ __device__ __forceinline__ float w_fixed(float p_in_1, float p_in_2, int code, f
     return -(p_in_1 + p_in_2) - (code == kNbFg ? inv_theta : 0.f);
 }
 
+// One component of g = grad w at x toward the neighbour with code n: wn is w
+// there when it is in RD, pa and pb the p components that flow into it when
+// it is fixed, 0 across the image border.  Selects, not branches (the same
+// values as the branching form).
+__device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, float w0, float inv_theta) {
+    const float w = n >= 0 ? wn : w_fixed(pa, pb, n, inv_theta);
+    return n == kNbOut ? 0.f : w - w0;
+}
+
 // ------------------------------------------------ persistent compact solver
 //
 // All iterations of a compact solve run in one cooperative launch: every
@@ -471,9 +480,8 @@ __device__ __forceinline__ void dual_one(const IterParams& P, int a, const Own<T
     const float wr = n_right >= 0 ? ldw(Wc + n_right) : 0.f;
     const float p2dl = nb_ld(P2i, n_dl);
     const float p1ur = nb_ld(P1i, n_ur);
-    float g1 = 0.f, g2 = 0.f;
-    if (n_down != kNbOut) g1 = (n_down >= 0 ? wd : w_fixed(p1, p2dl, n_down, P.inv_theta)) - w0;
-    if (n_right != kNbOut) g2 = (n_right >= 0 ? wr : w_fixed(p1ur, p2, n_right, P.inv_theta)) - w0;
+    const float g1 = g_comp(n_down, wd, p1, p2dl, w0, P.inv_theta);
+    const float g2 = g_comp(n_right, wr, p1ur, p2, w0, P.inv_theta);
     float q1, q2;
     chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
     const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
@@ -546,9 +554,8 @@ __device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<
     const float wdl = n_dl >= 0 ? ldw(Wi + n_dl) : 0.f;
     const float p2lld = nb_ld(P2i, n_lld);
     // p'(x)
-    float g1 = 0.f, g2 = 0.f;
-    if (n_down != kNbOut) g1 = (n_down >= 0 ? wd : w_fixed(p1, p2dl, n_down, P.inv_theta)) - w0;
-    if (n_right != kNbOut) g2 = (n_right >= 0 ? wr : w_fixed(p1ur, p2, n_right, P.inv_theta)) - w0;
+    const float g1 = g_comp(n_down, wd, p1, p2dl, w0, P.inv_theta);
+    const float g2 = g_comp(n_right, wr, p1ur, p2, w0, P.inv_theta);
     float q1, q2;
     chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
     const uint32_t rnd = mix32((uint32_t)a * 3u + seed_d);
@@ -557,8 +564,7 @@ __device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<
     // p1'(x - e1)
     float q1u = 0.f;
     if (n_up >= 0) {
-        float gu2 = 0.f;
-        if (n_ur != kNbOut) gu2 = (n_ur >= 0 ? wur : w_fixed(p1uur, p2U, n_ur, P.inv_theta)) - wU;
+        const float gu2 = g_comp(n_ur, wur, p1uur, p2U, wU, P.inv_theta);
         float b1, b2;
         chambolle_update(p1U, p2U, w0 - wU, gu2, P.tau, b1, b2);
         q1u = Store<T>::sr(b1, mix32((uint32_t)n_up * 3u + seed_d));
@@ -566,8 +572,7 @@ __device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<
     // p2'(x - e2)
     float q2l = 0.f;
     if (n_left >= 0) {
-        float gl1 = 0.f;
-        if (n_dl != kNbOut) gl1 = (n_dl >= 0 ? wdl : w_fixed(p1L, p2lld, n_dl, P.inv_theta)) - wL;
+        const float gl1 = g_comp(n_dl, wdl, p1L, p2lld, wL, P.inv_theta);
         float b1, b2;
         chambolle_update(p1L, p2L, gl1, w0 - wL, P.tau, b1, b2);
         q2l = Store<T>::sr(b2, mix32(mix32((uint32_t)n_left * 3u + seed_d) ^ 0x9e3779b9u));
@@ -654,10 +659,16 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
             const float* wi = wb ? Wc2 : Wc;
             float* wo = wb ? Wc : Wc2;
             float du2 = 0.f, dv2 = 0.f;
-            each1([&](int a) {
-                fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, Up, check, write_u, write_prev, seed_d, seed_p,
-                          du2, dv2);
-            });
+            if (!check && !write_prev)
+                each1([&](int a) {
+                    fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, Up, false, false, false, seed_d, seed_p, du2,
+                              dv2);
+                });
+            else
+                each1([&](int a) {
+                    fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, Up, check, write_u, write_prev, seed_d,
+                              seed_p, du2, dv2);
+                });
             pb ^= 1;
             wb ^= 1;
             if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);   // own pixels: no barrier
@@ -727,7 +738,12 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
         const T* q1s = p1c(); const T* q2s = p2c();
-        each([&](int a) { primal_one(P, a, O, q1s, q2s, Uu, Up, Wc, false, check, write_u, write_prev, seed, du2, dv2); });
+        if (!check && !write_prev)
+            each([&](int a) { primal_one(P, a, O, q1s, q2s, Uu, Up, Wc, false, false, false, false, seed, du2, dv2); });
+        else
+            each([&](int a) {
+                primal_one(P, a, O, q1s, q2s, Uu, Up, Wc, false, check, write_u, write_prev, seed, du2, dv2);
+            });
         if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);
         if (check) {
             float x = du2, y = dv2;
@@ -854,9 +870,11 @@ __device__ __forceinline__ void dual_gh(const IterParams& P, int i, int a, uint8
     // w below (RD) or p2 at x + e1 - e2 (below fixed; a p word of buffer pb)
     const float xd = D.sm[D.od[i] + (cd ? D.sh2 : 0)];
     const float xr = D.sm[D.orr[i] + (cr ? D.sh1 : 0)];
-    float g1 = 0.f, g2 = 0.f;
-    if (cd != 3) g1 = (cd == 0 ? xd : w_fixed(p1, xd, cd == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
-    if (cr != 3) g2 = (cr == 0 ? xr : w_fixed(xr, p2, cr == 2 ? kNbFg : kNbBg, P.inv_theta)) - w0;
+    // selects, not branches (the values of g_comp)
+    const float wd = cd == 0 ? xd : -(p1 + xd) - (cd == 2 ? P.inv_theta : 0.f);
+    const float wr = cr == 0 ? xr : -(xr + p2) - (cr == 2 ? P.inv_theta : 0.f);
+    const float g1 = cd == 3 ? 0.f : wd - w0;
+    const float g2 = cr == 3 ? 0.f : wr - w0;
     float q1, q2;
     chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
     const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
@@ -1042,11 +1060,18 @@ __device__ __forceinline__ bool compact_iterations_gh(const IterParams& P, const
         if (overlap) {
             GhostRegs<T> R;
             R.load(S, L.gd, L.gd + L.gp, pb, pb ? P1b : P1a, pb ? P2b : P2a, Wc, nt);
-            each([&](int a) {
-                const uint8_t f = S.fl[a - a0];
-                if (!(f & kFlPrimalGhost))
-                    primal_gh(P, a - a0, a, f, Q, Vs, F, U, Up, Wc, check, write_u, write_prev, seed, du2, dv2);
-            });
+            if (!check && !write_prev)
+                each([&](int a) {
+                    const uint8_t f = S.fl[a - a0];
+                    if (!(f & kFlPrimalGhost))
+                        primal_gh(P, a - a0, a, f, Q, Vs, F, U, Up, Wc, false, false, false, seed, du2, dv2);
+                });
+            else
+                each([&](int a) {
+                    const uint8_t f = S.fl[a - a0];
+                    if (!(f & kFlPrimalGhost))
+                        primal_gh(P, a - a0, a, f, Q, Vs, F, U, Up, Wc, check, write_u, write_prev, seed, du2, dv2);
+                });
             R.store(S, L.gd, L.gd + L.gp, pb, nt);
             __syncthreads();
             for (int e = tid; e < L.nbp; e += nt) {
@@ -1236,9 +1261,16 @@ __device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const
         Q.ou = S.off + 2 * L.nE;
         Q.ol = S.off + 2 * L.nE + L.n;
         T* Vs = S.v();
-        each([&](int a) {
-            primal_gh(P, a - a0, a, S.fl[a - a0], Q, Vs, F, U, Up, Wo, check, write_u, write_prev, seed, du2, dv2);
-        });
+        // the common iteration (no test, no u output) without their branches
+        if (!check && !write_prev)
+            each([&](int a) {
+                primal_gh(P, a - a0, a, S.fl[a - a0], Q, Vs, F, U, Up, Wo, false, false, false, seed, du2, dv2);
+            });
+        else
+            each([&](int a) {
+                primal_gh(P, a - a0, a, S.fl[a - a0], Q, Vs, F, U, Up, Wo, check, write_u, write_prev, seed, du2,
+                          dv2);
+            });
         if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);   // own pixels, same threads
         // stopping-test partials, double-buffered by check so that a fast
         // block cannot overwrite those a slow block is still summing
