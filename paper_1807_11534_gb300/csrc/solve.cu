@@ -480,8 +480,11 @@ __device__ __forceinline__ void dual_one(const IterParams& P, int a, const Own<T
     const float wr = n_right >= 0 ? ldw(Wc + n_right) : 0.f;
     const float p2dl = nb_ld(P2i, n_dl);
     const float p1ur = nb_ld(P1i, n_ur);
-    const float g1 = g_comp(n_down, wd, p1, p2dl, w0, P.inv_theta);
-    const float g2 = g_comp(n_right, wr, p1ur, p2, w0, P.inv_theta);
+    // (branches, not g_comp's selects: the neighbour loads above are
+    // conditional, and this form measured faster on this path)
+    float g1 = 0.f, g2 = 0.f;
+    if (n_down != kNbOut) g1 = (n_down >= 0 ? wd : w_fixed(p1, p2dl, n_down, P.inv_theta)) - w0;
+    if (n_right != kNbOut) g2 = (n_right >= 0 ? wr : w_fixed(p1ur, p2, n_right, P.inv_theta)) - w0;
     float q1, q2;
     chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
     const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
@@ -801,6 +804,7 @@ enum { GK_D = 0, GK_R, GK_UP, GK_LEFT, GK_KINDS };
 constexpr uint8_t kFlExport = 16;       // other blocks read this pixel
 constexpr uint8_t kFlDualGhost = 32;    // its dual step reads a ghost word
 constexpr uint8_t kFlPrimalGhost = 64;  // its primal step reads a ghost word
+constexpr uint8_t kFlLate = kFlDualGhost | kFlExport;   // one-barrier path: dual step after the ghost refill
 constexpr int kGhostRegs = 2;           // ghosts per thread carried in registers while the interior runs
 
 struct GhostLayout {
@@ -1140,7 +1144,7 @@ struct H1Layout {
     int n, r, nE;          // own pixels, ring pixels, n + r
     int ns1, ns2, nsw;     // region sizes (words) of P1, P2 (per buffer) and W: [own | ring | zero | ghosts]
     int p1, p2, w, v;      // word offsets of the regions
-    int ng, nbd;           // ghost words refilled per iteration; own pixels whose dual step reads one
+    int ng, nbd;           // ghost words refilled per iteration; late own pixels
     size_t off16, offfl, offr1, offgs, offgd, offbd, bytes;   // byte offsets of the tables
 };
 
@@ -1152,13 +1156,22 @@ struct H1State {
     const int32_t* r1;     // [r] compact index of each ring pixel
     const int32_t* gsrc;   // [ng] compact index of each ghost's pixel
     const uint16_t* gdst;  // [ng] word offset of each ghost (p words: buffer 0)
-    const uint16_t* bd;    // [nbd] own pixels whose dual step reads a ghost
+    const uint16_t* bd;    // [nbd] late own pixels (kFlLate)
     H1Layout L;
     __device__ __forceinline__ T* v() const { return reinterpret_cast<T*>(sm + L.v); }
 };
 
 // The iterations; returns false when a barrier timed out, else the final
 // iterate's count in *lf (its p is in buffer lf & 1).
+//
+// The grid barrier is split: a block arrives once its primal step is done
+// and, unless the iteration ends with a stopping test, runs the next
+// iteration's dual steps of its first UNROLL x NT "interior" pixels -- those
+// that read no ghost word and that no other block reads, so they touch only
+// the block's own words -- before it waits; the rest of the interior runs
+// while the ghost loads are in flight, and the "late" pixels (that read a
+// ghost or that another block reads: their global p must not change before
+// every block has read it) and the ring after the ghost words are stored.
 template <typename T, int NT, int UNROLL>
 __device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const H1State<T>& S, int a0, int a1,
                                                       int iters, int check_every, double tol, int64_t stride,
@@ -1188,32 +1201,55 @@ __device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const
             c[2 * stride + a] = to_f(V[i]) + Store<T>::vbias;
         }
     };
+    // the dual-step view of iteration it (p of buffer b)
+    auto dual_view = [&](int b) {
+        DualView D;
+        D.p1 = S.sm + L.p1 + b * L.ns1;
+        D.p2 = S.sm + L.p2 + b * L.ns2;
+        D.w = S.sm + L.w;
+        D.q1 = S.sm + L.p1 + (1 - b) * L.ns1;
+        D.q2 = S.sm + L.p2 + (1 - b) * L.ns2;
+        D.sm = S.sm;
+        D.sh1 = b * L.ns1;
+        D.sh2 = b * L.ns2;
+        D.od = S.off;
+        D.orr = S.off + L.nE;
+        return D;
+    };
+    auto dual_seed = [](int it) { return mix32(0x51ed270bu ^ (uint32_t)(it * 131)); };
+    // dual steps of the interior pixels among own pixels [i0, i1) (no ghost
+    // read, no global store)
+    const int iA = min(L.n, UNROLL * NT);
+    auto interior = [&](const DualView& D, uint32_t seed, int i0, int i1) {
+        int a = a0 + i0 + tid;
+        const int ae = a0 + i1;
+        auto op = [&](int b) {
+            const uint8_t f = S.fl[b - a0];
+            if (!(f & kFlLate)) dual_gh<T>(P, b - a0, b, f, D, nullptr, nullptr, seed);
+        };
+        for (; a + (UNROLL - 1) * nt < ae; a += UNROLL * nt) {
+#pragma unroll
+            for (int k = 0; k < UNROLL; ++k) op(a + k * nt);
+        }
+        for (; a < ae; a += nt) op(a);
+    };
     if (ckpt) save(0);
     const int C = check_every;
     *lf = iters;
+    bool early = false;   // this iteration's first interior pixels ran before the barrier
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
         const float* Wi = (it & 1) ? Wc2 : Wc;   // w of iterate it
         float* Wo = (it & 1) ? Wc : Wc2;         // w of iterate l (pixels other blocks read)
         {
-            const uint32_t seed = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
+            const uint32_t seed = dual_seed(it);
             T* o1 = pb ? P1a : P1b;
             T* o2 = pb ? P2a : P2b;
             const T* i1 = pb ? P1b : P1a;
             const T* i2 = pb ? P2b : P2a;
-            DualView D;
-            D.p1 = S.sm + L.p1 + pb * L.ns1;
-            D.p2 = S.sm + L.p2 + pb * L.ns2;
-            D.w = S.sm + L.w;
-            D.q1 = S.sm + L.p1 + (1 - pb) * L.ns1;
-            D.q2 = S.sm + L.p2 + (1 - pb) * L.ns2;
-            D.sm = S.sm;
-            D.sh1 = pb * L.ns1;
-            D.sh2 = pb * L.ns2;
-            D.od = S.off;
-            D.orr = S.off + L.nE;
-            // ghosts in flight (kGhostRegs per thread) while the pixels that
-            // read none update
+            const DualView D = dual_view(pb);
+            if (early && !grid_wait(h, nblocks, gen)) return false;
+            // ghosts in flight (kGhostRegs per thread) while interior pixels update
             float x[kGhostRegs];
 #pragma unroll
             for (int j = 0; j < kGhostRegs; ++j) {
@@ -1224,10 +1260,7 @@ __device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const
                     x[j] = dst >= L.w ? ldw(Wi + src) : dst >= L.p2 ? Store<T>::ldc(i2, src) : Store<T>::ldc(i1, src);
                 }
             }
-            each([&](int a) {
-                const uint8_t f = S.fl[a - a0];
-                if (!(f & kFlDualGhost)) dual_gh(P, a - a0, a, f, D, o1, o2, seed);
-            });
+            interior(D, seed, early ? iA : 0, L.n);
 #pragma unroll
             for (int j = 0; j < kGhostRegs; ++j) {
                 const int g = tid + j * nt;
@@ -1237,7 +1270,7 @@ __device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const
                 }
             }
             __syncthreads();
-            // own pixels that read ghosts, then the ring
+            // late own pixels, then the ring
             for (int e = tid; e < L.nbd + L.r; e += nt) {
                 const bool own = e < L.nbd;
                 const int i = own ? S.bd[e] : L.n + (e - L.nbd);
@@ -1283,40 +1316,44 @@ __device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const
                 part[2 * blockIdx.x + 1] = y;
             }
         }
-        if (!grid_sync(h, nblocks, gen)) return false;
-        if (check) {
-            // Section 4 stopping test: with a tolerance every block sums the
-            // block partials in the same fixed order, so all stop after the
-            // same iteration (squared norms against tol^2); block 0 records
-            // the norms
-            if (tol > 0.0 || blockIdx.x == 0) {
-                if (tid < 32) {
-                    double sx, sy;
-                    sum_partials_warp0(part, (int)nblocks, sx, sy);
-                    if (tid == 0) {
-                        const bool stop = tol > 0.0 && fmax(sx, sy) <= tol * tol;
-                        s_red[0] = stop ? 1.0 : 0.0;
-                        if (blockIdx.x == 0) {
-                            h->du2 = sx;
-                            h->dv2 = sy;
-                            h->last_check = l;
-                            if (stop) {
-                                h->iters_done = l;
-                                h->done = 1;
-                            }
+        grid_arrive(h, gen);
+        early = !check;   // (the last iteration is a check)
+        if (early) {
+            // the next iteration's first interior pixels, on the block's own words
+            interior(dual_view(pb), dual_seed(l), 0, iA);
+            continue;
+        }
+        if (!grid_wait(h, nblocks, gen)) return false;
+        // Section 4 stopping test: with a tolerance every block sums the
+        // block partials in the same fixed order, so all stop after the same
+        // iteration (squared norms against tol^2); block 0 records the norms
+        if (tol > 0.0 || blockIdx.x == 0) {
+            if (tid < 32) {
+                double sx, sy;
+                sum_partials_warp0(part, (int)nblocks, sx, sy);
+                if (tid == 0) {
+                    const bool stop = tol > 0.0 && fmax(sx, sy) <= tol * tol;
+                    s_red[0] = stop ? 1.0 : 0.0;
+                    if (blockIdx.x == 0) {
+                        h->du2 = sx;
+                        h->dv2 = sy;
+                        h->last_check = l;
+                        if (stop) {
+                            h->iters_done = l;
+                            h->done = 1;
                         }
                     }
                 }
-                __syncthreads();
-                const bool stop = s_red[0] != 0.0;
-                __syncthreads();
-                if (stop) {
-                    *lf = l;
-                    return true;
-                }
             }
-            ++chk;
+            __syncthreads();
+            const bool stop = s_red[0] != 0.0;
+            __syncthreads();
+            if (stop) {
+                *lf = l;
+                return true;
+            }
         }
+        ++chk;
     }
     return true;
 }
@@ -1395,7 +1432,7 @@ __device__ __forceinline__ int compact_solve_h1(
     L.offgs = L.offr1 + (size_t)4 * L.r;
     L.offgd = L.offgs + (size_t)4 * L.ng;
     L.offbd = L.offgd + (size_t)2 * L.ng;
-    L.bytes = L.offbd + (size_t)2 * min(nown, s_h[4]);
+    L.bytes = L.offbd + (size_t)2 * nown;
     const bool fits = L.bytes <= compact_smem(NT) && words < 65536 && L.ng <= kGhostRegs * NT;
     // the vote: every block adds 1 when it does not fit
     __shared__ unsigned s_vote;
@@ -1483,15 +1520,19 @@ __device__ __forceinline__ int compact_solve_h1(
     }
     if (!grid_sync(h, nblocks, gen)) return -1;   // every mark cleared, every table built
     for (int g = tid; g < L.ng; g += nt) mark[gsrc[g]] = 1u;
-    // stable list of the own pixels whose dual step reads a ghost
+    if (!grid_sync(h, nblocks, gen)) return -1;   // every mark set
+    for (int i = tid; i < nown; i += nt)
+        if (__ldcg(mark + a0 + i)) flg[i] |= kFlExport;
+    __syncthreads();
+    // stable list of the late own pixels
     __shared__ int s_nbd;
     if (tid < 32) {
         int cd = 0;
         for (int b = 0; b < nown; b += 32) {
             const int i = b + tid;
             const unsigned f = i < nown ? flg[i] : 0u;
-            const unsigned md = __ballot_sync(0xffffffffu, f & kFlDualGhost);
-            if (f & kFlDualGhost) lbd[cd + __popc(md & lanemask_lt(tid))] = (uint16_t)i;
+            const unsigned md = __ballot_sync(0xffffffffu, f & kFlLate);
+            if (f & kFlLate) lbd[cd + __popc(md & lanemask_lt(tid))] = (uint16_t)i;
             cd += __popc(md);
         }
         if (tid == 0) {
@@ -1500,9 +1541,6 @@ __device__ __forceinline__ int compact_solve_h1(
             atomicAdd(&h->n_h1_blocks, 1);
         }
     }
-    if (!grid_sync(h, nblocks, gen)) return -1;   // every mark set
-    for (int i = tid; i < nown; i += nt)
-        if (__ldcg(mark + a0 + i)) flg[i] |= kFlExport;
     __syncthreads();
     L.nbd = s_nbd;
     const H1State<T> S{sm, off, flg, r1, gsrc, gdst, lbd, L};
