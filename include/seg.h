@@ -72,7 +72,9 @@ typedef struct seg_params {
     double tol;         /* stop when max(||du||,||dv||) <= tol (Section 4); <= 0: run `iters` */
     int iters;          /* maximum number of outer iterations */
     int n_inner;        /* fixed-point sweeps for p per outer iteration (>= 1; default 1) */
-    int check_every;    /* evaluate the stopping test every this many iterations (>= 1) */
+    int check_every;    /* evaluate the stopping test every this many iterations (>= 1); with
+                           tol <= 0 the dense, compact and batch solves test only the last
+                           iteration (nothing is decided; stats hold that test's norms) */
     int warm_start;     /* 0: start from u = H(-f), p = 0, v = v-step(u); 1: from the u, v, p1, p2 given */
     int mode;           /* SEG_MODE_DENSE, SEG_MODE_COMPACT or SEG_MODE_TILED */
     int storage;        /* SEG_STORE_*; 16-bit storage is SEG_MODE_COMPACT only */
@@ -275,7 +277,8 @@ typedef struct seg_pd_params {
     double tau;         /* primal step (default 1/sqrt(8)); sigma tau <= 1/8 converges */
     double tol;         /* stop when max(||du||, ||dp||) <= tol; <= 0: run `iters` */
     int iters;          /* maximum number of iterations */
-    int check_every;    /* evaluate the stopping test every this many iterations (>= 1) */
+    int check_every;    /* evaluate the stopping test every this many iterations (>= 1); with
+                           tol <= 0 only the last iteration is tested */
     int warm_start;     /* 0: start from u = H(-f), p = 0; 1: from the u, p1, p2 given */
     int tile_h;         /* tile height used by seg_build_domain for this domain */
 } seg_pd_params;

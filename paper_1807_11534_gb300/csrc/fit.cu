@@ -103,9 +103,38 @@ __device__ __forceinline__ unsigned long long min_d2(const int2* sm, int m, int 
     return best;
 }
 
+// The same in 32-bit integers, exact when both image sides are at most
+// kSmallSide and every marker lies inside the image (every squared distance
+// is then below 2^31).
+constexpr int kSmallSide = 32767;
+
+// Whether every marker lies inside the H x W image (the same answer in every
+// block; all threads of the block must call it).
+__device__ __forceinline__ bool markers_inside(const int32_t* __restrict__ markers, int n_markers, int H, int W) {
+    int ok = 1;
+    for (int k = threadIdx.x; k < n_markers; k += blockDim.x) {
+        const int my = markers[2 * k], mx = markers[2 * k + 1];
+        ok &= (my >= 0 && my < H && mx >= 0 && mx < W) ? 1 : 0;
+    }
+    return __syncthreads_and(ok) != 0;
+}
+__device__ __forceinline__ unsigned min_d2_32(const int2* sm, int m, int i, int j, unsigned best) {
+    for (int k = 0; k < m; ++k) {
+        const int dy = i - sm[k].x, dx = j - sm[k].y;
+        const unsigned d = (unsigned)(dy * dy + dx * dx);
+        best = d < best ? d : best;
+    }
+    return best;
+}
+
 // Maximum over the image of the squared distance to the nearest marker.
-__global__ void k_marker_dmax(const int32_t* __restrict__ markers, int n_markers, int H, int W,
-                              WsHeader* h) {
+// SMALL (both sides <= kSmallSide) with every marker inside the image:
+// 32-bit distances, and each pixel's nearest squared distance is left in its
+// f word (as uint32 bits) for k_fitting<true>, which then skips the marker
+// loop.
+template <bool SMALL>
+__global__ void k_marker_dmax(const int32_t* __restrict__ markers, int n_markers, int H, int W, int ld,
+                              WsHeader* h, float* __restrict__ f) {
     __shared__ int2 sm[kMarkerChunk];
     __shared__ unsigned long long s_max[kFitThreads / 32];
     int64_t n = (int64_t)H * W;
@@ -115,17 +144,26 @@ __global__ void k_marker_dmax(const int32_t* __restrict__ markers, int n_markers
     // every thread of the block walks the same number of rounds so the
     // marker chunks can be staged with __syncthreads
     int64_t rounds = (n + stride - 1) / stride;
+    const bool small = SMALL && markers_inside(markers, n_markers, H, W);
     for (int64_t r = 0; r < rounds; ++r) {
         int64_t x = x0 + r * stride;
         const int i = (int)((uint32_t)x / (uint32_t)W), j = (int)(x - (int64_t)i * W);   // x < 2^31
         unsigned long long best = ~0ull;
+        unsigned best32 = ~0u;
         for (int c0 = 0; c0 < n_markers; c0 += kMarkerChunk) {
             int m = min(kMarkerChunk, n_markers - c0);
             __syncthreads();
             for (int k = threadIdx.x; k < m; k += blockDim.x)
                 sm[k] = make_int2(markers[2 * (c0 + k)], markers[2 * (c0 + k) + 1]);
             __syncthreads();
-            if (x < n) best = min_d2(sm, m, i, j, best);
+            if (x < n) {
+                if (small) best32 = min_d2_32(sm, m, i, j, best32);
+                else best = min_d2(sm, m, i, j, best);
+            }
+        }
+        if (small && x < n) {
+            best = best32;
+            reinterpret_cast<unsigned*>(f)[(int64_t)i * ld + j] = best32;
         }
         if (x < n && best > local) local = best;
     }
@@ -143,7 +181,10 @@ __global__ void k_marker_dmax(const int32_t* __restrict__ markers, int n_markers
 }
 
 // f = ((z-c1)^2 - (z-c2)^2) [+ gamma * sqrt(d2) / sqrt(d2max)], FP64, one
-// rounding per operation in this order, then rounded to float32.
+// rounding per operation in this order, then rounded to float32.  CACHED:
+// d2 is read from the pixel's f word where k_marker_dmax<true> left it
+// (every marker inside the image; else the marker loop runs here).
+template <bool CACHED>
 __global__ void k_fitting(const float* __restrict__ z, int H, int W, int ld,
                           const int32_t* __restrict__ markers, int n_markers, double gamma,
                           const WsHeader* __restrict__ h, float* __restrict__ f) {
@@ -155,17 +196,22 @@ __global__ void k_fitting(const float* __restrict__ z, int H, int W, int ld,
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t x0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t rounds = (n + stride - 1) / stride;
+    const bool cached = CACHED && markers_inside(markers, n_markers, H, W);
     for (int64_t r = 0; r < rounds; ++r) {
         int64_t x = x0 + r * stride;
         const int i = (int)((uint32_t)x / (uint32_t)W), j = (int)(x - (int64_t)i * W);   // x < 2^31
         unsigned long long best = ~0ull;
-        for (int c0 = 0; c0 < n_markers; c0 += kMarkerChunk) {
-            int m = min(kMarkerChunk, n_markers - c0);
-            __syncthreads();
-            for (int k = threadIdx.x; k < m; k += blockDim.x)
-                sm[k] = make_int2(markers[2 * (c0 + k)], markers[2 * (c0 + k) + 1]);
-            __syncthreads();
-            if (x < n) best = min_d2(sm, m, i, j, best);
+        if (cached) {
+            if (x < n) best = reinterpret_cast<const unsigned*>(f)[(int64_t)i * ld + j];
+        } else {
+            for (int c0 = 0; c0 < n_markers; c0 += kMarkerChunk) {
+                int m = min(kMarkerChunk, n_markers - c0);
+                __syncthreads();
+                for (int k = threadIdx.x; k < m; k += blockDim.x)
+                    sm[k] = make_int2(markers[2 * (c0 + k)], markers[2 * (c0 + k) + 1]);
+                __syncthreads();
+                if (x < n) best = min_d2(sm, m, i, j, best);
+            }
         }
         if (x >= n) continue;
         double zz = (double)z[(int64_t)i * ld + j];
@@ -223,12 +269,20 @@ extern "C" seg_status seg_make_fitting(const float* z, int H, int W, int ld, dou
     }
     int64_t n = (int64_t)H * W;
     int blocks = (int)std::min<int64_t>((n + kFitThreads - 1) / kFitThreads, 152 * 8);
-    if (n_markers > 0) {
-        k_marker_dmax<<<blocks, kFitThreads, 0, s>>>(markers, n_markers, H, W, h);
+    const bool small = H <= kSmallSide && W <= kSmallSide;
+    if (n_markers > 0 && small) {
+        k_marker_dmax<true><<<blocks, kFitThreads, 0, s>>>(markers, n_markers, H, W, ld, h, f);
         SEG_LAUNCHED("k_marker_dmax");
+        k_fitting<true><<<blocks, kFitThreads, 0, s>>>(z, H, W, ld, markers, n_markers, gamma, h, f);
+        SEG_LAUNCHED("k_fitting");
+    } else {
+        if (n_markers > 0) {
+            k_marker_dmax<false><<<blocks, kFitThreads, 0, s>>>(markers, n_markers, H, W, ld, h, f);
+            SEG_LAUNCHED("k_marker_dmax");
+        }
+        k_fitting<false><<<blocks, kFitThreads, 0, s>>>(z, H, W, ld, markers, n_markers, gamma, h, f);
+        SEG_LAUNCHED("k_fitting");
     }
-    k_fitting<<<blocks, kFitThreads, 0, s>>>(z, H, W, ld, markers, n_markers, gamma, h, f);
-    SEG_LAUNCHED("k_fitting");
     return SEG_OK;
 }
 

@@ -97,6 +97,13 @@ constexpr int kEnergyBlockThreads = 256;  // block size of the energy / error ke
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The stopping-test interval a solve runs with.  Without a tolerance
+// (tol <= 0) no test decides anything and only the last test's norms are
+// reported, so only the last iteration is tested.
+inline int test_interval(double tol, int check_every, int iters) {
+    return tol > 0.0 ? (check_every > 1 ? check_every : 1) : (iters > 1 ? iters : 1);
+}
+
 // Byte offsets of the workspace regions for one image geometry.
 struct WsLayout {
     size_t header, tile_cnt, tile_flag, tile_start, tile_pos, scan_tmp, partials,

@@ -2051,7 +2051,7 @@ static seg_status run_dense(const IterParams& P0, const seg_params* prm, const i
     const int64_t max_blocks = (n_tasks + kDenseWarps - 1) / kDenseWarps;
     const int grid = grid_for(kv[1][1], kDenseWarps * 32, max_blocks);
     int pb = 0, vb = 0;
-    const int C = std::max(1, prm->check_every);
+    const int C = test_interval(prm->tol, prm->check_every, prm->iters);
     for (int it = 0; it < prm->iters; ++it) {
         const int l = it + 1;
         for (int sw = 1; sw < prm->n_inner; ++sw) {
@@ -2127,7 +2127,8 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
                                       std::max<int64_t>(1, (most + NTs - 1) / NTs));
     grid = (int)std::min<int64_t>(grid, max_partials / 2);   // partials are double-buffered
-    int iters = prm->iters, n_inner = std::max(1, prm->n_inner), check_every = std::max(1, prm->check_every);
+    int iters = prm->iters, n_inner = std::max(1, prm->n_inner);
+    int check_every = test_interval(prm->tol, prm->check_every, prm->iters);
     double tol = prm->tol;
     int warm = prm->warm_start;
     int64_t stride = S.stride;
@@ -2933,7 +2934,7 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
                                       std::max<int64_t>(1, (most + kPdThreads - 1) / kPdThreads));
     grid = (int)std::min<int64_t>(grid, L.npartials / 2);
-    int iters = prm->iters, ce = prm->check_every;
+    int iters = prm->iters, ce = test_interval(prm->tol, prm->check_every, prm->iters);
     double tol = prm->tol;
     float sigma = (float)prm->sigma, tau = (float)prm->tau;
     const int32_t* cnt = totals;

@@ -401,7 +401,7 @@ extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, c
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), L.npartials / 2);
     grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (std::max<int64_t>(S.cap, 1) + kVolThreads - 1) /
                                                                   kVolThreads));
-    int iters = prm->iters, ce = prm->check_every;
+    int iters = prm->iters, ce = test_interval(prm->tol, prm->check_every, prm->iters);
     double tol = prm->tol;
     void* args[] = {&G, &iters, &ce, &tol, (void*)&counts, &u, &S, &partials, &h};
     if (iters > 0) {

@@ -62,6 +62,25 @@ def test_fitting_ds_bit_exact(orc, m):
     np.testing.assert_array_equal(f, f_o)
 
 
+@pytest.mark.parametrize("where", ["inside", "outside", "far"])
+def test_fitting_ds_markers_in_and_out_of_the_image(orc, where):
+    """Marker distances are exact integers: 32-bit with every marker inside
+    the image (each pixel's nearest distance computed once and reused),
+    64-bit when one lies outside, however far (the distance then exceeds
+    2^31); bit-exact against the oracle either way."""
+    rng = np.random.default_rng(7)
+    H, W = 120, 257
+    z = rng.uniform(0, 1, (H, W)).astype(np.float32)
+    mk = np.stack([rng.integers(0, H, 12), rng.integers(0, W, 12)], 1).astype(np.int32)
+    if where == "outside":
+        mk[3] = (-5, W + 40)
+    elif where == "far":
+        mk[0] = (-2_000_000_000, 2_000_000_000)
+    f, _ = _fitting_gpu(z, 0.25, 0.75, markers=mk, gamma=0.5)
+    _, f_o = orc.fitting(z, 0.25, 0.75, mk, 0.5)
+    np.testing.assert_array_equal(f, f_o)
+
+
 def test_fitting_label_means(orc):
     P = synth.ellipses_ds(seed=3, H=300, W=333)
     f, c = _fitting_gpu(P.z, label=P.label, markers=P.markers, gamma=P.gamma)
