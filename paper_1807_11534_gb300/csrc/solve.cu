@@ -2723,20 +2723,19 @@ constexpr int kPdThreads = 1024;   // two blocks per SM (32 registers): latency-
 
 __device__ __forceinline__ float pd_fixed(int code) { return code == kNbFg ? 1.f : 0.f; }
 
-__global__ void __launch_bounds__(kPdThreads, 2)
-k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
-           const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
-           float* P1a, float* P1b, float* P2a, float* P2b, float* U0, float* U1, float* Ub,
-           const float* __restrict__ F, double* partials, WsHeader* h) {
-    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
-    if (*(volatile int*)&h->done) return;
+// The primal-dual iteration on the global arrays (two grid barriers per
+// iteration); gen: barriers passed so far.
+template <int NT>
+__device__ __forceinline__ void pd_iterations(int iters, int check_every, double tol, float sigma, float tau,
+                                              int n, const int32_t* __restrict__ nb, int64_t stride,
+                                              float* P1a, float* P1b, float* P2a, float* P2b, float* U0,
+                                              float* U1, float* Ub, const float* __restrict__ F,
+                                              double* partials, WsHeader* h, double* s_red, unsigned& gen) {
     const unsigned nblocks = gridDim.x;
-    const int n = counts[1];
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
     const int tid = threadIdx.x;
     const int C = check_every;
-    unsigned gen = 0;
     int chk = 0;
     for (int l = 1; l <= iters; ++l) {
         const bool check = (l % C == 0) || l == iters;
@@ -2748,7 +2747,7 @@ k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
         const float* Ui = (l & 1) ? U0 : U1;
         float* Uo = (l & 1) ? U1 : U0;
         float du2 = 0.f, dp2 = 0.f;
-        for (int a = a0 + tid; a < a1; a += kPdThreads) {
+        for (int a = a0 + tid; a < a1; a += NT) {
             const int nd = __ldg(nb + NB_DOWN * stride + a), nr = __ldg(nb + NB_RIGHT * stride + a);
             const float ub = Ub[a];
             float g1 = 0.f, g2 = 0.f;
@@ -2770,7 +2769,7 @@ k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
             }
         }
         if (!grid_sync(h, nblocks, gen)) return;
-        for (int a = a0 + tid; a < a1; a += kPdThreads) {
+        for (int a = a0 + tid; a < a1; a += NT) {
             const int nu = __ldg(nb + NB_UP * stride + a), nl = __ldg(nb + NB_LEFT * stride + a);
             const float q1 = P1o[a], q2 = P2o[a];
             const float q1u = nu >= 0 ? P1o[nu] : 0.f, q2l = nl >= 0 ? P2o[nl] : 0.f;
@@ -2787,7 +2786,7 @@ k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
         double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
         if (check) {
             float x = du2, y = dp2;
-            block_sum2f<kPdThreads>(x, y, reinterpret_cast<float*>(s_red));
+            block_sum2f<NT>(x, y, reinterpret_cast<float*>(s_red));
             if (tid == 0) {
                 part[2 * blockIdx.x] = x;
                 part[2 * blockIdx.x + 1] = y;
@@ -2821,6 +2820,413 @@ k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
             if (stop) return;
         }
     }
+}
+
+// ---- the primal-dual iteration with shared-memory state and one grid barrier
+//
+// The layout and protocol of the one-barrier dual iteration (compact_solve_h1)
+// with u-bar in the part of w and u in that of v: each block keeps p (both
+// buffers), u-bar and u of its pixels and of its ring (the pixels other
+// blocks own directly above or left of its own; u of its own pixels only) in
+// shared memory and runs the ring's dual steps too, so the primal step
+// follows after a block barrier.  The dual step reads p only at its own
+// pixel (a fixed neighbour contributes its fixed u, not p flowing into it),
+// so the ring's p is read once, at the start, and p has no ghost words; the
+// ghost words are u-bar below / right of the block's pixels and of its ring,
+// and u-bar of the ring, refilled each iteration from the previous iterate,
+// which the global arrays keep in ping-pong buffers (written for the pixels
+// other blocks read).  The grid barrier is split as in
+// compact_iterations_h1; every block takes the Section 4 decision.  The
+// iterates are bit-identical to pd_iterations'.
+struct PdLayout {
+    int n, r, nE;          // own pixels, ring pixels, n + r
+    int nsp, nsu;          // region sizes (words): P1 / P2 per buffer [own | ring | zero], UB [own | ring | zero | ghosts]
+    int p1, p2, ub, u;     // word offsets of the regions (U: own pixels)
+    int ng, nbd;           // ghost words refilled per iteration; own pixels whose dual step reads one
+    size_t off16, offfl, offr1, offgs, offgd, offbd, bytes;
+};
+
+struct PdSmem {
+    float* sm;
+    const uint16_t* off;   // [D: nE][R: nE][UP: n][LEFT: n] word offsets (p words: buffer 0)
+    const uint8_t* fl;     // [nE]: classes below / right (bits 0-3), kFlExport, kFlDualGhost
+    const int32_t* r1;     // [r] compact index of each ring pixel
+    const int32_t* gsrc;   // [ng] compact index of each ghost's pixel
+    const uint16_t* gdst;  // [ng] word offset of each ghost
+    const uint16_t* bd;    // [nbd] own pixels whose dual step reads a ghost
+    PdLayout L;
+};
+
+// Dual step of entry i: p' = P(p + sigma grad u-bar), the fixed neighbours'
+// u-bar their fixed u (selects, the values of pd_iterations' branches); dp2
+// accumulates |p' - p|^2 when acc.
+__device__ __forceinline__ void pd_dual_sm(const PdSmem& S, int i, uint8_t fl, const float* P1, const float* P2,
+                                           float* Q1, float* Q2, float sigma, bool acc, float& dp2) {
+    const float ub0 = S.sm[S.L.ub + i];
+    const float xd = S.sm[S.off[i]], xr = S.sm[S.off[S.L.nE + i]];
+    const int cd = fl & 3, cr = (fl >> 2) & 3;   // 0 RD, 1 fixed Bg, 2 fixed Fg, 3 outside
+    const float ud = cd == 0 ? xd : (cd == 2 ? 1.f : 0.f);
+    const float ur = cr == 0 ? xr : (cr == 2 ? 1.f : 0.f);
+    const float g1 = cd == 3 ? 0.f : ud - ub0;
+    const float g2 = cr == 3 ? 0.f : ur - ub0;
+    const float p1 = P1[i], p2 = P2[i];
+    float q1 = fmaf(sigma, g1, p1), q2 = fmaf(sigma, g2, p2);
+    const float s2 = fmaf(q1, q1, q2 * q2);
+    const float r = s2 > 1.f ? rsqrtf(s2) : 1.f;
+    q1 *= r;
+    q2 *= r;
+    Q1[i] = q1;
+    Q2[i] = q2;
+    if (acc) {
+        const float d1 = q1 - p1, d2 = q2 - p2;
+        dp2 = fmaf(d1, d1, fmaf(d2, d2, dp2));
+    }
+}
+
+// Primal step of own pixel i (compact index a): u' = clip(u + tau div p' -
+// tau lambda f), u-bar' = 2u' - u (exported when other blocks read it).
+__device__ __forceinline__ void pd_primal_sm(const PdSmem& S, int i, int a, const float* Q1, const float* Q2,
+                                             int sh, float tau, const float* __restrict__ F, float* Ubo,
+                                             bool check, float& du2) {
+    const float q1 = Q1[i], q2 = Q2[i];
+    const float q1u = S.sm[S.off[2 * S.L.nE + i] + sh], q2l = S.sm[S.off[2 * S.L.nE + S.L.n + i] + sh];
+    const float div = (q1 - q1u) + (q2 - q2l);
+    float* U = S.sm + S.L.u;
+    const float uo = U[i];
+    const float un = clamp01(fmaf(tau, div, uo) - __ldg(F + a));   // F = tau lambda f
+    U[i] = un;
+    const float ubn = fmaf(2.f, un, -uo);
+    S.sm[S.L.ub + i] = ubn;
+    if (S.fl[i] & kFlExport) Ubo[a] = ubn;
+    if (check) {
+        const float d = un - uo;
+        du2 = fmaf(d, d, du2);
+    }
+}
+
+// Sets up and runs the shared-memory primal-dual iteration when every block's
+// state fits (a grid-wide vote).  Returns 1 when it ran the solve, 0 when
+// some block does not fit (nothing changed), -1 when a barrier timed out.
+template <int NT>
+__device__ __forceinline__ int pd_solve_sm(int iters, int check_every, double tol, float sigma, float tau, int n,
+                                           const int32_t* __restrict__ nb, int64_t stride, float* P1a,
+                                           float* P1b, float* P2a, float* P2b, float* U0, float* U1, float* Ub,
+                                           float* Ub2, const float* __restrict__ F, double* partials,
+                                           WsHeader* h, double* s_red, unsigned char* c_smem, unsigned& gen) {
+    const unsigned nblocks = gridDim.x;
+    const int tid = threadIdx.x, nt = NT;
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    const int nown = max(a1 - a0, 0);
+    auto other = [&](int m) { return m >= 0 && (m < a0 || m >= a1); };
+    auto dr_src = [&](int a, int k) { return __ldg(nb + (k == GK_D ? NB_DOWN : NB_RIGHT) * stride + a); };
+    // counts: [0] ring pixels, [1] u-bar ghost words past the ring's, [2] ghosts own pixels read
+    __shared__ int s_h[4];
+    if (tid < 4) s_h[tid] = 0;
+    __syncthreads();
+    {
+        int r = 0, gu = 0, go = 0;
+        for (int i = tid; i < nown; i += nt) {
+            const int a = a0 + i;
+#pragma unroll
+            for (int k = GK_D; k <= GK_R; ++k)
+                if (other(dr_src(a, k))) { ++gu; ++go; }
+#pragma unroll
+            for (int k = GK_UP; k <= GK_LEFT; ++k) {
+                const int y = __ldg(nb + (k == GK_UP ? NB_UP : NB_LEFT) * stride + a);
+                if (!other(y)) continue;
+                ++r;
+#pragma unroll
+                for (int k2 = GK_D; k2 <= GK_R; ++k2)
+                    if (other(dr_src(y, k2))) ++gu;
+            }
+        }
+        if (r) atomicAdd(&s_h[0], r);
+        if (gu) atomicAdd(&s_h[1], gu);
+        if (go) atomicAdd(&s_h[2], go);
+    }
+    __syncthreads();
+    PdLayout L{};
+    L.n = nown;
+    L.r = s_h[0];
+    L.nE = nown + L.r;
+    const int gux = s_h[1];
+    L.ng = gux + L.r;   // plus u-bar of every ring pixel
+    L.nsp = L.nE + 1;
+    L.nsu = L.nE + 1 + gux;
+    L.p1 = 0;
+    L.p2 = 2 * L.nsp;
+    L.ub = L.p2 + 2 * L.nsp;
+    L.u = L.ub + L.nsu;
+    const int words = L.u + nown;
+    L.off16 = (size_t)4 * words;
+    L.offfl = L.off16 + (size_t)2 * (2 * L.nE + 2 * nown);
+    L.offr1 = (L.offfl + L.nE + 3) & ~(size_t)3;
+    L.offgs = L.offr1 + (size_t)4 * L.r;
+    L.offgd = L.offgs + (size_t)4 * L.ng;
+    L.offbd = L.offgd + (size_t)2 * L.ng;
+    L.bytes = L.offbd + (size_t)2 * min(nown, s_h[2]);
+    const bool fits = L.bytes <= compact_smem(NT) && words < 65536 && L.ng <= kGhostRegs * NT;
+    __shared__ unsigned s_vote;
+    if (tid == 0 && !fits) atomicAdd(&h->h1_vote, 1u);
+    if (!grid_sync(h, nblocks, gen)) return -1;
+    if (tid == 0) s_vote = *(volatile unsigned*)&h->h1_vote;
+    __syncthreads();
+    const bool all_fit = s_vote == 0u;
+    __syncthreads();
+    if (!all_fit) return 0;
+
+    unsigned* mark = reinterpret_cast<unsigned*>(Ub2);   // export marks, before Ub2 holds u-bar
+    for (int i = tid; i < nown; i += nt) mark[a0 + i] = 0u;
+    float* sm = reinterpret_cast<float*>(c_smem);
+    uint16_t* off = reinterpret_cast<uint16_t*>(c_smem + L.off16);
+    uint8_t* flg = reinterpret_cast<uint8_t*>(c_smem + L.offfl);
+    int32_t* r1 = reinterpret_cast<int32_t*>(c_smem + L.offr1);
+    int32_t* gsrc = reinterpret_cast<int32_t*>(c_smem + L.offgs);
+    uint16_t* gdst = reinterpret_cast<uint16_t*>(c_smem + L.offgd);
+    uint16_t* lbd = reinterpret_cast<uint16_t*>(c_smem + L.offbd);
+    if (tid < 4) s_h[tid] = 0;   // [0] ring slots, [1] ghost area words, [2] ghost slots
+    if (tid == 0) {
+        sm[L.p1 + L.nE] = 0.f; sm[L.p1 + L.nsp + L.nE] = 0.f;
+        sm[L.p2 + L.nE] = 0.f; sm[L.p2 + L.nsp + L.nE] = 0.f;
+        sm[L.ub + L.nE] = 0.f;
+    }
+    __syncthreads();
+    // the u-bar word a D / R read of pixel a uses (a ghost word when another block owns it)
+    auto dr_off = [&](int a, int k, bool& ghost) {
+        const int m = dr_src(a, k);
+        ghost = false;
+        if (m >= a0 && m < a1) return L.ub + (m - a0);
+        if (m < 0) return L.ub + L.nE;   // fixed or outside: the class is in the flags
+        ghost = true;
+        const int o = L.ub + L.nE + 1 + atomicAdd(&s_h[1], 1);
+        const int slot = atomicAdd(&s_h[2], 1);
+        gsrc[slot] = m;
+        gdst[slot] = (uint16_t)o;
+        return o;
+    };
+    for (int i = tid; i < nown; i += nt) {
+        const int a = a0 + i;
+        bool gd = false, g;
+        off[i] = (uint16_t)dr_off(a, GK_D, g);
+        gd |= g;
+        off[L.nE + i] = (uint16_t)dr_off(a, GK_R, g);
+        gd |= g;
+        flg[i] = (uint8_t)(gk_codes(nb, stride, a) | (gd ? kFlDualGhost : 0));
+#pragma unroll
+        for (int k = GK_UP; k <= GK_LEFT; ++k) {
+            const int y = __ldg(nb + (k == GK_UP ? NB_UP : NB_LEFT) * stride + a);
+            const int base = k == GK_UP ? L.p1 : L.p2;
+            int o;
+            if (y >= a0 && y < a1) {
+                o = base + (y - a0);
+            } else if (y < 0) {
+                o = base + L.nE;
+            } else {   // a ring pixel: p read once, u-bar a ghost
+                const int j = atomicAdd(&s_h[0], 1);
+                const int e = nown + j;
+                o = base + e;
+                r1[j] = y;
+                off[e] = (uint16_t)dr_off(y, GK_D, g);
+                off[L.nE + e] = (uint16_t)dr_off(y, GK_R, g);
+                flg[e] = gk_codes(nb, stride, y);
+                sm[L.p1 + e] = P1a[y];
+                sm[L.p2 + e] = P2a[y];
+                const int slot = atomicAdd(&s_h[2], 1);
+                gsrc[slot] = y;
+                gdst[slot] = (uint16_t)(L.ub + e);
+            }
+            off[2 * L.nE + (k - GK_UP) * nown + i] = (uint16_t)o;
+        }
+        sm[L.p1 + i] = P1a[a];
+        sm[L.p2 + i] = P2a[a];
+        sm[L.ub + i] = Ub[a];
+        sm[L.u + i] = U0[a];
+    }
+    if (!grid_sync(h, nblocks, gen)) return -1;   // every mark cleared, every table built
+    for (int g = tid; g < L.ng; g += nt) mark[gsrc[g]] = 1u;
+    __shared__ int s_nbd;
+    if (tid < 32) {   // stable list of the own pixels whose dual step reads a ghost
+        int cd = 0;
+        for (int b = 0; b < nown; b += 32) {
+            const int i = b + tid;
+            const unsigned f = i < nown ? flg[i] : 0u;
+            const unsigned md = __ballot_sync(0xffffffffu, f & kFlDualGhost);
+            if (f & kFlDualGhost) lbd[cd + __popc(md & lanemask_lt(tid))] = (uint16_t)i;
+            cd += __popc(md);
+        }
+        if (tid == 0) {
+            s_nbd = cd;
+            atomicAdd(&h->n_smem_blocks, 1);
+            atomicAdd(&h->n_h1_blocks, 1);
+        }
+    }
+    if (!grid_sync(h, nblocks, gen)) return -1;   // every mark set
+    for (int i = tid; i < nown; i += nt)
+        if (__ldcg(mark + a0 + i)) flg[i] |= kFlExport;
+    __syncthreads();
+    L.nbd = s_nbd;
+    const PdSmem S{sm, off, flg, r1, gsrc, gdst, lbd, L};
+
+    // ---- iterations
+    const int C = check_every;
+    const int iA = min(nown, 4 * NT);
+    int pb = 0, chk = 0, lf = iters;
+    float dp2 = 0.f;
+    bool early = false;
+    // interior dual steps (no ghost read) of own pixels [i0, i1)
+    auto interior = [&](int b, bool acc, int i0, int i1) {
+        const float* P1 = sm + L.p1 + b * L.nsp;
+        const float* P2 = sm + L.p2 + b * L.nsp;
+        float* Q1 = sm + L.p1 + (1 - b) * L.nsp;
+        float* Q2 = sm + L.p2 + (1 - b) * L.nsp;
+        for (int i = i0 + tid; i < i1; i += nt) {
+            const uint8_t f = flg[i];
+            if (!(f & kFlDualGhost)) pd_dual_sm(S, i, f, P1, P2, Q1, Q2, sigma, acc, dp2);
+        }
+    };
+    for (int it = 0; it < iters; ++it) {
+        const int l = it + 1;
+        const bool check = (l % C == 0) || l == iters;
+        const float* Ubi = (it & 1) ? Ub2 : Ub;   // u-bar of iterate it
+        float* Ubo = (it & 1) ? Ub : Ub2;         // u-bar of iterate l (pixels other blocks read)
+        if (!early) dp2 = 0.f;
+        else if (!grid_wait(h, nblocks, gen)) return -1;
+        float x[kGhostRegs];
+#pragma unroll
+        for (int j = 0; j < kGhostRegs; ++j) {
+            const int g = tid + j * nt;
+            x[j] = g < L.ng ? Ubi[gsrc[g]] : 0.f;
+        }
+        interior(pb, check, early ? iA : 0, nown);
+#pragma unroll
+        for (int j = 0; j < kGhostRegs; ++j) {
+            const int g = tid + j * nt;
+            if (g < L.ng) sm[gdst[g]] = x[j];
+        }
+        __syncthreads();
+        {
+            const float* P1 = sm + L.p1 + pb * L.nsp;
+            const float* P2 = sm + L.p2 + pb * L.nsp;
+            float* Q1 = sm + L.p1 + (1 - pb) * L.nsp;
+            float* Q2 = sm + L.p2 + (1 - pb) * L.nsp;
+            for (int e = tid; e < L.nbd + L.r; e += nt) {
+                const bool own = e < L.nbd;
+                const int i = own ? lbd[e] : nown + (e - L.nbd);
+                pd_dual_sm(S, i, flg[i], P1, P2, Q1, Q2, sigma, check && own, dp2);
+            }
+        }
+        pb ^= 1;
+        __syncthreads();
+        float du2 = 0.f;
+        {
+            const float* Q1 = sm + L.p1 + pb * L.nsp;
+            const float* Q2 = sm + L.p2 + pb * L.nsp;
+            const int sh = pb * L.nsp;
+            if (check)
+                for (int i = tid; i < nown; i += nt)
+                    pd_primal_sm(S, i, a0 + i, Q1, Q2, sh, tau, F, Ubo, true, du2);
+            else
+                for (int i = tid; i < nown; i += nt)
+                    pd_primal_sm(S, i, a0 + i, Q1, Q2, sh, tau, F, Ubo, false, du2);
+        }
+        double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
+        if (check) {
+            float px = du2, py = dp2;
+            block_sum2f<NT>(px, py, reinterpret_cast<float*>(s_red));
+            if (tid == 0) {
+                part[2 * blockIdx.x] = px;
+                part[2 * blockIdx.x + 1] = py;
+            }
+        }
+        grid_arrive(h, gen);
+        early = !check;   // (the last iteration is a check)
+        if (early) {
+            dp2 = 0.f;
+            interior(pb, (l + 1) % C == 0 || l + 1 == iters, 0, iA);
+            continue;
+        }
+        if (!grid_wait(h, nblocks, gen)) return -1;
+        if (tol > 0.0 || blockIdx.x == 0) {
+            if (tid < 32) {
+                double sx, sy;
+                sum_partials_warp0(part, (int)nblocks, sx, sy);
+                if (tid == 0) {
+                    const bool stop = tol > 0.0 && fmax(sx, sy) <= tol * tol;
+                    s_red[0] = stop ? 1.0 : 0.0;
+                    if (blockIdx.x == 0) {
+                        h->du2 = sx;
+                        h->dv2 = sy;
+                        h->last_check = l;
+                        if (stop) {
+                            h->iters_done = l;
+                            h->done = 1;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            const bool stop = s_red[0] != 0.0;
+            __syncthreads();
+            if (stop) {
+                lf = l;
+                break;
+            }
+        }
+        ++chk;
+    }
+    __syncthreads();
+    // the final iterate: u and p of every own pixel, in the buffers of iterate lf
+    float* Uf = (lf & 1) ? U1 : U0;
+    float* G1 = (lf & 1) ? P1b : P1a;
+    float* G2 = (lf & 1) ? P2b : P2a;
+    const int fb = lf & 1;
+    for (int i = tid; i < nown; i += nt) {
+        Uf[a0 + i] = sm[L.u + i];
+        G1[a0 + i] = sm[L.p1 + fb * L.nsp + i];
+        G2[a0 + i] = sm[L.p2 + fb * L.nsp + i];
+    }
+    return 1;
+}
+
+// Which primal-dual kernel runs a solve (both are launched; the other returns
+// at once): the shared-memory one (one block per SM, grid1 blocks) while its
+// blocks' pixels are few enough for their state to fit, else k_solve_pd.
+constexpr int kPdSmemPerBlock = 6000;
+__device__ __forceinline__ bool pd_smem(int n, int grid1) {
+    return (n + grid1 - 1) / grid1 <= kPdSmemPerBlock;
+}
+
+__global__ void __launch_bounds__(kPdThreads, 2)
+k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
+           const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
+           float* P1a, float* P1b, float* P2a, float* P2b, float* U0, float* U1, float* Ub, float* Ub2,
+           const float* __restrict__ F, double* partials, WsHeader* h, int grid1) {
+    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
+    if (*(volatile int*)&h->done) return;
+    const int n = counts[1];
+    if (pd_smem(n, grid1)) return;
+    unsigned gen = 0;
+    pd_iterations<kPdThreads>(iters, check_every, tol, sigma, tau, n, nb, stride, P1a, P1b, P2a, P2b, U0, U1,
+                              Ub, F, partials, h, s_red, gen);
+}
+
+__global__ void __launch_bounds__(kPdThreads, 1)
+k_solve_pd_sm(int iters, int check_every, double tol, float sigma, float tau,
+              const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
+              float* P1a, float* P1b, float* P2a, float* P2b, float* U0, float* U1, float* Ub, float* Ub2,
+              const float* __restrict__ F, double* partials, WsHeader* h, int grid1) {
+    __shared__ double s_red[66];
+    extern __shared__ __align__(16) unsigned char c_smem[];
+    if (*(volatile int*)&h->done) return;
+    const int n = counts[1];
+    if (!pd_smem(n, grid1)) return;
+    unsigned gen = 0;
+    const int r = pd_solve_sm<kPdThreads>(iters, check_every, tol, sigma, tau, n, nb, stride, P1a, P1b, P2a,
+                                          P2b, U0, U1, Ub, Ub2, F, partials, h, s_red, c_smem, gen);
+    if (r == 0)   // some block's state does not fit: the global-memory iteration, one block per SM
+        pd_iterations<kPdThreads>(iters, check_every, tol, sigma, tau, n, nb, stride, P1a, P1b, P2a, P2b, U0,
+                                  U1, Ub, F, partials, h, s_red, gen);
 }
 
 // Dense u, p1, p2 of the final primal-dual iterate (fixed values outside RD).
@@ -2927,13 +3333,25 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
     SEG_LAUNCHED("k_compact_gather");
 
     const void* kern = (const void*)k_solve_pd;
-    int per_sm = 0;
+    const void* kern1 = (const void*)k_solve_pd_sm;
+    static bool smem_attr = false;
+    if (!smem_attr) {
+        SEG_TRY_CUDA(cudaFuncSetAttribute(kern1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)compact_smem(kPdThreads)));
+        smem_attr = true;
+    }
+    int per_sm = 0, per_sm1 = 0;
     SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPdThreads, 0));
-    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_pd cannot be resident");
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, kern1, kPdThreads,
+                                                               compact_smem(kPdThreads)));
+    if (per_sm <= 0 || per_sm1 <= 0) return fail(SEG_ERR_CUDA, "k_solve_pd cannot be resident");
     const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)H * W));
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
                                       std::max<int64_t>(1, (most + kPdThreads - 1) / kPdThreads));
     grid = (int)std::min<int64_t>(grid, L.npartials / 2);
+    // the shared-memory kernel: one block per SM (at most), the same decision
+    // (pd_smem) in both kernels from grid1
+    int grid1 = (int)std::min<int64_t>((int64_t)per_sm1 * sm_count(), L.npartials / 2);
     int iters = prm->iters, ce = test_interval(prm->tol, prm->check_every, prm->iters);
     double tol = prm->tol;
     float sigma = (float)prm->sigma, tau = (float)prm->tau;
@@ -2947,10 +3365,14 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
     float* U0 = S.u;
     float* U1 = S.w;
     float* Ub = S.up;
+    float* Ub2 = S.w2;   // the second u-bar buffer of the shared-memory kernel
     const float* F = S.f;
     void* args[] = {&iters, &ce, &tol, &sigma, &tau, (void*)&cnt, (void*)&nbp, &stride, &P1a, &P1b,
-                    &P2a, &P2b, &U0, &U1, &Ub, (void*)&F, &partials, &h};
+                    &P2a, &P2b, &U0, &U1, &Ub, &Ub2, (void*)&F, &partials, &h, &grid1};
     if (iters > 0) {
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern1, dim3(grid1), dim3(kPdThreads), args,
+                                                 compact_smem(kPdThreads), s));
+        count_launch();
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kPdThreads), args, 0, s));
         count_launch();
     }

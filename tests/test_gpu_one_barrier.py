@@ -5,9 +5,10 @@ step of the ring of pixels other blocks own directly above or left of its
 own, so one grid barrier ends an iteration.  Covered here: that every block
 ran it, the Section 4 stopping test (decided in every block), warm start, and
 the checkpoints of the differentiable forward (through the adjoint, against
-the oracle's reverse mode on a crop).  Parity against the oracle on sampled
-crops and against the dense solver on the whole image is in
-test_gpu_parity.py."""
+the oracle's reverse mode on a crop), and the primal-dual solver's
+shared-memory iteration built the same way.  Parity against the oracle on
+sampled crops and against the dense solver on the whole image is in
+test_gpu_parity.py (test_gpu_pd.py for the primal-dual solver)."""
 import numpy as np
 import pytest
 import torch
@@ -119,3 +120,29 @@ def test_checkpoints_through_the_adjoint_on_a_crop(orc, f_ds):
     assert np.all(gf[~inner] == 0)
     d = gf[sl] - gf_o
     assert np.linalg.norm(d) <= 1e-3 * np.linalg.norm(gf_o), (np.linalg.norm(d), np.linalg.norm(gf_o))
+
+
+def test_primal_dual_stops_at_a_check_with_the_cold_iterate(f_ds):
+    """The primal-dual solver's shared-memory iteration on the same image:
+    a tolerance between two checks stops it at the right check, with the
+    bits of a cold solve of that many iterations."""
+    seg = seg_mod()
+    S = _solver(f_ds)
+    norms = []
+    for l in range(5, 155, 5):
+        st = S.solve_pd(LAM, iters=l, check_every=5).cpu().numpy()
+        norms.append(max(st[1], st[2]))
+        assert st[7] > 0, st
+    norms = np.array(norms)
+    k = next(k for k in range(6, len(norms)) if norms[:k].min() > 1.05 * norms[k])
+    tol = float(np.sqrt(norms[:k].min() * norms[k]))
+    stop = 5 * (k + 1)
+    S.solve_pd(LAM, iters=stop, check_every=5)
+    torch.cuda.synchronize()
+    ref = {n: seg.download(getattr(S, n)).copy() for n in ("u", "p1", "p2")}
+    st = S.solve_pd(LAM, iters=600, tol=tol, check_every=5).cpu().numpy()
+    torch.cuda.synchronize()
+    S.check_status()
+    assert int(st[0]) == stop and int(st[5]) == stop
+    for n in ref:
+        np.testing.assert_array_equal(seg.download(getattr(S, n)), ref[n], err_msg=n)

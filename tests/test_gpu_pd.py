@@ -122,6 +122,7 @@ def test_pd_full_size_sampled(orc):
     assert worst <= TOL_U
     assert np.all(np.hypot(out["p1"], out["p2"]) <= 1 + 1e-6)
     assert out["u"].min() >= 0 and out["u"].max() <= 1
+    assert out["stats"][7] > 0   # the shared-memory, one-barrier iteration ran
 
 
 def test_pd_argument_and_capacity_errors():
