@@ -1800,7 +1800,7 @@ __device__ __forceinline__ bool compact_solve_range(
 // independent problems, so their iterates do not depend on the grouping);
 // stats then hold the norms of the last test summed over the waves, i.e.
 // over the whole batch, as without waves.
-constexpr int kWavePerBlock = 5000;
+constexpr int kWavePerBlock = 6000;
 
 inline bool compact_waves(int nimg, double tol, int n_inner, const float* ckpt) {
     return nimg > 1 && !(tol > 0.0) && n_inner == 1 && ckpt == nullptr;
