@@ -146,3 +146,25 @@ def test_primal_dual_stops_at_a_check_with_the_cold_iterate(f_ds):
     assert int(st[0]) == stop and int(st[5]) == stop
     for n in ref:
         np.testing.assert_array_equal(seg.download(getattr(S, n)), ref[n], err_msg=n)
+
+
+def test_two_barrier_shared_memory_path_when_the_ring_does_not_fit(orc, f_ds):
+    """At |RD|/N = 0.225 (6,209 pixels per block at tile height 16) the
+    blocks' state fits in shared memory without the ring but not with it:
+    the grid vote sends every block to the two-barrier shared-memory
+    iteration.  Every pixel against the dense solver on the same domain."""
+    seg = seg_mod()
+    K, q = 40, 0.225
+    out = {}
+    for mode in ("compact", "dense"):
+        S = seg.Solver(H, W, tile_h=16, mode=mode)
+        S.f[:, :W].copy_(torch.from_numpy(f_ds))
+        S.domain(q=q)
+        st = S.solve(LAM, iters=K).cpu().numpy()
+        out[mode] = (_state(S), st)
+    blocks = torch.cuda.get_device_properties(0).multi_processor_count
+    st = out["compact"][1]
+    assert st[7] == 0 and st[6] == blocks, st
+    for k in ("u", "v", "p1", "p2"):
+        d = np.abs(out["compact"][0][k].astype(np.float64) - out["dense"][0][k])
+        assert d.max() <= 1e-4, (k, d.max())
