@@ -3334,12 +3334,8 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
 
     const void* kern = (const void*)k_solve_pd;
     const void* kern1 = (const void*)k_solve_pd_sm;
-    static bool smem_attr = false;
-    if (!smem_attr) {
-        SEG_TRY_CUDA(cudaFuncSetAttribute(kern1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)compact_smem(kPdThreads)));
-        smem_attr = true;
-    }
+    SEG_TRY_CUDA(cudaFuncSetAttribute(kern1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)compact_smem(kPdThreads)));
     int per_sm = 0, per_sm1 = 0;
     SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPdThreads, 0));
     SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, kern1, kPdThreads,
