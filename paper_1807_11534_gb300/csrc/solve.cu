@@ -894,17 +894,18 @@ __device__ __forceinline__ void dual_gh(const IterParams& P, int i, int a, uint8
     D.q2[i] = q2;
 }
 
+// Primal step of own pixel i (compact index a) with fa = theta lambda f(a).
 template <typename T>
-__device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, uint8_t fl, const PrimalView& Q,
-                                          T* V, const float* F, float* U, float* Up, float* Wg, bool check,
-                                          bool write_u, bool write_prev, uint32_t seed, float& du2,
-                                          float& dv2) {
+__device__ __forceinline__ void primal_gh_f(const IterParams& P, int i, int a, uint8_t fl, const PrimalView& Q,
+                                            T* V, float fa, float* U, float* Up, float* Wg, bool check,
+                                            bool write_u, bool write_prev, uint32_t seed, float& du2,
+                                            float& dv2) {
     const float q1 = Q.q1[i], q2 = Q.q2[i];
     const float q1u = Q.n1[Q.ou[i]], q2l = Q.n2[Q.ol[i]];
     const float vv = Store<T>::ld_rw(V, i) + Store<T>::vbias;
     const float div = (q1 - q1u) + (q2 - q2l);
     const float un = fmaf(-P.theta, div, vv);
-    const float vn = clamp01(un - __ldg(F + a));   // F = theta lambda f
+    const float vn = clamp01(un - fa);   // fa = theta lambda f at a
     const float vs = Store<T>::st_sr(V, i, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
                      Store<T>::vbias;
     const float wv = div - vs * P.inv_theta;
@@ -917,6 +918,15 @@ __device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, uin
     }
     if (write_prev) Up[a] = un;
     if (write_u) U[a] = un;
+}
+
+// The same with theta lambda f read from F.
+template <typename T>
+__device__ __forceinline__ void primal_gh(const IterParams& P, int i, int a, uint8_t fl, const PrimalView& Q,
+                                          T* V, const float* F, float* U, float* Up, float* Wg, bool check,
+                                          bool write_u, bool write_prev, uint32_t seed, float& du2,
+                                          float& dv2) {
+    primal_gh_f<T>(P, i, a, fl, Q, V, __ldg(F + a), U, Up, Wg, check, write_u, write_prev, seed, du2, dv2);
 }
 
 // Refills ghosts [g0, g1) from the global arrays: w for the neighbours below /
@@ -1237,6 +1247,19 @@ __device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const
     const int C = check_every;
     *lf = iters;
     bool early = false;   // this iteration's first interior pixels ran before the barrier
+    // theta lambda f of the thread's pixels (at most kFSlots), in registers
+    // for the whole solve: the primal step then reads no global memory
+    constexpr int kFSlots = 6;
+    const bool fslots = L.n <= kFSlots * NT;
+    float fr[kFSlots];
+    auto load_f = [&]() {
+#pragma unroll
+        for (int k = 0; k < kFSlots; ++k) {
+            const int a = a0 + tid + k * nt;
+            fr[k] = (fslots && a < a1) ? __ldg(F + a) : 0.f;
+        }
+    };
+    load_f();
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
         const float* Wi = (it & 1) ? Wc2 : Wc;   // w of iterate it
@@ -1294,8 +1317,25 @@ __device__ __forceinline__ bool compact_iterations_h1(const IterParams& P, const
         Q.ou = S.off + 2 * L.nE;
         Q.ol = S.off + 2 * L.nE + L.n;
         T* Vs = S.v();
-        // the common iteration (no test, no u output) without their branches
-        if (!check && !write_prev)
+        if (fslots) {
+            if (!check && !write_prev) {
+#pragma unroll
+                for (int k = 0; k < kFSlots; ++k) {
+                    const int a = a0 + tid + k * nt;
+                    if (a < a1)
+                        primal_gh_f(P, a - a0, a, S.fl[a - a0], Q, Vs, fr[k], U, Up, Wo, false, false, false, seed,
+                                    du2, dv2);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kFSlots; ++k) {
+                    const int a = a0 + tid + k * nt;
+                    if (a < a1)
+                        primal_gh_f(P, a - a0, a, S.fl[a - a0], Q, Vs, fr[k], U, Up, Wo, check, write_u, write_prev,
+                                    seed, du2, dv2);
+                }
+            }
+        } else if (!check && !write_prev)
             each([&](int a) {
                 primal_gh(P, a - a0, a, S.fl[a - a0], Q, Vs, F, U, Up, Wo, false, false, false, seed, du2, dv2);
             });
@@ -2884,16 +2924,16 @@ __device__ __forceinline__ void pd_dual_sm(const PdSmem& S, int i, uint8_t fl, c
 }
 
 // Primal step of own pixel i (compact index a): u' = clip(u + tau div p' -
-// tau lambda f), u-bar' = 2u' - u (exported when other blocks read it).
+// tau lambda f), u-bar' = 2u' - u (exported when other blocks read it); fa
+// = tau lambda f(a).
 __device__ __forceinline__ void pd_primal_sm(const PdSmem& S, int i, int a, const float* Q1, const float* Q2,
-                                             int sh, float tau, const float* __restrict__ F, float* Ubo,
-                                             bool check, float& du2) {
+                                             int sh, float tau, float fa, float* Ubo, bool check, float& du2) {
     const float q1 = Q1[i], q2 = Q2[i];
     const float q1u = S.sm[S.off[2 * S.L.nE + i] + sh], q2l = S.sm[S.off[2 * S.L.nE + S.L.n + i] + sh];
     const float div = (q1 - q1u) + (q2 - q2l);
     float* U = S.sm + S.L.u;
     const float uo = U[i];
-    const float un = clamp01(fmaf(tau, div, uo) - __ldg(F + a));   // F = tau lambda f
+    const float un = clamp01(fmaf(tau, div, uo) - fa);   // fa = tau lambda f at a
     U[i] = un;
     const float ubn = fmaf(2.f, un, -uo);
     S.sm[S.L.ub + i] = ubn;
@@ -3074,6 +3114,16 @@ __device__ __forceinline__ int pd_solve_sm(int iters, int check_every, double to
     int pb = 0, chk = 0, lf = iters;
     float dp2 = 0.f;
     bool early = false;
+    // tau lambda f of the thread's pixels (at most kFSlots), in registers for
+    // the whole solve
+    constexpr int kFSlots = 6;
+    const bool fslots = nown <= kFSlots * NT;
+    float fr[kFSlots];
+#pragma unroll
+    for (int k = 0; k < kFSlots; ++k) {
+        const int i = tid + k * nt;
+        fr[k] = (fslots && i < nown) ? __ldg(F + a0 + i) : 0.f;
+    }
     // interior dual steps (no ghost read) of own pixels [i0, i1)
     auto interior = [&](int b, bool acc, int i0, int i1) {
         const float* P1 = sm + L.p1 + b * L.nsp;
@@ -3123,12 +3173,27 @@ __device__ __forceinline__ int pd_solve_sm(int iters, int check_every, double to
             const float* Q1 = sm + L.p1 + pb * L.nsp;
             const float* Q2 = sm + L.p2 + pb * L.nsp;
             const int sh = pb * L.nsp;
-            if (check)
+            if (fslots) {
+                if (check) {
+#pragma unroll
+                    for (int k = 0; k < kFSlots; ++k) {
+                        const int i = tid + k * nt;
+                        if (i < nown) pd_primal_sm(S, i, a0 + i, Q1, Q2, sh, tau, fr[k], Ubo, true, du2);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kFSlots; ++k) {
+                        const int i = tid + k * nt;
+                        if (i < nown) pd_primal_sm(S, i, a0 + i, Q1, Q2, sh, tau, fr[k], Ubo, false, du2);
+                    }
+                }
+            } else if (check) {
                 for (int i = tid; i < nown; i += nt)
-                    pd_primal_sm(S, i, a0 + i, Q1, Q2, sh, tau, F, Ubo, true, du2);
-            else
+                    pd_primal_sm(S, i, a0 + i, Q1, Q2, sh, tau, __ldg(F + a0 + i), Ubo, true, du2);
+            } else {
                 for (int i = tid; i < nown; i += nt)
-                    pd_primal_sm(S, i, a0 + i, Q1, Q2, sh, tau, F, Ubo, false, du2);
+                    pd_primal_sm(S, i, a0 + i, Q1, Q2, sh, tau, __ldg(F + a0 + i), Ubo, false, du2);
+            }
         }
         double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
         if (check) {
