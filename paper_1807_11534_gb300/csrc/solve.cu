@@ -436,8 +436,8 @@ __device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, flo
 //  * everything in global memory.
 constexpr int kBackwardThreads = 512;   // block size of the persistent reverse sweep (4 per SM)
 // dynamic shared memory of the persistent solver: one or two blocks per SM
-constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 110 * 1024; }
-constexpr int kCompactThreads = 1024;   // one block per SM
+constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 112 * 1024; }
+constexpr int kCompactThreads = 512;   // two blocks per SM: one block's block barriers overlap the other's work
 constexpr int kCompactWideUnroll = 2;   // pixels per thread in flight in k_solve_compact_wide
 constexpr int kCompactUnroll = 4;       // pixels per thread in flight in the two-phase iteration
 constexpr int kFusePerThread = 3;       // fused iteration up to this many pixels per thread
@@ -1602,15 +1602,16 @@ __device__ __forceinline__ int compact_solve_h1(
 }
 
 // Which of the two persistent compact kernels runs a solve (both are
-// launched; the other returns at once).  The shared-memory kernel (one
-// block per SM, grid1 blocks) unless even its table rows would not fit in
-// shared memory -- then every block would take the global-memory path, and
-// k_solve_compact_wide, the same path at two blocks per SM (twice the warps
-// to hide the latency of the table and neighbour loads), runs instead.
+// launched; the other returns at once).  The shared-memory kernel (two
+// 512-thread blocks per SM, grid1 blocks) unless even its table rows would
+// not fit in shared memory -- then every block would take the global-memory
+// path, and k_solve_compact_wide, the same path at four 512-thread blocks
+// per SM (twice the warps to hide the latency of the table and neighbour
+// loads), runs instead.
 template <typename T>
 __device__ __forceinline__ bool compact_wide(int n, int grid1) {
     const int64_t per1 = ((int64_t)n + grid1 - 1) / grid1;
-    return (size_t)per1 * (4 * NB_UUR + sizeof(T)) > compact_smem(1024);
+    return (size_t)per1 * (4 * NB_UUR + sizeof(T)) > compact_smem(kCompactThreads);
 }
 
 // All iterations of the compact solve over the RD pixels [w0, w0 + n) (the
@@ -1840,7 +1841,7 @@ __device__ __forceinline__ bool compact_solve_range(
 // independent problems, so their iterates do not depend on the grouping);
 // stats then hold the norms of the last test summed over the waves, i.e.
 // over the whole batch, as without waves.
-constexpr int kWavePerBlock = 6000;
+constexpr int kWavePerBlock = 3000;
 
 inline bool compact_waves(int nimg, double tol, int n_inner, const float* ckpt) {
     return nimg > 1 && !(tol > 0.0) && n_inner == 1 && ckpt == nullptr;
@@ -1891,7 +1892,7 @@ k_solve_compact(IterParams P, int iters, int n_inner, int check_every, double to
     }
 }
 
-// The global-memory path of k_solve_compact at two blocks per SM (32
+// The global-memory path of k_solve_compact at twice its blocks per SM (32
 // registers a thread), for solves too large for the shared-memory paths.
 template <typename T, int NT, int UNROLL>
 __global__ void __launch_bounds__(NT, 2048 / NT)

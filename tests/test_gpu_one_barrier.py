@@ -58,8 +58,10 @@ def test_every_block_runs_one_barrier_and_stops_at_a_check(f_ds):
     for l in range(5, 155, 5):
         st = S.solve(LAM, iters=l, check_every=5).cpu().numpy()
         norms.append(max(st[1], st[2]))
-        blocks = torch.cuda.get_device_properties(0).multi_processor_count
-        assert st[6] == blocks and st[7] == blocks, st   # shared-memory state, one barrier, every block
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        # shared-memory state and one barrier in every block of the grid
+        # (a whole number of blocks per SM)
+        assert st[6] == st[7] and st[6] >= sms and st[6] % sms == 0, st
     norms = np.array(norms)
     # tol between a check that sets a new low by more than 5 % and the lowest before it
     k = next(k for k in range(6, len(norms)) if norms[:k].min() > 1.05 * norms[k])
@@ -149,8 +151,9 @@ def test_primal_dual_stops_at_a_check_with_the_cold_iterate(f_ds):
 
 
 def test_two_barrier_shared_memory_path_when_the_ring_does_not_fit(orc, f_ds):
-    """At |RD|/N = 0.225 (6,209 pixels per block at tile height 16) the
-    blocks' state fits in shared memory without the ring but not with it:
+    """At |RD|/N = 0.225 (3,105 pixels per 512-thread block at tile height
+    16) the blocks' state fits in shared memory without the ring but not
+    with it:
     the grid vote sends every block to the two-barrier shared-memory
     iteration.  Every pixel against the dense solver on the same domain."""
     seg = seg_mod()
@@ -162,9 +165,9 @@ def test_two_barrier_shared_memory_path_when_the_ring_does_not_fit(orc, f_ds):
         S.domain(q=q)
         st = S.solve(LAM, iters=K).cpu().numpy()
         out[mode] = (_state(S), st)
-    blocks = torch.cuda.get_device_properties(0).multi_processor_count
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     st = out["compact"][1]
-    assert st[7] == 0 and st[6] == blocks, st
+    assert st[7] == 0 and st[6] >= sms and st[6] % sms == 0, st
     for k in ("u", "v", "p1", "p2"):
         d = np.abs(out["compact"][0][k].astype(np.float64) - out["dense"][0][k])
         assert d.max() <= 1e-4, (k, d.max())
