@@ -41,7 +41,7 @@ BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + 
 # delta = 0.2, float32), summarised in profiles/k_solve_compact_ds2048.md.
 # The iteration state is held on chip, so this is far below the algorithmic
 # bytes.
-COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (1283840 + 10486784) / 50}
+COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (1525760 + 11108864) / 50}
 
 
 def parse():
