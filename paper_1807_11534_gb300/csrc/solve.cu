@@ -2761,6 +2761,7 @@ extern "C" seg_status seg_backward(const float* f, int H, int W, int ld, const u
 // arrays: p1[0..1], p2[0..1], u (U0), w (U1), up (ubar), f.
 
 constexpr int kPdThreads = 1024;   // two blocks per SM (32 registers): latency-bound loads
+constexpr int kPdSmThreads = 512;  // the shared-memory kernel: two blocks per SM, 112 KB each
 
 __device__ __forceinline__ float pd_fixed(int code) { return code == kNbFg ? 1.f : 0.f; }
 
@@ -3256,9 +3257,9 @@ __device__ __forceinline__ int pd_solve_sm(int iters, int check_every, double to
 }
 
 // Which primal-dual kernel runs a solve (both are launched; the other returns
-// at once): the shared-memory one (one block per SM, grid1 blocks) while its
+// at once): the shared-memory one (two blocks per SM, grid1 blocks) while its
 // blocks' pixels are few enough for their state to fit, else k_solve_pd.
-constexpr int kPdSmemPerBlock = 6000;
+constexpr int kPdSmemPerBlock = 3000;
 __device__ __forceinline__ bool pd_smem(int n, int grid1) {
     return (n + grid1 - 1) / grid1 <= kPdSmemPerBlock;
 }
@@ -3277,7 +3278,7 @@ k_solve_pd(int iters, int check_every, double tol, float sigma, float tau,
                               Ub, F, partials, h, s_red, gen);
 }
 
-__global__ void __launch_bounds__(kPdThreads, 1)
+__global__ void __launch_bounds__(kPdSmThreads, 2)
 k_solve_pd_sm(int iters, int check_every, double tol, float sigma, float tau,
               const int32_t* __restrict__ counts, const int32_t* __restrict__ nb, int64_t stride,
               float* P1a, float* P1b, float* P2a, float* P2b, float* U0, float* U1, float* Ub, float* Ub2,
@@ -3288,10 +3289,10 @@ k_solve_pd_sm(int iters, int check_every, double tol, float sigma, float tau,
     const int n = counts[1];
     if (!pd_smem(n, grid1)) return;
     unsigned gen = 0;
-    const int r = pd_solve_sm<kPdThreads>(iters, check_every, tol, sigma, tau, n, nb, stride, P1a, P1b, P2a,
+    const int r = pd_solve_sm<kPdSmThreads>(iters, check_every, tol, sigma, tau, n, nb, stride, P1a, P1b, P2a,
                                           P2b, U0, U1, Ub, Ub2, F, partials, h, s_red, c_smem, gen);
-    if (r == 0)   // some block's state does not fit: the global-memory iteration, one block per SM
-        pd_iterations<kPdThreads>(iters, check_every, tol, sigma, tau, n, nb, stride, P1a, P1b, P2a, P2b, U0,
+    if (r == 0)   // some block's state does not fit: the global-memory iteration, in this grid
+        pd_iterations<kPdSmThreads>(iters, check_every, tol, sigma, tau, n, nb, stride, P1a, P1b, P2a, P2b, U0,
                                   U1, Ub, F, partials, h, s_red, gen);
 }
 
@@ -3401,17 +3402,17 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
     const void* kern = (const void*)k_solve_pd;
     const void* kern1 = (const void*)k_solve_pd_sm;
     SEG_TRY_CUDA(cudaFuncSetAttribute(kern1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)compact_smem(kPdThreads)));
+                                      (int)compact_smem(kPdSmThreads)));
     int per_sm = 0, per_sm1 = 0;
     SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPdThreads, 0));
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, kern1, kPdThreads,
-                                                               compact_smem(kPdThreads)));
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, kern1, kPdSmThreads,
+                                                               compact_smem(kPdSmThreads)));
     if (per_sm <= 0 || per_sm1 <= 0) return fail(SEG_ERR_CUDA, "k_solve_pd cannot be resident");
     const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)H * W));
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
                                       std::max<int64_t>(1, (most + kPdThreads - 1) / kPdThreads));
     grid = (int)std::min<int64_t>(grid, L.npartials / 2);
-    // the shared-memory kernel: one block per SM (at most), the same decision
+    // the shared-memory kernel: two blocks per SM (at most), the same decision
     // (pd_smem) in both kernels from grid1
     int grid1 = (int)std::min<int64_t>((int64_t)per_sm1 * sm_count(), L.npartials / 2);
     int iters = prm->iters, ce = test_interval(prm->tol, prm->check_every, prm->iters);
@@ -3432,8 +3433,8 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
     void* args[] = {&iters, &ce, &tol, &sigma, &tau, (void*)&cnt, (void*)&nbp, &stride, &P1a, &P1b,
                     &P2a, &P2b, &U0, &U1, &Ub, &Ub2, (void*)&F, &partials, &h, &grid1};
     if (iters > 0) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern1, dim3(grid1), dim3(kPdThreads), args,
-                                                 compact_smem(kPdThreads), s));
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern1, dim3(grid1), dim3(kPdSmThreads), args,
+                                                 compact_smem(kPdSmThreads), s));
         count_launch();
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kPdThreads), args, 0, s));
         count_launch();
