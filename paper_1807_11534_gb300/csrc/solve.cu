@@ -422,13 +422,17 @@ __device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, flo
 //   primal phase u', v', w', stop-test partials          -> barrier
 //   (check iterations) block 0 sums the partials in a fixed order and raises
 //   the done flag, which every block reads after the next barrier.
-// Each block takes the first of these that applies (blocks may differ; all
-// keep the same barrier protocol and the same global arrays current):
+// The grid takes one of these (the same in every block):
 //  * fused (n_inner = 1, few pixels per thread): one phase and one barrier
 //    per iteration; the thread of x also redoes the dual steps of x - e1 and
 //    x - e2 (same inputs, same arithmetic, same rounding as their owners),
 //    which is all the v-step of x needs, and w is ping-ponged.  The iterates
 //    are bit-identical to the two-phase ones.
+//  * one barrier with shared-memory state and a ring (n_inner = 1, every
+//    block's state fits, by a grid-wide vote): see compact_iterations_h1.
+// Otherwise each block takes the first of these that applies (blocks may
+// differ; all keep the same two-barrier protocol and the same global arrays
+// current):
 //  * shared-memory state (n_inner = 1, the block's pixels fit): see
 //    compact_iterations_gh below.
 //  * neighbour-table rows and v in shared memory, neighbour values from the
