@@ -20,16 +20,23 @@ constexpr int kMarkerChunk = 1024;
 __global__ void k_label_sums(const float* __restrict__ z, const uint8_t* __restrict__ label,
                              int H, int W, int ld, double* __restrict__ red) {
     __shared__ double s[4][kFitThreads];
-    double s1 = 0, s0 = 0, n1 = 0, n0 = 0;
+    double s1 = 0, s0 = 0;
+    unsigned c1 = 0, c0 = 0;
     int64_t n = (int64_t)H * W;
+    // both sums take an addition per pixel (0 for the other class: exact, so
+    // the sums are those of the class's pixels in the same order), with no
+    // divergence between the classes
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = (int64_t)((uint32_t)x / (uint32_t)W), j = x - i * W;   // x < 2^31
-        double zz = (double)z[i * ld + j];
-        if (label[i * ld + j]) { s1 = __dadd_rn(s1, zz); n1 += 1.0; }
-        else                   { s0 = __dadd_rn(s0, zz); n0 += 1.0; }
+        const double zz = (double)z[i * ld + j];
+        const bool in = label[i * ld + j] != 0;
+        s1 = __dadd_rn(s1, in ? zz : 0.0);
+        s0 = __dadd_rn(s0, in ? 0.0 : zz);
+        c1 += in ? 1u : 0u;
+        c0 += in ? 0u : 1u;
     }
-    s[0][threadIdx.x] = s1; s[1][threadIdx.x] = s0; s[2][threadIdx.x] = n1; s[3][threadIdx.x] = n0;
+    s[0][threadIdx.x] = s1; s[1][threadIdx.x] = s0; s[2][threadIdx.x] = (double)c1; s[3][threadIdx.x] = (double)c0;
     __syncthreads();
     for (int w = kFitThreads / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
@@ -66,16 +73,20 @@ __global__ void k_keep_c(WsHeader* h, double* c_out) {
 __global__ void k_class_sums(const float* __restrict__ z, const float* __restrict__ u, float thresh,
                              int H, int W, int ld, double* __restrict__ red) {
     __shared__ double s[4][kFitThreads];
-    double s1 = 0, s0 = 0, n1 = 0, n0 = 0;
+    double s1 = 0, s0 = 0;
+    unsigned c1 = 0, c0 = 0;
     int64_t n = (int64_t)H * W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = (int64_t)((uint32_t)x / (uint32_t)W), j = x - i * W;   // x < 2^31
-        double zz = (double)z[i * ld + j];
-        if (u[i * ld + j] > thresh) { s1 = __dadd_rn(s1, zz); n1 += 1.0; }
-        else                        { s0 = __dadd_rn(s0, zz); n0 += 1.0; }
+        const double zz = (double)z[i * ld + j];
+        const bool in = u[i * ld + j] > thresh;   // as k_label_sums: branch-free, exact
+        s1 = __dadd_rn(s1, in ? zz : 0.0);
+        s0 = __dadd_rn(s0, in ? 0.0 : zz);
+        c1 += in ? 1u : 0u;
+        c0 += in ? 0u : 1u;
     }
-    s[0][threadIdx.x] = s1; s[1][threadIdx.x] = s0; s[2][threadIdx.x] = n1; s[3][threadIdx.x] = n0;
+    s[0][threadIdx.x] = s1; s[1][threadIdx.x] = s0; s[2][threadIdx.x] = (double)c1; s[3][threadIdx.x] = (double)c0;
     __syncthreads();
     for (int w = kFitThreads / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
