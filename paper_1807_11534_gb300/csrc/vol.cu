@@ -69,7 +69,7 @@ __device__ __forceinline__ VolBuf vol_buf(const VolState& S, int b) {
     return b ? VolBuf{S.p[1][0], S.p[1][1], S.p[1][2]} : VolBuf{S.p[0][0], S.p[0][1], S.p[0][2]};
 }
 
-constexpr int kVolThreads = 1024;   // two blocks per SM (32 registers): latency-bound loads
+constexpr int kVolThreads = 512;   // four blocks per SM (32 registers): latency-bound loads
 constexpr int kVolArrays = 11 + VN_COUNT;
 constexpr int64_t kVolSlack = 256;
 
@@ -249,7 +249,7 @@ __device__ __forceinline__ void vol_primal(const VolGeom& G, float* U, const Vol
     if (write_u) U[__ldg(S.off + k)] = un;
 }
 
-__global__ void __launch_bounds__(kVolThreads, 2)
+__global__ void __launch_bounds__(kVolThreads, 4)
 k_solve_vol(VolGeom G, int iters, int check_every, double tol, const int32_t* __restrict__ counts, float* U,
             VolState S, double* partials, WsHeader* h) {
     __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
