@@ -444,7 +444,10 @@ constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 112 * 1
 constexpr int kCompactThreads = 512;   // two blocks per SM: one block's block barriers overlap the other's work
 constexpr int kCompactWideUnroll = 2;   // pixels per thread in flight in k_solve_compact_wide
 constexpr int kCompactUnroll = 4;       // pixels per thread in flight in the two-phase iteration
-constexpr int kFusePerThread = 3;       // fused iteration up to this many pixels per thread
+// fused iteration up to this many pixels per thread: 0, i.e. only for an
+// empty range (the one-barrier ring path measured faster at every size
+// tried, 0.6 to 5 pixels per thread)
+constexpr int kFusePerThread = 0;
 
 // Own-pixel arrays (neighbour-table rows, v) of the pixels a block updates:
 // SH, copies in shared memory indexed from the block's first pixel a0; else
