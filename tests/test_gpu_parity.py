@@ -353,10 +353,10 @@ def test_full_size_2048_ds_sampled(orc, mode, delta):
     configuration: K iterations on the GPU, then the oracle on crops of
     radius 2K+4 around sampled pixels (the iteration's domain of dependence
     grows by 2 pixels per iteration, so the crop centre is exact).  At
-    delta = 0.1 (237K RD pixels) the compact solver takes its fused
-    iteration, at 0.2 (863K, the benchmark's delta) the two-phase iteration
-    with shared-memory state, ghost words at block borders, and the final
-    write-back of pixels no other block reads."""
+    delta = 0.1 (237K RD pixels) and 0.2 (863K, the benchmark's delta) the
+    compact solver takes its one-barrier iteration with shared-memory state,
+    a ring of recomputed border pixels, ghost words and the final write-back
+    of pixels no other block reads."""
     seg = seg_mod()
     P = synth.ellipses_ds(seed=0, H=2048, W=2048)
     c1, c2 = orc.class_means(P.z, P.label)
@@ -379,8 +379,8 @@ def test_full_size_2048_ds_sampled(orc, mode, delta):
 @pytest.mark.slow
 @pytest.mark.parametrize("delta", [0.1, 0.2, 0.3])
 def test_compact_matches_dense_on_the_whole_image(orc, delta):
-    """Every pixel of the 2048x2048 workload: the compact solver (fused
-    iteration at delta = 0.1, shared-memory state with ghost words at 0.2,
+    """Every pixel of the 2048x2048 workload: the compact solver (the
+    one-barrier shared-memory iteration at delta = 0.1 and 0.2, the
     global-memory neighbour table at 0.3) against the dense solver run on the
     same restricted domain, itself checked against the oracle above; both
     are float32 iterations of the same steps."""
