@@ -1634,8 +1634,8 @@ __device__ __forceinline__ bool compact_solve_range(
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = w0 + (int)blockIdx.x * per, a1 = min(w0 + n, a0 + per);
     const int tid = threadIdx.x, nt = NT;
-    // the fused iteration pays off while barriers dominate, i.e. with few
-    // pixels per thread; the two-phase one reads six table rows, not eight
+    // the fused iteration (eight table rows) up to kFusePerThread pixels per
+    // thread; the other paths read six
     const int fuse = n_inner == 1 && per <= kFusePerThread * NT;
     const int rows = fuse ? NB_COUNT : NB_UUR;
     if (n_inner == 1 && !fuse) {
