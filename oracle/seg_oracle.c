@@ -21,10 +21,16 @@
  *    not say how many); the sweeps are Jacobi (all of RD from the same p^n).
  *  - The stopping norm of Section 4 is the Euclidean norm over all pixels.
  *
- * parity unpinned: the values of the restricted solution for 0 < q-hat < inf
- * have no closed form; they are pinned only through the special cases and
- * invariants the tests check (q-hat = 0, q-hat = inf, |p| <= 1, v in [0,1],
- * large lambda, the disk, the 1-D ROF sub-problem, weak duality).
+ * The restricted solution for 0 < q-hat < inf has no closed form.  It is
+ * pinned by what it minimises: Section 3's u-step keeps rho = 0 off RD (so
+ * only RD's |grad u| terms remain in TV) and evaluates the rho equation at RD
+ * points with the fixed v of Fg / Bg, so the converged iterate minimises
+ *   E_R(u, v) = sum_RD |grad u| + (1/2 theta) sum_all (u - v)^2
+ *               + lambda sum_RD f v,   v = H(-f) off RD, u free everywhere
+ * (u off RD is an auxiliary value the method never reports), which the tests
+ * compare with an independent minimiser; also by the special cases and
+ * invariants (q-hat = 0, q-hat = inf, |p| <= 1, v in [0,1], large lambda, the
+ * disk, the 1-D ROF sub-problem, weak duality).
  */
 #include "seg_oracle.h"
 

@@ -339,6 +339,99 @@ def test_iteration_reaches_the_df_minimum(orc, seed, lam):
     assert abs(e["edf"] - emin) <= 1e-5 * max(1.0, abs(emin))
 
 
+def _restricted_min(f, region, lam, theta, eps):
+    """Independent minimiser (scipy L-BFGS-B, TV smoothed by continuation as
+    in _smoothed_min) of the energy whose alternating minimisation is the
+    restricted iteration of Section 3:
+
+        E_R(u, v) = sum_{x in RD} |grad u(x)| + (1/2 theta) sum_{all x} (u - v)^2
+                    + lambda sum_{x in RD} f v,
+
+    with v = H(-f) held on Fg and Bg, v in [0, 1] on RD, and u free at every
+    pixel.  rho = 0 off RD keeps only RD's |grad u| terms (the dual of
+    sum_RD |grad u| is <u, div rho> over rho supported on RD), and the rho
+    equation evaluated at RD points reads theta div rho - v at fixed
+    neighbours too, so the u of this energy off RD is v - theta div rho, an
+    auxiliary value the method never reports (it reports the fixed 0 / 1
+    there).  Returns (min, u, v)."""
+    minimize = pytest.importorskip("scipy.optimize").minimize
+    H, W = f.shape
+    N = H * W
+    rdm = region == 2
+    rd = rdm.ravel()
+    nr = int(rd.sum())
+    vfix = (region == 1).astype(np.float64).ravel()
+    fr = f.astype(np.float64).ravel()[rd]
+
+    def obj(x, e):
+        u = x[:N].reshape(H, W)
+        v = vfix.copy()
+        v[rd] = x[N:]
+        a = np.zeros_like(u); a[:-1] = u[1:] - u[:-1]
+        b = np.zeros_like(u); b[:, :-1] = u[:, 1:] - u[:, :-1]
+        r = np.sqrt(a * a + b * b + e * e)
+        ga = np.where(rdm, a / r, 0.0)
+        gb = np.where(rdm, b / r, 0.0)
+        g = np.zeros_like(u)
+        g[1:] += ga[:-1]; g[:-1] -= ga[:-1]
+        g[:, 1:] += gb[:, :-1]; g[:, :-1] -= gb[:, :-1]
+        d = x[:N] - v
+        val = r[rdm].sum() + 0.5 * np.dot(d, d) / theta + lam * np.dot(fr, x[N:])
+        return val, np.concatenate([g.ravel() + d / theta, -d[rd] / theta + lam * fr])
+
+    x = np.concatenate([vfix, np.full(nr, 0.5)])
+    bounds = [(None, None)] * N + [(0, 1)] * nr
+    e = 1e-2
+    while True:
+        res = minimize(obj, x, args=(e,), jac=True, method="L-BFGS-B", bounds=bounds,
+                       options=dict(maxiter=200000, maxfun=400000, ftol=1e-16, gtol=1e-13,
+                                    maxcor=50))
+        x = res.x
+        if e <= eps:
+            break
+        e = max(eps, e / 10)
+    v = vfix.copy()
+    v[rd] = x[N:]
+    return res.fun, x[:N].reshape(H, W), v.reshape(H, W)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("delta", [0.1, 0.3])
+def test_restricted_iteration_reaches_the_restricted_minimum(orc, seed, delta):
+    """Section 3 for 0 < q-hat < inf: at convergence the restricted iterate
+    (u, v on RD) is the minimiser of E_R (see _restricted_min), found
+    independently by L-BFGS-B.  RD pixels here border fixed Fg and Bg
+    pixels on every side, so how a fixed neighbour enters the rho step (its
+    v, its div rho) and which |grad u| terms count are all exercised."""
+    rng = np.random.default_rng(20 + seed)
+    H, W = 8, 9
+    blk = np.zeros((H, W), bool)
+    blk[2:6, 2 + seed:6 + seed] = True
+    f = (np.where(blk, -0.4, 0.4) + rng.normal(0, 0.25, (H, W))).astype(np.float32)
+    reg = orc.domain(f, delta)
+    rd = reg == 2
+    assert 4 <= rd.sum() <= H * W // 2 and (reg == 1).any() and (reg == 0).any()
+    theta, lam, eps = 0.2, 2.0, 1e-7
+    st = orc.solve(f, reg, lam, theta, 0.125, iters=100000, tol=1e-13)
+    assert st.iters_done < 100000
+    emin, um, vm = _restricted_min(f, reg, lam, theta, eps)
+    np.testing.assert_allclose(st.u[rd], um[rd], rtol=0, atol=2e-5)
+    np.testing.assert_allclose(st.v[rd], vm[rd], rtol=0, atol=2e-5)
+    # E_R at the oracle's state (u off RD: the auxiliary v - theta div rho,
+    # with div written here by its definition as minus the adjoint of the
+    # forward difference): not below the smoothed minimum by more than the
+    # smoothing's N_RD eps, and not above it
+    d = np.zeros((H, W))
+    d[:-1, :] += st.p1[:-1, :]; d[1:, :] -= st.p1[:-1, :]
+    d[:, :-1] += st.p2[:, :-1]; d[:, 1:] -= st.p2[:, :-1]
+    u = np.where(rd, st.u, st.v - theta * d)
+    a = np.zeros_like(u); a[:-1] = u[1:] - u[:-1]
+    b = np.zeros_like(u); b[:, :-1] = u[:, 1:] - u[:, :-1]
+    er = (np.sqrt(a * a + b * b)[rd].sum() + 0.5 * np.sum((u - st.v) ** 2) / theta
+          + lam * np.sum(f.astype(np.float64)[rd] * st.v[rd]))
+    assert emin - rd.sum() * eps - 1e-9 <= er <= emin + 1e-7
+
+
 def test_tv_textbook_value(orc):
     """Isotropic discrete TV (forward differences): one raised pixel inside a
     3x3 image has TV = 2 + sqrt(2) (its own corner term is sqrt(1 + 1), the
