@@ -22,8 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "seg_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_OMP_PATH = os.path.join(_OUT_DIR, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp_lib = None
 
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
 
@@ -46,12 +48,56 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
-def _load():
-    global _lib
+def build_omp(force: bool = False) -> str | None:
+    """The same source compiled with -fopenmp into liboracle_omp.so: the
+    row and pixel loops of the solve run on all cores; every output element
+    is computed by the same operations as in the serial build and the
+    increments are summed per row, then over rows in order, so both builds
+    give identical bits.  Returns None when the compiler has no OpenMP."""
+    if os.environ.get("SEG_ORACLE_LIB"):
+        return None
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    hdr = os.path.join(_HERE, "seg_oracle.h")
+    if (not force and os.path.exists(_OMP_PATH)
+            and os.path.getmtime(_OMP_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
+        return _OMP_PATH
+    tmp = _OMP_PATH + f".tmp{os.getpid()}"
+    try:
+        subprocess.check_call(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"],
+                              stderr=subprocess.DEVNULL)
+    except (subprocess.CalledProcessError, OSError):
+        return None
+    os.replace(tmp, _OMP_PATH)
+    return _OMP_PATH
+
+
+def threads() -> int:
+    """Cores the OpenMP build uses (the process's CPU affinity, unless
+    OMP_NUM_THREADS says otherwise)."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    if env and env.isdigit():
+        return int(env)
+    return len(os.sched_getaffinity(0))
+
+
+def has_omp() -> bool:
+    return build_omp() is not None
+
+
+def _load(omp: bool = False):
+    global _lib, _omp_lib
     with _lock:
-        if _lib is not None:
+        if omp:
+            if _omp_lib is not None:
+                return _omp_lib
+            path = build_omp()
+            if path is None:
+                raise RuntimeError("the OpenMP build of the oracle is not available")
+        elif _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        else:
+            path = build()
+        lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
         I, L, D, F = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_float
         lib.oracle_fitting.argtypes = [P, I, I, D, D, P, I, D, P, P]
@@ -96,7 +142,10 @@ def _load():
         lib.oracle_energy.restype = None
         lib.oracle_errors.argtypes = [P, P, L, D, P]
         lib.oracle_errors.restype = None
-        _lib = lib
+        if omp:
+            _omp_lib = lib
+        else:
+            _lib = lib
         return lib
 
 
@@ -276,9 +325,10 @@ class State:
 
 
 def solve(f32, region, lam, theta=0.2, tau=0.125, iters=100, n_inner=1, tol=0.0,
-          state: State | None = None) -> State:
-    """Run the restricted dual iteration (Section 3); warm-starts from `state`."""
-    lib = _load()
+          state: State | None = None, parallel: bool = False) -> State:
+    """Run the restricted dual iteration (Section 3); warm-starts from `state`.
+    parallel: use the OpenMP build (same results, all cores)."""
+    lib = _load(omp=parallel)
     f = _c(f32, np.float32)
     reg = _c(region, np.uint8)
     H, W = f.shape

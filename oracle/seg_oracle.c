@@ -267,6 +267,7 @@ int64_t oracle_pixel_list_tiled(const uint8_t* region, int H, int W, int th, int
  * (first component) and last column (second component). */
 void oracle_grad(const double* w, int H, int W, double* g1, double* g2)
 {
+#pragma omp parallel for
     for (int i = 0; i < H; ++i)
         for (int j = 0; j < W; ++j) {
             g1[IDX(i, j)] = (i < H - 1) ? w[IDX(i + 1, j)] - w[IDX(i, j)] : 0.0;
@@ -278,6 +279,7 @@ void oracle_grad(const double* w, int H, int W, double* g1, double* g2)
  * (div p) = [i<H-1] p1(i,j) - [i>0] p1(i-1,j) + [j<W-1] p2(i,j) - [j>0] p2(i,j-1). */
 void oracle_div(const double* p1, const double* p2, int H, int W, double* d)
 {
+#pragma omp parallel for
     for (int i = 0; i < H; ++i)
         for (int j = 0; j < W; ++j) {
             double a = (i < H - 1 ? p1[IDX(i, j)] : 0.0) - (i > 0 ? p1[IDX(i - 1, j)] : 0.0);
@@ -310,6 +312,8 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
     double* g2 = (double*)malloc(sizeof(double) * (size_t)n);
     double* q1 = (double*)malloc(sizeof(double) * (size_t)n);
     double* q2 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* row_u = (double*)malloc(sizeof(double) * (size_t)H);
+    double* row_v = (double*)malloc(sizeof(double) * (size_t)H);
 
     if (!warm) {
         for (int64_t x = 0; x < n; ++x) {
@@ -336,8 +340,10 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
         /* fixed-point sweeps for rho with v held fixed */
         for (int s = 0; s < n_inner; ++s) {
             oracle_div(p1, p2, H, W, d);
+#pragma omp parallel for
             for (int64_t x = 0; x < n; ++x) w[x] = d[x] - v[x] / theta;
             oracle_grad(w, H, W, g1, g2);
+#pragma omp parallel for
             for (int64_t x = 0; x < n; ++x) {
                 if (region[x] == 2) {
                     double nrm = sqrt(g1[x] * g1[x] + g2[x] * g2[x]);
@@ -349,27 +355,41 @@ int oracle_solve(const float* f32, int H, int W, const uint8_t* region,
                     q2[x] = 0.0;
                 }
             }
-            memcpy(p1, q1, sizeof(double) * (size_t)n);
-            memcpy(p2, q2, sizeof(double) * (size_t)n);
+#pragma omp parallel for
+            for (int64_t x = 0; x < n; ++x) {
+                p1[x] = q1[x];
+                p2[x] = q2[x];
+            }
         }
-        /* u-step then v-step on RD */
+        /* u-step then v-step on RD; the increments' squared norms are summed
+         * per row, then over the rows in order */
         oracle_div(p1, p2, H, W, d);
+#pragma omp parallel for
+        for (int i = 0; i < H; ++i) {
+            double ru = 0.0, rv = 0.0;
+            for (int64_t x = IDX(i, 0); x < IDX(i, W); ++x) {
+                if (region[x] != 2) continue;
+                double un = v[x] - theta * d[x];
+                double vn = clamp01(un - theta * lambda * (double)f32[x]);
+                ru += (un - u[x]) * (un - u[x]);
+                rv += (vn - v[x]) * (vn - v[x]);
+                u[x] = un;
+                v[x] = vn;
+            }
+            row_u[i] = ru;
+            row_v[i] = rv;
+        }
         double su = 0.0, sv = 0.0;
-        for (int64_t x = 0; x < n; ++x) {
-            if (region[x] != 2) continue;
-            double un = v[x] - theta * d[x];
-            double vn = clamp01(un - theta * lambda * (double)f32[x]);
-            su += (un - u[x]) * (un - u[x]);
-            sv += (vn - v[x]) * (vn - v[x]);
-            u[x] = un;
-            v[x] = vn;
+        for (int i = 0; i < H; ++i) {
+            su += row_u[i];
+            sv += row_v[i];
         }
         double du = sqrt(su), dv = sqrt(sv);
         if (hist) { hist[2 * it] = du; hist[2 * it + 1] = dv; }
         done = it + 1;
         if (tol > 0.0 && (du > dv ? du : dv) <= tol) break;
     }
-    free(d); free(w); free(g1); free(g2); free(q1); free(q2);
+    free(d); free(w); free(g1); free(g2); free(q1); free(q2); free(row_u); free(row_v);
     return done;
 }
 

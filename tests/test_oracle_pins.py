@@ -939,3 +939,23 @@ def test_volume_solve_commutes_with_axis_permutations(orc, perm):
     for new_axis, old_axis in enumerate(perm):
         np.testing.assert_allclose(pb[comp_axis[new_axis]], pa[comp_axis[old_axis]].transpose(perm),
                                    atol=1e-12)
+
+
+def test_openmp_build_gives_the_same_bits(orc):
+    """The OpenMP build of the oracle (all cores, used for the full-size
+    parity tests and the timed CPU baseline) computes every element with the
+    same operations as the serial build and sums the increments in the same
+    order: identical iterates and history."""
+    if not orc.has_omp():
+        pytest.skip("no OpenMP in this compiler")
+    P = synth.small_example(seed=5, H=61, W=77)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    for delta in (0.15, np.inf):
+        reg = orc.domain(f, delta)
+        a = orc.solve(f, reg, 1.0, iters=120, n_inner=2)
+        b = orc.solve(f, reg, 1.0, iters=120, n_inner=2, parallel=True)
+        for x, y in ((a.u, b.u), (a.v, b.v), (a.p1, b.p1), (a.p2, b.p2), (a.hist, b.hist)):
+            np.testing.assert_array_equal(x, y)
+        c = orc.solve(f, reg, 1.0, iters=500, tol=1e-2, parallel=True)
+        d = orc.solve(f, reg, 1.0, iters=500, tol=1e-2)
+        assert c.iters_done == d.iters_done
