@@ -38,9 +38,8 @@ BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + 
 # DRAM bytes (read + write) per iteration of k_solve_compact, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a 50-iteration
 # launch / 50) of `bench.py --profile --profile-tiled --iters 50` (2048x2048,
-# delta = 0.2, float32), summarised in profiles/k_solve_compact_ds2048.md.
-# The iteration state is held on chip, so this is far below the algorithmic
-# bytes.
+# delta = 0.2, float32).  The iteration state is held on chip, so this is far
+# below the algorithmic bytes.
 COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (1525760 + 11108864) / 50}
 
 
@@ -657,7 +656,10 @@ def row_volume(dev, flush):
                      "frac_of_measured_hbm": gbs / hbm_peak()[0]}
         del S, g
     out["restricted_vs_full_per_iter"] = us["full"] / us["restricted"]
-    out["E1_vs_full"] = float((u_final["restricted"] == u_final["full"]).float().mean().item())
+    a, b = u_final["restricted"], u_final["full"]
+    inter, union = float((a & b).sum().item()), float((a | b).sum().item())
+    out["E1_vs_full"] = inter / union if union else 1.0       # Tanimoto index of Section 4
+    out["voxel_agreement_vs_full"] = float((a == b).float().mean().item())
     out["bytes_per_active_iter"] = VOL_BYTES_PER_ACTIVE_ITER
     return out
 
@@ -676,7 +678,7 @@ def run_rows(args, dev):
                                   "one persistent launch",
                         "active_pixels": b["A"], "ms_per_step": b["ms"], "us_per_iter": b["t_iter"] * 1e3,
                         "active_Mpixel_iter_per_s": b["A"] * b["iters"] / (b["ms"] * 1e-3) / 1e6,
-                        "frac_of_measured_hbm": b["ach"] / 6689.8, "tile_h": b["tile_h"]}
+                        "frac_of_measured_hbm": b["ach"] / hbm_peak()[0], "tile_h": b["tile_h"]}
     return rows
 
 

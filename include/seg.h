@@ -23,7 +23,8 @@
  *    caller allocates every buffer (through any allocator; PyTorch in the
  *    Python binding); the library never allocates device memory.  Scratch
  *    comes from a caller-provided workspace of seg_workspace_bytes() bytes,
- *    16-byte aligned, owned by the caller, used by one call at a time.
+ *    16-byte aligned, zero-filled before its first use, owned by the caller,
+ *    used by one call at a time.
  *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
  *    default stream) and returns a seg_status for errors found on the host
  *    (arguments, launch failures).  Errors found on the device (non-finite
@@ -106,6 +107,24 @@ size_t seg_state_bytes(int H, int ld, int64_t capacity, int mode, int storage);
 /* Synchronise `stream` and return the device status word of the workspace
  * (SEG_OK or the first device-side error), then clear it. */
 seg_status seg_read_status(void* ws, size_t ws_bytes, void* stream);
+
+/* Diagnostics of the device-side waits (no counterpart in the paper).  Every
+ * wait inside a kernel -- the grid barriers of the persistent solvers, the
+ * TMA completions of the tiled solver -- gives up after a bounded number of
+ * SM clock cycles, records SEG_ERR_TIMEOUT in the workspace status word,
+ * raises the workspace's done flag and returns, so a lost block never hangs
+ * the GPU.  This call sets, for later calls on this workspace:
+ *   wait_cycles     the bound (> 0), or 0 for the default of 2e9 cycles
+ *                   (about 1 s at the SM clock);
+ *   extra_arrivals  0 for normal operation; k > 0 makes every grid barrier
+ *                   wait for k arrivals beyond the launch's blocks, arrivals
+ *                   that never come, so that every such wait runs out after
+ *                   wait_cycles (the way the tests drive the timeout path).
+ * The values stay in the workspace header until the next call; a solve that
+ * timed out leaves its outputs undefined.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (negative values), WORKSPACE, CUDA. */
+seg_status seg_set_wait_limit(void* ws, size_t ws_bytes, long long wait_cycles, int extra_arrivals,
+                              void* stream);
 
 /* Fitting term (Section 1): Eq. CV  f = (z - c1)^2 - (z - c2)^2, and when
  * n_markers > 0 Eq. DS  f = CV + gamma P(x), with P the Euclidean distance to

@@ -166,6 +166,26 @@ extern "C" size_t seg_workspace_bytes(int H, int W, int ld, int tile_h) {
     return seg::ws_layout(H, W, tile_h).total;
 }
 
+namespace seg {
+__global__ void k_set_wait_limit(WsHeader* h, long long wait_cycles, unsigned extra) {
+    h->wait_cycles = wait_cycles;
+    h->bar_extra = extra;
+}
+}  // namespace seg
+
+extern "C" seg_status seg_set_wait_limit(void* ws, size_t ws_bytes, long long wait_cycles,
+                                         int extra_arrivals, void* stream) {
+    seg::clear_error();
+    if (!ws || ws_bytes < 256) return seg::fail(SEG_ERR_WORKSPACE, "workspace missing");
+    if (wait_cycles < 0 || extra_arrivals < 0)
+        return seg::fail(SEG_ERR_INVALID_ARG, "wait_cycles and extra_arrivals must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    seg::k_set_wait_limit<<<1, 1, 0, s>>>(static_cast<seg::WsHeader*>(ws), wait_cycles,
+                                           (unsigned)extra_arrivals);
+    SEG_LAUNCHED("k_set_wait_limit");
+    return SEG_OK;
+}
+
 extern "C" seg_status seg_read_status(void* ws, size_t ws_bytes, void* stream) {
     seg::clear_error();
     if (!ws || ws_bytes < 256) return seg::fail(SEG_ERR_WORKSPACE, "workspace missing");

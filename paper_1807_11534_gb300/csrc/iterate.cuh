@@ -36,7 +36,7 @@ __device__ __forceinline__ void chambolle_update(float p1, float p2, float g1, f
 // block's count of barriers passed, tracked in a register; the counter is
 // reset before each persistent launch).  Returns false after recording
 // SEG_ERR_TIMEOUT (and raising the done flag) if the others do not arrive
-// within ~1 s.
+// within the workspace's wait bound (~1 s by default).
 __device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -59,10 +59,10 @@ __device__ __forceinline__ bool grid_wait(WsHeader* h, unsigned nblocks, unsigne
     __shared__ int s_ok, s_done;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned target = nblocks * gen;
-        const long long t0 = clock64();
+        const unsigned target = nblocks * gen + h->bar_extra;
+        const long long t0 = clock64(), budget = wait_budget(h);
         while ((int)(ld_acquire_gpu(&h->bar_count) - target) < 0) {
-            if (clock64() - t0 > kWaitCycles) {
+            if (clock64() - t0 > budget) {
                 record_status(h, SEG_ERR_TIMEOUT);
                 h->done = 1;
                 ok = 0;

@@ -72,9 +72,13 @@ struct WsHeader {
     int n_smem_blocks;   // compact solver: blocks that held their state in shared memory
     int n_h1_blocks;     // compact solver: blocks that ran one grid barrier per iteration
     unsigned h1_vote;    // compact solver: blocks whose one-barrier state did not fit (a vote)
+    long long wait_cycles;   // bound of every device-side wait, SM clock cycles (0: kWaitCycles);
+                             // set by seg_set_wait_limit, kept across solves
     // grid barrier of the persistent solvers: monotonic arrival counter, on
     // its own cache line
     alignas(128) unsigned bar_count;
+    unsigned bar_extra;  // arrivals a grid barrier waits for beyond the launch's blocks: 0,
+                         // except to test the timeout path (seg_set_wait_limit)
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
@@ -310,13 +314,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for phase `parity` of `bar` for at most ~1 s of SM clock; returns
-// false (after recording SEG_ERR_TIMEOUT) when the wait runs out.
+// Default bound of a device-side wait: ~1 s of SM clock.  A workspace can
+// set its own (WsHeader::wait_cycles).
 constexpr long long kWaitCycles = 2000000000LL;
+__device__ __forceinline__ long long wait_budget(const WsHeader* h) {
+    const long long c = h->wait_cycles;
+    return c > 0 ? c : kWaitCycles;
+}
+
+// Waits for phase `parity` of `bar` for at most the workspace's wait bound;
+// returns false (after recording SEG_ERR_TIMEOUT) when the wait runs out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, WsHeader* h) {
-    const long long t0 = clock64();
+    const long long t0 = clock64(), budget = wait_budget(h);
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > budget) {
             record_status(h, SEG_ERR_TIMEOUT);
             return false;
         }

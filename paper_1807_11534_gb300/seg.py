@@ -87,6 +87,7 @@ SIGNATURES = {
     "seg_workspace_bytes": ([_I, _I, _I, _I], _Z),
     "seg_state_bytes": ([_I, _I, _L, _I, _I], _Z),
     "seg_read_status": ([_P, _Z, _P], _I),
+    "seg_set_wait_limit": ([_P, _Z, ctypes.c_longlong, _I, _P], _I),
     "seg_make_fitting": ([_P, _I, _I, _I, _D, _D, _P, _P, _I, _D, _P, _P, _P, _Z, _P], _I),
     "seg_build_domain": ([_P, _I, _I, _I, _D, _D, _I, _P, _P, _P, _P, _I, _P, _L, _P, _P, _P, _Z, _P], _I),
     "seg_build_domain_robust": ([_P, _P, _I, _I, _I, _D, _D, _I, _I, _P, _P, _P, _P, _I, _P, _L, _P,
@@ -183,6 +184,11 @@ def seg_state_bytes(H, ld, capacity, mode, storage):
 def seg_read_status(ws, stream=None):
     lib = load()
     _check(lib.seg_read_status(_ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def seg_set_wait_limit(ws, wait_cycles, extra_arrivals=0, stream=None):
+    _check(load().seg_set_wait_limit(_ptr(ws), _nbytes(ws), int(wait_cycles), int(extra_arrivals),
+                                     _stream(stream)))
 
 
 def seg_make_fitting(z, c1, c2, label, markers, gamma, f, c_out, ws, stream=None):

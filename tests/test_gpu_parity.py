@@ -292,23 +292,39 @@ def test_compact_capacity_overflow_is_reported():
     assert e.value.status == seg.SEG_ERR_CAPACITY
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+BF16_FAILS = ("bf16 storage of p and v does not meet the 1e-2 bound on u in the max norm: "
+              "8 significant bits, and its unbiased rounding noise accumulates in the slowly "
+              "contracting modes of the iteration (max |u - u_oracle| about 2e-2 here)")
+
+
+@pytest.mark.parametrize("storage", ["f16", pytest.param("bf16", marks=pytest.mark.xfail(
+    strict=True, reason=BF16_FAILS))])
 def test_16bit_storage(orc, storage):
-    """p and v in 16 bits (stochastic rounding), float32 arithmetic.  fp16 (11
-    significant bits) meets the 1e-2 bound on u; bf16 (8 bits) does not in the
-    max norm -- the slowly contracting iteration accumulates its rounding
-    noise -- so for bf16 the bound checked is the measured one (max 4e-2, mean
-    2e-3) and the thresholded masks must still agree."""
+    """p and v in 16 bits (stochastic rounding), float32 arithmetic, against
+    the FP64 oracle: max |u - u_oracle| <= 1e-2 and the masks at 0.5 agree.
+    fp16 (11 significant bits) meets it; bf16 does not (an expected failure,
+    strict: the day it passes, the mark must go)."""
     P = _problem((128, 160), seed=8)
     _, f = orc.fitting(P.z, 0.3, 0.7)
     out = run_gpu(f, delta=0.2, lam=1.0, iters=200, mode="compact", storage=storage)
     st = orc.solve(f, orc.domain(f, 0.2), 1.0, iters=200)
-    err = np.abs(out["u"] - st.u)
-    if storage == "f16":
-        assert err.max() <= TOL_U16, err.max()
-    else:
-        assert err.max() <= 4e-2 and err.mean() <= 2e-3, (err.max(), err.mean())
     assert np.mean((out["u"] > 0.5) != (st.u > 0.5)) < 1e-3
+    err = np.abs(out["u"] - st.u)
+    assert err.max() <= TOL_U16, err.max()
+
+
+def test_bf16_storage_mean_error_and_mask(orc):
+    """What bf16 storage does meet against the oracle on the same problem:
+    a small mean error and the same mask at 0.5 (its max-norm failure is the
+    expected failure above)."""
+    P = _problem((128, 160), seed=8)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    out = run_gpu(f, delta=0.2, lam=1.0, iters=200, mode="compact", storage="bf16")
+    st = orc.solve(f, orc.domain(f, 0.2), 1.0, iters=200)
+    err = np.abs(out["u"] - st.u)
+    assert err.mean() <= 1e-3, err.mean()
+    assert np.mean((out["u"] > 0.5) != (st.u > 0.5)) < 1e-3
+    assert out["v"].min() >= 0 and out["v"].max() <= 1
 
 
 # ----------------------------------------------------------------- energies
@@ -396,22 +412,22 @@ def test_compact_matches_dense_on_the_whole_image(orc, delta):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("storage", ["f16", pytest.param("bf16", marks=pytest.mark.xfail(
+    strict=True, reason=BF16_FAILS))])
 def test_16bit_storage_on_the_shared_memory_path(orc, storage):
-    """16-bit p, v on the benchmark image at its delta (0.2: the two-phase
-    iteration with shared-memory state) against float32 storage, with the
-    bounds of the small-image 16-bit test."""
+    """16-bit p, v on the benchmark image at its delta (0.2, the one-barrier
+    iteration with shared-memory state) against the FP64 oracle on the whole
+    image (OpenMP build when present)."""
     P = synth.ellipses_ds(seed=0, H=2048, W=2048)
     c1, c2 = orc.class_means(P.z, P.label)
     _, f = orc.fitting(P.z, c1, c2, P.markers, P.gamma)
     K, lam = 200, 2.0
-    o32 = run_gpu(f, delta=0.2, lam=lam, iters=K, mode="compact", tile_h=16)
     o16 = run_gpu(f, delta=0.2, lam=lam, iters=K, mode="compact", tile_h=16, storage=storage)
-    d = np.abs(o16["u"] - o32["u"])
-    assert d.max() <= (1e-2 if storage == "f16" else 4e-2), d.max()
-    assert d.mean() <= 2e-3
-    assert np.mean((o16["u"] > 0.5) != (o32["u"] > 0.5)) <= 1e-3
+    st = orc.solve(f, orc.domain(f, 0.2), lam, iters=K, parallel=orc.has_omp())
+    d = np.abs(o16["u"] - st.u)
+    assert np.mean((o16["u"] > 0.5) != (st.u > 0.5)) <= 1e-3
     assert o16["v"].min() >= 0 and o16["v"].max() <= 1
+    assert d.max() <= TOL_U16, d.max()
 
 
 @pytest.mark.slow
@@ -442,9 +458,10 @@ def test_largest_image_sampled(orc, mode):
 
 
 @pytest.mark.slow
-def test_full_size_4096_storage_sampled(orc):
-    """4096x4096 polygons, 16-bit storage against float32 storage and the
-    oracle on crops."""
+def test_full_size_4096_sampled(orc):
+    """4096x4096 polygons at float32 storage, 20 iterations, against the
+    oracle on crops (the 2000-iteration whole-image comparison is in
+    test_gpu_fullsize.py)."""
     P = synth.polygons(seed=0)
     _, f = orc.fitting(P.z, 0.3, 0.7)
     K, delta = 20, 0.1
@@ -454,6 +471,3 @@ def test_full_size_4096_storage_sampled(orc):
     act = np.argwhere(reg == 2)
     centres = [tuple(x) for x in act[rng.choice(len(act), 8, replace=False)]]
     assert _crop_check(orc, f, o32["u"], delta, 1.0, K, centres) <= TOL_U32
-    for storage, tol in (("f16", TOL_U16), ("bf16", 4e-2)):
-        o16 = run_gpu(f, delta=delta, iters=K, mode="compact", storage=storage, tile_h=16)
-        assert np.abs(o16["u"] - o32["u"]).max() <= tol, storage
