@@ -424,7 +424,11 @@ seg_status seg_energy(const float* f, int H, int W, int ld,
  * present on every GPU that loads it until the process exits.  Images above
  * 33,554,432 pixels are rejected with SEG_ERR_CAPACITY.  The first call on a
  * device looks up that array's address (cudaGetSymbolAddress) and caches it,
- * so make the first call before any stream capture.  No slot needs clearing
+ * so make the first call before any stream capture.  The cached address
+ * belongs to the device's current primary context: after cudaDeviceReset
+ * (or anything else that destroys that context) the library is loaded anew
+ * at another address and the cached one is stale, so do not call this entry
+ * point in a process after resetting the device.  No slot needs clearing
  * (each call writes every slot it reads); all calls share the array, so calls
  * that overlap on the GPU race and may return wrong sums.  It never calls
  * cudaMalloc or cudaFree.  Errors: INVALID_ARG, ALIGN, CAPACITY, CUDA. */

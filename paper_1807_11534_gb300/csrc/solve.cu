@@ -24,10 +24,10 @@
 //              iteration reads (or a code for a fixed / outside pixel).  One
 //              persistent cooperative launch runs every iteration: a dual
 //              phase (p') and a primal phase (u', v', and w = div p - v/theta
-//              for the next dual phase) separated by grid barriers, or one
-//              fused phase per iteration when each thread holds few pixels;
-//              each block keeps what it can of its pixels' state in shared
-//              memory (see the persistent compact solver below).
+//              for the next dual phase), with one grid barrier per iteration
+//              when the state fits in shared memory and two otherwise; each
+//              block keeps what it can of its pixels' state in shared memory
+//              (see the persistent compact solver below).
 // Per-block FP64 partial sums of |du|^2, |dv|^2 feed a fixed-order reduction,
 // so the stopping test is deterministic.  Once it fires, a device flag makes
 // every later launch of the solve return immediately.
@@ -228,10 +228,8 @@ __global__ void k_final_dense(IterParams P, const WsHeader* __restrict__ h, int 
 // ========================================================== compact stencil
 
 // neighbour slots of the table and the codes for pixels that are not in RD
-// (NB_UUR = (i-2, j+1) and NB_LLD = (i+1, j-2) are the neighbours of x - e1
-// and x - e2 that the fused iteration needs when it redoes their dual step)
-enum { NB_UP = 0, NB_LEFT = 1, NB_DOWN = 2, NB_RIGHT = 3, NB_DOWNLEFT = 4, NB_UPRIGHT = 5, NB_UUR = 6,
-       NB_LLD = 7, NB_COUNT = 8 };
+enum { NB_UP = 0, NB_LEFT = 1, NB_DOWN = 2, NB_RIGHT = 3, NB_DOWNLEFT = 4, NB_UPRIGHT = 5, NB_COUNT = 6 };
+constexpr int kNbRows = NB_COUNT;   // neighbour rows an iteration reads
 constexpr int kNbBg = -1;    // fixed background: p = 0, v = 0
 constexpr int kNbFg = -2;    // fixed foreground: p = 0, v = 1
 constexpr int kNbOut = -3;   // outside the image (the gradient there is 0)
@@ -242,7 +240,7 @@ struct CompactState {
     float* u;
     float* w;        // div p - v/theta of the current iterate
     int32_t* nb;     // [NB_COUNT][stride]
-    float* w2;       // the other w buffer of the fused iteration
+    float* w2;       // scratch of the one-barrier path (export marks)
     float* up;       // u of the iteration before a stopping test
     int64_t cap;
     int64_t stride;
@@ -376,8 +374,6 @@ __global__ void k_compact_gather(IterParams P, BatchDesc B, const int32_t* __res
     nb[NB_RIGHT * st + idx] = code(i, j + 1);
     nb[NB_DOWNLEFT * st + idx] = code(i + 1, j - 1);
     nb[NB_UPRIGHT * st + idx] = code(i - 1, j + 1);
-    nb[NB_UUR * st + idx] = code(i - 2, j + 1);
-    nb[NB_LLD * st + idx] = code(i + 1, j - 2);
 }
 
 template <typename T>
@@ -422,14 +418,9 @@ __device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, flo
 //   primal phase u', v', w', stop-test partials          -> barrier
 //   (check iterations) block 0 sums the partials in a fixed order and raises
 //   the done flag, which every block reads after the next barrier.
-// The grid takes one of these (the same in every block):
-//  * fused (n_inner = 1, few pixels per thread): one phase and one barrier
-//    per iteration; the thread of x also redoes the dual steps of x - e1 and
-//    x - e2 (same inputs, same arithmetic, same rounding as their owners),
-//    which is all the v-step of x needs, and w is ping-ponged.  The iterates
-//    are bit-identical to the two-phase ones.
-//  * one barrier with shared-memory state and a ring (n_inner = 1, every
-//    block's state fits, by a grid-wide vote): see compact_iterations_h1.
+// The grid takes the one-barrier path with shared-memory state and a ring
+// (n_inner = 1, every block's state fits, by a grid-wide vote): see
+// compact_iterations_h1.
 // Otherwise each block takes the first of these that applies (blocks may
 // differ; all keep the same two-barrier protocol and the same global arrays
 // current):
@@ -444,10 +435,6 @@ constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 112 * 1
 constexpr int kCompactThreads = 512;   // two blocks per SM: one block's block barriers overlap the other's work
 constexpr int kCompactWideUnroll = 2;   // pixels per thread in flight in k_solve_compact_wide
 constexpr int kCompactUnroll = 4;       // pixels per thread in flight in the two-phase iteration
-// fused iteration up to this many pixels per thread: 0, i.e. only for an
-// empty range (the one-barrier ring path measured faster at every size
-// tried, 0.6 to 5 pixels per thread)
-constexpr int kFusePerThread = 0;
 
 // Own-pixel arrays (neighbour-table rows, v) of the pixels a block updates:
 // SH, copies in shared memory indexed from the block's first pixel a0; else
@@ -474,8 +461,8 @@ struct Own {
 // neighbour is in RD, and formed from p(x) and p(x+e1-e2) (resp. p(x+e2-e1))
 // where it is fixed.  p1 vanishes on the last row and p2 on the last column
 // (their gradient component is 0 there and they start at 0).
-template <typename T, bool SH>
-__device__ __forceinline__ void dual_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1i,
+template <typename T, class OwnT>
+__device__ __forceinline__ void dual_one(const IterParams& P, int a, const OwnT& O, const T* P1i,
                                          const T* P2i, const float* Wc, T* P1o, T* P2o, uint32_t seed) {
     const int n_down = O.nbr(NB_DOWN, a);
     const int n_right = O.nbr(NB_RIGHT, a);
@@ -503,8 +490,8 @@ __device__ __forceinline__ void dual_one(const IterParams& P, int a, const Own<T
 // lambda f) (v updated in place), w' = div p' - v'/theta for the next dual
 // step.  wonly: just w = div p' - v/theta (between extra fixed-point sweeps,
 // or for a warm start).
-template <typename T, bool SH>
-__device__ __forceinline__ void primal_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1n,
+template <typename T, class OwnT>
+__device__ __forceinline__ void primal_one(const IterParams& P, int a, const OwnT& O, const T* P1n,
                                            const T* P2n, float* U, float* Up, float* Wc, bool wonly,
                                            bool check, bool write_u, bool write_prev, uint32_t seed,
                                            float& du2, float& dv2) {
@@ -532,94 +519,20 @@ __device__ __forceinline__ void primal_one(const IterParams& P, int a, const Own
     if (write_u) U[a] = un;
 }
 
-// One fused iteration at one RD pixel (n_inner = 1): p'(x) as the dual step
-// computes it, p1'(x - e1) and p2'(x - e2) as the dual steps of x - e1 and
-// x - e2 compute them (their neighbours below / right are x, x - e1 + e2 and
-// x + e1 - e2, x; a fixed one of those needs p at (i-2, j+1) resp.
-// (i+1, j-2)), each rounded as its owner stores it; then the primal step of
-// x.  Reads p, w of the current iterate (P1i, P2i, Wi), writes p', w' to the
-// other buffers and v in place.
-template <typename T, bool SH>
-__device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1i,
-                                          const T* P2i, const float* Wi, T* P1o, T* P2o, float* Wo, float* U,
-                                          float* Up, bool check, bool write_u, bool write_prev, uint32_t seed_d,
-                                          uint32_t seed_p, float& du2, float& dv2) {
-    const int n_up = O.nbr(NB_UP, a), n_left = O.nbr(NB_LEFT, a);
-    const int n_down = O.nbr(NB_DOWN, a), n_right = O.nbr(NB_RIGHT, a);
-    const int n_dl = O.nbr(NB_DOWNLEFT, a), n_ur = O.nbr(NB_UPRIGHT, a);
-    const int n_uur = n_up >= 0 ? O.nbr(NB_UUR, a) : kNbOut;
-    const int n_lld = n_left >= 0 ? O.nbr(NB_LLD, a) : kNbOut;
-    // every load of the step, independent of one another
-    const float p1 = Store<T>::ldc(P1i, a), p2 = Store<T>::ldc(P2i, a);
-    const float w0 = ldw(Wi + a);
-    const float wd = n_down >= 0 ? ldw(Wi + n_down) : 0.f;
-    const float wr = n_right >= 0 ? ldw(Wi + n_right) : 0.f;
-    const float p2dl = nb_ld(P2i, n_dl), p1ur = nb_ld(P1i, n_ur);
-    const float p1U = nb_ld(P1i, n_up), p2U = nb_ld(P2i, n_up);
-    const float wU = n_up >= 0 ? ldw(Wi + n_up) : 0.f;
-    const float wur = n_ur >= 0 ? ldw(Wi + n_ur) : 0.f;
-    const float p1uur = nb_ld(P1i, n_uur);
-    const float p1L = nb_ld(P1i, n_left), p2L = nb_ld(P2i, n_left);
-    const float wL = n_left >= 0 ? ldw(Wi + n_left) : 0.f;
-    const float wdl = n_dl >= 0 ? ldw(Wi + n_dl) : 0.f;
-    const float p2lld = nb_ld(P2i, n_lld);
-    // p'(x)
-    const float g1 = g_comp(n_down, wd, p1, p2dl, w0, P.inv_theta);
-    const float g2 = g_comp(n_right, wr, p1ur, p2, w0, P.inv_theta);
-    float q1, q2;
-    chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
-    const uint32_t rnd = mix32((uint32_t)a * 3u + seed_d);
-    q1 = Store<T>::st_sr(P1o, a, q1, rnd);
-    q2 = Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
-    // p1'(x - e1)
-    float q1u = 0.f;
-    if (n_up >= 0) {
-        const float gu2 = g_comp(n_ur, wur, p1uur, p2U, wU, P.inv_theta);
-        float b1, b2;
-        chambolle_update(p1U, p2U, w0 - wU, gu2, P.tau, b1, b2);
-        q1u = Store<T>::sr(b1, mix32((uint32_t)n_up * 3u + seed_d));
-    }
-    // p2'(x - e2)
-    float q2l = 0.f;
-    if (n_left >= 0) {
-        const float gl1 = g_comp(n_dl, wdl, p1L, p2lld, wL, P.inv_theta);
-        float b1, b2;
-        chambolle_update(p1L, p2L, gl1, w0 - wL, P.tau, b1, b2);
-        q2l = Store<T>::sr(b2, mix32(mix32((uint32_t)n_left * 3u + seed_d) ^ 0x9e3779b9u));
-    }
-    // primal step of x
-    const float div = (q1 - q1u) + (q2 - q2l);
-    const float vv = Store<T>::ld_rw(O.v, O.vi(a)) + Store<T>::vbias;
-    const float un = fmaf(-P.theta, div, vv);
-    const float vn = clamp01(un - O.fv(a));   // F = theta lambda f
-    const float vs = Store<T>::st_sr(O.v, O.vi(a), vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed_p)) +
-                     Store<T>::vbias;
-    Wo[a] = div - vs * P.inv_theta;
-    if (check) {
-        const float da = un - Up[a], db = vn - vv;
-        du2 = fmaf(da, da, du2);
-        dv2 = fmaf(db, db, dv2);
-    }
-    if (write_prev) Up[a] = un;
-    if (write_u) U[a] = un;
-}
-
 // The iterations of one block of the persistent compact solver (see above);
 // false when a grid barrier timed out.
-template <typename T, bool SH, int NT, int UNROLL>
-__device__ __forceinline__ bool compact_iterations(const IterParams& P, const Own<T, SH>& O, int a0, int a1,
+template <typename T, class OwnT, int NT, int UNROLL>
+__device__ __forceinline__ bool compact_iterations(const IterParams& P, const OwnT& O, int a0, int a1,
                                                    int iters, int n_inner, int check_every, double tol, int warm,
                                                    int64_t stride, T* P1a, T* P1b, T* P2a, T* P2b, float* Uu,
                                                    float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h,
-                                                   float* ckpt, int ckpt_every, double* s_red, int fuse,
-                                                   unsigned& gen) {
+                                                   float* ckpt, int ckpt_every, double* s_red, unsigned& gen) {
     // gen: barriers passed (the arrival counter starts at 0 each solve and
     // runs on across the waves of a batch)
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = NT;
     int pb = 0;
-    // the block's pixels, UNROLL per thread in flight (one in the fused
-    // step, which keeps about three times as many values live)
+    // the block's pixels, UNROLL per thread in flight
     auto each = [&](auto&& op) {
         int a = a0 + tid;
         for (; a + (UNROLL - 1) * nt < a1; a += UNROLL * nt) {
@@ -627,9 +540,6 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
             for (int k = 0; k < UNROLL; ++k) op(a + k * nt);
         }
         for (; a < a1; a += nt) op(a);
-    };
-    auto each1 = [&](auto&& op) {
-        for (int a = a0 + tid; a < a1; a += nt) op(a);
     };
     float dummy0 = 0.f, dummy1 = 0.f;
     // current / other ping-pong buffers of p, selected without indexing
@@ -655,76 +565,6 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
         }
     };
     if (ckpt) save(0);
-    if (fuse) {   // fused: one phase and one barrier per iteration
-        int wb = 0, chk = 0;
-        for (int it = 0; it < iters; ++it) {
-            const int l = it + 1;
-            const bool check = (l % C == 0) || l == iters;
-            const bool write_u = check;   // the output u and the stopped iterate
-        const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
-            const uint32_t seed_d = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
-            const uint32_t seed_p = mix32(0x2545f491u ^ (uint32_t)it);
-            const T* pi1 = p1c(); const T* pi2 = p2c();
-            T* po1 = p1o(); T* po2 = p2o();
-            const float* wi = wb ? Wc2 : Wc;
-            float* wo = wb ? Wc : Wc2;
-            float du2 = 0.f, dv2 = 0.f;
-            if (!check && !write_prev)
-                each1([&](int a) {
-                    fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, Up, false, false, false, seed_d, seed_p, du2,
-                              dv2);
-                });
-            else
-                each1([&](int a) {
-                    fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, Up, check, write_u, write_prev, seed_d,
-                              seed_p, du2, dv2);
-                });
-            pb ^= 1;
-            wb ^= 1;
-            if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);   // own pixels: no barrier
-            // stopping-test partials, double-buffered by check so that a fast
-            // block cannot overwrite those a slow block is still summing
-            double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
-            if (check) {
-                float x = du2, y = dv2;
-                block_sum2f<NT>(x, y, reinterpret_cast<float*>(s_red));
-                if (tid == 0) {
-                    part[2 * blockIdx.x] = x;
-                    part[2 * blockIdx.x + 1] = y;
-                }
-            }
-            if (!grid_sync(h, nblocks, gen)) return false;
-            if (check) {
-                // Section 4 stopping test: every block sums the block partials
-                // in the same fixed order, so all stop at the same iteration
-                // (squared norms against tol^2: the square roots are taken
-                // once, for the stats)
-                if (tid < 32) {
-                    double sx, sy;
-                    sum_partials_warp0(part, (int)nblocks, sx, sy);
-                    if (tid == 0) {
-                        const bool stop = tol > 0.0 && fmax(sx, sy) <= tol * tol;
-                        s_red[0] = stop ? 1.0 : 0.0;
-                        if (blockIdx.x == 0) {
-                            h->du2 = sx;
-                            h->dv2 = sy;
-                            h->last_check = l;
-                            if (stop) {
-                                h->iters_done = l;
-                                h->done = 1;
-                            }
-                        }
-                    }
-                }
-                __syncthreads();
-                const bool stop = s_red[0] != 0.0;
-                ++chk;
-                __syncthreads();
-                if (stop) return true;
-            }
-        }
-        return true;
-    }
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
         for (int sw = 0; sw < n_inner; ++sw) {
@@ -1618,7 +1458,7 @@ __device__ __forceinline__ int compact_solve_h1(
 template <typename T>
 __device__ __forceinline__ bool compact_wide(int n, int grid1) {
     const int64_t per1 = ((int64_t)n + grid1 - 1) / grid1;
-    return (size_t)per1 * (4 * NB_UUR + sizeof(T)) > compact_smem(kCompactThreads);
+    return (size_t)per1 * (4 * kNbRows + sizeof(T)) > compact_smem(kCompactThreads);
 }
 
 // All iterations of the compact solve over the RD pixels [w0, w0 + n) (the
@@ -1634,11 +1474,8 @@ __device__ __forceinline__ bool compact_solve_range(
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = w0 + (int)blockIdx.x * per, a1 = min(w0 + n, a0 + per);
     const int tid = threadIdx.x, nt = NT;
-    // the fused iteration (eight table rows) up to kFusePerThread pixels per
-    // thread; the other paths read six
-    const int fuse = n_inner == 1 && per <= kFusePerThread * NT;
-    const int rows = fuse ? NB_COUNT : NB_UUR;
-    if (n_inner == 1 && !fuse) {
+    const int rows = kNbRows;
+    if (n_inner == 1) {
         // w of the warm-start iterate first, from the global arrays (every
         // path below then starts from it)
         if (warm) {
@@ -1828,17 +1665,17 @@ __device__ __forceinline__ bool compact_solve_range(
         }
         __syncthreads();
         const Own<T, true> O{nb_s, per, v_s, F, a0};
-        if (!compact_iterations<T, true, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
-                                                     stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
-                                                     ckpt, ckpt_every, s_red, fuse, gen))
+        if (!compact_iterations<T, Own<T, true>, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol,
+                                                             warm, stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2,
+                                                             partials, h, ckpt, ckpt_every, s_red, gen))
             return false;
         for (int i = tid; i < a1 - a0; i += nt) V[a0 + i] = v_s[i];
         return true;
     }
     const Own<T, false> O{nb, stride, V, F, 0};
-    return compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
-                                                    stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
-                                                    ckpt, ckpt_every, s_red, fuse, gen);
+    return compact_iterations<T, Own<T, false>, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol,
+                                                            warm, stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2,
+                                                            partials, h, ckpt, ckpt_every, s_red, gen);
 }
 
 // Batches solved in waves: with a fixed iteration count (tol <= 0, so no
@@ -1915,14 +1752,11 @@ k_solve_compact_wide(IterParams P, int iters, int n_inner, int check_every, doub
     const unsigned nblocks = gridDim.x;
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
-    // (never the fused iteration: this kernel runs only when the one-block
-    // kernel's blocks would hold more than 8,000 pixels each, so with at
-    // most twice its blocks each block holds more than 3 x NT)
-    const Own<T, false> O{nb, stride, V, F, 0};
     unsigned gen = 0u;
-    compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm, stride, P1a,
-                                             P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h, ckpt, ckpt_every,
-                                             s_red, 0, gen);
+    const Own<T, false> O{nb, stride, V, F, 0};
+    compact_iterations<T, Own<T, false>, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
+                                                     stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
+                                                     ckpt, ckpt_every, s_red, gen);
 }
 
 // Dense u, v, p1, p2 of the final iterate of every image of the batch:

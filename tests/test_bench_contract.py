@@ -24,6 +24,8 @@ def test_reference_arm_line():
     for key in ("n_gpus", "steps", "warmup", "scaling", "vs_baseline", "dtype", "data", "config",
                 "cpu_baseline", "e2e"):
         assert key in line, key
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    import oracle
+    cores = oracle.threads() if oracle.has_omp() else 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == cores
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
-    assert line["config"]["workload"].startswith("ds256")
+    assert line["config"]["workload"].startswith("cv256")

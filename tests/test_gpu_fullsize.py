@@ -80,7 +80,11 @@ def _cmp32(out, st, theta=0.2):
         assert d <= TOL_U32, (k, d)
     d = theta * np.max(np.abs(_div(out["p1"], out["p2"]) - _div(st.p1, st.p2)))
     assert d <= TOL_P32, ("theta div p", d)
-    assert np.max(out["p1"] ** 2 + out["p2"] ** 2) <= 1 + 1e-6
+    # |p| <= 1 holds exactly in exact arithmetic; each float32 step (hardware
+    # reciprocal square root and fast divide, a few ulp) can leave |p| a few
+    # ulp above 1, and where |g| is near 0 the step barely contracts that
+    # excess, so it random-walks: about sqrt(K) x 1e-7 after K iterations
+    assert np.sqrt(np.max(out["p1"] ** 2 + out["p2"] ** 2)) <= 1 + 1e-4
 
 
 @pytest.mark.parametrize("mode,delta,tile_h", [("compact", 0.2, 32), ("dense", math.inf, 32)])
