@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--profile-next", action="store_true",
                     help="with --profile: also the primal-dual solve of the same image and a "
                          "128^3 spheres volume (restricted delta = 0.1), --iters iterations each")
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="with --profile: instead of the workload, one 1024^2 image of the "
+                         "differentiation workload, forward and adjoint, --iters iterations "
+                         "(default 40), checkpoints every 20")
     ap.add_argument("--profile-large", action="store_true",
                     help="with --profile: instead of the workload, the 4096^2 polygon image "
                          "(delta = --delta, storage = --storage) and the batch of 64 images, "
@@ -390,6 +394,21 @@ def run_profile(args):
     if args.profile_large:
         run_profile_large(args, dev)
         return
+    if args.profile_adjoint:
+        from paper_1807_11534_gb300 import synth
+        iters = args.iters or 40
+        Pd = synth.training_batch(seed=0, n_images=1, side=1024, iters=iters)[0]
+        S = seg.DiffSolver(1024, 1024, iters, 20, device=dev)
+        S.fitting(seg.upload(Pd.z, dev), 0.3, 0.7)
+        S.domain(delta=0.2)
+        S.solve_diff(1.0)
+        g = seg.image(1024, 1024, device=dev)
+        g[:, :1024] = S.u[:, :1024] - seg.upload(Pd.label.astype(np.float32), dev)[:, :1024]
+        S.backward(g)
+        torch.cuda.synchronize()
+        S.check_status()
+        print(f"adjoint: active={int(S.dom.counts[1])} iters={iters}")
+        return
     P = make_problem(args)
     H, W = P.z.shape
     z = seg.upload(P.z, dev)
@@ -586,35 +605,56 @@ def _graph_ms(g, stream, flush, reps=3):
 def row_adjoint(dev, flush):
     """Differentiation workload: 8 images of 1024x1024 (random shapes, CV term
     c1 = 0.3, c2 = 0.7, lambda = 1, delta = 0.2), K = 200 unrolled iterations
-    with checkpoints every 20, forward (seg_solve_diff) and hand-written
-    adjoint (seg_backward) of every image in one CUDA graph each; the BCE
-    gradient on u_K is formed once, its values do not change the work."""
+    with checkpoints every 20.  The batch: forward of all 8 images in one
+    persistent launch (seg_solve_diff_batch) and the hand-written adjoint of
+    all 8 in one reverse sweep (seg_backward_batch), each replayed from a
+    CUDA graph; beside it the same work image by image (seg_solve_diff,
+    seg_backward).  The BCE gradient on u_K is formed once; its values do
+    not change the work."""
     import torch
     from paper_1807_11534_gb300 import seg, synth
     stream = torch.cuda.current_stream()
     probs = synth.training_batch(seed=0, n_images=8, side=1024, iters=200)
-    sols, grads, A = [], [], 0
-    for P in probs:
-        S = seg.DiffSolver(1024, 1024, 200, 20, device=dev)
-        S.fitting(seg.upload(P.z, dev), 0.3, 0.7)
+    zs = [seg.upload(P.z, dev) for P in probs]
+    B = seg.BatchDiffSolver([(1024, 1024)] * 8, 200, 20, device=dev)
+    for S, z in zip(B.solvers, zs):
+        S.fitting(z, 0.3, 0.7)
         S.domain(delta=0.2)
-        S.solve_diff(1.0)
+    lams = [1.0] * 8
+    B.solve_diff(lams)
+    grads, A = [], 0
+    for P, S in zip(probs, B.solvers):
         u = S.u[:, :1024].clamp(1e-4, 1 - 1e-4)
         m = seg.upload(P.label.astype(np.float32), dev)[:, :1024]
         g = seg.image(1024, 1024, device=dev)
         g[:, :1024] = (u - m) / (u * (1 - u)) / u.numel()
-        torch.cuda.synchronize()
         A += int(S.dom.counts[1].item())
-        sols.append(S)
         grads.append(g)
-    gf = seg.capture_graph(lambda: [S.solve_diff(1.0) for S in sols])
-    gb = seg.capture_graph(lambda: [S.backward(g) for S, g in zip(sols, grads)])
+    torch.cuda.synchronize()
+    gf = seg.capture_graph(lambda: B.solve_diff(lams))
+    gb = seg.capture_graph(lambda: B.backward(grads))
     tf, tb = _graph_ms(gf, stream, flush), _graph_ms(gb, stream, flush)
+    B.check_status()
+    del gf, gb
+    # image by image
+    sols = []
+    for z in zs:
+        S = seg.DiffSolver(1024, 1024, 200, 20, device=dev)
+        S.fitting(z, 0.3, 0.7)
+        S.domain(delta=0.2)
+        S.solve_diff(1.0)
+        sols.append(S)
+    torch.cuda.synchronize()
+    gf1 = seg.capture_graph(lambda: [S.solve_diff(1.0) for S in sols])
+    gb1 = seg.capture_graph(lambda: [S.backward(g) for S, g in zip(sols, grads)])
+    tf1, tb1 = _graph_ms(gf1, stream, flush), _graph_ms(gb1, stream, flush)
     for S in sols:
         S.check_status()
-    return {"config": "8 x 1024^2, K=200, C=20, lambda=1, delta=0.2 (BCE on u_K)",
+    return {"config": "8 x 1024^2, K=200, C=20, lambda=1, delta=0.2 (BCE on u_K); the 8 images in one "
+                      "launch each way",
             "active_pixels": A, "forward_ms": tf, "backward_ms": tb, "backward_over_forward": tb / tf,
-            "active_Mpixel_iter_per_s": A * 200 / ((tf + tb) * 1e-3) / 1e6}
+            "active_Mpixel_iter_per_s": A * 200 / ((tf + tb) * 1e-3) / 1e6,
+            "per_image": {"forward_ms": tf1, "backward_ms": tb1, "backward_over_forward": tb1 / tf1}}
 
 
 def _oracle_parallel():

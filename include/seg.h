@@ -385,6 +385,46 @@ seg_status seg_solve_diff(const float* f, int H, int W, int ld,
                           int ckpt_every, void* ckpt, size_t ckpt_bytes, double* stats,
                           void* ws, size_t ws_bytes, void* stream);
 
+/* seg_solve_diff for a batch of images solved together (not in the paper):
+ * the images of seg_solve_batch in one persistent launch, compact mode,
+ * float32 storage, n_inner = 1, cold start, a fixed number of iterations
+ * (tol <= 0), writing the batch's iterate (p1, p2, v) every ckpt_every
+ * iterations into `ckpt` (seg_ckpt_bytes for the batch's capacity).  The
+ * images' iterates are those of seg_solve_diff on each image alone.  state
+ * as for seg_solve_batch; ws: seg_batch_workspace_bytes bytes.
+ * Errors: INVALID_ARG, ALIGN, CAPACITY, WORKSPACE, CUDA. */
+seg_status seg_solve_diff_batch(const seg_image* images, int n_images, const seg_params* prm,
+                                void* state, size_t state_bytes, int ckpt_every, void* ckpt,
+                                size_t ckpt_bytes, double* stats, void* ws, size_t ws_bytes,
+                                void* stream);
+
+/* Per-image arguments of seg_backward_batch (host struct holding device
+ * pointers), as the arguments of the same names of seg_backward. */
+typedef struct seg_adj_image {
+    const float* grad_u;   /* dL/du^K, [H][ld] */
+    const float* grad_v;   /* NULL or dL/dv^K, [H][ld] */
+    const float* z;        /* NULL, or the image z of Eq. CV (then c is required) */
+    const double* c;       /* with z: the c1, c2 used, device double[2] */
+    float* grad_f;         /* out: dL/df, [H][ld], 0 outside RD */
+    double* grad_out;      /* out: device double[3], dL/dlambda, dL/dc1, dL/dc2 */
+} seg_adj_image;
+
+/* Reverse mode of seg_solve_diff_batch (not in the paper): the adjoint of
+ * every image of the batch in one persistent reverse sweep (the segments
+ * are recomputed from the checkpoints as in seg_backward), with the
+ * per-image gradients of seg_backward.  images, state, ckpt and prm must be
+ * those of the seg_solve_diff_batch call, unmodified; adj holds n_images
+ * entries.  scratch: seg_backward_scratch_bytes for the batch's capacity;
+ * ws: seg_batch_workspace_bytes bytes (the compact bases are recomputed from
+ * the images' domain counts).  The per-image sums for lambda, c1 and c2 are
+ * reduced in the same fixed order as seg_backward's, so each image's
+ * gradients equal those of seg_backward on that image alone.
+ * Errors: INVALID_ARG, ALIGN, CAPACITY, WORKSPACE, CUDA. */
+seg_status seg_backward_batch(const seg_image* images, const seg_adj_image* adj, int n_images,
+                              const seg_params* prm, const void* state, size_t state_bytes,
+                              const void* ckpt, size_t ckpt_bytes, int ckpt_every, void* scratch,
+                              size_t scratch_bytes, void* ws, size_t ws_bytes, void* stream);
+
 /* Reverse mode of the unrolled iteration run by seg_solve_diff (not in the
  * paper): given dL/du^K (grad_u, [H][ld]) and optionally dL/dv^K (grad_v),
  * returns dL/df (grad_f, [H][ld], 0 outside RD) and grad_out = {dL/dlambda,

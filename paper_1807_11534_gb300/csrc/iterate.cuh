@@ -59,14 +59,18 @@ __device__ __forceinline__ bool grid_wait(WsHeader* h, unsigned nblocks, unsigne
     __shared__ int s_ok, s_done;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned target = nblocks * gen + h->bar_extra;
-        const long long t0 = clock64(), budget = wait_budget(h);
-        while ((int)(ld_acquire_gpu(&h->bar_count) - target) < 0) {
-            if (clock64() - t0 > budget) {
-                record_status(h, SEG_ERR_TIMEOUT);
-                h->done = 1;
-                ok = 0;
-                break;
+        const unsigned target = nblocks * gen;
+        // the wait bound is read only when the first poll fails, so the
+        // block that completes the barrier pays no extra load
+        if ((int)(ld_acquire_gpu(&h->bar_count) - target) < 0) {
+            const long long t0 = clock64(), budget = wait_budget(h);
+            while ((int)(ld_acquire_gpu(&h->bar_count) - target) < 0) {
+                if (clock64() - t0 > budget) {
+                    record_status(h, SEG_ERR_TIMEOUT);
+                    h->done = 1;
+                    ok = 0;
+                    break;
+                }
             }
         }
         s_ok = ok;

@@ -78,7 +78,8 @@ struct WsHeader {
     // its own cache line
     alignas(128) unsigned bar_count;
     unsigned bar_extra;  // arrivals a grid barrier waits for beyond the launch's blocks: 0,
-                         // except to test the timeout path (seg_set_wait_limit)
+                         // except to test the timeout path (seg_set_wait_limit); the
+                         // counter starts at -bar_extra instead of 0
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
@@ -325,6 +326,7 @@ __device__ __forceinline__ long long wait_budget(const WsHeader* h) {
 // Waits for phase `parity` of `bar` for at most the workspace's wait bound;
 // returns false (after recording SEG_ERR_TIMEOUT) when the wait runs out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, WsHeader* h) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64(), budget = wait_budget(h);
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > budget) {

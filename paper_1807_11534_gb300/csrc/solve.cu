@@ -24,10 +24,10 @@
 //              iteration reads (or a code for a fixed / outside pixel).  One
 //              persistent cooperative launch runs every iteration: a dual
 //              phase (p') and a primal phase (u', v', and w = div p - v/theta
-//              for the next dual phase), with one grid barrier per iteration
-//              when the state fits in shared memory and two otherwise; each
-//              block keeps what it can of its pixels' state in shared memory
-//              (see the persistent compact solver below).
+//              for the next dual phase) separated by grid barriers, or one
+//              fused phase per iteration when each block holds at most one
+//              pixel; each block keeps what it can of its pixels' state in
+//              shared memory (see the persistent compact solver below).
 // Per-block FP64 partial sums of |du|^2, |dv|^2 feed a fixed-order reduction,
 // so the stopping test is deterministic.  Once it fires, a device flag makes
 // every later launch of the solve return immediately.
@@ -228,8 +228,10 @@ __global__ void k_final_dense(IterParams P, const WsHeader* __restrict__ h, int 
 // ========================================================== compact stencil
 
 // neighbour slots of the table and the codes for pixels that are not in RD
-enum { NB_UP = 0, NB_LEFT = 1, NB_DOWN = 2, NB_RIGHT = 3, NB_DOWNLEFT = 4, NB_UPRIGHT = 5, NB_COUNT = 6 };
-constexpr int kNbRows = NB_COUNT;   // neighbour rows an iteration reads
+// (NB_UUR = (i-2, j+1) and NB_LLD = (i+1, j-2) are the neighbours of x - e1
+// and x - e2 that the fused iteration needs when it redoes their dual step)
+enum { NB_UP = 0, NB_LEFT = 1, NB_DOWN = 2, NB_RIGHT = 3, NB_DOWNLEFT = 4, NB_UPRIGHT = 5, NB_UUR = 6,
+       NB_LLD = 7, NB_COUNT = 8 };
 constexpr int kNbBg = -1;    // fixed background: p = 0, v = 0
 constexpr int kNbFg = -2;    // fixed foreground: p = 0, v = 1
 constexpr int kNbOut = -3;   // outside the image (the gradient there is 0)
@@ -240,7 +242,7 @@ struct CompactState {
     float* u;
     float* w;        // div p - v/theta of the current iterate
     int32_t* nb;     // [NB_COUNT][stride]
-    float* w2;       // scratch of the one-barrier path (export marks)
+    float* w2;       // the other w buffer of the fused iteration
     float* up;       // u of the iteration before a stopping test
     int64_t cap;
     int64_t stride;
@@ -374,6 +376,8 @@ __global__ void k_compact_gather(IterParams P, BatchDesc B, const int32_t* __res
     nb[NB_RIGHT * st + idx] = code(i, j + 1);
     nb[NB_DOWNLEFT * st + idx] = code(i + 1, j - 1);
     nb[NB_UPRIGHT * st + idx] = code(i - 1, j + 1);
+    nb[NB_UUR * st + idx] = code(i - 2, j + 1);
+    nb[NB_LLD * st + idx] = code(i + 1, j - 2);
 }
 
 template <typename T>
@@ -418,9 +422,15 @@ __device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, flo
 //   primal phase u', v', w', stop-test partials          -> barrier
 //   (check iterations) block 0 sums the partials in a fixed order and raises
 //   the done flag, which every block reads after the next barrier.
-// The grid takes the one-barrier path with shared-memory state and a ring
-// (n_inner = 1, every block's state fits, by a grid-wide vote): see
-// compact_iterations_h1.
+// The grid takes one of these (the same in every block):
+//  * fused (n_inner = 1, at most one pixel per block: very sparse domains,
+//    where the ring set-up below costs more than it saves): one phase and one barrier
+//    per iteration; the thread of x also redoes the dual steps of x - e1 and
+//    x - e2 (same inputs, same arithmetic, same rounding as their owners),
+//    which is all the v-step of x needs, and w is ping-ponged.  The iterates
+//    are bit-identical to the two-phase ones.
+//  * one barrier with shared-memory state and a ring (n_inner = 1, every
+//    block's state fits, by a grid-wide vote): see compact_iterations_h1.
 // Otherwise each block takes the first of these that applies (blocks may
 // differ; all keep the same two-barrier protocol and the same global arrays
 // current):
@@ -435,6 +445,10 @@ constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 112 * 1
 constexpr int kCompactThreads = 512;   // two blocks per SM: one block's block barriers overlap the other's work
 constexpr int kCompactWideUnroll = 2;   // pixels per thread in flight in k_solve_compact_wide
 constexpr int kCompactUnroll = 4;       // pixels per thread in flight in the two-phase iteration
+// the fused iteration for blocks of at most this many pixels (the one-barrier
+// ring path measured faster at every size tried above it, 0.6 to 5 pixels
+// per thread)
+constexpr int kFuseMaxPerBlock = 1;
 
 // Own-pixel arrays (neighbour-table rows, v) of the pixels a block updates:
 // SH, copies in shared memory indexed from the block's first pixel a0; else
@@ -461,8 +475,8 @@ struct Own {
 // neighbour is in RD, and formed from p(x) and p(x+e1-e2) (resp. p(x+e2-e1))
 // where it is fixed.  p1 vanishes on the last row and p2 on the last column
 // (their gradient component is 0 there and they start at 0).
-template <typename T, class OwnT>
-__device__ __forceinline__ void dual_one(const IterParams& P, int a, const OwnT& O, const T* P1i,
+template <typename T, bool SH>
+__device__ __forceinline__ void dual_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1i,
                                          const T* P2i, const float* Wc, T* P1o, T* P2o, uint32_t seed) {
     const int n_down = O.nbr(NB_DOWN, a);
     const int n_right = O.nbr(NB_RIGHT, a);
@@ -490,8 +504,8 @@ __device__ __forceinline__ void dual_one(const IterParams& P, int a, const OwnT&
 // lambda f) (v updated in place), w' = div p' - v'/theta for the next dual
 // step.  wonly: just w = div p' - v/theta (between extra fixed-point sweeps,
 // or for a warm start).
-template <typename T, class OwnT>
-__device__ __forceinline__ void primal_one(const IterParams& P, int a, const OwnT& O, const T* P1n,
+template <typename T, bool SH>
+__device__ __forceinline__ void primal_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1n,
                                            const T* P2n, float* U, float* Up, float* Wc, bool wonly,
                                            bool check, bool write_u, bool write_prev, uint32_t seed,
                                            float& du2, float& dv2) {
@@ -519,20 +533,94 @@ __device__ __forceinline__ void primal_one(const IterParams& P, int a, const Own
     if (write_u) U[a] = un;
 }
 
+// One fused iteration at one RD pixel (n_inner = 1): p'(x) as the dual step
+// computes it, p1'(x - e1) and p2'(x - e2) as the dual steps of x - e1 and
+// x - e2 compute them (their neighbours below / right are x, x - e1 + e2 and
+// x + e1 - e2, x; a fixed one of those needs p at (i-2, j+1) resp.
+// (i+1, j-2)), each rounded as its owner stores it; then the primal step of
+// x.  Reads p, w of the current iterate (P1i, P2i, Wi), writes p', w' to the
+// other buffers and v in place.
+template <typename T, bool SH>
+__device__ __forceinline__ void fused_one(const IterParams& P, int a, const Own<T, SH>& O, const T* P1i,
+                                          const T* P2i, const float* Wi, T* P1o, T* P2o, float* Wo, float* U,
+                                          float* Up, bool check, bool write_u, bool write_prev, uint32_t seed_d,
+                                          uint32_t seed_p, float& du2, float& dv2) {
+    const int n_up = O.nbr(NB_UP, a), n_left = O.nbr(NB_LEFT, a);
+    const int n_down = O.nbr(NB_DOWN, a), n_right = O.nbr(NB_RIGHT, a);
+    const int n_dl = O.nbr(NB_DOWNLEFT, a), n_ur = O.nbr(NB_UPRIGHT, a);
+    const int n_uur = n_up >= 0 ? O.nbr(NB_UUR, a) : kNbOut;
+    const int n_lld = n_left >= 0 ? O.nbr(NB_LLD, a) : kNbOut;
+    // every load of the step, independent of one another
+    const float p1 = Store<T>::ldc(P1i, a), p2 = Store<T>::ldc(P2i, a);
+    const float w0 = ldw(Wi + a);
+    const float wd = n_down >= 0 ? ldw(Wi + n_down) : 0.f;
+    const float wr = n_right >= 0 ? ldw(Wi + n_right) : 0.f;
+    const float p2dl = nb_ld(P2i, n_dl), p1ur = nb_ld(P1i, n_ur);
+    const float p1U = nb_ld(P1i, n_up), p2U = nb_ld(P2i, n_up);
+    const float wU = n_up >= 0 ? ldw(Wi + n_up) : 0.f;
+    const float wur = n_ur >= 0 ? ldw(Wi + n_ur) : 0.f;
+    const float p1uur = nb_ld(P1i, n_uur);
+    const float p1L = nb_ld(P1i, n_left), p2L = nb_ld(P2i, n_left);
+    const float wL = n_left >= 0 ? ldw(Wi + n_left) : 0.f;
+    const float wdl = n_dl >= 0 ? ldw(Wi + n_dl) : 0.f;
+    const float p2lld = nb_ld(P2i, n_lld);
+    // p'(x)
+    const float g1 = g_comp(n_down, wd, p1, p2dl, w0, P.inv_theta);
+    const float g2 = g_comp(n_right, wr, p1ur, p2, w0, P.inv_theta);
+    float q1, q2;
+    chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
+    const uint32_t rnd = mix32((uint32_t)a * 3u + seed_d);
+    q1 = Store<T>::st_sr(P1o, a, q1, rnd);
+    q2 = Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
+    // p1'(x - e1)
+    float q1u = 0.f;
+    if (n_up >= 0) {
+        const float gu2 = g_comp(n_ur, wur, p1uur, p2U, wU, P.inv_theta);
+        float b1, b2;
+        chambolle_update(p1U, p2U, w0 - wU, gu2, P.tau, b1, b2);
+        q1u = Store<T>::sr(b1, mix32((uint32_t)n_up * 3u + seed_d));
+    }
+    // p2'(x - e2)
+    float q2l = 0.f;
+    if (n_left >= 0) {
+        const float gl1 = g_comp(n_dl, wdl, p1L, p2lld, wL, P.inv_theta);
+        float b1, b2;
+        chambolle_update(p1L, p2L, gl1, w0 - wL, P.tau, b1, b2);
+        q2l = Store<T>::sr(b2, mix32(mix32((uint32_t)n_left * 3u + seed_d) ^ 0x9e3779b9u));
+    }
+    // primal step of x
+    const float div = (q1 - q1u) + (q2 - q2l);
+    const float vv = Store<T>::ld_rw(O.v, O.vi(a)) + Store<T>::vbias;
+    const float un = fmaf(-P.theta, div, vv);
+    const float vn = clamp01(un - O.fv(a));   // F = theta lambda f
+    const float vs = Store<T>::st_sr(O.v, O.vi(a), vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed_p)) +
+                     Store<T>::vbias;
+    Wo[a] = div - vs * P.inv_theta;
+    if (check) {
+        const float da = un - Up[a], db = vn - vv;
+        du2 = fmaf(da, da, du2);
+        dv2 = fmaf(db, db, dv2);
+    }
+    if (write_prev) Up[a] = un;
+    if (write_u) U[a] = un;
+}
+
 // The iterations of one block of the persistent compact solver (see above);
 // false when a grid barrier timed out.
-template <typename T, class OwnT, int NT, int UNROLL>
-__device__ __forceinline__ bool compact_iterations(const IterParams& P, const OwnT& O, int a0, int a1,
+template <typename T, bool SH, int NT, int UNROLL>
+__device__ __forceinline__ bool compact_iterations(const IterParams& P, const Own<T, SH>& O, int a0, int a1,
                                                    int iters, int n_inner, int check_every, double tol, int warm,
                                                    int64_t stride, T* P1a, T* P1b, T* P2a, T* P2b, float* Uu,
                                                    float* Up, float* Wc, float* Wc2, double* partials, WsHeader* h,
-                                                   float* ckpt, int ckpt_every, double* s_red, unsigned& gen) {
+                                                   float* ckpt, int ckpt_every, double* s_red, int fuse,
+                                                   unsigned& gen) {
     // gen: barriers passed (the arrival counter starts at 0 each solve and
     // runs on across the waves of a batch)
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = NT;
     int pb = 0;
-    // the block's pixels, UNROLL per thread in flight
+    // the block's pixels, UNROLL per thread in flight (one in the fused
+    // step, which keeps about three times as many values live)
     auto each = [&](auto&& op) {
         int a = a0 + tid;
         for (; a + (UNROLL - 1) * nt < a1; a += UNROLL * nt) {
@@ -540,6 +628,9 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
             for (int k = 0; k < UNROLL; ++k) op(a + k * nt);
         }
         for (; a < a1; a += nt) op(a);
+    };
+    auto each1 = [&](auto&& op) {
+        for (int a = a0 + tid; a < a1; a += nt) op(a);
     };
     float dummy0 = 0.f, dummy1 = 0.f;
     // current / other ping-pong buffers of p, selected without indexing
@@ -565,6 +656,76 @@ __device__ __forceinline__ bool compact_iterations(const IterParams& P, const Ow
         }
     };
     if (ckpt) save(0);
+    if (fuse) {   // fused: one phase and one barrier per iteration
+        int wb = 0, chk = 0;
+        for (int it = 0; it < iters; ++it) {
+            const int l = it + 1;
+            const bool check = (l % C == 0) || l == iters;
+            const bool write_u = check;   // the output u and the stopped iterate
+        const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
+            const uint32_t seed_d = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
+            const uint32_t seed_p = mix32(0x2545f491u ^ (uint32_t)it);
+            const T* pi1 = p1c(); const T* pi2 = p2c();
+            T* po1 = p1o(); T* po2 = p2o();
+            const float* wi = wb ? Wc2 : Wc;
+            float* wo = wb ? Wc : Wc2;
+            float du2 = 0.f, dv2 = 0.f;
+            if (!check && !write_prev)
+                each1([&](int a) {
+                    fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, Up, false, false, false, seed_d, seed_p, du2,
+                              dv2);
+                });
+            else
+                each1([&](int a) {
+                    fused_one(P, a, O, pi1, pi2, wi, po1, po2, wo, Uu, Up, check, write_u, write_prev, seed_d,
+                              seed_p, du2, dv2);
+                });
+            pb ^= 1;
+            wb ^= 1;
+            if (ckpt && l % ckpt_every == 0 && l < iters) save(l / ckpt_every);   // own pixels: no barrier
+            // stopping-test partials, double-buffered by check so that a fast
+            // block cannot overwrite those a slow block is still summing
+            double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
+            if (check) {
+                float x = du2, y = dv2;
+                block_sum2f<NT>(x, y, reinterpret_cast<float*>(s_red));
+                if (tid == 0) {
+                    part[2 * blockIdx.x] = x;
+                    part[2 * blockIdx.x + 1] = y;
+                }
+            }
+            if (!grid_sync(h, nblocks, gen)) return false;
+            if (check) {
+                // Section 4 stopping test: every block sums the block partials
+                // in the same fixed order, so all stop at the same iteration
+                // (squared norms against tol^2: the square roots are taken
+                // once, for the stats)
+                if (tid < 32) {
+                    double sx, sy;
+                    sum_partials_warp0(part, (int)nblocks, sx, sy);
+                    if (tid == 0) {
+                        const bool stop = tol > 0.0 && fmax(sx, sy) <= tol * tol;
+                        s_red[0] = stop ? 1.0 : 0.0;
+                        if (blockIdx.x == 0) {
+                            h->du2 = sx;
+                            h->dv2 = sy;
+                            h->last_check = l;
+                            if (stop) {
+                                h->iters_done = l;
+                                h->done = 1;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                const bool stop = s_red[0] != 0.0;
+                ++chk;
+                __syncthreads();
+                if (stop) return true;
+            }
+        }
+        return true;
+    }
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
         for (int sw = 0; sw < n_inner; ++sw) {
@@ -1458,7 +1619,7 @@ __device__ __forceinline__ int compact_solve_h1(
 template <typename T>
 __device__ __forceinline__ bool compact_wide(int n, int grid1) {
     const int64_t per1 = ((int64_t)n + grid1 - 1) / grid1;
-    return (size_t)per1 * (4 * kNbRows + sizeof(T)) > compact_smem(kCompactThreads);
+    return (size_t)per1 * (4 * NB_UUR + sizeof(T)) > compact_smem(kCompactThreads);
 }
 
 // All iterations of the compact solve over the RD pixels [w0, w0 + n) (the
@@ -1474,8 +1635,11 @@ __device__ __forceinline__ bool compact_solve_range(
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = w0 + (int)blockIdx.x * per, a1 = min(w0 + n, a0 + per);
     const int tid = threadIdx.x, nt = NT;
-    const int rows = kNbRows;
-    if (n_inner == 1) {
+    // the fused iteration (eight table rows) up to kFuseMaxPerBlock pixels
+    // per block; the other paths read six
+    const int fuse = n_inner == 1 && per <= kFuseMaxPerBlock;
+    const int rows = fuse ? NB_COUNT : NB_UUR;
+    if (n_inner == 1 && !fuse) {
         // w of the warm-start iterate first, from the global arrays (every
         // path below then starts from it)
         if (warm) {
@@ -1665,17 +1829,17 @@ __device__ __forceinline__ bool compact_solve_range(
         }
         __syncthreads();
         const Own<T, true> O{nb_s, per, v_s, F, a0};
-        if (!compact_iterations<T, Own<T, true>, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol,
-                                                             warm, stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2,
-                                                             partials, h, ckpt, ckpt_every, s_red, gen))
+        if (!compact_iterations<T, true, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
+                                                     stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
+                                                     ckpt, ckpt_every, s_red, fuse, gen))
             return false;
         for (int i = tid; i < a1 - a0; i += nt) V[a0 + i] = v_s[i];
         return true;
     }
     const Own<T, false> O{nb, stride, V, F, 0};
-    return compact_iterations<T, Own<T, false>, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol,
-                                                            warm, stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2,
-                                                            partials, h, ckpt, ckpt_every, s_red, gen);
+    return compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
+                                                    stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
+                                                    ckpt, ckpt_every, s_red, fuse, gen);
 }
 
 // Batches solved in waves: with a fixed iteration count (tol <= 0, so no
@@ -1752,11 +1916,14 @@ k_solve_compact_wide(IterParams P, int iters, int n_inner, int check_every, doub
     const unsigned nblocks = gridDim.x;
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
-    unsigned gen = 0u;
+    // (never the fused iteration: this kernel runs only when the one-block
+    // kernel's blocks would hold more than 8,000 pixels each, so with at
+    // most twice its blocks each block holds more than 3 x NT)
     const Own<T, false> O{nb, stride, V, F, 0};
-    compact_iterations<T, Own<T, false>, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm,
-                                                     stride, P1a, P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h,
-                                                     ckpt, ckpt_every, s_red, gen);
+    unsigned gen = 0u;
+    compact_iterations<T, false, NT, UNROLL>(P, O, a0, a1, iters, n_inner, check_every, tol, warm, stride, P1a,
+                                             P1b, P2a, P2b, U, Up, Wc, Wc2, partials, h, ckpt, ckpt_every,
+                                             s_red, 0, gen);
 }
 
 // Dense u, v, p1, p2 of the final iterate of every image of the batch:
@@ -1796,7 +1963,7 @@ __global__ void k_compact_scatter(BatchDesc B, const int32_t* __restrict__ base,
 // =================================================== stopping test, stats
 
 __global__ void k_solve_begin(WsHeader* h) {
-    h->bar_count = 0u;
+    h->bar_count = 0u - h->bar_extra;   // 0 unless the timeout path is under test
     h->done = 0;
     h->iters_done = 0;
     h->last_check = 0;
@@ -2124,7 +2291,7 @@ struct AdjArrays {
 
 // gathers dL/du^K, dL/dv^K into compact order and clears the adjoint
 __global__ void k_adj_gather(IterParams P, const uint32_t* __restrict__ act,
-                             const int32_t* __restrict__ wstart, const int32_t* __restrict__ counts,
+                             const int32_t* __restrict__ wstart, const int32_t* __restrict__ base,
                              const float* __restrict__ grad_u, const float* __restrict__ grad_v,
                              AdjArrays A) {
     const int lane = threadIdx.x & 31;
@@ -2136,7 +2303,7 @@ __global__ void k_adj_gather(IterParams P, const uint32_t* __restrict__ act,
     const int64_t wo = (int64_t)i * P.nw + wx;
     const uint32_t a = act[wo];
     if (!((a >> lane) & 1u)) return;
-    const int64_t idx = wstart[wo] + __popc(a & lanemask_lt(lane));
+    const int64_t idx = (base ? *base : 0) + wstart[wo] + __popc(a & lanemask_lt(lane));
     const int64_t o = (int64_t)i * P.ld + wx * 32 + lane;
     A.gu[idx] = grad_u[o];
     A.gv[idx] = grad_v ? grad_v[o] : 0.f;
@@ -2285,10 +2452,11 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
 // (fixed grid of kReduceBlocks blocks: deterministic).
 __global__ void __launch_bounds__(256)
 k_adj_scatter(IterParams P, const float* __restrict__ f, const uint32_t* __restrict__ act,
-              const int32_t* __restrict__ wstart, const float* __restrict__ Fbar,
-              const float* __restrict__ z, const double* __restrict__ c, float theta_lambda,
-              float* __restrict__ grad_f, double* __restrict__ red) {
+              const int32_t* __restrict__ wstart, const int32_t* __restrict__ base,
+              const float* __restrict__ Fbar, const float* __restrict__ z, const double* __restrict__ c,
+              float theta_lambda, float* __restrict__ grad_f, double* __restrict__ red) {
     __shared__ double s_red[8];
+    if (base) Fbar += *base;   // the image's compact range within a batch
     double sl = 0.0, s1 = 0.0, s2 = 0.0;
     const int64_t n = (int64_t)P.H * P.W;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
@@ -2515,6 +2683,76 @@ extern "C" seg_status seg_solve_diff(const float* f, int H, int W, int ld, const
     return SEG_OK;
 }
 
+// The adjoint of a batch of images solved together by the differentiable
+// forward (a single image is a batch of one): gathers dL/du^K, dL/dv^K of
+// every image into compact order, one persistent reverse sweep over the
+// whole compact range (the images' iterations are independent and lambda
+// only enters through F = theta lambda_k f, so the sweep needs no per-image
+// data), then dL/df and the FP64 sums of every image.  base: device array
+// of the images' compact bases (base[k], and the total RD pixels in
+// totals[1]); launched on stream s after the header's reset.
+static seg_status backward_batch(const seg_params* prm, const BatchDesc& B, const seg_adj_image* adj,
+                                 const int32_t* base, const int32_t* totals, const void* state,
+                                 size_t state_bytes, const void* ckpt, int ckpt_every, void* scratch,
+                                 double* red, WsHeader* h, cudaStream_t s) {
+    CompactLayout C = compact_layout(state_bytes, prm->storage);
+    const char* sb = static_cast<const char*>(state);
+    const float* F = reinterpret_cast<const float*>(sb + C.off[5]);
+    const int32_t* nbp = reinterpret_cast<const int32_t*>(sb + C.off[8]);
+    int64_t stride = C.stride;
+    AdjArrays A{};
+    float* sc = static_cast<float*>(scratch);
+    float** fields[] = {&A.p1b, &A.p2b, &A.vb, &A.ub, &A.gb1, &A.gb2, &A.pd1, &A.pd2, &A.fb, &A.gu, &A.gv};
+    for (size_t k = 0; k < adj_float_arrays(); ++k) *fields[k] = sc + k * stride;
+    A.seg = sc + adj_float_arrays() * stride;
+    int64_t pixels = 0;
+    for (int k = 0; k < B.n; ++k) {
+        const BatchImage& I = B.img[k];
+        IterParams Pk = iter_params(prm, I.H, I.W, I.ld);
+        const int64_t nwords = (int64_t)I.H * Pk.ntx;
+        const unsigned gblocks = (unsigned)((nwords + 7) / 8);
+        k_adj_gather<<<gblocks, 256, 0, s>>>(Pk, I.act, I.wstart, B.n > 1 ? base + k : nullptr, adj[k].grad_u,
+                                             adj[k].grad_v, A);
+        SEG_LAUNCHED("k_adj_gather");
+        pixels += (int64_t)I.H * I.W;
+    }
+    auto kern = k_backward_compact;
+    int per_sm = 0;
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBackwardThreads, 0));
+    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_backward_compact cannot be resident");
+    const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, pixels));
+    int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
+                                      std::max<int64_t>(1, (most + kBackwardThreads - 1) / kBackwardThreads));
+    IterParams P = iter_params(prm, B.img[0].H, B.img[0].W, B.img[0].ld);
+    int iters = prm->iters, ce = ckpt_every;
+    const float* ck = static_cast<const float*>(ckpt);
+    const int32_t* cnt = totals;
+    void* args[] = {&P, &iters, &ce, (void*)&cnt, (void*)&nbp, &stride, (void*)&F, (void*)&ck, &A, &h};
+    if (iters > 0) {
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kBackwardThreads), args,
+                                                 0, s));
+        count_launch();
+    }
+    for (int k = 0; k < B.n; ++k) {
+        const BatchImage& I = B.img[k];
+        IterParams Pk = iter_params(prm, I.H, I.W, I.ld);
+        k_adj_scatter<<<kReduceBlocks, 256, 0, s>>>(Pk, I.f, I.act, I.wstart, B.n > 1 ? base + k : nullptr, A.fb,
+                                                    adj[k].z, adj[k].c, I.theta_lambda, adj[k].grad_f, red);
+        SEG_LAUNCHED("k_adj_scatter");
+        SEG_TRY(reduce_partials(red, kReduceBlocks, 3, adj[k].grad_out, s));
+    }
+    return SEG_OK;
+}
+
+static seg_status check_diff_params(const seg_params* prm, const char* who) {
+    SEG_TRY(check_params(prm));
+    if (prm->mode != SEG_MODE_COMPACT || prm->storage != SEG_STORE_F32 || prm->n_inner != 1 ||
+        prm->warm_start || prm->tol > 0)
+        return fail(SEG_ERR_INVALID_ARG, "%s: compact mode, float32 storage, n_inner = 1, cold start, tol <= 0",
+                    who);
+    return SEG_OK;
+}
+
 extern "C" seg_status seg_backward(const float* f, int H, int W, int ld, const uint32_t* act,
                                    const uint32_t* fgm, const int32_t* wstart, const int32_t* counts,
                                    const seg_params* prm, const void* state, size_t state_bytes,
@@ -2545,43 +2783,118 @@ extern "C" seg_status seg_backward(const float* f, int H, int W, int ld, const u
     SEG_TRY(check_ws(ws, ws_bytes, L));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     WsHeader* h = ws_at<WsHeader>(ws, L.header);
-    IterParams P = iter_params(prm, H, W, ld);
-    const char* sb = static_cast<const char*>(state);
-    const float* F = reinterpret_cast<const float*>(sb + C.off[5]);
-    const int32_t* nbp = reinterpret_cast<const int32_t*>(sb + C.off[8]);
-    int64_t stride = C.stride;
-    AdjArrays A{};
-    float* sc = static_cast<float*>(scratch);
-    float** fields[] = {&A.p1b, &A.p2b, &A.vb, &A.ub, &A.gb1, &A.gb2, &A.pd1, &A.pd2, &A.fb, &A.gu, &A.gv};
-    for (size_t k = 0; k < adj_float_arrays(); ++k) *fields[k] = sc + k * stride;
-    A.seg = sc + adj_float_arrays() * stride;
-
+    BatchDesc B{};
+    B.n = 1;
+    BatchImage& I = B.img[0];
+    I.f = f; I.act = act; I.fg = fgm; I.wstart = wstart; I.counts = counts;
+    I.H = H; I.W = W; I.ld = ld; I.nw = ld / 32; I.ntx = (W + 31) / 32;
+    I.theta_lambda = (float)(prm->theta * prm->lambda);
+    seg_adj_image adj{grad_u, grad_v, z, c, grad_f, grad_out};
     k_solve_begin<<<1, 1, 0, s>>>(h);
     SEG_LAUNCHED("k_solve_begin");
-    const int64_t nwords = (int64_t)H * P.ntx;
-    const unsigned gblocks = (unsigned)((nwords + 7) / 8);
-    k_adj_gather<<<gblocks, 256, 0, s>>>(P, act, wstart, counts, grad_u, grad_v, A);
-    SEG_LAUNCHED("k_adj_gather");
-    auto kern = k_backward_compact;
-    int per_sm = 0;
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBackwardThreads, 0));
-    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_backward_compact cannot be resident");
-    const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, (int64_t)H * W));
-    int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
-                                      std::max<int64_t>(1, (most + kBackwardThreads - 1) / kBackwardThreads));
-    int iters = prm->iters, ce = ckpt_every;
-    const float* ck = static_cast<const float*>(ckpt);
-    void* args[] = {&P, &iters, &ce, (void*)&counts, (void*)&nbp, &stride, (void*)&F, (void*)&ck, &A, &h};
-    if (iters > 0) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kBackwardThreads), args,
-                                                 0, s));
-        count_launch();
+    return backward_batch(prm, B, &adj, nullptr, counts, state, state_bytes, ckpt, ckpt_every, scratch,
+                          ws_at<double>(ws, kWsRedOff), h, s);
+}
+
+// The images of a batch as BatchDesc (checks of seg_solve_batch).
+static seg_status batch_desc(const seg_image* images, int n_images, const seg_params* prm, BatchDesc& B,
+                             long long& pixels) {
+    if (!images || n_images <= 0 || n_images > kMaxBatch)
+        return fail(SEG_ERR_INVALID_ARG, "n_images=%d not in [1, %d]", n_images, kMaxBatch);
+    B = BatchDesc{};
+    B.n = n_images;
+    long long words = 0;
+    pixels = 0;
+    for (int k = 0; k < n_images; ++k) {
+        const seg_image& X = images[k];
+        if (!X.f || !X.act || !X.fg || !X.wstart || !X.counts || !X.u || !X.v || !X.p1 || !X.p2)
+            return fail(SEG_ERR_INVALID_ARG, "image %d: a required pointer is NULL", k);
+        if (X.H <= 0 || X.W <= 0 || X.ld < X.W || (int64_t)X.H * X.ld >= (1ll << 31))
+            return fail(SEG_ERR_INVALID_ARG, "image %d: bad size H=%d W=%d ld=%d", k, X.H, X.W, X.ld);
+        if (X.ld % 32) return fail(SEG_ERR_ALIGN, "image %d: ld=%d is not a multiple of 32", k, X.ld);
+        if (!std::isfinite(X.lambda)) return fail(SEG_ERR_INVALID_ARG, "image %d: lambda not finite", k);
+        BatchImage& I = B.img[k];
+        I.f = X.f; I.act = X.act; I.fg = X.fg; I.wstart = X.wstart; I.counts = X.counts;
+        I.u = X.u; I.v = X.v; I.p1 = X.p1; I.p2 = X.p2;
+        I.word_off = words; I.H = X.H; I.W = X.W; I.ld = X.ld; I.nw = X.ld / 32; I.ntx = (X.W + 31) / 32;
+        I.theta_lambda = (float)(prm->theta * X.lambda);
+        words += (long long)X.H * I.ntx;
+        pixels += (long long)X.H * X.W;
     }
-    double* red = ws_at<double>(ws, kWsRedOff);
-    k_adj_scatter<<<kReduceBlocks, 256, 0, s>>>(P, f, act, wstart, A.fb, z, c, P.theta_lambda, grad_f, red);
-    SEG_LAUNCHED("k_adj_scatter");
-    SEG_TRY(reduce_partials(red, kReduceBlocks, 3, grad_out, s));
+    B.total_words = words;
+    if (pixels >= (1ll << 31)) return fail(SEG_ERR_INVALID_ARG, "batch holds %lld pixels (< 2^31)", pixels);
     return SEG_OK;
+}
+
+extern "C" seg_status seg_solve_diff_batch(const seg_image* images, int n_images, const seg_params* prm,
+                                           void* state, size_t state_bytes, int ckpt_every, void* ckpt,
+                                           size_t ckpt_bytes, double* stats, void* ws, size_t ws_bytes,
+                                           void* stream) {
+    clear_error();
+    SEG_TRY(check_diff_params(prm, "seg_solve_diff_batch"));
+    if (!state || !stats || !ckpt) return fail(SEG_ERR_INVALID_ARG, "state, ckpt and stats must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(state) % 16 || reinterpret_cast<uintptr_t>(ws) % 16 ||
+        reinterpret_cast<uintptr_t>(ckpt) % 16)
+        return fail(SEG_ERR_ALIGN, "state / ckpt / workspace not 16-byte aligned");
+    if (!ws || ws_bytes < seg_batch_workspace_bytes(n_images, 0))
+        return fail(SEG_ERR_WORKSPACE, "batch workspace needs %zu bytes", seg_batch_workspace_bytes(n_images, 0));
+    if (ckpt_every < 1) return fail(SEG_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+    BatchDesc B;
+    long long pixels = 0;
+    SEG_TRY(batch_desc(images, n_images, prm, B, pixels));
+    CompactLayout C = compact_layout(state_bytes, prm->storage);
+    if (ckpt_bytes < seg_ckpt_bytes(C.cap, prm->iters, ckpt_every))
+        return fail(SEG_ERR_CAPACITY, "checkpoints need %zu bytes", seg_ckpt_bytes(C.cap, prm->iters, ckpt_every));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader* h = ws_at<WsHeader>(ws, kWsHeaderOff);
+    int32_t* base = ws_at<int32_t>(ws, kWsBatchOff);
+    double* partials = ws_at<double>(ws, align_up(kWsFixedBytes, 256));
+    IterParams P = iter_params(prm, images[0].H, images[0].W, images[0].ld);
+    k_solve_begin<<<1, 1, 0, s>>>(h);
+    SEG_LAUNCHED("k_solve_begin");
+    SEG_TRY(solve_compact_batch<float>(P, prm, B, pixels, state, state_bytes, base, base + kMaxBatch + 2,
+                                       partials, 4096, h, s, static_cast<float*>(ckpt), ckpt_every));
+    k_solve_end<<<1, 1, 0, s>>>(h, base + kMaxBatch + 2, prm->iters, stats);
+    SEG_LAUNCHED("k_solve_end");
+    return SEG_OK;
+}
+
+extern "C" seg_status seg_backward_batch(const seg_image* images, const seg_adj_image* adj, int n_images,
+                                         const seg_params* prm, const void* state, size_t state_bytes,
+                                         const void* ckpt, size_t ckpt_bytes, int ckpt_every, void* scratch,
+                                         size_t scratch_bytes, void* ws, size_t ws_bytes, void* stream) {
+    clear_error();
+    SEG_TRY(check_params(prm));
+    if (prm->mode != SEG_MODE_COMPACT || prm->storage != SEG_STORE_F32 || prm->n_inner != 1)
+        return fail(SEG_ERR_INVALID_ARG, "seg_backward_batch: compact mode, float32 storage, n_inner = 1");
+    if (!adj || !state || !ckpt || !scratch) return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
+    BatchDesc B;
+    long long pixels = 0;
+    SEG_TRY(batch_desc(images, n_images, prm, B, pixels));
+    for (int k = 0; k < n_images; ++k)
+        if (!adj[k].grad_u || !adj[k].grad_f || !adj[k].grad_out || (adj[k].z && !adj[k].c))
+            return fail(SEG_ERR_INVALID_ARG, "image %d: a required adjoint pointer is NULL", k);
+    if (ckpt_every < 1) return fail(SEG_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+    if (!ws || ws_bytes < seg_batch_workspace_bytes(n_images, 0))
+        return fail(SEG_ERR_WORKSPACE, "batch workspace needs %zu bytes", seg_batch_workspace_bytes(n_images, 0));
+    if (reinterpret_cast<uintptr_t>(scratch) % 16 || reinterpret_cast<uintptr_t>(ws) % 16)
+        return fail(SEG_ERR_ALIGN, "scratch / workspace not 16-byte aligned");
+    CompactLayout C = compact_layout(state_bytes, prm->storage);
+    if (ckpt_bytes < seg_ckpt_bytes(C.cap, prm->iters, ckpt_every))
+        return fail(SEG_ERR_CAPACITY, "checkpoint buffer smaller than the forward wrote");
+    if (scratch_bytes < seg_backward_scratch_bytes(C.cap, ckpt_every))
+        return fail(SEG_ERR_WORKSPACE, "backward scratch needs %zu bytes",
+                    seg_backward_scratch_bytes(C.cap, ckpt_every));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader* h = ws_at<WsHeader>(ws, kWsHeaderOff);
+    int32_t* base = ws_at<int32_t>(ws, kWsBatchOff);
+    k_solve_begin<<<1, 1, 0, s>>>(h);
+    SEG_LAUNCHED("k_solve_begin");
+    // the compact bases of the forward, recomputed from the domains' counts
+    k_batch_bases<<<1, 1, 0, s>>>(B, base, base + kMaxBatch + 2, C.cap, h);
+    SEG_LAUNCHED("k_batch_bases");
+    return backward_batch(prm, B, adj, base, base + kMaxBatch + 2, state, state_bytes, ckpt, ckpt_every,
+                          scratch, ws_at<double>(ws, kWsRedOff), h, s);
 }
 
 // ================================================== restricted primal-dual

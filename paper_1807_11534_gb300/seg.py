@@ -75,6 +75,11 @@ class seg_image(ctypes.Structure):
                 ("lambda_", ctypes.c_double)]
 
 
+class seg_adj_image(ctypes.Structure):
+    _fields_ = [("grad_u", ctypes.c_void_p), ("grad_v", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("c", ctypes.c_void_p), ("grad_f", ctypes.c_void_p), ("grad_out", ctypes.c_void_p)]
+
+
 _lib = None
 
 # exported entry points and their C signatures (include/seg.h)
@@ -87,7 +92,6 @@ SIGNATURES = {
     "seg_workspace_bytes": ([_I, _I, _I, _I], _Z),
     "seg_state_bytes": ([_I, _I, _L, _I, _I], _Z),
     "seg_read_status": ([_P, _Z, _P], _I),
-    "seg_set_wait_limit": ([_P, _Z, ctypes.c_longlong, _I, _P], _I),
     "seg_make_fitting": ([_P, _I, _I, _I, _D, _D, _P, _P, _I, _D, _P, _P, _P, _Z, _P], _I),
     "seg_build_domain": ([_P, _I, _I, _I, _D, _D, _I, _P, _P, _P, _P, _I, _P, _L, _P, _P, _P, _Z, _P], _I),
     "seg_build_domain_robust": ([_P, _P, _I, _I, _I, _D, _D, _I, _I, _P, _P, _P, _P, _I, _P, _L, _P,
@@ -113,6 +117,11 @@ SIGNATURES = {
                      _P, _P, _Z, _P, _P, _Z, _P], _I),
     "seg_solve_batch": ([ctypes.POINTER(seg_image), _I, ctypes.POINTER(seg_params), _P, _Z, _P, _P, _Z,
                          _P], _I),
+    "seg_solve_diff_batch": ([ctypes.POINTER(seg_image), _I, ctypes.POINTER(seg_params), _P, _Z, _I, _P, _Z,
+                              _P, _P, _Z, _P], _I),
+    "seg_backward_batch": ([ctypes.POINTER(seg_image), ctypes.POINTER(seg_adj_image), _I,
+                            ctypes.POINTER(seg_params), _P, _Z, _P, _Z, _I, _P, _Z, _P, _Z, _P], _I),
+    "seg_set_wait_limit": ([_P, _Z, ctypes.c_longlong, _I, _P], _I),
 }
 
 
@@ -326,6 +335,20 @@ def seg_backward(f, act, fg, wstart, counts, params: seg_params, state, ckpt, ck
                             _ptr(grad_u), _ptr(grad_v), _ptr(z), _ptr(c), _ptr(grad_f),
                             _ptr(grad_out), _ptr(scratch), _nbytes(scratch), _ptr(ws), _nbytes(ws),
                             _stream(stream)))
+
+
+def seg_solve_diff_batch(images, params: seg_params, state, ckpt_every, ckpt, stats, ws, stream=None):
+    """`images`: a ctypes array of seg_image (device pointers)."""
+    _check(load().seg_solve_diff_batch(images, len(images), ctypes.byref(params), _ptr(state), _nbytes(state),
+                                       int(ckpt_every), _ptr(ckpt), _nbytes(ckpt), _ptr(stats), _ptr(ws),
+                                       _nbytes(ws), _stream(stream)))
+
+
+def seg_backward_batch(images, adj, params: seg_params, state, ckpt, ckpt_every, scratch, ws, stream=None):
+    """`images`, `adj`: ctypes arrays of seg_image and seg_adj_image."""
+    _check(load().seg_backward_batch(images, adj, len(images), ctypes.byref(params), _ptr(state),
+                                     _nbytes(state), _ptr(ckpt), _nbytes(ckpt), int(ckpt_every), _ptr(scratch),
+                                     _nbytes(scratch), _ptr(ws), _nbytes(ws), _stream(stream)))
 
 
 def seg_errors(u_star, u_gt, eps, out, ws, stream=None):
@@ -722,6 +745,47 @@ class DiffSolver(Solver):
                      self.ckpt_every, grad_u, grad_v, z, c, self.grad_f, self.grad_out,
                      self.scratch, self.ws, self.stream)
         return self.grad_f, self.grad_out
+
+
+class BatchDiffSolver(BatchSolver):
+    """A float32 BatchSolver whose batched solve can be differentiated: the
+    forward (seg_solve_diff_batch) keeps checkpoints every `ckpt_every`
+    iterations and `backward` runs the adjoint of every image in one
+    persistent sweep (seg_backward_batch)."""
+
+    def __init__(self, shapes, iters, ckpt_every=20, tile_h=16, capacity=None, device="cuda", stream=None):
+        super().__init__(shapes, tile_h=tile_h, storage="f32", capacity=capacity, device=device,
+                         stream=stream)
+        self.iters, self.ckpt_every = int(iters), int(ckpt_every)
+        nb = seg_ckpt_bytes(self.capacity, self.iters, self.ckpt_every)
+        self.ckpt = torch.empty((nb + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        nb = seg_backward_scratch_bytes(self.capacity, self.ckpt_every)
+        self.scratch = torch.empty((nb + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        for S in self.solvers:
+            S.grad_f = image(S.H, S.W, device=self.device)
+            S.grad_out = torch.zeros(3, dtype=torch.float64, device=self.device)
+        self._prm = None
+        self._lams = None
+
+    def solve_diff(self, lams, theta=0.2, tau=0.125):
+        self._lams = list(lams)
+        self._prm = make_params(1.0, theta, tau, self.iters, 0.0, 1, self.iters, False, "compact", "f32",
+                                self.tile_h)
+        seg_solve_diff_batch(self.images(self._lams), self._prm, self.state, self.ckpt_every, self.ckpt,
+                             self.stats, self.ws, self.stream)
+
+    def backward(self, grads_u, grads_v=None, zs=None, cs=None):
+        n = len(self.solvers)
+        adj = (seg_adj_image * n)()
+        for k, S in enumerate(self.solvers):
+            gv = grads_v[k] if grads_v is not None else None
+            z = zs[k] if zs is not None else None
+            c = cs[k] if cs is not None else None
+            adj[k] = seg_adj_image(_ptr(grads_u[k]), _ptr(gv), _ptr(z), _ptr(c), _ptr(S.grad_f),
+                                   _ptr(S.grad_out))
+        seg_backward_batch(self.images(self._lams), adj, self._prm, self.state, self.ckpt, self.ckpt_every,
+                           self.scratch, self.ws, self.stream)
+        return [(S.grad_f, S.grad_out) for S in self.solvers]
 
 
 class SegSolveFn(torch.autograd.Function):

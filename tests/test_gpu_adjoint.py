@@ -144,3 +144,70 @@ def test_autograd_function(orc):
     assert abs(c1.grad.item() - np.sum(gf_o * -2 * (zz - 0.3))) <= 1e-3 * max(1.0, abs(c1.grad.item()))
     assert abs(c2.grad.item() - np.sum(gf_o * 2 * (zz - 0.7))) <= 1e-3 * max(1.0, abs(c2.grad.item()))
     assert abs(lam2.grad.item() - gl_o) <= 1e-3 * max(1.0, abs(gl_o))
+
+
+def _batch_vs_single(orc, shapes, lams, delta, iters, ce, with_c):
+    seg = seg_mod()
+    rng = np.random.default_rng(len(shapes) + iters)
+    probs = [synth.small_example(seed=10 + k, H=h, W=w) for k, (h, w) in enumerate(shapes)]
+    fs = [orc.fitting(P.z, 0.3, 0.7)[1] for P in probs]
+    gus = [rng.normal(size=s).astype(np.float32) for s in shapes]
+    gvs = [rng.normal(size=s).astype(np.float32) for s in shapes]
+    B = seg.BatchDiffSolver(shapes, iters, ce)
+    for S, f in zip(B.solvers, fs):
+        S.f[:, :f.shape[1]].copy_(torch.from_numpy(f))
+        S.domain(delta=delta)
+    B.solve_diff(lams)
+    g_u = [seg.upload(g) for g in gus]
+    g_v = [seg.upload(g) for g in gvs]
+    zs = [seg.upload(P.z) for P in probs] if with_c else None
+    cs = [torch.tensor([0.3, 0.7], dtype=torch.float64, device="cuda") for _ in probs] if with_c else None
+    out = B.backward(g_u, g_v, zs, cs)
+    torch.cuda.synchronize()
+    B.check_status()
+    for k, (f, P) in enumerate(zip(fs, probs)):
+        gf1, gout1, S1 = _gpu_grad(f, delta, lams[k], gus[k], gvs[k], iters, ce,
+                                   z=P.z if with_c else None, c=[0.3, 0.7] if with_c else None)
+        Sb = B.solvers[k]
+        np.testing.assert_array_equal(seg.download(Sb.u), seg.download(S1.u))
+        np.testing.assert_array_equal(seg.download(out[k][0]).astype(np.float64), gf1)
+        np.testing.assert_array_equal(out[k][1].cpu().numpy(), gout1)
+
+
+@pytest.mark.parametrize("delta,iters,ce,with_c", [(0.2, 40, 20, True), (np.inf, 25, 7, False),
+                                                   (0.12, 30, 30, False)])
+def test_batched_adjoint_equals_the_per_image_adjoint(orc, delta, iters, ce, with_c):
+    """seg_solve_diff_batch + seg_backward_batch on images of uneven size and
+    lambda give, image by image, the same bits as seg_solve_diff +
+    seg_backward on that image alone: the forward iterates (u), dL/df and the
+    FP64 sums for lambda, c1, c2 (the images are independent problems, the
+    reverse sweep's arithmetic is per pixel, and the sums run per image in
+    the same fixed order)."""
+    _batch_vs_single(orc, [(67, 131), (90, 45), (33, 200), (128, 96)], [1.0, 1.7, 0.6, 2.5], delta, iters, ce,
+                     with_c)
+
+
+@pytest.mark.slow
+def test_batched_adjoint_on_the_differentiation_workload(orc):
+    """The differentiation workload's shape (8 images of 1024 x 1024, K = 200,
+    checkpoints every 20, delta = 0.2; the global-memory paths of the forward
+    and the reverse sweep): the batch against the per-image adjoint on two
+    of its images, bit for bit, and the per-image adjoint against the
+    oracle's reverse mode is covered above."""
+    seg = seg_mod()
+    probs = synth.training_batch(seed=0, n_images=8, side=1024, iters=200)
+    fs = [orc.fitting(P.z, 0.3, 0.7)[1] for P in probs]
+    B = seg.BatchDiffSolver([(1024, 1024)] * 8, 200, 20)
+    for S, f in zip(B.solvers, fs):
+        S.f[:, :1024].copy_(torch.from_numpy(f))
+        S.domain(delta=0.2)
+    B.solve_diff([1.0] * 8)
+    rng = np.random.default_rng(3)
+    gus = [rng.normal(size=(1024, 1024)).astype(np.float32) for _ in probs]
+    out = B.backward([seg.upload(g) for g in gus])
+    torch.cuda.synchronize()
+    B.check_status()
+    for k in (0, 5):
+        gf1, gout1, _ = _gpu_grad(fs[k], 0.2, 1.0, gus[k], None, 200, 20)
+        np.testing.assert_array_equal(seg.download(out[k][0]).astype(np.float64), gf1)
+        np.testing.assert_array_equal(out[k][1].cpu().numpy(), gout1)

@@ -280,6 +280,22 @@ def test_empty_and_full_domain_edges(orc):
             _cmp_state(out, st, TOL_U32, TOL_P32)
 
 
+@pytest.mark.parametrize("q", [0.0005, 0.0015])
+def test_fused_iteration_on_a_very_sparse_domain(orc, q):
+    """At most one RD pixel per block (33 and 99 RD pixels of a 256 x 256
+    image, 128 blocks): the compact solver takes its fused iteration (one
+    phase per iteration, the dual steps of x - e1 and x - e2 redone by the
+    thread of x), neither shared-memory path (stats[6] = stats[7] = 0)."""
+    P = _problem((256, 256), seed=12)
+    _, f = orc.fitting(P.z, 0.3, 0.7)
+    out = run_gpu(f, q=q, iters=80, mode="compact", tile_h=16)
+    n = int(out["counts"][1])
+    assert 0 < n <= 128
+    assert out["stats"][6] == 0 and out["stats"][7] == 0
+    st = orc.solve(f, orc.domain(f, out["delta"]), 1.0, iters=80)
+    _cmp_state(out, st, TOL_U32, TOL_P32)
+
+
 def test_compact_capacity_overflow_is_reported():
     seg = seg_mod()
     f = np.random.default_rng(2).normal(0, 0.2, (64, 64)).astype(np.float32)
