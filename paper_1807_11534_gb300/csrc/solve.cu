@@ -439,7 +439,7 @@ __device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, flo
 //  * neighbour-table rows and v in shared memory, neighbour values from the
 //    global arrays (only the owner reads a pixel's rows and v).
 //  * everything in global memory.
-constexpr int kBackwardThreads = 512;   // block size of the persistent reverse sweep (4 per SM)
+constexpr int kBackwardThreads = 1024;  // block size of the persistent reverse sweep (2 per SM)
 // dynamic shared memory of the persistent solver: one or two blocks per SM
 constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 112 * 1024; }
 constexpr int kCompactThreads = 512;   // two blocks per SM: one block's block barriers overlap the other's work
@@ -2322,7 +2322,7 @@ __device__ __forceinline__ double block_sum1(double x, double* s_red) {
     return t;
 }
 
-__global__ void __launch_bounds__(kBackwardThreads, 4)
+__global__ void __launch_bounds__(kBackwardThreads, 2048 / kBackwardThreads)
 k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
                    const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
                    const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
@@ -2333,11 +2333,20 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
     const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
     const int tid = threadIdx.x, nt = blockDim.x;
     unsigned gen = 0u;
-    const int64_t S4 = 4 * stride;   // one state of the segment buffer
-    auto segp1 = [&](int m) { return A.seg + m * S4; };
-    auto segp2 = [&](int m) { return A.seg + m * S4 + stride; };
-    auto segv = [&](int m) { return A.seg + m * S4 + 2 * stride; };
-    auto segw = [&](int m) { return A.seg + m * S4 + 3 * stride; };
+    // neighbour-table rows
+    const int32_t* __restrict__ nU = nb + NB_UP * stride;
+    const int32_t* __restrict__ nL = nb + NB_LEFT * stride;
+    const int32_t* __restrict__ nD = nb + NB_DOWN * stride;
+    const int32_t* __restrict__ nR = nb + NB_RIGHT * stride;
+    const int32_t* __restrict__ nDL = nb + NB_DOWNLEFT * stride;
+    const int32_t* __restrict__ nUR = nb + NB_UPRIGHT * stride;
+    // the planes of recomputed iterate m in the segment buffer
+    struct Planes { float *p1, *p2, *v, *w; };
+    auto seg_at = [&](int m) {
+        float* b = A.seg + (int64_t)m * 4 * stride;
+        return Planes{b, b + stride, b + 2 * stride, b + 3 * stride};
+    };
+    const float theta = P.theta, tau = P.tau, inv_theta = P.inv_theta;
     // adjoint of the final iterate
     for (int a = a0 + tid; a < a1; a += nt) {
         A.p1b[a] = 0.f; A.p2b[a] = 0.f; A.vb[a] = A.gv[a]; A.fb[a] = 0.f;
@@ -2346,97 +2355,116 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
     for (int k = nseg - 1; k >= 0; --k) {
         const int n0 = k * ckpt_every;
         const int M = min(ckpt_every, iters - n0);
-        // ---- replay the segment from its checkpoint
+        // ---- replay the segment from its checkpoint (the forward's steps
+        // and rounding: dual_one, then the primal step of primal_one with v
+        // read from iterate m and written to iterate m + 1)
         const float* c = ckpt + (int64_t)k * 3 * stride;
-        for (int a = a0 + tid; a < a1; a += nt) {
-            segp1(0)[a] = c[a]; segp2(0)[a] = c[stride + a]; segv(0)[a] = c[2 * stride + a];
+        {
+            const Planes S0 = seg_at(0);
+            float d0 = 0.f, d1 = 0.f;
+            // w of the checkpoint, formed from the checkpoint's own planes
+            const Own<float, false> Oc{nb, stride, const_cast<float*>(c + 2 * stride), F, 0};
+            for (int a = a0 + tid; a < a1; a += nt) {
+                S0.p1[a] = c[a]; S0.p2[a] = c[stride + a]; S0.v[a] = c[2 * stride + a];
+                primal_one(P, a, Oc, c, c + stride, nullptr, nullptr, S0.w, true, false, false, false, 0u, d0, d1);
+            }
         }
         if (!grid_sync(h, nblocks, gen)) return;
-        float d0 = 0.f, d1 = 0.f;
-        for (int a = a0 + tid; a < a1; a += nt)
-            primal_one(P, a, Own<float, false>{nb, stride, segv(0), F, 0}, segp1(0), segp2(0), nullptr,
-                       nullptr, segw(0), true, false, false, false, 0u, d0, d1);
-        if (!grid_sync(h, nblocks, gen)) return;
         for (int m = 0; m < M; ++m) {
+            const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
             for (int a = a0 + tid; a < a1; a += nt)
-                dual_one(P, a, Own<float, false>{nb, stride, nullptr, F, 0}, segp1(m), segp2(m), segw(m),
-                         segp1(m + 1), segp2(m + 1), 0u);
+                dual_one(P, a, Own<float, false>{nb, stride, nullptr, F, 0}, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2,
+                         0u);
             if (!grid_sync(h, nblocks, gen)) return;
             for (int a = a0 + tid; a < a1; a += nt) {
-                segv(m + 1)[a] = segv(m)[a];    // primal_one updates v in place (same thread, no barrier)
-                primal_one(P, a, Own<float, false>{nb, stride, segv(m + 1), F, 0}, segp1(m + 1), segp2(m + 1),
-                           nullptr, nullptr, segw(m + 1), false, false, false, false, 0u, d0, d1);
+                const int n_up = __ldg(nU + a), n_left = __ldg(nL + a);
+                const float q1 = Sn.p1[a], q2 = Sn.p2[a];
+                const float q1u = n_up >= 0 ? Sn.p1[n_up] : 0.f;
+                const float q2l = n_left >= 0 ? Sn.p2[n_left] : 0.f;
+                const float div = (q1 - q1u) + (q2 - q2l);
+                const float un = fmaf(-theta, div, Sm.v[a]);
+                const float vn = clamp01(un - __ldg(F + a));
+                Sn.v[a] = vn;
+                Sn.w[a] = div - vn * inv_theta;
             }
             if (!grid_sync(h, nblocks, gen)) return;
         }
         // ---- walk back through the segment.  Phase A (clip, u^{n+1}) only
         // touches the pixel itself, so it runs at the end of phase C of the
-        // step before (and here for the first step of the segment).
-        auto phase_a = [&](int m, int a) {
-            const bool last = n0 + m + 1 == iters;
-            const float vn = segv(m + 1)[a];
-            const float sb = (vn > 0.f && vn < 1.f) ? A.vb[a] : 0.f;
-            A.ub[a] = sb + (last ? A.gu[a] : 0.f);
-            A.fb[a] -= sb;
-        };
-        for (int a = a0 + tid; a < a1; a += nt) phase_a(M - 1, a);
+        // step before (and here for the segment's last step).
+        {
+            const bool last = n0 + M == iters;
+            const float* vM = seg_at(M).v;
+            for (int a = a0 + tid; a < a1; a += nt) {
+                const float vn = vM[a];
+                const float sb = (vn > 0.f && vn < 1.f) ? A.vb[a] : 0.f;
+                A.ub[a] = sb + (last ? A.gu[a] : 0.f);
+                A.fb[a] -= sb;
+            }
+        }
         if (!grid_sync(h, nblocks, gen)) return;
         for (int m = M - 1; m >= 0; --m) {
+            const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
             // B: qbar = pbar + theta grad ubar, the fixed-point step
             for (int a = a0 + tid; a < a1; a += nt) {
-                const int n_down = __ldg(nb + NB_DOWN * stride + a);
-                const int n_right = __ldg(nb + NB_RIGHT * stride + a);
-                const int n_dl = __ldg(nb + NB_DOWNLEFT * stride + a);
-                const int n_ur = __ldg(nb + NB_UPRIGHT * stride + a);
+                const int n_down = __ldg(nD + a), n_right = __ldg(nR + a);
+                const int n_dl = __ldg(nDL + a), n_ur = __ldg(nUR + a);
                 const float ua = A.ub[a];
                 const float ud = n_down >= 0 ? A.ub[n_down] : 0.f;
                 const float ur = n_right >= 0 ? A.ub[n_right] : 0.f;
-                float qb1 = A.p1b[a] + (n_down != kNbOut ? P.theta * (ud - ua) : 0.f);
-                float qb2 = A.p2b[a] + (n_right != kNbOut ? P.theta * (ur - ua) : 0.f);
+                const float p1 = Sm.p1[a], p2 = Sm.p2[a], w0 = Sm.w[a];
+                const float wd = n_down >= 0 ? Sm.w[n_down] : 0.f;
+                const float wr = n_right >= 0 ? Sm.w[n_right] : 0.f;
+                const float p2dl = n_dl >= 0 ? Sm.p2[n_dl] : 0.f;
+                const float p1ur = n_ur >= 0 ? Sm.p1[n_ur] : 0.f;
+                const float q1 = Sn.p1[a], q2 = Sn.p2[a];
+                const float pb1 = A.p1b[a], pb2 = A.p2b[a];
+                const bool dn = n_down != kNbOut, rt = n_right != kNbOut;
+                const float qb1 = pb1 + (dn ? theta * (ud - ua) : 0.f);
+                const float qb2 = pb2 + (rt ? theta * (ur - ua) : 0.f);
                 // g^n as in the forward dual step
-                const float* p1s = segp1(m);
-                const float* p2s = segp2(m);
-                const float* ws = segw(m);
-                const float p1 = p1s[a], p2 = p2s[a], w0 = ws[a];
-                float g1 = 0.f, g2 = 0.f;
-                if (n_down != kNbOut)
-                    g1 = (n_down >= 0 ? ws[n_down] : w_fixed(p1, n_dl >= 0 ? p2s[n_dl] : 0.f, n_down, P.inv_theta)) - w0;
-                if (n_right != kNbOut)
-                    g2 = (n_right >= 0 ? ws[n_right] : w_fixed(n_ur >= 0 ? p1s[n_ur] : 0.f, p2, n_right, P.inv_theta)) - w0;
-                const float nrm = sqrtf(g1 * g1 + g2 * g2);
-                const float den = 1.f + P.tau * nrm;
-                const float q1 = segp1(m + 1)[a], q2 = segp2(m + 1)[a];
-                const float dot = qb1 * q1 + qb2 * q2;
-                const float h1 = nrm > 0.f ? g1 / nrm : 0.f, h2 = nrm > 0.f ? g2 / nrm : 0.f;
-                float gb1 = (P.tau / den) * (qb1 - dot * h1);
-                float gb2 = (P.tau / den) * (qb2 - dot * h2);
-                if (n_down == kNbOut) gb1 = 0.f;
-                if (n_right == kNbOut) gb2 = 0.f;
-                A.gb1[a] = gb1;
-                A.gb2[a] = gb2;
-                A.pd1[a] = qb1 / den;
-                A.pd2[a] = qb2 / den;
+                const float g1 = dn ? (n_down >= 0 ? wd : w_fixed(p1, p2dl, n_down, inv_theta)) - w0 : 0.f;
+                const float g2 = rt ? (n_right >= 0 ? wr : w_fixed(p1ur, p2, n_right, inv_theta)) - w0 : 0.f;
+                const float s2 = fmaf(g1, g1, g2 * g2);
+                const float inv_nrm = s2 > 0.f ? rsqrtf(s2) : 0.f;
+                const float r = __fdividef(1.0f, fmaf(tau, s2 * inv_nrm, 1.0f));   // 1 / (1 + tau |g|)
+                // gbar = (tau / d) (qbar - (qbar . q) g / |g|), d = 1 + tau |g|
+                const float dot = (qb1 * q1 + qb2 * q2) * inv_nrm;
+                const float tr = tau * r;
+                A.gb1[a] = dn ? tr * fmaf(-dot, g1, qb1) : 0.f;
+                A.gb2[a] = rt ? tr * fmaf(-dot, g2, qb2) : 0.f;
+                A.pd1[a] = qb1 * r;
+                A.pd2[a] = qb2 * r;
             }
             if (!grid_sync(h, nblocks, gen)) return;
-            // C: wbar = -div gbar at x, x+e1, x+e2; pbar, vbar of iterate n
+            // C: wbar = -div gbar at x, x+e1, x+e2; pbar, vbar of iterate n;
+            // then the next step's phase A (no other pixel's phase C reads ub)
             for (int a = a0 + tid; a < a1; a += nt) {
-                const int n_up = __ldg(nb + NB_UP * stride + a);
-                const int n_left = __ldg(nb + NB_LEFT * stride + a);
-                const int n_down = __ldg(nb + NB_DOWN * stride + a);
-                const int n_right = __ldg(nb + NB_RIGHT * stride + a);
-                const int n_dl = __ldg(nb + NB_DOWNLEFT * stride + a);
-                const int n_ur = __ldg(nb + NB_UPRIGHT * stride + a);
+                const int n_up = __ldg(nU + a), n_left = __ldg(nL + a);
+                const int n_down = __ldg(nD + a), n_right = __ldg(nR + a);
+                const int n_dl = __ldg(nDL + a), n_ur = __ldg(nUR + a);
                 const float g1 = A.gb1[a], g2 = A.gb2[a];
-                auto G1 = [&](int c2) { return c2 >= 0 ? A.gb1[c2] : 0.f; };
-                auto G2 = [&](int c2) { return c2 >= 0 ? A.gb2[c2] : 0.f; };
-                const float wb0 = -((g1 - G1(n_up)) + (g2 - G2(n_left)));
-                const float wbd = -((G1(n_down) - g1) + (G2(n_down) - G2(n_dl)));
-                const float wbr = -((G1(n_right) - G1(n_ur)) + (G2(n_right) - g2));
+                const float g1u = n_up >= 0 ? A.gb1[n_up] : 0.f;
+                const float g2l = n_left >= 0 ? A.gb2[n_left] : 0.f;
+                const float g1d = n_down >= 0 ? A.gb1[n_down] : 0.f;
+                const float g2d = n_down >= 0 ? A.gb2[n_down] : 0.f;
+                const float g2dl = n_dl >= 0 ? A.gb2[n_dl] : 0.f;
+                const float g1r = n_right >= 0 ? A.gb1[n_right] : 0.f;
+                const float g2r = n_right >= 0 ? A.gb2[n_right] : 0.f;
+                const float g1ur = n_ur >= 0 ? A.gb1[n_ur] : 0.f;
+                const float wb0 = -((g1 - g1u) + (g2 - g2l));
+                const float wbd = -((g1d - g1) + (g2d - g2dl));
+                const float wbr = -((g1r - g1ur) + (g2r - g2));
                 A.p1b[a] = A.pd1[a] - (n_down != kNbOut ? wbd - wb0 : 0.f);
                 A.p2b[a] = A.pd2[a] - (n_right != kNbOut ? wbr - wb0 : 0.f);
-                A.vb[a] = A.ub[a] - wb0 * P.inv_theta;
-                // the next step's phase A: no other pixel's phase C reads ub
-                if (m > 0) phase_a(m - 1, a);
+                const float vb = A.ub[a] - wb0 * inv_theta;
+                A.vb[a] = vb;
+                if (m > 0) {
+                    const float vn = Sm.v[a];
+                    const float sb = (vn > 0.f && vn < 1.f) ? vb : 0.f;
+                    A.ub[a] = sb;
+                    A.fb[a] -= sb;
+                }
             }
             if (!grid_sync(h, nblocks, gen)) return;
         }
