@@ -3,7 +3,10 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "seg_internal.cuh"
 
@@ -34,6 +37,57 @@ int sm_count() {
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------- tracing, debug
+
+static thread_local cudaStream_t t_stream = nullptr;
+static thread_local void* t_ws = nullptr;
+static thread_local int t_depth = 0;
+
+bool debug_mode() {
+    static const bool on = [] {
+        const char* e = std::getenv("SEG_DEBUG");
+        return e && e[0] && std::strcmp(e, "0") != 0;
+    }();
+    return on;
+}
+
+PhaseScope::PhaseScope(const char* name, void* stream, void* ws) {
+    nvtxRangePushA(name);
+    if (t_depth++ == 0) {
+        t_stream = static_cast<cudaStream_t>(stream);
+        t_ws = ws;
+    }
+}
+
+PhaseScope::~PhaseScope() {
+    if (--t_depth == 0) {
+        t_stream = nullptr;
+        t_ws = nullptr;
+    }
+    nvtxRangePop();
+}
+
+seg_status after_launch(const char* name) {
+    if (!debug_mode()) return SEG_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(t_stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return SEG_OK;   // nothing may synchronise a stream under capture
+    cudaError_t e = cudaStreamSynchronize(t_stream);
+    if (e != cudaSuccess)
+        return fail(SEG_ERR_CUDA, "%s: %s (debug check after the launch)", name, cudaGetErrorString(e));
+    if (t_ws) {
+        int st = 0;
+        e = cudaMemcpy(&st, t_ws, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return fail(SEG_ERR_CUDA, "%s: reading the status word: %s", name, cudaGetErrorString(e));
+        if (st != SEG_OK) {
+            cudaMemsetAsync(t_ws, 0, sizeof(int), t_stream);
+            return fail(st, "%s: device-side status %d after the launch (debug check)", name, st);
+        }
+    }
+    return SEG_OK;
+}
 
 seg_status check_ws(void* ws, size_t ws_bytes, const WsLayout& L) {
     if (!ws) return fail(SEG_ERR_WORKSPACE, "workspace is NULL");
@@ -176,6 +230,7 @@ __global__ void k_set_wait_limit(WsHeader* h, long long wait_cycles, unsigned ex
 extern "C" seg_status seg_set_wait_limit(void* ws, size_t ws_bytes, long long wait_cycles,
                                          int extra_arrivals, void* stream) {
     seg::clear_error();
+    seg::PhaseScope _scope("seg_set_wait_limit", stream, ws);
     if (!ws || ws_bytes < 256) return seg::fail(SEG_ERR_WORKSPACE, "workspace missing");
     if (wait_cycles < 0 || extra_arrivals < 0)
         return seg::fail(SEG_ERR_INVALID_ARG, "wait_cycles and extra_arrivals must be >= 0");

@@ -362,6 +362,7 @@ extern "C" seg_status seg_build_domain(const float* f, int H, int W, int ld, dou
                                        int32_t* tiles, int tiles_cap, int32_t* pixels,
                                        int64_t pixels_cap, int32_t* counts, float* delta_out,
                                        void* ws, size_t ws_bytes, void* stream) {
+    PhaseScope _scope("seg_build_domain", stream, ws);
     return build_domain(f, nullptr, H, W, ld, delta, q, 0, tile_h, act, fg, wstart, tiles,
                         tiles_cap, pixels, pixels_cap, counts, delta_out, ws, ws_bytes, stream);
 }
@@ -373,6 +374,7 @@ extern "C" seg_status seg_build_domain_robust(const float* f, const float* fbar,
                                               int32_t* pixels, int64_t pixels_cap,
                                               int32_t* counts, float* delta_out, void* ws,
                                               size_t ws_bytes, void* stream) {
+    PhaseScope _scope("seg_build_domain_robust", stream, ws);
     if (fbar == f) fbar = nullptr;
     return build_domain(f, fbar, H, W, ld, delta, q, radius, tile_h, act, fg, wstart, tiles,
                         tiles_cap, pixels, pixels_cap, counts, delta_out, ws, ws_bytes, stream);
@@ -381,6 +383,7 @@ extern "C" seg_status seg_build_domain_robust(const float* f, const float* fbar,
 extern "C" seg_status seg_box_mean(const float* f, int H, int W, int ld, int radius, float* out,
                                    void* stream) {
     clear_error();
+    PhaseScope _scope("seg_box_mean", stream, nullptr);
     if (!f || !out) return fail(SEG_ERR_INVALID_ARG, "f and out must be non-NULL");
     if (H <= 0 || W <= 0 || ld < W || (int64_t)H * W >= (1ll << 31))
         return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d", H, W, ld);

@@ -187,6 +187,7 @@ extern "C" seg_status seg_energy(const float* f, int H, int W, int ld, const flo
                                  const float* p1, const float* p2, double lambda, double theta,
                                  double* out, void* ws, size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_energy", stream, ws);
     SEG_TRY(check_image(f, H, W, ld));
     if (!u || !v || !p1 || !p2 || !out) return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
     if (!(theta > 0)) return fail(SEG_ERR_INVALID_ARG, "theta must be > 0");
@@ -205,6 +206,7 @@ extern "C" seg_status seg_energy(const float* f, int H, int W, int ld, const flo
 extern "C" seg_status seg_errors(const float* u_star, const float* u_gt, int H, int W, int ld,
                                  double eps, double* out, void* ws, size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_errors", stream, ws);
     SEG_TRY(check_image(u_star, H, W, ld));
     SEG_TRY(check_image(u_gt, H, W, ld));
     if (!out) return fail(SEG_ERR_INVALID_ARG, "out is NULL");

@@ -249,6 +249,7 @@ extern "C" seg_status seg_make_fitting(const float* z, int H, int W, int ld, dou
                                        double gamma, float* f, double* c_out, void* ws,
                                        size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_make_fitting", stream, ws);
     if (!z || !f) return fail(SEG_ERR_INVALID_ARG, "z and f must be non-NULL");
     if (H <= 0 || W <= 0 || ld < W || (int64_t)H * W >= (1ll << 31))
         return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d", H, W, ld);
@@ -306,6 +307,7 @@ extern "C" seg_status seg_update_means(const float* z, const float* u, int H, in
                                        double* c_out, void* ws, size_t ws_bytes, void* stream) {
     using namespace seg;
     clear_error();
+    PhaseScope _scope("seg_update_means", stream, ws);
     if (!z || !u) return fail(SEG_ERR_INVALID_ARG, "z and u must be non-NULL");
     if (H <= 0 || W <= 0 || ld < W || (int64_t)H * W >= (1ll << 31))
         return fail(SEG_ERR_INVALID_ARG, "bad image size H=%d W=%d ld=%d", H, W, ld);

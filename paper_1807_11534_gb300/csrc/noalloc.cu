@@ -71,6 +71,7 @@ extern "C" seg_status seg_energy_noalloc(const float* f, int H, int W, int ld, c
                                          const float* v, const float* p1, const float* p2,
                                          double lambda, double theta, double* out, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_energy_noalloc", stream, nullptr);
     if (!f || !u || !v || !p1 || !p2 || !out)
         return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
     if (H <= 0 || W <= 0 || ld < W)

@@ -39,6 +39,23 @@ void count_launch();
 // Streaming multiprocessors of the current device (queried once).
 int sm_count();
 
+// One public call: an NVTX range named after it for its launches, and the
+// stream and workspace that the debug mode's checks use (see after_launch).
+struct PhaseScope {
+    PhaseScope(const char* name, void* stream, void* ws);
+    ~PhaseScope();
+    PhaseScope(const PhaseScope&) = delete;
+    PhaseScope& operator=(const PhaseScope&) = delete;
+};
+
+// Debug mode (SEG_DEBUG=1 in the environment, read once): after every launch
+// of a public call, unless its stream is being captured into a graph, the
+// stream is synchronised, and a CUDA error or a device-side status recorded
+// in the call's workspace is returned by that call, with the name of the
+// launch that raised it.  Off: returns SEG_OK at once.
+seg_status after_launch(const char* name);
+bool debug_mode();
+
 // Checks the launch that was just issued.
 #define SEG_LAUNCHED(name)                                                           \
     do {                                                                             \
@@ -47,6 +64,7 @@ int sm_count();
         if (_e != cudaSuccess)                                                       \
             return ::seg::fail(SEG_ERR_CUDA, "launch of %s failed: %s", name,        \
                                cudaGetErrorString(_e));                              \
+        if (::seg::debug_mode()) SEG_TRY(::seg::after_launch(name));                \
     } while (0)
 
 // -------------------------------------------------------------- workspace

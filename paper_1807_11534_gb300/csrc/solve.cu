@@ -2207,9 +2207,11 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     if (iters > 0 || warm) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NTs), args, smem, s));
         count_launch();
+        if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
         if (!waves) {
             SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern2, dim3(grid2), dim3(NTs), args, 0, s));
             count_launch();
+            if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
         }
     }
     k_compact_scatter<T><<<gblocks, 256, 0, s>>>(B, base, totals, prm->iters, std::max(1, prm->n_inner),
@@ -2536,6 +2538,7 @@ extern "C" seg_status seg_solve(const float* f, int H, int W, int ld, const uint
                                 float* p1, float* p2, void* state, size_t state_bytes, double* stats,
                                 void* ws, size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_solve", stream, ws);
     SEG_TRY(check_params(prm));
     if (!f || !act || !fgm || !wstart || !tiles || !counts || !u || !v || !p1 || !p2 || !state || !stats)
         return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
@@ -2605,6 +2608,7 @@ extern "C" seg_status seg_solve_batch(const seg_image* images, int n_images, con
                                       void* state, size_t state_bytes, double* stats, void* ws,
                                       size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_solve_batch", stream, ws);
     SEG_TRY(check_params(prm));
     if (prm->mode != SEG_MODE_COMPACT)
         return fail(SEG_ERR_INVALID_ARG, "seg_solve_batch runs SEG_MODE_COMPACT only");
@@ -2671,6 +2675,7 @@ extern "C" seg_status seg_solve_diff(const float* f, int H, int W, int ld, const
                                      int ckpt_every, void* ckpt, size_t ckpt_bytes, double* stats,
                                      void* ws, size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_solve_diff", stream, ws);
     SEG_TRY(check_params(prm));
     if (prm->mode != SEG_MODE_COMPACT || prm->storage != SEG_STORE_F32 || prm->n_inner != 1 ||
         prm->warm_start || prm->tol > 0)
@@ -2760,6 +2765,7 @@ static seg_status backward_batch(const seg_params* prm, const BatchDesc& B, cons
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kBackwardThreads), args,
                                                  0, s));
         count_launch();
+        if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
     }
     for (int k = 0; k < B.n; ++k) {
         const BatchImage& I = B.img[k];
@@ -2789,6 +2795,7 @@ extern "C" seg_status seg_backward(const float* f, int H, int W, int ld, const u
                                    const double* c, float* grad_f, double* grad_out, void* scratch,
                                    size_t scratch_bytes, void* ws, size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_backward", stream, ws);
     SEG_TRY(check_params(prm));
     if (prm->mode != SEG_MODE_COMPACT || prm->storage != SEG_STORE_F32 || prm->n_inner != 1)
         return fail(SEG_ERR_INVALID_ARG, "seg_backward: compact mode, float32 storage, n_inner = 1");
@@ -2859,6 +2866,7 @@ extern "C" seg_status seg_solve_diff_batch(const seg_image* images, int n_images
                                            size_t ckpt_bytes, double* stats, void* ws, size_t ws_bytes,
                                            void* stream) {
     clear_error();
+    PhaseScope _scope("seg_solve_diff_batch", stream, ws);
     SEG_TRY(check_diff_params(prm, "seg_solve_diff_batch"));
     if (!state || !stats || !ckpt) return fail(SEG_ERR_INVALID_ARG, "state, ckpt and stats must be non-NULL");
     if (reinterpret_cast<uintptr_t>(state) % 16 || reinterpret_cast<uintptr_t>(ws) % 16 ||
@@ -2892,6 +2900,7 @@ extern "C" seg_status seg_backward_batch(const seg_image* images, const seg_adj_
                                          const void* ckpt, size_t ckpt_bytes, int ckpt_every, void* scratch,
                                          size_t scratch_bytes, void* ws, size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_backward_batch", stream, ws);
     SEG_TRY(check_params(prm));
     if (prm->mode != SEG_MODE_COMPACT || prm->storage != SEG_STORE_F32 || prm->n_inner != 1)
         return fail(SEG_ERR_INVALID_ARG, "seg_backward_batch: compact mode, float32 storage, n_inner = 1");
@@ -3515,6 +3524,7 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
                                    void* state, size_t state_bytes, double* stats, void* ws,
                                    size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_solve_pd", stream, ws);
     if (!prm) return fail(SEG_ERR_INVALID_ARG, "params must be non-NULL");
     if (!f || !act || !fgm || !wstart || !counts || !u || !p1 || !p2 || !state || !stats)
         return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
@@ -3618,8 +3628,10 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern1, dim3(grid1), dim3(kPdSmThreads), args,
                                                  compact_smem(kPdSmThreads), s));
         count_launch();
+        if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kPdThreads), args, 0, s));
         count_launch();
+        if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
     }
     k_pd_scatter<<<gblocks, 256, 0, s>>>(B, base, totals, prm->iters, S, h);
     SEG_LAUNCHED("k_pd_scatter");

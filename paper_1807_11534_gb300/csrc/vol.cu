@@ -339,6 +339,7 @@ extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, c
                                   float* p2, float* p3, void* state, size_t state_bytes, double* stats, void* ws,
                                   size_t ws_bytes, void* stream) {
     clear_error();
+    PhaseScope _scope("seg_solve3d", stream, ws);
     if (!prm) return fail(SEG_ERR_INVALID_ARG, "params must be non-NULL");
     if (!f || !act || !fgm || !wstart || !voxels || !counts || !u || !v || !p1 || !p2 || !p3 || !state || !stats)
         return fail(SEG_ERR_INVALID_ARG, "a required pointer is NULL");
@@ -407,6 +408,7 @@ extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, c
     if (iters > 0) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kVolThreads), args, 0, s));
         count_launch();
+        if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
     }
     k_vol_scatter<<<eblocks, 256, 0, s>>>(counts, h, prm->iters, S, u, v, p1, p2, p3);
     SEG_LAUNCHED("k_vol_scatter");
