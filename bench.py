@@ -41,15 +41,15 @@ BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + 
 #  * ds2048: k_solve_compact, `bench.py --profile --iters 50 --tile-h 32`
 #    (2048x2048, delta = 0.2, float32, 50 iterations); the iteration state is
 #    held on chip, so this is about 3 % of the algorithmic bytes;
-#  * poly4096_0.1: k_solve_compact_wide, `bench.py --profile --profile-large
-#    --iters 20 --delta 0.1 [--storage bf16]` (4096x4096 polygons, 20
-#    iterations): the state streams from DRAM, about twice the algorithmic
-#    bytes (neighbour table rows, the cached w, the p' re-read);
+#  * poly4096_0.1: k_solve_wide_rm (the row-major global-memory solve),
+#    `bench.py --profile --profile-large --iters 20 --delta 0.1 [--storage
+#    bf16]` (4096x4096 polygons, 20 iterations): most of the state is served
+#    from L2, the DRAM traffic is about 0.76 of the algorithmic bytes at
+#    float32 (1.96 with the tile-major table);
 #  * batch: k_solve_compact in waves, the same command's batch of 64 images
 #    (20 iterations; each wave's state is loaded once into shared memory).
 COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (38725376 + 504320) / 50,
-                               ("poly4096_0.1", "f32"): (2340738048 + 868453120) / 20,
-                               ("poly4096_0.1", "bf16"): (1617208064 + 519273216) / 20,
+                               ("poly4096_0.1", "f32"): (587285760 + 656970240) / 20,
                                ("batch", "f32"): (204115200 + 73946112) / 20}
 
 
@@ -1024,10 +1024,10 @@ def run_rows(args, dev):
     st = rows["a8_storage"]["delta_0.1"]
     rows["roofline_hbm_workloads"] = {
         "cfg4_4096_polygons_delta0.1_f32": roofline_entry(
-            "k_solve_compact_wide (one iteration)", BYTES_PER_ACTIVE_ITER["f32"], st["f32"]["active_pixels"],
+            "k_solve_wide_rm (one iteration)", BYTES_PER_ACTIVE_ITER["f32"], st["f32"]["active_pixels"],
             st["f32"]["us_per_iter"] * 1e-6, COMPACT_DRAM_BYTES_PER_ITER.get(("poly4096_0.1", "f32"))),
         "cfg4_4096_polygons_delta0.1_bf16": roofline_entry(
-            "k_solve_compact_wide (one iteration)", BYTES_PER_ACTIVE_ITER["bf16"],
+            "k_solve_wide_rm (one iteration)", BYTES_PER_ACTIVE_ITER["bf16"],
             st["bf16"]["active_pixels"], st["bf16"]["us_per_iter"] * 1e-6,
             COMPACT_DRAM_BYTES_PER_ITER.get(("poly4096_0.1", "bf16"))),
         "cfg3_batch_f32": roofline_entry(

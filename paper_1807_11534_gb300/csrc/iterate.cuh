@@ -164,6 +164,34 @@ seg_status run_tiled(const IterParams& P, const seg_params* prm, const uint32_t*
                      float* u, float* v, float* p1, float* p2, float* st, double* partials, int64_t npartials,
                      WsHeader* h, cudaStream_t s);
 
+// ------------------------------------------------ host entry of wide.cu
+
+// One image solved in row-major compact order when its RD is too large for
+// the shared-memory paths (wide.cu).  Every kernel of run_wide_rm returns at
+// once unless counts[1] > wide_above, the condition under which the
+// tile-major kernels of solve.cu return at once instead, so the choice is
+// made on the device and survives graph capture.
+struct RowMajorArgs {
+    const uint32_t* act;     // RD bit plane [H][nw]
+    const uint32_t* fg;      // f < 0 bit plane
+    const float* f;          // [H][ld]
+    float *u, *v, *p1, *p2;  // [H][ld]: warm-start input, result output
+    const int32_t* counts;   // counts[1] = |RD|
+    WsHeader* h;
+    int H, W, ld, nw, ntx;
+    float theta_lambda, inv_theta;
+    long long wide_above;
+    int32_t* rowstart;       // [H + 1] scratch: RD pixels before each row
+};
+struct RowMajorArrays {      // `cap` elements each, p and v in the storage type
+    void *p1[2], *p2[2], *v;
+    float *F, *U, *Up, *Wc;  // theta lambda f, u, u of the iteration before a test, w
+    uint16_t *dd, *du, *fl;  // offsets to the rows below / above, neighbour flags
+    long long cap;
+};
+seg_status run_wide_rm(const RowMajorArgs& R, const RowMajorArrays& A, const IterParams& P,
+                       const seg_params* prm, double* partials, long long max_partials, cudaStream_t s);
+
 // Number of windows of the tiled solve for an H x W image (validates sweep
 // and n_inner).
 seg_status tiled_geometry(int H, int W, int sweep, int n_inner, int* nwin);

@@ -32,6 +32,7 @@
 // so the stopping test is deterministic.  Once it fires, a device flag makes
 // every later launch of the solve return immediately.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "iterate.cuh"
@@ -321,8 +322,10 @@ __global__ void k_batch_bases(BatchDesc B, int32_t* base, int32_t* totals, int64
 // pixel into compact order and fills its row of the neighbour table.
 template <typename T>
 __global__ void k_compact_gather(IterParams P, BatchDesc B, const int32_t* __restrict__ base,
-                                 int warm, CompactState S, const WsHeader* __restrict__ h) {
+                                 int warm, CompactState S, const WsHeader* __restrict__ h,
+                                 const int32_t* __restrict__ totals, long long rm_above) {
     if (*(volatile const int*)&h->done) return;
+    if (totals[1] > rm_above) return;   // the row-major solve of wide.cu takes this image
     const int lane = threadIdx.x & 31;
     const long long word = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (word >= B.total_words) return;
@@ -1931,7 +1934,8 @@ k_solve_compact_wide(IterParams P, int iters, int n_inner, int check_every, doub
 template <typename T>
 __global__ void k_compact_scatter(BatchDesc B, const int32_t* __restrict__ base,
                                   const int32_t* __restrict__ totals, int iters, int n_inner,
-                                  CompactState S, const WsHeader* __restrict__ h) {
+                                  CompactState S, const WsHeader* __restrict__ h, long long rm_above) {
+    if (totals[1] > rm_above) return;   // scattered by wide.cu
     const int lane = threadIdx.x & 31;
     const long long word = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (word >= B.total_words) return;
@@ -2153,7 +2157,30 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     k_batch_bases<<<1, 1, 0, s>>>(B, base, totals, C.cap, h);
     SEG_LAUNCHED("k_batch_bases");
     const unsigned gblocks = (unsigned)std::max<long long>(1, (B.total_words + 7) / 8);
-    k_compact_gather<T><<<gblocks, 256, 0, s>>>(P0, B, base, prm->warm_start, S, h);
+    // one image without checkpoints, its columns within 16 bits: when its RD
+    // is too large for the shared-memory paths, the row-major solve of
+    // wide.cu runs instead of the tile-major global-memory kernel (decided
+    // on the device from the RD count, like the choice between the two
+    // tile-major kernels); wide_above is that count's threshold
+    const int NTs = kCompactThreads;
+    const bool rm = B.n == 1 && std::max(1, prm->n_inner) == 1 && ckpt == nullptr && B.img[0].W <= 65535 &&
+                    B.img[0].H <= 65535;
+    const int grid1_pre = [&] {
+        int ps = 0;
+        const void* k1 = compact_waves(B.n, prm->tol, std::max(1, prm->n_inner), ckpt)
+                             ? (const void*)k_solve_compact<T, kCompactThreads, kCompactUnroll, true>
+                             : (const void*)k_solve_compact<T, kCompactThreads, kCompactUnroll, false>;
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)compact_smem(NTs));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k1, NTs, compact_smem(NTs));
+        const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, max_pixels));
+        int g = (int)std::min<int64_t>((int64_t)std::max(ps, 1) * sm_count(),
+                                       std::max<int64_t>(1, (most + NTs - 1) / NTs));
+        return (int)std::min<int64_t>(g, max_partials / 2);
+    }();
+    const long long wide_above = (long long)grid1_pre *
+                                 (long long)(compact_smem(kCompactThreads) / (4 * NB_UUR + sizeof(T)));
+    const long long rm_above = rm ? wide_above : LLONG_MAX;
+    k_compact_gather<T><<<gblocks, 256, 0, s>>>(P0, B, base, prm->warm_start, S, h, totals, rm_above);
     SEG_LAUNCHED("k_compact_gather");
 
     T* P1a = static_cast<T*>(S.p1[0]);
@@ -2161,7 +2188,6 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     T* P2a = static_cast<T*>(S.p2[0]);
     T* P2b = static_cast<T*>(S.p2[1]);
     T* V = static_cast<T*>(S.v);
-    const int NTs = kCompactThreads;
     const bool waves = compact_waves(B.n, prm->tol, std::max(1, prm->n_inner), ckpt);
     const void* kern = waves ? (const void*)k_solve_compact<T, kCompactThreads, kCompactUnroll, true>
                              : (const void*)k_solve_compact<T, kCompactThreads, kCompactUnroll, false>;
@@ -2204,18 +2230,40 @@ static seg_status solve_compact_batch(const IterParams& P0, const seg_params* pr
     void* args[] = {&P, &iters, &n_inner, &check_every, &tol, &warm, (void*)&cnt, (void*)&nbp, &stride,
                     &P1a, &P1b, &P2a, &P2b, &V, &F, &U, &Up, &Wc, &Wc2, &partials, &h, &ckpt,
                     &ckpt_every, &grid1, &bases, &nimg};
+    if (grid != grid1_pre) return fail(SEG_ERR_CUDA, "k_solve_compact: inconsistent grid");
     if (iters > 0 || warm) {
         SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NTs), args, smem, s));
         count_launch();
-        if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
-        if (!waves) {
+        if (debug_mode()) SEG_TRY(after_launch("k_solve_compact"));
+        if (!waves && !rm) {
             SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern2, dim3(grid2), dim3(NTs), args, 0, s));
             count_launch();
-            if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
+            if (debug_mode()) SEG_TRY(after_launch("k_solve_compact_wide"));
         }
     }
+    if (rm) {
+        const BatchImage& I = B.img[0];
+        RowMajorArgs R{};
+        R.act = I.act; R.fg = I.fg; R.f = I.f;
+        R.u = I.u; R.v = I.v; R.p1 = I.p1; R.p2 = I.p2;
+        R.counts = totals; R.h = h;
+        R.H = I.H; R.W = I.W; R.ld = I.ld; R.nw = I.nw; R.ntx = I.ntx;
+        R.theta_lambda = I.theta_lambda; R.inv_theta = P0.inv_theta;
+        R.wide_above = wide_above;
+        RowMajorArrays A{};
+        A.p1[0] = S.p1[0]; A.p1[1] = S.p1[1]; A.p2[0] = S.p2[0]; A.p2[1] = S.p2[1]; A.v = S.v;
+        A.F = S.f; A.U = S.u; A.Up = S.up; A.Wc = S.w;
+        A.dd = reinterpret_cast<uint16_t*>(S.nb);
+        A.du = A.dd + S.stride;
+        A.fl = A.du + S.stride;
+        R.rowstart = reinterpret_cast<int32_t*>(A.fl + S.stride);   // H + 1 <= the rest of the table region
+        A.cap = S.cap;
+        IterParams Pi = P0;
+        Pi.H = I.H; Pi.W = I.W; Pi.ld = I.ld; Pi.nw = I.nw; Pi.ntx = I.ntx;
+        SEG_TRY(run_wide_rm(R, A, Pi, prm, partials, max_partials / 2, s));
+    }
     k_compact_scatter<T><<<gblocks, 256, 0, s>>>(B, base, totals, prm->iters, std::max(1, prm->n_inner),
-                                                 S, h);
+                                                 S, h, rm_above);
     SEG_LAUNCHED("k_compact_scatter");
     return SEG_OK;
 }
@@ -3588,7 +3636,7 @@ extern "C" seg_status seg_solve_pd(const float* f, int H, int W, int ld, const u
     k_batch_bases<<<1, 1, 0, s>>>(B, base, totals, C.cap, h);
     SEG_LAUNCHED("k_batch_bases");
     const unsigned gblocks = (unsigned)std::max<long long>(1, (B.total_words + 7) / 8);
-    k_compact_gather<float><<<gblocks, 256, 0, s>>>(P, B, base, prm->warm_start, S, h);
+    k_compact_gather<float><<<gblocks, 256, 0, s>>>(P, B, base, prm->warm_start, S, h, totals, LLONG_MAX);
     SEG_LAUNCHED("k_compact_gather");
 
     const void* kern = (const void*)k_solve_pd;

@@ -1,0 +1,459 @@
+// wide.cu -- the restricted iteration of Sections 2.1 and 3 for one image
+// whose RD is too large for the shared-memory paths of solve.cu, on a
+// compact state in row-major order.
+//
+// RD pixels are numbered row by row (rowstart[i] + the RD pixels before
+// column j in row i), so that in the compact arrays
+//   * the neighbours left and right of pixel a, when in RD, are a - 1 and
+//     a + 1;
+//   * the RD pixels of row i + 1 at columns >= j start at D0 = a + dD, and
+//     those of row i - 1 at columns >= j at U0 = a - dU, with 0 <= dD, dU
+//     <= W (the RD pixels of at most one row lie in between), so x + e1 is
+//     D0 and x + e1 - e2 is D0 - 1, x - e1 is U0 and x - e1 + e2 is U0 + 1
+//     (or U0 when x - e1 is fixed), whenever those pixels are in RD;
+// and the whole neighbourhood of a pixel is two 16-bit offsets and a 16-bit
+// word of flags (6 bytes, against the 24 of the six-row int32 table of the
+// tile-major order).  With the table that small the iteration's arrays (the
+// state, w, theta lambda f and the offsets) fit in L2 for images like the
+// 4096^2 precision workload, so the two phases of an iteration (dual step,
+// grid barrier, primal step, grid barrier) stream them from L2, not DRAM.
+// The arithmetic and rounding of every step are those of dual_one /
+// primal_one in solve.cu (the 16-bit stores' random words are drawn from the
+// compact index, as there, so 16-bit results differ in the rounding noise
+// only); the stopping test, the header fields and the stats are those of the
+// other compact paths.
+#include <algorithm>
+#include <cmath>
+
+#include "iterate.cuh"
+
+namespace seg {
+
+enum : uint16_t {
+    RM_DOWN_RD = 1u << 0,    // x + e1 in RD (at D0)
+    RM_DOWN_FG = 1u << 1,    // x + e1 fixed foreground (else background)
+    RM_DOWN_OUT = 1u << 2,   // x on the last row
+    RM_RIGHT_RD = 1u << 3,   // x + e2 in RD (at a + 1)
+    RM_RIGHT_FG = 1u << 4,
+    RM_RIGHT_OUT = 1u << 5,  // x on the last column
+    RM_DL_RD = 1u << 6,      // x + e1 - e2 in RD (at D0 - 1)
+    RM_UR_RD = 1u << 7,      // x - e1 + e2 in RD (at U0 + [x - e1 in RD])
+    RM_UP_RD = 1u << 8,      // x - e1 in RD (at U0)
+    RM_LEFT_RD = 1u << 9,    // x - e2 in RD (at a - 1)
+};
+
+template <typename T>
+struct RowMajorState {
+    T* p1[2];
+    T* p2[2];
+    T* v;
+    float *F, *U, *Up, *Wc;
+    uint16_t *dd, *du, *fl;
+};
+
+template <typename T>
+RowMajorState<T> rm_state(const RowMajorArrays& A) {
+    return RowMajorState<T>{{static_cast<T*>(A.p1[0]), static_cast<T*>(A.p1[1])},
+                            {static_cast<T*>(A.p2[0]), static_cast<T*>(A.p2[1])},
+                            static_cast<T*>(A.v), A.F, A.U, A.Up, A.Wc, A.dd, A.du, A.fl};
+}
+
+// w at a fixed neighbour: p there is 0, so div p is minus the two
+// components that flow into it, and v is its fixed value (as w_fixed)
+__device__ __forceinline__ float rm_w_fixed(float p_in_1, float p_in_2, bool fg, float inv_theta) {
+    return -(p_in_1 + p_in_2) - (fg ? inv_theta : 0.f);
+}
+
+// ------------------------------------------------------------ setup
+
+// RD pixels per row (one warp per row).
+__global__ void k_rm_rowcount(RowMajorArgs R) {
+    if (*(volatile const int*)&R.h->done || R.counts[1] <= R.wide_above) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= R.H) return;
+    int c = 0;
+    for (int k = lane; k < R.ntx; k += 32) c += __popc(__ldg(R.act + (int64_t)i * R.nw + k));
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+    if (lane == 0) R.rowstart[i] = c;
+}
+
+// Exclusive scan of the row counts in place (one block), rowstart[H] = total.
+__global__ void k_rm_rowscan(RowMajorArgs R) {
+    if (*(volatile const int*)&R.h->done || R.counts[1] <= R.wide_above) return;
+    __shared__ int s[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < R.H; base += 1024) {
+        const int i = base + (int)threadIdx.x;
+        const int x = i < R.H ? R.rowstart[i] : 0;
+        s[threadIdx.x] = x;
+        __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {   // inclusive Hillis-Steele scan
+            const int t = threadIdx.x >= (unsigned)d ? s[threadIdx.x - d] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < R.H) R.rowstart[i] = carry + s[threadIdx.x] - x;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += s[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) R.rowstart[R.H] = carry;
+}
+
+// The row-major position of pixel (r, j): rowstart[r] plus the RD pixels of
+// row r before column j, from the warp's running word prefix `pre` of row r
+// (RD pixels in the words before word k) and word `w` of row r.
+__device__ __forceinline__ int rm_pos(const int32_t* rowstart, int r, int pre, uint32_t w, int b) {
+    return rowstart[r] + pre + __popc(w & lanemask_lt(b));
+}
+
+// One warp per row: the compact state of every RD pixel of the row in
+// row-major order (f times theta lambda, the start iterate, w for a cold
+// start), its offsets and flags.  Lane l takes word k = 32 c + l of the
+// chunk c, with the same word of the rows above and below.
+template <typename T>
+__global__ void k_rm_gather(RowMajorArgs R, RowMajorState<T> S, int warm) {
+    if (*(volatile const int*)&R.h->done || R.counts[1] <= R.wide_above) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= R.H) return;
+    const unsigned FULL = 0xffffffffu;
+    int pre_u = 0, pre_c = 0, pre_d = 0;   // RD pixels of rows i-1, i, i+1 before this chunk
+    for (int c0 = 0; c0 < R.ntx; c0 += 32) {
+        const int k = c0 + lane;
+        const bool in = k < R.ntx;
+        const int64_t o = (int64_t)i * R.nw + k;
+        const uint32_t wc = in ? __ldg(R.act + o) : 0u;
+        const uint32_t fc = in ? __ldg(R.fg + o) : 0u;
+        const uint32_t wu = in && i > 0 ? __ldg(R.act + o - R.nw) : 0u;
+        const uint32_t wd = in && i + 1 < R.H ? __ldg(R.act + o + R.nw) : 0u;
+        const uint32_t fd = in && i + 1 < R.H ? __ldg(R.fg + o + R.nw) : 0u;
+        // the next word of this row (for the right neighbour of bit 31) and
+        // of the row above (for x - e1 + e2 of bit 31); the previous word of
+        // this row and of the row below (for bit 0)
+        const uint32_t wcn = k + 1 < R.ntx ? __ldg(R.act + o + 1) : 0u;
+        const uint32_t fcn = k + 1 < R.ntx ? __ldg(R.fg + o + 1) : 0u;
+        const uint32_t wun = k + 1 < R.ntx && i > 0 ? __ldg(R.act + o - R.nw + 1) : 0u;
+        const uint32_t wcp = in && k > 0 ? __ldg(R.act + o - 1) : 0u;
+        const uint32_t wdp = in && k > 0 && i + 1 < R.H ? __ldg(R.act + o + R.nw - 1) : 0u;
+        // exclusive prefix of the three rows' word counts across the lanes
+        int cu = __popc(wu), cc = __popc(wc), cd = __popc(wd);
+        int su = cu, sc = cc, sd = cd;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int tu = __shfl_up_sync(FULL, su, d), tc = __shfl_up_sync(FULL, sc, d),
+                      td = __shfl_up_sync(FULL, sd, d);
+            if (lane >= d) { su += tu; sc += tc; sd += td; }
+        }
+        const int wpre_u = pre_u + su - cu, wpre_c = pre_c + sc - cc, wpre_d = pre_d + sd - cd;
+        for (uint32_t bits = wc; bits; bits &= bits - 1) {
+            const int b = __ffs(bits) - 1;
+            const int j = 32 * k + b;
+            const int a = rm_pos(R.rowstart, i, wpre_c, wc, b);
+            uint16_t fl = 0;
+            const bool last_row = i + 1 >= R.H, last_col = j + 1 >= R.W;
+            if (last_row) fl |= RM_DOWN_OUT;
+            else {
+                if ((wd >> b) & 1u) fl |= RM_DOWN_RD;
+                else if ((fd >> b) & 1u) fl |= RM_DOWN_FG;
+                const bool dl = b > 0 ? ((wd >> (b - 1)) & 1u) : (j > 0 && (wdp >> 31));
+                if (dl) fl |= RM_DL_RD;
+            }
+            if (last_col) fl |= RM_RIGHT_OUT;
+            else {
+                const bool r_rd = b < 31 ? ((wc >> (b + 1)) & 1u) : (wcn & 1u);
+                const bool r_fg = b < 31 ? ((fc >> (b + 1)) & 1u) : (fcn & 1u);
+                if (r_rd) fl |= RM_RIGHT_RD;
+                else if (r_fg) fl |= RM_RIGHT_FG;
+                const bool ur = i > 0 && (b < 31 ? ((wu >> (b + 1)) & 1u) : (wun & 1u));
+                if (ur) fl |= RM_UR_RD;
+            }
+            if (i > 0 && ((wu >> b) & 1u)) fl |= RM_UP_RD;
+            if (j > 0 && (b > 0 ? ((wc >> (b - 1)) & 1u) : (wcp >> 31))) fl |= RM_LEFT_RD;
+            const int d0 = last_row ? a : rm_pos(R.rowstart, i + 1, wpre_d, wd, b);
+            const int u0 = i > 0 ? rm_pos(R.rowstart, i - 1, wpre_u, wu, b) : a;
+            S.dd[a] = (uint16_t)(d0 - a);
+            S.du[a] = (uint16_t)(a - u0);
+            S.fl[a] = fl;
+            const int64_t off = (int64_t)i * R.ld + j;
+            const float fv = R.f[off];
+            const float hh = ((fc >> b) & 1u) ? 1.f : 0.f;
+            S.F[a] = R.theta_lambda * fv;
+            if (warm) {
+                Store<T>::st(S.p1[0], a, i < R.H - 1 ? R.p1[off] : 0.f);
+                Store<T>::st(S.p2[0], a, j < R.W - 1 ? R.p2[off] : 0.f);
+                Store<T>::st(S.v, a, R.v[off] - Store<T>::vbias);
+                S.U[a] = R.u[off];
+                S.Up[a] = R.u[off];
+                S.Wc[a] = 0.f;   // formed by the solve from the whole state
+            } else {
+                Store<T>::st(S.p1[0], a, 0.f);
+                Store<T>::st(S.p2[0], a, 0.f);
+                Store<T>::st(S.v, a, clamp01(fmaf(-R.theta_lambda, fv, hh)) - Store<T>::vbias);
+                S.U[a] = hh;
+                S.Up[a] = hh;
+                S.Wc[a] = -(Store<T>::ld_rw(S.v, a) + Store<T>::vbias) * R.inv_theta;
+            }
+        }
+        pre_u = __shfl_sync(FULL, wpre_u + cu, 31);
+        pre_c = __shfl_sync(FULL, wpre_c + cc, 31);
+        pre_d = __shfl_sync(FULL, wpre_d + cd, 31);
+    }
+}
+
+// ------------------------------------------------------------ iteration
+
+constexpr int kRmThreads = 512;   // four blocks per SM (32 registers): latency-bound loads
+constexpr int kRmUnroll = 2;      // pixels per thread in flight
+
+// Dual step at pixel a (dual_one's arithmetic): reads p, w of the current
+// iterate, writes p' to the other buffers.
+template <typename T>
+__device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState<T>& S, int a, const T* P1i,
+                                        const T* P2i, T* P1o, T* P2o, uint32_t seed) {
+    const uint16_t fl = __ldg(S.fl + a);
+    const float p1 = Store<T>::ldc(P1i, a), p2 = Store<T>::ldc(P2i, a);
+    const float w0 = S.Wc[a];
+    float g1 = 0.f, g2 = 0.f;
+    if (!(fl & RM_DOWN_OUT)) {
+        const int d0 = a + (int)__ldg(S.dd + a);
+        if (fl & RM_DOWN_RD) {
+            g1 = S.Wc[d0] - w0;
+        } else {
+            const float p2dl = (fl & RM_DL_RD) ? Store<T>::ldc(P2i, d0 - 1) : 0.f;
+            g1 = rm_w_fixed(p1, p2dl, fl & RM_DOWN_FG, P.inv_theta) - w0;
+        }
+    }
+    if (!(fl & RM_RIGHT_OUT)) {
+        if (fl & RM_RIGHT_RD) {
+            g2 = S.Wc[a + 1] - w0;
+        } else {
+            float p1ur = 0.f;
+            if (fl & RM_UR_RD)
+                p1ur = Store<T>::ldc(P1i, a - (int)__ldg(S.du + a) + ((fl & RM_UP_RD) ? 1 : 0));
+            g2 = rm_w_fixed(p1ur, p2, fl & RM_RIGHT_FG, P.inv_theta) - w0;
+        }
+    }
+    float q1, q2;
+    chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
+    const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
+    Store<T>::st_sr(P1o, a, q1, rnd);
+    Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
+}
+
+// Primal step at pixel a (primal_one's arithmetic): u' = v - theta div p',
+// v' = clip(u' - theta lambda f) in place, w' for the next dual step; wonly:
+// just w = div p - v/theta (a warm start).
+template <typename T>
+__device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorState<T>& S, int a, const T* P1n,
+                                          const T* P2n, bool wonly, bool check, bool write_u, bool write_prev,
+                                          uint32_t seed, float& du2, float& dv2) {
+    const uint16_t fl = __ldg(S.fl + a);
+    const float q1 = Store<T>::ldc(P1n, a), q2 = Store<T>::ldc(P2n, a);
+    const float vv = Store<T>::ld_rw(S.v, a) + Store<T>::vbias;
+    const float q1u = (fl & RM_UP_RD) ? Store<T>::ldc(P1n, a - (int)__ldg(S.du + a)) : 0.f;
+    const float q2l = (fl & RM_LEFT_RD) ? Store<T>::ldc(P2n, a - 1) : 0.f;
+    const float div = (q1 - q1u) + (q2 - q2l);
+    if (wonly) {
+        S.Wc[a] = div - vv * P.inv_theta;
+        return;
+    }
+    const float un = fmaf(-P.theta, div, vv);
+    const float vn = clamp01(un - __ldg(S.F + a));   // F = theta lambda f
+    const float vs = Store<T>::st_sr(S.v, a, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
+                     Store<T>::vbias;
+    S.Wc[a] = div - vs * P.inv_theta;
+    if (check) {
+        const float da = un - S.Up[a], db = vn - vv;
+        du2 = fmaf(da, da, du2);
+        dv2 = fmaf(db, db, dv2);
+    }
+    if (write_prev) S.Up[a] = un;
+    if (write_u) S.U[a] = un;
+}
+
+// All iterations in one cooperative launch: each block owns a contiguous
+// range of the row-major compact order; dual phase, grid barrier, primal
+// phase (and the Section 4 partials), grid barrier; the stopping test as in
+// the other compact paths.
+template <typename T>
+__global__ void __launch_bounds__(kRmThreads, 2048 / kRmThreads)
+k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ counts, long long wide_above,
+                int iters, int check_every, double tol, int warm, double* partials, WsHeader* h) {
+    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
+    if (*(volatile int*)&h->done) return;
+    const int n = counts[1];
+    if (n <= wide_above) return;
+    const unsigned nblocks = gridDim.x;
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    const int tid = threadIdx.x, nt = kRmThreads;
+    unsigned gen = 0u;
+    auto each = [&](auto&& op) {
+        int a = a0 + tid;
+        for (; a + (kRmUnroll - 1) * nt < a1; a += kRmUnroll * nt) {
+#pragma unroll
+            for (int k = 0; k < kRmUnroll; ++k) op(a + k * nt);
+        }
+        for (; a < a1; a += nt) op(a);
+    };
+    float d0 = 0.f, d1 = 0.f;
+    if (warm) {
+        for (int a = a0 + tid; a < a1; a += nt)
+            rm_primal(P, S, a, S.p1[0], S.p2[0], true, false, false, false, 0u, d0, d1);
+        if (!grid_sync(h, nblocks, gen)) return;
+    }
+    const int C = check_every;
+    int pb = 0;
+    for (int it = 0; it < iters; ++it) {
+        const int l = it + 1;
+        const uint32_t seed_d = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
+        const T* pi1 = pb ? S.p1[1] : S.p1[0];
+        const T* pi2 = pb ? S.p2[1] : S.p2[0];
+        T* po1 = pb ? S.p1[0] : S.p1[1];
+        T* po2 = pb ? S.p2[0] : S.p2[1];
+        each([&](int a) { rm_dual(P, S, a, pi1, pi2, po1, po2, seed_d); });
+        pb ^= 1;
+        bool done;
+        if (!grid_sync_poll(h, nblocks, gen, it > 0 && (it % C == 0), done)) return;
+        if (done) return;   // the previous iteration's stopping test fired
+        const bool check = (l % C == 0) || l == iters;
+        const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
+        const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
+        float du2 = 0.f, dv2 = 0.f;
+        if (!check && !write_prev)
+            each([&](int a) { rm_primal(P, S, a, po1, po2, false, false, false, false, seed, du2, dv2); });
+        else
+            each([&](int a) { rm_primal(P, S, a, po1, po2, false, check, check, write_prev, seed, du2, dv2); });
+        if (check) {
+            float x = du2, y = dv2;
+            block_sum2f<kRmThreads>(x, y, reinterpret_cast<float*>(s_red));
+            if (tid == 0) {
+                partials[2 * blockIdx.x] = x;
+                partials[2 * blockIdx.x + 1] = y;
+            }
+        }
+        if (!grid_sync(h, nblocks, gen)) return;
+        if (check && blockIdx.x == 0) {
+            // Section 4 stopping test: fixed-order FP64 sum of the block
+            // partials, squared norms against tol^2
+            double sx = 0.0, sy = 0.0;
+            if (tid < 32) sum_partials_warp0(partials, (int)nblocks, sx, sy);
+            if (tid == 0) {
+                h->du2 = sx;
+                h->dv2 = sy;
+                h->last_check = l;
+                if (tol > 0.0 && fmax(sx, sy) <= tol * tol) {
+                    h->iters_done = l;
+                    __threadfence();
+                    h->done = 1;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------ scatter
+
+// Dense u, v, p1, p2 of the final iterate (one warp per row): compact values
+// on RD, the fixed values elsewhere.
+template <typename T>
+__global__ void k_rm_scatter(RowMajorArgs R, RowMajorState<T> S, int iters, long long cap) {
+    if (R.counts[1] <= R.wide_above) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= R.H) return;
+    const bool ok = R.counts[1] <= cap && R.rowstart[R.H] == R.counts[1];
+    const int l = R.h->done ? R.h->iters_done : iters;
+    const int pb = l & 1;
+    const T* P1 = pb ? S.p1[1] : S.p1[0];
+    const T* P2 = pb ? S.p2[1] : S.p2[0];
+    int pre = 0;
+    for (int c0 = 0; c0 < R.ntx; c0 += 32) {
+        const int k = c0 + lane;
+        const bool in = k < R.ntx;
+        const int64_t o = (int64_t)i * R.nw + k;
+        const uint32_t wc = in ? __ldg(R.act + o) : 0u;
+        const uint32_t fc = in ? __ldg(R.fg + o) : 0u;
+        const int cc = __popc(wc);
+        int sc = cc;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, sc, d);
+            if (lane >= d) sc += t;
+        }
+        const int wpre = pre + sc - cc;
+        if (in) {
+            for (int b = 0; b < 32; ++b) {
+                const int j = 32 * k + b;
+                if (j >= R.W) break;
+                const int64_t off = (int64_t)i * R.ld + j;
+                if (ok && ((wc >> b) & 1u)) {
+                    const int a = rm_pos(R.rowstart, i, wpre, wc, b);
+                    R.u[off] = S.U[a];
+                    R.v[off] = Store<T>::ld_rw(S.v, a) + Store<T>::vbias;
+                    R.p1[off] = Store<T>::ld_rw(P1, a);
+                    R.p2[off] = Store<T>::ld_rw(P2, a);
+                } else {
+                    const float hh = ((fc >> b) & 1u) ? 1.f : 0.f;
+                    R.u[off] = hh; R.v[off] = hh; R.p1[off] = 0.f; R.p2[off] = 0.f;
+                }
+            }
+        }
+        pre = __shfl_sync(0xffffffffu, wpre + cc, 31);
+    }
+}
+
+// ------------------------------------------------------------ host
+
+template <typename T>
+static seg_status run_wide_rm_t(const RowMajorArgs& R, const RowMajorArrays& A, const IterParams& P,
+                                const seg_params* prm, double* partials, long long max_partials,
+                                cudaStream_t s) {
+    const RowMajorState<T> S = rm_state<T>(A);
+    const unsigned row_blocks = (unsigned)std::max(1, (R.H * 32 + 255) / 256);
+    k_rm_rowcount<<<row_blocks, 256, 0, s>>>(R);
+    SEG_LAUNCHED("k_rm_rowcount");
+    k_rm_rowscan<<<1, 1024, 0, s>>>(R);
+    SEG_LAUNCHED("k_rm_rowscan");
+    k_rm_gather<T><<<row_blocks, 256, 0, s>>>(R, S, prm->warm_start);
+    SEG_LAUNCHED("k_rm_gather");
+    const void* kern = (const void*)k_solve_wide_rm<T>;
+    int per_sm = 0;
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRmThreads, 0));
+    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_wide_rm cannot be resident");
+    const long long most = std::max<long long>(1, std::min<long long>(A.cap, (long long)R.H * R.W));
+    int grid = (int)std::min<long long>((long long)per_sm * sm_count(), (most + kRmThreads - 1) / kRmThreads);
+    grid = std::max(1, (int)std::min<long long>(grid, max_partials));
+    IterParams Pk = P;
+    RowMajorState<T> Sk = S;
+    const int32_t* counts = R.counts;
+    long long above = R.wide_above;
+    int iters = prm->iters, ce = test_interval(prm->tol, prm->check_every, prm->iters);
+    double tol = prm->tol;
+    int warm = prm->warm_start;
+    WsHeader* h = R.h;
+    void* args[] = {&Pk, &Sk, (void*)&counts, &above, &iters, &ce, &tol, &warm, &partials, &h};
+    if (iters > 0 || warm) {
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kRmThreads), args, 0, s));
+        count_launch();
+        if (debug_mode()) SEG_TRY(after_launch("k_solve_wide_rm"));
+    }
+    k_rm_scatter<T><<<row_blocks, 256, 0, s>>>(R, S, prm->iters, A.cap);
+    SEG_LAUNCHED("k_rm_scatter");
+    return SEG_OK;
+}
+
+seg_status run_wide_rm(const RowMajorArgs& R, const RowMajorArrays& A, const IterParams& P,
+                       const seg_params* prm, double* partials, long long max_partials, cudaStream_t s) {
+    switch (prm->storage) {
+        case SEG_STORE_F32: return run_wide_rm_t<float>(R, A, P, prm, partials, max_partials, s);
+        case SEG_STORE_BF16: return run_wide_rm_t<__nv_bfloat16>(R, A, P, prm, partials, max_partials, s);
+        default: return run_wide_rm_t<__half>(R, A, P, prm, partials, max_partials, s);
+    }
+}
+
+}  // namespace seg
