@@ -45,12 +45,13 @@ BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + 
 #    `bench.py --profile --profile-large --iters 20 --delta 0.1 [--storage
 #    bf16]` (4096x4096 polygons, 20 iterations): most of the state is served
 #    from L2, the DRAM traffic is about 0.76 of the algorithmic bytes at
-#    float32 (1.96 with the tile-major table);
+#    float32 (1.96 with the tile-major table) and 0.19 at bf16;
 #  * batch: k_solve_compact in waves, the same command's batch of 64 images
 #    (20 iterations; each wave's state is loaded once into shared memory).
-COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (38725376 + 504320) / 50,
-                               ("poly4096_0.1", "f32"): (587285760 + 656970240) / 20,
-                               ("batch", "f32"): (204115200 + 73946112) / 20}
+COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (38689280 + 530176) / 50,
+                               ("poly4096_0.1", "f32"): (589960192 + 653882880) / 20,
+                               ("poly4096_0.1", "bf16"): (85928704 + 95115264) / 20,
+                               ("batch", "f32"): (204280832 + 71778048) / 20}
 
 
 def parse():
