@@ -211,3 +211,95 @@ def test_batched_adjoint_on_the_differentiation_workload(orc):
         gf1, gout1, _ = _gpu_grad(fs[k], 0.2, 1.0, gus[k], None, 200, 20)
         np.testing.assert_array_equal(seg.download(out[k][0]).astype(np.float64), gf1)
         np.testing.assert_array_equal(out[k][1].cpu().numpy(), gout1)
+
+
+
+
+def _clip_pattern(orc, f, reg, lam, iters):
+    """Where v = clip(u - theta lambda f, 0, 1) sits on a bound, iteration by
+    iteration (-1 at 1, +1 at 0, 0 inside): the loss is a smooth function of
+    f and lambda wherever this pattern does not change."""
+    st = orc.solve(f, reg, lam, iters=1)
+    pats = np.empty((iters,) + f.shape, np.int8)
+    for k in range(iters):
+        if k:
+            st = orc.solve(f, reg, lam, iters=1, state=st)
+        pats[k] = (st.v <= 0.0).astype(np.int8) - (st.v >= 1.0).astype(np.int8)
+    return st, pats
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_backward_matches_fp64_finite_differences(orc, seed):
+    """The GPU backward against central finite differences directly, to 1e-3
+    relative, on the differentiation workload's configuration: a 64x64 crop
+    (across a shape boundary) of a 1024x1024 training image, CV fitting term
+    from z with c1 = 0.3, c2 = 0.7, delta = 0.2, K = 200 unrolled iterations,
+    checkpoints every 20, L = <g, u_K> with g the BCE gradient at u_K.
+
+    The differences are taken on the FP64 oracle forward with the partition
+    held fixed (the adjoint's convention), along three random directions on
+    RD, along df/dc1 = -2(z - c1) and df/dc2 = 2(z - c2) (so the c
+    derivatives are the f derivative along those directions), and in lambda.
+    The unrolled map is piecewise smooth: it has a kink wherever an iterate
+    of v meets a bound of the clip, so each difference uses the largest step
+    h in {1e-5, 1e-6, 1e-7, 1e-8} at which the oracle's clip pattern over all K
+    iterations is the same at both ends as at the centre.  The oracle reads f
+    as float32, so the GPU's directional derivative is formed along the steps
+    actually taken.  A derivative that is a sum with more than hundredfold
+    cancellation is compared at 1e-3 of a hundredth of its sum of absolute
+    terms (float32 resolves each term to about 1e-6), which applies only to
+    dL/dc2 on some crops."""
+    rng = np.random.default_rng(40 + seed)
+    P = synth.training_batch(seed=seed, n_images=1, side=1024)[0]
+    K, lam, delta = 200, 1.0, 0.2
+    c1, c2 = 0.3, 0.7
+    for _ in range(400):
+        i0, j0 = rng.integers(0, 1024 - 64, 2)
+        z = np.ascontiguousarray(P.z[i0:i0 + 64, j0:j0 + 64])
+        _, f = orc.fitting(z, c1, c2)
+        reg = orc.domain(f, delta)
+        rd = reg == 2
+        # a boundary in the crop, and no RD pixel whose f a step could move across 0 (u0 = H(-f))
+        if 0.2 < P.label[i0:i0 + 64, j0:j0 + 64].mean() < 0.8 and np.abs(f[rd]).min() > 1e-4:
+            break
+    else:
+        pytest.skip("no crop across a boundary")
+    m = P.label[i0:i0 + 64, j0:j0 + 64].astype(np.float64)
+    st, pat0 = _clip_pattern(orc, f, reg, lam, K)
+    u = st.u
+    uc = np.clip(u, 1e-4, 1 - 1e-4)
+    gu = np.where((u > 1e-4) & (u < 1 - 1e-4), (uc - m) / (uc * (1 - uc)), 0.0) / u.size
+    gf, gout, _ = _gpu_grad(f, delta, lam, gu, None, K, 20, z=z, c=[c1, c2])
+
+    def loss(ff, ll=lam):
+        return float(np.sum(gu * orc.solve(ff, reg, ll, iters=K).u))
+
+    zz = z.astype(np.float64)
+    dirs = {f"f{k}": np.where(rd, np.clip(rng.normal(size=f.shape), -3, 3), 0.0) for k in range(3)}
+    dirs["c1"] = np.where(rd, -2 * (zz - c1), 0.0)
+    dirs["c2"] = np.where(rd, 2 * (zz - c2), 0.0)
+    results = {}
+    for name, d in dirs.items():
+        for h in (1e-5, 1e-6, 1e-7, 1e-8):
+            fp = (f.astype(np.float64) + h * d).astype(np.float32)
+            fm = (f.astype(np.float64) - h * d).astype(np.float32)
+            if np.array_equal(_clip_pattern(orc, fp, reg, lam, K)[1], pat0) and \
+                    np.array_equal(_clip_pattern(orc, fm, reg, lam, K)[1], pat0):
+                terms = gf * (fp.astype(np.float64) - fm) / (2 * h)
+                results[name] = ((loss(fp) - loss(fm)) / (2 * h), float(np.sum(terms)),
+                                 float(np.sum(np.abs(terms))), h)
+                break
+    for h in (1e-5, 1e-6, 1e-7, 1e-8):
+        if np.array_equal(_clip_pattern(orc, f, reg, lam + h, K)[1], pat0) and \
+                np.array_equal(_clip_pattern(orc, f, reg, lam - h, K)[1], pat0):
+            results["lambda"] = ((loss(f, lam + h) - loss(f, lam - h)) / (2 * h), float(gout[0]), 0.0, h)
+            break
+    assert set(results) == set(dirs) | {"lambda"}, sorted(results)   # a smooth step was found for each
+    for name, (fd, an, absum, h) in results.items():
+        scale = max(abs(fd), absum / 100)
+        assert abs(fd - an) <= 1e-3 * scale, (name, h, fd, an, absum)
+    # the c gradients are the f gradient's sums along df/dc (FP64 on both sides)
+    for k, name in ((1, "c1"), (2, "c2")):
+        e = float(np.sum(gf * dirs[name]))
+        assert abs(gout[k] - e) <= 1e-9 * float(np.sum(np.abs(gf * dirs[name]))), (name, gout[k], e)
