@@ -442,7 +442,9 @@ __device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, flo
 //  * neighbour-table rows and v in shared memory, neighbour values from the
 //    global arrays (only the owner reads a pixel's rows and v).
 //  * everything in global memory.
-constexpr int kBackwardThreads = 1024;  // block size of the persistent reverse sweep (2 per SM)
+constexpr int kBackwardThreads = 1024;  // block size of the persistent reverse sweep
+constexpr int kBackwardMinBlocks = 2;   // resident blocks per SM the registers are sized for
+constexpr int kBackwardUnroll = 1;      // pixels per thread whose loads are in flight together
 // dynamic shared memory of the persistent solver: one or two blocks per SM
 constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 112 * 1024; }
 constexpr int kCompactThreads = 512;   // two blocks per SM: one block's block barriers overlap the other's work
@@ -2372,7 +2374,212 @@ __device__ __forceinline__ double block_sum1(double x, double* s_red) {
     return t;
 }
 
-__global__ void __launch_bounds__(kBackwardThreads, 2048 / kBackwardThreads)
+// The replay's steps and phases B and C of a reverse step for U pixels of a
+// thread at a time: every load of all U (neighbour-table entries, then the
+// values they name) is issued before the first store.  No phase stores into
+// an array it loads from other pixels, and a pixel's own words are read
+// before they are written, so the U pixels' chains of dependent loads
+// overlap.  Every product that meets a sum is written as fmaf or __fmul_rn,
+// so that a pixel's rounding does not depend on which copy of the code (the
+// U-wide loop or the remainder) took it, and a batch and its images one by
+// one give the same bits.
+
+// Replay dual step (dual_one's arithmetic at float32): p' of iterate m + 1
+// from p, w of iterate m.
+template <int U>
+__device__ __forceinline__ void adj_replay_dual(const int (&a)[U], const int32_t* __restrict__ nD,
+                                                const int32_t* __restrict__ nR, const int32_t* __restrict__ nDL,
+                                                const int32_t* __restrict__ nUR, const float* __restrict__ P1,
+                                                const float* __restrict__ P2, const float* __restrict__ Wm,
+                                                float* __restrict__ Q1, float* __restrict__ Q2, float tau,
+                                                float inv_theta) {
+    int nd[U], nr[U], ndl[U], nur[U];
+    float p1[U], p2[U], w0[U], wd[U], wr[U], p2dl[U], p1ur[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        nd[k] = __ldg(nD + a[k]);
+        nr[k] = __ldg(nR + a[k]);
+        ndl[k] = __ldg(nDL + a[k]);
+        nur[k] = __ldg(nUR + a[k]);
+        p1[k] = P1[a[k]];
+        p2[k] = P2[a[k]];
+        w0[k] = Wm[a[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        wd[k] = nd[k] >= 0 ? Wm[nd[k]] : 0.f;
+        wr[k] = nr[k] >= 0 ? Wm[nr[k]] : 0.f;
+        p2dl[k] = ndl[k] >= 0 ? P2[ndl[k]] : 0.f;
+        p1ur[k] = nur[k] >= 0 ? P1[nur[k]] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        float g1 = 0.f, g2 = 0.f;
+        if (nd[k] != kNbOut) g1 = (nd[k] >= 0 ? wd[k] : w_fixed(p1[k], p2dl[k], nd[k], inv_theta)) - w0[k];
+        if (nr[k] != kNbOut) g2 = (nr[k] >= 0 ? wr[k] : w_fixed(p1ur[k], p2[k], nr[k], inv_theta)) - w0[k];
+        float q1, q2;
+        chambolle_update(p1[k], p2[k], g1, g2, tau, q1, q2);
+        Q1[a[k]] = q1;
+        Q2[a[k]] = q2;
+    }
+}
+
+// Replay primal step (primal_one's arithmetic and rounding, v read from
+// iterate m and written to iterate m + 1 with w).
+template <int U>
+__device__ __forceinline__ void adj_replay_primal(const int (&a)[U], const int32_t* __restrict__ nU,
+                                                  const int32_t* __restrict__ nL, const float* __restrict__ F,
+                                                  const float* __restrict__ P1, const float* __restrict__ P2,
+                                                  const float* __restrict__ Vm, float* Vn, float* Wn, float theta,
+                                                  float inv_theta) {
+    int nu[U], nl[U];
+    float q1[U], q2[U], vm[U], ff[U], xu[U], xl[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        nu[k] = __ldg(nU + a[k]);
+        nl[k] = __ldg(nL + a[k]);
+        q1[k] = P1[a[k]];
+        q2[k] = P2[a[k]];
+        vm[k] = Vm[a[k]];
+        ff[k] = __ldg(F + a[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        xu[k] = nu[k] >= 0 ? P1[nu[k]] : 0.f;
+        xl[k] = nl[k] >= 0 ? P2[nl[k]] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const float div = (q1[k] - xu[k]) + (q2[k] - xl[k]);
+        const float un = fmaf(-theta, div, vm[k]);
+        const float vn = clamp01(un - ff[k]);
+        Vn[a[k]] = vn;
+        Wn[a[k]] = fmaf(-vn, inv_theta, div);
+    }
+}
+
+// Phase B: qbar = pbar + theta grad ubar, then the adjoint of the
+// fixed-point step p' = (p + tau g) / (1 + tau |g|) at iterate m (p, w) with
+// p' of iterate m + 1: gbar (to gb1, gb2) and qbar / d (to pd1, pd2).
+template <int U>
+__device__ __forceinline__ void adj_phase_b(const int (&a)[U], const int32_t* __restrict__ nD,
+                                            const int32_t* __restrict__ nR, const int32_t* __restrict__ nDL,
+                                            const int32_t* __restrict__ nUR, const float* __restrict__ ub,
+                                            const float* __restrict__ P1, const float* __restrict__ P2,
+                                            const float* __restrict__ Wm, const float* __restrict__ Q1,
+                                            const float* __restrict__ Q2, const float* __restrict__ p1b,
+                                            const float* __restrict__ p2b, float* __restrict__ gb1,
+                                            float* __restrict__ gb2, float* __restrict__ pd1,
+                                            float* __restrict__ pd2, float theta, float tau, float inv_theta) {
+    int nd[U], nr[U], ndl[U], nur[U];
+    float ua[U], p1[U], p2[U], w0[U], q1[U], q2[U], pb1[U], pb2[U];
+    float ud[U], ur[U], wd[U], wr[U], p2dl[U], p1ur[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        nd[k] = __ldg(nD + a[k]);
+        nr[k] = __ldg(nR + a[k]);
+        ndl[k] = __ldg(nDL + a[k]);
+        nur[k] = __ldg(nUR + a[k]);
+        ua[k] = ub[a[k]];
+        p1[k] = P1[a[k]];
+        p2[k] = P2[a[k]];
+        w0[k] = Wm[a[k]];
+        q1[k] = Q1[a[k]];
+        q2[k] = Q2[a[k]];
+        pb1[k] = p1b[a[k]];
+        pb2[k] = p2b[a[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        ud[k] = nd[k] >= 0 ? ub[nd[k]] : 0.f;
+        ur[k] = nr[k] >= 0 ? ub[nr[k]] : 0.f;
+        wd[k] = nd[k] >= 0 ? Wm[nd[k]] : 0.f;
+        wr[k] = nr[k] >= 0 ? Wm[nr[k]] : 0.f;
+        p2dl[k] = ndl[k] >= 0 ? P2[ndl[k]] : 0.f;
+        p1ur[k] = nur[k] >= 0 ? P1[nur[k]] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const bool dn = nd[k] != kNbOut, rt = nr[k] != kNbOut;
+        const float qb1 = dn ? fmaf(theta, ud[k] - ua[k], pb1[k]) : pb1[k];
+        const float qb2 = rt ? fmaf(theta, ur[k] - ua[k], pb2[k]) : pb2[k];
+        // g^n as in the forward dual step
+        const float g1 = dn ? (nd[k] >= 0 ? wd[k] : w_fixed(p1[k], p2dl[k], nd[k], inv_theta)) - w0[k] : 0.f;
+        const float g2 = rt ? (nr[k] >= 0 ? wr[k] : w_fixed(p1ur[k], p2[k], nr[k], inv_theta)) - w0[k] : 0.f;
+        const float s2 = fmaf(g1, g1, g2 * g2);
+        const float inv_nrm = s2 > 0.f ? rsqrtf(s2) : 0.f;
+        const float r = __fdividef(1.0f, fmaf(tau, s2 * inv_nrm, 1.0f));   // 1 / (1 + tau |g|)
+        // gbar = (tau / d) (qbar - (qbar . q) g / |g|), d = 1 + tau |g|
+        const float dot = fmaf(qb1, q1[k], __fmul_rn(qb2, q2[k])) * inv_nrm;
+        const float tr = tau * r;
+        gb1[a[k]] = dn ? tr * fmaf(-dot, g1, qb1) : 0.f;
+        gb2[a[k]] = rt ? tr * fmaf(-dot, g2, qb2) : 0.f;
+        pd1[a[k]] = qb1 * r;
+        pd2[a[k]] = qb2 * r;
+    }
+}
+
+// Phase C: wbar = -div gbar at x, x + e1, x + e2; pbar, vbar of iterate m;
+// then (m > 0) the next step's phase A: the clip's adjoint at v of iterate m
+// into ubar and fbar.
+template <int U>
+__device__ __forceinline__ void adj_phase_c(const int (&a)[U], const int32_t* __restrict__ nU,
+                                            const int32_t* __restrict__ nL, const int32_t* __restrict__ nD,
+                                            const int32_t* __restrict__ nR, const int32_t* __restrict__ nDL,
+                                            const int32_t* __restrict__ nUR, const float* __restrict__ gb1,
+                                            const float* __restrict__ gb2, const float* __restrict__ pd1,
+                                            const float* __restrict__ pd2, const float* __restrict__ Vm,
+                                            float* __restrict__ p1b, float* __restrict__ p2b,
+                                            float* __restrict__ vb, float* ub, float* fb, bool phase_a,
+                                            float inv_theta) {
+    int nu[U], nl[U], nd[U], nr[U], ndl[U], nur[U];
+    float g1[U], g2[U], d1[U], d2[U], ua[U], vm[U], fbv[U];
+    float g1u[U], g2l[U], g1d[U], g2d[U], g2dl[U], g1r[U], g2r[U], g1ur[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        nu[k] = __ldg(nU + a[k]);
+        nl[k] = __ldg(nL + a[k]);
+        nd[k] = __ldg(nD + a[k]);
+        nr[k] = __ldg(nR + a[k]);
+        ndl[k] = __ldg(nDL + a[k]);
+        nur[k] = __ldg(nUR + a[k]);
+        g1[k] = gb1[a[k]];
+        g2[k] = gb2[a[k]];
+        d1[k] = pd1[a[k]];
+        d2[k] = pd2[a[k]];
+        ua[k] = ub[a[k]];
+        vm[k] = phase_a ? Vm[a[k]] : 0.f;
+        fbv[k] = phase_a ? fb[a[k]] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        g1u[k] = nu[k] >= 0 ? gb1[nu[k]] : 0.f;
+        g2l[k] = nl[k] >= 0 ? gb2[nl[k]] : 0.f;
+        g1d[k] = nd[k] >= 0 ? gb1[nd[k]] : 0.f;
+        g2d[k] = nd[k] >= 0 ? gb2[nd[k]] : 0.f;
+        g2dl[k] = ndl[k] >= 0 ? gb2[ndl[k]] : 0.f;
+        g1r[k] = nr[k] >= 0 ? gb1[nr[k]] : 0.f;
+        g2r[k] = nr[k] >= 0 ? gb2[nr[k]] : 0.f;
+        g1ur[k] = nur[k] >= 0 ? gb1[nur[k]] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const float wb0 = -((g1[k] - g1u[k]) + (g2[k] - g2l[k]));
+        const float wbd = -((g1d[k] - g1[k]) + (g2d[k] - g2dl[k]));
+        const float wbr = -((g1r[k] - g1ur[k]) + (g2r[k] - g2[k]));
+        p1b[a[k]] = d1[k] - (nd[k] != kNbOut ? wbd - wb0 : 0.f);
+        p2b[a[k]] = d2[k] - (nr[k] != kNbOut ? wbr - wb0 : 0.f);
+        const float v_b = fmaf(-wb0, inv_theta, ua[k]);
+        vb[a[k]] = v_b;
+        if (phase_a) {
+            const float sb = (vm[k] > 0.f && vm[k] < 1.f) ? v_b : 0.f;
+            ub[a[k]] = sb;
+            fb[a[k]] = fbv[k] - sb;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBackwardThreads, kBackwardMinBlocks)
 k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
                    const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
                    const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
@@ -2397,6 +2604,21 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
         return Planes{b, b + stride, b + 2 * stride, b + 3 * stride};
     };
     const float theta = P.theta, tau = P.tau, inv_theta = P.inv_theta;
+    // op(pixels[U]) over this block's range, U = kBackwardUnroll pixels a
+    // thread at a time (stride nt), then the rest one by one
+    auto each = [&](auto&& op) {
+        int a = a0 + tid;
+        for (; a + (kBackwardUnroll - 1) * nt < a1; a += kBackwardUnroll * nt) {
+            int b[kBackwardUnroll];
+#pragma unroll
+            for (int k = 0; k < kBackwardUnroll; ++k) b[k] = a + k * nt;
+            op(b);
+        }
+        for (; a < a1; a += nt) {
+            const int b[1] = {a};
+            op(b);
+        }
+    };
     // adjoint of the final iterate
     for (int a = a0 + tid; a < a1; a += nt) {
         A.p1b[a] = 0.f; A.p2b[a] = 0.f; A.vb[a] = A.gv[a]; A.fb[a] = 0.f;
@@ -2422,21 +2644,13 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
         if (!grid_sync(h, nblocks, gen)) return;
         for (int m = 0; m < M; ++m) {
             const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
-            for (int a = a0 + tid; a < a1; a += nt)
-                dual_one(P, a, Own<float, false>{nb, stride, nullptr, F, 0}, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2,
-                         0u);
+            each([&](const auto& b) {
+                adj_replay_dual(b, nD, nR, nDL, nUR, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, tau, inv_theta);
+            });
             if (!grid_sync(h, nblocks, gen)) return;
-            for (int a = a0 + tid; a < a1; a += nt) {
-                const int n_up = __ldg(nU + a), n_left = __ldg(nL + a);
-                const float q1 = Sn.p1[a], q2 = Sn.p2[a];
-                const float q1u = n_up >= 0 ? Sn.p1[n_up] : 0.f;
-                const float q2l = n_left >= 0 ? Sn.p2[n_left] : 0.f;
-                const float div = (q1 - q1u) + (q2 - q2l);
-                const float un = fmaf(-theta, div, Sm.v[a]);
-                const float vn = clamp01(un - __ldg(F + a));
-                Sn.v[a] = vn;
-                Sn.w[a] = div - vn * inv_theta;
-            }
+            each([&](const auto& b) {
+                adj_replay_primal(b, nU, nL, F, Sn.p1, Sn.p2, Sm.v, Sn.v, Sn.w, theta, inv_theta);
+            });
             if (!grid_sync(h, nblocks, gen)) return;
         }
         // ---- walk back through the segment.  Phase A (clip, u^{n+1}) only
@@ -2456,66 +2670,17 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
         for (int m = M - 1; m >= 0; --m) {
             const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
             // B: qbar = pbar + theta grad ubar, the fixed-point step
-            for (int a = a0 + tid; a < a1; a += nt) {
-                const int n_down = __ldg(nD + a), n_right = __ldg(nR + a);
-                const int n_dl = __ldg(nDL + a), n_ur = __ldg(nUR + a);
-                const float ua = A.ub[a];
-                const float ud = n_down >= 0 ? A.ub[n_down] : 0.f;
-                const float ur = n_right >= 0 ? A.ub[n_right] : 0.f;
-                const float p1 = Sm.p1[a], p2 = Sm.p2[a], w0 = Sm.w[a];
-                const float wd = n_down >= 0 ? Sm.w[n_down] : 0.f;
-                const float wr = n_right >= 0 ? Sm.w[n_right] : 0.f;
-                const float p2dl = n_dl >= 0 ? Sm.p2[n_dl] : 0.f;
-                const float p1ur = n_ur >= 0 ? Sm.p1[n_ur] : 0.f;
-                const float q1 = Sn.p1[a], q2 = Sn.p2[a];
-                const float pb1 = A.p1b[a], pb2 = A.p2b[a];
-                const bool dn = n_down != kNbOut, rt = n_right != kNbOut;
-                const float qb1 = pb1 + (dn ? theta * (ud - ua) : 0.f);
-                const float qb2 = pb2 + (rt ? theta * (ur - ua) : 0.f);
-                // g^n as in the forward dual step
-                const float g1 = dn ? (n_down >= 0 ? wd : w_fixed(p1, p2dl, n_down, inv_theta)) - w0 : 0.f;
-                const float g2 = rt ? (n_right >= 0 ? wr : w_fixed(p1ur, p2, n_right, inv_theta)) - w0 : 0.f;
-                const float s2 = fmaf(g1, g1, g2 * g2);
-                const float inv_nrm = s2 > 0.f ? rsqrtf(s2) : 0.f;
-                const float r = __fdividef(1.0f, fmaf(tau, s2 * inv_nrm, 1.0f));   // 1 / (1 + tau |g|)
-                // gbar = (tau / d) (qbar - (qbar . q) g / |g|), d = 1 + tau |g|
-                const float dot = (qb1 * q1 + qb2 * q2) * inv_nrm;
-                const float tr = tau * r;
-                A.gb1[a] = dn ? tr * fmaf(-dot, g1, qb1) : 0.f;
-                A.gb2[a] = rt ? tr * fmaf(-dot, g2, qb2) : 0.f;
-                A.pd1[a] = qb1 * r;
-                A.pd2[a] = qb2 * r;
-            }
+            each([&](const auto& b) {
+                adj_phase_b(b, nD, nR, nDL, nUR, A.ub, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, A.p1b, A.p2b, A.gb1,
+                            A.gb2, A.pd1, A.pd2, theta, tau, inv_theta);
+            });
             if (!grid_sync(h, nblocks, gen)) return;
             // C: wbar = -div gbar at x, x+e1, x+e2; pbar, vbar of iterate n;
             // then the next step's phase A (no other pixel's phase C reads ub)
-            for (int a = a0 + tid; a < a1; a += nt) {
-                const int n_up = __ldg(nU + a), n_left = __ldg(nL + a);
-                const int n_down = __ldg(nD + a), n_right = __ldg(nR + a);
-                const int n_dl = __ldg(nDL + a), n_ur = __ldg(nUR + a);
-                const float g1 = A.gb1[a], g2 = A.gb2[a];
-                const float g1u = n_up >= 0 ? A.gb1[n_up] : 0.f;
-                const float g2l = n_left >= 0 ? A.gb2[n_left] : 0.f;
-                const float g1d = n_down >= 0 ? A.gb1[n_down] : 0.f;
-                const float g2d = n_down >= 0 ? A.gb2[n_down] : 0.f;
-                const float g2dl = n_dl >= 0 ? A.gb2[n_dl] : 0.f;
-                const float g1r = n_right >= 0 ? A.gb1[n_right] : 0.f;
-                const float g2r = n_right >= 0 ? A.gb2[n_right] : 0.f;
-                const float g1ur = n_ur >= 0 ? A.gb1[n_ur] : 0.f;
-                const float wb0 = -((g1 - g1u) + (g2 - g2l));
-                const float wbd = -((g1d - g1) + (g2d - g2dl));
-                const float wbr = -((g1r - g1ur) + (g2r - g2));
-                A.p1b[a] = A.pd1[a] - (n_down != kNbOut ? wbd - wb0 : 0.f);
-                A.p2b[a] = A.pd2[a] - (n_right != kNbOut ? wbr - wb0 : 0.f);
-                const float vb = A.ub[a] - wb0 * inv_theta;
-                A.vb[a] = vb;
-                if (m > 0) {
-                    const float vn = Sm.v[a];
-                    const float sb = (vn > 0.f && vn < 1.f) ? vb : 0.f;
-                    A.ub[a] = sb;
-                    A.fb[a] -= sb;
-                }
-            }
+            each([&](const auto& b) {
+                adj_phase_c(b, nU, nL, nD, nR, nDL, nUR, A.gb1, A.gb2, A.pd1, A.pd2, Sm.v, A.p1b, A.p2b, A.vb,
+                            A.ub, A.fb, m > 0, inv_theta);
+            });
             if (!grid_sync(h, nblocks, gen)) return;
         }
     }

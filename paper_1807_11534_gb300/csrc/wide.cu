@@ -206,73 +206,108 @@ __global__ void k_rm_gather(RowMajorArgs R, RowMajorState<T> S, int warm) {
 
 // ------------------------------------------------------------ iteration
 
-constexpr int kRmThreads = 512;   // four blocks per SM (32 registers): latency-bound loads
-constexpr int kRmUnroll = 2;      // pixels per thread in flight
+constexpr int kRmThreads = 512;   // threads per block
+constexpr int kRmMinBlocks = 3;   // resident blocks per SM the registers are sized for
+constexpr int kRmUnroll = 3;      // pixels per thread whose loads are in flight together
 
-// Dual step at pixel a (dual_one's arithmetic): reads p, w of the current
-// iterate, writes p' to the other buffers.
-template <typename T>
-__device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState<T>& S, int a, const T* P1i,
-                                        const T* P2i, T* P1o, T* P2o, uint32_t seed) {
-    const uint16_t fl = __ldg(S.fl + a);
-    const float p1 = Store<T>::ldc(P1i, a), p2 = Store<T>::ldc(P2i, a);
-    const float w0 = S.Wc[a];
-    float g1 = 0.f, g2 = 0.f;
-    if (!(fl & RM_DOWN_OUT)) {
-        const int d0 = a + (int)__ldg(S.dd + a);
-        if (fl & RM_DOWN_RD) {
-            g1 = S.Wc[d0] - w0;
-        } else {
-            const float p2dl = (fl & RM_DL_RD) ? Store<T>::ldc(P2i, d0 - 1) : 0.f;
-            g1 = rm_w_fixed(p1, p2dl, fl & RM_DOWN_FG, P.inv_theta) - w0;
-        }
+// The two phases below take U pixels of a thread at a time and issue every
+// load of all U before the first store: the stores go to other arrays than
+// the loads of the same phase (p' to the other buffers in the dual step; v
+// and w of the pixel itself in the primal step), so nothing orders a later
+// pixel's loads after an earlier pixel's stores, and U pixels' chains of two
+// dependent loads (the neighbourhood, then the neighbours) overlap.  Loads
+// whose use depends on a flag are issued unconditionally where the index is
+// always valid (w at a + 1, p2 at a - 1, clamped into [0, n)) and selected
+// afterwards.
+
+// Dual step (dual_one's arithmetic) at pixels a[0..U): reads p, w of the
+// current iterate, writes p' to the other buffers.
+template <typename T, int U>
+__device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState<T>& S, const int (&a)[U], int n,
+                                        const T* __restrict__ P1i, const T* __restrict__ P2i,
+                                        T* __restrict__ P1o, T* __restrict__ P2o, uint32_t seed) {
+    const float* __restrict__ Wc = S.Wc;
+    uint32_t fl[U];
+    int dd[U], du[U];
+    float p1[U], p2[U], w0[U], wr[U], xd[U], xr[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        fl[k] = __ldg(S.fl + a[k]);
+        dd[k] = __ldg(S.dd + a[k]);
+        du[k] = __ldg(S.du + a[k]);
+        p1[k] = Store<T>::ldc(P1i, a[k]);
+        p2[k] = Store<T>::ldc(P2i, a[k]);
+        w0[k] = Wc[a[k]];
+        wr[k] = Wc[min(a[k] + 1, n - 1)];
     }
-    if (!(fl & RM_RIGHT_OUT)) {
-        if (fl & RM_RIGHT_RD) {
-            g2 = S.Wc[a + 1] - w0;
-        } else {
-            float p1ur = 0.f;
-            if (fl & RM_UR_RD)
-                p1ur = Store<T>::ldc(P1i, a - (int)__ldg(S.du + a) + ((fl & RM_UP_RD) ? 1 : 0));
-            g2 = rm_w_fixed(p1ur, p2, fl & RM_RIGHT_FG, P.inv_theta) - w0;
-        }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        // x + e1: w there when in RD, else p2 at x + e1 - e2 (0 unless in RD);
+        // x + e2 fixed: p1 at x - e1 + e2 (0 unless in RD)
+        const int d0 = a[k] + dd[k];
+        const int ur = a[k] - du[k] + ((fl[k] & RM_UP_RD) ? 1 : 0);
+        xd[k] = (fl[k] & RM_DOWN_RD) ? Wc[d0] : (fl[k] & RM_DL_RD) ? Store<T>::ldc(P2i, d0 - 1) : 0.f;
+        xr[k] = (fl[k] & (RM_RIGHT_RD | RM_UR_RD)) == RM_UR_RD ? Store<T>::ldc(P1i, ur) : 0.f;
     }
-    float q1, q2;
-    chambolle_update(p1, p2, g1, g2, P.tau, q1, q2);
-    const uint32_t rnd = mix32((uint32_t)a * 3u + seed);
-    Store<T>::st_sr(P1o, a, q1, rnd);
-    Store<T>::st_sr(P2o, a, q2, mix32(rnd ^ 0x9e3779b9u));
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const uint32_t f = fl[k];
+        float g1 = 0.f, g2 = 0.f;
+        if (!(f & RM_DOWN_OUT))
+            g1 = ((f & RM_DOWN_RD) ? xd[k] : rm_w_fixed(p1[k], xd[k], f & RM_DOWN_FG, P.inv_theta)) - w0[k];
+        if (!(f & RM_RIGHT_OUT))
+            g2 = ((f & RM_RIGHT_RD) ? wr[k] : rm_w_fixed(xr[k], p2[k], f & RM_RIGHT_FG, P.inv_theta)) - w0[k];
+        float q1, q2;
+        chambolle_update(p1[k], p2[k], g1, g2, P.tau, q1, q2);
+        const uint32_t rnd = mix32((uint32_t)a[k] * 3u + seed);
+        Store<T>::st_sr(P1o, a[k], q1, rnd);
+        Store<T>::st_sr(P2o, a[k], q2, mix32(rnd ^ 0x9e3779b9u));
+    }
 }
 
-// Primal step at pixel a (primal_one's arithmetic): u' = v - theta div p',
-// v' = clip(u' - theta lambda f) in place, w' for the next dual step; wonly:
-// just w = div p - v/theta (a warm start).
-template <typename T>
-__device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorState<T>& S, int a, const T* P1n,
-                                          const T* P2n, bool wonly, bool check, bool write_u, bool write_prev,
-                                          uint32_t seed, float& du2, float& dv2) {
-    const uint16_t fl = __ldg(S.fl + a);
-    const float q1 = Store<T>::ldc(P1n, a), q2 = Store<T>::ldc(P2n, a);
-    const float vv = Store<T>::ld_rw(S.v, a) + Store<T>::vbias;
-    const float q1u = (fl & RM_UP_RD) ? Store<T>::ldc(P1n, a - (int)__ldg(S.du + a)) : 0.f;
-    const float q2l = (fl & RM_LEFT_RD) ? Store<T>::ldc(P2n, a - 1) : 0.f;
-    const float div = (q1 - q1u) + (q2 - q2l);
-    if (wonly) {
-        S.Wc[a] = div - vv * P.inv_theta;
-        return;
+// Primal step (primal_one's arithmetic) at pixels a[0..U): u' = v - theta
+// div p', v' = clip(u' - theta lambda f) in place, w' for the next dual step;
+// wonly: just w = div p - v/theta (a warm start).
+template <typename T, int U>
+__device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorState<T>& S, const int (&a)[U], int n,
+                                          const T* __restrict__ P1n, const T* __restrict__ P2n, bool wonly,
+                                          bool check, bool write_u, bool write_prev, uint32_t seed, float& du2,
+                                          float& dv2) {
+    uint32_t fl[U];
+    int du[U];
+    float q1[U], q2[U], vv[U], ff[U], q2l[U], q1u[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        fl[k] = __ldg(S.fl + a[k]);
+        du[k] = __ldg(S.du + a[k]);
+        q1[k] = Store<T>::ldc(P1n, a[k]);
+        q2[k] = Store<T>::ldc(P2n, a[k]);
+        vv[k] = Store<T>::ld_rw(S.v, a[k]) + Store<T>::vbias;
+        ff[k] = __ldg(S.F + a[k]);   // theta lambda f
+        q2l[k] = Store<T>::ldc(P2n, max(a[k] - 1, 0));
     }
-    const float un = fmaf(-P.theta, div, vv);
-    const float vn = clamp01(un - __ldg(S.F + a));   // F = theta lambda f
-    const float vs = Store<T>::st_sr(S.v, a, vn - Store<T>::vbias, mix32((uint32_t)a * 5u + seed)) +
-                     Store<T>::vbias;
-    S.Wc[a] = div - vs * P.inv_theta;
-    if (check) {
-        const float da = un - S.Up[a], db = vn - vv;
-        du2 = fmaf(da, da, du2);
-        dv2 = fmaf(db, db, dv2);
+#pragma unroll
+    for (int k = 0; k < U; ++k) q1u[k] = (fl[k] & RM_UP_RD) ? Store<T>::ldc(P1n, a[k] - du[k]) : 0.f;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const float div = (q1[k] - q1u[k]) + (q2[k] - ((fl[k] & RM_LEFT_RD) ? q2l[k] : 0.f));
+        if (wonly) {
+            S.Wc[a[k]] = div - vv[k] * P.inv_theta;
+            continue;
+        }
+        const float un = fmaf(-P.theta, div, vv[k]);
+        const float vn = clamp01(un - ff[k]);
+        const float vs = Store<T>::st_sr(S.v, a[k], vn - Store<T>::vbias, mix32((uint32_t)a[k] * 5u + seed)) +
+                         Store<T>::vbias;
+        S.Wc[a[k]] = div - vs * P.inv_theta;
+        if (check) {
+            const float da = un - S.Up[a[k]], db = vn - vv[k];
+            du2 = fmaf(da, da, du2);
+            dv2 = fmaf(db, db, dv2);
+        }
+        if (write_prev) S.Up[a[k]] = un;
+        if (write_u) S.U[a[k]] = un;
     }
-    if (write_prev) S.Up[a] = un;
-    if (write_u) S.U[a] = un;
 }
 
 // All iterations in one cooperative launch: each block owns a contiguous
@@ -280,7 +315,7 @@ __device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorSta
 // phase (and the Section 4 partials), grid barrier; the stopping test as in
 // the other compact paths.
 template <typename T>
-__global__ void __launch_bounds__(kRmThreads, 2048 / kRmThreads)
+__global__ void __launch_bounds__(kRmThreads, kRmMinBlocks)
 k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ counts, long long wide_above,
                 int iters, int check_every, double tol, int warm, double* partials, WsHeader* h) {
     __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
@@ -292,18 +327,27 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
     const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
     const int tid = threadIdx.x, nt = kRmThreads;
     unsigned gen = 0u;
+    // op(pixels[U]) over this block's range, U = kRmUnroll pixels a thread
+    // at a time (stride nt), then the rest one by one
     auto each = [&](auto&& op) {
         int a = a0 + tid;
         for (; a + (kRmUnroll - 1) * nt < a1; a += kRmUnroll * nt) {
+            int b[kRmUnroll];
 #pragma unroll
-            for (int k = 0; k < kRmUnroll; ++k) op(a + k * nt);
+            for (int k = 0; k < kRmUnroll; ++k) b[k] = a + k * nt;
+            op(b);
         }
-        for (; a < a1; a += nt) op(a);
+        for (; a < a1; a += nt) {
+            const int b[1] = {a};
+            op(b);
+        }
     };
     float d0 = 0.f, d1 = 0.f;
     if (warm) {
-        for (int a = a0 + tid; a < a1; a += nt)
-            rm_primal(P, S, a, S.p1[0], S.p2[0], true, false, false, false, 0u, d0, d1);
+        for (int a = a0 + tid; a < a1; a += nt) {
+            const int b[1] = {a};
+            rm_primal(P, S, b, n, S.p1[0], S.p2[0], true, false, false, false, 0u, d0, d1);
+        }
         if (!grid_sync(h, nblocks, gen)) return;
     }
     const int C = check_every;
@@ -311,11 +355,15 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
         const uint32_t seed_d = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
-        const T* pi1 = pb ? S.p1[1] : S.p1[0];
-        const T* pi2 = pb ? S.p2[1] : S.p2[0];
-        T* po1 = pb ? S.p1[0] : S.p1[1];
-        T* po2 = pb ? S.p2[0] : S.p2[1];
-        each([&](int a) { rm_dual(P, S, a, pi1, pi2, po1, po2, seed_d); });
+        // the ping-pong buffers picked by the parity in two copies of each
+        // phase, so that every array base stays a kernel parameter
+        auto dual = [&](const T* pi1, const T* pi2, T* po1, T* po2) {
+            each([&](const auto& b) { rm_dual(P, S, b, n, pi1, pi2, po1, po2, seed_d); });
+        };
+        if (pb)
+            dual(S.p1[1], S.p2[1], S.p1[0], S.p2[0]);
+        else
+            dual(S.p1[0], S.p2[0], S.p1[1], S.p2[1]);
         pb ^= 1;
         bool done;
         if (!grid_sync_poll(h, nblocks, gen, it > 0 && (it % C == 0), done)) return;
@@ -324,10 +372,20 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
         const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
-        if (!check && !write_prev)
-            each([&](int a) { rm_primal(P, S, a, po1, po2, false, false, false, false, seed, du2, dv2); });
+        auto primal = [&](const T* q1, const T* q2) {   // p' in q1, q2
+            if (!check && !write_prev)
+                each([&](const auto& b) {
+                    rm_primal(P, S, b, n, q1, q2, false, false, false, false, seed, du2, dv2);
+                });
+            else
+                each([&](const auto& b) {
+                    rm_primal(P, S, b, n, q1, q2, false, check, check, write_prev, seed, du2, dv2);
+                });
+        };
+        if (pb)
+            primal(S.p1[1], S.p2[1]);
         else
-            each([&](int a) { rm_primal(P, S, a, po1, po2, false, check, check, write_prev, seed, du2, dv2); });
+            primal(S.p1[0], S.p2[0]);
         if (check) {
             float x = du2, y = dv2;
             block_sum2f<kRmThreads>(x, y, reinterpret_cast<float*>(s_red));
