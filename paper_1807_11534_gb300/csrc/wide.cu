@@ -220,21 +220,38 @@ constexpr int kRmUnroll = 3;      // pixels per thread whose loads are in flight
 // always valid (w at a + 1, p2 at a - 1, clamped into [0, n)) and selected
 // afterwards.
 
+// Where a block reads its pixels' neighbourhoods and theta lambda f, which no
+// step writes: SM, copies in shared memory made at the start of the launch
+// (indexed from the block's first pixel a0), so that the first load of each
+// step's chain of two is a shared-memory load and only the neighbours' values
+// come from L2; else the global arrays.
+template <bool SM>
+struct RmNbh {
+    const uint16_t *fl, *dd, *du;
+    const float* F;
+    int a0;
+    __device__ __forceinline__ uint32_t flags(int a) const { return SM ? fl[a - a0] : __ldg(fl + a); }
+    __device__ __forceinline__ int down(int a) const { return SM ? dd[a - a0] : __ldg(dd + a); }
+    __device__ __forceinline__ int up(int a) const { return SM ? du[a - a0] : __ldg(du + a); }
+    __device__ __forceinline__ float tlf(int a) const { return SM ? F[a - a0] : __ldg(F + a); }
+};
+
 // Dual step (dual_one's arithmetic) at pixels a[0..U): reads p, w of the
 // current iterate, writes p' to the other buffers.
-template <typename T, int U>
-__device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState<T>& S, const int (&a)[U], int n,
-                                        const T* __restrict__ P1i, const T* __restrict__ P2i,
-                                        T* __restrict__ P1o, T* __restrict__ P2o, uint32_t seed) {
+template <typename T, bool SM, int U>
+__device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM>& N,
+                                        const int (&a)[U], int n, const T* __restrict__ P1i,
+                                        const T* __restrict__ P2i, T* __restrict__ P1o, T* __restrict__ P2o,
+                                        uint32_t seed) {
     const float* __restrict__ Wc = S.Wc;
     uint32_t fl[U];
     int dd[U], du[U];
     float p1[U], p2[U], w0[U], wr[U], xd[U], xr[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        fl[k] = __ldg(S.fl + a[k]);
-        dd[k] = __ldg(S.dd + a[k]);
-        du[k] = __ldg(S.du + a[k]);
+        fl[k] = N.flags(a[k]);
+        dd[k] = N.down(a[k]);
+        du[k] = N.up(a[k]);
         p1[k] = Store<T>::ldc(P1i, a[k]);
         p2[k] = Store<T>::ldc(P2i, a[k]);
         w0[k] = Wc[a[k]];
@@ -268,22 +285,22 @@ __device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState
 // Primal step (primal_one's arithmetic) at pixels a[0..U): u' = v - theta
 // div p', v' = clip(u' - theta lambda f) in place, w' for the next dual step;
 // wonly: just w = div p - v/theta (a warm start).
-template <typename T, int U>
-__device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorState<T>& S, const int (&a)[U], int n,
-                                          const T* __restrict__ P1n, const T* __restrict__ P2n, bool wonly,
-                                          bool check, bool write_u, bool write_prev, uint32_t seed, float& du2,
-                                          float& dv2) {
+template <typename T, bool SM, int U>
+__device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM>& N,
+                                          const int (&a)[U], const T* __restrict__ P1n,
+                                          const T* __restrict__ P2n, bool wonly, bool check, bool write_u,
+                                          bool write_prev, uint32_t seed, float& du2, float& dv2) {
     uint32_t fl[U];
     int du[U];
     float q1[U], q2[U], vv[U], ff[U], q2l[U], q1u[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        fl[k] = __ldg(S.fl + a[k]);
-        du[k] = __ldg(S.du + a[k]);
+        fl[k] = N.flags(a[k]);
+        du[k] = N.up(a[k]);
         q1[k] = Store<T>::ldc(P1n, a[k]);
         q2[k] = Store<T>::ldc(P2n, a[k]);
         vv[k] = Store<T>::ld_rw(S.v, a[k]) + Store<T>::vbias;
-        ff[k] = __ldg(S.F + a[k]);   // theta lambda f
+        ff[k] = N.tlf(a[k]);   // theta lambda f
         q2l[k] = Store<T>::ldc(P2n, max(a[k] - 1, 0));
     }
 #pragma unroll
@@ -310,21 +327,15 @@ __device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorSta
     }
 }
 
-// All iterations in one cooperative launch: each block owns a contiguous
-// range of the row-major compact order; dual phase, grid barrier, primal
-// phase (and the Section 4 partials), grid barrier; the stopping test as in
-// the other compact paths.
-template <typename T>
-__global__ void __launch_bounds__(kRmThreads, kRmMinBlocks)
-k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ counts, long long wide_above,
-                int iters, int check_every, double tol, int warm, double* partials, WsHeader* h) {
-    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
-    if (*(volatile int*)&h->done) return;
-    const int n = counts[1];
-    if (n <= wide_above) return;
+// All iterations of one launch for a block that owns the pixels [a0, a1) of
+// the row-major compact order: dual phase, grid barrier, primal phase (and
+// the Section 4 partials), grid barrier; the stopping test as in the other
+// compact paths.
+template <typename T, bool SM>
+__device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM>& N,
+                                              int n, int a0, int a1, int iters, int check_every, double tol,
+                                              int warm, double* partials, WsHeader* h, double* s_red) {
     const unsigned nblocks = gridDim.x;
-    const int per = (n + (int)nblocks - 1) / (int)nblocks;
-    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
     const int tid = threadIdx.x, nt = kRmThreads;
     unsigned gen = 0u;
     // op(pixels[U]) over this block's range, U = kRmUnroll pixels a thread
@@ -346,7 +357,7 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
     if (warm) {
         for (int a = a0 + tid; a < a1; a += nt) {
             const int b[1] = {a};
-            rm_primal(P, S, b, n, S.p1[0], S.p2[0], true, false, false, false, 0u, d0, d1);
+            rm_primal(P, S, N, b, S.p1[0], S.p2[0], true, false, false, false, 0u, d0, d1);
         }
         if (!grid_sync(h, nblocks, gen)) return;
     }
@@ -358,7 +369,7 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
         // the ping-pong buffers picked by the parity in two copies of each
         // phase, so that every array base stays a kernel parameter
         auto dual = [&](const T* pi1, const T* pi2, T* po1, T* po2) {
-            each([&](const auto& b) { rm_dual(P, S, b, n, pi1, pi2, po1, po2, seed_d); });
+            each([&](const auto& b) { rm_dual(P, S, N, b, n, pi1, pi2, po1, po2, seed_d); });
         };
         if (pb)
             dual(S.p1[1], S.p2[1], S.p1[0], S.p2[0]);
@@ -375,11 +386,11 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
         auto primal = [&](const T* q1, const T* q2) {   // p' in q1, q2
             if (!check && !write_prev)
                 each([&](const auto& b) {
-                    rm_primal(P, S, b, n, q1, q2, false, false, false, false, seed, du2, dv2);
+                    rm_primal(P, S, N, b, q1, q2, false, false, false, false, seed, du2, dv2);
                 });
             else
                 each([&](const auto& b) {
-                    rm_primal(P, S, b, n, q1, q2, false, check, check, write_prev, seed, du2, dv2);
+                    rm_primal(P, S, N, b, q1, q2, false, check, check, write_prev, seed, du2, dv2);
                 });
         };
         if (pb)
@@ -412,6 +423,48 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
             }
             __syncthreads();
         }
+    }
+}
+
+// Shared memory of one block: theta lambda f (4 bytes) and the
+// neighbourhood (three 16-bit words) of up to kRmSmemPixels pixels, sized
+// for kRmMinBlocks blocks per SM.
+constexpr int kRmSmemPixels = 7360;
+constexpr size_t kRmSmemBytes = (size_t)kRmSmemPixels * (4 + 3 * 2);
+
+// All iterations in one cooperative launch: each block owns a contiguous
+// range of the row-major compact order and keeps its pixels' neighbourhoods
+// and theta lambda f in shared memory when they fit (the same choice in every
+// block: the ranges differ by at most one pixel).
+template <typename T>
+__global__ void __launch_bounds__(kRmThreads, kRmMinBlocks)
+k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ counts, long long wide_above,
+                int iters, int check_every, double tol, int warm, double* partials, WsHeader* h) {
+    __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
+    extern __shared__ __align__(16) unsigned char rm_smem[];
+    if (*(volatile int*)&h->done) return;
+    const int n = counts[1];
+    if (n <= wide_above) return;
+    const unsigned nblocks = gridDim.x;
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    if (per <= kRmSmemPixels) {
+        float* sF = reinterpret_cast<float*>(rm_smem);
+        uint16_t* sfl = reinterpret_cast<uint16_t*>(sF + kRmSmemPixels);
+        uint16_t* sdd = sfl + kRmSmemPixels;
+        uint16_t* sdu = sdd + kRmSmemPixels;
+        for (int i = threadIdx.x; i < a1 - a0; i += kRmThreads) {
+            sF[i] = __ldg(S.F + a0 + i);
+            sfl[i] = __ldg(S.fl + a0 + i);
+            sdd[i] = __ldg(S.dd + a0 + i);
+            sdu[i] = __ldg(S.du + a0 + i);
+        }
+        __syncthreads();
+        rm_iterations<T, true>(P, S, RmNbh<true>{sfl, sdd, sdu, sF, a0}, n, a0, a1, iters, check_every, tol, warm,
+                               partials, h, s_red);
+    } else {
+        rm_iterations<T, false>(P, S, RmNbh<false>{S.fl, S.dd, S.du, S.F, 0}, n, a0, a1, iters, check_every, tol,
+                                warm, partials, h, s_red);
     }
 }
 
@@ -480,8 +533,9 @@ static seg_status run_wide_rm_t(const RowMajorArgs& R, const RowMajorArrays& A, 
     k_rm_gather<T><<<row_blocks, 256, 0, s>>>(R, S, prm->warm_start);
     SEG_LAUNCHED("k_rm_gather");
     const void* kern = (const void*)k_solve_wide_rm<T>;
+    SEG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRmSmemBytes));
     int per_sm = 0;
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRmThreads, 0));
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRmThreads, kRmSmemBytes));
     if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_wide_rm cannot be resident");
     const long long most = std::max<long long>(1, std::min<long long>(A.cap, (long long)R.H * R.W));
     int grid = (int)std::min<long long>((long long)per_sm * sm_count(), (most + kRmThreads - 1) / kRmThreads);
@@ -496,7 +550,7 @@ static seg_status run_wide_rm_t(const RowMajorArgs& R, const RowMajorArrays& A, 
     WsHeader* h = R.h;
     void* args[] = {&Pk, &Sk, (void*)&counts, &above, &iters, &ce, &tol, &warm, &partials, &h};
     if (iters > 0 || warm) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kRmThreads), args, 0, s));
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kRmThreads), args, kRmSmemBytes, s));
         count_launch();
         if (debug_mode()) SEG_TRY(after_launch("k_solve_wide_rm"));
     }
