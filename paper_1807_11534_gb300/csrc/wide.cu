@@ -330,7 +330,14 @@ __device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorSta
 // All iterations of one launch for a block that owns the pixels [a0, a1) of
 // the row-major compact order: dual phase, grid barrier, primal phase (and
 // the Section 4 partials), grid barrier; the stopping test as in the other
-// compact paths.
+// compact paths.  Each barrier is split into arrival and wait around the
+// block's interior pixels of the next phase, which read only what this block
+// wrote: the primal steps of the pixels whose up and left neighbours are the
+// block's own ([ep, a1)), and the next iteration's dual steps of the pixels
+// whose right and lower neighbours' w are the block's own ([a0, bd)).  The
+// rest (the first and last row or so of the range) waits for the barrier.
+// A dual step done after the stopping test fired writes only the p buffer
+// that is not the result's.
 template <typename T, bool SM>
 __device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM>& N,
                                               int n, int a0, int a1, int iters, int check_every, double tol,
@@ -338,17 +345,40 @@ __device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajo
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = kRmThreads;
     unsigned gen = 0u;
-    // op(pixels[U]) over this block's range, U = kRmUnroll pixels a thread
-    // at a time (stride nt), then the rest one by one
-    auto each = [&](auto&& op) {
-        int a = a0 + tid;
-        for (; a + (kRmUnroll - 1) * nt < a1; a += kRmUnroll * nt) {
+    // the split points: bd = the first pixel whose dual step reads w of
+    // another block (x + e1 or x + e2 in RD at or beyond a1; the lower
+    // neighbours' positions grow with a, so every later pixel is treated
+    // alike), ep = one past the last pixel whose primal step reads p' of
+    // another block (x - e1 or x - e2 in RD before a0)
+    __shared__ int s_split[2];
+    if (tid == 0) {
+        s_split[0] = a1;
+        s_split[1] = a0;
+    }
+    __syncthreads();
+    {
+        int bd = a1, ep = a0;
+        for (int a = a0 + tid; a < a1; a += nt) {
+            const uint32_t f = N.flags(a);
+            if (((f & RM_DOWN_RD) && a + N.down(a) >= a1) || ((f & RM_RIGHT_RD) && a + 1 >= a1)) bd = min(bd, a);
+            if (((f & RM_UP_RD) && a - N.up(a) < a0) || ((f & RM_LEFT_RD) && a - 1 < a0)) ep = max(ep, a + 1);
+        }
+        if (bd < a1) atomicMin(&s_split[0], bd);
+        if (ep > a0) atomicMax(&s_split[1], ep);
+    }
+    __syncthreads();
+    const int bd = s_split[0], ep = s_split[1];
+    // op(pixels[U]) over [b0, b1), U = kRmUnroll pixels a thread at a time
+    // (stride nt), then the rest one by one
+    auto each = [&](int b0, int b1, auto&& op) {
+        int a = b0 + tid;
+        for (; a + (kRmUnroll - 1) * nt < b1; a += kRmUnroll * nt) {
             int b[kRmUnroll];
 #pragma unroll
             for (int k = 0; k < kRmUnroll; ++k) b[k] = a + k * nt;
             op(b);
         }
-        for (; a < a1; a += nt) {
+        for (; a < b1; a += nt) {
             const int b[1] = {a};
             op(b);
         }
@@ -361,42 +391,60 @@ __device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajo
         }
         if (!grid_sync(h, nblocks, gen)) return;
     }
+    // dual steps of iteration `it` over [b0, b1): p of buffer it & 1 into the
+    // other (the buffers picked by the parity in two copies, so that every
+    // array base stays a kernel parameter)
+    auto dual = [&](int it, int b0, int b1) {
+        const uint32_t seed_d = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
+        if (it & 1)
+            each(b0, b1, [&](const auto& b) { rm_dual(P, S, N, b, n, S.p1[1], S.p2[1], S.p1[0], S.p2[0], seed_d); });
+        else
+            each(b0, b1, [&](const auto& b) { rm_dual(P, S, N, b, n, S.p1[0], S.p2[0], S.p1[1], S.p2[1], seed_d); });
+    };
     const int C = check_every;
-    int pb = 0;
+    if (iters > 0) dual(0, a0, a1);
     for (int it = 0; it < iters; ++it) {
         const int l = it + 1;
-        const uint32_t seed_d = mix32(0x51ed270bu ^ (uint32_t)(it * 131));
-        // the ping-pong buffers picked by the parity in two copies of each
-        // phase, so that every array base stays a kernel parameter
-        auto dual = [&](const T* pi1, const T* pi2, T* po1, T* po2) {
-            each([&](const auto& b) { rm_dual(P, S, N, b, n, pi1, pi2, po1, po2, seed_d); });
-        };
-        if (pb)
-            dual(S.p1[1], S.p2[1], S.p1[0], S.p2[0]);
-        else
-            dual(S.p1[0], S.p2[0], S.p1[1], S.p2[1]);
-        pb ^= 1;
-        bool done;
-        if (!grid_sync_poll(h, nblocks, gen, it > 0 && (it % C == 0), done)) return;
-        if (done) return;   // the previous iteration's stopping test fired
+        // p' of this iteration is in buffer l & 1
+        grid_arrive(h, gen);
         const bool check = (l % C == 0) || l == iters;
         const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
         const uint32_t seed = mix32(0x2545f491u ^ (uint32_t)it);
         float du2 = 0.f, dv2 = 0.f;
-        auto primal = [&](const T* q1, const T* q2) {   // p' in q1, q2
-            if (!check && !write_prev)
-                each([&](const auto& b) {
-                    rm_primal(P, S, N, b, q1, q2, false, false, false, false, seed, du2, dv2);
-                });
-            else
-                each([&](const auto& b) {
-                    rm_primal(P, S, N, b, q1, q2, false, check, check, write_prev, seed, du2, dv2);
-                });
+        // primal steps over [b0, b1) with p' of buffer l & 1
+        auto primal = [&](int b0, int b1) {
+            if (l & 1) {
+                if (!check && !write_prev)
+                    each(b0, b1, [&](const auto& b) {
+                        rm_primal(P, S, N, b, S.p1[1], S.p2[1], false, false, false, false, seed, du2, dv2);
+                    });
+                else
+                    each(b0, b1, [&](const auto& b) {
+                        rm_primal(P, S, N, b, S.p1[1], S.p2[1], false, check, check, write_prev, seed, du2, dv2);
+                    });
+            } else {
+                if (!check && !write_prev)
+                    each(b0, b1, [&](const auto& b) {
+                        rm_primal(P, S, N, b, S.p1[0], S.p2[0], false, false, false, false, seed, du2, dv2);
+                    });
+                else
+                    each(b0, b1, [&](const auto& b) {
+                        rm_primal(P, S, N, b, S.p1[0], S.p2[0], false, check, check, write_prev, seed, du2, dv2);
+                    });
+            }
         };
-        if (pb)
-            primal(S.p1[1], S.p2[1]);
+        // after a stopping test the barrier may end the solve, so no primal
+        // step runs before it there
+        const bool poll = it > 0 && (it % C == 0);
+        const bool early = !(poll && tol > 0.0);
+        if (early) primal(ep, a1);
+        bool done;
+        if (!grid_wait(h, nblocks, gen, poll, done)) return;
+        if (done) return;   // the previous iteration's stopping test fired
+        if (early)
+            primal(a0, ep);
         else
-            primal(S.p1[0], S.p2[0]);
+            primal(a0, a1);
         if (check) {
             float x = du2, y = dv2;
             block_sum2f<kRmThreads>(x, y, reinterpret_cast<float*>(s_red));
@@ -405,7 +453,9 @@ __device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajo
                 partials[2 * blockIdx.x + 1] = y;
             }
         }
-        if (!grid_sync(h, nblocks, gen)) return;
+        grid_arrive(h, gen);
+        if (l < iters) dual(l, a0, bd);
+        if (!grid_wait(h, nblocks, gen)) return;
         if (check && blockIdx.x == 0) {
             // Section 4 stopping test: fixed-order FP64 sum of the block
             // partials, squared norms against tol^2
@@ -423,6 +473,7 @@ __device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajo
             }
             __syncthreads();
         }
+        if (l < iters) dual(l, bd, a1);
     }
 }
 

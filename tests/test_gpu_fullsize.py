@@ -129,3 +129,23 @@ def test_polygons_4096_16bit_mean_error_and_mask(orc, delta, storage):
     d = np.abs(out["u"] - st.u)
     assert d.mean() <= 1e-3, d.mean()
     assert np.mean((out["u"] > 0.5) != (st.u > 0.5)) <= 1e-4
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_polygons_4096_stopping_test_on_the_row_major_path(orc, storage):
+    """The 4096^2 image at delta 0.1 (an RD beyond the shared-memory paths:
+    the row-major solve, whose barriers are split around each block's
+    interior pixels) with the Section 4 stopping test: a solve stopped by
+    tol gives the bits of the same solve run for exactly that many
+    iterations without a test, and the test's rule holds at the stop."""
+    f = _poly4096()
+    base = run_gpu(f, delta=0.1, lam=1.0, iters=300, check_every=10, storage=storage)
+    # a tolerance the increments cross between iterations 10 and 300
+    tol = 1.5 * max(base["stats"][1], base["stats"][2])
+    a = run_gpu(f, delta=0.1, lam=1.0, iters=300, tol=tol, check_every=10, storage=storage)
+    n = int(a["stats"][0])
+    assert 10 <= n < 300 and n % 10 == 0, n
+    assert max(a["stats"][1], a["stats"][2]) <= tol
+    b = run_gpu(f, delta=0.1, lam=1.0, iters=n, check_every=10, storage=storage)
+    for k in ("u", "v", "p1", "p2"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
