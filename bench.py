@@ -43,14 +43,14 @@ BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + 
 #    held on chip, so this is about 3 % of the algorithmic bytes;
 #  * poly4096_0.1: k_solve_wide_rm (the row-major global-memory solve),
 #    `bench.py --profile --profile-large --iters 20 --delta 0.1 [--storage
-#    bf16]` (4096x4096 polygons, 20 iterations): most of the state is served
-#    from L2, the DRAM traffic is about 0.76 of the algorithmic bytes at
-#    float32 (1.96 with the tile-major table) and 0.19 at bf16;
+#    bf16]` (4096x4096 polygons, 20 iterations): the neighbourhoods are in
+#    shared memory and most of the state is served from L2, the DRAM traffic
+#    is about 0.43 of the algorithmic bytes at float32 and 0.11 at bf16;
 #  * batch: k_solve_compact in waves, the same command's batch of 64 images
 #    (20 iterations; each wave's state is loaded once into shared memory).
 COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (38689280 + 530176) / 50,
-                               ("poly4096_0.1", "f32"): (589960192 + 653882880) / 20,
-                               ("poly4096_0.1", "bf16"): (85928704 + 95115264) / 20,
+                               ("poly4096_0.1", "f32"): (122818560 + 576565248) / 20,
+                               ("poly4096_0.1", "bf16"): (58687488 + 43230464) / 20,
                                ("batch", "f32"): (204280832 + 71778048) / 20}
 
 
