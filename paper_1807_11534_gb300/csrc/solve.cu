@@ -2374,6 +2374,37 @@ __device__ __forceinline__ double block_sum1(double x, double* s_red) {
     return t;
 }
 
+// Where the reverse sweep reads its pixels' neighbour-table rows (up, left,
+// down, right, down-left, up-right) and theta lambda f, which nothing
+// writes: SM, copies in shared memory made at the start of the launch
+// (indexed from the block's first pixel a0), so that the first load of each
+// phase's dependent chain is a shared-memory load; else the global table.
+enum { ADJ_U = 0, ADJ_L, ADJ_D, ADJ_R, ADJ_DL, ADJ_UR, ADJ_ROWS };
+// pixels a block can keep (28 bytes each) at kBackwardMinBlocks blocks per SM
+constexpr int kAdjSmemPixels = (225 * 1024 / kBackwardMinBlocks - 2048) / 28 / 32 * 32;
+__host__ __device__ constexpr int adj_table_row(int k) {
+    return k == ADJ_U ? NB_UP : k == ADJ_L ? NB_LEFT : k == ADJ_D ? NB_DOWN : k == ADJ_R ? NB_RIGHT
+         : k == ADJ_DL ? NB_DOWNLEFT : NB_UPRIGHT;
+}
+template <bool SM>
+struct AdjNb;
+template <>
+struct AdjNb<true> {   // rows of kAdjSmemPixels words, then theta lambda f
+    const int32_t* t;
+    int a0;
+    __device__ __forceinline__ int nb(int k, int a) const { return t[k * kAdjSmemPixels + (a - a0)]; }
+    __device__ __forceinline__ float tlf(int a) const {
+        return reinterpret_cast<const float*>(t + ADJ_ROWS * kAdjSmemPixels)[a - a0];
+    }
+};
+template <>
+struct AdjNb<false> {   // the rows of the global table
+    const int32_t* r[ADJ_ROWS];
+    const float* F;
+    __device__ __forceinline__ int nb(int k, int a) const { return __ldg(r[k] + a); }
+    __device__ __forceinline__ float tlf(int a) const { return __ldg(F + a); }
+};
+
 // The replay's steps and phases B and C of a reverse step for U pixels of a
 // thread at a time: every load of all U (neighbour-table entries, then the
 // values they name) is issued before the first store.  No phase stores into
@@ -2386,10 +2417,8 @@ __device__ __forceinline__ double block_sum1(double x, double* s_red) {
 
 // Replay dual step (dual_one's arithmetic at float32): p' of iterate m + 1
 // from p, w of iterate m.
-template <int U>
-__device__ __forceinline__ void adj_replay_dual(const int (&a)[U], const int32_t* __restrict__ nD,
-                                                const int32_t* __restrict__ nR, const int32_t* __restrict__ nDL,
-                                                const int32_t* __restrict__ nUR, const float* __restrict__ P1,
+template <bool SM, int U>
+__device__ __forceinline__ void adj_replay_dual(const int (&a)[U], const AdjNb<SM>& N, const float* __restrict__ P1,
                                                 const float* __restrict__ P2, const float* __restrict__ Wm,
                                                 float* __restrict__ Q1, float* __restrict__ Q2, float tau,
                                                 float inv_theta) {
@@ -2397,10 +2426,10 @@ __device__ __forceinline__ void adj_replay_dual(const int (&a)[U], const int32_t
     float p1[U], p2[U], w0[U], wd[U], wr[U], p2dl[U], p1ur[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        nd[k] = __ldg(nD + a[k]);
-        nr[k] = __ldg(nR + a[k]);
-        ndl[k] = __ldg(nDL + a[k]);
-        nur[k] = __ldg(nUR + a[k]);
+        nd[k] = N.nb(ADJ_D, a[k]);
+        nr[k] = N.nb(ADJ_R, a[k]);
+        ndl[k] = N.nb(ADJ_DL, a[k]);
+        nur[k] = N.nb(ADJ_UR, a[k]);
         p1[k] = P1[a[k]];
         p2[k] = P2[a[k]];
         w0[k] = Wm[a[k]];
@@ -2426,22 +2455,20 @@ __device__ __forceinline__ void adj_replay_dual(const int (&a)[U], const int32_t
 
 // Replay primal step (primal_one's arithmetic and rounding, v read from
 // iterate m and written to iterate m + 1 with w).
-template <int U>
-__device__ __forceinline__ void adj_replay_primal(const int (&a)[U], const int32_t* __restrict__ nU,
-                                                  const int32_t* __restrict__ nL, const float* __restrict__ F,
-                                                  const float* __restrict__ P1, const float* __restrict__ P2,
-                                                  const float* __restrict__ Vm, float* Vn, float* Wn, float theta,
-                                                  float inv_theta) {
+template <bool SM, int U>
+__device__ __forceinline__ void adj_replay_primal(const int (&a)[U], const AdjNb<SM>& N, const float* __restrict__ P1,
+                                                  const float* __restrict__ P2, const float* __restrict__ Vm,
+                                                  float* Vn, float* Wn, float theta, float inv_theta) {
     int nu[U], nl[U];
     float q1[U], q2[U], vm[U], ff[U], xu[U], xl[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        nu[k] = __ldg(nU + a[k]);
-        nl[k] = __ldg(nL + a[k]);
+        nu[k] = N.nb(ADJ_U, a[k]);
+        nl[k] = N.nb(ADJ_L, a[k]);
         q1[k] = P1[a[k]];
         q2[k] = P2[a[k]];
         vm[k] = Vm[a[k]];
-        ff[k] = __ldg(F + a[k]);
+        ff[k] = N.tlf(a[k]);
     }
 #pragma unroll
     for (int k = 0; k < U; ++k) {
@@ -2461,10 +2488,8 @@ __device__ __forceinline__ void adj_replay_primal(const int (&a)[U], const int32
 // Phase B: qbar = pbar + theta grad ubar, then the adjoint of the
 // fixed-point step p' = (p + tau g) / (1 + tau |g|) at iterate m (p, w) with
 // p' of iterate m + 1: gbar (to gb1, gb2) and qbar / d (to pd1, pd2).
-template <int U>
-__device__ __forceinline__ void adj_phase_b(const int (&a)[U], const int32_t* __restrict__ nD,
-                                            const int32_t* __restrict__ nR, const int32_t* __restrict__ nDL,
-                                            const int32_t* __restrict__ nUR, const float* __restrict__ ub,
+template <bool SM, int U>
+__device__ __forceinline__ void adj_phase_b(const int (&a)[U], const AdjNb<SM>& N, const float* __restrict__ ub,
                                             const float* __restrict__ P1, const float* __restrict__ P2,
                                             const float* __restrict__ Wm, const float* __restrict__ Q1,
                                             const float* __restrict__ Q2, const float* __restrict__ p1b,
@@ -2476,10 +2501,10 @@ __device__ __forceinline__ void adj_phase_b(const int (&a)[U], const int32_t* __
     float ud[U], ur[U], wd[U], wr[U], p2dl[U], p1ur[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        nd[k] = __ldg(nD + a[k]);
-        nr[k] = __ldg(nR + a[k]);
-        ndl[k] = __ldg(nDL + a[k]);
-        nur[k] = __ldg(nUR + a[k]);
+        nd[k] = N.nb(ADJ_D, a[k]);
+        nr[k] = N.nb(ADJ_R, a[k]);
+        ndl[k] = N.nb(ADJ_DL, a[k]);
+        nur[k] = N.nb(ADJ_UR, a[k]);
         ua[k] = ub[a[k]];
         p1[k] = P1[a[k]];
         p2[k] = P2[a[k]];
@@ -2522,11 +2547,8 @@ __device__ __forceinline__ void adj_phase_b(const int (&a)[U], const int32_t* __
 // Phase C: wbar = -div gbar at x, x + e1, x + e2; pbar, vbar of iterate m;
 // then (m > 0) the next step's phase A: the clip's adjoint at v of iterate m
 // into ubar and fbar.
-template <int U>
-__device__ __forceinline__ void adj_phase_c(const int (&a)[U], const int32_t* __restrict__ nU,
-                                            const int32_t* __restrict__ nL, const int32_t* __restrict__ nD,
-                                            const int32_t* __restrict__ nR, const int32_t* __restrict__ nDL,
-                                            const int32_t* __restrict__ nUR, const float* __restrict__ gb1,
+template <bool SM, int U>
+__device__ __forceinline__ void adj_phase_c(const int (&a)[U], const AdjNb<SM>& N, const float* __restrict__ gb1,
                                             const float* __restrict__ gb2, const float* __restrict__ pd1,
                                             const float* __restrict__ pd2, const float* __restrict__ Vm,
                                             float* __restrict__ p1b, float* __restrict__ p2b,
@@ -2537,12 +2559,12 @@ __device__ __forceinline__ void adj_phase_c(const int (&a)[U], const int32_t* __
     float g1u[U], g2l[U], g1d[U], g2d[U], g2dl[U], g1r[U], g2r[U], g1ur[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        nu[k] = __ldg(nU + a[k]);
-        nl[k] = __ldg(nL + a[k]);
-        nd[k] = __ldg(nD + a[k]);
-        nr[k] = __ldg(nR + a[k]);
-        ndl[k] = __ldg(nDL + a[k]);
-        nur[k] = __ldg(nUR + a[k]);
+        nu[k] = N.nb(ADJ_U, a[k]);
+        nl[k] = N.nb(ADJ_L, a[k]);
+        nd[k] = N.nb(ADJ_D, a[k]);
+        nr[k] = N.nb(ADJ_R, a[k]);
+        ndl[k] = N.nb(ADJ_DL, a[k]);
+        nur[k] = N.nb(ADJ_UR, a[k]);
         g1[k] = gb1[a[k]];
         g2[k] = gb2[a[k]];
         d1[k] = pd1[a[k]];
@@ -2579,24 +2601,15 @@ __device__ __forceinline__ void adj_phase_c(const int (&a)[U], const int32_t* __
     }
 }
 
-__global__ void __launch_bounds__(kBackwardThreads, kBackwardMinBlocks)
-k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
-                   const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
-                   const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
-    if (*(volatile int*)&h->done) return;
+// The reverse sweep of a block that owns the compact pixels [a0, a1).
+template <bool SM>
+__device__ __forceinline__ void adj_sweep(const IterParams& P, int iters, int ckpt_every, int n, int a0, int a1,
+                                          const int32_t* __restrict__ nb, int64_t stride,
+                                          const float* __restrict__ F, const float* __restrict__ ckpt,
+                                          const AdjArrays& A, WsHeader* h, const AdjNb<SM>& N) {
     const unsigned nblocks = gridDim.x;
-    const int n = counts[1];
-    const int per = (n + (int)nblocks - 1) / (int)nblocks;
-    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
     const int tid = threadIdx.x, nt = blockDim.x;
     unsigned gen = 0u;
-    // neighbour-table rows
-    const int32_t* __restrict__ nU = nb + NB_UP * stride;
-    const int32_t* __restrict__ nL = nb + NB_LEFT * stride;
-    const int32_t* __restrict__ nD = nb + NB_DOWN * stride;
-    const int32_t* __restrict__ nR = nb + NB_RIGHT * stride;
-    const int32_t* __restrict__ nDL = nb + NB_DOWNLEFT * stride;
-    const int32_t* __restrict__ nUR = nb + NB_UPRIGHT * stride;
     // the planes of recomputed iterate m in the segment buffer
     struct Planes { float *p1, *p2, *v, *w; };
     auto seg_at = [&](int m) {
@@ -2642,15 +2655,18 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
             }
         }
         if (!grid_sync(h, nblocks, gen)) return;
-        for (int m = 0; m < M; ++m) {
+        auto dual_op = [&](int m) {
             const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
-            each([&](const auto& b) {
-                adj_replay_dual(b, nD, nR, nDL, nUR, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, tau, inv_theta);
-            });
+            return [=](const auto& b) { adj_replay_dual(b, N, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, tau, inv_theta); };
+        };
+        auto primal_op = [&](int m) {
+            const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
+            return [=](const auto& b) { adj_replay_primal(b, N, Sn.p1, Sn.p2, Sm.v, Sn.v, Sn.w, theta, inv_theta); };
+        };
+        for (int m = 0; m < M; ++m) {
+            each(dual_op(m));
             if (!grid_sync(h, nblocks, gen)) return;
-            each([&](const auto& b) {
-                adj_replay_primal(b, nU, nL, F, Sn.p1, Sn.p2, Sm.v, Sn.v, Sn.w, theta, inv_theta);
-            });
+            each(primal_op(m));
             if (!grid_sync(h, nblocks, gen)) return;
         }
         // ---- walk back through the segment.  Phase A (clip, u^{n+1}) only
@@ -2667,20 +2683,27 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
             }
         }
         if (!grid_sync(h, nblocks, gen)) return;
-        for (int m = M - 1; m >= 0; --m) {
+        // B: qbar = pbar + theta grad ubar, the fixed-point step
+        auto b_op = [&](int m) {
             const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
-            // B: qbar = pbar + theta grad ubar, the fixed-point step
-            each([&](const auto& b) {
-                adj_phase_b(b, nD, nR, nDL, nUR, A.ub, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, A.p1b, A.p2b, A.gb1,
-                            A.gb2, A.pd1, A.pd2, theta, tau, inv_theta);
-            });
+            return [=](const auto& b) {
+                adj_phase_b(b, N, A.ub, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, A.p1b, A.p2b, A.gb1, A.gb2, A.pd1,
+                            A.pd2, theta, tau, inv_theta);
+            };
+        };
+        // C: wbar = -div gbar at x, x+e1, x+e2; pbar, vbar of iterate n;
+        // then the next step's phase A (no other pixel's phase C reads ub)
+        auto c_op = [&](int m) {
+            const Planes Sm = seg_at(m);
+            return [=](const auto& b) {
+                adj_phase_c(b, N, A.gb1, A.gb2, A.pd1, A.pd2, Sm.v, A.p1b, A.p2b, A.vb, A.ub, A.fb, m > 0,
+                            inv_theta);
+            };
+        };
+        for (int m = M - 1; m >= 0; --m) {
+            each(b_op(m));
             if (!grid_sync(h, nblocks, gen)) return;
-            // C: wbar = -div gbar at x, x+e1, x+e2; pbar, vbar of iterate n;
-            // then the next step's phase A (no other pixel's phase C reads ub)
-            each([&](const auto& b) {
-                adj_phase_c(b, nU, nL, nD, nR, nDL, nUR, A.gb1, A.gb2, A.pd1, A.pd2, Sm.v, A.p1b, A.p2b, A.vb,
-                            A.ub, A.fb, m > 0, inv_theta);
-            });
+            each(c_op(m));
             if (!grid_sync(h, nblocks, gen)) return;
         }
     }
@@ -2688,6 +2711,45 @@ k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __res
     for (int a = a0 + tid; a < a1; a += nt) {
         const float v0 = ckpt[2 * stride + a];
         if (v0 > 0.f && v0 < 1.f) A.fb[a] -= A.vb[a];
+    }
+}
+
+// Shared memory of one block: the six neighbour-table rows and theta lambda
+// f of up to kAdjSmemPixels pixels, sized for kBackwardMinBlocks blocks per
+// SM.
+constexpr size_t kAdjSmemBytes = (size_t)kAdjSmemPixels * (4 * ADJ_ROWS + 4);
+
+// SM: the block's neighbour-table rows and theta lambda f are copied into
+// shared memory first (the launch gives kAdjSmemBytes, and every block's
+// share of the largest possible RD fits); else they are read from the global
+// table.  Two kernels, so that each gets its own register allocation.
+template <bool SM>
+__global__ void __launch_bounds__(kBackwardThreads, kBackwardMinBlocks)
+k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
+                   const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
+                   const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
+    extern __shared__ __align__(16) unsigned char adj_smem[];
+    if (*(volatile int*)&h->done) return;
+    const unsigned nblocks = gridDim.x;
+    const int n = counts[1];
+    const int per = (n + (int)nblocks - 1) / (int)nblocks;
+    const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
+    if constexpr (SM) {
+        int32_t* sr = reinterpret_cast<int32_t*>(adj_smem);
+        float* sF = reinterpret_cast<float*>(sr + ADJ_ROWS * kAdjSmemPixels);
+        for (int i = threadIdx.x; i < a1 - a0; i += blockDim.x) {
+#pragma unroll
+            for (int k = 0; k < ADJ_ROWS; ++k)
+                sr[k * kAdjSmemPixels + i] = __ldg(nb + adj_table_row(k) * stride + a0 + i);
+            sF[i] = __ldg(F + a0 + i);
+        }
+        __syncthreads();
+        adj_sweep<true>(P, iters, ckpt_every, n, a0, a1, nb, stride, F, ckpt, A, h, AdjNb<true>{sr, a0});
+    } else {
+        const AdjNb<false> N{{nb + NB_UP * stride, nb + NB_LEFT * stride, nb + NB_DOWN * stride,
+                              nb + NB_RIGHT * stride, nb + NB_DOWNLEFT * stride, nb + NB_UPRIGHT * stride},
+                             F};
+        adj_sweep<false>(P, iters, ckpt_every, n, a0, a1, nb, stride, F, ckpt, A, h, N);
     }
 }
 
@@ -2962,21 +3024,34 @@ static seg_status backward_batch(const seg_params* prm, const BatchDesc& B, cons
         SEG_LAUNCHED("k_adj_gather");
         pixels += (int64_t)I.H * I.W;
     }
-    auto kern = k_backward_compact;
-    int per_sm = 0;
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBackwardThreads, 0));
-    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_backward_compact cannot be resident");
+    // the tables in shared memory when every block's share of the largest
+    // possible RD fits (otherwise no shared memory: the L1 keeps it for the
+    // global path)
     const int64_t most = std::max<int64_t>(1, std::min<int64_t>(C.cap, pixels));
+    const void* ks = (const void*)k_backward_compact<true>;
+    SEG_TRY_CUDA(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes));
+    int per_sm = 0;
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks, kBackwardThreads, kAdjSmemBytes));
+    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_backward_compact cannot be resident");
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
                                       std::max<int64_t>(1, (most + kBackwardThreads - 1) / kBackwardThreads));
+    const bool use_smem = (most + grid - 1) / grid <= kAdjSmemPixels;
+    const void* kern = use_smem ? ks : (const void*)k_backward_compact<false>;
+    if (!use_smem) {
+        int pg = 0;
+        SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pg, kern, kBackwardThreads, 0));
+        if (pg <= 0) return fail(SEG_ERR_CUDA, "k_backward_compact cannot be resident");
+        grid = (int)std::min<int64_t>((int64_t)pg * sm_count(),
+                                      std::max<int64_t>(1, (most + kBackwardThreads - 1) / kBackwardThreads));
+    }
+    const size_t smem = use_smem ? kAdjSmemBytes : 0;
     IterParams P = iter_params(prm, B.img[0].H, B.img[0].W, B.img[0].ld);
     int iters = prm->iters, ce = ckpt_every;
     const float* ck = static_cast<const float*>(ckpt);
     const int32_t* cnt = totals;
     void* args[] = {&P, &iters, &ce, (void*)&cnt, (void*)&nbp, &stride, (void*)&F, (void*)&ck, &A, &h};
     if (iters > 0) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kBackwardThreads), args,
-                                                 0, s));
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kBackwardThreads), args, smem, s));
         count_launch();
         if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
     }
