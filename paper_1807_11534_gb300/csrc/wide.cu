@@ -206,9 +206,9 @@ __global__ void k_rm_gather(RowMajorArgs R, RowMajorState<T> S, int warm) {
 
 // ------------------------------------------------------------ iteration
 
-constexpr int kRmThreads = 512;   // threads per block
-constexpr int kRmMinBlocks = 3;   // resident blocks per SM the registers are sized for
-constexpr int kRmUnroll = 3;      // pixels per thread whose loads are in flight together
+constexpr int kRmThreads = 768;   // threads per block
+constexpr int kRmMinBlocks = 2;   // resident blocks per SM the registers are sized for
+constexpr int kRmUnroll = 2;      // pixels per thread whose loads are in flight together
 
 // The two phases below take U pixels of a thread at a time and issue every
 // load of all U before the first store: the stores go to other arrays than
@@ -480,7 +480,7 @@ __device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajo
 // Shared memory of one block: theta lambda f (4 bytes) and the
 // neighbourhood (three 16-bit words) of up to kRmSmemPixels pixels, sized
 // for kRmMinBlocks blocks per SM.
-constexpr int kRmSmemPixels = 7360;
+constexpr int kRmSmemPixels = (225 * 1024 / kRmMinBlocks - 2048) / 10 / 32 * 32;
 constexpr size_t kRmSmemBytes = (size_t)kRmSmemPixels * (4 + 3 * 2);
 
 // All iterations in one cooperative launch: each block owns a contiguous
