@@ -221,11 +221,13 @@ constexpr int kRmUnroll = 2;      // pixels per thread whose loads are in flight
 // afterwards.
 
 // Where a block reads its pixels' neighbourhoods and theta lambda f, which no
-// step writes: SM, copies in shared memory made at the start of the launch
-// (indexed from the block's first pixel a0), so that the first load of each
-// step's chain of two is a shared-memory load and only the neighbours' values
-// come from L2; else the global arrays.
-template <bool SM>
+// step writes.  The neighbourhoods from copies in shared memory made at the
+// start of the launch (indexed from the block's first pixel a0) when SM, so
+// that the first load of each step's chain of two is a shared-memory load and
+// only the neighbours' values come from L2; theta lambda f from shared memory
+// too when SMF (an independent load: worth the 4 bytes only while they
+// leave the block's pixels room); else from the global arrays.
+template <bool SM, bool SMF>
 struct RmNbh {
     const uint16_t *fl, *dd, *du;
     const float* F;
@@ -233,13 +235,13 @@ struct RmNbh {
     __device__ __forceinline__ uint32_t flags(int a) const { return SM ? fl[a - a0] : __ldg(fl + a); }
     __device__ __forceinline__ int down(int a) const { return SM ? dd[a - a0] : __ldg(dd + a); }
     __device__ __forceinline__ int up(int a) const { return SM ? du[a - a0] : __ldg(du + a); }
-    __device__ __forceinline__ float tlf(int a) const { return SM ? F[a - a0] : __ldg(F + a); }
+    __device__ __forceinline__ float tlf(int a) const { return SMF ? F[a - a0] : __ldg(F + a); }
 };
 
 // Dual step (dual_one's arithmetic) at pixels a[0..U): reads p, w of the
 // current iterate, writes p' to the other buffers.
-template <typename T, bool SM, int U>
-__device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM>& N,
+template <typename T, bool SM, bool SMF, int U>
+__device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM, SMF>& N,
                                         const int (&a)[U], int n, const T* __restrict__ P1i,
                                         const T* __restrict__ P2i, T* __restrict__ P1o, T* __restrict__ P2o,
                                         uint32_t seed) {
@@ -285,8 +287,8 @@ __device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState
 // Primal step (primal_one's arithmetic) at pixels a[0..U): u' = v - theta
 // div p', v' = clip(u' - theta lambda f) in place, w' for the next dual step;
 // wonly: just w = div p - v/theta (a warm start).
-template <typename T, bool SM, int U>
-__device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM>& N,
+template <typename T, bool SM, bool SMF, int U>
+__device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM, SMF>& N,
                                           const int (&a)[U], const T* __restrict__ P1n,
                                           const T* __restrict__ P2n, bool wonly, bool check, bool write_u,
                                           bool write_prev, uint32_t seed, float& du2, float& dv2) {
@@ -338,8 +340,9 @@ __device__ __forceinline__ void rm_primal(const IterParams& P, const RowMajorSta
 // rest (the first and last row or so of the range) waits for the barrier.
 // A dual step done after the stopping test fired writes only the p buffer
 // that is not the result's.
-template <typename T, bool SM>
-__device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajorState<T>& S, const RmNbh<SM>& N,
+template <typename T, bool SM, bool SMF>
+__device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajorState<T>& S,
+                                              const RmNbh<SM, SMF>& N,
                                               int n, int a0, int a1, int iters, int check_every, double tol,
                                               int warm, double* partials, WsHeader* h, double* s_red) {
     const unsigned nblocks = gridDim.x;
@@ -477,16 +480,17 @@ __device__ __forceinline__ void rm_iterations(const IterParams& P, const RowMajo
     }
 }
 
-// Shared memory of one block: theta lambda f (4 bytes) and the
-// neighbourhood (three 16-bit words) of up to kRmSmemPixels pixels, sized
-// for kRmMinBlocks blocks per SM.
-constexpr int kRmSmemPixels = (225 * 1024 / kRmMinBlocks - 2048) / 10 / 32 * 32;
-constexpr size_t kRmSmemBytes = (size_t)kRmSmemPixels * (4 + 3 * 2);
+// Shared memory of one block, sized for kRmMinBlocks blocks per SM: the
+// neighbourhood (three 16-bit words) and theta lambda f of up to
+// kRmSmemPixelsF pixels, or the neighbourhood alone of up to kRmSmemPixels.
+constexpr size_t kRmSmemBytes = (225 * 1024 / kRmMinBlocks - 2048) / 60 * 60;
+constexpr int kRmSmemPixelsF = (int)(kRmSmemBytes / 10);
+constexpr int kRmSmemPixels = (int)(kRmSmemBytes / 6);
 
 // All iterations in one cooperative launch: each block owns a contiguous
-// range of the row-major compact order and keeps its pixels' neighbourhoods
-// and theta lambda f in shared memory when they fit (the same choice in every
-// block: the ranges differ by at most one pixel).
+// range of the row-major compact order and keeps its pixels' neighbourhoods,
+// and theta lambda f, in shared memory as far as they fit (the same choice in
+// every block: the ranges differ by at most one pixel).
 template <typename T>
 __global__ void __launch_bounds__(kRmThreads, kRmMinBlocks)
 k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ counts, long long wide_above,
@@ -499,11 +503,11 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
     const unsigned nblocks = gridDim.x;
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
-    if (per <= kRmSmemPixels) {
+    if (per <= kRmSmemPixelsF) {   // the same choice in every block
         float* sF = reinterpret_cast<float*>(rm_smem);
-        uint16_t* sfl = reinterpret_cast<uint16_t*>(sF + kRmSmemPixels);
-        uint16_t* sdd = sfl + kRmSmemPixels;
-        uint16_t* sdu = sdd + kRmSmemPixels;
+        uint16_t* sfl = reinterpret_cast<uint16_t*>(sF + kRmSmemPixelsF);
+        uint16_t* sdd = sfl + kRmSmemPixelsF;
+        uint16_t* sdu = sdd + kRmSmemPixelsF;
         for (int i = threadIdx.x; i < a1 - a0; i += kRmThreads) {
             sF[i] = __ldg(S.F + a0 + i);
             sfl[i] = __ldg(S.fl + a0 + i);
@@ -511,11 +515,23 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
             sdu[i] = __ldg(S.du + a0 + i);
         }
         __syncthreads();
-        rm_iterations<T, true>(P, S, RmNbh<true>{sfl, sdd, sdu, sF, a0}, n, a0, a1, iters, check_every, tol, warm,
-                               partials, h, s_red);
+        rm_iterations<T, true, true>(P, S, RmNbh<true, true>{sfl, sdd, sdu, sF, a0}, n, a0, a1, iters,
+                                     check_every, tol, warm, partials, h, s_red);
+    } else if (per <= kRmSmemPixels) {
+        uint16_t* sfl = reinterpret_cast<uint16_t*>(rm_smem);
+        uint16_t* sdd = sfl + kRmSmemPixels;
+        uint16_t* sdu = sdd + kRmSmemPixels;
+        for (int i = threadIdx.x; i < a1 - a0; i += kRmThreads) {
+            sfl[i] = __ldg(S.fl + a0 + i);
+            sdd[i] = __ldg(S.dd + a0 + i);
+            sdu[i] = __ldg(S.du + a0 + i);
+        }
+        __syncthreads();
+        rm_iterations<T, true, false>(P, S, RmNbh<true, false>{sfl, sdd, sdu, S.F, a0}, n, a0, a1, iters,
+                                      check_every, tol, warm, partials, h, s_red);
     } else {
-        rm_iterations<T, false>(P, S, RmNbh<false>{S.fl, S.dd, S.du, S.F, 0}, n, a0, a1, iters, check_every, tol,
-                                warm, partials, h, s_red);
+        rm_iterations<T, false, false>(P, S, RmNbh<false, false>{S.fl, S.dd, S.du, S.F, 0}, n, a0, a1, iters,
+                                       check_every, tol, warm, partials, h, s_red);
     }
 }
 
