@@ -488,22 +488,32 @@ constexpr int kRmSmemPixelsF = (int)(kRmSmemBytes / 10);
 constexpr int kRmSmemPixels = (int)(kRmSmemBytes / 6);
 
 // All iterations in one cooperative launch: each block owns a contiguous
-// range of the row-major compact order and keeps its pixels' neighbourhoods,
-// and theta lambda f, in shared memory as far as they fit (the same choice in
-// every block: the ranges differ by at most one pixel).
-template <typename T>
+// range of the row-major compact order.  SMEM (launched with kRmSmemBytes of
+// shared memory, for RD counts up to smem_above): each block keeps its
+// pixels' neighbourhoods, and theta lambda f, in shared memory as far as they
+// fit (the same choice in every block: the ranges differ by at most one
+// pixel).  Else (launched without, so that the L1 keeps the whole of its
+// on-chip memory for the global arrays; above smem_above) everything is read
+// from the global arrays.  Both are launched when the RD count is not known
+// on the host; the one that does not apply returns at once.
+template <typename T, bool SMEM>
 __global__ void __launch_bounds__(kRmThreads, kRmMinBlocks)
 k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ counts, long long wide_above,
-                int iters, int check_every, double tol, int warm, double* partials, WsHeader* h) {
+                long long smem_above, int iters, int check_every, double tol, int warm, double* partials,
+                WsHeader* h) {
     __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
     extern __shared__ __align__(16) unsigned char rm_smem[];
     if (*(volatile int*)&h->done) return;
     const int n = counts[1];
     if (n <= wide_above) return;
+    if (SMEM ? n > smem_above : n <= smem_above) return;   // the other launch's
     const unsigned nblocks = gridDim.x;
     const int per = (n + (int)nblocks - 1) / (int)nblocks;
     const int a0 = (int)blockIdx.x * per, a1 = min(n, a0 + per);
-    if (per <= kRmSmemPixelsF) {   // the same choice in every block
+    if (!SMEM) {
+        rm_iterations<T, false, false>(P, S, RmNbh<false, false>{S.fl, S.dd, S.du, S.F, 0}, n, a0, a1, iters,
+                                       check_every, tol, warm, partials, h, s_red);
+    } else if (per <= kRmSmemPixelsF) {   // the same choice in every block
         float* sF = reinterpret_cast<float*>(rm_smem);
         uint16_t* sfl = reinterpret_cast<uint16_t*>(sF + kRmSmemPixelsF);
         uint16_t* sdd = sfl + kRmSmemPixelsF;
@@ -529,9 +539,6 @@ k_solve_wide_rm(IterParams P, RowMajorState<T> S, const int32_t* __restrict__ co
         __syncthreads();
         rm_iterations<T, true, false>(P, S, RmNbh<true, false>{sfl, sdd, sdu, S.F, a0}, n, a0, a1, iters,
                                       check_every, tol, warm, partials, h, s_red);
-    } else {
-        rm_iterations<T, false, false>(P, S, RmNbh<false, false>{S.fl, S.dd, S.du, S.F, 0}, n, a0, a1, iters,
-                                       check_every, tol, warm, partials, h, s_red);
     }
 }
 
@@ -599,27 +606,40 @@ static seg_status run_wide_rm_t(const RowMajorArgs& R, const RowMajorArrays& A, 
     SEG_LAUNCHED("k_rm_rowscan");
     k_rm_gather<T><<<row_blocks, 256, 0, s>>>(R, S, prm->warm_start);
     SEG_LAUNCHED("k_rm_gather");
-    const void* kern = (const void*)k_solve_wide_rm<T>;
-    SEG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRmSmemBytes));
-    int per_sm = 0;
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRmThreads, kRmSmemBytes));
-    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_wide_rm cannot be resident");
     const long long most = std::max<long long>(1, std::min<long long>(A.cap, (long long)R.H * R.W));
-    int grid = (int)std::min<long long>((long long)per_sm * sm_count(), (most + kRmThreads - 1) / kRmThreads);
-    grid = std::max(1, (int)std::min<long long>(grid, max_partials));
+    auto grid_of = [&](const void* k, size_t smem, int& grid) -> seg_status {
+        int per_sm = 0;
+        SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRmThreads, smem));
+        if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_wide_rm cannot be resident");
+        grid = (int)std::min<long long>((long long)per_sm * sm_count(), (most + kRmThreads - 1) / kRmThreads);
+        grid = std::max(1, (int)std::min<long long>(grid, max_partials));
+        return SEG_OK;
+    };
+    const void* ks = (const void*)k_solve_wide_rm<T, true>;
+    const void* kg = (const void*)k_solve_wide_rm<T, false>;
+    SEG_TRY_CUDA(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRmSmemBytes));
+    int grid_s = 1, grid_g = 1;
+    SEG_TRY(grid_of(ks, kRmSmemBytes, grid_s));
+    SEG_TRY(grid_of(kg, 0, grid_g));
     IterParams Pk = P;
     RowMajorState<T> Sk = S;
     const int32_t* counts = R.counts;
     long long above = R.wide_above;
+    long long smem_above = (long long)kRmSmemPixels * grid_s;   // per <= kRmSmemPixels in every block
     int iters = prm->iters, ce = test_interval(prm->tol, prm->check_every, prm->iters);
     double tol = prm->tol;
     int warm = prm->warm_start;
     WsHeader* h = R.h;
-    void* args[] = {&Pk, &Sk, (void*)&counts, &above, &iters, &ce, &tol, &warm, &partials, &h};
+    void* args[] = {&Pk, &Sk, (void*)&counts, &above, &smem_above, &iters, &ce, &tol, &warm, &partials, &h};
     if (iters > 0 || warm) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kRmThreads), args, kRmSmemBytes, s));
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(ks, dim3(grid_s), dim3(kRmThreads), args, kRmSmemBytes, s));
         count_launch();
-        if (debug_mode()) SEG_TRY(after_launch("k_solve_wide_rm"));
+        if (debug_mode()) SEG_TRY(after_launch("k_solve_wide_rm (shared memory)"));
+        if (most > smem_above) {   // an RD count beyond the shared-memory launch is possible
+            SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kg, dim3(grid_g), dim3(kRmThreads), args, 0, s));
+            count_launch();
+            if (debug_mode()) SEG_TRY(after_launch("k_solve_wide_rm (global memory)"));
+        }
     }
     k_rm_scatter<T><<<row_blocks, 256, 0, s>>>(R, S, prm->iters, A.cap);
     SEG_LAUNCHED("k_rm_scatter");

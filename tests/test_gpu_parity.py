@@ -409,13 +409,15 @@ def test_full_size_2048_ds_sampled(orc, mode, delta):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("delta", [0.1, 0.2, 0.3])
+@pytest.mark.parametrize("delta", [0.1, 0.2, 0.3, 0.5, math.inf])
 def test_compact_matches_dense_on_the_whole_image(orc, delta):
     """Every pixel of the 2048x2048 workload: the compact solver (the
-    one-barrier shared-memory iteration at delta = 0.1 and 0.2, the
-    global-memory neighbour table at 0.3) against the dense solver run on the
-    same restricted domain, itself checked against the oracle above; both
-    are float32 iterations of the same steps."""
+    one-barrier shared-memory iteration at delta = 0.1 and 0.2; the row-major
+    solve beyond, with each block's neighbourhoods and theta lambda f in
+    shared memory at 0.3, its neighbourhoods alone at 0.5 and on the full
+    domain) against the dense solver run on the same restricted domain,
+    itself checked against the oracle above; both are float32 iterations of
+    the same steps."""
     P = synth.ellipses_ds(seed=0, H=2048, W=2048)
     c1, c2 = orc.class_means(P.z, P.label)
     _, f = orc.fitting(P.z, c1, c2, P.markers, P.gamma)
