@@ -69,7 +69,9 @@ __device__ __forceinline__ VolBuf vol_buf(const VolState& S, int b) {
     return b ? VolBuf{S.p[1][0], S.p[1][1], S.p[1][2]} : VolBuf{S.p[0][0], S.p[0][1], S.p[0][2]};
 }
 
-constexpr int kVolThreads = 512;   // four blocks per SM (32 registers): latency-bound loads
+constexpr int kVolThreads = 512;   // threads per block
+constexpr int kVolMinBlocks = 2;   // resident blocks per SM of the staged solve (64 registers)
+constexpr int kVolUnroll = 2;      // voxels per thread whose loads are in flight together (staged solve)
 constexpr int kVolArrays = 11 + VN_COUNT;
 constexpr int64_t kVolSlack = 256;
 
@@ -192,9 +194,146 @@ __global__ void k_vol_warm_w(const int32_t* __restrict__ counts, VolGeom G, VolS
         S.w[k] = vol_div(S, B, k) - S.v[k] * G.inv_theta;
 }
 
-// Dual (fixed-point) step at compact voxel k from the previous p (Bi) into Bo.
+// The two phases take U voxels of a thread at a time and issue every load of
+// all U before the first store, stage by stage (the table entries, then what
+// they name): the stores of a phase go to other arrays than its loads (p' to
+// the other buffers; v and w of the voxel itself), so the U voxels' chains of
+// dependent loads overlap instead of queueing behind each other's stores.
+
+// Dual (fixed-point) step at compact voxels k[0..U) from the previous p (Bi)
+// into Bo.
+template <int U>
 __device__ __forceinline__ void vol_dual(const VolGeom& G, const VolState& S, const VolBuf& Bi, const VolBuf& Bo,
-                                         int k) {
+                                         const int (&k)[U]) {
+    const int64_t st = S.stride;
+    const float* __restrict__ W = S.w;
+    const float* __restrict__ I1 = Bi.p1;
+    const float* __restrict__ I2 = Bi.p2;
+    const float* __restrict__ I3 = Bi.p3;
+    int nd[U], nr[U], nf[U];
+    float w0[U], p1[U], p2[U], p3[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int* nb = S.nb + k[u];
+        nd[u] = __ldg(nb + VN_DOWN * st);
+        nr[u] = __ldg(nb + VN_RIGHT * st);
+        nf[u] = __ldg(nb + VN_FRONT * st);
+        w0[u] = W[k[u]];
+        p1[u] = I1[k[u]];
+        p2[u] = I2[k[u]];
+        p3[u] = I3[k[u]];
+    }
+    // per forward neighbour y: w(y) when y is in RD; when y is fixed, the
+    // table entries of its other backward neighbours, then their p
+    // components (0 where those are not in RD)
+    float xd[U], xr[U], xf[U];
+    int s1[U][3], s2[U][3];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int* nb = S.nb + k[u];
+        const bool fd = nd[u] < 0 && nd[u] != kVOut, fr = nr[u] < 0 && nr[u] != kVOut,
+                   ff = nf[u] < 0 && nf[u] != kVOut;
+        xd[u] = nd[u] >= 0 ? W[nd[u]] : 0.f;
+        xr[u] = nr[u] >= 0 ? W[nr[u]] : 0.f;
+        xf[u] = nf[u] >= 0 ? W[nf[u]] : 0.f;
+        s1[u][0] = fd ? __ldg(nb + VN_DOWN_LEFT * st) : -1;
+        s2[u][0] = fd ? __ldg(nb + VN_DOWN_BACK * st) : -1;
+        s1[u][1] = fr ? __ldg(nb + VN_RIGHT_UP * st) : -1;
+        s2[u][1] = fr ? __ldg(nb + VN_RIGHT_BACK * st) : -1;
+        s1[u][2] = ff ? __ldg(nb + VN_FRONT_UP * st) : -1;
+        s2[u][2] = ff ? __ldg(nb + VN_FRONT_LEFT * st) : -1;
+    }
+    float a1[U][3], a2[U][3];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        a1[u][0] = vol_pat(I2, s1[u][0]);
+        a2[u][0] = vol_pat(I3, s2[u][0]);
+        a1[u][1] = vol_pat(I1, s1[u][1]);
+        a2[u][1] = vol_pat(I3, s2[u][1]);
+        a1[u][2] = vol_pat(I1, s1[u][2]);
+        a2[u][2] = vol_pat(I2, s2[u][2]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+        if (nd[u] >= 0) {
+            g1 = xd[u] - w0[u];
+        } else if (nd[u] != kVOut) {   // w at a fixed y = x + e1: its p1 backward neighbour is x itself
+            const float sm = p1[u] + a1[u][0] + a2[u][0];
+            g1 = (-sm - (nd[u] == kVFg ? G.inv_theta : 0.f)) - w0[u];
+        }
+        if (nr[u] >= 0) {
+            g2 = xr[u] - w0[u];
+        } else if (nr[u] != kVOut) {
+            const float sm = a1[u][1] + p2[u] + a2[u][1];
+            g2 = (-sm - (nr[u] == kVFg ? G.inv_theta : 0.f)) - w0[u];
+        }
+        if (nf[u] >= 0) {
+            g3 = xf[u] - w0[u];
+        } else if (nf[u] != kVOut) {
+            const float sm = a1[u][2] + a2[u][2] + p3[u];
+            g3 = (-sm - (nf[u] == kVFg ? G.inv_theta : 0.f)) - w0[u];
+        }
+        const float s2n = fmaf(g1, g1, fmaf(g2, g2, g3 * g3));
+        const float nrm = s2n > 0.f ? s2n * rsqrtf(s2n) : 0.f;
+        const float rc = __fdividef(1.0f, fmaf(G.tau, nrm, 1.0f));
+        Bo.p1[k[u]] = fmaf(G.tau, g1, p1[u]) * rc;
+        Bo.p2[k[u]] = fmaf(G.tau, g2, p2[u]) * rc;
+        Bo.p3[k[u]] = fmaf(G.tau, g3, p3[u]) * rc;
+    }
+}
+
+// Primal step at compact voxels k[0..U) with the new p (Bo): v in place, w
+// for the next dual step, u to the dense output on a stopping-test iteration.
+template <int U>
+__device__ __forceinline__ void vol_primal(const VolGeom& G, float* U_out, const VolState& S, const VolBuf& Bo,
+                                           const int (&k)[U], bool check, bool write_u, bool write_prev,
+                                           float& du2, float& dv2) {
+    const int64_t st = S.stride;
+    const float* __restrict__ Q1 = Bo.p1;
+    const float* __restrict__ Q2 = Bo.p2;
+    const float* __restrict__ Q3 = Bo.p3;
+    int nu[U], nl[U], nbk[U];
+    float q1[U], q2[U], q3[U], vv[U], ff[U], xu[U], xl[U], xb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        nu[u] = __ldg(S.nb + VN_UP * st + k[u]);
+        nl[u] = __ldg(S.nb + VN_LEFT * st + k[u]);
+        nbk[u] = __ldg(S.nb + VN_BACK * st + k[u]);
+        q1[u] = Q1[k[u]];
+        q2[u] = Q2[k[u]];
+        q3[u] = Q3[k[u]];
+        vv[u] = S.v[k[u]];
+        ff[u] = __ldg(S.f + k[u]);   // f premultiplied by theta lambda
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        xu[u] = vol_pat(Q1, nu[u]);
+        xl[u] = vol_pat(Q2, nl[u]);
+        xb[u] = vol_pat(Q3, nbk[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const float div = (q1[u] - xu[u]) + (q2[u] - xl[u]) + (q3[u] - xb[u]);
+        const float un = fmaf(-G.theta, div, vv[u]);
+        const float vn = clamp01(un - ff[u]);
+        S.v[k[u]] = vn;
+        S.w[k[u]] = div - vn * G.inv_theta;
+        if (check) {
+            const float da = un - S.up[k[u]], db = vn - vv[u];
+            du2 = fmaf(da, da, du2);
+            dv2 = fmaf(db, db, dv2);
+        }
+        if (write_prev) S.up[k[u]] = un;
+        if (write_u) U_out[__ldg(S.off + k[u])] = un;
+    }
+}
+
+// One voxel at a time (the solve of dense volumes, where every neighbour is
+// in RD and more warps hide the two-load chain better than staging).
+// Dual (fixed-point) step at compact voxel k from the previous p (Bi) into Bo.
+__device__ __forceinline__ void vol_dual1(const VolGeom& G, const VolState& S, const VolBuf& Bi, const VolBuf& Bo,
+                                          int k) {
     const int64_t st = S.stride;
     const int* nb = S.nb + k;
     const int nd = __ldg(nb + VN_DOWN * st), nr = __ldg(nb + VN_RIGHT * st), nf = __ldg(nb + VN_FRONT * st);
@@ -232,8 +371,8 @@ __device__ __forceinline__ void vol_dual(const VolGeom& G, const VolState& S, co
 
 // Primal step at compact voxel k with the new p (Bo): v in place, w for the
 // next dual step, u to the dense output on a stopping-test iteration.
-__device__ __forceinline__ void vol_primal(const VolGeom& G, float* U, const VolState& S, const VolBuf& Bo, int k,
-                                           bool check, bool write_u, bool write_prev, float& du2, float& dv2) {
+__device__ __forceinline__ void vol_primal1(const VolGeom& G, float* U, const VolState& S, const VolBuf& Bo, int k,
+                                            bool check, bool write_u, bool write_prev, float& du2, float& dv2) {
     const float div = vol_div(S, Bo, k);
     const float vv = S.v[k];
     const float un = fmaf(-G.theta, div, vv);
@@ -249,26 +388,54 @@ __device__ __forceinline__ void vol_primal(const VolGeom& G, float* U, const Vol
     if (write_u) U[__ldg(S.off + k)] = un;
 }
 
-__global__ void __launch_bounds__(kVolThreads, 4)
+// STAGED: kVolUnroll voxels a thread, staged loads, kVolMinBlocks blocks per
+// SM, for RD counts up to staged_upto (restricted volumes); else one voxel
+// at a time at four blocks per SM (dense volumes).  Both are launched (the
+// RD count is on the device); the one that does not apply returns at once.
+template <bool STAGED>
+__global__ void __launch_bounds__(kVolThreads, STAGED ? kVolMinBlocks : 4)
 k_solve_vol(VolGeom G, int iters, int check_every, double tol, const int32_t* __restrict__ counts, float* U,
-            VolState S, double* partials, WsHeader* h) {
+            VolState S, double* partials, WsHeader* h, long long staged_upto) {
     __shared__ double s_red[66];   // block_sum2f (as floats), stop flag
     if (*(volatile int*)&h->done) return;
     const unsigned nblocks = gridDim.x;
     const int n = counts[1];
+    if (STAGED ? n > staged_upto : n <= staged_upto) return;   // the other launch's
     const int tid = threadIdx.x;
     const int k0 = (int)blockIdx.x * kVolThreads + tid, stride = (int)nblocks * kVolThreads;
     const int C = check_every;
     unsigned gen = 0;
     int chk = 0;
+    // op(voxels[U]) over this thread's voxels k0, k0 + stride, ..., U =
+    // kVolUnroll at a time, then the rest one by one
+    constexpr int UN = STAGED ? kVolUnroll : 1;
+    auto each = [&](auto&& op) {
+        int k = k0;
+        for (; k + (UN - 1) * stride < n; k += UN * stride) {
+            int b[UN];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) b[u] = k + u * stride;
+            op(b);
+        }
+        for (; k < n; k += stride) {
+            const int b[1] = {k};
+            op(b);
+        }
+    };
     for (int l = 1; l <= iters; ++l) {
         const bool check = (l % C == 0) || l == iters;
         const bool write_prev = l < iters && ((l + 1) % C == 0 || l + 1 == iters);
         const VolBuf Bi = vol_buf(S, (l - 1) & 1), Bo = vol_buf(S, l & 1);
-        for (int k = k0; k < n; k += stride) vol_dual(G, S, Bi, Bo, k);
+        if constexpr (STAGED)
+            each([&](const auto& ks) { vol_dual(G, S, Bi, Bo, ks); });
+        else
+            for (int k = k0; k < n; k += stride) vol_dual1(G, S, Bi, Bo, k);
         if (!grid_sync(h, nblocks, gen)) return;
         float du2 = 0.f, dv2 = 0.f;
-        for (int k = k0; k < n; k += stride) vol_primal(G, U, S, Bo, k, check, check, write_prev, du2, dv2);
+        if constexpr (STAGED)
+            each([&](const auto& ks) { vol_primal(G, U, S, Bo, ks, check, check, write_prev, du2, dv2); });
+        else
+            for (int k = k0; k < n; k += stride) vol_primal1(G, U, S, Bo, k, check, check, write_prev, du2, dv2);
         double* part = partials + 2 * (int64_t)nblocks * (chk & 1);
         if (check) {
             float x = du2, y = dv2;
@@ -395,20 +562,34 @@ extern "C" seg_status seg_solve3d(const float* f, int D, int H, int W, int ld, c
     }
     k_vol_fixed<<<eblocks, 256, 0, s>>>(G, act, fgm, u, v, p1, p2, p3);
     SEG_LAUNCHED("k_vol_fixed");
-    const void* kern = (const void*)k_solve_vol;
-    int per_sm = 0;
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVolThreads, 0));
-    if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_vol cannot be resident");
-    int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), L.npartials / 2);
-    grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (std::max<int64_t>(S.cap, 1) + kVolThreads - 1) /
-                                                                  kVolThreads));
+    auto grid_of = [&](const void* k, int& grid) -> seg_status {
+        int per_sm = 0;
+        SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kVolThreads, 0));
+        if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_solve_vol cannot be resident");
+        grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), L.npartials / 2);
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (std::max<int64_t>(S.cap, 1) + kVolThreads - 1) /
+                                                                      kVolThreads));
+        return SEG_OK;
+    };
+    const void* ks = (const void*)k_solve_vol<true>;
+    const void* kd = (const void*)k_solve_vol<false>;
+    int grid_s = 1, grid_d = 1;
+    SEG_TRY(grid_of(ks, grid_s));
+    SEG_TRY(grid_of(kd, grid_d));
+    // the staged solve for RD up to half the volume, the plain one above
+    long long staged_upto = nvox / 2;
     int iters = prm->iters, ce = test_interval(prm->tol, prm->check_every, prm->iters);
     double tol = prm->tol;
-    void* args[] = {&G, &iters, &ce, &tol, (void*)&counts, &u, &S, &partials, &h};
+    void* args[] = {&G, &iters, &ce, &tol, (void*)&counts, &u, &S, &partials, &h, &staged_upto};
     if (iters > 0) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kVolThreads), args, 0, s));
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(ks, dim3(grid_s), dim3(kVolThreads), args, 0, s));
         count_launch();
-        if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
+        if (debug_mode()) SEG_TRY(after_launch("persistent solve (staged)"));
+        if (std::min<int64_t>(S.cap, nvox) > staged_upto) {
+            SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kd, dim3(grid_d), dim3(kVolThreads), args, 0, s));
+            count_launch();
+            if (debug_mode()) SEG_TRY(after_launch("persistent solve (plain)"));
+        }
     }
     k_vol_scatter<<<eblocks, 256, 0, s>>>(counts, h, prm->iters, S, u, v, p1, p2, p3);
     SEG_LAUNCHED("k_vol_scatter");
