@@ -367,8 +367,9 @@ seg_status seg_solve_batch(const seg_image* images, int n_images, const seg_para
  * ceil(iters / ckpt_every) iterates, for a state of `capacity` RD pixels. */
 size_t seg_ckpt_bytes(int64_t capacity, int iters, int ckpt_every);
 
-/* Scratch bytes of seg_backward (adjoint fields and one segment of
- * ckpt_every + 1 recomputed iterates). */
+/* Scratch bytes of seg_backward (adjoint fields and two segment buffers of
+ * ckpt_every + 1 recomputed iterates each: one segment is recomputed while
+ * the reverse steps walk back through the next later one). */
 size_t seg_backward_scratch_bytes(int64_t capacity, int ckpt_every);
 
 /* Differentiable forward (not in the paper): seg_solve in compact mode with

@@ -442,7 +442,8 @@ __device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, flo
 //  * neighbour-table rows and v in shared memory, neighbour values from the
 //    global arrays (only the owner reads a pixel's rows and v).
 //  * everything in global memory.
-constexpr int kBackwardThreads = 1024;  // block size of the persistent reverse sweep
+constexpr int kBackwardThreads = 1024;  // block size of the persistent reverse sweep (tables in global memory)
+constexpr int kBackwardThreadsSm = 512;  // block size of the sweep with its tables in shared memory
 constexpr int kBackwardMinBlocks = 2;   // resident blocks per SM the registers are sized for
 constexpr int kBackwardUnroll = 1;      // pixels per thread whose loads are in flight together
 // dynamic shared memory of the persistent solver: one or two blocks per SM
@@ -2338,7 +2339,7 @@ static IterParams iter_params(const seg_params* prm, int H, int W, int ld) {
 
 struct AdjArrays {
     float *p1b, *p2b, *vb, *ub, *gb1, *gb2, *pd1, *pd2, *fb, *gu, *gv;   // [stride] each
-    float* seg;        // segment buffer: [(C + 1)][4][stride]  (p1, p2, v, w)
+    float *seg, *seg2;   // two segment buffers: [(C + 1)][4][stride]  (p1, p2, v, w)
 };
 
 // gathers dL/du^K, dL/dv^K into compact order and clears the adjoint
@@ -2610,10 +2611,12 @@ __device__ __forceinline__ void adj_sweep(const IterParams& P, int iters, int ck
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, nt = blockDim.x;
     unsigned gen = 0u;
-    // the planes of recomputed iterate m in the segment buffer
+    // the planes of recomputed iterate m in segment buffer `buf` (two: the
+    // replay of one segment fills one while the reverse steps of the next
+    // later segment read the other)
     struct Planes { float *p1, *p2, *v, *w; };
-    auto seg_at = [&](int m) {
-        float* b = A.seg + (int64_t)m * 4 * stride;
+    auto seg_at = [&](int buf, int m) {
+        float* b = (buf ? A.seg2 : A.seg) + (int64_t)m * 4 * stride;
         return Planes{b, b + stride, b + 2 * stride, b + 3 * stride};
     };
     const float theta = P.theta, tau = P.tau, inv_theta = P.inv_theta;
@@ -2637,74 +2640,119 @@ __device__ __forceinline__ void adj_sweep(const IterParams& P, int iters, int ck
         A.p1b[a] = 0.f; A.p2b[a] = 0.f; A.vb[a] = A.gv[a]; A.fb[a] = 0.f;
     }
     const int nseg = (iters + ckpt_every - 1) / ckpt_every;
-    for (int k = nseg - 1; k >= 0; --k) {
-        const int n0 = k * ckpt_every;
-        const int M = min(ckpt_every, iters - n0);
-        // ---- replay the segment from its checkpoint (the forward's steps
-        // and rounding: dual_one, then the primal step of primal_one with v
-        // read from iterate m and written to iterate m + 1)
-        const float* c = ckpt + (int64_t)k * 3 * stride;
-        {
-            const Planes S0 = seg_at(0);
+    auto seg_len = [&](int k) { return min(ckpt_every, iters - k * ckpt_every); };
+    // Phase j of the replay of segment k into buffer buf: 0, the checkpoint
+    // and its w (formed from the checkpoint's own planes); then the dual and
+    // the primal step of each iteration m (the forward's steps and rounding:
+    // dual_one, then primal_one's primal step with v read from iterate m and
+    // written to iterate m + 1).
+    auto replay_phase = [&](int k, int buf, int j) {
+        if (j == 0) {
+            const float* c = ckpt + (int64_t)k * 3 * stride;
+            const Planes S0 = seg_at(buf, 0);
             float d0 = 0.f, d1 = 0.f;
-            // w of the checkpoint, formed from the checkpoint's own planes
             const Own<float, false> Oc{nb, stride, const_cast<float*>(c + 2 * stride), F, 0};
             for (int a = a0 + tid; a < a1; a += nt) {
                 S0.p1[a] = c[a]; S0.p2[a] = c[stride + a]; S0.v[a] = c[2 * stride + a];
                 primal_one(P, a, Oc, c, c + stride, nullptr, nullptr, S0.w, true, false, false, false, 0u, d0, d1);
             }
+            return;
         }
-        if (!grid_sync(h, nblocks, gen)) return;
-        auto dual_op = [&](int m) {
-            const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
-            return [=](const auto& b) { adj_replay_dual(b, N, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, tau, inv_theta); };
-        };
-        auto primal_op = [&](int m) {
-            const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
-            return [=](const auto& b) { adj_replay_primal(b, N, Sn.p1, Sn.p2, Sm.v, Sn.v, Sn.w, theta, inv_theta); };
-        };
-        for (int m = 0; m < M; ++m) {
-            each(dual_op(m));
-            if (!grid_sync(h, nblocks, gen)) return;
-            each(primal_op(m));
-            if (!grid_sync(h, nblocks, gen)) return;
-        }
-        // ---- walk back through the segment.  Phase A (clip, u^{n+1}) only
-        // touches the pixel itself, so it runs at the end of phase C of the
-        // step before (and here for the segment's last step).
-        {
-            const bool last = n0 + M == iters;
-            const float* vM = seg_at(M).v;
+        const int m = (j - 1) >> 1;
+        const Planes Sm = seg_at(buf, m), Sn = seg_at(buf, m + 1);
+        if (((j - 1) & 1) == 0)
+            each([&](const auto& b) { adj_replay_dual(b, N, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, tau, inv_theta); });
+        else
+            each([&](const auto& b) {
+                adj_replay_primal(b, N, Sn.p1, Sn.p2, Sm.v, Sn.v, Sn.w, theta, inv_theta);
+            });
+    };
+    // Phase j of the walk back through segment k in buffer buf: 0, phase A
+    // of its last step (clip, u^{n+1}; phase A only touches the pixel itself,
+    // so for the other steps it runs at the end of phase C of the step
+    // after); then phases B and C of each step m, last to first.
+    //   B: qbar = pbar + theta grad ubar, the fixed-point step;
+    //   C: wbar = -div gbar at x, x+e1, x+e2; pbar, vbar of iterate m; then
+    //      the next step's phase A (no other pixel's phase C reads ub).
+    auto reverse_phase = [&](int k, int buf, int j) {
+        const int M = seg_len(k);
+        if (j == 0) {
+            const bool last = k * ckpt_every + M == iters;
+            const float* vM = seg_at(buf, M).v;
             for (int a = a0 + tid; a < a1; a += nt) {
                 const float vn = vM[a];
                 const float sb = (vn > 0.f && vn < 1.f) ? A.vb[a] : 0.f;
                 A.ub[a] = sb + (last ? A.gu[a] : 0.f);
                 A.fb[a] -= sb;
             }
+            return;
         }
-        if (!grid_sync(h, nblocks, gen)) return;
-        // B: qbar = pbar + theta grad ubar, the fixed-point step
-        auto b_op = [&](int m) {
-            const Planes Sm = seg_at(m), Sn = seg_at(m + 1);
-            return [=](const auto& b) {
+        const int m = M - 1 - ((j - 1) >> 1);
+        const Planes Sm = seg_at(buf, m), Sn = seg_at(buf, m + 1);
+        if (((j - 1) & 1) == 0)
+            each([&](const auto& b) {
                 adj_phase_b(b, N, A.ub, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, A.p1b, A.p2b, A.gb1, A.gb2, A.pd1,
                             A.pd2, theta, tau, inv_theta);
-            };
-        };
-        // C: wbar = -div gbar at x, x+e1, x+e2; pbar, vbar of iterate n;
-        // then the next step's phase A (no other pixel's phase C reads ub)
-        auto c_op = [&](int m) {
-            const Planes Sm = seg_at(m);
-            return [=](const auto& b) {
+            });
+        else
+            each([&](const auto& b) {
                 adj_phase_c(b, N, A.gb1, A.gb2, A.pd1, A.pd2, Sm.v, A.p1b, A.p2b, A.vb, A.ub, A.fb, m > 0,
                             inv_theta);
-            };
-        };
-        for (int m = M - 1; m >= 0; --m) {
-            each(b_op(m));
+            });
+    };
+    const int lastk = nseg - 1;
+    if constexpr (SM) {
+        // The replay of segment k - 1 runs in step with the walk back
+        // through segment k (the two touch disjoint arrays: the other
+        // segment buffer and the checkpoints; the adjoint arrays), so each
+        // grid barrier serves one phase of each; the last segment's replay
+        // runs alone first.
+        for (int j = 0; j < 2 * seg_len(lastk) + 1; ++j) {
+            replay_phase(lastk, lastk & 1, j);
             if (!grid_sync(h, nblocks, gen)) return;
-            each(c_op(m));
+        }
+        for (int k = lastk; k >= 0; --k) {
+            const int lr = 2 * seg_len(k) + 1, lp = k > 0 ? 2 * seg_len(k - 1) + 1 : 0;
+            for (int j = 0; j < max(lr, lp); ++j) {
+                if (j < lr) reverse_phase(k, k & 1, j);
+                if (j < lp) replay_phase(k - 1, (k - 1) & 1, j);
+                if (!grid_sync(h, nblocks, gen)) return;
+            }
+        }
+    } else {
+        // one segment at a time: its replay, then the walk back through it
+        // (with the tables in global memory, two phases' loads between
+        // barriers cost more than the barriers saved)
+        for (int k = lastk; k >= 0; --k) {
+            const int M = seg_len(k);
+            replay_phase(k, 0, 0);
             if (!grid_sync(h, nblocks, gen)) return;
+            for (int m = 0; m < M; ++m) {
+                const Planes Sm = seg_at(0, m), Sn = seg_at(0, m + 1);
+                each([&](const auto& b) {
+                    adj_replay_dual(b, N, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, tau, inv_theta);
+                });
+                if (!grid_sync(h, nblocks, gen)) return;
+                each([&](const auto& b) {
+                    adj_replay_primal(b, N, Sn.p1, Sn.p2, Sm.v, Sn.v, Sn.w, theta, inv_theta);
+                });
+                if (!grid_sync(h, nblocks, gen)) return;
+            }
+            reverse_phase(k, 0, 0);
+            if (!grid_sync(h, nblocks, gen)) return;
+            for (int m = M - 1; m >= 0; --m) {
+                const Planes Sm = seg_at(0, m), Sn = seg_at(0, m + 1);
+                each([&](const auto& b) {
+                    adj_phase_b(b, N, A.ub, Sm.p1, Sm.p2, Sm.w, Sn.p1, Sn.p2, A.p1b, A.p2b, A.gb1, A.gb2,
+                                A.pd1, A.pd2, theta, tau, inv_theta);
+                });
+                if (!grid_sync(h, nblocks, gen)) return;
+                each([&](const auto& b) {
+                    adj_phase_c(b, N, A.gb1, A.gb2, A.pd1, A.pd2, Sm.v, A.p1b, A.p2b, A.vb, A.ub, A.fb, m > 0,
+                                inv_theta);
+                });
+                if (!grid_sync(h, nblocks, gen)) return;
+            }
         }
     }
     // v0 = clip(u0 - F): its clipped value is in checkpoint 0
@@ -2721,10 +2769,13 @@ constexpr size_t kAdjSmemBytes = (size_t)kAdjSmemPixels * (4 * ADJ_ROWS + 4);
 
 // SM: the block's neighbour-table rows and theta lambda f are copied into
 // shared memory first (the launch gives kAdjSmemBytes, and every block's
-// share of the largest possible RD fits); else they are read from the global
-// table.  Two kernels, so that each gets its own register allocation.
+// share of the largest possible RD fits), the replay of one segment runs in
+// step with the walk back through the next later one, and blocks have
+// kBackwardThreadsSm threads; else the tables are read from the global
+// table, one segment at a time, in kBackwardThreads-thread blocks.  Two
+// kernels, so that each gets its own register allocation.
 template <bool SM>
-__global__ void __launch_bounds__(kBackwardThreads, kBackwardMinBlocks)
+__global__ void __launch_bounds__(SM ? kBackwardThreadsSm : kBackwardThreads, kBackwardMinBlocks)
 k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
                    const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
                    const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
@@ -2940,7 +2991,7 @@ extern "C" size_t seg_ckpt_bytes(int64_t capacity, int iters, int ckpt_every) {
 
 extern "C" size_t seg_backward_scratch_bytes(int64_t capacity, int ckpt_every) {
     const int64_t st = compact_stride(capacity);
-    return (adj_float_arrays() + 4 * (size_t)(std::max(ckpt_every, 1) + 1)) * 4 * (size_t)st + 16 * 256;
+    return (adj_float_arrays() + 8 * (size_t)(std::max(ckpt_every, 1) + 1)) * 4 * (size_t)st + 16 * 256;
 }
 
 extern "C" seg_status seg_solve_diff(const float* f, int H, int W, int ld, const uint32_t* act,
@@ -3013,6 +3064,7 @@ static seg_status backward_batch(const seg_params* prm, const BatchDesc& B, cons
     float** fields[] = {&A.p1b, &A.p2b, &A.vb, &A.ub, &A.gb1, &A.gb2, &A.pd1, &A.pd2, &A.fb, &A.gu, &A.gv};
     for (size_t k = 0; k < adj_float_arrays(); ++k) *fields[k] = sc + k * stride;
     A.seg = sc + adj_float_arrays() * stride;
+    A.seg2 = A.seg + 4 * (int64_t)(ckpt_every + 1) * stride;
     int64_t pixels = 0;
     for (int k = 0; k < B.n; ++k) {
         const BatchImage& I = B.img[k];
@@ -3031,12 +3083,13 @@ static seg_status backward_batch(const seg_params* prm, const BatchDesc& B, cons
     const void* ks = (const void*)k_backward_compact<true>;
     SEG_TRY_CUDA(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes));
     int per_sm = 0;
-    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks, kBackwardThreads, kAdjSmemBytes));
+    SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks, kBackwardThreadsSm, kAdjSmemBytes));
     if (per_sm <= 0) return fail(SEG_ERR_CUDA, "k_backward_compact cannot be resident");
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(),
-                                      std::max<int64_t>(1, (most + kBackwardThreads - 1) / kBackwardThreads));
+                                      std::max<int64_t>(1, (most + kBackwardThreadsSm - 1) / kBackwardThreadsSm));
     const bool use_smem = (most + grid - 1) / grid <= kAdjSmemPixels;
     const void* kern = use_smem ? ks : (const void*)k_backward_compact<false>;
+    const int threads = use_smem ? kBackwardThreadsSm : kBackwardThreads;
     if (!use_smem) {
         int pg = 0;
         SEG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pg, kern, kBackwardThreads, 0));
@@ -3051,7 +3104,7 @@ static seg_status backward_batch(const seg_params* prm, const BatchDesc& B, cons
     const int32_t* cnt = totals;
     void* args[] = {&P, &iters, &ce, (void*)&cnt, (void*)&nbp, &stride, (void*)&F, (void*)&ck, &A, &h};
     if (iters > 0) {
-        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kBackwardThreads), args, smem, s));
+        SEG_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, smem, s));
         count_launch();
         if (debug_mode()) SEG_TRY(after_launch("persistent solve"));
     }
