@@ -444,7 +444,8 @@ __device__ __forceinline__ float g_comp(int n, float wn, float pa, float pb, flo
 //  * everything in global memory.
 constexpr int kBackwardThreads = 1024;  // block size of the persistent reverse sweep (tables in global memory)
 constexpr int kBackwardThreadsSm = 512;  // block size of the sweep with its tables in shared memory
-constexpr int kBackwardMinBlocks = 2;   // resident blocks per SM the registers are sized for
+constexpr int kBackwardMinBlocks = 2;   // resident blocks per SM the registers are sized for (global tables)
+constexpr int kBackwardMinBlocksSm = 2;   // the same, tables in shared memory
 constexpr int kBackwardUnroll = 1;      // pixels per thread whose loads are in flight together
 // dynamic shared memory of the persistent solver: one or two blocks per SM
 constexpr size_t compact_smem(int nt) { return nt == 1024 ? 226 * 1024 : 112 * 1024; }
@@ -2381,8 +2382,8 @@ __device__ __forceinline__ double block_sum1(double x, double* s_red) {
 // (indexed from the block's first pixel a0), so that the first load of each
 // phase's dependent chain is a shared-memory load; else the global table.
 enum { ADJ_U = 0, ADJ_L, ADJ_D, ADJ_R, ADJ_DL, ADJ_UR, ADJ_ROWS };
-// pixels a block can keep (28 bytes each) at kBackwardMinBlocks blocks per SM
-constexpr int kAdjSmemPixels = (225 * 1024 / kBackwardMinBlocks - 2048) / 28 / 32 * 32;
+// pixels a block can keep (28 bytes each) at kBackwardMinBlocksSm blocks per SM
+constexpr int kAdjSmemPixels = (225 * 1024 / kBackwardMinBlocksSm - 2048) / 28 / 32 * 32;
 __host__ __device__ constexpr int adj_table_row(int k) {
     return k == ADJ_U ? NB_UP : k == ADJ_L ? NB_LEFT : k == ADJ_D ? NB_DOWN : k == ADJ_R ? NB_RIGHT
          : k == ADJ_DL ? NB_DOWNLEFT : NB_UPRIGHT;
@@ -2763,7 +2764,7 @@ __device__ __forceinline__ void adj_sweep(const IterParams& P, int iters, int ck
 }
 
 // Shared memory of one block: the six neighbour-table rows and theta lambda
-// f of up to kAdjSmemPixels pixels, sized for kBackwardMinBlocks blocks per
+// f of up to kAdjSmemPixels pixels, sized for kBackwardMinBlocksSm blocks per
 // SM.
 constexpr size_t kAdjSmemBytes = (size_t)kAdjSmemPixels * (4 * ADJ_ROWS + 4);
 
@@ -2775,7 +2776,7 @@ constexpr size_t kAdjSmemBytes = (size_t)kAdjSmemPixels * (4 * ADJ_ROWS + 4);
 // table, one segment at a time, in kBackwardThreads-thread blocks.  Two
 // kernels, so that each gets its own register allocation.
 template <bool SM>
-__global__ void __launch_bounds__(SM ? kBackwardThreadsSm : kBackwardThreads, kBackwardMinBlocks)
+__global__ void __launch_bounds__(SM ? kBackwardThreadsSm : kBackwardThreads, SM ? kBackwardMinBlocksSm : kBackwardMinBlocks)
 k_backward_compact(IterParams P, int iters, int ckpt_every, const int32_t* __restrict__ counts,
                    const int32_t* __restrict__ nb, int64_t stride, const float* __restrict__ F,
                    const float* __restrict__ ckpt, AdjArrays A, WsHeader* h) {
