@@ -23,6 +23,7 @@
 // only); the stopping test, the header fields and the stats are those of the
 // other compact paths.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 #include "iterate.cuh"
@@ -279,8 +280,11 @@ __device__ __forceinline__ void rm_dual(const IterParams& P, const RowMajorState
         float q1, q2;
         chambolle_update(p1[k], p2[k], g1, g2, P.tau, q1, q2);
         const uint32_t rnd = mix32((uint32_t)a[k] * 3u + seed);
+        // bf16 rounding takes the low 16 bits of its word, so one hash serves
+        // both components there (its high half for p2)
+        const uint32_t rnd2 = std::is_same<T, __nv_bfloat16>::value ? rnd >> 16 : mix32(rnd ^ 0x9e3779b9u);
         Store<T>::st_sr(P1o, a[k], q1, rnd);
-        Store<T>::st_sr(P2o, a[k], q2, mix32(rnd ^ 0x9e3779b9u));
+        Store<T>::st_sr(P2o, a[k], q2, rnd2);
     }
 }
 
