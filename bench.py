@@ -50,7 +50,7 @@ BYTES_PER_ACTIVE_ITER = {"f32": 28, "bf16": 16, "f16": 16}   # read p1,p2,v,f + 
 #    (20 iterations; each wave's state is loaded once into shared memory).
 COMPACT_DRAM_BYTES_PER_ITER = {("ds2048", "f32"): (38689280 + 530176) / 50,
                                ("poly4096_0.1", "f32"): (119940864 + 578539264) / 20,
-                               ("poly4096_0.1", "bf16"): (58752000 + 41105408) / 20,
+                               ("poly4096_0.1", "bf16"): (58861824 + 42755328) / 20,
                                ("batch", "f32"): (204280832 + 71778048) / 20}
 
 
