@@ -37,10 +37,12 @@ def _f(H, W, seed):
     return (0.8 * P.z - 0.4).astype(np.float32)
 
 
-@pytest.mark.parametrize("shape,delta", [((96, 130), 0.15), ((2048, 1024), math.inf)])
+@pytest.mark.parametrize("shape,delta", [((96, 130), 0.15), ((2048, 1024), math.inf), ((4096, 2048), math.inf)])
 def test_compact_solve_times_out_and_recovers(orc, shape, delta):
     """(96 x 130, delta 0.15): the shared-memory one-barrier path; (2048 x
-    1024, full domain, 2.1 M RD pixels): the global-memory wide kernel."""
+    1024, full domain, 2.1 M RD pixels): the row-major solve with its
+    neighbourhoods in shared memory; (4096 x 2048, full domain, 8.4 M RD
+    pixels): the row-major solve launched without shared memory."""
     seg = seg_mod()
     H, W = shape
     f = _f(H, W, 3)
@@ -94,6 +96,44 @@ def test_primal_dual_and_volume_solves_time_out(orc):
     VS.solve(2.0, iters=20)
     torch.cuda.synchronize()
     VS.check_status()
+    # the full volume: the one-voxel kernel (RD above half the volume)
+    VS.domain(delta=math.inf)
+    seg.seg_set_wait_limit(VS.ws, SHORT, 2, VS.stream)
+    VS.solve(2.0, iters=20)
+    torch.cuda.synchronize()
+    _expect_timeout(VS.check_status)
+    seg.seg_set_wait_limit(VS.ws, 0, 0, VS.stream)
+    VS.solve(2.0, iters=20)
+    torch.cuda.synchronize()
+    VS.check_status()
+
+
+def test_reverse_sweep_times_out_and_recovers(orc):
+    """The adjoint's persistent sweep (its shared-memory kernel at this
+    size): the barrier wait runs out, the status says so, and a second
+    backward on the same forward state matches the oracle's reverse mode."""
+    seg = seg_mod()
+    rng = np.random.default_rng(8)
+    H, W, K, C = 48, 64, 30, 10
+    f = _f(H, W, 6)
+    gu = rng.normal(size=(H, W))
+    S = seg.DiffSolver(H, W, K, C)
+    S.f[:, :W].copy_(torch.from_numpy(f))
+    S.domain(delta=0.2)
+    S.solve_diff(1.0)
+    g = seg.upload(gu.astype(np.float32))
+    seg.seg_set_wait_limit(S.ws, SHORT, 1, S.stream)
+    S.backward(g)
+    torch.cuda.synchronize()
+    _expect_timeout(S.check_status)
+    seg.seg_set_wait_limit(S.ws, 0, 0, S.stream)
+    gf, gout = S.backward(g)
+    torch.cuda.synchronize()
+    S.check_status()
+    gf_o, gl_o = orc.solve_grad(f, orc.domain(f, 0.2), 1.0, gu, None, iters=K)
+    gf = seg.download(gf).astype(np.float64)
+    assert np.linalg.norm(gf - gf_o) <= 1e-3 * np.linalg.norm(gf_o)
+    assert abs(gout.cpu().numpy()[0] - gl_o) <= 1e-3 * max(1.0, abs(gl_o))
 
 
 def test_batch_solve_times_out_and_recovers(orc):
