@@ -149,3 +149,33 @@ def test_polygons_4096_stopping_test_on_the_row_major_path(orc, storage):
     b = run_gpu(f, delta=0.1, lam=1.0, iters=n, check_every=10, storage=storage)
     for k in ("u", "v", "p1", "p2"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+@pytest.mark.parametrize("which,delta", [("ds2048", 0.3), ("ds2048", 0.5), ("poly4096", math.inf)])
+def test_warm_start_on_the_row_major_path(orc, which, delta):
+    """Warm start on the row-major solve (the 2048^2 image at delta 0.3: each
+    block's neighbourhoods and theta lambda f in shared memory; at 0.5: its
+    neighbourhoods alone; the 4096^2 full domain: the launch without shared
+    memory): 20 iterations, then 20 more from the returned state, against 40
+    cold iterations."""
+    import torch
+    seg = seg_mod()
+    f = _ds2048() if which == "ds2048" else _poly4096()
+    H, W = f.shape
+    S = seg.Solver(H, W, tile_h=32 if which == "ds2048" else 16, mode="compact")
+    S.f[:, :W].copy_(torch.from_numpy(f))
+    S.domain(delta=delta)
+    lam = 2.0 if which == "ds2048" else 1.0
+
+    def state():
+        torch.cuda.synchronize()
+        S.check_status()
+        return {k: seg.download(getattr(S, k)).astype(np.float64) for k in ("u", "v", "p1", "p2")}
+
+    S.solve(lam, iters=40)
+    cold = state()
+    S.solve(lam, iters=20)
+    S.solve(lam, iters=20, warm_start=True)
+    warm = state()
+    for k in cold:
+        assert np.max(np.abs(warm[k] - cold[k])) <= 1e-5, k
