@@ -13,18 +13,20 @@
 //     (or U0 when x - e1 is fixed), whenever those pixels are in RD;
 // and the whole neighbourhood of a pixel is two 16-bit offsets and a 16-bit
 // word of flags (6 bytes, against the 24 of the six-row int32 table of the
-// tile-major order).  With the table that small the iteration's arrays (the
-// state, w, theta lambda f and the offsets) fit in L2 for images like the
-// 4096^2 precision workload, so the two phases of an iteration (dual step,
-// grid barrier, primal step, grid barrier) stream them from L2, not DRAM.
-// The arithmetic and rounding of every step are those of dual_one /
-// primal_one in solve.cu (the 16-bit stores' random words are drawn from the
-// compact index, as there, so 16-bit results differ in the rounding noise
+// tile-major order).  Each block keeps its pixels' neighbourhoods (and theta
+// lambda f, while they fit with it) in shared memory for the whole launch,
+// and the rest of the iteration's arrays (both p buffers, w, v) stay in L2
+// for images like the 4096^2 precision workload, so the two phases of an
+// iteration (dual step, grid barrier, primal step, grid barrier) take one L2
+// round trip each.  The arithmetic and rounding of every step are those of
+// dual_one / primal_one in solve.cu (the 16-bit stores' random words are
+// drawn from the compact index, as there, and at bf16 both components of p'
+// take halves of one word, so 16-bit results differ in the rounding noise
 // only); the stopping test, the header fields and the stats are those of the
 // other compact paths.
 #include <algorithm>
-#include <type_traits>
 #include <cmath>
+#include <type_traits>
 
 #include "iterate.cuh"
 
